@@ -1,0 +1,188 @@
+/*
+ * fmbem.h -- C ABI of the GB300 (sm_103a) fast-multipole boundary-element library for 3-D
+ * electromagnetic scattering by homogeneous scatterers, after Wang, Zheng, Xiao, Lin & Chan,
+ * "Fast multipole boundary element method for three dimensional electromagnetic scattering
+ * problem" (arXiv 1211.7177).
+ *
+ * The library applies the Nystrom-discretised electric-field integral-equation operator of
+ * Eqs. (2.9)-(2.13),  [Gamma Lambda][Phi; Psi] = Phi_inc,  with the fast multipole method of
+ * Section 2.2 (octree of Appendix C, P2M Eqs. (2.18)-(2.19), M2M Eq. (2.20), M2L + L2L
+ * Eq. (2.21), L2P + near field Eqs. (2.22)-(2.23), analytic self terms of Appendix B), and solves
+ * the system with right-preconditioned GMRES, Eq. (3.1), using the block-diagonal
+ * preconditioner M = A_self of Eq. (3.2).  Every numerical step runs in CUDA kernels on the
+ * device; the host only validates input, sequences launches and runs the (m x m) Hessenberg
+ * recurrences of GMRES.
+ *
+ * Conventions shared by every entry point
+ *   - Time factor exp(-i omega t) (Section 2.1).  Relative permittivity eps_d and permeability
+ *     mu_d per domain d: d = 0 is the background, d = 1..J the scatterers.  The wavenumber of
+ *     domain d is k_d = k0 sqrt(eps_d mu_d), the root with Im k_d >= 0; T_j and gamma_j follow
+ *     Eq. (2.13) with eps_0, mu_0 the background's relative values.
+ *   - Nystrom nodes (one-point rule, Eq. 2.8): CENTROID mode uses triangle centroids weighted
+ *     by the triangle area (the paper's "simplest case"); VERTEX mode uses mesh vertices weighted
+ *     by one third of the incident triangle areas, with the area-weighted vertex normal.
+ *   - A vector of unknowns or results holds, per right-hand side and per node in USER order
+ *     (vertex order in VERTEX mode, triangle order in CENTROID mode), 6 complex numbers as
+ *     interleaved (re, im) doubles: layout [n_rhs][N][6] complex128.  Unknowns per node are
+ *     (Phi_x, Phi_y, Phi_z, Psi_x, Psi_y, Psi_z) with Phi = E_0 and Psi = n x curl E_0 for the
+ *     scatterer's outward normal n (Eq. 2.12); results per node are (background equation x,y,z,
+ *     scatterer equation x,y,z).
+ *   - Device pointers are plain CUDA device addresses (for example torch.Tensor.data_ptr()),
+ *     read or written only during the call and in the order of the given stream; the stream
+ *     argument is a cudaStream_t (NULL = legacy default stream).  The caller keeps ownership
+ *     of every buffer it passes.
+ *   - Every entry point returns an fmbem_status and never throws; fmbem_last_error() gives a
+ *     message for the last failure on a handle.  A handle must not be used by two host threads
+ *     or two streams at the same time.
+ */
+#ifndef FMBEM_H
+#define FMBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMBEM_OK = 0,
+    FMBEM_ERR_INVALID_ARGUMENT = 1, /* a NULL pointer, a non-positive size, an unknown option  */
+    FMBEM_ERR_INVALID_MESH = 2,     /* mesh not usable: see fmbem_create                       */
+    FMBEM_ERR_OOM = 3,              /* a device allocation failed                              */
+    FMBEM_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed             */
+    FMBEM_ERR_NOT_CONVERGED = 5,    /* fmbem_solve reached max_iter above the tolerance        */
+    FMBEM_ERR_BREAKDOWN = 6         /* GMRES produced a non-finite value                       */
+} fmbem_status;
+
+typedef enum { FMBEM_NODES_VERTEX = 0, FMBEM_NODES_CENTROID = 1 } fmbem_node_mode;
+
+/* Arithmetic of the near-field and far-field passes.  FP64: everything in double precision.
+ * FP32: P2P, P2M, M2M, M2L, L2L and L2P in single precision (double-float node positions),
+ * with the analytic self blocks, the final accumulation of every result and the GMRES vectors
+ * in double precision. */
+typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1 } fmbem_precision;
+
+typedef struct { double re, im; } fmbem_c64;
+
+/* Closed, consistently oriented triangle mesh.  vertices [n_vertices][3] and triangles
+ * [n_triangles][3] (counter-clockwise seen from outside, so (B-A) x (C-A) points out of the
+ * scatterer) and tri_domain [n_triangles] (scatterer ids 1..n_scatterers) are HOST arrays. */
+typedef struct {
+    int64_t n_vertices;
+    const double *vertices;
+    int64_t n_triangles;
+    const int32_t *triangles;
+    const int32_t *tri_domain;
+    int32_t n_scatterers;
+} fmbem_mesh;
+
+/* Options; fmbem_default_options() fills the defaults given in brackets. */
+typedef struct {
+    int node_mode;           /* fmbem_node_mode [VERTEX]                                         */
+    int p;                   /* truncation number p of Eq. (2.17): degrees n = 0..p-1 [8]         */
+    int leaf_size;           /* the octree is refined (Appendix C) until no leaf holds more than
+                                leaf_size nodes, l_max >= 2 [64]                                 */
+    int max_level;           /* upper bound on l_max [10]                                         */
+    int gmres_restart;       /* GMRES restart length m [50]                                       */
+    int solve_precision;     /* fmbem_precision used by fmbem_solve's Krylov iterations [FP64];
+                                with FP32 the solve is refined: outer true residuals with the FP64
+                                operator, inner GMRES with the FP32 operator                      */
+    double inner_tol;        /* relative tolerance of each inner FP32 solve [1e-2]                */
+    int profile_phases;      /* non-zero: record CUDA events around the matvec phases so that
+                                fmbem_last_matvec_times can report them [0]                       */
+} fmbem_options;
+
+void fmbem_default_options(fmbem_options *opt);
+
+typedef struct fmbem fmbem;  /* opaque handle */
+
+/* Builds everything that depends on geometry and frequency, Sections 2.1-2.2 and Appendices
+ * B-C: nodes, weights and normals (Eq. 2.8); the self-patch integrals of Appendix B (Eqs.
+ * B.2-B.9) on a planar patch around each node -- the triangle itself for CENTROID nodes, the
+ * barycentric dual cell projected on the node's tangent plane for VERTEX nodes -- and the 6x6
+ * preconditioner blocks A_self (Eq. 3.2) with their LU factors; the octree with
+ * Children/Parent/Neighbor/FF lists (Appendix C); the multipole bases and the S|S, S|R, R|R
+ * translation matrices for every level and domain wavenumber (Eqs. 2.14-2.21).
+ *   mesh        host mesh, copied; the caller keeps it.  Rejected with FMBEM_ERR_INVALID_MESH
+ *               when an index is out of range, a triangle is degenerate, a domain id is outside
+ *               1..n_scatterers, an edge is not shared by exactly two triangles of opposite
+ *               orientation, or (VERTEX mode) a vertex is unused or touches two scatterers.
+ *   eps, mu     host arrays [n_scatterers + 1] of relative permittivity / permeability,
+ *               index 0 = background; mu must be non-zero, eps non-zero.
+ *   k0          vacuum wavenumber (> 0).
+ *   opt         options, NULL = defaults.
+ *   stream      cudaStream_t for the set-up kernels (the call synchronises it before returning).
+ *   out         receives the handle (NULL on failure).  The handle owns all device memory it
+ *               allocates; fmbem_destroy frees it. */
+fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
+                          const fmbem_options *opt, void *stream, fmbem **out);
+
+void fmbem_destroy(fmbem *h);
+
+/* Message of the last failure on this handle ("" if none); NULL handle: last fmbem_create
+ * failure of the calling thread. */
+const char *fmbem_last_error(const fmbem *h);
+
+/* Number of Nystrom nodes N (a vector holds 6N complex numbers per right-hand side). */
+int64_t fmbem_num_nodes(const fmbem *h);
+
+/* Node positions [N][3], outward normals [N][3] and weights [N], host arrays in user order
+ * (any of them may be NULL).  Eq. (2.8). */
+fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, double *weight);
+
+/* Octree summary: l_max, number of leaves, total number of boxes on levels 2..l_max, and the
+ * number of near-field (source, target) node pairs and of far-field box pairs (S|R
+ * translations) per domain.  Any pointer may be NULL. */
+fmbem_status fmbem_tree_info(const fmbem *h, int32_t *l_max, int64_t *n_leaves, int64_t *n_boxes,
+                             int64_t *near_pairs, int64_t *ff_pairs);
+
+/* Right-hand sides of Eq. (2.9) for plane waves E_inc = e exp(i k_0 d . r) (Eq. 2.12,
+ * Phi_inc): e in the background rows, 0 in the scatterer rows (no incident field inside).
+ *   dir   host [n_rhs][3] unit propagation directions; pol host [n_rhs][3] complex polarisations.
+ *   b_dev device [n_rhs][N][6] complex128, written. */
+fmbem_status fmbem_plane_wave_rhs(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, void *b_dev,
+                                  void *stream);
+
+/* y = A x for the operator of Eq. (2.9), evaluated as in Section 2.2: far field by the fast
+ * multipole passes (Eqs. 2.18-2.21, L2P of Eq. 2.23), near field by direct one-point sums over
+ * the node's own leaf and its Neighbor leaves (Eq. 2.23), self blocks analytically
+ * (Appendix B).
+ *   x_dev, y_dev  device [n_rhs][N][6] complex128 (user order); x is read, y written; they
+ *                 must not overlap.
+ *   precision     fmbem_precision of the passes (see above).
+ * Scratch (expansion coefficients, source densities) is owned by the handle and grown on
+ * demand, so the first call with a larger n_rhs allocates. */
+fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision, void *stream);
+
+/* Solves A x = b (Eq. 2.9) by right-preconditioned restarted GMRES (Eq. 3.1) with the
+ * block-diagonal preconditioner M = A_self (Eq. 3.2) applied exactly (6x6 LU per node), each
+ * right-hand side in its own Krylov space, all right-hand sides batched through one matvec per
+ * iteration.  Arnoldi orthogonalisation (classical Gram-Schmidt applied twice) and the true
+ * residual ||b - A x|| / ||b|| are computed in double precision; convergence is declared on
+ * the true residual.  With solve_precision = FP32 the solve is iteratively refined: each outer
+ * step computes the true residual with the FP64 operator and solves the correction with the
+ * FP32 operator to inner_tol.
+ *   b_dev    device [n_rhs][N][6] complex128, read.
+ *   x_dev    device [n_rhs][N][6] complex128: initial guess on entry, solution on exit.
+ *   tol      relative residual target (> 0); max_iter bounds the total number of Krylov
+ *            iterations (matvecs) per solve.
+ *   iters_host, relres_host  host [n_rhs]: iterations used and final true relative residual
+ *            (either may be NULL).
+ * Returns FMBEM_ERR_NOT_CONVERGED (x = last iterate) when a right-hand side stays above tol. */
+fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
+                         int32_t *iters_host, double *relres_host, void *stream);
+
+/* z = M^{-1} v with M = A_self (Eq. 3.2), per node 6x6 complex LU; v_dev, z_dev device
+ * [n_rhs][N][6] complex128 (may be the same buffer). */
+fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream);
+
+/* Wall-clock milliseconds of the phases of the last fmbem_matvec call, measured with CUDA
+ * events on its stream: [0] source densities + P2M, [1] M2M, [2] M2L + L2L, [3] near field
+ * + L2P + self, [4] total.  ms_host [5]. */
+fmbem_status fmbem_last_matvec_times(const fmbem *h, double *ms_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMBEM_H */

@@ -1,0 +1,275 @@
+"""GB300 (sm_103a) fast-multipole boundary-element method for 3-D electromagnetic scattering
+(after arXiv 1211.7177): Python binding of the C ABI in ``include/fmbem.h``.
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of ``libfmbem.so``.
+PyTorch provides device memory (complex128 tensors on ``cuda``) and the current stream.  There is
+no CPU fallback: importing works without a GPU, but every call needs the built library and a
+CUDA device, and fails loudly otherwise.
+
+The module-level functions carry the C names (``fmbem_create``, ``fmbem_matvec``, ...); ``FMBEM``
+wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "FMBEM", "load_library", "fmbem_default_options", "fmbem_create", "fmbem_destroy", "fmbem_last_error",
+    "fmbem_num_nodes", "fmbem_node_geometry", "fmbem_tree_info", "fmbem_plane_wave_rhs", "fmbem_matvec",
+    "fmbem_solve", "fmbem_precond_apply", "fmbem_last_matvec_times", "FP64", "FP32", "FMBEMError",
+]
+
+FP64, FP32 = 0, 1
+NODES_VERTEX, NODES_CENTROID = 0, 1
+STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_MESH", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED", 6: "BREAKDOWN"}
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fmbem.h")
+
+
+class FMBEMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fmbem {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("node_mode", ctypes.c_int), ("p", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("max_level", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("solve_precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("profile_phases", ctypes.c_int)]
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("vertices", ctypes.c_void_p), ("n_triangles", ctypes.c_int64),
+                ("triangles", ctypes.c_void_p), ("tri_domain", ctypes.c_void_p), ("n_scatterers", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load ``libfmbem.so`` (building it with nvcc first if needed); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is missing or stale; run paper_1211_7177_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "fmbem_default_options": (None, [ctypes.POINTER(Options)]),
+        "fmbem_create": (i32, [ctypes.POINTER(Mesh), P, P, dbl, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
+        "fmbem_destroy": (None, [P]),
+        "fmbem_last_error": (ctypes.c_char_p, [P]),
+        "fmbem_num_nodes": (i64, [P]),
+        "fmbem_node_geometry": (i32, [P, P, P, P]),
+        "fmbem_tree_info": (i32, [P, P, P, P, P, P]),
+        "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
+        "fmbem_matvec": (i32, [P, P, P, i64, i32, P]),
+        "fmbem_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
+        "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
+        "fmbem_last_matvec_times": (i32, [P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions():
+    """Names of the functions declared in include/fmbem.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmbem_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if isinstance(stream, int):          # a raw cudaStream_t value (0 = legacy default stream)
+        return ctypes.c_void_p(stream)
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(h, st):
+    if st != 0:
+        raise FMBEMError(st, fmbem_last_error(h))
+
+
+# ------------------------------------------------------------------ C-named thin wrappers
+def fmbem_default_options(**kw):
+    o = Options()
+    load_library().fmbem_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def fmbem_create(V, F, D, eps, mu, k0, options=None, stream=None):
+    """Returns a handle (ctypes void pointer).  V [nv,3] float64, F [nt,3] int32 (counter-clockwise
+    from outside), D [nt] int32 scatterer ids 1..J; eps, mu sequences of J+1 complex values."""
+    lib = load_library()
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    J = int(D.max())
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.complex128))
+    mu = np.ascontiguousarray(np.asarray(mu, dtype=np.complex128))
+    if len(eps) != J + 1 or len(mu) != J + 1:
+        raise ValueError("eps and mu need J+1 entries (background first)")
+    m = Mesh(len(V), V.ctypes.data, len(F), F.ctypes.data, D.ctypes.data, J)
+    h = ctypes.c_void_p()
+    opt = options if options is not None else fmbem_default_options()
+    st = lib.fmbem_create(ctypes.byref(m), _ptr(eps), _ptr(mu), float(k0), ctypes.byref(opt), _stream(stream),
+                          ctypes.byref(h))
+    if st != 0:
+        raise FMBEMError(st, lib.fmbem_last_error(None).decode())
+    return h
+
+
+def fmbem_destroy(h):
+    load_library().fmbem_destroy(h)
+
+
+def fmbem_last_error(h):
+    return load_library().fmbem_last_error(h).decode()
+
+
+def fmbem_num_nodes(h):
+    return int(load_library().fmbem_num_nodes(h))
+
+
+def fmbem_node_geometry(h):
+    N = fmbem_num_nodes(h)
+    pos, nrm, w = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros(N)
+    _check(h, load_library().fmbem_node_geometry(h, _ptr(pos), _ptr(nrm), _ptr(w)))
+    return pos, nrm, w
+
+
+def fmbem_tree_info(h):
+    lm = ctypes.c_int32()
+    nl, nb, npairs, nff = (ctypes.c_int64() for _ in range(4))
+    _check(h, load_library().fmbem_tree_info(h, ctypes.byref(lm), ctypes.byref(nl), ctypes.byref(nb),
+                                             ctypes.byref(npairs), ctypes.byref(nff)))
+    return dict(l_max=lm.value, n_leaves=nl.value, n_boxes=nb.value, near_pairs=npairs.value, ff_pairs=nff.value)
+
+
+def _dev(t, N, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if t.dim() != 3 or t.shape[1] != N or t.shape[2] != 6:
+        raise ValueError(f"{name} must have shape [n_rhs, {N}, 6]")
+    return t
+
+
+def fmbem_plane_wave_rhs(h, dirs, pols, out=None, stream=None):
+    import torch
+    N = fmbem_num_nodes(h)
+    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    pols = np.ascontiguousarray(np.atleast_2d(pols), dtype=np.complex128)
+    n = len(dirs)
+    b = out if out is not None else torch.empty((n, N, 6), dtype=torch.complex128, device="cuda")
+    _check(h, load_library().fmbem_plane_wave_rhs(h, n, _ptr(dirs), _ptr(pols), ctypes.c_void_p(b.data_ptr()),
+                                                   _stream(stream)))
+    return b
+
+
+def fmbem_matvec(h, x, y=None, precision=FP64, stream=None):
+    import torch
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    y = torch.empty_like(x) if y is None else _dev(y, N, "y")
+    _check(h, load_library().fmbem_matvec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                          x.shape[0], int(precision), _stream(stream)))
+    return y
+
+
+def fmbem_solve(h, b, x=None, tol=1e-6, max_iter=1000, stream=None, raise_on_failure=False):
+    """Returns (x, iters [n_rhs], relres [n_rhs], status)."""
+    import torch
+    N = fmbem_num_nodes(h)
+    b = _dev(b, N, "b")
+    x = torch.zeros_like(b) if x is None else _dev(x, N, "x")
+    n = b.shape[0]
+    it = np.zeros(n, dtype=np.int32)
+    rr = np.zeros(n)
+    st = load_library().fmbem_solve(h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), n, float(tol),
+                                    int(max_iter), _ptr(it), _ptr(rr), _stream(stream))
+    if st not in (0, 5) or (raise_on_failure and st != 0):
+        raise FMBEMError(st, fmbem_last_error(h))
+    return x, it, rr, st
+
+
+def fmbem_precond_apply(h, v, z=None, stream=None):
+    import torch
+    N = fmbem_num_nodes(h)
+    v = _dev(v, N, "v")
+    z = torch.empty_like(v) if z is None else _dev(z, N, "z")
+    _check(h, load_library().fmbem_precond_apply(h, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                                 v.shape[0], _stream(stream)))
+    return z
+
+
+def fmbem_last_matvec_times(h):
+    ms = np.zeros(5)
+    _check(h, load_library().fmbem_last_matvec_times(h, _ptr(ms)))
+    return dict(p2m=ms[0], m2m=ms[1], m2l_l2l=ms[2], near_l2p_self=ms[3], total=ms[4])
+
+
+class FMBEM:
+    """Owner of one handle: ``FMBEM(V, F, D, eps, mu, k0, p=8, ...)``."""
+
+    def __init__(self, V, F, D, eps, mu, k0, stream=None, **options):
+        self.options = fmbem_default_options(**options)
+        self.h = fmbem_create(V, F, D, eps, mu, k0, self.options, stream)
+        self.N = fmbem_num_nodes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fmbem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def node_geometry(self):
+        return fmbem_node_geometry(self.h)
+
+    def tree_info(self):
+        return fmbem_tree_info(self.h)
+
+    def plane_wave_rhs(self, dirs, pols, out=None, stream=None):
+        return fmbem_plane_wave_rhs(self.h, dirs, pols, out, stream)
+
+    def matvec(self, x, y=None, precision=FP64, stream=None):
+        return fmbem_matvec(self.h, x, y, precision, stream)
+
+    def solve(self, b, x=None, tol=1e-6, max_iter=1000, stream=None):
+        return fmbem_solve(self.h, b, x, tol, max_iter, stream)
+
+    def precond_apply(self, v, z=None, stream=None):
+        return fmbem_precond_apply(self.h, v, z, stream)
+
+    def last_matvec_times(self):
+        return fmbem_last_matvec_times(self.h)

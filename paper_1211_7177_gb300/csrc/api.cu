@@ -1,0 +1,247 @@
+// api.cu -- the C ABI of include/fmbem.h: argument checks, handle life cycle and error capture.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fmbem_internal.cuh"
+
+static thread_local std::string g_create_error;
+
+std::string cuda_msg(cudaError_t e, const char *what) {
+    return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+void *dev_alloc(fmbem *h, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw fmbem_error{FMBEM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+    }
+    h->allocations.push_back(p);
+    return p;
+}
+
+void dev_free(fmbem *h, void *p) {
+    if (!p) return;
+    auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
+    if (it != h->allocations.end()) {
+        *it = h->allocations.back();
+        h->allocations.pop_back();
+    }
+    cudaFree(p);
+}
+
+static void free_all(fmbem *h) {
+    for (void *p : h->allocations) cudaFree(p);
+    h->allocations.clear();
+    for (auto &e : h->ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+}
+
+// wraps a call: converts exceptions into a status and the handle's message
+template <typename F>
+static fmbem_status guarded(fmbem *h, F &&f) {
+    try {
+        f();
+        if (h) h->err.clear();
+        return FMBEM_OK;
+    } catch (const fmbem_error &e) {
+        if (h) h->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        if (h) h->err = "host allocation failed";
+        return FMBEM_ERR_OOM;
+    } catch (...) {
+        if (h) h->err = "unexpected C++ exception";
+        return FMBEM_ERR_CUDA;
+    }
+}
+
+static c64 root_with_nonneg_imag(c64 z) {
+    // principal square root, then the sign that gives Im >= 0
+    double r = cabsd(z);
+    double a = std::sqrt(std::max(0.0, 0.5 * (r + z.re)));
+    double b = std::sqrt(std::max(0.0, 0.5 * (r - z.re)));
+    if (z.im < 0) b = -b;
+    c64 s = {a, b};
+    if (s.im < 0 || (s.im == 0 && s.re < 0)) s = -s;
+    return s;
+}
+
+extern "C" {
+
+void fmbem_default_options(fmbem_options *o) {
+    if (!o) return;
+    o->node_mode = FMBEM_NODES_VERTEX;
+    o->p = 8;
+    o->leaf_size = 64;
+    o->max_level = 10;
+    o->gmres_restart = 50;
+    o->solve_precision = FMBEM_FP64;
+    o->inner_tol = 1e-2;
+    o->profile_phases = 0;
+}
+
+fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
+                          const fmbem_options *opt, void *stream, fmbem **out) {
+    if (out) *out = nullptr;
+    if (!mesh || !eps || !mu || !out || !mesh->vertices || !mesh->triangles || !mesh->tri_domain) {
+        g_create_error = "NULL argument";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    if (!(k0 > 0) || !std::isfinite(k0) || mesh->n_scatterers < 1 || mesh->n_scatterers > 64) {
+        g_create_error = "k0 must be positive and n_scatterers in 1..64";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    fmbem *h = new (std::nothrow) fmbem();
+    if (!h) { g_create_error = "host allocation failed"; return FMBEM_ERR_OOM; }
+    fmbem_default_options(&h->opt);
+    if (opt) h->opt = *opt;
+    const fmbem_options &o = h->opt;
+    if ((o.node_mode != FMBEM_NODES_VERTEX && o.node_mode != FMBEM_NODES_CENTROID) || o.p < 2 || o.p > 20 ||
+        o.leaf_size < 1 || o.max_level < 2 || o.gmres_restart < 1 || o.gmres_restart > 500 ||
+        (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1)) {
+        g_create_error = "invalid option value";
+        delete h;
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    fmbem_status st = guarded(h, [&] {
+        h->J = mesh->n_scatterers;
+        h->k0 = k0;
+        h->p = o.p;
+        h->p2 = o.p * o.p;
+        h->profile = o.profile_phases != 0;
+        h->eps.resize(h->J + 1);
+        h->mu.resize(h->J + 1);
+        h->k.resize(h->J + 1);
+        h->gam.resize(h->J + 1);
+        for (int d = 0; d <= h->J; ++d) {
+            h->eps[d] = {eps[d].re, eps[d].im};
+            h->mu[d] = {mu[d].re, mu[d].im};
+            if (!(cabsd(h->eps[d]) > 0) || !(cabsd(h->mu[d]) > 0) || !std::isfinite(eps[d].re + eps[d].im + mu[d].re + mu[d].im))
+                throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "eps and mu must be finite and non-zero"};
+            // Eq. (2.13): k_d = k0 sqrt(eps_d mu_d), gamma_d = mu_d / mu_0
+            h->k[d] = k0 * root_with_nonneg_imag(h->eps[d] * h->mu[d]);
+            h->gam[d] = d == 0 ? c64{1.0, 0.0} : cdiv(h->mu[d], h->mu[0]);
+        }
+        build_geometry(h, mesh, s);
+        build_tree(h, s);
+        build_tables(h, s);
+        std::vector<c64> dc(3 * (h->J + 1));
+        for (int d = 0; d <= h->J; ++d) {
+            dc[3 * d] = h->k[d];
+            dc[3 * d + 1] = d == 0 ? c64{0, 0} : cdiv(h->eps[0] - h->eps[d], h->eps[d]);
+            dc[3 * d + 2] = h->gam[d];
+        }
+        h->dcons = (c64 *)dev_alloc(h, sizeof(c64) * dc.size());
+        CK(cudaMemcpyAsync(h->dcons, dc.data(), sizeof(c64) * dc.size(), cudaMemcpyHostToDevice, s));
+        if (h->profile)
+            for (auto &e : h->ev) CK(cudaEventCreate(&e));
+        CK(cudaStreamSynchronize(s));
+    });
+    if (st != FMBEM_OK) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return FMBEM_OK;
+}
+
+void fmbem_destroy(fmbem *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+const char *fmbem_last_error(const fmbem *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t fmbem_num_nodes(const fmbem *h) { return h ? h->N : 0; }
+
+fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, double *weight) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (pos) std::memcpy(pos, h->h_pos.data(), sizeof(double) * 3 * h->N);
+    if (normal) std::memcpy(normal, h->h_nrm.data(), sizeof(double) * 3 * h->N);
+    if (weight) std::memcpy(weight, h->h_w.data(), sizeof(double) * h->N);
+    return FMBEM_OK;
+}
+
+fmbem_status fmbem_tree_info(const fmbem *h, int32_t *l_max, int64_t *n_leaves, int64_t *n_boxes, int64_t *near_pairs,
+                             int64_t *ff_pairs) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (l_max) *l_max = h->lmax;
+    if (n_leaves) *n_leaves = h->lev[h->lmax].n;
+    if (n_boxes) {
+        int64_t t = 0;
+        for (int l = 2; l <= h->lmax; ++l) t += h->lev[l].n;
+        *n_boxes = t;
+    }
+    if (near_pairs) *near_pairs = h->near_pairs;
+    if (ff_pairs) *ff_pairs = h->n_ff;
+    return FMBEM_OK;
+}
+
+fmbem_status fmbem_plane_wave_rhs(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, void *b_dev,
+                                  void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || !dir || !pol || !b_dev) { h->err = "invalid argument"; return FMBEM_ERR_INVALID_ARGUMENT; }
+    return guarded(h, [&] { run_plane_wave(h, n_rhs, dir, pol, (c64 *)b_dev, (cudaStream_t)stream); });
+}
+
+fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || !x_dev || !y_dev || x_dev == y_dev || (precision != FMBEM_FP64 && precision != FMBEM_FP32)) {
+        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64 or FP32)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] { run_matvec(h, (const c64 *)x_dev, (c64 *)y_dev, n_rhs, precision, (cudaStream_t)stream); });
+}
+
+fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
+                         int32_t *iters_host, double *relres_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || !b_dev || !x_dev || !(tol > 0) || max_iter < 1) {
+        h->err = "invalid argument";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    fmbem_status res = FMBEM_OK;
+    fmbem_status st = guarded(h, [&] {
+        res = run_solve(h, (const c64 *)b_dev, (c64 *)x_dev, n_rhs, tol, max_iter, iters_host, relres_host,
+                        (cudaStream_t)stream);
+    });
+    if (st != FMBEM_OK) return st;
+    if (res == FMBEM_ERR_NOT_CONVERGED) h->err = "GMRES did not reach the tolerance within max_iter";
+    if (res == FMBEM_ERR_BREAKDOWN) h->err = "GMRES produced a non-finite value";
+    return res;
+}
+
+fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || !v_dev || !z_dev) { h->err = "invalid argument"; return FMBEM_ERR_INVALID_ARGUMENT; }
+    return guarded(h, [&] { run_precond(h, (const c64 *)v_dev, (c64 *)z_dev, n_rhs, (cudaStream_t)stream); });
+}
+
+fmbem_status fmbem_last_matvec_times(const fmbem *h, double *ms) {
+    if (!h || !ms) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (!h->have_times) {
+        for (int i = 0; i < 5; ++i) ms[i] = 0;
+        return FMBEM_OK;
+    }
+    if (cudaEventSynchronize(h->ev[4]) != cudaSuccess) return FMBEM_ERR_CUDA;
+    float t;
+    for (int i = 0; i < 4; ++i) {
+        cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]);
+        ms[i] = t;
+    }
+    cudaEventElapsedTime(&t, h->ev[0], h->ev[4]);
+    ms[4] = t;
+    return FMBEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// fmbem_internal.cuh -- shared declarations of the GB300 FMM-BEM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fmbem.h"
+
+// ------------------------------------------------------------------------------------------
+// complex arithmetic on plain (re, im) pairs, usable for double and float
+template <typename R>
+struct cx {
+    R re, im;
+};
+using c64 = cx<double>;
+using c32 = cx<float>;
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, R s) { return {s * a.re, s * a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> &operator+=(cx<R> &a, cx<R> b) { a.re += b.re; a.im += b.im; return a; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> &operator-=(cx<R> &a, cx<R> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> conjg(cx<R> a) { return {a.re, -a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ R abs2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// a += b * c
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cx<R> &a, cx<R> b, cx<R> c) {
+    a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+    a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+__host__ __device__ __forceinline__ c64 cdiv(c64 a, c64 b) {
+    double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+__host__ __device__ __forceinline__ c64 cexpd(c64 z) {
+    double e = exp(z.re), s, c;
+    sincos(z.im, &s, &c);
+    return {e * c, e * s};
+}
+__host__ __device__ __forceinline__ double cabsd(c64 z) { return hypot(z.re, z.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> to(c64 a) { return {(R)a.re, (R)a.im}; }
+
+// ------------------------------------------------------------------------------------------
+// handle
+struct LevelInfo {
+    int64_t off = 0;  // first global box index of the level
+    int64_t n = 0;    // number of non-empty boxes
+    double w = 0;     // box width
+};
+
+struct DevBuf {  // owning device buffer
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct fmbem {
+    fmbem_options opt{};
+    std::string err;
+    cudaStream_t setup_stream = nullptr;
+
+    // problem
+    int64_t N = 0;
+    int J = 0;
+    double k0 = 0;
+    std::vector<c64> eps, mu, k, gam;  // [J+1]
+    int p = 0, p2 = 0;                 // truncation number and p^2 coefficients
+
+    // host copies of geometry (user order)
+    std::vector<double> h_pos, h_nrm, h_w;
+
+    // device geometry in user order (from the node set-up)
+    double *upos = nullptr, *unrm = nullptr, *uw = nullptr;  // [N][3], [N][3], [N]
+    int32_t *udom = nullptr;                                 // [N] scatterer id 1..J
+    // device geometry, sorted (Morton) order
+    int32_t *perm = nullptr;   // sorted -> user
+    int32_t *iperm = nullptr;  // user -> sorted
+    double *pos = nullptr, *nrm = nullptr, *w = nullptr;  // [N][3], [N][3], [N]
+    int32_t *dom = nullptr;                                // [N]
+    float *pos_hi = nullptr, *pos_lo = nullptr, *nrm_f = nullptr;  // [N][3]
+    // self blocks (user order): M = A_self [N][6][6], LU factors and pivots
+    c64 *Mself = nullptr, *Mlu = nullptr;
+    int8_t *piv = nullptr;
+
+    // octree (Appendix C)
+    int lmax = 0;
+    double root_min[3] = {0, 0, 0};
+    double root_w = 0;
+    std::vector<LevelInfo> lev;  // [lmax+1]
+    int64_t nbox = 0;            // total boxes, levels 0..lmax
+    uint64_t *box_key = nullptr; // [nbox] Morton key at its level
+    double *box_ctr = nullptr;   // [nbox][3]
+    int32_t *box_parent = nullptr;                        // [nbox] global index (-1 at level 0)
+    int32_t *box_cbeg = nullptr, *box_cend = nullptr;     // [nbox] children range (global)
+    int32_t *box_nbeg = nullptr, *box_nend = nullptr;     // [nbox] sorted-node range
+    int32_t *node_leaf = nullptr;                         // [N] global leaf box of each sorted node
+    int32_t *nbr_start = nullptr, *nbr_idx = nullptr;     // leaf-level CSR of Neighbor+self (global ids)
+    int32_t *ff_start = nullptr, *ff_src = nullptr;       // CSR of FF lists over global boxes
+    int16_t *ff_off = nullptr;                            // offset code 0..315 per FF entry
+    int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;
+    std::vector<int64_t> h_ff_count_level;
+
+    // multipole bases and translations, per domain d in 0..J
+    std::vector<double> lam;  // [(J+1)*(lmax+1)] scale lambda = |k_d| w_l
+    c64 *B_p2m64 = nullptr, *B_l2p64 = nullptr;   // [2][N][4][p2], [2][N][p2] (side 0 bg, 1 own)
+    c32 *B_p2m32 = nullptr, *B_l2p32 = nullptr;
+    c64 *T_m2l64 = nullptr, *T_mm64 = nullptr, *T_ll64 = nullptr;  // see tables.cu for layout
+    c32 *T_m2l32 = nullptr, *T_mm32 = nullptr, *T_ll32 = nullptr;
+
+    // scratch grown on demand
+    int64_t scratch_rhs = 0;
+    void *dens = nullptr;   // source densities
+    void *Cexp = nullptr;   // multipole coefficients [J+1][nbox][3 n_rhs][p2]
+    void *Dexp = nullptr;   // local coefficients
+    int scratch_prec = -1;
+
+    // solver scratch
+    int64_t solver_rhs = 0;
+    c64 *sv = nullptr;      // Krylov basis and work vectors
+    size_t sv_bytes = 0;
+    double *sdots = nullptr;
+    size_t sdots_bytes = 0;
+
+    // per-domain constants (k_d, t_d = (eps_0 - eps_d)/eps_d, gamma_d), device [J+1][3] c64
+    c64 *dcons = nullptr;
+
+    // timing
+    bool profile = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool have_times = false;
+
+    std::vector<void *> allocations;
+};
+
+// ------------------------------------------------------------------------------------------
+// helpers shared between translation units
+#define FMBEM_PI 3.14159265358979323846
+
+// layout of the translation tables, per domain d and level l (global matrix index):
+//   M2L  [d][l][316]  for l = 2..lmax (levels below 2 unused)
+//   M2M  [d][l][8]    child level l = 3..lmax, child octant o
+//   L2L  [d][l][8]    child level l = 3..lmax
+// each matrix p2 x p2 stored column-by-input: T[c][r] = coefficient from input c to output r.
+__host__ __device__ __forceinline__ int64_t m2l_matrix(int d, int l, int o, int lmax) {
+    return ((int64_t)d * (lmax + 1) + l) * 316 + o;
+}
+__host__ __device__ __forceinline__ int64_t oct_matrix(int d, int l, int o, int lmax) {
+    return ((int64_t)d * (lmax + 1) + l) * 8 + o;
+}
+
+// the 316 M2L offsets: (dx,dy,dz) in [-3,3]^3 minus [-1,1]^3, enumerated in lexicographic order
+__host__ __device__ __forceinline__ int m2l_offset_code(int dx, int dy, int dz) {
+    int c = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);  // 0..342
+    // subtract the inner 27 codes that precede c
+    int inner_before = 0;
+    // inner codes have all |d|<=1; count those with code < c
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+            for (int e = -1; e <= 1; ++e) {
+                int ci = ((a + 3) * 7 + (b + 3)) * 7 + (e + 3);
+                inner_before += ci < c;
+            }
+    return c - inner_before;
+}
+
+// error handling inside the library
+std::string cuda_msg(cudaError_t e, const char *what);
+void *dev_alloc(fmbem *h, size_t bytes);  // records the allocation; throws std::bad_alloc on failure
+void dev_free(fmbem *h, void *p);
+
+struct fmbem_error {
+    fmbem_status st;
+    std::string msg;
+};
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) throw fmbem_error{FMBEM_ERR_CUDA, cuda_msg(e_, #call)}; \
+    } while (0)
+#define CKL(what)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = cudaGetLastError();                                       \
+        if (e_ != cudaSuccess) throw fmbem_error{FMBEM_ERR_CUDA, cuda_msg(e_, what)}; \
+    } while (0)
+
+// set-up stages (each throws fmbem_error)
+void build_geometry(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s);
+void build_tree(fmbem *h, cudaStream_t s);
+void build_tables(fmbem *h, cudaStream_t s);
+// per-call operations
+void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
+void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
+void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);
+fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t n_rhs, double tol, int max_iter, int32_t *iters,
+                       double *relres, cudaStream_t s);

@@ -1,0 +1,385 @@
+// fmm.cu -- the fast multipole matrix-vector product of Section 2.2 (Steps 1-4).
+//
+// For every domain d (background d = 0 over all nodes with normal n0 = -n; scatterer j over its
+// own nodes with normal +n) and every Cartesian component i, Eq. (2.12) is a scalar Helmholtz
+// sum over the sources beta of domain d:
+//   y_i(alpha) = sum_beta [ Q_i g_d(s_beta, s_alpha) + m_i . grad' g_d(s_beta, s_alpha) ],
+//   Q = w q,  m_i = w [ v_i n' + (n'.v) e_i - n'_i v ],
+// with v = T_d Phi and q = gamma_d Psi^(d) (Psi^(0) = -Psi): the bracket of Eq. (2.12) applied to
+// v, [n' grad'g - (n'.grad'g) I - grad'g n'].v = grad'g . m / w, enters with a minus sign, and
+// -(...)_i = m_i . grad'g / w.  Far interactions go through P2M -> M2M -> M2L -> L2L -> L2P
+// (Eqs. 2.18-2.21, first term of 2.23); the sources in the node's own leaf and its Neighbor
+// leaves are summed directly (second term of Eq. 2.23), beta = alpha excluded and replaced by the
+// analytic self block A_self (Appendix B).
+#include <algorithm>
+
+#include "fmbem_internal.cuh"
+
+namespace {
+
+inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
+
+struct DomainConsts {  // per domain, device array
+    c64 k, t, gamma;
+};
+
+// ---------------------------------------------------------------- source densities (a2)
+// dens[side][r][i][6] = (w v, w q) for side 0 (background: v = Phi, q = -Psi) and side 1 (own
+// scatterer j: v = T_j Phi, q = gamma_j Psi), nodes in sorted order.
+template <typename R>
+__global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm, const double *w,
+                       const int32_t *dom, const DomainConsts *dc, cx<R> *dens) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t r = blockIdx.y;
+    if (i >= N) return;
+    const c64 *xi = x + (r * N + perm[i]) * 6;
+    double n[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    double wi = w[i];
+    int j = dom[i];
+    c64 Phi[3] = {xi[0], xi[1], xi[2]}, Psi[3] = {xi[3], xi[4], xi[5]};
+    cx<R> *d0 = dens + ((0 * nr + r) * N + i) * 6;
+    cx<R> *d1 = dens + ((1 * nr + r) * N + i) * 6;
+    c64 nP = n[0] * Phi[0] + n[1] * Phi[1] + n[2] * Phi[2];
+    c64 tn = dc[j].t * nP;
+    c64 gw = dc[j].gamma * wi;
+    for (int q = 0; q < 3; ++q) {
+        d0[q] = to<R>(wi * Phi[q]);
+        d0[3 + q] = to<R>(-wi * Psi[q]);
+        d1[q] = to<R>(wi * (Phi[q] + n[q] * tn));
+        d1[3 + q] = to<R>(gw * Psi[q]);
+    }
+}
+
+// ---------------------------------------------------------------- P2M (Eqs. 2.18-2.19)
+// grid (leaf, domain, rhs); thread per coefficient nm; C[d][g][3r+i][nm]
+template <typename R>
+__global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+                      const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens, const cx<R> *Bp2m,
+                      cx<R> *C) {
+    int64_t g = leaf_off + blockIdx.x;
+    int d = blockIdx.y;
+    int64_t r = blockIdx.z;
+    int side = d == 0 ? 0 : 1;
+    R sg = d == 0 ? (R)-1 : (R)1;
+    int i0 = nbeg[g], i1 = nend[g];
+    for (int q = threadIdx.x; q < p2; q += blockDim.x) {
+        cx<R> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int i = i0; i < i1; ++i) {
+            if (d > 0 && dom[i] != d) continue;
+            const cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
+            cx<R> v[3] = {dn[0], dn[1], dn[2]}, qq[3] = {dn[3], dn[4], dn[5]};
+            R n[3] = {sg * (R)nrm[3 * i], sg * (R)nrm[3 * i + 1], sg * (R)nrm[3 * i + 2]};
+            const cx<R> *B = Bp2m + ((int64_t)side * N + i) * 4 * p2;
+            cx<R> b0 = B[q], G[3] = {B[p2 + q], B[2 * p2 + q], B[3 * p2 + q]};
+            cx<R> nG = n[0] * G[0] + n[1] * G[1] + n[2] * G[2];
+            cx<R> nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+            cx<R> vG = v[0] * G[0] + v[1] * G[1] + v[2] * G[2];
+            for (int c = 0; c < 3; ++c) {
+                // m_c . G = v_c (n.G) + (n.v) G_c - n_c (v.G), plus the monopole q_c R
+                cx<R> t = v[c] * nG + nv * G[c] - n[c] * vG + qq[c] * b0;
+                acc[c] += t;
+            }
+        }
+        for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
+    }
+}
+
+// ---------------------------------------------------------------- translation apply helper
+// acc[cc] += sum_c T[c][r] X[cc][c] for the thread's output row r; X in shared memory
+template <typename R, int CC>
+__device__ __forceinline__ void apply_T(const cx<R> *__restrict__ T, const cx<R> *X, int p2, int r, int ncol, cx<R> *acc) {
+    for (int c = 0; c < p2; ++c) {
+        cx<R> t = T[(int64_t)c * p2 + r];
+#pragma unroll
+        for (int cc = 0; cc < CC; ++cc)
+            if (cc < ncol) cfma(acc[cc], t, X[cc * p2 + c]);
+    }
+}
+
+constexpr int CC = 6;  // columns per CTA in the translation kernels
+
+// M2M (Eq. 2.20): parent multipole = sum over children S|S(child octant) child multipole
+// grid (parent box at level l-1, domain, column chunk)
+template <typename R>
+__global__ void k_m2m(int64_t par_off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *cbeg,
+                      const int32_t *cend, const uint64_t *key, const cx<R> *Tmm, cx<R> *C) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
+    int64_t g = par_off + blockIdx.x;
+    int d = blockIdx.y;
+    int col0 = blockIdx.z * CC;
+    int ncol = min(CC, (int)(3 * nr) - col0);
+    int r = threadIdx.x;
+    cx<R> acc[CC];
+    for (int cc = 0; cc < CC; ++cc) acc[cc] = {0, 0};
+    for (int ch = cbeg[g]; ch < cend[g]; ++ch) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
+            X[e] = C[(((int64_t)d * nbox + ch) * 3 * nr + col0 + e / p2) * p2 + e % p2];
+        __syncthreads();
+        int o = (int)(key[ch] & 7);
+        if (r < p2) apply_T<R, CC>(Tmm + oct_matrix(d, l, o, lmax) * p2 * p2, X, p2, r, ncol, acc);
+    }
+    if (r < p2)
+        for (int cc = 0; cc < ncol; ++cc) C[(((int64_t)d * nbox + g) * 3 * nr + col0 + cc) * p2 + r] = acc[cc];
+}
+
+// M2L + L2L (Eq. 2.21): D(l,q) = R|R D(parent) + sum_{FF(l,q)} S|R C(source)
+template <typename R>
+__global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *parent,
+                       const uint64_t *key, const int32_t *ff_start, const int32_t *ff_src, const int16_t *ff_off,
+                       const cx<R> *Tm2l, const cx<R> *Tll, const cx<R> *C, cx<R> *D) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
+    int64_t g = off + blockIdx.x;
+    int d = blockIdx.y;
+    int col0 = blockIdx.z * CC;
+    int ncol = min(CC, (int)(3 * nr) - col0);
+    int r = threadIdx.x;
+    cx<R> acc[CC];
+    for (int cc = 0; cc < CC; ++cc) acc[cc] = {0, 0};
+    if (l >= 3) {
+        int64_t P = parent[g];
+        for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
+            X[e] = D[(((int64_t)d * nbox + P) * 3 * nr + col0 + e / p2) * p2 + e % p2];
+        __syncthreads();
+        int o = (int)(key[g] & 7);
+        if (r < p2) apply_T<R, CC>(Tll + oct_matrix(d, l, o, lmax) * p2 * p2, X, p2, r, ncol, acc);
+    }
+    for (int e0 = ff_start[g]; e0 < ff_start[g + 1]; ++e0) {
+        __syncthreads();
+        int src = ff_src[e0];
+        for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
+            X[e] = C[(((int64_t)d * nbox + src) * 3 * nr + col0 + e / p2) * p2 + e % p2];
+        __syncthreads();
+        if (r < p2) apply_T<R, CC>(Tm2l + m2l_matrix(d, l, ff_off[e0], lmax) * p2 * p2, X, p2, r, ncol, acc);
+    }
+    if (r < p2)
+        for (int cc = 0; cc < ncol; ++cc) D[(((int64_t)d * nbox + g) * 3 * nr + col0 + cc) * p2 + r] = acc[cc];
+}
+
+// ---------------------------------------------------------------- near field + L2P + self (Step 4)
+template <typename R>
+struct SrcTile {
+    R px[128], py[128], pz[128];   // position (or position high part)
+    R lx[128], ly[128], lz[128];   // low part (single precision only)
+    R nx[128], ny[128], nz[128];
+    int dom[128];
+    int idx[128];
+    cx<R> dv[2][6][128];           // densities of the current right-hand side, both sides
+};
+
+template <typename R>
+__device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R> k, R nx, R ny, R nz, const cx<R> *v,
+                                            const cx<R> *q, cx<R> *acc) {
+    // g = e^{ikR}/(4 pi R), grad'g = c r with c = g (ik - 1/R)/R
+    R e = exp(-k.im * Rr);
+    R sn, cs;
+    sincos(k.re * Rr, &sn, &cs);
+    R f = e * inv * (R)(0.25 / FMBEM_PI);
+    cx<R> g = {f * cs, f * sn};
+    // (i k - 1/R)/R with i k = -Im k + i Re k
+    cx<R> c = g * cx<R>{(-k.im - inv) * inv, k.re * inv};
+    cx<R> rv = rx * v[0] + ry * v[1] + rz * v[2];
+    cx<R> nv = nx * v[0] + ny * v[1] + nz * v[2];
+    R nr = nx * rx + ny * ry + nz * rz;
+    R rr[3] = {rx, ry, rz}, nn[3] = {nx, ny, nz};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        // -(K v)_i = -c [n_i (r.v) - (n.r) v_i - r_i (n.v)]
+        cx<R> kv = nn[i] * rv - nr * v[i] - rr[i] * nv;
+        acc[i] -= c * kv;
+        cfma(acc[i], g, q[i]);
+    }
+}
+
+template <typename R, bool DOUBLE_FLOAT>
+__global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                              const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                              const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
+                                              const int32_t *dom, const int32_t *perm, const cx<R> *dens,
+                                              const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
+                                              const c64 *x, c64 *y) {
+    __shared__ SrcTile<R> T;
+    __shared__ int rng_beg[32], rng_cum[33];
+    __shared__ cx<R> red[3][6][32];
+    const int64_t g = leaf_off + blockIdx.x;
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        for (int q = 0; q < nnb; ++q) {
+            int b = nbr_idx[nb0 + q];
+            rng_beg[q] = nbeg[b];
+            rng_cum[q] = cum;
+            cum += nend[b] - nbeg[b];
+        }
+        rng_cum[nnb] = cum;
+    }
+    __syncthreads();
+    const int nsrc = rng_cum[nnb];
+    const int t0 = nbeg[g], t1 = nend[g];
+    for (int64_t r = 0; r < nr; ++r) {
+        for (int tb = t0; tb < t1; tb += 32) {
+            const int a = tb + lane;
+            const bool active = a < t1;
+            R ax = 0, ay = 0, az = 0, alx = 0, aly = 0, alz = 0;
+            int adom = -1;
+            if (active) {
+                ax = pos_hi[3 * a]; ay = pos_hi[3 * a + 1]; az = pos_hi[3 * a + 2];
+                if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
+                adom = dom[a];
+            }
+            cx<R> kb = to<R>(dc[0].k), kj = to<R>(dc[active ? adom : 0].k);
+            cx<R> acc0[3] = {{0, 0}, {0, 0}, {0, 0}}, acc1[3] = {{0, 0}, {0, 0}, {0, 0}};
+            for (int s0 = 0; s0 < nsrc; s0 += 128) {
+                __syncthreads();
+                {  // load a tile of sources
+                    int e = s0 + threadIdx.x;
+                    if (e < nsrc) {
+                        int q = 0;
+                        while (q + 1 < nnb && rng_cum[q + 1] <= e) ++q;
+                        int i = rng_beg[q] + (e - rng_cum[q]);
+                        T.px[threadIdx.x] = pos_hi[3 * i]; T.py[threadIdx.x] = pos_hi[3 * i + 1]; T.pz[threadIdx.x] = pos_hi[3 * i + 2];
+                        if (DOUBLE_FLOAT) {
+                            T.lx[threadIdx.x] = pos_lo[3 * i]; T.ly[threadIdx.x] = pos_lo[3 * i + 1]; T.lz[threadIdx.x] = pos_lo[3 * i + 2];
+                        }
+                        T.nx[threadIdx.x] = nrm[3 * i]; T.ny[threadIdx.x] = nrm[3 * i + 1]; T.nz[threadIdx.x] = nrm[3 * i + 2];
+                        T.dom[threadIdx.x] = dom[i];
+                        T.idx[threadIdx.x] = i;
+                        for (int sd = 0; sd < 2; ++sd)
+                            for (int c = 0; c < 6; ++c) T.dv[sd][c][threadIdx.x] = dens[((sd * nr + r) * N + i) * 6 + c];
+                    }
+                }
+                __syncthreads();
+                const int ns = min(128, nsrc - s0);
+                if (active)
+                    for (int u = slice; u < ns; u += 4) {
+                        if (T.idx[u] == a) continue;
+                        R rx = T.px[u] - ax, ry = T.py[u] - ay, rz = T.pz[u] - az;
+                        if (DOUBLE_FLOAT) { rx += T.lx[u] - alx; ry += T.ly[u] - aly; rz += T.lz[u] - alz; }
+                        R R2 = rx * rx + ry * ry + rz * rz;
+                        R inv = (R)1 / sqrt(R2);
+                        R Rr = R2 * inv;
+                        cx<R> v[3], q[3];
+                        for (int c = 0; c < 3; ++c) { v[c] = T.dv[0][c][u]; q[c] = T.dv[0][3 + c][u]; }
+                        pair_kernel<R>(rx, ry, rz, inv, Rr, kb, -T.nx[u], -T.ny[u], -T.nz[u], v, q, acc0);
+                        if (T.dom[u] == adom) {
+                            for (int c = 0; c < 3; ++c) { v[c] = T.dv[1][c][u]; q[c] = T.dv[1][3 + c][u]; }
+                            pair_kernel<R>(rx, ry, rz, inv, Rr, kj, T.nx[u], T.ny[u], T.nz[u], v, q, acc1);
+                        }
+                    }
+            }
+            // reduce the 4 source slices
+            __syncthreads();
+            if (slice > 0)
+                for (int c = 0; c < 3; ++c) { red[slice - 1][c][lane] = acc0[c]; red[slice - 1][3 + c][lane] = acc1[c]; }
+            __syncthreads();
+            if (slice == 0 && active) {
+                for (int s = 0; s < 3; ++s)
+                    for (int c = 0; c < 3; ++c) { acc0[c] += red[s][c][lane]; acc1[c] += red[s][3 + c][lane]; }
+                // far field, L2P: y_i += sum_nm D[d][leaf][3r+i][nm] B_l2p[side][a][nm]
+                for (int sd = 0; sd < 2; ++sd) {
+                    int d = sd == 0 ? 0 : adom;
+                    const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r) * p2;
+                    const cx<R> *B = Bl2p + ((int64_t)sd * N + a) * p2;
+                    cx<R> *acc = sd == 0 ? acc0 : acc1;
+                    for (int q = 0; q < p2; ++q) {
+                        cx<R> b = B[q];
+                        cfma(acc[0], Dl[q], b);
+                        cfma(acc[1], Dl[p2 + q], b);
+                        cfma(acc[2], Dl[2 * p2 + q], b);
+                    }
+                }
+                // self block A_self x (double precision) and store in user order
+                int64_t u = perm[a];
+                const c64 *M = Mself + 36 * u;
+                const c64 *xa = x + (r * N + u) * 6;
+                c64 *ya = y + (r * N + u) * 6;
+                for (int row = 0; row < 6; ++row) {
+                    c64 s = row < 3 ? c64{(double)acc0[row].re, (double)acc0[row].im}
+                                    : c64{(double)acc1[row - 3].re, (double)acc1[row - 3].im};
+                    for (int c = 0; c < 6; ++c) cfma(s, M[row * 6 + c], xa[c]);
+                    ya[row] = s;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+static void ensure_scratch(fmbem *h, int64_t nr) {
+    if (h->scratch_rhs >= nr) return;
+    if (h->dens) { dev_free(h, h->dens); dev_free(h, h->Cexp); dev_free(h, h->Dexp); }
+    const size_t cb = sizeof(c64);
+    h->dens = dev_alloc(h, cb * 2 * nr * h->N * 6);
+    h->Cexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
+    h->Dexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
+    h->scratch_rhs = nr;
+}
+
+template <typename R>
+static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc) {
+    const int64_t N = h->N;
+    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const bool f32 = sizeof(R) == 4;
+    cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
+    const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
+    const cx<R> *Bl2p = f32 ? (const cx<R> *)h->B_l2p32 : (const cx<R> *)h->B_l2p64;
+    const cx<R> *Tm2l = f32 ? (const cx<R> *)h->T_m2l32 : (const cx<R> *)h->T_m2l64;
+    const cx<R> *Tmm = f32 ? (const cx<R> *)h->T_mm32 : (const cx<R> *)h->T_mm64;
+    const cx<R> *Tll = f32 ? (const cx<R> *)h->T_ll32 : (const cx<R> *)h->T_ll64;
+    const bool timing = h->profile && h->ev[0] != nullptr;
+    if (timing) CK(cudaEventRecord(h->ev[0], s));
+
+    k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens);
+    CKL("k_prep");
+    const LevelInfo &L = h->lev[lmax];
+    const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
+    k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+                                                                       h->dom, h->nrm, dens, Bp2m, C);
+    CKL("k_p2m");
+    if (timing) CK(cudaEventRecord(h->ev[1], s));
+    const int ncc = (int)((3 * nr + CC - 1) / CC);
+    const size_t sm = sizeof(cx<R>) * CC * p2;
+    const int tbt = ((p2 + 31) / 32) * 32;
+    for (int l = lmax; l >= 3; --l) {
+        const LevelInfo &P = h->lev[l - 1];
+        k_m2m<R><<<dim3((unsigned)P.n, J + 1, ncc), tbt, sm, s>>>(P.off, l, lmax, nr, p2, h->nbox, h->box_cbeg,
+                                                                  h->box_cend, h->box_key, Tmm, C);
+        CKL("k_m2m");
+    }
+    if (timing) CK(cudaEventRecord(h->ev[2], s));
+    for (int l = 2; l <= lmax; ++l) {
+        const LevelInfo &Lv = h->lev[l];
+        k_down<R><<<dim3((unsigned)Lv.n, J + 1, ncc), tbt, sm, s>>>(Lv.off, l, lmax, nr, p2, h->nbox, h->box_parent,
+                                                                    h->box_key, h->ff_start, h->ff_src, h->ff_off, Tm2l,
+                                                                    Tll, C, D);
+        CKL("k_down");
+    }
+    if (timing) CK(cudaEventRecord(h->ev[3], s));
+    const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
+    const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
+    const R *nn = f32 ? (const R *)h->nrm_f : (const R *)h->nrm;
+    if (f32)
+        k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
+                                                      h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D, h->Mself,
+                                                      x, y);
+    else
+        k_near<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
+                                                       h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D,
+                                                       h->Mself, x, y);
+    CKL("k_near");
+    if (timing) CK(cudaEventRecord(h->ev[4], s));
+}
+
+void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
+    ensure_scratch(h, nr);
+    static_assert(sizeof(DomainConsts) == 3 * sizeof(c64), "layout");
+    DomainConsts *dc = (DomainConsts *)h->dcons;
+    if (precision == FMBEM_FP32) matvec_impl<float>(h, x, y, nr, s, dc);
+    else matvec_impl<double>(h, x, y, nr, s, dc);
+    h->have_times = h->profile && h->ev[0] != nullptr;
+}

@@ -1,0 +1,317 @@
+// tables.cu -- multipole bases of the nodes and translation matrices, Eqs. (2.14)-(2.21).
+//
+// Scaled coefficients.  With lambda = |k_d| w_l on level l (box width w_l) the library stores
+//   multipole  Ct_n^m = C_n^m / lambda^(n+1),   local  Dt_n^m = D_n^m lambda^n,
+// so that neither underflows nor overflows in single precision when |k| w << 1 (the expansions
+// themselves are those of Eq. 2.17, truncated at n = p-1).
+//
+// P2M (Eqs. 2.18-2.19) for a source with monopole strength Q and dipole moment m at s:
+//   Ct_n^m += (i k / lambda^(n+1)) [ Q R_n^{-m}(s - c) + m . grad R_n^{-m}(s - c) ]
+// L2P (first term of Eq. 2.23):  phi(r) = sum Dt_n^m R_n^m(r - c) / lambda^n.
+//
+// Translation matrices are obtained by projecting the translated basis function on the sphere
+// |x| = rho around the new centre: for the column of input basis function F_c(x + t),
+//   T[r][c] = (1 / rad_{n_r}(k rho)) int F_c(rho xhat + t) conj(Y_r(xhat)) dOmega,
+// rad = j_n for regular output bases (S|R of Eq. 2.21 and R|R), h_n for singular output bases
+// (S|S of Eq. 2.20).  The integral uses Gauss-Legendre nodes in cos(theta) and the trapezoid rule
+// in phi, exact for spherical-harmonic degree well above p, so the aliasing error is set by the
+// decay of F_c's harmonic content on the sphere (rho/|t| <= 1/2 for S|R with rho = w_l,
+// |t|/rho < 1/2 for S|S with rho = 2 w_l).
+#include <algorithm>
+#include <cmath>
+
+#include "fmbem_internal.cuh"
+#include "special.cuh"
+
+namespace {
+
+constexpr int PMAX = 20;  // largest supported truncation number
+
+inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
+
+// Gauss-Legendre nodes and weights on [-1,1] (Newton iteration on P_n)
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = cos(FMBEM_PI * (i + 0.75) / (n + 0.5)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = 0;
+            for (int j = 1; j <= n; ++j) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+__global__ void k_to32(const c64 *a, c32 *b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to<float>(a[i]);
+}
+
+// per node and side: P2M basis (scaled, with the i k prefactor) and L2P basis
+__global__ void k_node_bases(int64_t N, int p, const double *pos, const int32_t *dom, const int32_t *node_leaf,
+                             const double *box_ctr, const c64 *kd, const double *lam /* [J+1] at the leaf level */,
+                             c64 *Bp2m, c64 *Bl2p) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int side = blockIdx.y;
+    if (i >= N) return;
+    int d = side == 0 ? 0 : dom[i];
+    c64 k = kd[d];
+    double la = lam[d];
+    const double *c = box_ctr + 3 * node_leaf[i];
+    double r[3] = {pos[3 * i] - c[0], pos[3 * i + 1] - c[1], pos[3 * i + 2] - c[2]};
+    c64 R[(PMAX + 1) * (PMAX + 1)], rad[PMAX + 2];
+    double Pb[(PMAX + 2) * (PMAX + 3) / 2];
+    wave_functions<false>(p, k, r, R, rad, Pb);  // degrees 0..p (one more for the gradient)
+    const int p2 = p * p;
+    c64 ik = c64{-k.im, k.re};
+    c64 *bp = Bp2m + ((int64_t)side * N + i) * 4 * p2;
+    c64 *bl = Bl2p + ((int64_t)side * N + i) * p2;
+    double lpow = 1.0;  // lambda^n
+    for (int n = 0; n < p; ++n) {
+        double sm = 1.0 / (lpow * la);  // 1/lambda^(n+1)
+        for (int m = -n; m <= n; ++m) {
+            int q = n * n + n + m;
+            c64 g[3];
+            grad_regular(p, k, R, n, -m, g);
+            bp[0 * p2 + q] = (ik * R[n * n + n - m]) * sm;
+            bp[1 * p2 + q] = (ik * g[0]) * sm;
+            bp[2 * p2 + q] = (ik * g[1]) * sm;
+            bp[3 * p2 + q] = (ik * g[2]) * sm;
+            bl[q] = R[q] * (1.0 / lpow);
+        }
+        lpow *= la;
+    }
+}
+
+// evaluate the input basis functions of a batch of translations at the quadrature points:
+// F[m][q][c] = F_c(rho xhat_q + t_m), c = 0..p2-1; F_c = S_c (singular) or R_c (regular)
+template <bool SINGULAR>
+__global__ void k_eval_cols(int nmat, int Q, int p, c64 k, double rho, const double *xq /* [Q][3] unit */,
+                            const double *tvec /* [nmat][3] */, c64 *F) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nmat * Q) return;
+    int m = (int)(idx / Q), q = (int)(idx % Q);
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = rho * xq[3 * q + a] + tvec[3 * m + a];
+    c64 V[PMAX * PMAX], rad[PMAX + 1];
+    double Pb[(PMAX + 1) * (PMAX + 2) / 2];
+    wave_functions<SINGULAR>(p - 1, k, r, V, rad, Pb);
+    c64 *out = F + idx * (int64_t)(p * p);
+    for (int c = 0; c < p * p; ++c) out[c] = V[c];
+}
+
+// projection weights Yc[q][r] = W_q conj(Y_r(xhat_q)) / rad_{n_r}(k rho)
+__global__ void k_proj_weights(int Q, int p, const double *xq, const double *wq, c64 k, double rho, bool singular_out,
+                               c64 *Yc) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    double Pb[(PMAX + 1) * (PMAX + 2) / 2];
+    double r[3] = {xq[3 * q], xq[3 * q + 1], xq[3 * q + 2]};
+    double ct = r[2];
+    double phi = (r[0] == 0.0 && r[1] == 0.0) ? 0.0 : atan2(r[1], r[0]);
+    legendre_bar(p - 1, ct, Pb);
+    c64 radv[PMAX + 1];
+    c64 z = k * rho;
+    if (singular_out) sph_h1(p - 1, z, radv);
+    else sph_j(p - 1, z, radv);
+    for (int n = 0; n < p; ++n)
+        for (int m = -n; m <= n; ++m) {
+            int am = m < 0 ? -m : m;
+            double sgn = (am & 1) ? -1.0 : 1.0;
+            double sp, cp;
+            sincos(m * phi, &sp, &cp);
+            c64 Ynm = c64{cp, sp} * (sgn * Pb[n * (n + 1) / 2 + am]);
+            c64 v = cdiv(conjg(Ynm) * wq[q], radv[n]);
+            Yc[(int64_t)q * p * p + n * n + n + m] = v;
+        }
+}
+
+// T[m][r][c] = sum_q Yc[q][r] F[m][q][c]  (complex FP64 GEMM per matrix, 16x16 tiles),
+// then scaled: out[m][c][r] = sr[r] * T * sc[c], stored input-major for the apply kernels
+__global__ void k_project(int nmat, int Q, int p2, const c64 *Yc, const c64 *F, const double *sr, const double *sc,
+                          c64 *out64, c32 *out32, const int64_t *dst /* [nmat] destination matrix index */) {
+    __shared__ c64 As[16][17], Bs[16][17];
+    int m = blockIdx.z;
+    int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+    int tr = threadIdx.y, tc = threadIdx.x;
+    const c64 *Fm = F + (int64_t)m * Q * p2;
+    c64 acc = {0, 0};
+    for (int q0 = 0; q0 < Q; q0 += 16) {
+        int q = q0 + tc;
+        As[tr][tc] = (q < Q && r0 + tr < p2) ? Yc[(int64_t)q * p2 + r0 + tr] : c64{0, 0};
+        int q2 = q0 + tr;
+        Bs[tr][tc] = (q2 < Q && c0 + tc < p2) ? Fm[(int64_t)q2 * p2 + c0 + tc] : c64{0, 0};
+        __syncthreads();
+        for (int u = 0; u < 16; ++u) cfma(acc, As[tr][u], Bs[u][tc]);
+        __syncthreads();
+    }
+    int r = r0 + tr, c = c0 + tc;
+    if (r < p2 && c < p2) {
+        c64 v = acc * (sr[r] * sc[c]);
+        int64_t o = dst[m] * (int64_t)p2 * p2 + (int64_t)c * p2 + r;
+        out64[o] = v;
+        out32[o] = to<float>(v);
+    }
+}
+
+}  // namespace
+
+void build_tables(fmbem *h, cudaStream_t s) {
+    const int p = h->p, p2 = p * p, J = h->J, lmax = h->lmax;
+    const int64_t N = h->N;
+    if (p < 2 || p > PMAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "p must be in 2..20"};
+    // scales lambda = |k_d| w_l
+    h->lam.assign((size_t)(J + 1) * (lmax + 1), 0.0);
+    for (int d = 0; d <= J; ++d)
+        for (int l = 0; l <= lmax; ++l) h->lam[d * (lmax + 1) + l] = cabsd(h->k[d]) * h->lev[l].w;
+
+    // ---- node bases
+    c64 *dk = (c64 *)dev_alloc(h, sizeof(c64) * (J + 1));
+    double *dl = (double *)dev_alloc(h, sizeof(double) * (J + 1));
+    std::vector<double> lleaf(J + 1);
+    for (int d = 0; d <= J; ++d) lleaf[d] = h->lam[d * (lmax + 1) + lmax];
+    CK(cudaMemcpyAsync(dk, h->k.data(), sizeof(c64) * (J + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dl, lleaf.data(), sizeof(double) * (J + 1), cudaMemcpyHostToDevice, s));
+    h->B_p2m64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * 4 * p2);
+    h->B_l2p64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * p2);
+    {
+        dim3 grid(nblk(N, 64), 2);
+        k_node_bases<<<grid, 64, 0, s>>>(N, p, h->pos, h->dom, h->node_leaf, h->box_ctr, dk, dl, h->B_p2m64, h->B_l2p64);
+        CKL("k_node_bases");
+    }
+    h->B_p2m32 = (c32 *)dev_alloc(h, sizeof(c32) * 2 * N * 4 * p2);
+    h->B_l2p32 = (c32 *)dev_alloc(h, sizeof(c32) * 2 * N * p2);
+    k_to32<<<nblk(2 * N * 4 * p2, 256), 256, 0, s>>>(h->B_p2m64, h->B_p2m32, 2 * N * 4 * p2);
+    k_to32<<<nblk(2 * N * p2, 256), 256, 0, s>>>(h->B_l2p64, h->B_l2p32, 2 * N * p2);
+    CKL("k_to32");
+
+    // ---- translation matrices
+    const int Lt = p / 2 + 22, Lp = p + 44, Q = Lt * Lp;
+    std::vector<double> gx, gw;
+    gauss_legendre(Lt, gx, gw);
+    std::vector<double> xq(3 * Q), wq(Q);
+    for (int i = 0; i < Lt; ++i)
+        for (int j = 0; j < Lp; ++j) {
+            double ct = gx[i], st = sqrt(std::max(0.0, 1 - ct * ct)), ph = 2 * FMBEM_PI * j / Lp;
+            int q = i * Lp + j;
+            xq[3 * q] = st * cos(ph);
+            xq[3 * q + 1] = st * sin(ph);
+            xq[3 * q + 2] = ct;
+            wq[q] = gw[i] * 2 * FMBEM_PI / Lp;
+        }
+    double *dxq = (double *)dev_alloc(h, sizeof(double) * 3 * Q);
+    double *dwq = (double *)dev_alloc(h, sizeof(double) * Q);
+    CK(cudaMemcpyAsync(dxq, xq.data(), sizeof(double) * 3 * Q, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dwq, wq.data(), sizeof(double) * Q, cudaMemcpyHostToDevice, s));
+
+    const int64_t n_m2l = (int64_t)(J + 1) * (lmax + 1) * 316, n_oct = (int64_t)(J + 1) * (lmax + 1) * 8;
+    h->T_m2l64 = (c64 *)dev_alloc(h, sizeof(c64) * n_m2l * p2 * p2);
+    h->T_m2l32 = (c32 *)dev_alloc(h, sizeof(c32) * n_m2l * p2 * p2);
+    h->T_mm64 = (c64 *)dev_alloc(h, sizeof(c64) * n_oct * p2 * p2);
+    h->T_mm32 = (c32 *)dev_alloc(h, sizeof(c32) * n_oct * p2 * p2);
+    h->T_ll64 = (c64 *)dev_alloc(h, sizeof(c64) * n_oct * p2 * p2);
+    h->T_ll32 = (c32 *)dev_alloc(h, sizeof(c32) * n_oct * p2 * p2);
+    CK(cudaMemsetAsync(h->T_m2l64, 0, sizeof(c64) * n_m2l * p2 * p2, s));
+    CK(cudaMemsetAsync(h->T_m2l32, 0, sizeof(c32) * n_m2l * p2 * p2, s));
+    CK(cudaMemsetAsync(h->T_mm64, 0, sizeof(c64) * n_oct * p2 * p2, s));
+    CK(cudaMemsetAsync(h->T_mm32, 0, sizeof(c32) * n_oct * p2 * p2, s));
+    CK(cudaMemsetAsync(h->T_ll64, 0, sizeof(c64) * n_oct * p2 * p2, s));
+    CK(cudaMemsetAsync(h->T_ll32, 0, sizeof(c32) * n_oct * p2 * p2, s));
+
+    const int BATCH = 316;
+    c64 *F = (c64 *)dev_alloc(h, sizeof(c64) * (int64_t)BATCH * Q * p2);
+    c64 *Yc = (c64 *)dev_alloc(h, sizeof(c64) * (int64_t)Q * p2);
+    double *dt = (double *)dev_alloc(h, sizeof(double) * 3 * BATCH);
+    int64_t *ddst = (int64_t *)dev_alloc(h, sizeof(int64_t) * BATCH);
+    double *dsr = (double *)dev_alloc(h, sizeof(double) * p2);
+    double *dsc = (double *)dev_alloc(h, sizeof(double) * p2);
+    std::vector<double> sr(p2), sc(p2);
+
+    // one batch of translations sharing (k, rho, output basis): evaluate, project, scale, store
+    auto run_batch = [&](bool sing_in, bool sing_out, c64 k, double rho, const std::vector<double> &tv,
+                         const std::vector<int64_t> &dst, c64 *o64, c32 *o32) {
+        int nm = (int)dst.size();
+        CK(cudaMemcpyAsync(dt, tv.data(), sizeof(double) * 3 * nm, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * nm, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dsr, sr.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
+        k_proj_weights<<<nblk(Q, 64), 64, 0, s>>>(Q, p, dxq, dwq, k, rho, sing_out, Yc);
+        CKL("k_proj_weights");
+        if (sing_in) k_eval_cols<true><<<nblk((int64_t)nm * Q, 64), 64, 0, s>>>(nm, Q, p, k, rho, dxq, dt, F);
+        else k_eval_cols<false><<<nblk((int64_t)nm * Q, 64), 64, 0, s>>>(nm, Q, p, k, rho, dxq, dt, F);
+        CKL("k_eval_cols");
+        dim3 grid((p2 + 15) / 16, (p2 + 15) / 16, nm), tb(16, 16);
+        k_project<<<grid, tb, 0, s>>>(nm, Q, p2, Yc, F, dsr, dsc, o64, o32, ddst);
+        CKL("k_project");
+        CK(cudaStreamSynchronize(s));  // the staging buffers are reused by the next batch
+    };
+    auto nof = [](int q) { int n = 0; while ((n + 1) * (n + 1) <= q) ++n; return n; };
+
+    for (int d = 0; d <= J; ++d) {
+        const c64 k = h->k[d];
+        for (int l = 2; l <= lmax; ++l) {
+            const double w = h->lev[l].w, la = h->lam[d * (lmax + 1) + l];
+            // S|R (M2L), t = c_target - c_source = -(offset) w, rho = w
+            std::vector<double> tv;
+            std::vector<int64_t> dst;
+            for (int dx = -3; dx <= 3; ++dx)
+                for (int dy = -3; dy <= 3; ++dy)
+                    for (int dz = -3; dz <= 3; ++dz) {
+                        if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+                        tv.push_back(-dx * w); tv.push_back(-dy * w); tv.push_back(-dz * w);
+                        dst.push_back(m2l_matrix(d, l, m2l_offset_code(dx, dy, dz), lmax));
+                    }
+            for (int q = 0; q < p2; ++q) {
+                int n = nof(q);
+                sr[q] = pow(la, n);          // output local: times lambda^n
+                sc[q] = pow(la, n + 1);      // input multipole: C = Ct lambda^(n+1)
+            }
+            run_batch(true, false, k, w, tv, dst, h->T_m2l64, h->T_m2l32);
+            if (l >= 3) {
+                const double lp = h->lam[d * (lmax + 1) + l - 1];
+                // S|S (M2M): child octant o at level l, t = c_parent - c_child = (0.5 - o) w, rho = 2 w
+                std::vector<double> tm, tl;
+                std::vector<int64_t> dm;
+                for (int o = 0; o < 8; ++o) {
+                    int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;  // Morton bit order x,y,z
+                    tm.push_back((0.5 - ox) * w); tm.push_back((0.5 - oy) * w); tm.push_back((0.5 - oz) * w);
+                    tl.push_back((ox - 0.5) * w); tl.push_back((oy - 0.5) * w); tl.push_back((oz - 0.5) * w);
+                    dm.push_back(oct_matrix(d, l, o, lmax));
+                }
+                for (int q = 0; q < p2; ++q) {
+                    int n = nof(q);
+                    sr[q] = 1.0 / pow(lp, n + 1);  // output parent multipole
+                    sc[q] = pow(la, n + 1);        // input child multipole
+                }
+                run_batch(true, true, k, 2 * w, tm, dm, h->T_mm64, h->T_mm32);
+                // R|R (L2L): t = c_child - c_parent, rho = w
+                for (int q = 0; q < p2; ++q) {
+                    int n = nof(q);
+                    sr[q] = pow(la, n);            // output child local
+                    sc[q] = 1.0 / pow(lp, n);      // input parent local
+                }
+                run_batch(false, false, k, w, tl, dm, h->T_ll64, h->T_ll32);
+            }
+        }
+    }
+    dev_free(h, F);
+    dev_free(h, Yc);
+    dev_free(h, dt);
+    dev_free(h, ddst);
+    dev_free(h, dsr);
+    dev_free(h, dsc);
+    dev_free(h, dxq);
+    dev_free(h, dwq);
+    dev_free(h, dk);
+    dev_free(h, dl);
+}

@@ -1,0 +1,471 @@
+// tree.cu -- octree over the Nystrom nodes and its box relations (Appendix C, Section 2.2):
+// root cube around the nodes, Morton keys, stable radix sort of the nodes, non-empty boxes on
+// every level (empty boxes are dropped), Parent/Children, Neighbor lists of the leaves and FF
+// lists (children of the parent's neighbours that are not neighbours themselves) on levels 2..l_max.
+#include <algorithm>
+#include <cstring>
+
+#include "fmbem_internal.cuh"
+
+namespace {
+
+constexpr int KEY_LEVELS = 10;  // Morton keys resolve 2^10 boxes per axis
+
+// ---------------------------------------------------------------- device-wide exclusive scan
+constexpr int SCAN_TB = 1024;
+
+__global__ void k_scan_block(const int32_t *in, int32_t *out, int32_t *block_sums, int64_t n) {
+    __shared__ int32_t s[SCAN_TB];
+    int64_t i = blockIdx.x * (int64_t)SCAN_TB + threadIdx.x;
+    int32_t v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < SCAN_TB; off <<= 1) {
+        int32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;  // exclusive
+    if (threadIdx.x == SCAN_TB - 1) block_sums[blockIdx.x] = s[SCAN_TB - 1];
+}
+__global__ void k_scan_add(int32_t *out, const int32_t *block_off, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)SCAN_TB + threadIdx.x;
+    if (i < n) out[i] += block_off[blockIdx.x];
+}
+
+// exclusive scan of n int32 values; returns the total
+int64_t scan_exclusive(fmbem *h, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s) {
+    if (n == 0) return 0;
+    int64_t nb = (n + SCAN_TB - 1) / SCAN_TB;
+    int32_t *sums = (int32_t *)dev_alloc(h, sizeof(int32_t) * (nb + 1));
+    int32_t *offs = (int32_t *)dev_alloc(h, sizeof(int32_t) * (nb + 1));
+    k_scan_block<<<(unsigned)nb, SCAN_TB, 0, s>>>(in, out, sums, n);
+    CKL("k_scan_block");
+    int64_t total;
+    if (nb > 1) {
+        total = scan_exclusive(h, sums, offs, nb, s);
+        k_scan_add<<<(unsigned)nb, SCAN_TB, 0, s>>>(out, offs, n);
+        CKL("k_scan_add");
+    } else {
+        int32_t t;
+        CK(cudaMemcpyAsync(&t, sums, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        total = t;
+    }
+    dev_free(h, sums);
+    dev_free(h, offs);
+    return total;
+}
+
+// ---------------------------------------------------------------- bounding box
+__global__ void k_bbox(const double *pos, int64_t N, double *out /* [nblocks][6] */) {
+    __shared__ double s[6][256];
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int q = 0; q < 3; ++q) { mn[q] = fmin(mn[q], pos[3 * i + q]); mx[q] = fmax(mx[q], pos[3 * i + q]); }
+    for (int q = 0; q < 3; ++q) { s[q][threadIdx.x] = mn[q]; s[3 + q][threadIdx.x] = mx[q]; }
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int q = 0; q < 3; ++q) {
+                s[q][threadIdx.x] = fmin(s[q][threadIdx.x], s[q][threadIdx.x + off]);
+                s[3 + q][threadIdx.x] = fmax(s[3 + q][threadIdx.x], s[3 + q][threadIdx.x + off]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) out[6 * blockIdx.x + q] = s[q][0];
+}
+
+// ---------------------------------------------------------------- Morton keys
+__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v) {  // 10 bits -> every third bit
+    uint64_t x = v & 0x3ff;
+    x = (x | (x << 16)) & 0x30000ffULL;
+    x = (x | (x << 8)) & 0x300f00fULL;
+    x = (x | (x << 4)) & 0x30c30c3ULL;
+    x = (x | (x << 2)) & 0x9249249ULL;
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x9249249ULL;
+    x = (x | (x >> 2)) & 0x30c30c3ULL;
+    x = (x | (x >> 4)) & 0x300f00fULL;
+    x = (x | (x >> 8)) & 0x30000ffULL;
+    x = (x | (x >> 16)) & 0x3ffULL;
+    return (uint32_t)x;
+}
+__host__ __device__ __forceinline__ uint64_t morton(uint32_t ix, uint32_t iy, uint32_t iz) {
+    return (spread3(ix) << 2) | (spread3(iy) << 1) | spread3(iz);
+}
+__host__ __device__ __forceinline__ void demorton(uint64_t key, int &ix, int &iy, int &iz) {
+    ix = (int)compact3(key >> 2);
+    iy = (int)compact3(key >> 1);
+    iz = (int)compact3(key);
+}
+
+// box index along each axis = floor((x - x_min) / w) clamped to [0, 2^10 - 1]
+__global__ void k_keys(const double *pos, int64_t N, double x0, double y0, double z0, double inv_w, uint64_t *key,
+                       int32_t *idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int M = 1 << KEY_LEVELS;
+    double o[3] = {x0, y0, z0};
+    uint32_t c[3];
+    for (int q = 0; q < 3; ++q) {
+        double t = floor((pos[3 * i + q] - o[q]) * inv_w);
+        int v = (int)t;
+        c[q] = (uint32_t)min(max(v, 0), M - 1);
+    }
+    key[i] = morton(c[0], c[1], c[2]);
+    idx[i] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------- stable 1-bit split radix sort
+__global__ void k_bitflag(const uint64_t *key, int64_t n, int bit, int32_t *zero_flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) zero_flag[i] = ((key[i] >> bit) & 1ULL) ? 0 : 1;
+}
+__global__ void k_bitscatter(const uint64_t *key, const int32_t *idx, const int32_t *zpos, int64_t n, int64_t nzero, int bit,
+                             uint64_t *key2, int32_t *idx2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool one = (key[i] >> bit) & 1ULL;
+    int64_t dst = one ? nzero + (i - zpos[i]) : zpos[i];
+    key2[dst] = key[i];
+    idx2[dst] = idx[i];
+}
+
+// ---------------------------------------------------------------- per-level boxes
+__global__ void k_level_flags(const uint64_t *key, int64_t n, int shift, int32_t *flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (i == 0 || (key[i] >> shift) != (key[i - 1] >> shift)) ? 1 : 0;
+}
+// node -> box id (inclusive scan - 1) and box start positions
+__global__ void k_level_boxes(const uint64_t *key, const int32_t *flag, const int32_t *excl, int64_t n, int shift,
+                              int32_t *node_box, int32_t *box_start, uint64_t *box_key) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t b = excl[i] + flag[i] - 1;
+    node_box[i] = b;
+    if (flag[i]) {
+        box_start[b] = (int32_t)i;
+        box_key[b] = key[i] >> shift;
+    }
+}
+__global__ void k_max_occupancy(const int32_t *box_start, int64_t nb, int64_t n, int32_t *out) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int32_t e = b + 1 < nb ? box_start[b + 1] : (int32_t)n;
+    atomicMax(out, e - box_start[b]);
+}
+
+// fill global box arrays of one level
+__global__ void k_fill_level(int64_t nb, int64_t off, int l, const int32_t *box_start, const uint64_t *lkey, int64_t n,
+                             const int32_t *node_box_parent /* level l-1, or null */, int64_t off_parent,
+                             double x0, double y0, double z0, double w, uint64_t *gkey, double *gctr,
+                             int32_t *gparent, int32_t *nbeg, int32_t *nend) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int64_t g = off + b;
+    uint64_t kk = lkey[b];
+    gkey[g] = kk;
+    int ix, iy, iz;
+    demorton(kk, ix, iy, iz);
+    gctr[3 * g + 0] = x0 + (ix + 0.5) * w;
+    gctr[3 * g + 1] = y0 + (iy + 0.5) * w;
+    gctr[3 * g + 2] = z0 + (iz + 0.5) * w;
+    int32_t s = box_start[b];
+    nbeg[g] = s;
+    nend[g] = b + 1 < nb ? box_start[b + 1] : (int32_t)n;
+    gparent[g] = node_box_parent ? (int32_t)(off_parent + node_box_parent[s]) : -1;
+}
+// children range of the boxes of level l from the node->box map of level l+1
+__global__ void k_children(int64_t nb, int64_t off, const int32_t *nbeg, const int32_t *nend, const int32_t *node_box_child,
+                           int64_t off_child, int32_t *cbeg, int32_t *cend) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int64_t g = off + b;
+    cbeg[g] = (int32_t)(off_child + node_box_child[nbeg[g]]);
+    cend[g] = (int32_t)(off_child + node_box_child[nend[g] - 1] + 1);
+}
+
+// binary search of a key among the sorted keys of one level; returns global index or -1
+__device__ __forceinline__ int64_t find_box(const uint64_t *gkey, int64_t off, int64_t nb, uint64_t kk) {
+    int64_t lo = 0, hi = nb;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (gkey[off + mid] < kk) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < nb && gkey[off + lo] == kk) ? off + lo : -1;
+}
+
+// Neighbor(l,q) plus the box itself, for the leaves (pass 0 counts, pass 1 fills)
+__global__ void k_neighbors(int64_t nb, int64_t off, int l, const uint64_t *gkey, const int32_t *start, int32_t *cnt,
+                            int32_t *idx, const int32_t *nbeg, const int32_t *nend, int64_t *pair_count) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int64_t g = off + b;
+    int ix, iy, iz;
+    demorton(gkey[g], ix, iy, iz);
+    const int M = 1 << l;
+    int c = 0;
+    int64_t pairs = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+                if (jx < 0 || jy < 0 || jz < 0 || jx >= M || jy >= M || jz >= M) continue;
+                int64_t q = find_box(gkey, off, nb, morton(jx, jy, jz));
+                if (q < 0) continue;
+                if (idx) idx[start[b] + c] = (int32_t)q;
+                pairs += nend[q] - nbeg[q];
+                ++c;
+            }
+    if (cnt) cnt[b] = c;
+    if (pair_count) atomicAdd((unsigned long long *)pair_count, (unsigned long long)(pairs * (nend[g] - nbeg[g])));
+}
+
+// FF(l,q) = Children(Neighbor(Parent(l,q))) \ Neighbor(l,q), with the offset code of each entry
+__global__ void k_farfield(int64_t nb, int64_t off, int l, const uint64_t *gkey, int64_t off_par, int64_t nb_par,
+                           const int32_t *cbeg, const int32_t *cend, const int32_t *start, int32_t *cnt, int32_t *src,
+                           int16_t *code) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int64_t g = off + b;
+    int ix, iy, iz;
+    demorton(gkey[g], ix, iy, iz);
+    int px = ix >> 1, py = iy >> 1, pz = iz >> 1;
+    const int Mp = 1 << (l - 1);
+    int c = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int qx = px + dx, qy = py + dy, qz = pz + dz;
+                if (qx < 0 || qy < 0 || qz < 0 || qx >= Mp || qy >= Mp || qz >= Mp) continue;
+                int64_t P = find_box(gkey, off_par, nb_par, morton(qx, qy, qz));
+                if (P < 0) continue;
+                for (int ch = cbeg[P]; ch < cend[P]; ++ch) {
+                    int jx, jy, jz;
+                    demorton(gkey[ch], jx, jy, jz);
+                    int ex = jx - ix, ey = jy - iy, ez = jz - iz;
+                    if (abs(ex) <= 1 && abs(ey) <= 1 && abs(ez) <= 1) continue;  // a neighbour
+                    if (src) {
+                        src[start[b] + c] = ch;
+                        code[start[b] + c] = (int16_t)m2l_offset_code(ex, ey, ez);
+                    }
+                    ++c;
+                }
+            }
+    if (cnt) cnt[b] = c;
+}
+
+// sorted copies of the node geometry, double-float positions for the single-precision passes
+__global__ void k_sorted_geometry(int64_t N, const int32_t *perm, const double *upos, const double *unrm, const double *uw,
+                                  const int32_t *udom, double *pos, double *nrm, double *w, int32_t *dom, int32_t *iperm,
+                                  float *hi, float *lo, float *nf) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int32_t u = perm[i];
+    iperm[u] = (int32_t)i;
+    for (int q = 0; q < 3; ++q) {
+        double x = upos[3 * u + q];
+        pos[3 * i + q] = x;
+        nrm[3 * i + q] = unrm[3 * u + q];
+        float xh = (float)x;
+        hi[3 * i + q] = xh;
+        lo[3 * i + q] = (float)(x - (double)xh);
+        nf[3 * i + q] = (float)unrm[3 * u + q];
+    }
+    w[i] = uw[u];
+    dom[i] = udom[u];
+}
+
+__global__ void k_add_offset(int32_t *a, int64_t n, int32_t off) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] += off;
+}
+
+inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
+
+}  // namespace
+
+void build_tree(fmbem *h, cudaStream_t s) {
+    const int64_t N = h->N;
+    const int TB = 256;
+    // root cube: centre of the bounding box, side 1.000001 x the largest extent
+    int nbb = (int)std::min<int64_t>(nblk(N, TB), 1024);
+    double *bb = (double *)dev_alloc(h, sizeof(double) * 6 * nbb);
+    k_bbox<<<nbb, TB, 0, s>>>(h->upos, N, bb);
+    CKL("k_bbox");
+    std::vector<double> hb(6 * nbb);
+    CK(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * 6 * nbb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dev_free(h, bb);
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int b = 0; b < nbb; ++b)
+        for (int q = 0; q < 3; ++q) { mn[q] = std::min(mn[q], hb[6 * b + q]); mx[q] = std::max(mx[q], hb[6 * b + 3 + q]); }
+    double ext = std::max(mx[0] - mn[0], std::max(mx[1] - mn[1], mx[2] - mn[2]));
+    if (!(ext > 0)) throw fmbem_error{FMBEM_ERR_INVALID_MESH, "all nodes coincide"};
+    double side = 1.000001 * ext;
+    for (int q = 0; q < 3; ++q) h->root_min[q] = 0.5 * (mn[q] + mx[q]) - 0.5 * side;
+    h->root_w = side;
+
+    // keys and stable sort
+    uint64_t *key = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * N), *key2 = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * N);
+    int32_t *idx = (int32_t *)dev_alloc(h, sizeof(int32_t) * N), *idx2 = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    int32_t *f = (int32_t *)dev_alloc(h, sizeof(int32_t) * N), *fs = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    k_keys<<<nblk(N, TB), TB, 0, s>>>(h->upos, N, h->root_min[0], h->root_min[1], h->root_min[2],
+                                      (double)(1 << KEY_LEVELS) / side, key, idx);
+    CKL("k_keys");
+    for (int bit = 0; bit < 3 * KEY_LEVELS; ++bit) {
+        k_bitflag<<<nblk(N, TB), TB, 0, s>>>(key, N, bit, f);
+        int64_t nzero = scan_exclusive(h, f, fs, N, s);
+        k_bitscatter<<<nblk(N, TB), TB, 0, s>>>(key, idx, fs, N, nzero, bit, key2, idx2);
+        CKL("k_bitscatter");
+        std::swap(key, key2);
+        std::swap(idx, idx2);
+    }
+    h->perm = idx;
+    dev_free(h, idx2);
+
+    // node -> box maps of every level up to KEY_LEVELS, and max occupancy per level
+    std::vector<int32_t *> node_box(KEY_LEVELS + 1, nullptr), box_start(KEY_LEVELS + 1, nullptr);
+    std::vector<uint64_t *> lkey(KEY_LEVELS + 1, nullptr);
+    std::vector<int64_t> nbl(KEY_LEVELS + 1, 0);
+    int32_t *occ = (int32_t *)dev_alloc(h, sizeof(int32_t));
+    int lmax = -1;
+    const int cap = std::max(2, std::min(h->opt.max_level, KEY_LEVELS));
+    for (int l = 0; l <= cap; ++l) {
+        int shift = 3 * (KEY_LEVELS - l);
+        k_level_flags<<<nblk(N, TB), TB, 0, s>>>(key, N, shift, f);
+        int64_t nb = scan_exclusive(h, f, fs, N, s);
+        nbl[l] = nb;
+        node_box[l] = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+        box_start[l] = (int32_t *)dev_alloc(h, sizeof(int32_t) * nb);
+        lkey[l] = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * nb);
+        k_level_boxes<<<nblk(N, TB), TB, 0, s>>>(key, f, fs, N, shift, node_box[l], box_start[l], lkey[l]);
+        CKL("k_level_boxes");
+        CK(cudaMemsetAsync(occ, 0, sizeof(int32_t), s));
+        k_max_occupancy<<<nblk(nb, TB), TB, 0, s>>>(box_start[l], nb, N, occ);
+        int32_t mo;
+        CK(cudaMemcpyAsync(&mo, occ, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (l >= 2 && (mo <= h->opt.leaf_size || l == cap)) { lmax = l; break; }
+    }
+    dev_free(h, occ);
+    h->lmax = lmax;
+    h->lev.assign(lmax + 1, LevelInfo{});
+    int64_t tot = 0;
+    for (int l = 0; l <= lmax; ++l) {
+        h->lev[l].off = tot;
+        h->lev[l].n = nbl[l];
+        h->lev[l].w = side / (double)(1 << l);
+        tot += nbl[l];
+    }
+    h->nbox = tot;
+    h->box_key = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * tot);
+    h->box_ctr = (double *)dev_alloc(h, sizeof(double) * 3 * tot);
+    h->box_parent = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_cbeg = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_cend = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_nbeg = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_nend = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    CK(cudaMemsetAsync(h->box_cbeg, 0, sizeof(int32_t) * tot, s));
+    CK(cudaMemsetAsync(h->box_cend, 0, sizeof(int32_t) * tot, s));
+    for (int l = 0; l <= lmax; ++l) {
+        k_fill_level<<<nblk(nbl[l], TB), TB, 0, s>>>(nbl[l], h->lev[l].off, l, box_start[l], lkey[l], N,
+                                                     l > 0 ? node_box[l - 1] : nullptr, l > 0 ? h->lev[l - 1].off : 0,
+                                                     h->root_min[0], h->root_min[1], h->root_min[2], h->lev[l].w,
+                                                     h->box_key, h->box_ctr, h->box_parent, h->box_nbeg, h->box_nend);
+        CKL("k_fill_level");
+    }
+    for (int l = 0; l < lmax; ++l) {
+        k_children<<<nblk(nbl[l], TB), TB, 0, s>>>(nbl[l], h->lev[l].off, h->box_nbeg, h->box_nend, node_box[l + 1],
+                                                   h->lev[l + 1].off, h->box_cbeg, h->box_cend);
+        CKL("k_children");
+    }
+
+    // Neighbor lists of the leaves (including the leaf itself) and the near-pair count
+    {
+        const int l = lmax;
+        const int64_t nb = nbl[l], off = h->lev[l].off;
+        int32_t *cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * (nb + 1));
+        h->nbr_start = (int32_t *)dev_alloc(h, sizeof(int32_t) * (nb + 1));
+        int64_t *pc = (int64_t *)dev_alloc(h, sizeof(int64_t));
+        CK(cudaMemsetAsync(pc, 0, sizeof(int64_t), s));
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nb + 1), s));
+        k_neighbors<<<nblk(nb, TB), TB, 0, s>>>(nb, off, l, h->box_key, nullptr, cnt, nullptr, h->box_nbeg, h->box_nend, pc);
+        CKL("k_neighbors count");
+        int64_t total = scan_exclusive(h, cnt, h->nbr_start, nb + 1, s);
+        h->n_nbr = total;
+        h->nbr_idx = (int32_t *)dev_alloc(h, sizeof(int32_t) * std::max<int64_t>(total, 1));
+        k_neighbors<<<nblk(nb, TB), TB, 0, s>>>(nb, off, l, h->box_key, h->nbr_start, nullptr, h->nbr_idx, h->box_nbeg,
+                                                h->box_nend, nullptr);
+        CKL("k_neighbors fill");
+        int64_t pairs;
+        CK(cudaMemcpyAsync(&pairs, pc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        h->near_pairs = pairs - N;  // minus the self pairs
+        dev_free(h, cnt);
+        dev_free(h, pc);
+    }
+    // FF lists on levels 2..lmax (global CSR over all boxes; empty for levels 0..1)
+    {
+        int32_t *cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tot + 1));
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (tot + 1), s));
+        for (int l = 2; l <= lmax; ++l)
+            k_farfield<<<nblk(nbl[l], TB), TB, 0, s>>>(nbl[l], h->lev[l].off, l, h->box_key, h->lev[l - 1].off, nbl[l - 1],
+                                                       h->box_cbeg, h->box_cend, nullptr, cnt + h->lev[l].off, nullptr,
+                                                       nullptr);
+        CKL("k_farfield count");
+        h->ff_start = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tot + 1));
+        int64_t total = scan_exclusive(h, cnt, h->ff_start, tot + 1, s);
+        h->n_ff = total;
+        h->ff_src = (int32_t *)dev_alloc(h, sizeof(int32_t) * std::max<int64_t>(total, 1));
+        h->ff_off = (int16_t *)dev_alloc(h, sizeof(int16_t) * std::max<int64_t>(total, 1));
+        for (int l = 2; l <= lmax; ++l)
+            k_farfield<<<nblk(nbl[l], TB), TB, 0, s>>>(nbl[l], h->lev[l].off, l, h->box_key, h->lev[l - 1].off, nbl[l - 1],
+                                                       h->box_cbeg, h->box_cend, h->ff_start + h->lev[l].off, nullptr,
+                                                       h->ff_src, h->ff_off);
+        CKL("k_farfield fill");
+        std::vector<int32_t> hs(tot + 1);
+        CK(cudaMemcpyAsync(hs.data(), h->ff_start, sizeof(int32_t) * (tot + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        h->h_ff_count_level.assign(lmax + 1, 0);
+        for (int l = 2; l <= lmax; ++l)
+            h->h_ff_count_level[l] = hs[h->lev[l].off + h->lev[l].n] - hs[h->lev[l].off];
+        dev_free(h, cnt);
+    }
+
+    // leaf of every sorted node
+    h->node_leaf = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    CK(cudaMemcpyAsync(h->node_leaf, node_box[lmax], sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    k_add_offset<<<nblk(N, TB), TB, 0, s>>>(h->node_leaf, N, (int32_t)h->lev[lmax].off);
+    CKL("k_add_offset");
+
+    // sorted geometry
+    h->iperm = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    h->pos = (double *)dev_alloc(h, sizeof(double) * 3 * N);
+    h->nrm = (double *)dev_alloc(h, sizeof(double) * 3 * N);
+    h->w = (double *)dev_alloc(h, sizeof(double) * N);
+    h->dom = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    h->pos_hi = (float *)dev_alloc(h, sizeof(float) * 3 * N);
+    h->pos_lo = (float *)dev_alloc(h, sizeof(float) * 3 * N);
+    h->nrm_f = (float *)dev_alloc(h, sizeof(float) * 3 * N);
+    k_sorted_geometry<<<nblk(N, TB), TB, 0, s>>>(N, h->perm, h->upos, h->unrm, h->uw, h->udom, h->pos, h->nrm, h->w, h->dom,
+                                                 h->iperm, h->pos_hi, h->pos_lo, h->nrm_f);
+    CKL("k_sorted_geometry");
+    CK(cudaStreamSynchronize(s));
+    for (int l = 0; l <= KEY_LEVELS; ++l) {
+        if (node_box[l]) dev_free(h, node_box[l]);
+        if (box_start[l]) dev_free(h, box_start[l]);
+        if (lkey[l]) dev_free(h, lkey[l]);
+    }
+    dev_free(h, key);
+    dev_free(h, key2);
+    dev_free(h, f);
+    dev_free(h, fs);
+}

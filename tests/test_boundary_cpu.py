@@ -1,0 +1,72 @@
+"""Host-side checks of the C-ABI boundary that need no GPU: the library builds for sm_103a,
+loads, exports every function include/fmbem.h declares, and rejects invalid input on the host
+(mesh validation happens before any device work)."""
+import numpy as np
+import pytest
+
+import fmbem_inputs as fi
+import paper_1211_7177_gb300 as fm
+
+
+def test_library_loads_and_exports_header():
+    lib = fm.load_library()
+    names = fm.header_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_options():
+    o = fm.fmbem_default_options()
+    assert o.node_mode == fm.NODES_VERTEX and o.p == 8 and o.leaf_size == 64 and o.gmres_restart == 50
+    assert o.solve_precision == fm.FP64 and o.profile_phases == 0
+
+
+def _create(V, F, D, eps=(1.0, 2.25), mu=(1.0, 1.0), k0=1.0, **opt):
+    return fm.fmbem_create(V, F, D, eps, mu, k0, fm.fmbem_default_options(**opt), stream=0)
+
+
+@pytest.mark.parametrize("case", ["open", "flipped", "index", "domain", "degenerate", "junction"])
+def test_invalid_meshes_rejected_on_host(case):
+    V, F, D = fi.icosphere(1)
+    F = F.copy()
+    if case == "open":
+        F = F[1:]
+        D = D[1:]
+    elif case == "flipped":
+        F[3] = F[3][[0, 2, 1]]
+    elif case == "index":
+        F[0, 0] = len(V) + 5
+    elif case == "domain":
+        D = D.copy()
+        D[0] = 7
+    elif case == "degenerate":
+        V = V.copy()
+        a, b, c = F[5]
+        V[c] = V[a] + 2.0 * (V[b] - V[a])        # collinear triangle
+    elif case == "junction":
+        D = D.copy()
+        D[: len(D) // 2] = 2                      # one closed surface split between two scatterers
+    eps = (1.0, 2.25, 3.0) if case in ("domain", "junction") else (1.0, 2.25)
+    mu = (1.0, 1.0, 1.0) if case in ("domain", "junction") else (1.0, 1.0)
+    if case == "domain":
+        eps, mu = (1.0, 2.25), (1.0, 1.0)
+        with pytest.raises(ValueError):
+            _create(V, F, D, eps, mu)
+        return
+    with pytest.raises(fm.FMBEMError) as e:
+        _create(V, F, D, eps, mu)
+    assert e.value.status == 2, str(e.value)
+
+
+def test_invalid_arguments_rejected():
+    V, F, D = fi.icosphere(1)
+    with pytest.raises(fm.FMBEMError) as e:
+        _create(V, F, D, k0=-1.0)
+    assert e.value.status == 1
+    with pytest.raises(fm.FMBEMError) as e:
+        _create(V, F, D, p=40)
+    assert e.value.status == 1
+    with pytest.raises(fm.FMBEMError) as e:
+        _create(V, F, D, eps=(1.0, 0.0))
+    assert e.value.status == 1

@@ -1,0 +1,174 @@
+"""GPU parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the fast multipole matvec must match the dense one-point operator to a relative L2
+error <= 1e-4 (in FP64 and in FP32 arithmetic); exact steps that involve no multipole expansion
+(node geometry, plane-wave right-hand side, preconditioner) match to round-off; solved surface
+fields must agree with the oracle's solve to a relative L2 error <= 1e-3."""
+import numpy as np
+import pytest
+
+import fmbem_inputs as fi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1211_7177_gb300 as fm  # noqa: E402
+
+MATVEC_TOL = 1e-4
+SOLVE_TOL = 1e-3
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def case(mesh, eps, mu, k0, **opt):
+    V, F, D = mesh
+    o = oracle.Oracle(V, F, D, eps, mu, k0, mode="centroid" if opt.get("node_mode", 0) == 1 else "vertex")
+    g = fm.FMBEM(V, F, D, eps, mu, k0, **opt)
+    return o, g
+
+
+@pytest.fixture(scope="module")
+def sphere_s4():
+    """Dielectric sphere a=1, eps=2.25, k0 a=1, icosphere subdivision 4 (2562 nodes)."""
+    return case(fi.icosphere(4), [1.0, 2.25], [1.0, 1.0], 1.0)
+
+
+def test_node_geometry(sphere_s4):
+    o, g = sphere_s4
+    pos, nrm, w = g.node_geometry()
+    np.testing.assert_allclose(pos, o.s, atol=1e-14)
+    np.testing.assert_allclose(nrm, o.n, atol=1e-13)
+    np.testing.assert_allclose(w, o.w, rtol=1e-12)
+
+
+def test_plane_wave_rhs(sphere_s4):
+    o, g = sphere_s4
+    dirs, pols = fi.plane_wave_batch(3, seed=3)
+    b = g.plane_wave_rhs(dirs, pols).cpu().numpy()
+    np.testing.assert_allclose(b, o.plane_wave_rhs(dirs, pols), atol=1e-13)
+
+
+def test_preconditioner(sphere_s4):
+    o, g = sphere_s4
+    v = fi.random_complex((2, o.N, 6), seed=5)
+    z = g.precond_apply(to_dev(v)).cpu().numpy()
+    assert rel(z, o.precond_apply(v)) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [fm.FP64, fm.FP32])
+def test_matvec_sphere_s4(sphere_s4, precision):
+    o, g = sphere_s4
+    x = fi.random_complex((1, o.N, 6), seed=1)
+    y = g.matvec(to_dev(x), precision=precision).cpu().numpy()
+    yo = o.matvec(x)
+    err = rel(y, yo)
+    print(f"matvec precision={precision} rel L2 = {err:.3e}")
+    assert err < MATVEC_TOL
+    # both row groups separately
+    assert rel(y[..., :3], yo[..., :3]) < MATVEC_TOL and rel(y[..., 3:], yo[..., 3:]) < MATVEC_TOL
+    # a physical (smooth) input as well
+    b = o.plane_wave_rhs([0, 0, 1.0], [1.0, 0, 0])
+    assert rel(g.matvec(to_dev(b), precision=precision).cpu().numpy(), o.matvec(b)) < MATVEC_TOL
+
+
+def test_matvec_multi_rhs_columns(sphere_s4):
+    o, g = sphere_s4
+    x = fi.random_complex((3, o.N, 6), seed=7)
+    Y = g.matvec(to_dev(x)).cpu().numpy()
+    for r in range(3):
+        y1 = g.matvec(to_dev(x[r:r + 1])).cpu().numpy()
+        assert rel(Y[r:r + 1], y1) < 1e-12
+
+
+def test_solve_sphere_s4(sphere_s4):
+    o, g = sphere_s4
+    b = o.plane_wave_rhs([0, 0, 1.0], [1.0, 0, 0])
+    xo, its_o, res_o, conv_o = o.gmres(b, tol=1e-6)
+    x, its, res, st = g.solve(to_dev(b), tol=1e-6)
+    x = x.cpu().numpy()
+    assert st == 0 and res[0] <= 1e-6
+    # the reported residual is the true one
+    r = o.matvec(x) - b
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-4
+    err = rel(x, xo)
+    print(f"solve iters gpu={its[0]} oracle={its_o[0]}  rel L2 to oracle solve = {err:.3e}")
+    assert err < SOLVE_TOL
+
+
+def test_solve_mixed_precision_refinement():
+    o, g = case(fi.icosphere(4), [1.0, 2.25], [1.0, 1.0], 1.0, solve_precision=fm.FP32)
+    b = o.plane_wave_rhs([0, 0, 1.0], [1.0, 0, 0])
+    xo, _, _, _ = o.gmres(b, tol=1e-6)
+    x, its, res, st = g.solve(to_dev(b), tol=1e-6)
+    assert st == 0 and res[0] <= 1e-6
+    assert rel(x.cpu().numpy(), xo) < SOLVE_TOL
+
+
+# small leaves put more of the operator into the expansions, so they need a larger p for 1e-4
+@pytest.mark.parametrize("opt", [dict(node_mode=1), dict(p=4), dict(p=12), dict(leaf_size=8, p=10),
+                                 dict(leaf_size=400)])
+def test_matvec_options(opt):
+    mesh = fi.icosphere(3)
+    o, g = case(mesh, [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5, **opt)
+    x = fi.random_complex((1, o.N, 6), seed=11)
+    yo = o.matvec(x)
+    tol = 1e-2 if opt.get("p") == 4 else MATVEC_TOL
+    for prec in (fm.FP64, fm.FP32):
+        err = rel(g.matvec(to_dev(x), precision=prec).cpu().numpy(), yo)
+        print(opt, prec, f"{err:.3e}", g.tree_info())
+        assert err < tol
+
+
+def test_two_scatterers_and_permeability():
+    m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
+    m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
+    mesh = fi.merge_meshes(m1, m2)
+    o, g = case(mesh, [1.0, 2.25, -4 + 0.3j], [1.0, 1.3, 1.0], 1.2)
+    x = fi.random_complex((2, o.N, 6), seed=12)
+    yo = o.matvec(x)
+    for prec in (fm.FP64, fm.FP32):
+        assert rel(g.matvec(to_dev(x), precision=prec).cpu().numpy(), yo) < MATVEC_TOL
+
+
+def test_tiny_mesh():
+    o, g = case(fi.icosphere(1), [1.0, 2.25], [1.0, 1.0], 1.0)
+    x = fi.random_complex((1, o.N, 6), seed=2)
+    assert rel(g.matvec(to_dev(x)).cpu().numpy(), o.matvec(x)) < MATVEC_TOL
+
+
+def test_silver_sphere_s7_sampled_rows():
+    """Silver-like sphere, eps=-8.5+0.3i, k0 a=0.5, icosphere subdivision 7 (163842 nodes):
+    2048 seeded node rows of the dense operator."""
+    o, g = case(fi.icosphere(7), [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5)
+    x = fi.random_complex((1, o.N, 6), seed=1)
+    rows = fi.sample_rows(o.N, 2048, seed=2)
+    yo = o.matvec_rows(x, rows)
+    for prec in (fm.FP64, fm.FP32):
+        y = g.matvec(to_dev(x), precision=prec).cpu().numpy()[:, rows]
+        err = rel(y, yo)
+        print(f"s7 precision={prec} rel L2 on 2048 rows = {err:.3e}", g.tree_info())
+        assert err < MATVEC_TOL
+
+
+def test_torus_sampled_rows_multi_rhs():
+    """Torus R=1, r=0.25 on the 512x128 grid, eps=-10+0.4i, k0 R=1.5; 4 plane waves."""
+    o, g = case(fi.torus(), [1.0, -10 + 0.4j], [1.0, 1.0], 1.5)
+    dirs, pols = fi.plane_wave_batch(2, seed=3)
+    x = o.plane_wave_rhs(dirs, pols) + 0.1 * fi.random_complex((4, o.N, 6), seed=4)
+    rows = fi.sample_rows(o.N, 512, seed=5)
+    yo = o.matvec_rows(x, rows)
+    for prec in (fm.FP64, fm.FP32):
+        y = g.matvec(to_dev(x), precision=prec).cpu().numpy()[:, rows]
+        err = rel(y, yo)
+        print(f"torus precision={prec} rel L2 = {err:.3e}", g.tree_info())
+        assert err < MATVEC_TOL
