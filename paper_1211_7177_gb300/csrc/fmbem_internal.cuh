@@ -118,7 +118,18 @@ struct fmbem {
     int32_t *ff_start = nullptr, *ff_src = nullptr;       // CSR of FF lists over global boxes
     int16_t *ff_off = nullptr;                            // offset code 0..315 per FF entry
     int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;
+    int32_t max_leaf = 0;                                 // largest leaf occupancy
     std::vector<int64_t> h_ff_count_level;
+    // FF pairs of each level regrouped by translation offset, for the chunked M2L kernel:
+    // pair_e[]: CSR positions sorted by (level, offset, target); chunk k of level l covers
+    // pair_e[chunk_beg[k] .. chunk_beg[k] + chunk_cnt[k]) with one offset chunk_off[k]
+    int32_t *pair_e = nullptr, *pair_tgt = nullptr;       // [n_ff], [n_ff] (target of each CSR entry)
+    int32_t *chunk_beg = nullptr, *chunk_cnt = nullptr;
+    int16_t *chunk_off = nullptr;
+    std::vector<int64_t> h_chunk_first;                   // [lmax+2] first chunk of each level
+    std::vector<int64_t> h_pair_first;                    // [lmax+2] first CSR position of each level
+    void *ybuf = nullptr;                                 // per-pair M2L results
+    size_t ybuf_bytes = 0;
 
     // multipole bases and translations, per domain d in 0..J
     std::vector<double> lam;  // [(J+1)*(lmax+1)] scale lambda = |k_d| w_l
@@ -155,6 +166,8 @@ struct fmbem {
 // ------------------------------------------------------------------------------------------
 // helpers shared between translation units
 #define FMBEM_PI 3.14159265358979323846
+
+constexpr int M2L_CHUNK = 32;  // FF pairs per chunk of the offset-grouped M2L kernel
 
 // layout of the translation tables, per domain d and level l (global matrix index):
 //   M2L  [d][l][316]  for l = 2..lmax (levels below 2 unused)

@@ -158,24 +158,132 @@ __global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t
         for (int cc = 0; cc < ncol; ++cc) D[(((int64_t)d * nbox + g) * 3 * nr + col0 + cc) * p2 + r] = acc[cc];
 }
 
+// M2L on a chunk of FF pairs that share one offset o (S|R part of Eq. 2.21): the chunk's
+// translation matrix is staged once in shared memory and applied to every pair of the chunk,
+// Y[e][col][r] = sum_k T_o[k][r] C[src(e)][col0 + col][k], stored at the pair's CSR position e so
+// that k_l2l_reduce can sum each target's pairs in a fixed order.
+// Threads: rows_pad (= p2 rounded up to a warp multiple) x cg column groups; a warp shares its
+// columns, so the gathered inputs are read as shared-memory broadcasts.
+template <typename R, int MAXC>
+__global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0,
+                             int ncol, int pc, int cg, const int32_t *chunk_beg, const int32_t *chunk_cnt,
+                             const int16_t *chunk_off, const int32_t *pair_e, const int32_t *ff_src,
+                             const cx<R> *Tm2l, const cx<R> *C, cx<R> *Y, int64_t e_first) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *Ts = reinterpret_cast<cx<R> *>(smem_raw);  // [k][r]
+    cx<R> *Xs = Ts + p2 * p2;                          // [pair * ncol + col][k]
+    const int64_t ck = chunk0 + blockIdx.x;
+    const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+    const cx<R> *T = Tm2l + m2l_matrix(d, l, chunk_off[ck], lmax) * p2 * p2;
+    for (int i = threadIdx.x; i < p2 * p2; i += blockDim.x) Ts[i] = T[i];
+    const int rows_pad = blockDim.x / cg;
+    const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
+    for (int b0 = 0; b0 < cnt; b0 += pc) {
+        const int np = min(pc, cnt - b0);
+        const int nct = np * ncol;
+        __syncthreads();
+        for (int i = threadIdx.x; i < nct * p2; i += blockDim.x) {
+            int j = i / p2, k = i - j * p2;
+            int pr = j / ncol, col = j - pr * ncol;
+            int src = ff_src[pair_e[beg + b0 + pr]];
+            Xs[i] = C[(((int64_t)d * nbox + src) * 3 * nr + col0 + col) * p2 + k];
+        }
+        __syncthreads();
+        const int per = (nct + cg - 1) / cg;
+        const int j0 = grp * per, nj = min(nct, j0 + per) - j0;
+        if (r < p2 && nj > 0) {
+            cx<R> acc[MAXC];
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
+            const cx<R> *xb = Xs + j0 * p2;
+            for (int k = 0; k < p2; ++k) {
+                cx<R> t = Ts[k * p2 + r];
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q)
+                    if (q < nj) cfma(acc[q], t, xb[q * p2 + k]);
+            }
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q)
+                if (q < nj) {
+                    int j = j0 + q, pr = j / ncol, col = j - pr * ncol;
+                    int64_t e = pair_e[beg + b0 + pr];
+                    Y[((e - e_first) * ncol + col) * p2 + r] = acc[q];
+                }
+        }
+    }
+}
+
+// D(l,q) = R|R D(parent) + sum of the target's M2L pair results (Eq. 2.21), columns col0..col0+ncol
+template <typename R, int MAXC>
+__global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
+                             const int32_t *parent, const uint64_t *key, const int32_t *ff_start, const cx<R> *Tll,
+                             const cx<R> *Y, int64_t e_first, cx<R> *D) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
+    const int64_t g = off + blockIdx.x;
+    const int r = threadIdx.x;
+    cx<R> acc[MAXC];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
+    if (l >= 3) {
+        const int64_t P = parent[g];
+        for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
+            X[e] = D[(((int64_t)d * nbox + P) * 3 * nr + col0 + e / p2) * p2 + e % p2];
+        __syncthreads();
+        if (r < p2) {
+            const cx<R> *T = Tll + oct_matrix(d, l, (int)(key[g] & 7), lmax) * p2 * p2;
+            for (int k = 0; k < p2; ++k) {
+                cx<R> t = T[(int64_t)k * p2 + r];
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q)
+                    if (q < ncol) cfma(acc[q], t, X[q * p2 + k]);
+            }
+        }
+    }
+    if (r >= p2) return;
+    for (int e = ff_start[g]; e < ff_start[g + 1]; ++e) {
+        const cx<R> *y = Y + (e - e_first) * ncol * p2 + r;
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q)
+            if (q < ncol) acc[q] += y[q * p2];
+    }
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+        if (q < ncol) D[(((int64_t)d * nbox + g) * 3 * nr + col0 + q) * p2 + r] = acc[q];
+}
+
 // ---------------------------------------------------------------- near field + L2P + self (Step 4)
 template <typename R>
 struct SrcTile {
-    R px[128], py[128], pz[128];   // position (or position high part)
-    R lx[128], ly[128], lz[128];   // low part (single precision only)
+    R px[128], py[128], pz[128];   // position (or its high part)
+    R lx[128], ly[128], lz[128];   // low part (double-float positions only)
     R nx[128], ny[128], nz[128];
     int dom[128];
-    int idx[128];
     cx<R> dv[2][6][128];           // densities of the current right-hand side, both sides
 };
+template <typename R>
+union NearSmem {
+    SrcTile<R> tile;
+    cx<R> red[6][128];             // partial sums of the source slices
+};
 
+// fast single-precision transcendentals, precise double-precision ones
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float exp_(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ void sincos_(float x, float *s, float *c) { __sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+
+// one (source, target) pair of one domain: acc_i += -(K v)_i + g q_i  (Eq. 2.12 for beta != alpha)
+// r = s_beta - s_alpha, inv = 1/|r| (0 for the node itself, which then contributes nothing)
 template <typename R>
 __device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R> k, R nx, R ny, R nz, const cx<R> *v,
                                             const cx<R> *q, cx<R> *acc) {
     // g = e^{ikR}/(4 pi R), grad'g = c r with c = g (ik - 1/R)/R
-    R e = exp(-k.im * Rr);
+    R e = exp_(-k.im * Rr);
     R sn, cs;
-    sincos(k.re * Rr, &sn, &cs);
+    sincos_(k.re * Rr, &sn, &cs);
     R f = e * inv * (R)(0.25 / FMBEM_PI);
     cx<R> g = {f * cs, f * sn};
     // (i k - 1/R)/R with i k = -Im k + i Re k
@@ -193,6 +301,10 @@ __device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R>
     }
 }
 
+// Step 4 for one leaf: near field over the leaf and its Neighbor leaves (both domains), far field
+// from the leaf's local expansions (L2P), the analytic self block in double precision, and the
+// store of the 6 result rows in user order.  Up to 128 targets per pass; the 128 threads split as
+// (target, source slice) with 128 / n_targets slices, reduced in a fixed order.
 template <typename R, bool DOUBLE_FLOAT>
 __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
                                               const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
@@ -200,11 +312,10 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                                               const int32_t *dom, const int32_t *perm, const cx<R> *dens,
                                               const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
                                               const c64 *x, c64 *y) {
-    __shared__ SrcTile<R> T;
+    __shared__ NearSmem<R> S;
     __shared__ int rng_beg[32], rng_cum[33];
-    __shared__ cx<R> red[3][6][32];
+    SrcTile<R> &T = S.tile;
     const int64_t g = leaf_off + blockIdx.x;
-    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
     if (threadIdx.x == 0) {
         int cum = 0;
@@ -220,21 +331,20 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
     const int nsrc = rng_cum[nnb];
     const int t0 = nbeg[g], t1 = nend[g];
     for (int64_t r = 0; r < nr; ++r) {
-        for (int tb = t0; tb < t1; tb += 32) {
-            const int a = tb + lane;
-            const bool active = a < t1;
-            R ax = 0, ay = 0, az = 0, alx = 0, aly = 0, alz = 0;
-            int adom = -1;
-            if (active) {
-                ax = pos_hi[3 * a]; ay = pos_hi[3 * a + 1]; az = pos_hi[3 * a + 2];
-                if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
-                adom = dom[a];
-            }
-            cx<R> kb = to<R>(dc[0].k), kj = to<R>(dc[active ? adom : 0].k);
+        for (int tb = t0; tb < t1; tb += 128) {
+            const int nt = min(128, t1 - tb);
+            const int nsl = 128 / nt;
+            const int tg = threadIdx.x % nt, slice = threadIdx.x / nt;
+            const bool active = slice < nsl;
+            const int a = tb + tg;
+            R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2], alx = 0, aly = 0, alz = 0;
+            if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
+            const int adom = dom[a];
+            const cx<R> kb = to<R>(dc[0].k), kj = to<R>(dc[adom].k);
             cx<R> acc0[3] = {{0, 0}, {0, 0}, {0, 0}}, acc1[3] = {{0, 0}, {0, 0}, {0, 0}};
             for (int s0 = 0; s0 < nsrc; s0 += 128) {
                 __syncthreads();
-                {  // load a tile of sources
+                {  // stage a tile of sources
                     int e = s0 + threadIdx.x;
                     if (e < nsrc) {
                         int q = 0;
@@ -246,7 +356,6 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                         }
                         T.nx[threadIdx.x] = nrm[3 * i]; T.ny[threadIdx.x] = nrm[3 * i + 1]; T.nz[threadIdx.x] = nrm[3 * i + 2];
                         T.dom[threadIdx.x] = dom[i];
-                        T.idx[threadIdx.x] = i;
                         for (int sd = 0; sd < 2; ++sd)
                             for (int c = 0; c < 6; ++c) T.dv[sd][c][threadIdx.x] = dens[((sd * nr + r) * N + i) * 6 + c];
                     }
@@ -254,12 +363,11 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                 __syncthreads();
                 const int ns = min(128, nsrc - s0);
                 if (active)
-                    for (int u = slice; u < ns; u += 4) {
-                        if (T.idx[u] == a) continue;
+                    for (int u = slice; u < ns; u += nsl) {
                         R rx = T.px[u] - ax, ry = T.py[u] - ay, rz = T.pz[u] - az;
                         if (DOUBLE_FLOAT) { rx += T.lx[u] - alx; ry += T.ly[u] - aly; rz += T.lz[u] - alz; }
                         R R2 = rx * rx + ry * ry + rz * rz;
-                        R inv = (R)1 / sqrt(R2);
+                        R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
                         R Rr = R2 * inv;
                         cx<R> v[3], q[3];
                         for (int c = 0; c < 3; ++c) { v[c] = T.dv[0][c][u]; q[c] = T.dv[0][3 + c][u]; }
@@ -270,14 +378,16 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                         }
                     }
             }
-            // reduce the 4 source slices
+            // reduce the source slices in a fixed order
             __syncthreads();
-            if (slice > 0)
-                for (int c = 0; c < 3; ++c) { red[slice - 1][c][lane] = acc0[c]; red[slice - 1][3 + c][lane] = acc1[c]; }
+            for (int c = 0; c < 3; ++c) { S.red[c][threadIdx.x] = acc0[c]; S.red[3 + c][threadIdx.x] = acc1[c]; }
             __syncthreads();
-            if (slice == 0 && active) {
-                for (int s = 0; s < 3; ++s)
-                    for (int c = 0; c < 3; ++c) { acc0[c] += red[s][c][lane]; acc1[c] += red[s][3 + c][lane]; }
+            if (threadIdx.x < nt) {
+                for (int sl = 1; sl < nsl; ++sl)
+                    for (int c = 0; c < 3; ++c) {
+                        acc0[c] += S.red[c][sl * nt + threadIdx.x];
+                        acc1[c] += S.red[3 + c][sl * nt + threadIdx.x];
+                    }
                 // far field, L2P: y_i += sum_nm D[d][leaf][3r+i][nm] B_l2p[side][a][nm]
                 for (int sd = 0; sd < 2; ++sd) {
                     int d = sd == 0 ? 0 : adom;
@@ -291,16 +401,16 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                         cfma(acc[2], Dl[2 * p2 + q], b);
                     }
                 }
-                // self block A_self x (double precision) and store in user order
+                // self block A_self x in double precision, store in user order
                 int64_t u = perm[a];
                 const c64 *M = Mself + 36 * u;
                 const c64 *xa = x + (r * N + u) * 6;
                 c64 *ya = y + (r * N + u) * 6;
                 for (int row = 0; row < 6; ++row) {
-                    c64 s = row < 3 ? c64{(double)acc0[row].re, (double)acc0[row].im}
-                                    : c64{(double)acc1[row - 3].re, (double)acc1[row - 3].im};
-                    for (int c = 0; c < 6; ++c) cfma(s, M[row * 6 + c], xa[c]);
-                    ya[row] = s;
+                    c64 sacc = row < 3 ? c64{(double)acc0[row].re, (double)acc0[row].im}
+                                       : c64{(double)acc1[row - 3].re, (double)acc1[row - 3].im};
+                    for (int c = 0; c < 6; ++c) cfma(sacc, M[row * 6 + c], xa[c]);
+                    ya[row] = sacc;
                 }
             }
         }
@@ -318,6 +428,14 @@ static void ensure_scratch(fmbem *h, int64_t nr) {
     h->Cexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
     h->Dexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
     h->scratch_rhs = nr;
+    // per-pair M2L results of one level, one domain and up to 24 columns (chunked path only)
+    if (h->ybuf) { dev_free(h, h->ybuf); h->ybuf = nullptr; }
+    if (3 * nr <= 24) {
+        int64_t mp = 1;
+        for (int l = 2; l <= h->lmax; ++l) mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l]);
+        h->ybuf_bytes = cb * (size_t)mp * std::min<int64_t>(3 * nr, 24) * h->p2;
+        h->ybuf = dev_alloc(h, h->ybuf_bytes);
+    }
 }
 
 template <typename R>
@@ -344,20 +462,54 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     if (timing) CK(cudaEventRecord(h->ev[1], s));
     const int ncc = (int)((3 * nr + CC - 1) / CC);
     const size_t sm = sizeof(cx<R>) * CC * p2;
-    const int tbt = ((p2 + 31) / 32) * 32;
+    const int rows_pad = ((p2 + 31) / 32) * 32;
     for (int l = lmax; l >= 3; --l) {
         const LevelInfo &P = h->lev[l - 1];
-        k_m2m<R><<<dim3((unsigned)P.n, J + 1, ncc), tbt, sm, s>>>(P.off, l, lmax, nr, p2, h->nbox, h->box_cbeg,
-                                                                  h->box_cend, h->box_key, Tmm, C);
+        k_m2m<R><<<dim3((unsigned)P.n, J + 1, ncc), rows_pad, sm, s>>>(P.off, l, lmax, nr, p2, h->nbox, h->box_cbeg,
+                                                                       h->box_cend, h->box_key, Tmm, C);
         CKL("k_m2m");
     }
     if (timing) CK(cudaEventRecord(h->ev[2], s));
-    for (int l = 2; l <= lmax; ++l) {
-        const LevelInfo &Lv = h->lev[l];
-        k_down<R><<<dim3((unsigned)Lv.n, J + 1, ncc), tbt, sm, s>>>(Lv.off, l, lmax, nr, p2, h->nbox, h->box_parent,
-                                                                    h->box_key, h->ff_start, h->ff_src, h->ff_off, Tm2l,
-                                                                    Tll, C, D);
-        CKL("k_down");
+    // downward pass: offset-chunked M2L with a per-target reduction for few columns, the
+    // target-major kernel (translation matrices reused across many columns) otherwise
+    constexpr int MAXC = 24;
+    const int cg = std::max(1, std::min(4, 1024 / rows_pad));
+    const int ncol = (int)std::min<int64_t>(3 * nr, MAXC);
+    const size_t tbytes = sizeof(cx<R>) * p2 * p2;
+    int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
+    const size_t budget = 200 * 1024;
+    while (pc > 0 && tbytes + sizeof(cx<R>) * pc * ncol * p2 > budget) --pc;
+    const bool chunked = 3 * nr <= MAXC && pc >= 4 && h->ybuf != nullptr;
+    if (chunked) {
+        const size_t smc = tbytes + sizeof(cx<R>) * pc * ncol * p2;
+        CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+        cx<R> *Y = (cx<R> *)h->ybuf;
+        for (int l = 2; l <= lmax; ++l) {
+            const LevelInfo &Lv = h->lev[l];
+            const int64_t c0 = h->h_chunk_first[l], nch = h->h_chunk_first[l + 1] - c0;
+            const int64_t e_first = h->h_pair_first[l];
+            for (int d = 0; d <= J; ++d)
+                for (int col0 = 0; col0 < 3 * nr; col0 += ncol) {
+                    const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
+                    if (nch > 0)
+                        k_m2l_chunks<R, MAXC><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
+                            c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt, h->chunk_off,
+                            h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
+                    CKL("k_m2l_chunks");
+                    k_l2l_reduce<R, MAXC><<<(unsigned)Lv.n, rows_pad, sizeof(cx<R>) * nc * p2, s>>>(
+                        Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, h->box_parent, h->box_key, h->ff_start, Tll, Y,
+                        e_first, D);
+                    CKL("k_l2l_reduce");
+                }
+        }
+    } else {
+        for (int l = 2; l <= lmax; ++l) {
+            const LevelInfo &Lv = h->lev[l];
+            k_down<R><<<dim3((unsigned)Lv.n, J + 1, ncc), rows_pad, sm, s>>>(Lv.off, l, lmax, nr, p2, h->nbox,
+                                                                             h->box_parent, h->box_key, h->ff_start,
+                                                                             h->ff_src, h->ff_off, Tm2l, Tll, C, D);
+            CKL("k_down");
+        }
     }
     if (timing) CK(cudaEventRecord(h->ev[3], s));
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;

@@ -283,6 +283,23 @@ __global__ void k_sorted_geometry(int64_t N, const int32_t *perm, const double *
     dom[i] = udom[u];
 }
 
+// target box of every FF CSR entry
+__global__ void k_pair_targets(int64_t nbox, const int32_t *ff_start, int32_t *pair_tgt) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    for (int e = ff_start[b]; e < ff_start[b + 1]; ++e) pair_tgt[e] = (int32_t)b;
+}
+__global__ void k_count_offsets(int64_t e0, int64_t e1, const int16_t *code, int32_t *cnt) {
+    int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < e1) atomicAdd(&cnt[code[e]], 1);
+}
+// the order inside an offset bucket does not matter: every pair's result is stored at its own
+// CSR position and reduced per target in CSR order
+__global__ void k_fill_offsets(int64_t e0, int64_t e1, const int16_t *code, int32_t *next, int32_t *pair_e) {
+    int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < e1) pair_e[atomicAdd(&next[code[e]], 1)] = (int32_t)e;
+}
+
 __global__ void k_add_offset(int32_t *a, int64_t n, int32_t off) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) a[i] += off;
@@ -353,7 +370,9 @@ void build_tree(fmbem *h, cudaStream_t s) {
         int32_t mo;
         CK(cudaMemcpyAsync(&mo, occ, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (l >= 2 && (mo <= h->opt.leaf_size || l == cap)) { lmax = l; break; }
+        h->max_leaf = mo;
+        // refine until the mean leaf occupancy is at most leaf_size ("several elements" per leaf)
+        if (l >= 2 && ((double)N / (double)nb <= (double)h->opt.leaf_size || l == cap)) { lmax = l; break; }
     }
     dev_free(h, occ);
     h->lmax = lmax;
@@ -438,6 +457,56 @@ void build_tree(fmbem *h, cudaStream_t s) {
         for (int l = 2; l <= lmax; ++l)
             h->h_ff_count_level[l] = hs[h->lev[l].off + h->lev[l].n] - hs[h->lev[l].off];
         dev_free(h, cnt);
+
+        // regroup the FF pairs of each level by offset (counting sort) and cut chunks of at
+        // most M2L_CHUNK pairs sharing one translation matrix
+        const int64_t nff = std::max<int64_t>(total, 1);
+        h->pair_tgt = (int32_t *)dev_alloc(h, sizeof(int32_t) * nff);
+        h->pair_e = (int32_t *)dev_alloc(h, sizeof(int32_t) * nff);
+        k_pair_targets<<<nblk(tot, TB), TB, 0, s>>>(tot, h->ff_start, h->pair_tgt);
+        CKL("k_pair_targets");
+        int32_t *ocnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * 316);
+        std::vector<int32_t> hb(316), hbeg(316);
+        std::vector<int32_t> cbeg, ccnt;
+        std::vector<int16_t> coff;
+        h->h_chunk_first.assign(lmax + 2, 0);
+        h->h_pair_first.assign(lmax + 2, 0);
+        for (int l = 0; l <= lmax + 1; ++l) h->h_pair_first[l] = l <= lmax ? hs[h->lev[l].off] : hs[tot];
+        for (int l = 0; l <= lmax; ++l) {
+            h->h_chunk_first[l] = (int64_t)cbeg.size();
+            const int64_t e0 = hs[h->lev[l].off], e1 = hs[h->lev[l].off + h->lev[l].n];
+            if (e1 <= e0) continue;
+            CK(cudaMemsetAsync(ocnt, 0, sizeof(int32_t) * 316, s));
+            k_count_offsets<<<nblk(e1 - e0, TB), TB, 0, s>>>(e0, e1, h->ff_off, ocnt);
+            CKL("k_count_offsets");
+            CK(cudaMemcpyAsync(hb.data(), ocnt, sizeof(int32_t) * 316, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            int32_t acc = (int32_t)e0;
+            for (int o = 0; o < 316; ++o) {
+                hbeg[o] = acc;
+                for (int32_t c = 0; c < hb[o]; c += M2L_CHUNK) {
+                    cbeg.push_back(acc + c);
+                    ccnt.push_back(std::min(M2L_CHUNK, hb[o] - c));
+                    coff.push_back((int16_t)o);
+                }
+                acc += hb[o];
+            }
+            CK(cudaMemcpyAsync(ocnt, hbeg.data(), sizeof(int32_t) * 316, cudaMemcpyHostToDevice, s));
+            k_fill_offsets<<<nblk(e1 - e0, TB), TB, 0, s>>>(e0, e1, h->ff_off, ocnt, h->pair_e);
+            CKL("k_fill_offsets");
+        }
+        h->h_chunk_first[lmax + 1] = (int64_t)cbeg.size();
+        const size_t nc = std::max<size_t>(cbeg.size(), 1);
+        h->chunk_beg = (int32_t *)dev_alloc(h, sizeof(int32_t) * nc);
+        h->chunk_cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * nc);
+        h->chunk_off = (int16_t *)dev_alloc(h, sizeof(int16_t) * nc);
+        if (!cbeg.empty()) {
+            CK(cudaMemcpyAsync(h->chunk_beg, cbeg.data(), sizeof(int32_t) * cbeg.size(), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(h->chunk_cnt, ccnt.data(), sizeof(int32_t) * ccnt.size(), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(h->chunk_off, coff.data(), sizeof(int16_t) * coff.size(), cudaMemcpyHostToDevice, s));
+        }
+        CK(cudaStreamSynchronize(s));
+        dev_free(h, ocnt);
     }
 
     // leaf of every sorted node

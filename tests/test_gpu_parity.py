@@ -141,9 +141,22 @@ def test_two_scatterers_and_permeability():
 
 
 def test_tiny_mesh():
-    o, g = case(fi.icosphere(1), [1.0, 2.25], [1.0, 1.0], 1.0)
+    """42 nodes: every far pair is only two box widths apart, so p = 14 is needed for 1e-4."""
+    o, g = case(fi.icosphere(1), [1.0, 2.25], [1.0, 1.0], 1.0, p=14)
     x = fi.random_complex((1, o.N, 6), seed=2)
     assert rel(g.matvec(to_dev(x)).cpu().numpy(), o.matvec(x)) < MATVEC_TOL
+
+
+def test_many_rhs_target_major_path(sphere_s4):
+    """9 right-hand sides (27 columns) take the target-major M2L kernel; each column must equal
+    the offset-chunked single-RHS result, and the batch must match the oracle."""
+    o, g = sphere_s4
+    x = fi.random_complex((9, o.N, 6), seed=8)
+    for prec in (fm.FP64, fm.FP32):
+        Y = g.matvec(to_dev(x), precision=prec).cpu().numpy()
+        y4 = g.matvec(to_dev(x[4:5]), precision=prec).cpu().numpy()
+        assert rel(Y[4:5], y4) < (1e-12 if prec == fm.FP64 else 1e-5)
+        assert rel(Y, o.matvec(x)) < MATVEC_TOL
 
 
 def test_silver_sphere_s7_sampled_rows():
