@@ -178,29 +178,35 @@ __global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr,
     for (int i = threadIdx.x; i < p2 * p2; i += blockDim.x) Ts[i] = T[i];
     const int rows_pad = blockDim.x / cg;
     const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
+    // every column group owns exactly MAXC columns; columns past the sub-batch are zero-filled,
+    // so the inner product loop carries no per-column predicate
+    const int ncap = cg * MAXC;
     for (int b0 = 0; b0 < cnt; b0 += pc) {
         const int np = min(pc, cnt - b0);
         const int nct = np * ncol;
         __syncthreads();
-        for (int i = threadIdx.x; i < nct * p2; i += blockDim.x) {
+        for (int i = threadIdx.x; i < ncap * p2; i += blockDim.x) {
             int j = i / p2, k = i - j * p2;
-            int pr = j / ncol, col = j - pr * ncol;
-            int src = ff_src[pair_e[beg + b0 + pr]];
-            Xs[i] = C[(((int64_t)d * nbox + src) * 3 * nr + col0 + col) * p2 + k];
+            cx<R> v = {0, 0};
+            if (j < nct) {
+                int pr = j / ncol, col = j - pr * ncol;
+                int src = ff_src[pair_e[beg + b0 + pr]];
+                v = C[(((int64_t)d * nbox + src) * 3 * nr + col0 + col) * p2 + k];
+            }
+            Xs[i] = v;
         }
         __syncthreads();
-        const int per = (nct + cg - 1) / cg;
-        const int j0 = grp * per, nj = min(nct, j0 + per) - j0;
+        const int j0 = grp * MAXC, nj = min(MAXC, nct - j0);
         if (r < p2 && nj > 0) {
             cx<R> acc[MAXC];
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
             const cx<R> *xb = Xs + j0 * p2;
+#pragma unroll 2
             for (int k = 0; k < p2; ++k) {
                 cx<R> t = Ts[k * p2 + r];
 #pragma unroll
-                for (int q = 0; q < MAXC; ++q)
-                    if (q < nj) cfma(acc[q], t, xb[q * p2 + k]);
+                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, xb[q * p2 + k]);
             }
 #pragma unroll
             for (int q = 0; q < MAXC; ++q)
@@ -213,53 +219,133 @@ __global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr,
     }
 }
 
-// D(l,q) = R|R D(parent) + sum of the target's M2L pair results (Eq. 2.21), columns col0..col0+ncol
-template <typename R, int MAXC>
+// D(l,q) = R|R D(parent) + sum of the target's M2L pair results (Eq. 2.21), columns col0..col0+ncol.
+// Threads: rows_pad x ct column threads; a thread owns columns c = ct_id, ct_id + ct, ...
+template <typename R>
 __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
-                             const int32_t *parent, const uint64_t *key, const int32_t *ff_start, const cx<R> *Tll,
-                             const cx<R> *Y, int64_t e_first, cx<R> *D) {
+                             int ct, const int32_t *parent, const uint64_t *key, const int32_t *ff_start,
+                             const cx<R> *Tll, const cx<R> *Y, int64_t e_first, cx<R> *D) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
     const int64_t g = off + blockIdx.x;
-    const int r = threadIdx.x;
-    cx<R> acc[MAXC];
-#pragma unroll
-    for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
+    const int rows_pad = blockDim.x / ct;
+    const int r = threadIdx.x % rows_pad, cid = threadIdx.x / rows_pad;
+    const cx<R> *T = nullptr;
     if (l >= 3) {
         const int64_t P = parent[g];
         for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
             X[e] = D[(((int64_t)d * nbox + P) * 3 * nr + col0 + e / p2) * p2 + e % p2];
+        T = Tll + oct_matrix(d, l, (int)(key[g] & 7), lmax) * p2 * p2;
         __syncthreads();
-        if (r < p2) {
-            const cx<R> *T = Tll + oct_matrix(d, l, (int)(key[g] & 7), lmax) * p2 * p2;
-            for (int k = 0; k < p2; ++k) {
-                cx<R> t = T[(int64_t)k * p2 + r];
-#pragma unroll
-                for (int q = 0; q < MAXC; ++q)
-                    if (q < ncol) cfma(acc[q], t, X[q * p2 + k]);
-            }
-        }
     }
     if (r >= p2) return;
-    for (int e = ff_start[g]; e < ff_start[g + 1]; ++e) {
-        const cx<R> *y = Y + (e - e_first) * ncol * p2 + r;
-#pragma unroll
-        for (int q = 0; q < MAXC; ++q)
-            if (q < ncol) acc[q] += y[q * p2];
+    const int e0 = ff_start[g], e1 = ff_start[g + 1];
+    for (int c = cid; c < ncol; c += ct) {
+        cx<R> a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+        if (T)
+            for (int k = 0; k < p2; ++k) cfma(a0, T[(int64_t)k * p2 + r], X[c * p2 + k]);
+        const cx<R> *y = Y + ((e0 - e_first) * ncol + c) * p2 + r;
+        const int64_t st = (int64_t)ncol * p2;
+        int e = e0;
+        for (; e + 4 <= e1; e += 4, y += 4 * st) {
+            a0 += y[0];
+            a1 += y[st];
+            a2 += y[2 * st];
+            a3 += y[3 * st];
+        }
+        for (; e < e1; ++e, y += st) a0 += y[0];
+        D[(((int64_t)d * nbox + g) * 3 * nr + col0 + c) * p2 + r] = (a0 + a1) + (a2 + a3);
     }
+}
+
+// M2L + L2L for many columns (Eq. 2.21) as a register-tiled complex GEMM per target box:
+// D[t][:, tile] = T_ll(oct) D[parent][:, tile] + sum_FF T_o C[src][:, tile], tile = 64 columns.
+// For every translation the CTA stages T (input-major, p2 x p2) and the input columns transposed
+// to [k][col]; thread (rg, cgp) accumulates rows 4rg..4rg+3 x columns 4cgp..4cgp+3.
+constexpr int MT_COLS = 64;
+template <typename R>
+__device__ __forceinline__ void mt_stage(const cx<R> *__restrict__ T, const cx<R> *__restrict__ Xg, int p2, int ncol_here,
+                                         cx<R> *Ts, cx<R> *Cs) {
+    for (int i = threadIdx.x; i < p2 * p2; i += blockDim.x) Ts[i] = T[i];
+    // Xg points at column 0 of the tile: element (c, k) at Xg[c * p2 + k]
+    for (int i = threadIdx.x; i < p2 * MT_COLS; i += blockDim.x) {
+        int c = i / p2, k = i - c * p2;
+        Cs[k * MT_COLS + c] = c < ncol_here ? Xg[(int64_t)c * p2 + k] : cx<R>{0, 0};
+    }
+}
+template <typename R>
+__device__ __forceinline__ void mt_accumulate(const cx<R> *Ts, const cx<R> *Cs, int p2, int rg, int cgp, cx<R> acc[4][4]) {
+    const int r0 = 4 * rg, c0 = 4 * cgp;
+#pragma unroll 4
+    for (int k = 0; k < p2; ++k) {
+        cx<R> t[4], c[4];
 #pragma unroll
-    for (int q = 0; q < MAXC; ++q)
-        if (q < ncol) D[(((int64_t)d * nbox + g) * 3 * nr + col0 + q) * p2 + r] = acc[q];
+        for (int i = 0; i < 4; ++i) t[i] = (r0 + i < p2) ? Ts[k * p2 + r0 + i] : cx<R>{0, 0};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = Cs[k * MT_COLS + c0 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cfma(acc[i][j], t[i], c[j]);
+    }
+}
+template <typename R>
+__global__ void k_m2l_multi(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *parent,
+                            const uint64_t *key, const int32_t *ff_start, const int32_t *ff_src, const int16_t *ff_off,
+                            const cx<R> *Tm2l, const cx<R> *Tll, const cx<R> *C, cx<R> *D) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *Ts = reinterpret_cast<cx<R> *>(smem_raw);
+    cx<R> *Cs = Ts + p2 * p2;
+    const int64_t g = off + blockIdx.x;
+    const int d = blockIdx.y;
+    const int ncols = (int)(3 * nr);
+    const int col0 = blockIdx.z * MT_COLS;
+    const int nh = min(MT_COLS, ncols - col0);
+    const int rg = threadIdx.x % ((p2 + 3) / 4), cgp = threadIdx.x / ((p2 + 3) / 4);
+    cx<R> acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = {0, 0};
+    if (l >= 3) {
+        const int64_t P = parent[g];
+        mt_stage<R>(Tll + oct_matrix(d, l, (int)(key[g] & 7), lmax) * p2 * p2,
+                    D + (((int64_t)d * nbox + P) * ncols + col0) * p2, p2, nh, Ts, Cs);
+        __syncthreads();
+        mt_accumulate<R>(Ts, Cs, p2, rg, cgp, acc);
+    }
+    for (int e = ff_start[g]; e < ff_start[g + 1]; ++e) {
+        __syncthreads();
+        mt_stage<R>(Tm2l + m2l_matrix(d, l, ff_off[e], lmax) * p2 * p2,
+                    C + (((int64_t)d * nbox + ff_src[e]) * ncols + col0) * p2, p2, nh, Ts, Cs);
+        __syncthreads();
+        mt_accumulate<R>(Ts, Cs, p2, rg, cgp, acc);
+    }
+    const int r0 = 4 * rg, c0 = 4 * cgp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (c0 + j < nh)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (r0 + i < p2) D[(((int64_t)d * nbox + g) * ncols + col0 + c0 + j) * p2 + r0 + i] = acc[i][j];
 }
 
 // ---------------------------------------------------------------- near field + L2P + self (Step 4)
 template <typename R>
+struct __align__(4 * sizeof(R)) V4 {
+    R x, y, z, w;
+};
+template <typename R>
+struct __align__(2 * sizeof(R)) V2 {
+    R x, y;
+};
+// one tile of 128 sources, packed so that a pair reads its source with a few vector loads
+template <typename R>
 struct SrcTile {
-    R px[128], py[128], pz[128];   // position (or its high part)
-    R lx[128], ly[128], lz[128];   // low part (double-float positions only)
-    R nx[128], ny[128], nz[128];
-    int dom[128];
-    cx<R> dv[2][6][128];           // densities of the current right-hand side, both sides
+    V4<R> pa[128];      // position (high part) and scatterer id
+    V4<R> pb[128];      // position low part (double-float only) and n_x
+    V2<R> pn[128];      // n_y, n_z
+    V4<R> dv[2][3][128];  // densities (v0, v1), (v2, q0), (q1, q2) of the current RHS, both sides
 };
 template <typename R>
 union NearSmem {
@@ -281,7 +367,7 @@ template <typename R>
 __device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R> k, R nx, R ny, R nz, const cx<R> *v,
                                             const cx<R> *q, cx<R> *acc) {
     // g = e^{ikR}/(4 pi R), grad'g = c r with c = g (ik - 1/R)/R
-    R e = exp_(-k.im * Rr);
+    R e = k.im != (R)0 ? exp_(-k.im * Rr) : (R)1;  // warp-uniform: k is per domain
     R sn, cs;
     sincos_(k.re * Rr, &sn, &cs);
     R f = e * inv * (R)(0.25 / FMBEM_PI);
@@ -350,31 +436,43 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                         int q = 0;
                         while (q + 1 < nnb && rng_cum[q + 1] <= e) ++q;
                         int i = rng_beg[q] + (e - rng_cum[q]);
-                        T.px[threadIdx.x] = pos_hi[3 * i]; T.py[threadIdx.x] = pos_hi[3 * i + 1]; T.pz[threadIdx.x] = pos_hi[3 * i + 2];
-                        if (DOUBLE_FLOAT) {
-                            T.lx[threadIdx.x] = pos_lo[3 * i]; T.ly[threadIdx.x] = pos_lo[3 * i + 1]; T.lz[threadIdx.x] = pos_lo[3 * i + 2];
+                        const int t = threadIdx.x;
+                        T.pa[t] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
+                        R lo[3] = {0, 0, 0};
+                        if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
+                        T.pb[t] = V4<R>{lo[0], lo[1], lo[2], nrm[3 * i]};
+                        T.pn[t] = V2<R>{nrm[3 * i + 1], nrm[3 * i + 2]};
+                        for (int sd = 0; sd < 2; ++sd) {
+                            const cx<R> *dn = dens + ((sd * nr + r) * N + i) * 6;
+                            for (int c = 0; c < 3; ++c)
+                                T.dv[sd][c][t] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
                         }
-                        T.nx[threadIdx.x] = nrm[3 * i]; T.ny[threadIdx.x] = nrm[3 * i + 1]; T.nz[threadIdx.x] = nrm[3 * i + 2];
-                        T.dom[threadIdx.x] = dom[i];
-                        for (int sd = 0; sd < 2; ++sd)
-                            for (int c = 0; c < 6; ++c) T.dv[sd][c][threadIdx.x] = dens[((sd * nr + r) * N + i) * 6 + c];
                     }
                 }
                 __syncthreads();
                 const int ns = min(128, nsrc - s0);
+                const R adom_r = (R)adom;
                 if (active)
                     for (int u = slice; u < ns; u += nsl) {
-                        R rx = T.px[u] - ax, ry = T.py[u] - ay, rz = T.pz[u] - az;
-                        if (DOUBLE_FLOAT) { rx += T.lx[u] - alx; ry += T.ly[u] - aly; rz += T.lz[u] - alz; }
+                        const V4<R> pa = T.pa[u], pb = T.pb[u];
+                        const V2<R> pn = T.pn[u];
+                        R rx = pa.x - ax, ry = pa.y - ay, rz = pa.z - az;
+                        if (DOUBLE_FLOAT) { rx += pb.x - alx; ry += pb.y - aly; rz += pb.z - alz; }
                         R R2 = rx * rx + ry * ry + rz * rz;
                         R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
                         R Rr = R2 * inv;
                         cx<R> v[3], q[3];
-                        for (int c = 0; c < 3; ++c) { v[c] = T.dv[0][c][u]; q[c] = T.dv[0][3 + c][u]; }
-                        pair_kernel<R>(rx, ry, rz, inv, Rr, kb, -T.nx[u], -T.ny[u], -T.nz[u], v, q, acc0);
-                        if (T.dom[u] == adom) {
-                            for (int c = 0; c < 3; ++c) { v[c] = T.dv[1][c][u]; q[c] = T.dv[1][3 + c][u]; }
-                            pair_kernel<R>(rx, ry, rz, inv, Rr, kj, T.nx[u], T.ny[u], T.nz[u], v, q, acc1);
+                        {
+                            const V4<R> a0 = T.dv[0][0][u], a1 = T.dv[0][1][u], a2 = T.dv[0][2][u];
+                            v[0] = {a0.x, a0.y}; v[1] = {a0.z, a0.w}; v[2] = {a1.x, a1.y};
+                            q[0] = {a1.z, a1.w}; q[1] = {a2.x, a2.y}; q[2] = {a2.z, a2.w};
+                        }
+                        pair_kernel<R>(rx, ry, rz, inv, Rr, kb, -pb.w, -pn.x, -pn.y, v, q, acc0);
+                        if (pa.w == adom_r) {
+                            const V4<R> a0 = T.dv[1][0][u], a1 = T.dv[1][1][u], a2 = T.dv[1][2][u];
+                            v[0] = {a0.x, a0.y}; v[1] = {a0.z, a0.w}; v[2] = {a1.x, a1.y};
+                            q[0] = {a1.z, a1.w}; q[1] = {a2.x, a2.y}; q[2] = {a2.z, a2.w};
+                            pair_kernel<R>(rx, ry, rz, inv, Rr, kj, pb.w, pn.x, pn.y, v, q, acc1);
                         }
                     }
             }
@@ -473,15 +571,15 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // downward pass: offset-chunked M2L with a per-target reduction for few columns, the
     // target-major kernel (translation matrices reused across many columns) otherwise
     constexpr int MAXC = 24;
-    const int cg = std::max(1, std::min(4, 1024 / rows_pad));
     const int ncol = (int)std::min<int64_t>(3 * nr, MAXC);
     const size_t tbytes = sizeof(cx<R>) * p2 * p2;
-    int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
     const size_t budget = 200 * 1024;
-    while (pc > 0 && tbytes + sizeof(cx<R>) * pc * ncol * p2 > budget) --pc;
-    const bool chunked = 3 * nr <= MAXC && pc >= 4 && h->ybuf != nullptr;
+    int cg = std::max(1, std::min(4, 1024 / rows_pad));
+    while (cg > 1 && tbytes + sizeof(cx<R>) * cg * MAXC * p2 > budget) --cg;
+    const size_t smc = tbytes + sizeof(cx<R>) * cg * MAXC * p2;
+    const int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
+    const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr;
     if (chunked) {
-        const size_t smc = tbytes + sizeof(cx<R>) * pc * ncol * p2;
         CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         cx<R> *Y = (cx<R> *)h->ybuf;
         for (int l = 2; l <= lmax; ++l) {
@@ -496,11 +594,24 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                             c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt, h->chunk_off,
                             h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
                     CKL("k_m2l_chunks");
-                    k_l2l_reduce<R, MAXC><<<(unsigned)Lv.n, rows_pad, sizeof(cx<R>) * nc * p2, s>>>(
-                        Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, h->box_parent, h->box_key, h->ff_start, Tll, Y,
-                        e_first, D);
+                    const int ct = std::max(1, std::min(nc, 1024 / rows_pad));
+                    k_l2l_reduce<R><<<(unsigned)Lv.n, rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
+                        Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll,
+                        Y, e_first, D);
                     CKL("k_l2l_reduce");
                 }
+        }
+    } else if (sizeof(cx<R>) * (size_t)(p2 * p2 + p2 * MT_COLS) <= budget) {
+        const size_t smm = sizeof(cx<R>) * (size_t)(p2 * p2 + p2 * MT_COLS);
+        CK(cudaFuncSetAttribute(k_m2l_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+        const int nt = ((p2 + 3) / 4) * (MT_COLS / 4);
+        const unsigned ntile = (unsigned)((3 * nr + MT_COLS - 1) / MT_COLS);
+        for (int l = 2; l <= lmax; ++l) {
+            const LevelInfo &Lv = h->lev[l];
+            k_m2l_multi<R><<<dim3((unsigned)Lv.n, J + 1, ntile), nt, smm, s>>>(Lv.off, l, lmax, nr, p2, h->nbox,
+                                                                             h->box_parent, h->box_key, h->ff_start,
+                                                                             h->ff_src, h->ff_off, Tm2l, Tll, C, D);
+            CKL("k_m2l_multi");
         }
     } else {
         for (int l = 2; l <= lmax; ++l) {
