@@ -1,14 +1,17 @@
 """Benchmark of the fast-multipole BEM matvec (and the GMRES solve it drives) on GB300.
 
 Default workload: silver-like sphere a=1, eps=-8.5+0.3i, k0 a=0.5, icosphere subdivision 7
-(163842 Nystrom nodes), one x-polarised plane wave along +z, plain FP64 method.  One step = one
-fast-multipole matvec y = A x through every pass (source densities, P2M, M2M, M2L + L2L, near
-field + L2P + self blocks).  value = nodes x right-hand sides per second of device time, inputs
-resident in HBM; L2 is flushed (256 MiB write) before every timed step.
+(163842 Nystrom nodes), one x-polarised plane wave along +z, plain FP64 method, truncation p=10
+(the FMM tolerance 1e-5 class: 4.7e-6 relative L2 against the dense FP64 oracle on 2048 rows).
+One step = one fast-multipole matvec y = A x through every pass (source densities, P2M, M2M,
+M2L + L2L, near field + L2P + self blocks).  value = nodes x right-hand sides per second of device
+time, inputs resident in HBM; L2 is flushed (256 MiB write) before every timed step.
 
 Also reported: e2e (same metric through the C ABI with pinned host buffers and the host<->device
-copies inside the timed region), the roofline of the dominant kernel, the solve time to a 1e-4
-relative residual, and the FP64 CPU oracle timed on a bounded sample of rows (cpu_baseline).
+copies inside the timed region), the roofline of the dominant kernel, the same matvec in FP32
+arithmetic, the solve time to a 1e-4 relative residual for the plain FP64 solve and for the
+FP32-inner / FP64-outer refined solve, and the FP64 CPU oracle timed on a bounded sample of rows
+(cpu_baseline).  ``--workload torus_512x128`` runs the 128-right-hand-side batch.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm of this comparison).
 """
@@ -32,14 +35,19 @@ import fmbem_inputs as fi  # noqa: E402
 
 WORKLOADS = {
     "silver_sphere_s7": dict(mesh=lambda: fi.icosphere(7), eps=[1.0, -8.5 + 0.3j], mu=[1.0, 1.0], k0=0.5, n_rhs=1,
-                             desc="silver-like sphere a=1, eps=-8.5+0.3i, k0 a=0.5, icosphere subdivision 7"),
-    "sphere_s4": dict(mesh=lambda: fi.icosphere(4), eps=[1.0, 2.25], mu=[1.0, 1.0], k0=1.0, n_rhs=1,
+                             p=10, desc="silver-like sphere a=1, eps=-8.5+0.3i, k0 a=0.5, icosphere subdivision 7"),
+    "sphere_s4": dict(mesh=lambda: fi.icosphere(4), eps=[1.0, 2.25], mu=[1.0, 1.0], k0=1.0, n_rhs=1, p=8,
                       desc="dielectric sphere a=1, eps=2.25, k0 a=1, icosphere subdivision 4"),
-    "torus_512x128": dict(mesh=lambda: fi.torus(), eps=[1.0, -10 + 0.4j], mu=[1.0, 1.0], k0=1.5, n_rhs=128,
+    "torus_512x128": dict(mesh=lambda: fi.torus(), eps=[1.0, -10 + 0.4j], mu=[1.0, 1.0], k0=1.5, n_rhs=128, p=8,
                           desc="torus R=1 r=0.25 512x128 grid, eps=-10+0.4i, k0 R=1.5, 128 plane waves"),
 }
 METRIC = "FMM-BEM matvec points*RHS/s"
 UNIT = "points*RHS/s"
+# flops per (near pair, domain): geometry and kernel scalars, and per right-hand side, counted
+# from the near-field kernel's source (FMA = 2)
+NEAR_PAIR = 21
+NEAR_RHS = 103
+PEAK_TFLOPS = {"fp64": 1.2, "fp32": 74.6}  # measured FMA throughput on GB300 (self-written probe)
 
 
 def parse():
@@ -50,18 +58,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="silver_sphere_s7", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--p", type=int, default=0, help="truncation number (0 = the workload's)")
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def rhs_batch(n_rhs):
@@ -72,7 +78,7 @@ def rhs_batch(n_rhs):
 
 # ------------------------------------------------------------------------------- CPU oracle
 def oracle_rows_rate(wl, rows_per_call, calls, seed=2):
-    """FP64 oracle: rows of the dense operator per second on a bounded sample."""
+    """FP64 oracle: seconds for rows_per_call rows of the dense operator, `calls` times."""
     import oracle
     V, F, D = wl["mesh"]()
     o = oracle.Oracle(V, F, D, wl["eps"], wl["mu"], wl["k0"])
@@ -92,8 +98,8 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    rows = 512 if wl["n_rhs"] == 1 else 64
-    N, _, _ = oracle_rows_rate(wl, rows, 1)  # warm-up / build
+    rows = 512 if wl["n_rhs"] == 1 else 32
+    N, _, _ = oracle_rows_rate(wl, rows, 1)
     for _ in range(max(0, args.warmup - 1)):
         oracle_rows_rate(wl, rows, 1)
     _, times, cores = oracle_rows_rate(wl, rows, args.steps)
@@ -118,8 +124,9 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
@@ -153,6 +160,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- GPU arm
+def roofline(info, p, nr, n_dom, phases, precision):
+    keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
+    avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
+    dom = max(keys, key=lambda k: avg[k])
+    if dom == "m2l_l2l":
+        flops = 8.0 * p ** 4 * 3 * nr * info["ff_pairs"] * n_dom
+        name = "M2L + L2L (k_m2l_chunks + k_l2l_reduce / k_m2l_multi)"
+    elif dom == "near_l2p_self":
+        flops = info["near_pairs"] * n_dom * (NEAR_PAIR + NEAR_RHS * nr)
+        name = "near field + L2P + self (k_near)"
+    else:
+        flops, name = None, dom
+    achieved = flops / (avg[dom] * 1e-3) / 1e12 if flops else None
+    peak = PEAK_TFLOPS[precision]
+    return dict(kernel=name, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=achieved / peak if achieved else None, traffic=None,
+                peak_source=f"measured {precision.upper()} FMA throughput of GB300 (self-written probe)",
+                algorithmic_flops_per_launch=flops, phase_ms=avg)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -164,14 +191,16 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
+    p = args.p or wl["p"]
     prec = fm.FP64 if args.precision == "fp64" else fm.FP32
     V, F, D = wl["mesh"]()
     t0 = time.perf_counter()
-    g = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=args.p, leaf_size=args.leaf, profile_phases=1)
+    g = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, profile_phases=1)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     info = g.tree_info()
     N, nr = g.N, wl["n_rhs"]
+    n_dom = len(wl["eps"])
     dirs, pols = rhs_batch(nr)
     b = g.plane_wave_rhs(dirs, pols)
     x = b.clone()
@@ -179,45 +208,45 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        g.matvec(x, y, precision=prec)
+    def timed(precision, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            g.matvec(x, y, precision=precision)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if clocks else None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        phases = []
+        wall0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            g.matvec(x, y, precision=precision)
+            ev[k][1].record(stream)
+            phases.append(g.last_matvec_times())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if world > 1:
+            dist.barrier()
+        clk = sampler.stop() if sampler else None
+        ms = statistics.mean(a.elapsed_time(bb) for a, bb in ev)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, phases, wall, clk
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    # per-phase times of one matvec (events recorded inside the library on this stream)
-    phases = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-        phases.append(g.last_matvec_times())
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = [a.elapsed_time(bb) for a, bb in ev]
-    ms_step = sum(ms) / len(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step, phases, wall, clk = timed(prec, args.steps, args.warmup, clocks=True)
     value = world * N * nr / (ms_step * 1e-3)
+    roof = roofline(info, p, nr, n_dom, phases, args.precision)
 
     # e2e through the C ABI: pinned host x -> device, matvec, device -> pinned host y
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     for _ in range(2):
         x.copy_(xh, non_blocking=True)
-        step()
+        g.matvec(x, y, precision=prec)
         yh.copy_(y, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -226,7 +255,7 @@ def run_ours(args):
         flush.fill_(float(k))
         e0.record(stream)
         x.copy_(xh, non_blocking=True)
-        step()
+        g.matvec(x, y, precision=prec)
         yh.copy_(y, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
@@ -234,67 +263,72 @@ def run_ours(args):
     e2e_val = world * N * nr / (statistics.mean(e2e_ms) * 1e-3)
     nbytes = x.numel() * 16
 
-    # roofline of the dominant kernel (phase with the largest share)
-    keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
-    avg = {kk: statistics.mean(ph[kk] for ph in phases) for kk in keys}
-    dom = max(keys, key=lambda kk: avg[kk])
-    p = args.p
-    cols = 3 * nr
-    n_dom = len(wl["eps"])
-    peaks = {"fp64": 1.2e12, "fp32": 74.6e12}
-    if dom == "m2l_l2l":
-        flops = 8.0 * p ** 4 * cols * info["ff_pairs"] * n_dom
-        name = "k_down (M2L + L2L)"
-    elif dom == "near_l2p_self":
-        flops = info["near_pairs"] * n_dom * (NEAR_PAIR + NEAR_RHS * nr)
-        name = "k_near (P2P + L2P + self)"
-    else:
-        flops = None
-        name = dom
-    achieved = flops / (avg[dom] * 1e-3) if flops else None
-    peak = peaks[args.precision]
-    roof = dict(kernel=name, bound="alu", achieved=achieved / 1e12 if achieved else None, peak=peak / 1e12,
-                unit="TFLOP/s", frac=(achieved / peak) if achieved else None, traffic=None,
-                peak_source=f"measured {args.precision.upper()} FMA throughput on GB300 (self-written probe)",
-                phase_ms=avg)
+    other = None
+    if args.precision == "fp64" and not args.no_fp32:
+        ms32, ph32, _, _ = timed(fm.FP32, args.steps, args.warmup)
+        other = dict(precision="fp32", value=world * N * nr / (ms32 * 1e-3), ms_per_step=ms32,
+                     roofline=roofline(info, p, nr, n_dom, ph32, "fp32"))
+    if nr > 1:
+        # the plain method's form for comparison: FP64 arithmetic, one right-hand side per matvec
+        x1, y1 = x[:1].contiguous(), y[:1].contiguous()
+        for _ in range(2):
+            g.matvec(x1, y1, precision=fm.FP64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            g.matvec(x1, y1, precision=fm.FP64)
+        e1.record(stream)
+        e1.synchronize()
+        ms1 = e0.elapsed_time(e1) / 3
+        other = dict(other or {}, fp64_single_rhs=dict(value=world * N / (ms1 * 1e-3), ms_per_step=ms1))
 
     solve = None
     if not args.no_solve:
-        xs = torch.zeros_like(b)
-        torch.cuda.synchronize()
-        s0 = time.perf_counter()
-        _, its, rr, st = g.solve(b, xs, tol=1e-4, max_iter=500)
-        torch.cuda.synchronize()
-        solve = dict(tol=1e-4, ms=1e3 * (time.perf_counter() - s0), iters=int(its.max()), relres=float(rr.max()),
-                     status=int(st), precision="fp64")
+        solve = {}
+        kinds = (("plain_fp64", fm.FP64), ("fp32_inner_fp64_refined", fm.FP32)) if nr == 1 else \
+            (("fp32_inner_fp64_refined", fm.FP32),)
+        for label, sp in kinds:
+            h2 = g if sp == fm.FP64 else fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf,
+                                                   solve_precision=fm.FP32)
+            xs = torch.zeros_like(b)
+            h2.solve(b, xs, tol=1e-4, max_iter=1000)  # warm-up (allocates the Krylov basis)
+            xs.zero_()
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            _, its, rr, st = h2.solve(b, xs, tol=1e-4, max_iter=1000)
+            torch.cuda.synchronize()
+            solve[label] = dict(tol=1e-4, ms=1e3 * (time.perf_counter() - s0), iters=int(its.max()),
+                                relres=float(rr.max()), status=int(st))
+            if h2 is not g:
+                h2.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rows = 1024 if nr == 1 else 64
+        rows = 1024 if nr == 1 else 16
         Nn, times, cores = oracle_rows_rate(wl, rows, 2)
         cpu = dict(value=rows * nr / min(times), unit=UNIT, cores=cores, kind="oracle",
-                   sample=f"{rows} seeded node rows of the {Nn}-node dense FP64 operator, best of 2")
+                   sample=f"{rows} seeded node rows x {nr} RHS of the {Nn}-node dense FP64 operator, best of 2")
 
-    launches_per_step = 3 + (info["l_max"] - 2) + (info["l_max"] - 1)
+    # kernels per matvec: k_prep, k_p2m, k_m2m per level 3..l_max, the downward pass per level
+    # 2..l_max (chunked: k_m2l_chunks + k_l2l_reduce per domain; many columns: k_m2l_multi), k_near
+    chunked = 3 * nr <= 24
+    n_down = (info["l_max"] - 1) * (2 * n_dom if chunked else 1)
+    launches_per_step = 3 + (info["l_max"] - 2) + n_down
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64" if args.precision == "fp64" else "f32", data="synthetic",
                 config=dict(workload=args.workload, desc=wl["desc"], nodes=N, n_rhs=nr, p=p, leaf_size=args.leaf,
-                            tree=info, parallelism=f"replicas x{world}", l2="flushed (256 MiB write) before each step",
-                            setup_s=setup_s, wall_s=wall),
+                            tree=info, parallelism=f"replicas x{world}",
+                            l2="flushed (256 MiB write) before each step", setup_s=setup_s, wall_s=wall),
                 e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes),
-                roofline=roof, cpu_baseline=cpu, solve=solve, gpu_launches=launches_per_step * args.steps,
-                clocks=clk)
+                roofline=roof, other_precision=other, solve=solve, cpu_baseline=cpu,
+                gpu_launches=launches_per_step * args.steps, clocks=clk)
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
         dist.destroy_process_group()
-
-
-# flops per (near pair, domain): geometry and kernel scalars, and per right-hand side
-NEAR_PAIR = 21
-NEAR_RHS = 103
 
 
 def main():
