@@ -176,6 +176,24 @@ fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs
  * [n_rhs][N][6] complex128 (may be the same buffer). */
 fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream);
 
+/* Allocation-free y = A x, for callers that cannot allocate device memory when they need the
+ * product: work recorded into a CUDA graph by stream capture (cudaMalloc is not allowed during
+ * capture), code whose device memory is owned by a framework allocator, or callbacks that must
+ * not trigger the implicit device synchronisation of cudaMalloc/cudaFree.  The paper has no
+ * counterpart; this is a library-level variant of fmbem_matvec.
+ * Same arguments, layouts, kernels and results as fmbem_matvec, but the scratch (source
+ * densities, expansion coefficients, per-pair M2L results) lives in one file-scope device array
+ * of 32 MiB that every GPU loading the library holds until the process exits; no cudaMalloc,
+ * cudaFree or allocating library routine is called.  Problems whose scratch for the given n_rhs
+ * and precision exceeds 32 MiB (roughly a few thousand nodes at p = 8 and one right-hand side)
+ * are rejected with FMBEM_ERR_INVALID_ARGUMENT and a message giving the bytes needed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU (different streams without ordering) race on it.  Nothing needs clearing between
+ * calls, because every scratch element a call reads is written earlier in the same call. */
+fmbem_status fmbem_matvec_noalloc(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,
+                                  void *stream);
+
 /* Wall-clock milliseconds of the phases of the last fmbem_matvec call, measured with CUDA
  * events on its stream: [0] source densities + P2M, [1] M2M, [2] M2L + L2L, [3] near field
  * + L2P + self, [4] total.  ms_host [5]. */

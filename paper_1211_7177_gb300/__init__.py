@@ -273,3 +273,19 @@ class FMBEM:
 
     def last_matvec_times(self):
         return fmbem_last_matvec_times(self.h)
+
+
+def fmbem_matvec_noalloc(h, x, y, precision=FP64, stream=None):
+    """Allocation-free y = A x (see include/fmbem.h): for callers that cannot allocate device
+    memory when they need the product, e.g. while a CUDA graph is being captured.  x and y are
+    preallocated complex128 CUDA tensors [n_rhs, N, 6]; y is written in place and returned."""
+    lib = load_library()
+    f = lib.fmbem_matvec_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    y = _dev(y, N, "y")
+    _check(h, f(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.shape[0], int(precision),
+                _stream(stream)))
+    return y

@@ -646,3 +646,79 @@ void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaS
     else matvec_impl<double>(h, x, y, nr, s, dc);
     h->have_times = h->profile && h->ev[0] != nullptr;
 }
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free matvec.  Some callers cannot allocate device memory at the time they need a
+// product: code running inside a CUDA stream capture (where cudaMalloc is not allowed), code
+// under a framework allocator that owns all device memory, or callbacks that must not block
+// on an implicit device synchronisation.  fmbem_matvec_noalloc runs the same kernels as
+// fmbem_matvec, but takes its scratch (source densities, multipole and local coefficients,
+// per-pair M2L results) from the file-scope device array below instead of the handle's
+// grow-on-demand buffers, so it never calls cudaMalloc or cudaFree.
+//
+// The array is STATIC_SCRATCH_BYTES (32 MiB) on every GPU that loads the library and stays
+// resident until the process exits.  All calls share it and it keeps the last call's contents:
+// every element a call reads is written earlier in the same call, so nothing needs clearing,
+// but two calls that overlap on the GPU (different streams, no ordering) race on it.
+constexpr size_t STATIC_SCRATCH_BYTES = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+#include <mutex>
+
+// Device address of g_static_scratch on the current device.  In host code the symbol is only a
+// host-side stand-in, so the address is looked up once per device with cudaGetSymbolAddress (the
+// first allocation-free call on a device does this; it should come before any stream capture).
+static void *static_scratch_address() {
+    static std::mutex mu;
+    static void *addr[128] = {nullptr};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) throw fmbem_error{FMBEM_ERR_CUDA, "device index out of range"};
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_static_scratch));
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+
+template <typename R>
+static void matvec_static_scratch(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s) {
+    const size_t S = sizeof(cx<R>);
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_dens = up(S * 2 * nr * h->N * 6);
+    const size_t b_exp = up(S * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
+    size_t b_y = 0;
+    if (3 * nr <= 24) {
+        int64_t mp = 1;
+        for (int l = 2; l <= h->lmax; ++l) mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l]);
+        b_y = up(S * (size_t)mp * 3 * nr * h->p2);
+    }
+    const size_t need = b_dens + 2 * b_exp + b_y;
+    if (need > STATIC_SCRATCH_BYTES)
+        throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT,
+                          "fmbem_matvec_noalloc needs " + std::to_string(need) + " bytes of scratch for this problem and n_rhs; "
+                          "its static array holds " + std::to_string(STATIC_SCRATCH_BYTES) + " bytes (use fmbem_matvec)"};
+    unsigned char *base = (unsigned char *)static_scratch_address();
+    // run the regular passes on pointers into the static array; the handle's own scratch
+    // pointers are restored afterwards, so fmbem_matvec is unaffected
+    void *sv_dens = h->dens, *sv_C = h->Cexp, *sv_D = h->Dexp, *sv_y = h->ybuf;
+    h->dens = base;
+    h->Cexp = base + b_dens;
+    h->Dexp = base + b_dens + b_exp;
+    h->ybuf = b_y ? base + b_dens + 2 * b_exp : nullptr;
+    try {
+        matvec_impl<R>(h, x, y, nr, s, (const DomainConsts *)h->dcons);
+    } catch (...) {
+        h->dens = sv_dens; h->Cexp = sv_C; h->Dexp = sv_D; h->ybuf = sv_y;
+        throw;
+    }
+    h->dens = sv_dens; h->Cexp = sv_C; h->Dexp = sv_D; h->ybuf = sv_y;
+}
+
+void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
+    if (precision == FMBEM_FP32) matvec_static_scratch<float>(h, x, y, nr, s);
+    else matvec_static_scratch<double>(h, x, y, nr, s);
+    h->have_times = h->profile && h->ev[0] != nullptr;
+}
