@@ -36,6 +36,9 @@ import fmbem_inputs as fi  # noqa: E402
 WORKLOADS = {
     "silver_sphere_s7": dict(mesh=lambda: fi.icosphere(7), eps=[1.0, -8.5 + 0.3j], mu=[1.0, 1.0], k0=0.5, n_rhs=1,
                              p=10, desc="silver-like sphere a=1, eps=-8.5+0.3i, k0 a=0.5, icosphere subdivision 7"),
+    "silver_sphere_s6": dict(mesh=lambda: fi.icosphere(6), eps=[1.0, -8.5 + 0.3j], mu=[1.0, 1.0], k0=0.5, n_rhs=1,
+                             p=10, desc="silver-like sphere a=1, eps=-8.5+0.3i, k0 a=0.5, icosphere subdivision 6 "
+                                        "(the profiling case)"),
     "sphere_s4": dict(mesh=lambda: fi.icosphere(4), eps=[1.0, 2.25], mu=[1.0, 1.0], k0=1.0, n_rhs=1, p=8,
                       desc="dielectric sphere a=1, eps=2.25, k0 a=1, icosphere subdivision 4"),
     "torus_512x128": dict(mesh=lambda: fi.torus(), eps=[1.0, -10 + 0.4j], mu=[1.0, 1.0], k0=1.5, n_rhs=128, p=8,
@@ -160,13 +163,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- GPU arm
+def m2l_flops_per_column(p, nr):
+    """Algorithmic real flops of one S|R translation of one column: dense p^2 x p^2 complex matrix
+    (8 p^4), or, in the rotation form the library uses for p >= 9 with at most 8 right-hand sides,
+    two degree-block rotations and one order-block coaxial translation."""
+    if p >= 9 and 3 * nr <= 24:
+        rot = p * (2 * p - 1) * (2 * p + 1) // 3
+        coax = p * (2 * p * p + 1) // 3
+        return 8.0 * (2 * rot + coax), "rotation form (rotate, coaxial S|R, rotate back)"
+    return 8.0 * p ** 4, "dense S|R matrices"
+
+
 def roofline(info, p, nr, n_dom, phases, precision):
     keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
     avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
     dom = max(keys, key=lambda k: avg[k])
     if dom == "m2l_l2l":
-        flops = 8.0 * p ** 4 * 3 * nr * info["ff_pairs"] * n_dom
-        name = "M2L + L2L (k_m2l_chunks + k_l2l_reduce / k_m2l_multi)"
+        per_col, form = m2l_flops_per_column(p, nr)
+        flops = per_col * 3 * nr * info["ff_pairs"] * n_dom
+        name = f"M2L + L2L, {form}"
     elif dom == "near_l2p_self":
         flops = info["near_pairs"] * n_dom * (NEAR_PAIR + NEAR_RHS * nr)
         name = "near field + L2P + self (k_near)"
@@ -289,8 +304,11 @@ def run_ours(args):
         kinds = (("plain_fp64", fm.FP64), ("fp32_inner_fp64_refined", fm.FP32)) if nr == 1 else \
             (("fp32_inner_fp64_refined", fm.FP32),)
         for label, sp in kinds:
+            # refined solve: FP32 inner GMRES to half the tolerance, true residual with FP64 vectors
+            # (FP64 passes for one right-hand side, FP32 passes with FP64 accumulation for batches)
             h2 = g if sp == fm.FP64 else fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf,
-                                                   solve_precision=fm.FP32)
+                                                   solve_precision=fm.FP32, inner_tol=0.5e-4,
+                                                   outer_precision=fm.FP64 if nr == 1 else fm.FP32)
             xs = torch.zeros_like(b)
             h2.solve(b, xs, tol=1e-4, max_iter=1000)  # warm-up (allocates the Krylov basis)
             xs.zero_()

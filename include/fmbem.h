@@ -88,6 +88,12 @@ typedef struct {
                                 with FP32 the solve is refined: outer true residuals with the FP64
                                 operator, inner GMRES with the FP32 operator                      */
     double inner_tol;        /* relative tolerance of each inner FP32 solve [1e-2]                */
+    int outer_precision;     /* fmbem_precision of the passes in the refined solve's outer true-
+                                residual matvec (vectors and the residual are always FP64) [FP64] */
+    int m2l_rotation;        /* S|R translations for few right-hand sides: 0 dense p^2 x p^2
+                                matrices, 1 rotation form (rotate to the translation axis, coaxial
+                                translation, rotate back; ~3.3 p^3 instead of p^4 operations),
+                                -1 automatic: rotation form for p >= 9 [-1]                      */
     int profile_phases;      /* non-zero: record CUDA events around the matvec phases so that
                                 fmbem_last_matvec_times can report them [0]                       */
 } fmbem_options;

@@ -82,6 +82,8 @@ void fmbem_default_options(fmbem_options *o) {
     o->gmres_restart = 50;
     o->solve_precision = FMBEM_FP64;
     o->inner_tol = 1e-2;
+    o->outer_precision = FMBEM_FP64;
+    o->m2l_rotation = -1;
     o->profile_phases = 0;
 }
 
@@ -103,7 +105,9 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
     const fmbem_options &o = h->opt;
     if ((o.node_mode != FMBEM_NODES_VERTEX && o.node_mode != FMBEM_NODES_CENTROID) || o.p < 2 || o.p > 20 ||
         o.leaf_size < 1 || o.max_level < 2 || o.gmres_restart < 1 || o.gmres_restart > 500 ||
-        (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1)) {
+        (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
+        (o.outer_precision != FMBEM_FP64 && o.outer_precision != FMBEM_FP32) || o.m2l_rotation < -1 ||
+        o.m2l_rotation > 1) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
@@ -115,6 +119,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         h->p = o.p;
         h->p2 = o.p * o.p;
         h->profile = o.profile_phases != 0;
+        h->m2l_rotation = o.m2l_rotation == 1 || (o.m2l_rotation == -1 && o.p >= 9);
         h->eps.resize(h->J + 1);
         h->mu.resize(h->J + 1);
         h->k.resize(h->J + 1);

@@ -137,6 +137,12 @@ struct fmbem {
     c32 *B_p2m32 = nullptr, *B_l2p32 = nullptr;
     c64 *T_m2l64 = nullptr, *T_mm64 = nullptr, *T_ll64 = nullptr;  // see tables.cu for layout
     c32 *T_m2l32 = nullptr, *T_mm32 = nullptr, *T_ll32 = nullptr;
+    // rotation form of S|R (see tables.cu): A, B [316][p2][p2], Z [J+1][lmax+1][n_tlen][p2][p2]
+    bool m2l_rotation = false;
+    int n_tlen = 0;
+    int8_t *rot_tidx = nullptr;  // [316] index of the offset's length among the distinct lengths
+    c64 *R_A64 = nullptr, *R_B64 = nullptr, *R_Z64 = nullptr;
+    c32 *R_A32 = nullptr, *R_B32 = nullptr, *R_Z32 = nullptr;
 
     // scratch grown on demand
     int64_t scratch_rhs = 0;

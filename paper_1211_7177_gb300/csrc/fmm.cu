@@ -164,18 +164,22 @@ __global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t
 // that k_l2l_reduce can sum each target's pairs in a fixed order.
 // Threads: rows_pad (= p2 rounded up to a warp multiple) x cg column groups; a warp shares its
 // columns, so the gathered inputs are read as shared-memory broadcasts.
-template <typename R, int MAXC>
+// TSM: the translation matrix is staged in shared memory; otherwise (large p in double
+// precision) it is read from L2, coalesced across the rows, and shared memory holds the columns.
+template <typename R, int MAXC, bool TSM>
 __global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0,
                              int ncol, int pc, int cg, const int32_t *chunk_beg, const int32_t *chunk_cnt,
                              const int16_t *chunk_off, const int32_t *pair_e, const int32_t *ff_src,
                              const cx<R> *Tm2l, const cx<R> *C, cx<R> *Y, int64_t e_first) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<R> *Ts = reinterpret_cast<cx<R> *>(smem_raw);  // [k][r]
-    cx<R> *Xs = Ts + p2 * p2;                          // [pair * ncol + col][k]
+    cx<R> *Tsh = reinterpret_cast<cx<R> *>(smem_raw);  // [k][r]
+    cx<R> *Xs = Tsh + (TSM ? p2 * p2 : 0);              // [pair * ncol + col][k]
     const int64_t ck = chunk0 + blockIdx.x;
     const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
-    const cx<R> *T = Tm2l + m2l_matrix(d, l, chunk_off[ck], lmax) * p2 * p2;
-    for (int i = threadIdx.x; i < p2 * p2; i += blockDim.x) Ts[i] = T[i];
+    const cx<R> *__restrict__ T = Tm2l + m2l_matrix(d, l, chunk_off[ck], lmax) * p2 * p2;
+    if (TSM)
+        for (int i = threadIdx.x; i < p2 * p2; i += blockDim.x) Tsh[i] = T[i];
+    const cx<R> *Ts = TSM ? Tsh : T;
     const int rows_pad = blockDim.x / cg;
     const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
     // every column group owns exactly MAXC columns; columns past the sub-batch are zero-filled,
@@ -214,6 +218,123 @@ __global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr,
                     int j = j0 + q, pr = j / ncol, col = j - pr * ncol;
                     int64_t e = pair_e[beg + b0 + pr];
                     Y[((e - e_first) * ncol + col) * p2 + r] = acc[q];
+                }
+        }
+    }
+}
+
+// M2L on offset chunks in rotation form (S|R of Eq. 2.21 factored as T_o = B_o Z_{|t|} A_o):
+// C' = A_o C rotates each degree block into the frame whose z axis is the translation,
+// D' = Z C' translates along z (block-diagonal in the order m), Y = B_o D' rotates back.
+// Per column this costs sum_n (2n+1)^2 * 2 + sum_m (p-|m|)^2 complex multiply-adds instead of p^4.
+// The compact blocks of A_o, B_o and Z are staged in shared memory once per chunk; a thread owns
+// one output coefficient (n, m) for MAXC columns in each of the three stages.
+__device__ __forceinline__ int rot_off(int n) { return n * (2 * n - 1) * (2 * n + 1) / 3; }
+template <typename R, int MAXC>
+__global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox, int col0, int ncol,
+                          int pc, int cg, const int32_t *chunk_beg, const int32_t *chunk_cnt, const int16_t *chunk_off,
+                          const int32_t *pair_e, const int32_t *ff_src, const int8_t *tidx, int n_tlen,
+                          const cx<R> *RA, const cx<R> *RB, const cx<R> *RZ, const cx<R> *C, cx<R> *Y,
+                          int64_t e_first) {
+    const int p2 = p * p;
+    const int nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *Ab = reinterpret_cast<cx<R> *>(smem_raw);
+    cx<R> *Bb = Ab + nrot;
+    cx<R> *Zb = Bb + nrot;
+    const int ncap = cg * MAXC;
+    cx<R> *X = Zb + ncoax;       // [ncap][p2]
+    cx<R> *U = X + ncap * p2;    // [ncap][p2]
+    const int64_t ck = chunk0 + blockIdx.x;
+    const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+    const int o = chunk_off[ck];
+    const cx<R> *A = RA + (int64_t)o * p2 * p2, *B = RB + (int64_t)o * p2 * p2;
+    const cx<R> *Z = RZ + (((int64_t)d * (lmax + 1) + l) * n_tlen + tidx[o]) * p2 * p2;
+    for (int i = threadIdx.x; i < nrot; i += blockDim.x) {
+        int n = 0;
+        while (rot_off(n + 1) <= i) ++n;
+        const int w = 2 * n + 1, loc = i - rot_off(n), row = loc / w, col = loc - row * w;
+        // row/col index the output/input order within the degree block: m = index - n
+        Ab[i] = A[(int64_t)(n * n + col) * p2 + n * n + row];
+        Bb[i] = B[(int64_t)(n * n + col) * p2 + n * n + row];
+    }
+    for (int i = threadIdx.x; i < ncoax; i += blockDim.x) {
+        int m = -(p - 1), base = 0;
+        while (base + (p - abs(m)) * (p - abs(m)) <= i) { base += (p - abs(m)) * (p - abs(m)); ++m; }
+        const int am = abs(m), w = p - am, loc = i - base, row = loc / w, col = loc - row * w;
+        const int np = am + row, n = am + col;  // output degree n', input degree n
+        Zb[i] = Z[(int64_t)(n * n + n + m) * p2 + np * np + np + m];
+    }
+    const int rows_pad = blockDim.x / cg;
+    const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
+    int rn = (int)sqrtf((float)r);
+    while (rn * rn > r) --rn;
+    while ((rn + 1) * (rn + 1) <= r) ++rn;
+    const int rm = r - rn * rn - rn;  // this thread's output coefficient (rn, rm)
+    int zbase = 0;
+    for (int m = -(p - 1); m < rm; ++m) zbase += (p - abs(m)) * (p - abs(m));
+    const int arm = abs(rm), zw = p - arm;
+    for (int b0 = 0; b0 < cnt; b0 += pc) {
+        const int np = min(pc, cnt - b0);
+        const int nct = np * ncol;
+        __syncthreads();
+        for (int i = threadIdx.x; i < ncap * p2; i += blockDim.x) {
+            int j = i / p2, k = i - j * p2;
+            cx<R> v = {0, 0};
+            if (j < nct) {
+                int pr = j / ncol, c = j - pr * ncol;
+                v = C[(((int64_t)d * nbox + ff_src[pair_e[beg + b0 + pr]]) * 3 * nr + col0 + c) * p2 + k];
+            }
+            X[i] = v;
+        }
+        __syncthreads();
+        const int j0 = grp * MAXC, nj = min(MAXC, nct - j0);
+        cx<R> acc[MAXC];
+        // stage 1: rotate into the translation frame, per degree
+        if (r < p2 && nj > 0) {
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
+            const cx<R> *a = Ab + rot_off(rn) + (rm + rn) * (2 * rn + 1);
+            for (int jj = 0; jj < 2 * rn + 1; ++jj) {
+                const cx<R> t = a[jj];
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, X[(j0 + q) * p2 + rn * rn + jj]);
+            }
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) U[(j0 + q) * p2 + r] = acc[q];
+        }
+        __syncthreads();
+        // stage 2: coaxial translation along z, per order m
+        if (r < p2 && nj > 0) {
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
+            const cx<R> *z = Zb + zbase + (rn - arm) * zw;
+            for (int jj = 0; jj < zw; ++jj) {
+                const cx<R> t = z[jj];
+                const int n = arm + jj;
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, U[(j0 + q) * p2 + n * n + n + rm]);
+            }
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) X[(j0 + q) * p2 + r] = acc[q];
+        }
+        __syncthreads();
+        // stage 3: rotate back, per degree, and store at the pairs' CSR positions
+        if (r < p2 && nj > 0) {
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
+            const cx<R> *bb = Bb + rot_off(rn) + (rm + rn) * (2 * rn + 1);
+            for (int jj = 0; jj < 2 * rn + 1; ++jj) {
+                const cx<R> t = bb[jj];
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, X[(j0 + q) * p2 + rn * rn + jj]);
+            }
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q)
+                if (q < nj) {
+                    int j = j0 + q, pr = j / ncol, c = j - pr * ncol;
+                    int64_t e = pair_e[beg + b0 + pr];
+                    Y[((e - e_first) * ncol + c) * p2 + r] = acc[q];
                 }
         }
     }
@@ -515,6 +636,203 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
     }
 }
 
+// ---------------------------------------------------------------- near field for blocks of RHS
+// The kernel scalars of a pair and domain (g and c of grad'g = c r) do not depend on the right-
+// hand side, so for many right-hand sides they are computed once and applied to RB of them.
+template <typename R>
+__device__ __forceinline__ void pair_scalars(R inv, R Rr, cx<R> k, cx<R> &g, cx<R> &c) {
+    R e = k.im != (R)0 ? exp_(-k.im * Rr) : (R)1;
+    R sn, cs;
+    sincos_(k.re * Rr, &sn, &cs);
+    R f = e * inv * (R)(0.25 / FMBEM_PI);
+    g = {f * cs, f * sn};
+    c = g * cx<R>{(-k.im - inv) * inv, k.re * inv};
+}
+// acc_i += -(K v)_i + g q_i with -(K v)_i = -c [n_i (r.v) - (n.r) v_i - r_i (n.v)]
+template <typename R>
+__device__ __forceinline__ void pair_apply(const R *rr, const R *nn, R nr, cx<R> g, cx<R> c, const cx<R> *v,
+                                           const cx<R> *q, cx<R> *acc) {
+    cx<R> rv = rr[0] * v[0] + rr[1] * v[1] + rr[2] * v[2];
+    cx<R> nv = nn[0] * v[0] + nn[1] * v[1] + nn[2] * v[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cx<R> kv = nn[i] * rv - nr * v[i] - rr[i] * nv;
+        acc[i] -= c * kv;
+        cfma(acc[i], g, q[i]);
+    }
+}
+
+constexpr int NB_TILE = 64;  // sources per shared-memory tile in the blocked kernel
+template <typename R, int RB>
+struct SrcTileRB {
+    V4<R> pa[NB_TILE];
+    V4<R> pb[NB_TILE];
+    V2<R> pn[NB_TILE];
+    V4<R> dv[2][RB][3][NB_TILE];  // per side and RHS of the block: (v0, v1), (v2, q0), (q1, q2)
+};
+template <typename R, int RB>
+union NearSmemRB {
+    SrcTileRB<R, RB> tile;
+    cx<R> red[6][RB][128];
+};
+
+template <typename R, bool DOUBLE_FLOAT, int RB>
+__global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                                 const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                                 const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
+                                                 const R *nrm, const int32_t *dom, const int32_t *perm,
+                                                 const cx<R> *dens, const DomainConsts *dc, const cx<R> *Bl2p,
+                                                 const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    NearSmemRB<R, RB> &S = *reinterpret_cast<NearSmemRB<R, RB> *>(smem_raw);
+    SrcTileRB<R, RB> &T = S.tile;
+    __shared__ int rng_beg[32], rng_cum[33];
+    const int64_t g = leaf_off + blockIdx.x;
+    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        for (int q = 0; q < nnb; ++q) {
+            int b = nbr_idx[nb0 + q];
+            rng_beg[q] = nbeg[b];
+            rng_cum[q] = cum;
+            cum += nend[b] - nbeg[b];
+        }
+        rng_cum[nnb] = cum;
+    }
+    __syncthreads();
+    const int nsrc = rng_cum[nnb];
+    const int t0 = nbeg[g], t1 = nend[g];
+    for (int64_t rb0 = 0; rb0 < nr; rb0 += RB) {
+        const int nrb = (int)min((int64_t)RB, nr - rb0);
+        for (int tb = t0; tb < t1; tb += 128) {
+            const int nt = min(128, t1 - tb);
+            const int nsl = 128 / nt;
+            const int tg = threadIdx.x % nt, slice = threadIdx.x / nt;
+            const bool active = slice < nsl;
+            const int a = tb + tg;
+            R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2], alx = 0, aly = 0, alz = 0;
+            if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
+            const int adom = dom[a];
+            const R adom_r = (R)adom;
+            const cx<R> kb = to<R>(dc[0].k), kj = to<R>(dc[adom].k);
+            cx<R> acc0[RB][3], acc1[RB][3];
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { acc0[rr][c] = {0, 0}; acc1[rr][c] = {0, 0}; }
+            for (int s0 = 0; s0 < nsrc; s0 += NB_TILE) {
+                __syncthreads();
+                for (int e2 = threadIdx.x; e2 < NB_TILE * (1 + 2 * RB); e2 += blockDim.x) {
+                    const int t = e2 % NB_TILE, part = e2 / NB_TILE;  // part 0: geometry, 1..: (side, rhs)
+                    const int e = s0 + t;
+                    if (e >= nsrc) continue;
+                    int q = 0;
+                    while (q + 1 < nnb && rng_cum[q + 1] <= e) ++q;
+                    const int i = rng_beg[q] + (e - rng_cum[q]);
+                    if (part == 0) {
+                        T.pa[t] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
+                        R lo[3] = {0, 0, 0};
+                        if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
+                        T.pb[t] = V4<R>{lo[0], lo[1], lo[2], nrm[3 * i]};
+                        T.pn[t] = V2<R>{nrm[3 * i + 1], nrm[3 * i + 2]};
+                    } else {
+                        const int sd = (part - 1) / RB, rr = (part - 1) % RB;
+                        if (rr < nrb) {
+                            const cx<R> *dn = dens + ((sd * nr + rb0 + rr) * N + i) * 6;
+                            for (int c = 0; c < 3; ++c)
+                                T.dv[sd][rr][c][t] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
+                        } else {
+                            for (int c = 0; c < 3; ++c) T.dv[sd][rr][c][t] = V4<R>{0, 0, 0, 0};
+                        }
+                    }
+                }
+                __syncthreads();
+                const int ns = min(NB_TILE, nsrc - s0);
+                if (active)
+                    for (int u = slice; u < ns; u += nsl) {
+                        const V4<R> pa = T.pa[u], pb = T.pb[u];
+                        const V2<R> pn = T.pn[u];
+                        R rv3[3] = {pa.x - ax, pa.y - ay, pa.z - az};
+                        if (DOUBLE_FLOAT) { rv3[0] += pb.x - alx; rv3[1] += pb.y - aly; rv3[2] += pb.z - alz; }
+                        R R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
+                        R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
+                        R Rr = R2 * inv;
+                        R n1[3] = {pb.w, pn.x, pn.y};
+                        R n0[3] = {-pb.w, -pn.x, -pn.y};
+                        R nr1 = n1[0] * rv3[0] + n1[1] * rv3[1] + n1[2] * rv3[2];
+                        cx<R> gs, cs;
+                        pair_scalars<R>(inv, Rr, kb, gs, cs);
+#pragma unroll
+                        for (int rr = 0; rr < RB; ++rr) {
+                            const V4<R> a0 = T.dv[0][rr][0][u], a1 = T.dv[0][rr][1][u], a2 = T.dv[0][rr][2][u];
+                            cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
+                            cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                            pair_apply<R>(rv3, n0, -nr1, gs, cs, v, qv, acc0[rr]);
+                        }
+                        if (pa.w == adom_r) {
+                            pair_scalars<R>(inv, Rr, kj, gs, cs);
+#pragma unroll
+                            for (int rr = 0; rr < RB; ++rr) {
+                                const V4<R> a0 = T.dv[1][rr][0][u], a1 = T.dv[1][rr][1][u], a2 = T.dv[1][rr][2][u];
+                                cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
+                                cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                                pair_apply<R>(rv3, n1, nr1, gs, cs, v, qv, acc1[rr]);
+                            }
+                        }
+                    }
+            }
+            // reduce the source slices in a fixed order
+            __syncthreads();
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    S.red[c][rr][threadIdx.x] = acc0[rr][c];
+                    S.red[3 + c][rr][threadIdx.x] = acc1[rr][c];
+                }
+            __syncthreads();
+            if (threadIdx.x < nt) {
+                const int64_t u = perm[a];
+                const c64 *M = Mself + 36 * u;
+                for (int rr = 0; rr < nrb; ++rr) {
+                    cx<R> s0v[3], s1v[3];
+                    for (int c = 0; c < 3; ++c) {
+                        s0v[c] = S.red[c][rr][threadIdx.x];
+                        s1v[c] = S.red[3 + c][rr][threadIdx.x];
+                        for (int sl = 1; sl < nsl; ++sl) {
+                            s0v[c] += S.red[c][rr][sl * nt + threadIdx.x];
+                            s1v[c] += S.red[3 + c][rr][sl * nt + threadIdx.x];
+                        }
+                    }
+                    const int64_t r = rb0 + rr;
+                    // far field (L2P) of both domains
+                    for (int sd = 0; sd < 2; ++sd) {
+                        int d = sd == 0 ? 0 : adom;
+                        const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r) * p2;
+                        const cx<R> *B = Bl2p + ((int64_t)sd * N + a) * p2;
+                        cx<R> *acc = sd == 0 ? s0v : s1v;
+                        for (int qq = 0; qq < p2; ++qq) {
+                            cx<R> bq = B[qq];
+                            cfma(acc[0], Dl[qq], bq);
+                            cfma(acc[1], Dl[p2 + qq], bq);
+                            cfma(acc[2], Dl[2 * p2 + qq], bq);
+                        }
+                    }
+                    // self block in double precision, store in user order
+                    const c64 *xa = x + (r * N + u) * 6;
+                    c64 *ya = y + (r * N + u) * 6;
+                    for (int row = 0; row < 6; ++row) {
+                        c64 sacc = row < 3 ? c64{(double)s0v[row].re, (double)s0v[row].im}
+                                           : c64{(double)s1v[row - 3].re, (double)s1v[row - 3].im};
+                        for (int c = 0; c < 6; ++c) cfma(sacc, M[row * 6 + c], xa[c]);
+                        ya[row] = sacc;
+                    }
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -574,13 +892,39 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const int ncol = (int)std::min<int64_t>(3 * nr, MAXC);
     const size_t tbytes = sizeof(cx<R>) * p2 * p2;
     const size_t budget = 200 * 1024;
-    int cg = std::max(1, std::min(4, 1024 / rows_pad));
-    while (cg > 1 && tbytes + sizeof(cx<R>) * cg * MAXC * p2 > budget) --cg;
-    const size_t smc = tbytes + sizeof(cx<R>) * cg * MAXC * p2;
+    auto xs_bytes = [&](int c) { return sizeof(cx<R>) * c * MAXC * p2; };
+    // threads per block are capped by the kernel's register use
+    cudaFuncAttributes fa_t{}, fa_g{};
+    CK(cudaFuncGetAttributes(&fa_t, k_m2l_chunks<R, MAXC, true>));
+    CK(cudaFuncGetAttributes(&fa_g, k_m2l_chunks<R, MAXC, false>));
+    const int max_thr = std::min(fa_t.maxThreadsPerBlock, fa_g.maxThreadsPerBlock);
+    int cg = std::max(1, std::min(4, max_thr / rows_pad));
+    // stage T in shared memory when it fits beside the full column groups; otherwise read T from
+    // L2 and keep the column groups (occupancy matters more than T reuse from shared memory)
+    const bool tsm = tbytes + xs_bytes(cg) <= budget;
+    while (cg > 1 && (tsm ? tbytes : 0) + xs_bytes(cg) > budget) --cg;
+    const size_t smc = (tsm ? tbytes : 0) + xs_bytes(cg);
     const int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
-    const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr;
+    const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr && rows_pad <= max_thr;
+    // rotation form of the chunked S|R (when its tables were built)
+    constexpr int RMAXC = 12;
+    const int pp = h->p, nrot = pp * (2 * pp - 1) * (2 * pp + 1) / 3, ncoax = pp * (2 * pp * pp + 1) / 3;
+    cudaFuncAttributes fa_r{};
+    CK(cudaFuncGetAttributes(&fa_r, k_m2l_rot<R, RMAXC>));
+    auto rot_bytes = [&](int c) { return sizeof(cx<R>) * ((size_t)(2 * nrot + ncoax) + 2 * (size_t)c * RMAXC * p2); };
+    int cgr = std::max(1, std::min(4, fa_r.maxThreadsPerBlock / rows_pad));
+    while (cgr > 1 && rot_bytes(cgr) > budget) --cgr;
+    const int pcr = std::min(M2L_CHUNK, cgr * RMAXC / ncol);
+    const bool use_rot = chunked && h->m2l_rotation && h->R_A64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
+                         rows_pad <= fa_r.maxThreadsPerBlock;
     if (chunked) {
-        CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+        if (tsm) CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+        else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+        if (use_rot)
+            CK(cudaFuncSetAttribute(k_m2l_rot<R, RMAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_bytes(cgr)));
+        const cx<R> *RA = f32 ? (const cx<R> *)h->R_A32 : (const cx<R> *)h->R_A64;
+        const cx<R> *RB = f32 ? (const cx<R> *)h->R_B32 : (const cx<R> *)h->R_B64;
+        const cx<R> *RZ = f32 ? (const cx<R> *)h->R_Z32 : (const cx<R> *)h->R_Z64;
         cx<R> *Y = (cx<R> *)h->ybuf;
         for (int l = 2; l <= lmax; ++l) {
             const LevelInfo &Lv = h->lev[l];
@@ -589,10 +933,20 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             for (int d = 0; d <= J; ++d)
                 for (int col0 = 0; col0 < 3 * nr; col0 += ncol) {
                     const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
-                    if (nch > 0)
-                        k_m2l_chunks<R, MAXC><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
-                            c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt, h->chunk_off,
-                            h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
+                    if (nch > 0) {
+                        if (use_rot)
+                            k_m2l_rot<R, RMAXC><<<(unsigned)nch, rows_pad * cgr, rot_bytes(cgr), s>>>(
+                                c0, l, lmax, d, nr, pp, h->nbox, col0, nc, pcr, cgr, h->chunk_beg, h->chunk_cnt,
+                                h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RA, RB, RZ, C, Y, e_first);
+                        else if (tsm)
+                            k_m2l_chunks<R, MAXC, true><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
+                                c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt,
+                                h->chunk_off, h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
+                        else
+                            k_m2l_chunks<R, MAXC, false><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
+                                c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt,
+                                h->chunk_off, h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
+                    }
                     CKL("k_m2l_chunks");
                     const int ct = std::max(1, std::min(nc, 1024 / rows_pad));
                     k_l2l_reduce<R><<<(unsigned)Lv.n, rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
@@ -601,7 +955,12 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                     CKL("k_l2l_reduce");
                 }
         }
-    } else if (sizeof(cx<R>) * (size_t)(p2 * p2 + p2 * MT_COLS) <= budget) {
+    } else if (sizeof(cx<R>) * (size_t)(p2 * p2 + p2 * MT_COLS) <= budget &&
+               ((p2 + 3) / 4) * (MT_COLS / 4) <= [] {
+                   cudaFuncAttributes fa{};
+                   CK(cudaFuncGetAttributes(&fa, k_m2l_multi<R>));
+                   return fa.maxThreadsPerBlock;
+               }()) {
         const size_t smm = sizeof(cx<R>) * (size_t)(p2 * p2 + p2 * MT_COLS);
         CK(cudaFuncSetAttribute(k_m2l_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
         const int nt = ((p2 + 3) / 4) * (MT_COLS / 4);
@@ -626,7 +985,20 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
     const R *nn = f32 ? (const R *)h->nrm_f : (const R *)h->nrm;
-    if (f32)
+    // right-hand-side blocks: the pair scalars are shared by RB right-hand sides
+    constexpr int RBLK = sizeof(R) == 4 ? 8 : 2;
+    if (nr >= 4) {
+        auto kern = f32 ? (void (*)(int64_t, int64_t, int64_t, int, int64_t, const int32_t *, const int32_t *,
+                                    const int32_t *, const int32_t *, const R *, const R *, const R *, const int32_t *,
+                                    const int32_t *, const cx<R> *, const DomainConsts *, const cx<R> *, const cx<R> *,
+                                    const c64 *, const c64 *, c64 *))k_near_rb<R, true, RBLK>
+                        : k_near_rb<R, false, RBLK>;
+        const size_t smn = sizeof(NearSmemRB<R, RBLK>);
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn));
+        kern<<<(unsigned)L.n, 128, smn, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx,
+                                             ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D, h->Mself, x, y);
+        CKL("k_near_rb");
+    } else if (f32)
         k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
                                                       h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D, h->Mself,
                                                       x, y);

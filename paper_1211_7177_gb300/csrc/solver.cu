@@ -252,14 +252,15 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
         if (!refine) {
             gmres(h, W, FMBEM_FP64, b, x, tol, max_iter, its, rr, conv, breakdown);
         } else {
-            // iterative refinement: r = b - A64 x; solve A32 d = r to inner_tol; x += d
+            // iterative refinement: r = b - A x (outer_precision passes, FP64 vectors); solve
+            // A32 d = r to inner_tol with the FP32 operator; x += d
             c64 *base = h->sv + (size_t)(m + 1) * nr * n + 2 * nr * n;
             c64 *r = base, *d = base + nr * n;
             std::vector<int> itot(nr, 0);
             std::vector<double> bn;
             W.norms(b, bn);
             for (int outer = 0;; ++outer) {
-                run_matvec(h, x, r, nr, FMBEM_FP64, s);
+                run_matvec(h, x, r, nr, h->opt.outer_precision, s);
                 k_axpy<<<dim3(nblk(n, 256), (unsigned)nr), 256, 0, s>>>(1, nullptr, b, r, n, nr);
                 CKL("k_axpy");
                 std::vector<double> rn;

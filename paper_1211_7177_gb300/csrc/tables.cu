@@ -110,8 +110,33 @@ __global__ void k_eval_cols(int nmat, int Q, int p, c64 k, double rho, const dou
     for (int c = 0; c < p * p; ++c) out[c] = V[c];
 }
 
-// projection weights Yc[q][r] = W_q conj(Y_r(xhat_q)) / rad_{n_r}(k rho)
-__global__ void k_proj_weights(int Q, int p, const double *xq, const double *wq, c64 k, double rho, bool singular_out,
+// spherical harmonics at rotated quadrature points: F[m][q][c] = Y_c(M_m xhat_q), M_m a 3x3
+// rotation (row-major); projected on Y_r this gives the degree-preserving rotation matrices
+__global__ void k_eval_rot(int nmat, int Q, int p, const double *xq, const double *Mrot, c64 *F) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nmat * Q) return;
+    int m = (int)(idx / Q), q = (int)(idx % Q);
+    const double *M = Mrot + 9 * m, *x = xq + 3 * q;
+    double v[3];
+    for (int a = 0; a < 3; ++a) v[a] = M[3 * a] * x[0] + M[3 * a + 1] * x[1] + M[3 * a + 2] * x[2];
+    double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double ct = v[2] / nv;
+    double phi = (v[0] == 0.0 && v[1] == 0.0) ? 0.0 : atan2(v[1], v[0]);
+    double Pb[(PMAX + 1) * (PMAX + 2) / 2];
+    legendre_bar(p - 1, ct, Pb);
+    c64 *out = F + idx * (int64_t)(p * p);
+    for (int n = 0; n < p; ++n)
+        for (int mm = -n; mm <= n; ++mm) {
+            int am = mm < 0 ? -mm : mm;
+            double sp, cp;
+            sincos(mm * phi, &sp, &cp);
+            out[n * n + n + mm] = c64{cp, sp} * (((am & 1) ? -1.0 : 1.0) * Pb[n * (n + 1) / 2 + am]);
+        }
+}
+
+// projection weights Yc[q][r] = W_q conj(Y_r(xhat_q)) / rad_{n_r}(k rho), rad = j_n (radial 0),
+// h_n (radial 1) or 1 (radial 2)
+__global__ void k_proj_weights(int Q, int p, const double *xq, const double *wq, c64 k, double rho, int radial,
                                c64 *Yc) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= Q) return;
@@ -122,8 +147,10 @@ __global__ void k_proj_weights(int Q, int p, const double *xq, const double *wq,
     legendre_bar(p - 1, ct, Pb);
     c64 radv[PMAX + 1];
     c64 z = k * rho;
-    if (singular_out) sph_h1(p - 1, z, radv);
-    else sph_j(p - 1, z, radv);
+    if (radial == 1) sph_h1(p - 1, z, radv);
+    else if (radial == 0) sph_j(p - 1, z, radv);
+    else
+        for (int n = 0; n < p; ++n) radv[n] = {1.0, 0.0};
     for (int n = 0; n < p; ++n)
         for (int m = -n; m <= n; ++m) {
             int am = m < 0 ? -m : m;
@@ -245,7 +272,7 @@ void build_tables(fmbem *h, cudaStream_t s) {
         CK(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * nm, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dsr, sr.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
-        k_proj_weights<<<nblk(Q, 64), 64, 0, s>>>(Q, p, dxq, dwq, k, rho, sing_out, Yc);
+        k_proj_weights<<<nblk(Q, 64), 64, 0, s>>>(Q, p, dxq, dwq, k, rho, sing_out ? 1 : 0, Yc);
         CKL("k_proj_weights");
         if (sing_in) k_eval_cols<true><<<nblk((int64_t)nm * Q, 64), 64, 0, s>>>(nm, Q, p, k, rho, dxq, dt, F);
         else k_eval_cols<false><<<nblk((int64_t)nm * Q, 64), 64, 0, s>>>(nm, Q, p, k, rho, dxq, dt, F);
@@ -303,6 +330,97 @@ void build_tables(fmbem *h, cudaStream_t s) {
                 run_batch(false, false, k, w, tl, dm, h->T_ll64, h->T_ll32);
             }
         }
+    }
+
+    // ---- rotation form of S|R: T_o = B_o Z_{|t_o|} A_o, with A_o rotating the multipole
+    // expansion into the frame whose z axis is t_o = c_target - c_source, Z the coaxial S|R
+    // translation along z by |t_o| (block-diagonal in m) and B_o rotating the local expansion back.
+    // A_o[r = (n,m')][c = (n,m)] = int Y_c(Q^T xhat) conj(Y_r(xhat)), B_o = same with Q, Q t_o = |t_o| z.
+    if (h->m2l_rotation) {
+        std::vector<int> sq;  // distinct squared offset lengths
+        for (int dx = -3; dx <= 3; ++dx)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dz = -3; dz <= 3; ++dz) {
+                    if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+                    int v = dx * dx + dy * dy + dz * dz;
+                    if (std::find(sq.begin(), sq.end(), v) == sq.end()) sq.push_back(v);
+                }
+        std::sort(sq.begin(), sq.end());
+        h->n_tlen = (int)sq.size();
+        std::vector<int8_t> tidx(316);
+        std::vector<double> Mq(9 * 316), MqT(9 * 316);
+        std::vector<int64_t> dst(316);
+        for (int dx = -3; dx <= 3; ++dx)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dz = -3; dz <= 3; ++dz) {
+                    if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+                    int o = m2l_offset_code(dx, dy, dz);
+                    int v = dx * dx + dy * dy + dz * dz;
+                    tidx[o] = (int8_t)(std::find(sq.begin(), sq.end(), v) - sq.begin());
+                    // direction of t = -(dx, dy, dz)
+                    double tx = -dx, ty = -dy, tz = -dz, tn = sqrt((double)v);
+                    double ct = tz / tn, st = sqrt(std::max(0.0, 1 - ct * ct));
+                    double ph = (tx == 0 && ty == 0) ? 0.0 : atan2(ty, tx), cp = cos(ph), sp = sin(ph);
+                    // Q = R_y(-theta) R_z(-phi) maps t/|t| to z
+                    double Rz[9] = {cp, sp, 0, -sp, cp, 0, 0, 0, 1};
+                    double Ry[9] = {ct, 0, -st, 0, 1, 0, st, 0, ct};
+                    double *Qm = &Mq[9 * o];
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) {
+                            double acc = 0;
+                            for (int c = 0; c < 3; ++c) acc += Ry[3 * a + c] * Rz[3 * c + b];
+                            Qm[3 * a + b] = acc;
+                        }
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) MqT[9 * o + 3 * a + b] = Qm[3 * b + a];
+                    dst[o] = o;
+                }
+        h->rot_tidx = (int8_t *)dev_alloc(h, 316);
+        CK(cudaMemcpyAsync(h->rot_tidx, tidx.data(), 316, cudaMemcpyHostToDevice, s));
+        h->R_A64 = (c64 *)dev_alloc(h, sizeof(c64) * 316 * p2 * p2);
+        h->R_A32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * p2 * p2);
+        h->R_B64 = (c64 *)dev_alloc(h, sizeof(c64) * 316 * p2 * p2);
+        h->R_B32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * p2 * p2);
+        double *dM = (double *)dev_alloc(h, sizeof(double) * 9 * 316);
+        for (int q = 0; q < p2; ++q) { sr[q] = 1.0; sc[q] = 1.0; }
+        CK(cudaMemcpyAsync(dsr, sr.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * 316, cudaMemcpyHostToDevice, s));
+        k_proj_weights<<<nblk(Q, 64), 64, 0, s>>>(Q, p, dxq, dwq, c64{0, 0}, 1.0, 2, Yc);
+        CKL("k_proj_weights");
+        for (int pass = 0; pass < 2; ++pass) {
+            CK(cudaMemcpyAsync(dM, pass == 0 ? MqT.data() : Mq.data(), sizeof(double) * 9 * 316, cudaMemcpyHostToDevice, s));
+            k_eval_rot<<<nblk((int64_t)316 * Q, 64), 64, 0, s>>>(316, Q, p, dxq, dM, F);
+            CKL("k_eval_rot");
+            dim3 grid((p2 + 15) / 16, (p2 + 15) / 16, 316), tb(16, 16);
+            k_project<<<grid, tb, 0, s>>>(316, Q, p2, Yc, F, dsr, dsc, pass == 0 ? h->R_A64 : h->R_B64,
+                                          pass == 0 ? h->R_A32 : h->R_B32, ddst);
+            CKL("k_project");
+            CK(cudaStreamSynchronize(s));
+        }
+        dev_free(h, dM);
+        // coaxial S|R per (domain, level, distinct length), scaled like the dense S|R
+        const int64_t nz = (int64_t)(J + 1) * (lmax + 1) * h->n_tlen;
+        h->R_Z64 = (c64 *)dev_alloc(h, sizeof(c64) * nz * p2 * p2);
+        h->R_Z32 = (c32 *)dev_alloc(h, sizeof(c32) * nz * p2 * p2);
+        CK(cudaMemsetAsync(h->R_Z64, 0, sizeof(c64) * nz * p2 * p2, s));
+        CK(cudaMemsetAsync(h->R_Z32, 0, sizeof(c32) * nz * p2 * p2, s));
+        for (int d = 0; d <= J; ++d)
+            for (int l = 2; l <= lmax; ++l) {
+                const double w = h->lev[l].w, la = h->lam[d * (lmax + 1) + l];
+                std::vector<double> tv;
+                std::vector<int64_t> dz;
+                for (int i = 0; i < h->n_tlen; ++i) {
+                    tv.push_back(0.0); tv.push_back(0.0); tv.push_back(sqrt((double)sq[i]) * w);
+                    dz.push_back(((int64_t)d * (lmax + 1) + l) * h->n_tlen + i);
+                }
+                for (int q = 0; q < p2; ++q) {
+                    int n = nof(q);
+                    sr[q] = pow(la, n);
+                    sc[q] = pow(la, n + 1);
+                }
+                run_batch(true, false, h->k[d], w, tv, dz, h->R_Z64, h->R_Z32);
+            }
     }
     dev_free(h, F);
     dev_free(h, Yc);

@@ -129,6 +129,24 @@ def test_matvec_options(opt):
         assert err < tol
 
 
+@pytest.mark.parametrize("p", [6, 9, 10])
+def test_m2l_rotation_form_matches_dense(p):
+    """S|R as rotate - coaxial translate - rotate back must reproduce the dense S|R matrices
+    (both are exact translations of the truncated expansion) and meet the oracle bar."""
+    V, F, D = fi.icosphere(4)
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    gd = fm.FMBEM(V, F, D, eps, mu, k0, p=p, m2l_rotation=0)
+    gr = fm.FMBEM(V, F, D, eps, mu, k0, p=p, m2l_rotation=1)
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    x = fi.random_complex((1, o.N, 6), seed=31)
+    yo = o.matvec(x)
+    for prec in (fm.FP64, fm.FP32):
+        yd = gd.matvec(to_dev(x), precision=prec).cpu().numpy()
+        yr = gr.matvec(to_dev(x), precision=prec).cpu().numpy()
+        assert rel(yr, yd) < (1e-10 if prec == fm.FP64 else 2e-6), (p, prec, rel(yr, yd))
+        assert rel(yr, yo) < (2e-4 if p == 6 else MATVEC_TOL)
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
