@@ -51,6 +51,17 @@ UNIT = "points*RHS/s"
 NEAR_PAIR = 21
 NEAR_RHS = 103
 PEAK_TFLOPS = {"fp64": 1.2, "fp32": 74.6}  # measured FMA throughput on GB300 (self-written probe)
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor-core rate
+
+
+def tensor_peak_tf32():
+    """Dense TF32 tensor-core peak: the measured cuBLAS BF16 burst rate times the nominal ratio."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16, src = float(json.load(f)["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1900.0, "of fallback"
+    return bf16 * TF32_OVER_BF16, f"{src} BF16 GEMM burst rate x nominal TF32/BF16 ratio 1.1/2.25"
 
 
 def parse():
@@ -60,12 +71,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="silver_sphere_s7", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
     ap.add_argument("--p", type=int, default=0, help="truncation number (0 = the workload's)")
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--restart", type=int, default=50, help="GMRES restart length of the timed solves")
     return ap.parse_args()
 
 
@@ -188,11 +200,34 @@ def roofline(info, p, nr, n_dom, phases, precision):
     else:
         flops, name = None, dom
     achieved = flops / (avg[dom] * 1e-3) / 1e12 if flops else None
-    peak = PEAK_TFLOPS[precision]
-    return dict(kernel=name, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                frac=achieved / peak if achieved else None, traffic=None,
-                peak_source=f"measured {precision.upper()} FMA throughput of GB300 (self-written probe)",
+    if precision == "tf32" and dom == "m2l_l2l" and tensor_path(nr):
+        peak, src = tensor_peak_tf32()
+        bound, name = "tensor", name.replace("M2L + L2L", "M2L + L2L on tcgen05 TF32")
+    else:
+        arith = "fp32" if precision == "tf32" else precision
+        peak, bound = PEAK_TFLOPS[arith], "alu"
+        src = f"measured {arith.upper()} FMA throughput of GB300 (self-written probe)"
+    return dict(kernel=name, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=achieved / peak if achieved else None, traffic=None, peak_source=src,
                 algorithmic_flops_per_launch=flops, phase_ms=avg)
+
+
+def tensor_path(nr):
+    """The TF32 matvec runs M2L + L2L on the tensor cores for at least 16 right-hand sides."""
+    return 3 * nr >= 48
+
+
+def launches_per_matvec(lmax, nr, n_dom, precision):
+    """Kernels per matvec: k_prep, k_p2m, k_m2m per level 3..l_max, the downward pass per level
+    2..l_max (tensor path: one k_m2l_tc; chunked: k_m2l_chunks or k_m2l_rot plus k_l2l_reduce per
+    domain; many columns: k_m2l_multi), k_near."""
+    if precision == "tf32" and tensor_path(nr):
+        down = lmax - 1
+    elif 3 * nr <= 24:
+        down = (lmax - 1) * 2 * n_dom
+    else:
+        down = lmax - 1
+    return 3 + (lmax - 2) + down
 
 
 def run_ours(args):
@@ -207,7 +242,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     p = args.p or wl["p"]
-    prec = fm.FP64 if args.precision == "fp64" else fm.FP32
+    prec = {"fp64": fm.FP64, "fp32": fm.FP32, "tf32": fm.TF32}[args.precision]
     V, F, D = wl["mesh"]()
     t0 = time.perf_counter()
     g = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, profile_phases=1)
@@ -279,10 +314,12 @@ def run_ours(args):
     nbytes = x.numel() * 16
 
     other = None
-    if args.precision == "fp64" and not args.no_fp32:
-        ms32, ph32, _, _ = timed(fm.FP32, args.steps, args.warmup)
-        other = dict(precision="fp32", value=world * N * nr / (ms32 * 1e-3), ms_per_step=ms32,
-                     roofline=roofline(info, p, nr, n_dom, ph32, "fp32"))
+    if not args.no_fp32:
+        others = [o for o in ("fp32", "tf32") if o != args.precision and (o == "fp32" or tensor_path(nr))]
+        for o in others:
+            mso, pho, _, _ = timed({"fp32": fm.FP32, "tf32": fm.TF32}[o], args.steps, args.warmup)
+            other = dict(other or {}, **{o: dict(value=world * N * nr / (mso * 1e-3), ms_per_step=mso,
+                                                 roofline=roofline(info, p, nr, n_dom, pho, o))})
     if nr > 1:
         # the plain method's form for comparison: FP64 arithmetic, one right-hand side per matvec
         x1, y1 = x[:1].contiguous(), y[:1].contiguous()
@@ -301,14 +338,17 @@ def run_ours(args):
     solve = None
     if not args.no_solve:
         solve = {}
-        kinds = (("plain_fp64", fm.FP64), ("fp32_inner_fp64_refined", fm.FP32)) if nr == 1 else \
-            (("fp32_inner_fp64_refined", fm.FP32),)
+        if nr == 1:
+            kinds = (("plain_fp64", fm.FP64), ("fp32_inner_fp64_refined", fm.FP32))
+        else:
+            kinds = (("fp32_inner_fp32_refined", fm.FP32),) + \
+                ((("tf32_inner_fp32_refined", fm.TF32),) if tensor_path(nr) else ())
         for label, sp in kinds:
-            # refined solve: FP32 inner GMRES to half the tolerance, true residual with FP64 vectors
-            # (FP64 passes for one right-hand side, FP32 passes with FP64 accumulation for batches)
-            h2 = g if sp == fm.FP64 else fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf,
-                                                   solve_precision=fm.FP32, inner_tol=0.5e-4,
-                                                   outer_precision=fm.FP64 if nr == 1 else fm.FP32)
+            # refined solve: FP32 (or TF32 tensor-core M2L) inner GMRES to half the tolerance, true
+            # residual with FP64 vectors (FP64 passes for one right-hand side, FP32 passes with FP64
+            # accumulation for batches)
+            h2 = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, gmres_restart=args.restart,
+                          solve_precision=sp, inner_tol=0.5e-4, outer_precision=fm.FP64 if nr == 1 else fm.FP32)
             xs = torch.zeros_like(b)
             h2.solve(b, xs, tol=1e-4, max_iter=1000)  # warm-up (allocates the Krylov basis)
             xs.zero_()
@@ -317,9 +357,8 @@ def run_ours(args):
             _, its, rr, st = h2.solve(b, xs, tol=1e-4, max_iter=1000)
             torch.cuda.synchronize()
             solve[label] = dict(tol=1e-4, ms=1e3 * (time.perf_counter() - s0), iters=int(its.max()),
-                                relres=float(rr.max()), status=int(st))
-            if h2 is not g:
-                h2.close()
+                                relres=float(rr.max()), status=int(st), restart=args.restart)
+            h2.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -328,14 +367,11 @@ def run_ours(args):
         cpu = dict(value=rows * nr / min(times), unit=UNIT, cores=cores, kind="oracle",
                    sample=f"{rows} seeded node rows x {nr} RHS of the {Nn}-node dense FP64 operator, best of 2")
 
-    # kernels per matvec: k_prep, k_p2m, k_m2m per level 3..l_max, the downward pass per level
-    # 2..l_max (chunked: k_m2l_chunks + k_l2l_reduce per domain; many columns: k_m2l_multi), k_near
-    chunked = 3 * nr <= 24
-    n_down = (info["l_max"] - 1) * (2 * n_dom if chunked else 1)
-    launches_per_step = 3 + (info["l_max"] - 2) + n_down
+    launches_per_step = launches_per_matvec(info["l_max"], nr, n_dom, args.precision)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64" if args.precision == "fp64" else "f32", data="synthetic",
+                dtype={"fp64": "f64", "fp32": "f32", "tf32": "f32 (M2L on TF32 tensor cores)"}[args.precision],
+                data="synthetic",
                 config=dict(workload=args.workload, desc=wl["desc"], nodes=N, n_rhs=nr, p=p, leaf_size=args.leaf,
                             tree=info, parallelism=f"replicas x{world}",
                             l2="flushed (256 MiB write) before each step", setup_s=setup_s, wall_s=wall),

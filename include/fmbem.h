@@ -60,7 +60,10 @@ typedef enum { FMBEM_NODES_VERTEX = 0, FMBEM_NODES_CENTROID = 1 } fmbem_node_mod
  * FP32: P2P, P2M, M2M, M2L, L2L and L2P in single precision (double-float node positions),
  * with the analytic self blocks, the final accumulation of every result and the GMRES vectors
  * in double precision. */
-typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1 } fmbem_precision;
+/* TF32: as FP32, except that for 16 or more right-hand sides (and an even p <= 8) the M2L and L2L
+ * products run on the tensor cores (tcgen05.mma, TF32 inputs, FP32 accumulation in tensor
+ * memory); meant for the inner iterations of the refined solve. */
+typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1, FMBEM_TF32 = 2 } fmbem_precision;
 
 typedef struct { double re, im; } fmbem_c64;
 

@@ -25,7 +25,7 @@ __all__ = [
     "fmbem_solve", "fmbem_precond_apply", "fmbem_last_matvec_times", "FP64", "FP32", "FMBEMError",
 ]
 
-FP64, FP32 = 0, 1
+FP64, FP32, TF32 = 0, 1, 2
 NODES_VERTEX, NODES_CENTROID = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_MESH", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED", 6: "BREAKDOWN"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fmbem.h")

@@ -138,6 +138,9 @@ struct fmbem {
     c64 *T_m2l64 = nullptr, *T_mm64 = nullptr, *T_ll64 = nullptr;  // see tables.cu for layout
     c32 *T_m2l32 = nullptr, *T_mm32 = nullptr, *T_ll32 = nullptr;
     // rotation form of S|R (see tables.cu): A, B [316][p2][p2], Z [J+1][lmax+1][n_tlen][p2][p2]
+    // tensor-core (tcgen05, TF32) M2L tables: real-form core-matrix images, see m2l_tc.cu
+    float *Atc = nullptr, *Lltc = nullptr;
+    int *tc_err = nullptr;
     bool m2l_rotation = false;
     int n_tlen = 0;
     int8_t *rot_tidx = nullptr;  // [316] index of the offset's length among the distinct lengths
@@ -229,6 +232,9 @@ void build_tables(fmbem *h, cudaStream_t s);
 // per-call operations
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
+bool m2l_tc_supported(const fmbem *h);
+void build_tc_tables(fmbem *h, cudaStream_t s);
+void run_m2l_tc(fmbem *h, const float *C, float *D, int64_t nr, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);
 fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t n_rhs, double tol, int max_iter, int32_t *iters,

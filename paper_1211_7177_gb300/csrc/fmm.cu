@@ -837,25 +837,33 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
 
 // ------------------------------------------------------------------------------------------
 static void ensure_scratch(fmbem *h, int64_t nr) {
-    if (h->scratch_rhs >= nr) return;
-    if (h->dens) { dev_free(h, h->dens); dev_free(h, h->Cexp); dev_free(h, h->Dexp); }
     const size_t cb = sizeof(c64);
-    h->dens = dev_alloc(h, cb * 2 * nr * h->N * 6);
-    h->Cexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
-    h->Dexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
-    h->scratch_rhs = nr;
-    // per-pair M2L results of one level, one domain and up to 24 columns (chunked path only)
-    if (h->ybuf) { dev_free(h, h->ybuf); h->ybuf = nullptr; }
+    if (h->scratch_rhs < nr) {
+        if (h->dens) { dev_free(h, h->dens); dev_free(h, h->Cexp); dev_free(h, h->Dexp); }
+        h->dens = dev_alloc(h, cb * 2 * nr * h->N * 6);
+        h->Cexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
+        h->Dexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
+        h->scratch_rhs = nr;
+    }
+    // per-pair M2L results of one level, one domain and up to 24 columns (chunked path only);
+    // sized by the columns of this call, so that a few-column call after a many-column one
+    // still takes the chunked path
     if (3 * nr <= 24) {
         int64_t mp = 1;
         for (int l = 2; l <= h->lmax; ++l) mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l]);
-        h->ybuf_bytes = cb * (size_t)mp * std::min<int64_t>(3 * nr, 24) * h->p2;
-        h->ybuf = dev_alloc(h, h->ybuf_bytes);
+        const size_t need = cb * (size_t)mp * (size_t)(3 * nr) * h->p2;
+        if (h->ybuf == nullptr || h->ybuf_bytes < need) {
+            if (h->ybuf) dev_free(h, h->ybuf);
+            h->ybuf = nullptr;
+            h->ybuf = dev_alloc(h, need);
+            h->ybuf_bytes = need;
+        }
     }
 }
 
 template <typename R>
-static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc) {
+static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
+                        bool tensor_cores = false) {
     const int64_t N = h->N;
     const int p2 = h->p2, lmax = h->lmax, J = h->J;
     const bool f32 = sizeof(R) == 4;
@@ -917,7 +925,9 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const int pcr = std::min(M2L_CHUNK, cgr * RMAXC / ncol);
     const bool use_rot = chunked && h->m2l_rotation && h->R_A64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
                          rows_pad <= fa_r.maxThreadsPerBlock;
-    if (chunked) {
+    if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
+        run_m2l_tc(h, (const float *)C, (float *)D, nr, s);
+    } else if (chunked) {
         if (tsm) CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         if (use_rot)
@@ -1014,8 +1024,19 @@ void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaS
     ensure_scratch(h, nr);
     static_assert(sizeof(DomainConsts) == 3 * sizeof(c64), "layout");
     DomainConsts *dc = (DomainConsts *)h->dcons;
-    if (precision == FMBEM_FP32) matvec_impl<float>(h, x, y, nr, s, dc);
-    else matvec_impl<double>(h, x, y, nr, s, dc);
+    if (precision == FMBEM_TF32) {
+        matvec_impl<float>(h, x, y, nr, s, dc, true);
+        if (h->tc_err) {  // bounded mbarrier waits of the tensor-core kernel report time-outs here
+            int e = 0;
+            CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (e) throw fmbem_error{FMBEM_ERR_CUDA, "tensor-core M2L: an mbarrier wait timed out"};
+        }
+    } else if (precision == FMBEM_FP32) {
+        matvec_impl<float>(h, x, y, nr, s, dc);
+    } else {
+        matvec_impl<double>(h, x, y, nr, s, dc);
+    }
     h->have_times = h->profile && h->ev[0] != nullptr;
 }
 

@@ -226,7 +226,7 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
                        double *relres, cudaStream_t s) {
     const int m = std::max(1, h->opt.gmres_restart);
     const int64_t n = 6 * h->N;
-    const bool refine = h->opt.solve_precision == FMBEM_FP32;
+    const bool refine = h->opt.solve_precision != FMBEM_FP64;
     size_t need = sizeof(c64) * ((size_t)(m + 1) * nr * n + 2 * nr * n + (refine ? 3 * nr * n : 0));
     if (h->sv_bytes < need) {
         if (h->sv) dev_free(h, h->sv);
@@ -281,7 +281,7 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
                 std::vector<double> ir;
                 std::vector<char> ic;
                 double itol = std::max(h->opt.inner_tol, 0.5 * tol);
-                gmres(h, W, FMBEM_FP32, r, d, itol, max_iter - used, ii, ir, ic, breakdown);
+                gmres(h, W, h->opt.solve_precision, r, d, itol, max_iter - used, ii, ir, ic, breakdown);
                 for (int64_t q = 0; q < nr; ++q) itot[q] += ii[q];
                 k_axpy<<<dim3(nblk(n, 256), (unsigned)nr), 256, 0, s>>>(2, nullptr, d, x, n, nr);
                 CKL("k_axpy");

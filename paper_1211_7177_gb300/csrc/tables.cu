@@ -432,4 +432,6 @@ void build_tables(fmbem *h, cudaStream_t s) {
     dev_free(h, dwq);
     dev_free(h, dk);
     dev_free(h, dl);
+    // tensor-core images of the S|R and R|R matrices for the batched TF32 path
+    if (m2l_tc_supported(h)) build_tc_tables(h, s);
 }

@@ -147,6 +147,28 @@ def test_m2l_rotation_form_matches_dense(p):
         assert rel(yr, yo) < (2e-4 if p == 6 else MATVEC_TOL)
 
 
+def test_tf32_tensor_core_m2l():
+    """16 right-hand sides (48 columns per domain) send M2L and L2L to the tcgen05 kernel in the
+    TF32 mode; its result must stay close to the FP32 CUDA-core result and to the oracle.
+    TF32 keeps 10 mantissa bits, so only the far-field part carries ~1e-4 relative rounding."""
+    V, F, D = fi.icosphere(5)  # 10242 nodes, l_max 3: both S|R and R|R products
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    o, g = case((V, F, D), eps, mu, k0)
+    assert g.tree_info()["l_max"] >= 3
+    x = fi.random_complex((16, o.N, 6), seed=41)
+    y32 = g.matvec(to_dev(x), precision=fm.FP32).cpu().numpy()
+    ytc = g.matvec(to_dev(x), precision=fm.TF32).cpu().numpy()
+    ytc2 = g.matvec(to_dev(x), precision=fm.TF32).cpu().numpy()
+    rows = fi.sample_rows(o.N, 256, seed=42)
+    yo = o.matvec_rows(x, rows)
+    d32 = rel(ytc, y32)
+    print(f"TF32 vs FP32 {d32:.3e}; TF32 vs oracle rows {rel(ytc[:, rows], yo):.3e}; "
+          f"FP32 vs oracle rows {rel(y32[:, rows], yo):.3e}")
+    assert np.array_equal(ytc, ytc2)          # deterministic
+    assert d32 < 1e-3
+    assert rel(ytc[:, rows], yo) < 1e-3
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
