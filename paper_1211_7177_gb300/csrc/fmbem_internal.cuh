@@ -234,7 +234,7 @@ void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cu
 void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
-void run_m2l_tc(fmbem *h, const float *C, float *D, int64_t nr, cudaStream_t s);
+void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);
 fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t n_rhs, double tol, int max_iter, int32_t *iters,

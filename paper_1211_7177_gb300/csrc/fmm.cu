@@ -926,7 +926,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const bool use_rot = chunked && h->m2l_rotation && h->R_A64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
                          rows_pad <= fa_r.maxThreadsPerBlock;
     if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
-        run_m2l_tc(h, (const float *)C, (float *)D, nr, s);
+        run_m2l_tc(h, (float *)C, (float *)D, nr, s);
     } else if (chunked) {
         if (tsm) CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));

@@ -1,56 +1,64 @@
 // m2l_tc.cu -- M2L + L2L (Eq. 2.21) for many right-hand sides on the GB300 tensor cores
-// (tcgen05.mma, kind::tf32, accumulators in tensor memory).
+// (tcgen05.mma kind::tf32 with the accumulator in tensor memory, operands brought in by TMA).
 //
-// For one target box, one domain and a tile of 64 columns (3 Cartesian components x right-hand
+// For one target box, one domain and a tile of N columns (3 Cartesian components x right-hand
 // sides), D[:, tile] = T_ll(oct) D[parent][:, tile] + sum_FF T_o C[src][:, tile] is a chain of
-// complex (p^2 x p^2) x (p^2 x 64) products.  Written in interleaved real form -- row 2r + a is
-// the real (a = 0) or imaginary (a = 1) part of coefficient r, and likewise for K -- each product
-// is a real 128 x 128 x 64 GEMM (p <= 8, zero padded):
-//   A[2r+a][2k+b] = [[Re T, -Im T], [Im T, Re T]][a][b],  B[2k+b][n] = (Re, Im)[b] C[src][n][k],
-// and B column n is exactly the coefficient vector of column n as stored (re, im interleaved), so
-// it is K-major without any rearrangement.  The A matrices are precomputed once per (domain,
-// level, offset), rounded to TF32 and stored in the canonical no-swizzle K-major core-matrix
-// layout (8 rows x 16 bytes per core matrix, K-adjacent core matrices 128 bytes apart, 8-row
-// groups 4096 bytes apart), so staging A is a straight 64 KiB copy.
+// complex (p^2 x p^2) x (p^2 x N) products.  In interleaved real form -- row 2r + a is the real
+// (a = 0) or imaginary (a = 1) part of coefficient r, and likewise along K -- each product is a
+// real 128 x (2 p^2) x N GEMM:
+//   A[2r+a][2k+b] = [[Re T, -Im T], [Im T, Re T]][a][b],   B[2k+b][n] = (Re, Im)[b] C[src][n][k].
+// Column n of B is the coefficient vector of column n exactly as the expansions are stored
+// (re, im interleaved, 2 p^2 floats), so B is K-major in global memory as it stands: TMA reads a
+// 32-float (128-byte) K block of N consecutive columns into shared memory with the 128-byte
+// swizzle.  The A images are precomputed per (domain, level, offset), rounded to TF32 and stored
+// in global memory already in the same swizzled K-major layout, one 16 KiB block per K block, so
+// a plain bulk copy stages them.
 //
-// One CTA of 128 threads: all threads stage A and B into one of two shared-memory stages; thread
-// 0 issues the 16 MMAs of the product (K = 8 each) and commits them to the stage's mbarrier;
-// while the tensor cores work, the threads stage the next product into the other stage.  Waits
-// on mbarriers are bounded: on time-out the kernel records an error flag and stops issuing work.
-// Finally each warp reads its 32 accumulator lanes with tcgen05.ld and writes the complex result.
+// Roles (128 threads, one CTA per (target box, domain, column tile)): thread 0 is the producer
+// (waits for a free stage, arms the stage's mbarrier with the byte count, issues the A bulk copy
+// and the B tensor copy), thread 32 issues the MMAs (waits for a full stage, four K = 8 MMAs per
+// K block, commits to the stage's "empty" mbarrier, finally to the "done" mbarrier), and all four
+// warps read the accumulator with tcgen05.ld and write D.  Every mbarrier wait is bounded (2 s by
+// %globaltimer); on time-out the kernel raises an error flag, stops issuing work, waits (bounded)
+// for its own copies and MMAs in flight, frees its tensor memory and returns.
+#include <cuda.h>  // CUtensorMap and its enums; the encoder itself is looked up at run time
+
 #include <algorithm>
+#include <string>
 
 #include "fmbem_internal.cuh"
 
 namespace {
 
-constexpr int TC_M = 128;          // real-form rows (p^2 <= 64 complex)
-constexpr int TC_K = 128;          // real-form reduction length
-constexpr int TC_N = 64;           // columns per tile
-constexpr int A_BYTES = TC_M * TC_K * 4;   // 64 KiB
-constexpr int B_BYTES = TC_N * TC_K * 4;   // 32 KiB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr unsigned SPIN_LIMIT = 1u << 22;  // one product takes about a microsecond
+constexpr int TC_M = 128;                    // real-form rows (2 p^2 <= 128)
+constexpr int KBLK = 32;                     // TF32 elements per 128-byte swizzle row
+constexpr int A_KB_BYTES = TC_M * KBLK * 4;  // 16 KiB of A per K block
+constexpr int MAX_STAGES = 8;
+constexpr int SMEM_BUDGET = 200 * 1024;      // dynamic shared memory for the stages
+constexpr uint64_t WAIT_NS = 2000000000ull;  // a stage turns over in about a microsecond
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// float index of element (row, k) in the core-matrix layout of a rows x 128 K-major operand
-__host__ __device__ __forceinline__ int core_index(int row, int k) {
-    return (row >> 3) * 1024 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+// float index of element (row, k) of one 128-row K block in the 128-byte-swizzled K-major layout:
+// rows 128 bytes apart, the 16-byte chunk c of row m stored at chunk c ^ (m mod 8)
+__host__ __device__ __forceinline__ int sw128_index(int row, int k) {
+    return row * KBLK + (((k >> 2) ^ (row & 7)) << 2) + (k & 3);
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    const uint64_t lbo = 128, sbo = 4096;  // K-adjacent core matrices, 8-row groups
+// shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= ((lbo >> 4) & 0x3FFFu) << 16;
-    d |= ((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family; base offset 0, no swizzle
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version of the sm_100 family
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
     return d;
 }
 
-// instruction descriptor: D f32, A and B tf32, both K-major, N and M
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                           ((uint32_t)(TC_M >> 4) << 24);
+// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
 
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
@@ -58,6 +66,11 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
 }
@@ -70,18 +83,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; returns false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
-    for (unsigned it = 0; it < SPIN_LIMIT; ++it)
-        if (mbar_try_wait(m, parity)) return true;
-    return false;
+// bounded wait for the phase of the given parity; false on time-out
+__device__ __noinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(m, parity)) return true;
+        if (globaltimer() - t0 > WAIT_NS) return false;
+    }
 }
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on the mbarrier
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+// 2-D tiled tensor copy global -> shared (box and swizzle from the tensor map)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(m))
+        : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *m) {
@@ -89,46 +123,49 @@ __device__ __forceinline__ void mma_commit(uint64_t *m) {
                  : "memory");
 }
 
-// stage one product: A (precomputed layout, straight copy) and B (64 columns of interleaved
-// complex coefficients, p2 complex each, rounded to tf32, zero beyond p2 and beyond ncol)
-__device__ __forceinline__ void stage_product(float *sA, float *sB, const float4 *__restrict__ Ag, const float *Bcols,
-                                              int p2, int ncol) {
-    float4 *sA4 = reinterpret_cast<float4 *>(sA);
-    for (int i = threadIdx.x; i < A_BYTES / 16; i += blockDim.x) sA4[i] = Ag[i];
-    // B: column n, K chunk kc (4 floats): core_index(n, 4kc) .. +3
-    for (int i = threadIdx.x; i < TC_N * (TC_K / 4); i += blockDim.x) {
-        const int n = i / (TC_K / 4), kc = i % (TC_K / 4);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n < ncol && 4 * kc < 2 * p2) {
-            const float4 g = *reinterpret_cast<const float4 *>(Bcols + (int64_t)n * 2 * p2 + 4 * kc);
-            v = make_float4(to_tf32(g.x), to_tf32(g.y), to_tf32(g.z), to_tf32(g.w));
-        }
-        *reinterpret_cast<float4 *>(sB + core_index(n, 4 * kc)) = v;
-    }
-}
+struct TcLevel {
+    int64_t off;          // first box of the level
+    int l, lmax;
+    int64_t nbox;
+    int ncols;            // 3 * n_rhs
+    int p2, kblocks;      // K blocks of 32 real-form elements: ceil(2 p^2 / 32)
+    int n, stages;        // columns per tile (multiple of 16), pipeline depth
+    uint32_t tmem_cols;   // power of two >= n
+    int round_out;        // round D to TF32 (it feeds the next level's L2L product)
+};
 
-__global__ void __launch_bounds__(128) k_m2l_tc(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t nbox,
-                                                const int32_t *parent, const uint64_t *key, const int32_t *ff_start,
-                                                const int32_t *ff_src, const int16_t *ff_off, const float4 *Atc,
-                                                const float4 *Lltc, const float *C, float *D, int *err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t mbar[2];
+__global__ void __launch_bounds__(128, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmD, const TcLevel P,
+             const int32_t *__restrict__ parent, const uint64_t *__restrict__ key, const int32_t *__restrict__ ff_start,
+             const int32_t *__restrict__ ff_src, const int16_t *__restrict__ ff_off, const float *__restrict__ Atc,
+             const float *__restrict__ Lltc, float *D, int *err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full[MAX_STAGES], empty[MAX_STAGES], done;
     __shared__ uint32_t tmem_slot;
-    const int64_t g = off + blockIdx.x;
-    const int d = blockIdx.y;
-    const int ncols = (int)(3 * nr);
-    const int col0 = blockIdx.z * TC_N;
-    const int nh = min(TC_N, ncols - col0);
+    __shared__ volatile int s_abort;
+    __shared__ int s_fin;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = P.off + blockIdx.x;
+    const int d = blockIdx.y;
+    const int col0 = blockIdx.z * P.n;
+    const int nh = min(P.n, P.ncols - col0);
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
+    const uint32_t stage_bytes = A_KB_BYTES + (uint32_t)P.n * 128u;
 
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int s = 0; s < P.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_abort = *(volatile int *)err;  // an earlier CTA timed out: issue nothing
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmD)) : "memory");
     }
     if (warp == 0)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TC_N)
+                     "r"(P.tmem_cols)
                      : "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -136,63 +173,79 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int64_t off, int l, int lmax, in
     const uint32_t tmem = tmem_slot;
 
     const int e0 = ff_start[g], e1 = ff_start[g + 1];
-    const bool has_l2l = l >= 3;
-    const int nprod = (has_l2l ? 1 : 0) + (e1 - e0);
-    const int64_t tbl_level = ((int64_t)d * (lmax + 1) + l);
-    // waits are taken by thread 0 alone and their outcome is shared, so every thread leaves the
-    // loop at the same product even when a bounded wait times out
-    __shared__ int s_ok;
-    bool ok = true;
-    for (int i = 0; i < nprod && ok; ++i) {
-        const int s = i & 1;
-        float *sA = reinterpret_cast<float *>(smem_raw + s * STAGE_BYTES);
-        float *sB = reinterpret_cast<float *>(smem_raw + s * STAGE_BYTES + A_BYTES);
-        if (i >= 2) {  // the MMAs that read this stage two products ago must be done
-            if (threadIdx.x == 0) s_ok = mbar_wait(&mbar[s], ((i - 2) >> 1) & 1) ? 1 : 0;
-            __syncthreads();
-            ok = s_ok != 0;
-            if (!ok) break;
+    const int has_l2l = P.l >= 3 ? 1 : 0;
+    const int nprod = has_l2l + (e1 - e0);
+    const int nunits = nprod * P.kblocks;
+    const int64_t tbl = (int64_t)d * (P.lmax + 1) + P.l;
+    const int64_t a_mat = (int64_t)P.kblocks * (A_KB_BYTES / 4);  // floats per A image
+    int issued = 0;
+
+    if (threadIdx.x == 0 && nunits > 0) {
+        // ------------------------------------------------------------------ producer
+        bool ok = true;
+        int s = 0, q = 0;
+        for (int u = 0; u < nunits; ++u) {
+            if (q > 0 && !mbar_wait(&empty[s], (uint32_t)(q - 1) & 1u)) { ok = false; break; }
+            if (s_abort || *(volatile int *)err) break;
+            const int i = u / P.kblocks, kb = u - i * P.kblocks;
+            const float *Asrc;
+            const CUtensorMap *tm;
+            int y;
+            if (has_l2l && i == 0) {
+                Asrc = Lltc + (tbl * 8 + (int)(key[g] & 7)) * a_mat;
+                tm = &tmD;
+                y = (int)(((int64_t)d * P.nbox + parent[g]) * P.ncols + col0);
+            } else {
+                const int e = e0 + i - has_l2l;
+                Asrc = Atc + (tbl * 316 + ff_off[e]) * a_mat;
+                tm = &tmC;
+                y = (int)(((int64_t)d * P.nbox + ff_src[e]) * P.ncols + col0);
+            }
+            const uint32_t sA = sbase + (uint32_t)s * stage_bytes, sB = sA + A_KB_BYTES;
+            mbar_arrive_expect_tx(&full[s], stage_bytes);
+            bulk_load(sA, Asrc + (int64_t)kb * (A_KB_BYTES / 4), A_KB_BYTES, &full[s]);
+            tma_load_2d(sB, tm, kb * KBLK, y, &full[s]);
+            ++issued;
+            if (++s == P.stages) { s = 0; ++q; }
         }
-        const float4 *Ag;
-        const float *Bc;
-        if (has_l2l && i == 0) {
-            Ag = Lltc + (tbl_level * 8 + (int)(key[g] & 7)) * (A_BYTES / 16);
-            Bc = D + (((int64_t)d * nbox + parent[g]) * ncols + col0) * 2 * p2;
-        } else {
-            const int e = e0 + i - (has_l2l ? 1 : 0);
-            Ag = Atc + (tbl_level * 316 + ff_off[e]) * (A_BYTES / 16);
-            Bc = C + (((int64_t)d * nbox + ff_src[e]) * ncols + col0) * 2 * p2;
-        }
-        stage_product(sA, sB, Ag, Bc, p2, nh);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make generic stores visible to the tensor cores
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (!ok) { atomicExch(err, 1); s_abort = 1; }
+    } else if (threadIdx.x == 32 && nunits > 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_tf32(P.n);
+        bool ok = true;
+        int s = 0, q = 0;
+        for (int u = 0; u < nunits && !s_abort; ++u) {
+            if (!mbar_wait(&full[s], (uint32_t)q & 1u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t sA = sbase + (uint32_t)s * stage_bytes, sB = sA + A_KB_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < TC_K / 8; ++kk)  // each MMA consumes two K-adjacent core matrices
-                mma_tf32(tmem, smem_desc(a0 + kk * 256), smem_desc(b0 + kk * 256), (i > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&mbar[s]);
+            for (int j = 0; j < KBLK / 8; ++j)  // K = 8 TF32 per MMA = 32 bytes along the swizzled row
+                mma_tf32(tmem, smem_desc_sw128(sA + 32u * j), smem_desc_sw128(sB + 32u * j), idesc,
+                         (u > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            if (++s == P.stages) { s = 0; ++q; }
         }
+        mma_commit(&done);  // arrives once every MMA issued above has completed
+        if (!ok) { atomicExch(err, 1); s_abort = 1; }
     }
+    __syncwarp();
+    __syncthreads();
     if (threadIdx.x == 0) {
-        bool fin = ok;
-        if (fin && nprod > 0) fin = mbar_wait(&mbar[(nprod - 1) & 1], ((nprod - 1) >> 1) & 1);
-        if (!fin) atomicExch(err, 1);
-        s_ok = fin ? 1 : 0;
+        bool fin = !s_abort;
+        if (nunits > 0 && !mbar_wait(&done, 0)) { fin = false; atomicExch(err, 1); }
+        s_fin = fin ? 1 : 0;
     }
     __syncthreads();
-    ok = s_ok != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    float *Dout = D + (((int64_t)d * P.nbox + g) * P.ncols + col0) * 2 * P.p2;
     if (nprod == 0) {  // no translation reaches this box: its local expansion is zero
-        float *Dout = D + (((int64_t)d * nbox + g) * ncols + col0) * 2 * p2;
-        for (int i = threadIdx.x; i < nh * 2 * p2; i += blockDim.x) Dout[i] = 0.f;
-    } else if (ok) {
-        // warp w owns accumulator lanes 32w..32w+31 = real-form rows; row R = 2r + a
-        const int R = warp * 32 + lane, r = R >> 1, a = R & 1;
-        float *Dout = D + (((int64_t)d * nbox + g) * ncols + col0) * 2 * p2;
-#pragma unroll
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+        for (int i = threadIdx.x; i < nh * 2 * P.p2; i += blockDim.x) Dout[i] = 0.f;
+    } else if (s_fin) {
+        // warp w owns accumulator lanes 32w..32w+31 = real-form rows R = 2r + a
+        const int R = warp * 32 + lane;
+        const bool row_ok = R < 2 * P.p2;
+        for (int c0 = 0; c0 < P.n; c0 += 16) {
             uint32_t v[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile(
@@ -201,67 +254,139 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int64_t off, int l, int lmax, in
                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (r < p2)
+            if (row_ok)
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    if (c0 + j < nh) Dout[(int64_t)(c0 + j) * 2 * p2 + 2 * r + a] = __uint_as_float(v[j]);
+                    if (c0 + j < nh) {
+                        const float x = __uint_as_float(v[j]);
+                        Dout[(int64_t)(c0 + j) * 2 * P.p2 + R] = P.round_out ? to_tf32(x) : x;
+                    }
         }
+    }
+    if (threadIdx.x == 0 && issued > 0) {
+        // copies still in flight after an abort: wait (bounded) for the last copy of each stage
+        for (int u = max(0, issued - P.stages); u < issued; ++u)
+            if (!mbar_wait(&full[u % P.stages], (uint32_t)(u / P.stages) & 1u)) atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 }
 
 // real-form TF32 image of one complex p2 x p2 matrix stored input-major (T[c][r]) in double
-// precision, written in the core-matrix layout: A[2r+a][2k+b]
-__global__ void k_build_tc_tables(const c64 *T, int64_t nmat, int p2, float *out) {
+// precision, written as kblocks swizzled K blocks: A[2r+a][2k+b]
+__global__ void k_build_tc_tables(const c64 *T, int64_t nmat, int p2, int kblocks, float *out) {
+    const int64_t per = (int64_t)kblocks * TC_M * KBLK;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= nmat * TC_M * TC_K) return;
-    const int64_t m = idx / (TC_M * TC_K);
-    const int R = (int)(idx % (TC_M * TC_K)) / TC_K, K = (int)(idx % TC_K);
+    if (idx >= nmat * per) return;
+    const int64_t m = idx / per;
+    const int rem = (int)(idx % per);
+    const int kb = rem / (TC_M * KBLK), R = (rem % (TC_M * KBLK)) / KBLK, kk = rem % KBLK;
+    const int K = kb * KBLK + kk;
     const int r = R >> 1, a = R & 1, k = K >> 1, b = K & 1;
     float v = 0.f;
     if (r < p2 && k < p2) {
         const c64 t = T[(m * p2 + k) * p2 + r];
-        // [[Re, -Im], [Im, Re]]
-        double x = (a == 0) ? (b == 0 ? t.re : -t.im) : (b == 0 ? t.im : t.re);
+        const double x = (a == 0) ? (b == 0 ? t.re : -t.im) : (b == 0 ? t.im : t.re);  // [[Re, -Im], [Im, Re]]
         v = to_tf32((float)x);
     }
-    out[m * (TC_M * TC_K) + core_index(R, K)] = v;
+    out[m * per + (int64_t)kb * TC_M * KBLK + sw128_index(R, kk)] = v;
 }
+
+// round a float array to TF32 in place (the expansions the tensor-core products read as B)
+__global__ void k_round_tf32(float *x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = to_tf32(x[i]);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || p == nullptr)
+            throw fmbem_error{FMBEM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver"};
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// rows of 2 p^2 floats (one column's coefficients), boxes of 32 floats x n rows, 128-byte swizzle
+CUtensorMap make_column_map(const float *base, int64_t rows, int p2, int n) {
+    CUtensorMap tm;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * p2), (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * p2) * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)n};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides,
+                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        throw fmbem_error{FMBEM_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r)};
+    return tm;
+}
+
+int tc_kblocks(int p2) { return (2 * p2 + KBLK - 1) / KBLK; }
 
 }  // namespace
 
-// p^2 <= 64 fills the 128-row real form; an even p keeps every column 16-byte aligned
-bool m2l_tc_supported(const fmbem *h) { return h->p <= 8 && h->p % 2 == 0; }
+// 2 p^2 <= 128 fills the 128-row real form; p >= 4 makes a column's 2 p^2 floats at least one
+// full 128-byte K block; an even p keeps the rows a multiple of 16 bytes, as a tensor map needs
+bool m2l_tc_supported(const fmbem *h) { return h->p >= 4 && h->p <= 8 && h->p % 2 == 0; }
 
 void build_tc_tables(fmbem *h, cudaStream_t s) {
-    const int p2 = h->p2;
+    const int p2 = h->p2, kb = tc_kblocks(p2);
+    const int64_t per = (int64_t)kb * TC_M * KBLK;
     const int64_t n_m2l = (int64_t)(h->J + 1) * (h->lmax + 1) * 316, n_oct = (int64_t)(h->J + 1) * (h->lmax + 1) * 8;
-    h->Atc = (float *)dev_alloc(h, (size_t)A_BYTES * n_m2l);
-    h->Lltc = (float *)dev_alloc(h, (size_t)A_BYTES * n_oct);
+    h->Atc = (float *)dev_alloc(h, sizeof(float) * per * n_m2l);
+    h->Lltc = (float *)dev_alloc(h, sizeof(float) * per * n_oct);
     const int tb = 256;
-    k_build_tc_tables<<<(unsigned)((n_m2l * TC_M * TC_K + tb - 1) / tb), tb, 0, s>>>(h->T_m2l64, n_m2l, p2, h->Atc);
+    k_build_tc_tables<<<(unsigned)((n_m2l * per + tb - 1) / tb), tb, 0, s>>>(h->T_m2l64, n_m2l, p2, kb, h->Atc);
     CKL("k_build_tc_tables");
-    k_build_tc_tables<<<(unsigned)((n_oct * TC_M * TC_K + tb - 1) / tb), tb, 0, s>>>(h->T_ll64, n_oct, p2, h->Lltc);
+    k_build_tc_tables<<<(unsigned)((n_oct * per + tb - 1) / tb), tb, 0, s>>>(h->T_ll64, n_oct, p2, kb, h->Lltc);
     CKL("k_build_tc_tables");
     h->tc_err = (int *)dev_alloc(h, sizeof(int));
     CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
 }
 
-// downward pass for all levels, single precision coefficients (C, D as interleaved floats)
-void run_m2l_tc(fmbem *h, const float *C, float *D, int64_t nr, cudaStream_t s) {
-    const size_t smem = 2 * (size_t)STAGE_BYTES;
+// columns per tile: the fewest tiles of at most 256 columns, split evenly, rounded up to 16
+void tc_tile_shape(int64_t ncols, int *n, int *ntile) {
+    const int64_t t = (ncols + 255) / 256;
+    *ntile = (int)t;
+    *n = (int)(((ncols + t - 1) / t + 15) / 16 * 16);
+}
+
+// downward pass for all levels: the multipole expansions C are rounded to TF32 in place first
+// (from here on only these products read them), then one launch per level
+void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s) {
+    const int64_t ncols = 3 * nr;
+    const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
+    k_round_tf32<<<152 * 8, 256, 0, s>>>(C, nfloat);
+    CKL("k_round_tf32");
+    int n, ntile;
+    tc_tile_shape(ncols, &n, &ntile);
+    const int stage = A_KB_BYTES + n * 128;
+    const int stages = std::min(MAX_STAGES, SMEM_BUDGET / stage);
+    const size_t smem = (size_t)stages * stage + 1024;  // + slack to align the stages to 1024 bytes
+    uint32_t tcols = 32;
+    while ((int)tcols < n) tcols <<= 1;
     CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned ntile = (unsigned)((3 * nr + TC_N - 1) / TC_N);
+    const int64_t rows = (int64_t)(h->J + 1) * h->nbox * ncols;
+    const CUtensorMap tmC = make_column_map(C, rows, h->p2, n), tmD = make_column_map(D, rows, h->p2, n);
     for (int l = 2; l <= h->lmax; ++l) {
         const LevelInfo &Lv = h->lev[l];
-        k_m2l_tc<<<dim3((unsigned)Lv.n, h->J + 1, ntile), 128, smem, s>>>(
-            Lv.off, l, h->lmax, nr, h->p2, h->nbox, h->box_parent, h->box_key, h->ff_start, h->ff_src, h->ff_off,
-            (const float4 *)h->Atc, (const float4 *)h->Lltc, C, D, h->tc_err);
+        const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), n, stages, tcols,
+                        l < h->lmax ? 1 : 0};
+        k_m2l_tc<<<dim3((unsigned)Lv.n, h->J + 1, (unsigned)ntile), 128, smem, s>>>(
+            tmC, tmD, P, h->box_parent, h->box_key, h->ff_start, h->ff_src, h->ff_off, h->Atc, h->Lltc, D, h->tc_err);
         CKL("k_m2l_tc");
     }
 }

@@ -147,26 +147,31 @@ def test_m2l_rotation_form_matches_dense(p):
         assert rel(yr, yo) < (2e-4 if p == 6 else MATVEC_TOL)
 
 
-def test_tf32_tensor_core_m2l():
-    """16 right-hand sides (48 columns per domain) send M2L and L2L to the tcgen05 kernel in the
-    TF32 mode; its result must stay close to the FP32 CUDA-core result and to the oracle.
-    TF32 keeps 10 mantissa bits, so only the far-field part carries ~1e-4 relative rounding."""
+@pytest.mark.parametrize("n_rhs,p", [(16, 8), (100, 8), (40, 6)])
+def test_tf32_tensor_core_m2l(n_rhs, p):
+    """At least 16 right-hand sides send M2L and L2L to the tcgen05 kernel in the TF32 mode; its
+    result must stay close to the FP32 CUDA-core result and to the oracle.  The cases cover one
+    48-column tile, two 160-column tiles with a ragged second tile (300 columns), and p = 6
+    (three 32-element K blocks, the last one partly past the coefficients).  TF32 keeps 10
+    mantissa bits, so only the far-field part carries ~1e-4 relative rounding."""
     V, F, D = fi.icosphere(5)  # 10242 nodes, l_max 3: both S|R and R|R products
     eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
-    o, g = case((V, F, D), eps, mu, k0)
+    o, g = case((V, F, D), eps, mu, k0, p=p)
     assert g.tree_info()["l_max"] >= 3
-    x = fi.random_complex((16, o.N, 6), seed=41)
+    x = fi.random_complex((n_rhs, o.N, 6), seed=41)
     y32 = g.matvec(to_dev(x), precision=fm.FP32).cpu().numpy()
     ytc = g.matvec(to_dev(x), precision=fm.TF32).cpu().numpy()
     ytc2 = g.matvec(to_dev(x), precision=fm.TF32).cpu().numpy()
-    rows = fi.sample_rows(o.N, 256, seed=42)
+    rows = fi.sample_rows(o.N, 128, seed=42)
     yo = o.matvec_rows(x, rows)
     d32 = rel(ytc, y32)
-    print(f"TF32 vs FP32 {d32:.3e}; TF32 vs oracle rows {rel(ytc[:, rows], yo):.3e}; "
+    print(f"n_rhs {n_rhs} p {p}: TF32 vs FP32 {d32:.3e}; TF32 vs oracle rows {rel(ytc[:, rows], yo):.3e}; "
           f"FP32 vs oracle rows {rel(y32[:, rows], yo):.3e}")
     assert np.array_equal(ytc, ytc2)          # deterministic
     assert d32 < 1e-3
     assert rel(ytc[:, rows], yo) < 1e-3
+    for r in (0, n_rhs - 1):                  # first and last right-hand side of the batch
+        assert rel(ytc[r], y32[r]) < 1e-3
 
 
 def test_two_scatterers_and_permeability():
