@@ -59,10 +59,12 @@ typedef enum { FMBEM_NODES_VERTEX = 0, FMBEM_NODES_CENTROID = 1 } fmbem_node_mod
 /* Arithmetic of the near-field and far-field passes.  FP64: everything in double precision.
  * FP32: P2P, P2M, M2M, M2L, L2L and L2P in single precision (double-float node positions),
  * with the analytic self blocks, the final accumulation of every result and the GMRES vectors
- * in double precision. */
-/* TF32: as FP32, except that for 16 or more right-hand sides (and an even p <= 8) the M2L and L2L
- * products run on the tensor cores (tcgen05.mma, TF32 inputs, FP32 accumulation in tensor
- * memory); meant for the inner iterations of the refined solve. */
+ * in double precision.
+ * TF32: as FP32, except that for 16 or more right-hand sides (and p = 4, 6 or 8) the M2L and
+ * L2L products run on the tensor cores (tcgen05.mma, inputs rounded to TF32, FP32 accumulation
+ * in tensor memory); meant for the inner iterations of the refined solve.  The rounding adds a
+ * relative error of about 1e-5 to a matvec and makes it slightly nonlinear, so an inner GMRES
+ * on it should stop at a loose tolerance (1e-2) and let the outer refinement finish. */
 typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1, FMBEM_TF32 = 2 } fmbem_precision;
 
 typedef struct { double re, im; } fmbem_c64;

@@ -101,6 +101,7 @@ struct fmbem {
     // self blocks (user order): M = A_self [N][6][6], LU factors and pivots
     c64 *Mself = nullptr, *Mlu = nullptr;
     int8_t *piv = nullptr;
+    c32 *Minv32 = nullptr;  // single-precision explicit inverses for the inner iterations (lazy)
 
     // octree (Appendix C)
     int lmax = 0;
@@ -137,13 +138,14 @@ struct fmbem {
     c32 *B_p2m32 = nullptr, *B_l2p32 = nullptr;
     c64 *T_m2l64 = nullptr, *T_mm64 = nullptr, *T_ll64 = nullptr;  // see tables.cu for layout
     c32 *T_m2l32 = nullptr, *T_mm32 = nullptr, *T_ll32 = nullptr;
-    // rotation form of S|R (see tables.cu): A, B [316][p2][p2], Z [J+1][lmax+1][n_tlen][p2][p2]
-    // tensor-core (tcgen05, TF32) M2L tables: real-form core-matrix images, see m2l_tc.cu
+    // tensor-core (tcgen05, TF32) M2L tables: real-form 128-byte-swizzled images, see m2l_tc.cu
     float *Atc = nullptr, *Lltc = nullptr;
     int *tc_err = nullptr;
     bool m2l_rotation = false;
     int n_tlen = 0;
     int8_t *rot_tidx = nullptr;  // [316] index of the offset's length among the distinct lengths
+    // rotation form of S|R (tables.cu builds them dense, pack_rot_tables in fmm.cu packs them):
+    // A, B [316][degree blocks], Z [J+1][lmax+1][n_tlen][order blocks]
     c64 *R_A64 = nullptr, *R_B64 = nullptr, *R_Z64 = nullptr;
     c32 *R_A32 = nullptr, *R_B32 = nullptr, *R_Z32 = nullptr;
 
@@ -235,7 +237,9 @@ void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int preci
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
+void pack_rot_tables(fmbem *h, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
+void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);
 fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t n_rhs, double tol, int max_iter, int32_t *iters,
                        double *relres, cudaStream_t s);

@@ -13,6 +13,8 @@
 // analytic self block A_self (Appendix B).
 #include <algorithm>
 
+#include <type_traits>
+
 #include "fmbem_internal.cuh"
 
 namespace {
@@ -81,6 +83,56 @@ __global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t n
             }
         }
         for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
+    }
+}
+
+// P2M for blocks of RB right-hand sides: the basis values of a (node, coefficient) are read once
+// and applied to every right-hand side of the block; grid (leaf, domain, rhs block), thread per
+// coefficient; same arithmetic, order and layout as k_p2m
+template <typename R, int RB>
+__global__ void k_p2m_rb(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+                         const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens,
+                         const cx<R> *Bp2m, cx<R> *C) {
+    const int64_t g = leaf_off + blockIdx.x;
+    const int d = blockIdx.y;
+    const int64_t rb0 = (int64_t)blockIdx.z * RB;
+    const int nrb = (int)min((int64_t)RB, nr - rb0);
+    const int side = d == 0 ? 0 : 1;
+    const R sg = d == 0 ? (R)-1 : (R)1;
+    const int i0 = nbeg[g], i1 = nend[g];
+    for (int q = threadIdx.x; q < p2; q += blockDim.x) {
+        cx<R> acc[RB][3];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[rr][c] = {0, 0};
+        for (int i = i0; i < i1; ++i) {
+            if (d > 0 && dom[i] != d) continue;
+            const R n[3] = {sg * (R)nrm[3 * i], sg * (R)nrm[3 * i + 1], sg * (R)nrm[3 * i + 2]};
+            const cx<R> *B = Bp2m + ((int64_t)side * N + i) * 4 * p2;
+            const cx<R> b0 = B[q], G[3] = {B[p2 + q], B[2 * p2 + q], B[3 * p2 + q]};
+            const cx<R> nG = n[0] * G[0] + n[1] * G[1] + n[2] * G[2];
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) {
+                if (rr >= nrb) break;
+                const cx<R> *dn = dens + ((side * nr + rb0 + rr) * N + i) * 6;
+                const cx<R> v[3] = {dn[0], dn[1], dn[2]}, qq[3] = {dn[3], dn[4], dn[5]};
+                const cx<R> nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+                const cx<R> vG = v[0] * G[0] + v[1] * G[1] + v[2] * G[2];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    // m_c . G = v_c (n.G) + (n.v) G_c - n_c (v.G), plus the monopole q_c R
+                    const cx<R> t = v[c] * nG + nv * G[c] - n[c] * vG + qq[c] * b0;
+                    acc[rr][c] += t;
+                }
+            }
+        }
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            if (rr >= nrb) break;
+            for (int c = 0; c < 3; ++c)
+                C[(((int64_t)d * nbox + g) * 3 * nr + 3 * (rb0 + rr) + c) * p2 + q] = acc[rr][c];
+        }
     }
 }
 
@@ -248,23 +300,14 @@ __global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, in
     const int64_t ck = chunk0 + blockIdx.x;
     const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
     const int o = chunk_off[ck];
-    const cx<R> *A = RA + (int64_t)o * p2 * p2, *B = RB + (int64_t)o * p2 * p2;
-    const cx<R> *Z = RZ + (((int64_t)d * (lmax + 1) + l) * n_tlen + tidx[o]) * p2 * p2;
+    // packed tables (see pack_rot_tables): a straight copy of this offset's blocks
+    const cx<R> *A = RA + (int64_t)o * nrot, *B = RB + (int64_t)o * nrot;
+    const cx<R> *Z = RZ + (((int64_t)d * (lmax + 1) + l) * n_tlen + tidx[o]) * ncoax;
     for (int i = threadIdx.x; i < nrot; i += blockDim.x) {
-        int n = 0;
-        while (rot_off(n + 1) <= i) ++n;
-        const int w = 2 * n + 1, loc = i - rot_off(n), row = loc / w, col = loc - row * w;
-        // row/col index the output/input order within the degree block: m = index - n
-        Ab[i] = A[(int64_t)(n * n + col) * p2 + n * n + row];
-        Bb[i] = B[(int64_t)(n * n + col) * p2 + n * n + row];
+        Ab[i] = A[i];
+        Bb[i] = B[i];
     }
-    for (int i = threadIdx.x; i < ncoax; i += blockDim.x) {
-        int m = -(p - 1), base = 0;
-        while (base + (p - abs(m)) * (p - abs(m)) <= i) { base += (p - abs(m)) * (p - abs(m)); ++m; }
-        const int am = abs(m), w = p - am, loc = i - base, row = loc / w, col = loc - row * w;
-        const int np = am + row, n = am + col;  // output degree n', input degree n
-        Zb[i] = Z[(int64_t)(n * n + n + m) * p2 + np * np + np + m];
-    }
+    for (int i = threadIdx.x; i < ncoax; i += blockDim.x) Zb[i] = Z[i];
     const int rows_pad = blockDim.x / cg;
     const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
     int rn = (int)sqrtf((float)r);
@@ -508,6 +551,41 @@ __device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R>
     }
 }
 
+// Epilogue of one result row of one target node a (row = 3 * side + component): the sum of the
+// source slices' partial results red[sl * nt + ti] in slice order, plus the far field (L2P,
+// Eq. 2.23 first term) of that side's domain from the leaf's local expansion, plus the row of the
+// analytic self block applied to x in double precision; stored in user order.
+template <typename R>
+__device__ __forceinline__ void near_epilogue(const cx<R> *red, int ti, int nt, int nsl, int a, int row, int64_t r,
+                                              int64_t g, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                              const int32_t *dom, const int32_t *perm, const cx<R> *Bl2p,
+                                              const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
+    const int sd = row / 3, c = row % 3;
+    cx<R> v = red[ti];
+    for (int sl = 1; sl < nsl; ++sl) v += red[sl * nt + ti];
+    const int d = sd == 0 ? 0 : dom[a];
+    const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2;
+    const cx<R> *B = Bl2p + ((int64_t)sd * N + a) * p2;
+    for (int q = 0; q < p2; ++q) cfma(v, Dl[q], B[q]);
+    const int64_t u = perm[a];
+    const c64 *M = Mself + 36 * u + 6 * row;
+    const c64 *xa = x + (r * N + u) * 6;
+    c64 sacc = {(double)v.re, (double)v.im};
+    for (int cc = 0; cc < 6; ++cc) cfma(sacc, M[cc], xa[cc]);
+    y[(r * N + u) * 6 + row] = sacc;
+}
+
+// index of the neighbour range holding source e: the last q with cum[q] <= e (binary search)
+__device__ __forceinline__ int source_range(const int *cum, int nnb, int e) {
+    int lo = 0, hi = nnb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cum[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Step 4 for one leaf: near field over the leaf and its Neighbor leaves (both domains), far field
 // from the leaf's local expansions (L2P), the analytic self block in double precision, and the
 // store of the 6 result rows in user order.  Up to 128 targets per pass; the 128 threads split as
@@ -554,8 +632,7 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                 {  // stage a tile of sources
                     int e = s0 + threadIdx.x;
                     if (e < nsrc) {
-                        int q = 0;
-                        while (q + 1 < nnb && rng_cum[q + 1] <= e) ++q;
+                        const int q = source_range(rng_cum, nnb, e);
                         int i = rng_beg[q] + (e - rng_cum[q]);
                         const int t = threadIdx.x;
                         T.pa[t] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
@@ -597,40 +674,15 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                         }
                     }
             }
-            // reduce the source slices in a fixed order
+            // reduce the source slices in a fixed order, then far field (L2P), self block and store,
+            // one (target, result row) item per thread so that all warps share the epilogue
             __syncthreads();
             for (int c = 0; c < 3; ++c) { S.red[c][threadIdx.x] = acc0[c]; S.red[3 + c][threadIdx.x] = acc1[c]; }
             __syncthreads();
-            if (threadIdx.x < nt) {
-                for (int sl = 1; sl < nsl; ++sl)
-                    for (int c = 0; c < 3; ++c) {
-                        acc0[c] += S.red[c][sl * nt + threadIdx.x];
-                        acc1[c] += S.red[3 + c][sl * nt + threadIdx.x];
-                    }
-                // far field, L2P: y_i += sum_nm D[d][leaf][3r+i][nm] B_l2p[side][a][nm]
-                for (int sd = 0; sd < 2; ++sd) {
-                    int d = sd == 0 ? 0 : adom;
-                    const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r) * p2;
-                    const cx<R> *B = Bl2p + ((int64_t)sd * N + a) * p2;
-                    cx<R> *acc = sd == 0 ? acc0 : acc1;
-                    for (int q = 0; q < p2; ++q) {
-                        cx<R> b = B[q];
-                        cfma(acc[0], Dl[q], b);
-                        cfma(acc[1], Dl[p2 + q], b);
-                        cfma(acc[2], Dl[2 * p2 + q], b);
-                    }
-                }
-                // self block A_self x in double precision, store in user order
-                int64_t u = perm[a];
-                const c64 *M = Mself + 36 * u;
-                const c64 *xa = x + (r * N + u) * 6;
-                c64 *ya = y + (r * N + u) * 6;
-                for (int row = 0; row < 6; ++row) {
-                    c64 sacc = row < 3 ? c64{(double)acc0[row].re, (double)acc0[row].im}
-                                       : c64{(double)acc1[row - 3].re, (double)acc1[row - 3].im};
-                    for (int c = 0; c < 6; ++c) cfma(sacc, M[row * 6 + c], xa[c]);
-                    ya[row] = sacc;
-                }
+            for (int it = threadIdx.x; it < nt * 6; it += blockDim.x) {
+                const int ti = it % nt, row = it / nt;
+                near_epilogue<R>(S.red[row], ti, nt, nsl, tb + ti, row, r, g, N, nr, p2, nbox, dom, perm, Bl2p, D,
+                                 Mself, x, y);
             }
         }
     }
@@ -702,7 +754,8 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
     __syncthreads();
     const int nsrc = rng_cum[nnb];
     const int t0 = nbeg[g], t1 = nend[g];
-    for (int64_t rb0 = 0; rb0 < nr; rb0 += RB) {
+    {
+        const int64_t rb0 = (int64_t)blockIdx.y * RB;  // this block's right-hand sides
         const int nrb = (int)min((int64_t)RB, nr - rb0);
         for (int tb = t0; tb < t1; tb += 128) {
             const int nt = min(128, t1 - tb);
@@ -726,8 +779,7 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
                     const int t = e2 % NB_TILE, part = e2 / NB_TILE;  // part 0: geometry, 1..: (side, rhs)
                     const int e = s0 + t;
                     if (e >= nsrc) continue;
-                    int q = 0;
-                    while (q + 1 < nnb && rng_cum[q + 1] <= e) ++q;
+                    const int q = source_range(rng_cum, nnb, e);
                     const int i = rng_beg[q] + (e - rng_cum[q]);
                     if (part == 0) {
                         T.pa[t] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
@@ -791,51 +843,220 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
                     S.red[3 + c][rr][threadIdx.x] = acc1[rr][c];
                 }
             __syncthreads();
-            if (threadIdx.x < nt) {
-                const int64_t u = perm[a];
-                const c64 *M = Mself + 36 * u;
-                for (int rr = 0; rr < nrb; ++rr) {
-                    cx<R> s0v[3], s1v[3];
-                    for (int c = 0; c < 3; ++c) {
-                        s0v[c] = S.red[c][rr][threadIdx.x];
-                        s1v[c] = S.red[3 + c][rr][threadIdx.x];
-                        for (int sl = 1; sl < nsl; ++sl) {
-                            s0v[c] += S.red[c][rr][sl * nt + threadIdx.x];
-                            s1v[c] += S.red[3 + c][rr][sl * nt + threadIdx.x];
+            for (int it = threadIdx.x; it < nt * 6 * nrb; it += blockDim.x) {
+                const int ti = it % nt, rest = it / nt, row = rest % 6, rr = rest / 6;
+                near_epilogue<R>(S.red[row][rr], ti, nt, nsl, tb + ti, row, rb0 + rr, g, N, nr, p2, nbox, dom, perm,
+                                 Bl2p, D, Mself, x, y);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- warp-independent near field
+// One warp owns one work item: up to 32 target nodes of one leaf (a lane per target), one side
+// (domain 0, or the target's own scatterer) and one block of RB right-hand sides.  It streams the
+// sources of the leaf's Neighbor list through a warp-private shared-memory tile of 32 (each lane
+// stages one source: geometry and the RB densities of its side), synchronising only the warp, so
+// warps never wait for one another.  Per (source, target) pair it evaluates the kernel scalars
+// once and applies them to the RB right-hand sides; then each lane adds the far field (L2P) of
+// its side and the side's three rows of the self block (double precision) and stores them.
+template <typename R, int RB>
+struct WarpTile {
+    V4<R> pa[32];           // position (high part) and scatterer id
+    V4<R> pb[32];           // position low part (double-float only) and n_x
+    V2<R> pn[32];           // n_y, n_z
+    V4<R> dv[RB][3][32];    // densities (v0, v1), (v2, q0), (q1, q2) of the side, per RHS
+};
+
+template <typename R, bool DOUBLE_FLOAT, int RB>
+__global__ void __launch_bounds__(128) k_near_w(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                                const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                                const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
+                                                const R *nrm, const int32_t *dom, const int32_t *perm,
+                                                const cx<R> *dens, const DomainConsts *dc, const cx<R> *Bl2p,
+                                                const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int rng_beg[32], rng_cum[33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<R, RB> &T = reinterpret_cast<WarpTile<R, RB> *>(smem_raw)[warp];
+    const int64_t g = leaf_off + blockIdx.x;
+    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        for (int q = 0; q < nnb; ++q) {
+            const int b = nbr_idx[nb0 + q];
+            rng_beg[q] = nbeg[b];
+            rng_cum[q] = cum;
+            cum += nend[b] - nbeg[b];
+        }
+        rng_cum[nnb] = cum;
+    }
+    __syncthreads();  // the only block-wide barrier
+    const int item = blockIdx.y * (blockDim.x >> 5) + warp;
+    const int side = item & 1;
+    const int64_t rb0 = (int64_t)(item >> 1) * RB;
+    if (rb0 >= nr) return;
+    const int nrb = (int)min((int64_t)RB, nr - rb0);
+    const int nsrc = rng_cum[nnb];
+    const int t0 = nbeg[g], t1 = nend[g];
+    const R sgn = side == 0 ? (R)-1 : (R)1;  // domain 0 sees the scatterer normal reversed
+    for (int tb = t0; tb < t1; tb += 32) {
+        const int nt = min(32, t1 - tb);
+        const int a = tb + min(lane, nt - 1);  // idle lanes shadow the last target and never store
+        const R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2];
+        R alx = 0, aly = 0, alz = 0;
+        if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
+        const int adom = dom[a];
+        const R adom_r = (R)adom;
+        const cx<R> k = to<R>(dc[side == 0 ? 0 : adom].k);
+        cx<R> acc[RB][3];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[rr][c] = {0, 0};
+        for (int s0 = 0; s0 < nsrc; s0 += 32) {
+            __syncwarp();
+            {  // stage one source per lane
+                const int e = s0 + lane;
+                if (e < nsrc) {
+                    const int q = source_range(rng_cum, nnb, e);
+                    const int i = rng_beg[q] + (e - rng_cum[q]);
+                    T.pa[lane] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
+                    R lo[3] = {0, 0, 0};
+                    if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
+                    T.pb[lane] = V4<R>{lo[0], lo[1], lo[2], nrm[3 * i]};
+                    T.pn[lane] = V2<R>{nrm[3 * i + 1], nrm[3 * i + 2]};
+#pragma unroll
+                    for (int rr = 0; rr < RB; ++rr) {
+                        if (rr < nrb) {
+                            const cx<R> *dn = dens + ((side * nr + rb0 + rr) * N + i) * 6;
+#pragma unroll
+                            for (int c = 0; c < 3; ++c)
+                                T.dv[rr][c][lane] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) T.dv[rr][c][lane] = V4<R>{0, 0, 0, 0};
                         }
                     }
-                    const int64_t r = rb0 + rr;
-                    // far field (L2P) of both domains
-                    for (int sd = 0; sd < 2; ++sd) {
-                        int d = sd == 0 ? 0 : adom;
-                        const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r) * p2;
-                        const cx<R> *B = Bl2p + ((int64_t)sd * N + a) * p2;
-                        cx<R> *acc = sd == 0 ? s0v : s1v;
-                        for (int qq = 0; qq < p2; ++qq) {
-                            cx<R> bq = B[qq];
-                            cfma(acc[0], Dl[qq], bq);
-                            cfma(acc[1], Dl[p2 + qq], bq);
-                            cfma(acc[2], Dl[2 * p2 + qq], bq);
-                        }
-                    }
-                    // self block in double precision, store in user order
-                    const c64 *xa = x + (r * N + u) * 6;
-                    c64 *ya = y + (r * N + u) * 6;
-                    for (int row = 0; row < 6; ++row) {
-                        c64 sacc = row < 3 ? c64{(double)s0v[row].re, (double)s0v[row].im}
-                                           : c64{(double)s1v[row - 3].re, (double)s1v[row - 3].im};
-                        for (int c = 0; c < 6; ++c) cfma(sacc, M[row * 6 + c], xa[c]);
-                        ya[row] = sacc;
-                    }
+                }
+            }
+            __syncwarp();
+            const int ns = min(32, nsrc - s0);
+            for (int u = 0; u < ns; ++u) {
+                const V4<R> pa = T.pa[u], pb = T.pb[u];
+                const V2<R> pn = T.pn[u];
+                if (side == 1 && pa.w != adom_r) continue;  // a scatterer's sum runs over its own nodes
+                R rv3[3] = {pa.x - ax, pa.y - ay, pa.z - az};
+                if (DOUBLE_FLOAT) { rv3[0] += pb.x - alx; rv3[1] += pb.y - aly; rv3[2] += pb.z - alz; }
+                const R R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
+                const R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
+                const R Rr = R2 * inv;
+                const R nn[3] = {sgn * pb.w, sgn * pn.x, sgn * pn.y};
+                const R nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
+                cx<R> gs, cs;
+                pair_scalars<R>(inv, Rr, k, gs, cs);
+#pragma unroll
+                for (int rr = 0; rr < RB; ++rr) {
+                    const V4<R> a0 = T.dv[rr][0][u], a1 = T.dv[rr][1][u], a2 = T.dv[rr][2][u];
+                    const cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
+                    const cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                    pair_apply<R>(rv3, nn, nrv, gs, cs, v, qv, acc[rr]);
+                }
+            }
+        }
+        if (lane < nt) {
+            // far field (L2P) of this side's domain: the basis row of the target is read once
+            const int d = side == 0 ? 0 : adom;
+            const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * rb0) * p2;
+            const cx<R> *B = Bl2p + ((int64_t)side * N + a) * p2;
+            for (int q = 0; q < p2; ++q) {
+                const cx<R> b = B[q];
+#pragma unroll
+                for (int rr = 0; rr < RB; ++rr)
+                    if (rr < nrb)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) cfma(acc[rr][c], Dl[(3 * rr + c) * p2 + q], b);
+            }
+            // the side's rows of the self block in double precision, stored in user order
+            const int64_t u = perm[a];
+            const c64 *M = Mself + 36 * u + 18 * side;
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) {
+                if (rr >= nrb) break;
+                const c64 *xa = x + ((rb0 + rr) * N + u) * 6;
+                c64 *ya = y + ((rb0 + rr) * N + u) * 6 + 3 * side;
+                for (int c = 0; c < 3; ++c) {
+                    c64 sacc = {(double)acc[rr][c].re, (double)acc[rr][c].im};
+                    for (int cc = 0; cc < 6; ++cc) cfma(sacc, M[6 * c + cc], xa[cc]);
+                    ya[c] = sacc;
                 }
             }
         }
     }
 }
 
+// Packed rotation-form tables, in the order k_m2l_rot reads them.  A and B (per offset): the
+// degree blocks n = 0..p-1 one after the other, each (2n+1) x (2n+1) row-major with the row the
+// output order m' + n and the column the input order m + n.  Z (per domain, level and offset
+// length): the order blocks m = -(p-1)..p-1, each (p-|m|) x (p-|m|) row-major with the row the
+// output degree n' - |m| and the column the input degree n - |m|.  The dense tables are stored
+// input-major, T[c][r] at c * p2 + r.
+template <typename R>
+__global__ void k_pack_rot_ab(int p, int64_t noff, const cx<R> *A, cx<R> *Ap) {
+    const int p2 = p * p, nrot = rot_off(p);
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= noff * nrot) return;
+    const int64_t o = idx / nrot;
+    const int i = (int)(idx - o * nrot);
+    int n = 0;
+    while (rot_off(n + 1) <= i) ++n;
+    const int w = 2 * n + 1, loc = i - rot_off(n), row = loc / w, col = loc - row * w;
+    Ap[idx] = A[o * p2 * p2 + (int64_t)(n * n + col) * p2 + n * n + row];
+}
+template <typename R>
+__global__ void k_pack_rot_z(int p, int64_t nz, const cx<R> *Z, cx<R> *Zp) {
+    const int p2 = p * p, ncoax = p * (2 * p * p + 1) / 3;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nz * ncoax) return;
+    const int64_t t = idx / ncoax;
+    const int i = (int)(idx - t * ncoax);
+    int m = -(p - 1), base = 0;
+    while (base + (p - abs(m)) * (p - abs(m)) <= i) { base += (p - abs(m)) * (p - abs(m)); ++m; }
+    const int am = abs(m), w = p - am, loc = i - base, row = loc / w, col = loc - row * w;
+    const int np = am + row, n = am + col;  // output degree n', input degree n
+    Zp[idx] = Z[t * p2 * p2 + (int64_t)(n * n + n + m) * p2 + np * np + np + m];
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
+// replace the dense rotation-form tables (R_A, R_B per offset; R_Z per domain, level and length)
+// by their packed form
+void pack_rot_tables(fmbem *h, cudaStream_t s) {
+    const int p = h->p, p2 = h->p2;
+    const int64_t nrot = p * (2 * p - 1) * (2 * p + 1) / 3, ncoax = p * (2 * p * p + 1) / 3;
+    const int64_t nz = (int64_t)(h->J + 1) * (h->lmax + 1) * h->n_tlen;
+    (void)p2;
+    auto pack = [&](auto *&Ad, auto *&Bd, auto *&Zd) {
+        using T = std::remove_reference_t<decltype(*Ad)>;
+        T *Ap = (T *)dev_alloc(h, sizeof(T) * 316 * nrot), *Bp = (T *)dev_alloc(h, sizeof(T) * 316 * nrot);
+        T *Zp = (T *)dev_alloc(h, sizeof(T) * nz * ncoax);
+        k_pack_rot_ab<<<(unsigned)((316 * nrot + 255) / 256), 256, 0, s>>>(p, 316, Ad, Ap);
+        k_pack_rot_ab<<<(unsigned)((316 * nrot + 255) / 256), 256, 0, s>>>(p, 316, Bd, Bp);
+        k_pack_rot_z<<<(unsigned)((nz * ncoax + 255) / 256), 256, 0, s>>>(p, nz, Zd, Zp);
+        CKL("k_pack_rot");
+        CK(cudaStreamSynchronize(s));
+        dev_free(h, Ad);
+        dev_free(h, Bd);
+        dev_free(h, Zd);
+        Ad = Ap;
+        Bd = Bp;
+        Zd = Zp;
+    };
+    pack(h->R_A64, h->R_B64, h->R_Z64);
+    pack(h->R_A32, h->R_B32, h->R_Z32);
+}
+
 static void ensure_scratch(fmbem *h, int64_t nr) {
     const size_t cb = sizeof(c64);
     if (h->scratch_rhs < nr) {
@@ -880,8 +1101,13 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     CKL("k_prep");
     const LevelInfo &L = h->lev[lmax];
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
-    k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
-                                                                       h->dom, h->nrm, dens, Bp2m, C);
+    constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
+    if (nr >= 4)
+        k_p2m_rb<R, P2M_RB><<<dim3((unsigned)L.n, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+    else
+        k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg,
+                                                                           h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     CKL("k_p2m");
     if (timing) CK(cudaEventRecord(h->ev[1], s));
     const int ncc = (int)((3 * nr + CC - 1) / CC);
@@ -995,27 +1221,37 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
     const R *nn = f32 ? (const R *)h->nrm_f : (const R *)h->nrm;
-    // right-hand-side blocks: the pair scalars are shared by RB right-hand sides
-    constexpr int RBLK = sizeof(R) == 4 ? 8 : 2;
-    if (nr >= 4) {
-        auto kern = f32 ? (void (*)(int64_t, int64_t, int64_t, int, int64_t, const int32_t *, const int32_t *,
-                                    const int32_t *, const int32_t *, const R *, const R *, const R *, const int32_t *,
-                                    const int32_t *, const cx<R> *, const DomainConsts *, const cx<R> *, const cx<R> *,
-                                    const c64 *, const c64 *, c64 *))k_near_rb<R, true, RBLK>
-                        : k_near_rb<R, false, RBLK>;
+    // near field: in single precision the warp-independent kernel with blocks of RB right-hand
+    // sides (the pair scalars are shared by the block); for fewer than 4 right-hand sides, and in
+    // double precision, the block-cooperative kernels (more threads per leaf, FP64 pipe busier)
+    auto launch_w = [&](auto kern, int rb, size_t tile_bytes) {
+        const int64_t items = 2 * ((nr + rb - 1) / rb);
+        const int wpb = (int)std::min<int64_t>(4, items);
+        const size_t smw = tile_bytes * wpb;
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+        kern<<<dim3((unsigned)L.n, (unsigned)((items + wpb - 1) / wpb)), 32 * wpb, smw, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm,
+            dens, dc, Bl2p, D, h->Mself, x, y);
+    };
+    if constexpr (sizeof(R) == 4) {
+        if (nr >= 8) launch_w(k_near_w<R, true, 8>, 8, sizeof(WarpTile<R, 8>));
+        else if (nr >= 4) launch_w(k_near_w<R, true, 4>, 4, sizeof(WarpTile<R, 4>));
+        else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
+            k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+                                                          h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens,
+                                                          dc, Bl2p, D, h->Mself, x, y);
+    } else if (nr >= 4) {
+        constexpr int RBLK = 2;
         const size_t smn = sizeof(NearSmemRB<R, RBLK>);
-        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn));
-        kern<<<(unsigned)L.n, 128, smn, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx,
-                                             ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D, h->Mself, x, y);
-        CKL("k_near_rb");
-    } else if (f32)
-        k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
-                                                      h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D, h->Mself,
-                                                      x, y);
-    else
+        CK(cudaFuncSetAttribute(k_near_rb<R, false, RBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn));
+        k_near_rb<R, false, RBLK><<<dim3((unsigned)L.n, (unsigned)((nr + RBLK - 1) / RBLK)), 128, smn, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm,
+            dens, dc, Bl2p, D, h->Mself, x, y);
+    } else {
         k_near<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
                                                        h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D,
                                                        h->Mself, x, y);
+    }
     CKL("k_near");
     if (timing) CK(cudaEventRecord(h->ev[4], s));
 }

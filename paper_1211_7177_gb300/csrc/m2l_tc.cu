@@ -14,11 +14,12 @@
 // in global memory already in the same swizzled K-major layout, one 16 KiB block per K block, so
 // a plain bulk copy stages them.
 //
-// Roles (128 threads, one CTA per (target box, domain, column tile)): thread 0 is the producer
-// (waits for a free stage, arms the stage's mbarrier with the byte count, issues the A bulk copy
-// and the B tensor copy), thread 32 issues the MMAs (waits for a full stage, four K = 8 MMAs per
-// K block, commits to the stage's "empty" mbarrier, finally to the "done" mbarrier), and all four
-// warps read the accumulator with tcgen05.ld and write D.  Every mbarrier wait is bounded (2 s by
+// Roles (128 threads, one CTA per (target box, domain, tile of up to 512 columns held as one or
+// two accumulators of up to 256 TMEM columns)): thread 0 is the producer (waits for a free stage,
+// arms the stage's mbarrier with the byte count, issues the A bulk copy and one B tensor copy per
+// sub-tile), thread 32 issues the MMAs (waits for a full stage, four K = 8 MMAs per K block and
+// sub-tile, commits to the stage's "empty" mbarrier, finally to the "done" mbarrier), and all
+// four warps read the accumulators with tcgen05.ld and write D.  Every mbarrier wait is bounded (2 s by
 // %globaltimer); on time-out the kernel raises an error flag, stops issuing work, waits (bounded)
 // for its own copies and MMAs in flight, frees its tensor memory and returns.
 #include <cuda.h>  // CUtensorMap and its enums; the encoder itself is looked up at run time
@@ -129,8 +130,8 @@ struct TcLevel {
     int64_t nbox;
     int ncols;            // 3 * n_rhs
     int p2, kblocks;      // K blocks of 32 real-form elements: ceil(2 p^2 / 32)
-    int n, stages;        // columns per tile (multiple of 16), pipeline depth
-    uint32_t tmem_cols;   // power of two >= n
+    int n, nsub, stages;  // columns per sub-tile (multiple of 16, <= 256), sub-tiles per CTA, depth
+    uint32_t tmem_cols;   // power of two >= nsub * n
     int round_out;        // round D to TF32 (it feeds the next level's L2L product)
 };
 
@@ -147,10 +148,10 @@ __global__ void __launch_bounds__(128, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t g = P.off + blockIdx.x;
     const int d = blockIdx.y;
-    const int col0 = blockIdx.z * P.n;
-    const int nh = min(P.n, P.ncols - col0);
+    const int col0 = blockIdx.z * P.n * P.nsub;  // first column of this CTA's tile
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
-    const uint32_t stage_bytes = A_KB_BYTES + (uint32_t)P.n * 128u;
+    const uint32_t b_bytes = (uint32_t)P.n * 128u;                 // one sub-tile's K block of B
+    const uint32_t stage_bytes = A_KB_BYTES + (uint32_t)P.nsub * b_bytes;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.stages; ++s) {
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t sA = sbase + (uint32_t)s * stage_bytes, sB = sA + A_KB_BYTES;
             mbar_arrive_expect_tx(&full[s], stage_bytes);
             bulk_load(sA, Asrc + (int64_t)kb * (A_KB_BYTES / 4), A_KB_BYTES, &full[s]);
-            tma_load_2d(sB, tm, kb * KBLK, y, &full[s]);
+            for (int j = 0; j < P.nsub; ++j) tma_load_2d(sB + j * b_bytes, tm, kb * KBLK, y + j * P.n, &full[s]);
             ++issued;
             if (++s == P.stages) { s = 0; ++q; }
         }
@@ -218,10 +219,11 @@ __global__ void __launch_bounds__(128, 1)
             if (!mbar_wait(&full[s], (uint32_t)q & 1u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sA = sbase + (uint32_t)s * stage_bytes, sB = sA + A_KB_BYTES;
+            for (int t = 0; t < P.nsub; ++t)  // one accumulator of n TMEM columns per sub-tile
 #pragma unroll
-            for (int j = 0; j < KBLK / 8; ++j)  // K = 8 TF32 per MMA = 32 bytes along the swizzled row
-                mma_tf32(tmem, smem_desc_sw128(sA + 32u * j), smem_desc_sw128(sB + 32u * j), idesc,
-                         (u > 0 || j > 0) ? 1u : 0u);
+                for (int j = 0; j < KBLK / 8; ++j)  // K = 8 TF32 per MMA = 32 bytes along the swizzled row
+                    mma_tf32(tmem + (uint32_t)(t * P.n), smem_desc_sw128(sA + 32u * j),
+                             smem_desc_sw128(sB + t * b_bytes + 32u * j), idesc, (u > 0 || j > 0) ? 1u : 0u);
             mma_commit(&empty[s]);
             if (++s == P.stages) { s = 0; ++q; }
         }
@@ -238,14 +240,16 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
+    const int nh = min(P.n * P.nsub, P.ncols - col0);  // valid columns of this CTA's tile
     float *Dout = D + (((int64_t)d * P.nbox + g) * P.ncols + col0) * 2 * P.p2;
     if (nprod == 0) {  // no translation reaches this box: its local expansion is zero
         for (int i = threadIdx.x; i < nh * 2 * P.p2; i += blockDim.x) Dout[i] = 0.f;
     } else if (s_fin) {
-        // warp w owns accumulator lanes 32w..32w+31 = real-form rows R = 2r + a
+        // warp w owns accumulator lanes 32w..32w+31 = real-form rows R = 2r + a; sub-tile t sits
+        // in TMEM columns t n .. t n + n - 1, so tile column c is TMEM column c
         const int R = warp * 32 + lane;
         const bool row_ok = R < 2 * P.p2;
-        for (int c0 = 0; c0 < P.n; c0 += 16) {
+        for (int c0 = 0; c0 < P.n * P.nsub; c0 += 16) {
             uint32_t v[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile(
@@ -357,11 +361,15 @@ void build_tc_tables(fmbem *h, cudaStream_t s) {
     CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
 }
 
-// columns per tile: the fewest tiles of at most 256 columns, split evenly, rounded up to 16
-void tc_tile_shape(int64_t ncols, int *n, int *ntile) {
-    const int64_t t = (ncols + 255) / 256;
+// tile shape: a CTA covers up to 512 columns (the whole tensor memory) as one or two sub-tiles of
+// at most 256 columns (one MMA's N), so each A image is loaded once per product for up to 170
+// right-hand sides; sub-tiles split the columns evenly, rounded up to 16
+void tc_tile_shape(int64_t ncols, int *n, int *nsub, int *ntile) {
+    const int64_t t = (ncols + 511) / 512;
+    const int64_t per = (ncols + t - 1) / t;
     *ntile = (int)t;
-    *n = (int)(((ncols + t - 1) / t + 15) / 16 * 16);
+    *nsub = per > 256 ? 2 : 1;
+    *n = (int)(((per + *nsub - 1) / *nsub + 15) / 16 * 16);
 }
 
 // downward pass for all levels: the multipole expansions C are rounded to TF32 in place first
@@ -371,19 +379,19 @@ void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s) {
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
     k_round_tf32<<<152 * 8, 256, 0, s>>>(C, nfloat);
     CKL("k_round_tf32");
-    int n, ntile;
-    tc_tile_shape(ncols, &n, &ntile);
-    const int stage = A_KB_BYTES + n * 128;
+    int n, nsub, ntile;
+    tc_tile_shape(ncols, &n, &nsub, &ntile);
+    const int stage = A_KB_BYTES + nsub * n * 128;
     const int stages = std::min(MAX_STAGES, SMEM_BUDGET / stage);
     const size_t smem = (size_t)stages * stage + 1024;  // + slack to align the stages to 1024 bytes
     uint32_t tcols = 32;
-    while ((int)tcols < n) tcols <<= 1;
+    while ((int)tcols < nsub * n) tcols <<= 1;
     CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t rows = (int64_t)(h->J + 1) * h->nbox * ncols;
     const CUtensorMap tmC = make_column_map(C, rows, h->p2, n), tmD = make_column_map(D, rows, h->p2, n);
     for (int l = 2; l <= h->lmax; ++l) {
         const LevelInfo &Lv = h->lev[l];
-        const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), n, stages, tcols,
+        const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), n, nsub, stages, tcols,
                         l < h->lmax ? 1 : 0};
         k_m2l_tc<<<dim3((unsigned)Lv.n, h->J + 1, (unsigned)ntile), 128, smem, s>>>(
             tmC, tmD, P, h->box_parent, h->box_key, h->ff_start, h->ff_src, h->ff_off, h->Atc, h->Lltc, D, h->tc_err);

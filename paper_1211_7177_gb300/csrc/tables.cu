@@ -421,6 +421,7 @@ void build_tables(fmbem *h, cudaStream_t s) {
                 }
                 run_batch(true, false, h->k[d], w, tv, dz, h->R_Z64, h->R_Z32);
             }
+        pack_rot_tables(h, s);
     }
     dev_free(h, F);
     dev_free(h, Yc);
