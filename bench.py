@@ -46,10 +46,12 @@ WORKLOADS = {
 }
 METRIC = "FMM-BEM matvec points*RHS/s"
 UNIT = "points*RHS/s"
-# flops per (near pair, domain): geometry and kernel scalars, and per right-hand side, counted
-# from the near-field kernel's source (FMA = 2)
-NEAR_PAIR = 21
-NEAR_RHS = 103
+# flops per (near pair, domain): geometry (double-float difference, |r|, n.r, w = n x r) and the
+# kernel scalars g, c; and per (near pair, domain, right-hand side): u = w x v + (n.r) v and two
+# complex FMAs per row -- counted from the near-field kernels' source (FADD/FMUL = 1, FFMA = 2,
+# each transcendental = 1)
+NEAR_PAIR = 52
+NEAR_RHS = 78
 PEAK_TFLOPS = {"fp64": 1.2, "fp32": 74.6}  # measured FMA throughput on GB300 (self-written probe)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor-core rate
 
@@ -219,16 +221,18 @@ def tensor_path(nr):
 
 
 def launches_per_matvec(lmax, nr, n_dom, precision):
-    """Kernels per matvec: k_prep, k_p2m, k_m2m per level 3..l_max, the downward pass per level
-    2..l_max (tensor path: one k_m2l_tc; chunked: k_m2l_chunks or k_m2l_rot plus k_l2l_reduce per
-    domain; many columns: k_m2l_multi), k_near."""
+    """Kernels per matvec: k_prep, P2M, k_m2m per level 3..l_max, the downward pass per level
+    2..l_max (tensor path: k_round_tf32 then one k_m2l_tc per level; chunked: k_m2l_chunks or
+    k_m2l_rot plus k_l2l_reduce per domain; many columns: k_m2l_multi), and the near field
+    (single precision with at least 4 right-hand sides: k_near_w and k_l2p_self; else one kernel)."""
     if precision == "tf32" and tensor_path(nr):
-        down = lmax - 1
+        down = 1 + (lmax - 1)
     elif 3 * nr <= 24:
         down = (lmax - 1) * 2 * n_dom
     else:
         down = lmax - 1
-    return 3 + (lmax - 2) + down
+    near = 2 if precision != "fp64" and nr >= 4 else 1
+    return 2 + (lmax - 2) + down + near
 
 
 def run_ours(args):

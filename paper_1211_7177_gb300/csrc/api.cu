@@ -137,6 +137,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         build_geometry(h, mesh, s);
         build_tree(h, s);
         build_tables(h, s);
+        near_work_items(h, s);
         std::vector<c64> dc(3 * (h->J + 1));
         for (int d = 0; d <= h->J; ++d) {
             dc[3 * d] = h->k[d];

@@ -119,6 +119,8 @@ struct fmbem {
     int32_t *ff_start = nullptr, *ff_src = nullptr;       // CSR of FF lists over global boxes
     int16_t *ff_off = nullptr;                            // offset code 0..315 per FF entry
     int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;
+    int4 *near_items = nullptr;  // warp work items of the near field (leaf, target offset, tg, nsl)
+    int n_near_items = 0;
     int32_t max_leaf = 0;                                 // largest leaf occupancy
     std::vector<int64_t> h_ff_count_level;
     // FF pairs of each level regrouped by translation offset, for the chunked M2L kernel:
@@ -238,6 +240,7 @@ bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
+void near_work_items(fmbem *h, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);

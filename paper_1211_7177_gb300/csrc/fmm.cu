@@ -136,6 +136,102 @@ __global__ void k_p2m_rb(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_
     }
 }
 
+// P2M for many right-hand sides as a register-tiled product.  For one leaf and domain,
+//   C[col][q] = sum over (node i, k = 0..3) of B_k(i, q) W_k(i, col),
+// with B_0 = R_n^{-m} (monopole) and B_{1..3} = grad R (the P2M basis rows) and, for column col =
+// 3 r + c (right-hand side r, component c), W_0 = q_c and W_k = v_c n_k + (n.v) delta_ck - n_c v_k
+// (so that sum_k W_k B_k = m_c . grad R + q_c R, Eqs. 2.18-2.19).  Nodes are taken P2M_KC at a time:
+// the block stages their basis rows and weights in shared memory, and each thread accumulates a
+// 4 x 4 tile of (coefficient, column) outputs.  Grid (leaf, domain, tile of P2M_MT columns).
+constexpr int P2M_KC = 8;   // nodes per shared-memory chunk
+constexpr int P2M_MT = 48;  // columns per block (16 right-hand sides)
+template <typename R>
+__global__ void k_p2m_gemm(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+                           const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens,
+                           const cx<R> *Bp2m, cx<R> *C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *Bs = reinterpret_cast<cx<R> *>(smem_raw);  // [4 P2M_KC][p2]
+    cx<R> *Ws = Bs + 4 * P2M_KC * p2;                   // [4 P2M_KC][P2M_MT]
+    const int64_t g = leaf_off + blockIdx.x;
+    const int d = blockIdx.y;
+    const int ncols = (int)(3 * nr), col0 = blockIdx.z * P2M_MT;
+    const int nh = min(P2M_MT, ncols - col0);
+    const int side = d == 0 ? 0 : 1;
+    const R sg = d == 0 ? (R)-1 : (R)1;
+    const int i0 = nbeg[g], i1 = nend[g];
+    const int nrg = (p2 + 3) / 4;
+    const int rg = threadIdx.x % nrg, cgp = threadIdx.x / nrg;  // 4 coefficients x 4 columns
+    const int r0 = 4 * rg, c0 = 4 * cgp;
+    const bool owner = cgp < P2M_MT / 4;
+    cx<R> acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = {0, 0};
+    for (int ib = i0; ib < i1; ib += P2M_KC) {
+        const int nk = min(P2M_KC, i1 - ib);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 4 * P2M_KC * p2; e += blockDim.x) {
+            const int kk = e / p2, q = e - kk * p2, il = kk >> 2;
+            const int i = ib + il;
+            cx<R> v = {0, 0};
+            if (il < nk && (d == 0 || dom[i] == d)) v = Bp2m[((int64_t)side * N + i) * 4 * p2 + (int64_t)(kk & 3) * p2 + q];
+            Bs[e] = v;
+        }
+        for (int e = threadIdx.x; e < P2M_KC * (P2M_MT / 3); e += blockDim.x) {
+            const int il = e / (P2M_MT / 3), rl = e - il * (P2M_MT / 3);
+            const int i = ib + il, col = 3 * rl;
+            cx<R> w[4][3];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) w[k][c] = {0, 0};
+            if (il < nk && col < nh && (d == 0 || dom[i] == d)) {
+                const int64_t r = (col0 + col) / 3;
+                const cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
+                const cx<R> v[3] = {dn[0], dn[1], dn[2]};
+                const R n[3] = {sg * (R)nrm[3 * i], sg * (R)nrm[3 * i + 1], sg * (R)nrm[3 * i + 2]};
+                const cx<R> nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    w[0][c] = dn[3 + c];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        cx<R> t = n[k] * v[c] - n[c] * v[k];
+                        if (k == c) t += nv;
+                        w[1 + k][c] = t;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Ws[(4 * il + k) * P2M_MT + col + c] = w[k][c];
+        }
+        __syncthreads();
+        if (owner) {
+            for (int kk = 0; kk < 4 * nk; ++kk) {
+                cx<R> bq[4], wc[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) bq[a] = (r0 + a < p2) ? Bs[kk * p2 + r0 + a] : cx<R>{0, 0};
+#pragma unroll
+                for (int b = 0; b < 4; ++b) wc[b] = Ws[kk * P2M_MT + c0 + b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) cfma(acc[a][b], bq[a], wc[b]);
+            }
+        }
+    }
+    if (owner)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (c0 + b < nh)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    if (r0 + a < p2) C[(((int64_t)d * nbox + g) * ncols + col0 + c0 + b) * p2 + r0 + a] = acc[a][b];
+}
+
 // ---------------------------------------------------------------- translation apply helper
 // acc[cc] += sum_c T[c][r] X[cc][c] for the thread's output row r; X in shared memory
 template <typename R, int CC>
@@ -525,8 +621,22 @@ __device__ __forceinline__ double exp_(double x) { return exp(x); }
 __device__ __forceinline__ void sincos_(float x, float *s, float *c) { __sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
 
-// one (source, target) pair of one domain: acc_i += -(K v)_i + g q_i  (Eq. 2.12 for beta != alpha)
-// r = s_beta - s_alpha, inv = 1/|r| (0 for the node itself, which then contributes nothing)
+// One (source, target) pair of one domain: acc_i += -(K v)_i + g q_i (Eq. 2.12 for beta != alpha),
+// r = s_beta - s_alpha, inv = 1/|r| (0 for the node itself, which then contributes nothing).  With
+// grad'g = c r, the bracket applied to v is -c [n (r.v) - (n.r) v - r (n.v)], which by
+// a x (b x c) = b (a.c) - c (a.b) equals c [(n x r) x v + (n.r) v]; w = n x r is formed once per
+// pair, so each right-hand side costs one real-vector cross product and two complex FMAs per row.
+template <typename R>
+__device__ __forceinline__ void cross_apply(const R *w, R nr, cx<R> g, cx<R> c, const cx<R> *v, const cx<R> *q,
+                                            cx<R> *acc) {
+    const cx<R> u[3] = {w[1] * v[2] - w[2] * v[1] + nr * v[0], w[2] * v[0] - w[0] * v[2] + nr * v[1],
+                        w[0] * v[1] - w[1] * v[0] + nr * v[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cfma(acc[i], c, u[i]);
+        cfma(acc[i], g, q[i]);
+    }
+}
 template <typename R>
 __device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R> k, R nx, R ny, R nz, const cx<R> *v,
                                             const cx<R> *q, cx<R> *acc) {
@@ -538,17 +648,9 @@ __device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R inv, R Rr, cx<R>
     cx<R> g = {f * cs, f * sn};
     // (i k - 1/R)/R with i k = -Im k + i Re k
     cx<R> c = g * cx<R>{(-k.im - inv) * inv, k.re * inv};
-    cx<R> rv = rx * v[0] + ry * v[1] + rz * v[2];
-    cx<R> nv = nx * v[0] + ny * v[1] + nz * v[2];
-    R nr = nx * rx + ny * ry + nz * rz;
-    R rr[3] = {rx, ry, rz}, nn[3] = {nx, ny, nz};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        // -(K v)_i = -c [n_i (r.v) - (n.r) v_i - r_i (n.v)]
-        cx<R> kv = nn[i] * rv - nr * v[i] - rr[i] * nv;
-        acc[i] -= c * kv;
-        cfma(acc[i], g, q[i]);
-    }
+    const R w[3] = {ny * rz - nz * ry, nz * rx - nx * rz, nx * ry - ny * rx};
+    const R nr = nx * rx + ny * ry + nz * rz;
+    cross_apply<R>(w, nr, g, c, v, q, acc);
 }
 
 // Epilogue of one result row of one target node a (row = 3 * side + component): the sum of the
@@ -700,20 +802,6 @@ __device__ __forceinline__ void pair_scalars(R inv, R Rr, cx<R> k, cx<R> &g, cx<
     g = {f * cs, f * sn};
     c = g * cx<R>{(-k.im - inv) * inv, k.re * inv};
 }
-// acc_i += -(K v)_i + g q_i with -(K v)_i = -c [n_i (r.v) - (n.r) v_i - r_i (n.v)]
-template <typename R>
-__device__ __forceinline__ void pair_apply(const R *rr, const R *nn, R nr, cx<R> g, cx<R> c, const cx<R> *v,
-                                           const cx<R> *q, cx<R> *acc) {
-    cx<R> rv = rr[0] * v[0] + rr[1] * v[1] + rr[2] * v[2];
-    cx<R> nv = nn[0] * v[0] + nn[1] * v[1] + nn[2] * v[2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        cx<R> kv = nn[i] * rv - nr * v[i] - rr[i] * nv;
-        acc[i] -= c * kv;
-        cfma(acc[i], g, q[i]);
-    }
-}
-
 constexpr int NB_TILE = 64;  // sources per shared-memory tile in the blocked kernel
 template <typename R, int RB>
 struct SrcTileRB {
@@ -809,9 +897,12 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
                         R R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
                         R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
                         R Rr = R2 * inv;
-                        R n1[3] = {pb.w, pn.x, pn.y};
-                        R n0[3] = {-pb.w, -pn.x, -pn.y};
-                        R nr1 = n1[0] * rv3[0] + n1[1] * rv3[1] + n1[2] * rv3[2];
+                        const R n1[3] = {pb.w, pn.x, pn.y};
+                        const R nr1 = n1[0] * rv3[0] + n1[1] * rv3[1] + n1[2] * rv3[2];
+                        // w = n x r for the scatterer normal; domain 0 (normal reversed) uses -w, -n.r
+                        const R w1[3] = {n1[1] * rv3[2] - n1[2] * rv3[1], n1[2] * rv3[0] - n1[0] * rv3[2],
+                                         n1[0] * rv3[1] - n1[1] * rv3[0]};
+                        const R w0[3] = {-w1[0], -w1[1], -w1[2]};
                         cx<R> gs, cs;
                         pair_scalars<R>(inv, Rr, kb, gs, cs);
 #pragma unroll
@@ -819,7 +910,7 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
                             const V4<R> a0 = T.dv[0][rr][0][u], a1 = T.dv[0][rr][1][u], a2 = T.dv[0][rr][2][u];
                             cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
                             cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
-                            pair_apply<R>(rv3, n0, -nr1, gs, cs, v, qv, acc0[rr]);
+                            cross_apply<R>(w0, -nr1, gs, cs, v, qv, acc0[rr]);
                         }
                         if (pa.w == adom_r) {
                             pair_scalars<R>(inv, Rr, kj, gs, cs);
@@ -828,7 +919,7 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
                                 const V4<R> a0 = T.dv[1][rr][0][u], a1 = T.dv[1][rr][1][u], a2 = T.dv[1][rr][2][u];
                                 cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
                                 cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
-                                pair_apply<R>(rv3, n1, nr1, gs, cs, v, qv, acc1[rr]);
+                                cross_apply<R>(w1, nr1, gs, cs, v, qv, acc1[rr]);
                             }
                         }
                     }
@@ -853,13 +944,15 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
 }
 
 // ---------------------------------------------------------------- warp-independent near field
-// One warp owns one work item: up to 32 target nodes of one leaf (a lane per target), one side
-// (domain 0, or the target's own scatterer) and one block of RB right-hand sides.  It streams the
-// sources of the leaf's Neighbor list through a warp-private shared-memory tile of 32 (each lane
-// stages one source: geometry and the RB densities of its side), synchronising only the warp, so
-// warps never wait for one another.  Per (source, target) pair it evaluates the kernel scalars
-// once and applies them to the RB right-hand sides; then each lane adds the far field (L2P) of
-// its side and the side's three rows of the self block (double precision) and stores them.
+// One warp owns one work item: a group of tg target nodes of one leaf, split over nsl source
+// slices (tg * nsl <= 32 lanes, nsl a power of two; lane = target + tg * slice), for one side
+// (domain 0, or the target's own scatterer) and one block of RB right-hand sides.  The items are
+// built once per tree (near_work_items) so that leaves of every size keep most lanes busy.  The
+// warp streams the sources of the leaf's Neighbor list through a warp-private shared-memory tile
+// of 32 (each lane stages one source: geometry and the RB densities of its side) and synchronises
+// only itself.  Per (source, target) pair it evaluates the kernel scalars once and applies them to
+// the RB right-hand sides; the slices are then summed by a fixed shuffle tree, and the slice-0 lane
+// of each target stores the side's three near-field rows (k_l2p_self adds the rest).
 template <typename R, int RB>
 struct WarpTile {
     V4<R> pa[32];           // position (high part) and scatterer id
@@ -867,128 +960,217 @@ struct WarpTile {
     V2<R> pn[32];           // n_y, n_z
     V4<R> dv[RB][3][32];    // densities (v0, v1), (v2, q0), (q1, q2) of the side, per RHS
 };
+constexpr int NW_WARPS = 4;  // warps (independent work items) per block
 
 template <typename R, bool DOUBLE_FLOAT, int RB>
-__global__ void __launch_bounds__(128) k_near_w(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
-                                                const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
-                                                const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
-                                                const R *nrm, const int32_t *dom, const int32_t *perm,
-                                                const cx<R> *dens, const DomainConsts *dc, const cx<R> *Bl2p,
-                                                const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
+__global__ void __launch_bounds__(32 * NW_WARPS) k_near_w(
+    int64_t leaf_off, const int4 *__restrict__ items, int n_items, int64_t N, int64_t nr, int p2, int64_t nbox,
+    const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx, const R *pos_hi,
+    const R *pos_lo, const R *nrm, const int32_t *dom, const int32_t *perm, const cx<R> *dens, const DomainConsts *dc,
+    const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int rng_beg[32], rng_cum[33];
+    __shared__ int rng_beg[NW_WARPS][32], rng_cum[NW_WARPS][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item_id = blockIdx.x * NW_WARPS + warp;
+    if (item_id >= n_items) return;  // no block-wide barrier below
     WarpTile<R, RB> &T = reinterpret_cast<WarpTile<R, RB> *>(smem_raw)[warp];
-    const int64_t g = leaf_off + blockIdx.x;
-    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
-    if (threadIdx.x == 0) {
+    int *rb_ = rng_beg[warp], *rc_ = rng_cum[warp];
+    const int4 it = items[item_id];
+    const int leaf = it.x, tg = it.z, nsl = it.w;
+    const int64_t g = leaf_off + leaf;
+    const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
+    if (lane == 0) {
         int cum = 0;
         for (int q = 0; q < nnb; ++q) {
             const int b = nbr_idx[nb0 + q];
-            rng_beg[q] = nbeg[b];
-            rng_cum[q] = cum;
+            rb_[q] = nbeg[b];
+            rc_[q] = cum;
             cum += nend[b] - nbeg[b];
         }
-        rng_cum[nnb] = cum;
+        rc_[nnb] = cum;
     }
-    __syncthreads();  // the only block-wide barrier
-    const int item = blockIdx.y * (blockDim.x >> 5) + warp;
-    const int side = item & 1;
-    const int64_t rb0 = (int64_t)(item >> 1) * RB;
-    if (rb0 >= nr) return;
+    __syncwarp();
+    const int side = blockIdx.y & 1;
+    const int64_t rb0 = (int64_t)(blockIdx.y >> 1) * RB;
     const int nrb = (int)min((int64_t)RB, nr - rb0);
-    const int nsrc = rng_cum[nnb];
-    const int t0 = nbeg[g], t1 = nend[g];
+    const int nsrc = rc_[nnb];
+    const int ti = lane % tg, sl = lane / tg;
+    const bool busy = sl < nsl;
+    const int a = nbeg[g] + it.y + ti;  // lanes past tg * nsl shadow a valid target and never store
     const R sgn = side == 0 ? (R)-1 : (R)1;  // domain 0 sees the scatterer normal reversed
-    for (int tb = t0; tb < t1; tb += 32) {
-        const int nt = min(32, t1 - tb);
-        const int a = tb + min(lane, nt - 1);  // idle lanes shadow the last target and never store
-        const R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2];
-        R alx = 0, aly = 0, alz = 0;
-        if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
-        const int adom = dom[a];
-        const R adom_r = (R)adom;
-        const cx<R> k = to<R>(dc[side == 0 ? 0 : adom].k);
-        cx<R> acc[RB][3];
+    const R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2];
+    R alx = 0, aly = 0, alz = 0;
+    if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
+    const int adom = dom[a];
+    const R adom_r = (R)adom;
+    const cx<R> k = to<R>(dc[side == 0 ? 0 : adom].k);
+    cx<R> acc[RB][3];
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr)
+    for (int rr = 0; rr < RB; ++rr)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[rr][c] = {0, 0};
-        for (int s0 = 0; s0 < nsrc; s0 += 32) {
-            __syncwarp();
-            {  // stage one source per lane
-                const int e = s0 + lane;
-                if (e < nsrc) {
-                    const int q = source_range(rng_cum, nnb, e);
-                    const int i = rng_beg[q] + (e - rng_cum[q]);
-                    T.pa[lane] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
-                    R lo[3] = {0, 0, 0};
-                    if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
-                    T.pb[lane] = V4<R>{lo[0], lo[1], lo[2], nrm[3 * i]};
-                    T.pn[lane] = V2<R>{nrm[3 * i + 1], nrm[3 * i + 2]};
+        for (int c = 0; c < 3; ++c) acc[rr][c] = {0, 0};
+    for (int s0 = 0; s0 < nsrc; s0 += 32) {
+        __syncwarp();
+        {  // stage one source per lane
+            const int e = s0 + lane;
+            if (e < nsrc) {
+                const int q = source_range(rc_, nnb, e);
+                const int i = rb_[q] + (e - rc_[q]);
+                T.pa[lane] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
+                R lo[3] = {0, 0, 0};
+                if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
+                T.pb[lane] = V4<R>{lo[0], lo[1], lo[2], nrm[3 * i]};
+                T.pn[lane] = V2<R>{nrm[3 * i + 1], nrm[3 * i + 2]};
 #pragma unroll
-                    for (int rr = 0; rr < RB; ++rr) {
-                        if (rr < nrb) {
-                            const cx<R> *dn = dens + ((side * nr + rb0 + rr) * N + i) * 6;
+                for (int rr = 0; rr < RB; ++rr) {
+                    if (rr < nrb) {
+                        const cx<R> *dn = dens + ((side * nr + rb0 + rr) * N + i) * 6;
 #pragma unroll
-                            for (int c = 0; c < 3; ++c)
-                                T.dv[rr][c][lane] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
-                        } else {
+                        for (int c = 0; c < 3; ++c)
+                            T.dv[rr][c][lane] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
+                    } else {
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) T.dv[rr][c][lane] = V4<R>{0, 0, 0, 0};
-                        }
+                        for (int c = 0; c < 3; ++c) T.dv[rr][c][lane] = V4<R>{0, 0, 0, 0};
                     }
                 }
             }
-            __syncwarp();
-            const int ns = min(32, nsrc - s0);
-            for (int u = 0; u < ns; ++u) {
-                const V4<R> pa = T.pa[u], pb = T.pb[u];
-                const V2<R> pn = T.pn[u];
-                if (side == 1 && pa.w != adom_r) continue;  // a scatterer's sum runs over its own nodes
-                R rv3[3] = {pa.x - ax, pa.y - ay, pa.z - az};
-                if (DOUBLE_FLOAT) { rv3[0] += pb.x - alx; rv3[1] += pb.y - aly; rv3[2] += pb.z - alz; }
-                const R R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
-                const R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
-                const R Rr = R2 * inv;
-                const R nn[3] = {sgn * pb.w, sgn * pn.x, sgn * pn.y};
-                const R nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
-                cx<R> gs, cs;
-                pair_scalars<R>(inv, Rr, k, gs, cs);
-#pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    const V4<R> a0 = T.dv[rr][0][u], a1 = T.dv[rr][1][u], a2 = T.dv[rr][2][u];
-                    const cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
-                    const cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
-                    pair_apply<R>(rv3, nn, nrv, gs, cs, v, qv, acc[rr]);
-                }
-            }
         }
-        if (lane < nt) {
-            // far field (L2P) of this side's domain: the basis row of the target is read once
-            const int d = side == 0 ? 0 : adom;
-            const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * rb0) * p2;
-            const cx<R> *B = Bl2p + ((int64_t)side * N + a) * p2;
-            for (int q = 0; q < p2; ++q) {
-                const cx<R> b = B[q];
-#pragma unroll
-                for (int rr = 0; rr < RB; ++rr)
-                    if (rr < nrb)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) cfma(acc[rr][c], Dl[(3 * rr + c) * p2 + q], b);
-            }
-            // the side's rows of the self block in double precision, stored in user order
-            const int64_t u = perm[a];
-            const c64 *M = Mself + 36 * u + 18 * side;
+        __syncwarp();
+        const int ns = busy ? min(32, nsrc - s0) : 0;
+        for (int u = sl; u < ns; u += nsl) {
+            const V4<R> pa = T.pa[u], pb = T.pb[u];
+            const V2<R> pn = T.pn[u];
+            if (side == 1 && pa.w != adom_r) continue;  // a scatterer's sum runs over its own nodes
+            R rv3[3] = {pa.x - ax, pa.y - ay, pa.z - az};
+            if (DOUBLE_FLOAT) { rv3[0] += pb.x - alx; rv3[1] += pb.y - aly; rv3[2] += pb.z - alz; }
+            const R R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
+            const R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
+            const R Rr = R2 * inv;
+            const R nn[3] = {sgn * pb.w, sgn * pn.x, sgn * pn.y};
+            const R nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
+            const R w[3] = {nn[1] * rv3[2] - nn[2] * rv3[1], nn[2] * rv3[0] - nn[0] * rv3[2],
+                            nn[0] * rv3[1] - nn[1] * rv3[0]};
+            cx<R> gs, cs;
+            pair_scalars<R>(inv, Rr, k, gs, cs);
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) {
-                if (rr >= nrb) break;
-                const c64 *xa = x + ((rb0 + rr) * N + u) * 6;
-                c64 *ya = y + ((rb0 + rr) * N + u) * 6 + 3 * side;
-                for (int c = 0; c < 3; ++c) {
-                    c64 sacc = {(double)acc[rr][c].re, (double)acc[rr][c].im};
-                    for (int cc = 0; cc < 6; ++cc) cfma(sacc, M[6 * c + cc], xa[cc]);
-                    ya[c] = sacc;
+                const V4<R> a0 = T.dv[rr][0][u], a1 = T.dv[rr][1][u], a2 = T.dv[rr][2][u];
+                const cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
+                const cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                cross_apply<R>(w, nrv, gs, cs, v, qv, acc[rr]);
+            }
+        }
+    }
+    // sum the slices of each target: lane ti + tg * sl, fixed tree over sl
+    for (int off = nsl >> 1; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R re = __shfl_down_sync(0xffffffffu, acc[rr][c].re, off * tg);
+                const R im = __shfl_down_sync(0xffffffffu, acc[rr][c].im, off * tg);
+                if (sl < off) { acc[rr][c].re += re; acc[rr][c].im += im; }
+            }
+    }
+    if (sl == 0) {  // the side's near-field rows; k_l2p_self adds the far field and the self block
+        const int64_t u = perm[a];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            if (rr >= nrb) break;
+            c64 *ya = y + ((rb0 + rr) * N + u) * 6 + 3 * side;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ya[c] = c64{(double)acc[rr][c].re, (double)acc[rr][c].im};
+        }
+    }
+}
+
+// Far field (L2P, Eq. 2.23 first term) and self block (App. B) for many right-hand sides, added to
+// the near-field rows k_near_w stored: for one leaf, one side and a tile of L2P_MT columns,
+//   y[col][a][3 side + c] += sum_q B_l2p[side][a][q] D[d][leaf][col][q]
+//                            + sum_{c' < 3} M[a][3 side + c][c'] x[a][c'] + M[a][3 side + c][3 + c] x[a][3 + c]
+// (the Psi columns of each self block row are diagonal).  The L2P part is a (targets x p^2) by
+// (p^2 x columns) product: each thread owns targets tgr + 16 i and columns cgp + 12 j (i, j < 4),
+// with the shared rows padded to p^2 + 1 so that the 16 target rows a warp reads fall in distinct
+// banks.  The self part runs in double precision.  On the scatterer side d is each target's own
+// scatterer, so the leaf's scatterers are taken in turn.
+constexpr int L2P_MT = 48;  // columns per block (16 right-hand sides)
+constexpr int L2P_NT = 64;  // targets per pass
+template <typename R>
+__global__ void __launch_bounds__(192) k_l2p_self(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, int J,
+                                                  const int32_t *nbeg, const int32_t *nend, const int32_t *dom,
+                                                  const int32_t *perm, const cx<R> *Bl2p, const cx<R> *D,
+                                                  const c64 *Mself, const c64 *x, c64 *y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = p2 + 1;                              // padded row length
+    cx<R> *Bs = reinterpret_cast<cx<R> *>(smem_raw);  // [L2P_NT][ld]
+    cx<R> *Ds = Bs + L2P_NT * ld;                       // [L2P_MT][ld]
+    __shared__ int present;
+    const int64_t g = leaf_off + blockIdx.x;
+    const int side = blockIdx.y;
+    const int ncols = (int)(3 * nr), col0 = blockIdx.z * L2P_MT;
+    const int nh = min(L2P_MT, ncols - col0);
+    const int t0 = nbeg[g], t1 = nend[g];
+    const int tgr = threadIdx.x % 16, cgp = threadIdx.x / 16;  // targets tgr + 16 i, columns cgp + 12 j
+    for (int tb = t0; tb < t1; tb += L2P_NT) {
+        const int nt = min(L2P_NT, t1 - tb);
+        for (int d = side == 0 ? 0 : 1; d <= (side == 0 ? 0 : J); ++d) {
+            __syncthreads();
+            if (threadIdx.x == 0) present = 0;
+            __syncthreads();
+            if (threadIdx.x < nt && (side == 0 || dom[tb + threadIdx.x] == d)) present = 1;
+            __syncthreads();
+            if (!present) continue;
+            for (int e = threadIdx.x; e < L2P_NT * p2; e += blockDim.x) {
+                const int t = e / p2, q = e - t * p2;
+                cx<R> v = {0, 0};
+                if (t < nt && (side == 0 || dom[tb + t] == d)) v = Bl2p[((int64_t)side * N + tb + t) * p2 + q];
+                Bs[t * ld + q] = v;
+            }
+            for (int e = threadIdx.x; e < L2P_MT * p2; e += blockDim.x) {
+                const int c = e / p2, q = e - c * p2;
+                Ds[c * ld + q] = c < nh ? D[(((int64_t)d * nbox + g) * ncols + col0 + c) * p2 + q] : cx<R>{0, 0};
+            }
+            __syncthreads();
+            cx<R> acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = {0, 0};
+#pragma unroll 4
+            for (int q = 0; q < p2; ++q) {
+                cx<R> bt[4], dc4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) bt[i] = Bs[(tgr + 16 * i) * ld + q];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dc4[j] = Ds[(cgp + 12 * j) * ld + q];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cfma(acc[i][j], bt[i], dc4[j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int t = tgr + 16 * i;
+                if (t >= nt) break;
+                const int a = tb + t;
+                if (side == 1 && dom[a] != d) continue;
+                const int64_t u = perm[a];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int col = cgp + 12 * j;
+                    if (col >= nh) break;
+                    const int64_t r = (col0 + col) / 3;
+                    const int c = (col0 + col) - 3 * (int)r, row = 3 * side + c;
+                    const c64 *M = Mself + 36 * u + 6 * row;
+                    const c64 *xa = x + (r * N + u) * 6;
+                    c64 *ya = y + (r * N + u) * 6 + row;
+                    c64 sacc = *ya;
+                    sacc += c64{(double)acc[i][j].re, (double)acc[i][j].im};
+                    cfma(sacc, M[0], xa[0]);
+                    cfma(sacc, M[1], xa[1]);
+                    cfma(sacc, M[2], xa[2]);
+                    cfma(sacc, M[3 + c], xa[3 + c]);
+                    *ya = sacc;
                 }
             }
         }
@@ -1057,6 +1239,38 @@ void pack_rot_tables(fmbem *h, cudaStream_t s) {
     pack(h->R_A32, h->R_B32, h->R_Z32);
 }
 
+// warp work items of the near field (see k_near_w): per leaf of nt targets, the layout of W
+// warps x (tg targets x nsl slices) with the least lane time W / nsl, tg = ceil(nt / W) <= 32,
+// nsl the largest power of two with tg * nsl <= 32, up to 8 warps per leaf
+void near_work_items(fmbem *h, cudaStream_t s) {
+    if (h->near_items) return;
+    const LevelInfo &L = h->lev[h->lmax];
+    std::vector<int32_t> nb(L.n), ne(L.n);
+    CK(cudaMemcpyAsync(nb.data(), h->box_nbeg + L.off, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ne.data(), h->box_nend + L.off, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int4> items;
+    for (int64_t leaf = 0; leaf < L.n; ++leaf) {
+        const int nt = ne[leaf] - nb[leaf];
+        if (nt <= 0) continue;
+        int bestW = (nt + 31) / 32, bestP = 1;
+        double best = bestW;
+        for (int W = 1; W <= std::max(8, (nt + 31) / 32); ++W) {
+            const int tg = (nt + W - 1) / W;
+            if (tg > 32) continue;
+            int p = 1;
+            while (2 * p * tg <= 32) p *= 2;
+            if ((double)W / p < best - 1e-12) { best = (double)W / p; bestW = W; bestP = p; }
+        }
+        const int tg = (nt + bestW - 1) / bestW;
+        for (int t = 0; t < nt; t += tg) items.push_back(int4{(int)leaf, t, std::min(tg, nt - t), bestP});
+    }
+    h->n_near_items = (int)items.size();
+    h->near_items = (int4 *)dev_alloc(h, sizeof(int4) * items.size());
+    CK(cudaMemcpyAsync(h->near_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+}
+
 static void ensure_scratch(fmbem *h, int64_t nr) {
     const size_t cb = sizeof(c64);
     if (h->scratch_rhs < nr) {
@@ -1102,7 +1316,13 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const LevelInfo &L = h->lev[lmax];
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
     constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
-    if (nr >= 4)
+    if (nr >= 16) {
+        const int nthr = ((p2 + 3) / 4) * (P2M_MT / 4);
+        const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + P2M_MT);
+        CK(cudaFuncSetAttribute(k_p2m_gemm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+        k_p2m_gemm<R><<<dim3((unsigned)L.n, J + 1, (unsigned)((3 * nr + P2M_MT - 1) / P2M_MT)), nthr, smp, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+    } else if (nr >= 4)
         k_p2m_rb<R, P2M_RB><<<dim3((unsigned)L.n, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
             L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     else
@@ -1225,13 +1445,19 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // sides (the pair scalars are shared by the block); for fewer than 4 right-hand sides, and in
     // double precision, the block-cooperative kernels (more threads per leaf, FP64 pipe busier)
     auto launch_w = [&](auto kern, int rb, size_t tile_bytes) {
-        const int64_t items = 2 * ((nr + rb - 1) / rb);
-        const int wpb = (int)std::min<int64_t>(4, items);
-        const size_t smw = tile_bytes * wpb;
+        if (h->near_items == nullptr) throw fmbem_error{FMBEM_ERR_CUDA, "near-field work items were not built"};
+        const size_t smw = tile_bytes * NW_WARPS;
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
-        kern<<<dim3((unsigned)L.n, (unsigned)((items + wpb - 1) / wpb)), 32 * wpb, smw, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm,
-            dens, dc, Bl2p, D, h->Mself, x, y);
+        kern<<<dim3((unsigned)((h->n_near_items + NW_WARPS - 1) / NW_WARPS), (unsigned)(2 * ((nr + rb - 1) / rb))),
+               32 * NW_WARPS, smw, s>>>(L.off, h->near_items, h->n_near_items, N, nr, p2, h->nbox, h->box_nbeg,
+                                        h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc,
+                                        Bl2p, D, h->Mself, x, y);
+        CKL("k_near_w");
+        const size_t sml = sizeof(cx<R>) * (size_t)(p2 + 1) * (L2P_NT + L2P_MT);
+        CK(cudaFuncSetAttribute(k_l2p_self<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml));
+        k_l2p_self<R><<<dim3((unsigned)L.n, 2, (unsigned)((3 * nr + L2P_MT - 1) / L2P_MT)), (L2P_NT / 4) * (L2P_MT / 4),
+                        sml, s>>>(L.off, N, nr, p2, h->nbox, J, h->box_nbeg, h->box_nend, h->dom, h->perm, Bl2p, D,
+                                  h->Mself, x, y);
     };
     if constexpr (sizeof(R) == 4) {
         if (nr >= 8) launch_w(k_near_w<R, true, 8>, 8, sizeof(WarpTile<R, 8>));
