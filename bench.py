@@ -181,11 +181,12 @@ class ClockSampler:
 def m2l_flops_per_column(p, nr):
     """Algorithmic real flops of one S|R translation of one column: dense p^2 x p^2 complex matrix
     (8 p^4), or, in the rotation form the library uses for p >= 9 with at most 8 right-hand sides,
-    two degree-block rotations and one order-block coaxial translation."""
+    an azimuthal phase, a real polar rotation per degree block (real x complex, 4 flops per
+    entry), the complex coaxial S|R per order block, the real polar rotation back and a phase."""
     if p >= 9 and 3 * nr <= 24:
         rot = p * (2 * p - 1) * (2 * p + 1) // 3
         coax = p * (2 * p * p + 1) // 3
-        return 8.0 * (2 * rot + coax), "rotation form (rotate, coaxial S|R, rotate back)"
+        return 4.0 * 2 * rot + 8.0 * coax + 6.0 * 2 * p * p, "rotation form (phase, real polar rotation, coaxial S|R, back)"
     return 8.0 * p ** 4, "dense S|R matrices"
 
 

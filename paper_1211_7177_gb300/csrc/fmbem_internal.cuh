@@ -146,10 +146,13 @@ struct fmbem {
     bool m2l_rotation = false;
     int n_tlen = 0;
     int8_t *rot_tidx = nullptr;  // [316] index of the offset's length among the distinct lengths
-    // rotation form of S|R (tables.cu builds them dense, pack_rot_tables in fmm.cu packs them):
-    // A, B [316][degree blocks], Z [J+1][lmax+1][n_tlen][order blocks]
-    c64 *R_A64 = nullptr, *R_B64 = nullptr, *R_Z64 = nullptr;
-    c32 *R_A32 = nullptr, *R_B32 = nullptr, *R_Z32 = nullptr;
+    // rotation form of S|R = (back rotation) (coaxial) (forward rotation), packed by fmm.cu:
+    // R_D [316][2][real degree blocks] (forward, back polar rotations), R_P [316][2][p2] (forward,
+    // back azimuthal phases), R_Z [J+1][lmax+1][n_tlen][order blocks] (coaxial S|R)
+    double *R_D64 = nullptr;
+    float *R_D32 = nullptr;
+    c64 *R_P64 = nullptr, *R_Z64 = nullptr;
+    c32 *R_P32 = nullptr, *R_Z32 = nullptr;
 
     // scratch grown on demand
     int64_t scratch_rhs = 0;
@@ -240,6 +243,7 @@ bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
+void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s);
 void near_work_items(fmbem *h, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s);

@@ -13,6 +13,7 @@
 // analytic self block A_self (Appendix B).
 #include <algorithm>
 
+#include <cstring>
 #include <type_traits>
 
 #include "fmbem_internal.cuh"
@@ -382,27 +383,28 @@ template <typename R, int MAXC>
 __global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox, int col0, int ncol,
                           int pc, int cg, const int32_t *chunk_beg, const int32_t *chunk_cnt, const int16_t *chunk_off,
                           const int32_t *pair_e, const int32_t *ff_src, const int8_t *tidx, int n_tlen,
-                          const cx<R> *RA, const cx<R> *RB, const cx<R> *RZ, const cx<R> *C, cx<R> *Y,
+                          const R *RD, const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y,
                           int64_t e_first) {
     const int p2 = p * p;
     const int nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<R> *Ab = reinterpret_cast<cx<R> *>(smem_raw);
-    cx<R> *Bb = Ab + nrot;
-    cx<R> *Zb = Bb + nrot;
+    R *Df = reinterpret_cast<R *>(smem_raw);  // forward polar rotation, real degree blocks
+    R *Db = Df + nrot;                         // back polar rotation
+    cx<R> *Pf = reinterpret_cast<cx<R> *>(Db + nrot);  // forward azimuthal phases [p2]
+    cx<R> *Pb = Pf + p2;                                // back azimuthal phases [p2]
+    cx<R> *Zb = Pb + p2;
     const int ncap = cg * MAXC;
     cx<R> *X = Zb + ncoax;       // [ncap][p2]
     cx<R> *U = X + ncap * p2;    // [ncap][p2]
     const int64_t ck = chunk0 + blockIdx.x;
     const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
     const int o = chunk_off[ck];
-    // packed tables (see pack_rot_tables): a straight copy of this offset's blocks
-    const cx<R> *A = RA + (int64_t)o * nrot, *B = RB + (int64_t)o * nrot;
+    // packed factors of this offset (pack_rot_factors) and the coaxial blocks of its length
+    const R *D2 = RD + (int64_t)o * 2 * nrot;
+    const cx<R> *P2 = RP + (int64_t)o * 2 * p2;
     const cx<R> *Z = RZ + (((int64_t)d * (lmax + 1) + l) * n_tlen + tidx[o]) * ncoax;
-    for (int i = threadIdx.x; i < nrot; i += blockDim.x) {
-        Ab[i] = A[i];
-        Bb[i] = B[i];
-    }
+    for (int i = threadIdx.x; i < 2 * nrot; i += blockDim.x) Df[i] = D2[i];
+    for (int i = threadIdx.x; i < 2 * p2; i += blockDim.x) Pf[i] = P2[i];
     for (int i = threadIdx.x; i < ncoax; i += blockDim.x) Zb[i] = Z[i];
     const int rows_pad = blockDim.x / cg;
     const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
@@ -420,24 +422,28 @@ __global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, in
         for (int i = threadIdx.x; i < ncap * p2; i += blockDim.x) {
             int j = i / p2, k = i - j * p2;
             cx<R> v = {0, 0};
-            if (j < nct) {
+            if (j < nct) {  // the azimuthal part of the forward rotation is diagonal: applied here
                 int pr = j / ncol, c = j - pr * ncol;
-                v = C[(((int64_t)d * nbox + ff_src[pair_e[beg + b0 + pr]]) * 3 * nr + col0 + c) * p2 + k];
+                v = C[(((int64_t)d * nbox + ff_src[pair_e[beg + b0 + pr]]) * 3 * nr + col0 + c) * p2 + k] * Pf[k];
             }
             X[i] = v;
         }
         __syncthreads();
         const int j0 = grp * MAXC, nj = min(MAXC, nct - j0);
         cx<R> acc[MAXC];
-        // stage 1: rotate into the translation frame, per degree
+        // stage 1: polar rotation into the translation frame, per degree (real blocks)
         if (r < p2 && nj > 0) {
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
-            const cx<R> *a = Ab + rot_off(rn) + (rm + rn) * (2 * rn + 1);
+            const R *a = Df + rot_off(rn) + (rm + rn) * (2 * rn + 1);
             for (int jj = 0; jj < 2 * rn + 1; ++jj) {
-                const cx<R> t = a[jj];
+                const R t = a[jj];
 #pragma unroll
-                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, X[(j0 + q) * p2 + rn * rn + jj]);
+                for (int q = 0; q < MAXC; ++q) {
+                    const cx<R> xv = X[(j0 + q) * p2 + rn * rn + jj];
+                    acc[q].re = fma(t, xv.re, acc[q].re);
+                    acc[q].im = fma(t, xv.im, acc[q].im);
+                }
             }
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) U[(j0 + q) * p2 + r] = acc[q];
@@ -458,22 +464,28 @@ __global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, in
             for (int q = 0; q < MAXC; ++q) X[(j0 + q) * p2 + r] = acc[q];
         }
         __syncthreads();
-        // stage 3: rotate back, per degree, and store at the pairs' CSR positions
+        // stage 3: polar rotation back, per degree (real blocks), then the azimuthal phase; store
+        // at the pairs' CSR positions
         if (r < p2 && nj > 0) {
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
-            const cx<R> *bb = Bb + rot_off(rn) + (rm + rn) * (2 * rn + 1);
+            const R *bb = Db + rot_off(rn) + (rm + rn) * (2 * rn + 1);
             for (int jj = 0; jj < 2 * rn + 1; ++jj) {
-                const cx<R> t = bb[jj];
+                const R t = bb[jj];
 #pragma unroll
-                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, X[(j0 + q) * p2 + rn * rn + jj]);
+                for (int q = 0; q < MAXC; ++q) {
+                    const cx<R> xv = X[(j0 + q) * p2 + rn * rn + jj];
+                    acc[q].re = fma(t, xv.re, acc[q].re);
+                    acc[q].im = fma(t, xv.im, acc[q].im);
+                }
             }
+            const cx<R> ph = Pb[r];
 #pragma unroll
             for (int q = 0; q < MAXC; ++q)
                 if (q < nj) {
                     int j = j0 + q, pr = j / ncol, c = j - pr * ncol;
                     int64_t e = pair_e[beg + b0 + pr];
-                    Y[((e - e_first) * ncol + c) * p2 + r] = acc[q];
+                    Y[((e - e_first) * ncol + c) * p2 + r] = acc[q] * ph;
                 }
         }
     }
@@ -1177,23 +1189,44 @@ __global__ void __launch_bounds__(192) k_l2p_self(int64_t leaf_off, int64_t N, i
     }
 }
 
-// Packed rotation-form tables, in the order k_m2l_rot reads them.  A and B (per offset): the
-// degree blocks n = 0..p-1 one after the other, each (2n+1) x (2n+1) row-major with the row the
-// output order m' + n and the column the input order m + n.  Z (per domain, level and offset
-// length): the order blocks m = -(p-1)..p-1, each (p-|m|) x (p-|m|) row-major with the row the
-// output degree n' - |m| and the column the input degree n - |m|.  The dense tables are stored
-// input-major, T[c][r] at c * p2 + r.
-template <typename R>
-__global__ void k_pack_rot_ab(int p, int64_t noff, const cx<R> *A, cx<R> *Ap) {
+// Packed rotation-form tables, in the order k_m2l_rot reads them.  Polar rotations (per offset,
+// forward then back): the degree blocks n = 0..p-1 one after the other, each (2n+1) x (2n+1)
+// row-major with the row the output order m' + n and the column the input order m + n, real.
+// Azimuthal phases (per offset, forward then back): the diagonal, p2 complex.  Coaxial Z (per
+// domain, level and offset length): the order blocks m = -(p-1)..p-1, each (p-|m|) x (p-|m|)
+// row-major with the row the output degree n' - |m| and the column the input degree n - |m|.  The
+// dense projected tables are stored input-major, T[c][r] at c * p2 + r.  The polar factors must be
+// real and the azimuthal ones diagonal (to rounding); the largest departure is recorded in
+// dev[0] (imaginary parts) and dev[1] (off-diagonal entries) as the bit patterns of non-negative
+// doubles, so that atomicMax orders them.
+__global__ void k_pack_rot_d(int p, const c64 *Tf, const c64 *Tb, double *D64, float *D32, unsigned long long *dev) {
     const int p2 = p * p, nrot = rot_off(p);
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= noff * nrot) return;
-    const int64_t o = idx / nrot;
-    const int i = (int)(idx - o * nrot);
+    if (idx >= (int64_t)316 * 2 * nrot) return;
+    const int64_t o = idx / (2 * nrot);
+    const int within = (int)(idx - o * 2 * nrot), fb = within / nrot, i = within - fb * nrot;
     int n = 0;
     while (rot_off(n + 1) <= i) ++n;
     const int w = 2 * n + 1, loc = i - rot_off(n), row = loc / w, col = loc - row * w;
-    Ap[idx] = A[o * p2 * p2 + (int64_t)(n * n + col) * p2 + n * n + row];
+    const c64 v = (fb == 0 ? Tf : Tb)[o * p2 * p2 + (int64_t)(n * n + col) * p2 + n * n + row];
+    D64[idx] = v.re;
+    D32[idx] = (float)v.re;
+    atomicMax(&dev[0], (unsigned long long)__double_as_longlong(fabs(v.im)));
+}
+__global__ void k_pack_rot_p(int p, const c64 *Tf, const c64 *Tb, c64 *P64, c32 *P32, unsigned long long *dev) {
+    const int p2 = p * p;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)316 * 2 * p2 * p2) return;
+    const int64_t o = idx / (2 * p2 * p2);
+    const int within = (int)(idx - o * 2 * p2 * p2), fb = within / (p2 * p2), e = within - fb * p2 * p2;
+    const int c = e / p2, r = e - c * p2;
+    const c64 v = (fb == 0 ? Tf : Tb)[o * p2 * p2 + e];
+    if (c == r) {
+        P64[(o * 2 + fb) * p2 + r] = v;
+        P32[(o * 2 + fb) * p2 + r] = c32{(float)v.re, (float)v.im};
+    } else {
+        atomicMax(&dev[1], (unsigned long long)__double_as_longlong(sqrt(v.re * v.re + v.im * v.im)));
+    }
 }
 template <typename R>
 __global__ void k_pack_rot_z(int p, int64_t nz, const cx<R> *Z, cx<R> *Zp) {
@@ -1212,31 +1245,51 @@ __global__ void k_pack_rot_z(int p, int64_t nz, const cx<R> *Z, cx<R> *Zp) {
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// replace the dense rotation-form tables (R_A, R_B per offset; R_Z per domain, level and length)
-// by their packed form
+// replace the dense coaxial tables R_Z (per domain, level and offset length) by their packed form
 void pack_rot_tables(fmbem *h, cudaStream_t s) {
-    const int p = h->p, p2 = h->p2;
-    const int64_t nrot = p * (2 * p - 1) * (2 * p + 1) / 3, ncoax = p * (2 * p * p + 1) / 3;
+    const int p = h->p;
+    const int64_t ncoax = p * (2 * p * p + 1) / 3;
     const int64_t nz = (int64_t)(h->J + 1) * (h->lmax + 1) * h->n_tlen;
-    (void)p2;
-    auto pack = [&](auto *&Ad, auto *&Bd, auto *&Zd) {
-        using T = std::remove_reference_t<decltype(*Ad)>;
-        T *Ap = (T *)dev_alloc(h, sizeof(T) * 316 * nrot), *Bp = (T *)dev_alloc(h, sizeof(T) * 316 * nrot);
+    auto pack = [&](auto *&Zd) {
+        using T = std::remove_reference_t<decltype(*Zd)>;
         T *Zp = (T *)dev_alloc(h, sizeof(T) * nz * ncoax);
-        k_pack_rot_ab<<<(unsigned)((316 * nrot + 255) / 256), 256, 0, s>>>(p, 316, Ad, Ap);
-        k_pack_rot_ab<<<(unsigned)((316 * nrot + 255) / 256), 256, 0, s>>>(p, 316, Bd, Bp);
         k_pack_rot_z<<<(unsigned)((nz * ncoax + 255) / 256), 256, 0, s>>>(p, nz, Zd, Zp);
-        CKL("k_pack_rot");
+        CKL("k_pack_rot_z");
         CK(cudaStreamSynchronize(s));
-        dev_free(h, Ad);
-        dev_free(h, Bd);
         dev_free(h, Zd);
-        Ad = Ap;
-        Bd = Bp;
         Zd = Zp;
     };
-    pack(h->R_A64, h->R_B64, h->R_Z64);
-    pack(h->R_A32, h->R_B32, h->R_Z32);
+    pack(h->R_Z64);
+    pack(h->R_Z32);
+}
+
+// the packed rotation factors from the projected ones: forward T(Rz^T) (azimuthal), T(Ry^T)
+// (polar), back T(Ry) (polar), T(Rz) (azimuthal), each [316][p2][p2] input-major; fails loudly if
+// the polar factors are not real or the azimuthal ones not diagonal
+void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s) {
+    const int p = h->p, p2 = h->p2;
+    const int64_t nrot = p * (2 * p - 1) * (2 * p + 1) / 3;
+    h->R_D64 = (double *)dev_alloc(h, sizeof(double) * 316 * 2 * nrot);
+    h->R_D32 = (float *)dev_alloc(h, sizeof(float) * 316 * 2 * nrot);
+    h->R_P64 = (c64 *)dev_alloc(h, sizeof(c64) * 316 * 2 * p2);
+    h->R_P32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * 2 * p2);
+    unsigned long long *dev = (unsigned long long *)dev_alloc(h, 2 * sizeof(unsigned long long));
+    CK(cudaMemsetAsync(dev, 0, 2 * sizeof(unsigned long long), s));
+    k_pack_rot_d<<<(unsigned)((316 * 2 * nrot + 255) / 256), 256, 0, s>>>(p, Tyf, Tyb, h->R_D64, h->R_D32, dev);
+    CKL("k_pack_rot_d");
+    const int64_t np = (int64_t)316 * 2 * p2 * p2;
+    k_pack_rot_p<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(p, Tzf, Tzb, h->R_P64, h->R_P32, dev);
+    CKL("k_pack_rot_p");
+    unsigned long long hd[2];
+    CK(cudaMemcpyAsync(hd, dev, sizeof(hd), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dev_free(h, dev);
+    double im_max, off_max;
+    std::memcpy(&im_max, &hd[0], sizeof(double));
+    std::memcpy(&off_max, &hd[1], sizeof(double));
+    if (!(im_max < 1e-9) || !(off_max < 1e-9))
+        throw fmbem_error{FMBEM_ERR_CUDA, "rotation factors: polar part not real (" + std::to_string(im_max) +
+                                              ") or azimuthal part not diagonal (" + std::to_string(off_max) + ")"};
 }
 
 // warp work items of the near field (see k_near_w): per leaf of nt targets, the layout of W
@@ -1365,11 +1418,13 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const int pp = h->p, nrot = pp * (2 * pp - 1) * (2 * pp + 1) / 3, ncoax = pp * (2 * pp * pp + 1) / 3;
     cudaFuncAttributes fa_r{};
     CK(cudaFuncGetAttributes(&fa_r, k_m2l_rot<R, RMAXC>));
-    auto rot_bytes = [&](int c) { return sizeof(cx<R>) * ((size_t)(2 * nrot + ncoax) + 2 * (size_t)c * RMAXC * p2); };
+    auto rot_bytes = [&](int c) {
+        return sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)c * RMAXC * p2);
+    };
     int cgr = std::max(1, std::min(4, fa_r.maxThreadsPerBlock / rows_pad));
     while (cgr > 1 && rot_bytes(cgr) > budget) --cgr;
     const int pcr = std::min(M2L_CHUNK, cgr * RMAXC / ncol);
-    const bool use_rot = chunked && h->m2l_rotation && h->R_A64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
+    const bool use_rot = chunked && h->m2l_rotation && h->R_D64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
                          rows_pad <= fa_r.maxThreadsPerBlock;
     if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
         run_m2l_tc(h, (float *)C, (float *)D, nr, s);
@@ -1378,8 +1433,8 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
         else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         if (use_rot)
             CK(cudaFuncSetAttribute(k_m2l_rot<R, RMAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_bytes(cgr)));
-        const cx<R> *RA = f32 ? (const cx<R> *)h->R_A32 : (const cx<R> *)h->R_A64;
-        const cx<R> *RB = f32 ? (const cx<R> *)h->R_B32 : (const cx<R> *)h->R_B64;
+        const R *RD = f32 ? (const R *)h->R_D32 : (const R *)h->R_D64;
+        const cx<R> *RP = f32 ? (const cx<R> *)h->R_P32 : (const cx<R> *)h->R_P64;
         const cx<R> *RZ = f32 ? (const cx<R> *)h->R_Z32 : (const cx<R> *)h->R_Z64;
         cx<R> *Y = (cx<R> *)h->ybuf;
         for (int l = 2; l <= lmax; ++l) {
@@ -1393,7 +1448,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                         if (use_rot)
                             k_m2l_rot<R, RMAXC><<<(unsigned)nch, rows_pad * cgr, rot_bytes(cgr), s>>>(
                                 c0, l, lmax, d, nr, pp, h->nbox, col0, nc, pcr, cgr, h->chunk_beg, h->chunk_cnt,
-                                h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RA, RB, RZ, C, Y, e_first);
+                                h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD, RP, RZ, C, Y, e_first);
                         else if (tsm)
                             k_m2l_chunks<R, MAXC, true><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
                                 c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt,

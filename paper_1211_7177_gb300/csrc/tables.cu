@@ -348,7 +348,8 @@ void build_tables(fmbem *h, cudaStream_t s) {
         std::sort(sq.begin(), sq.end());
         h->n_tlen = (int)sq.size();
         std::vector<int8_t> tidx(316);
-        std::vector<double> Mq(9 * 316), MqT(9 * 316);
+        // per offset: Rz (the azimuthal rotation), Ry (the polar one) and their transposes
+        std::vector<double> Mz(9 * 316), MzT(9 * 316), My(9 * 316), MyT(9 * 316);
         std::vector<int64_t> dst(316);
         for (int dx = -3; dx <= 3; ++dx)
             for (int dy = -3; dy <= 3; ++dy)
@@ -364,23 +365,24 @@ void build_tables(fmbem *h, cudaStream_t s) {
                     // Q = R_y(-theta) R_z(-phi) maps t/|t| to z
                     double Rz[9] = {cp, sp, 0, -sp, cp, 0, 0, 0, 1};
                     double Ry[9] = {ct, 0, -st, 0, 1, 0, st, 0, ct};
-                    double *Qm = &Mq[9 * o];
                     for (int a = 0; a < 3; ++a)
                         for (int b = 0; b < 3; ++b) {
-                            double acc = 0;
-                            for (int c = 0; c < 3; ++c) acc += Ry[3 * a + c] * Rz[3 * c + b];
-                            Qm[3 * a + b] = acc;
+                            Mz[9 * o + 3 * a + b] = Rz[3 * a + b];
+                            MzT[9 * o + 3 * a + b] = Rz[3 * b + a];
+                            My[9 * o + 3 * a + b] = Ry[3 * a + b];
+                            MyT[9 * o + 3 * a + b] = Ry[3 * b + a];
                         }
-                    for (int a = 0; a < 3; ++a)
-                        for (int b = 0; b < 3; ++b) MqT[9 * o + 3 * a + b] = Qm[3 * b + a];
                     dst[o] = o;
                 }
         h->rot_tidx = (int8_t *)dev_alloc(h, 316);
         CK(cudaMemcpyAsync(h->rot_tidx, tidx.data(), 316, cudaMemcpyHostToDevice, s));
-        h->R_A64 = (c64 *)dev_alloc(h, sizeof(c64) * 316 * p2 * p2);
-        h->R_A32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * p2 * p2);
-        h->R_B64 = (c64 *)dev_alloc(h, sizeof(c64) * 316 * p2 * p2);
-        h->R_B32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * p2 * p2);
+        // Q = Ry Rz maps t/|t| to z.  With T(M)[c][r] = <Y_r, Y_c o M>, T(M1 M2) = T(M1) T(M2), so the
+        // forward factor T(Q^T) = T(Rz^T) T(Ry^T) and the back factor T(Q) = T(Ry) T(Rz); the z
+        // factors are diagonal (phases e^{i m phi}) and the y factors real (see pack_rot_factors)
+        const std::vector<double> *mats[4] = {&MzT, &MyT, &My, &Mz};
+        c64 *Tf[4];
+        c32 *Tf32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * p2 * p2);  // unused single-precision copy
+        for (int f = 0; f < 4; ++f) Tf[f] = (c64 *)dev_alloc(h, sizeof(c64) * 316 * p2 * p2);
         double *dM = (double *)dev_alloc(h, sizeof(double) * 9 * 316);
         for (int q = 0; q < p2; ++q) { sr[q] = 1.0; sc[q] = 1.0; }
         CK(cudaMemcpyAsync(dsr, sr.data(), sizeof(double) * p2, cudaMemcpyHostToDevice, s));
@@ -388,17 +390,19 @@ void build_tables(fmbem *h, cudaStream_t s) {
         CK(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * 316, cudaMemcpyHostToDevice, s));
         k_proj_weights<<<nblk(Q, 64), 64, 0, s>>>(Q, p, dxq, dwq, c64{0, 0}, 1.0, 2, Yc);
         CKL("k_proj_weights");
-        for (int pass = 0; pass < 2; ++pass) {
-            CK(cudaMemcpyAsync(dM, pass == 0 ? MqT.data() : Mq.data(), sizeof(double) * 9 * 316, cudaMemcpyHostToDevice, s));
+        for (int pass = 0; pass < 4; ++pass) {
+            CK(cudaMemcpyAsync(dM, mats[pass]->data(), sizeof(double) * 9 * 316, cudaMemcpyHostToDevice, s));
             k_eval_rot<<<nblk((int64_t)316 * Q, 64), 64, 0, s>>>(316, Q, p, dxq, dM, F);
             CKL("k_eval_rot");
             dim3 grid((p2 + 15) / 16, (p2 + 15) / 16, 316), tb(16, 16);
-            k_project<<<grid, tb, 0, s>>>(316, Q, p2, Yc, F, dsr, dsc, pass == 0 ? h->R_A64 : h->R_B64,
-                                          pass == 0 ? h->R_A32 : h->R_B32, ddst);
+            k_project<<<grid, tb, 0, s>>>(316, Q, p2, Yc, F, dsr, dsc, Tf[pass], Tf32, ddst);
             CKL("k_project");
             CK(cudaStreamSynchronize(s));
         }
         dev_free(h, dM);
+        pack_rot_factors(h, Tf[0], Tf[1], Tf[2], Tf[3], s);
+        for (int f = 0; f < 4; ++f) dev_free(h, Tf[f]);
+        dev_free(h, Tf32);
         // coaxial S|R per (domain, level, distinct length), scaled like the dense S|R
         const int64_t nz = (int64_t)(J + 1) * (lmax + 1) * h->n_tlen;
         h->R_Z64 = (c64 *)dev_alloc(h, sizeof(c64) * nz * p2 * p2);
