@@ -52,6 +52,9 @@ UNIT = "points*RHS/s"
 # each transcendental = 1)
 NEAR_PAIR = 52
 NEAR_RHS = 78
+# FP64 with fewer than 4 right-hand sides reads g and c from the near-field cache built at create:
+# per (pair, domain) only r, w = n x r and n.r remain
+NEAR_PAIR_CACHED = 17
 PEAK_TFLOPS = {"fp64": 1.2, "fp32": 74.6}  # measured FMA throughput on GB300 (self-written probe)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor-core rate
 
@@ -199,7 +202,8 @@ def roofline(info, p, nr, n_dom, phases, precision):
         flops = per_col * 3 * nr * info["ff_pairs"] * n_dom
         name = f"M2L + L2L, {form}"
     elif dom == "near_l2p_self":
-        flops = info["near_pairs"] * n_dom * (NEAR_PAIR + NEAR_RHS * nr)
+        per_pair = NEAR_PAIR_CACHED if precision == "fp64" and nr < 4 else NEAR_PAIR
+        flops = info["near_pairs"] * n_dom * (per_pair + NEAR_RHS * nr)
         name = "near field + L2P + self (k_near)"
     else:
         flops, name = None, dom

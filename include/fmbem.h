@@ -85,8 +85,9 @@ typedef struct {
 typedef struct {
     int node_mode;           /* fmbem_node_mode [VERTEX]                                         */
     int p;                   /* truncation number p of Eq. (2.17): degrees n = 0..p-1 [8]         */
-    int leaf_size;           /* the octree is refined (Appendix C) until no leaf holds more than
-                                leaf_size nodes, l_max >= 2 [64]                                 */
+    int leaf_size;           /* the octree (Appendix C) is refined to the smallest depth l_max >= 2
+                                at which the non-empty leaves hold at most leaf_size nodes on
+                                average [64]                                                     */
     int max_level;           /* upper bound on l_max [10]                                         */
     int gmres_restart;       /* GMRES restart length m [50]                                       */
     int solve_precision;     /* fmbem_precision used by fmbem_solve's Krylov iterations [FP64];
@@ -101,6 +102,12 @@ typedef struct {
                                 -1 automatic: rotation form for p >= 9 [-1]                      */
     int profile_phases;      /* non-zero: record CUDA events around the matvec phases so that
                                 fmbem_last_matvec_times can report them [0]                       */
+    int near_cache;          /* near-field kernel scalars g, c of every (target, source, domain)
+                                pair, which depend on the geometry only, computed once at create
+                                in FP64 and read by the FP64 matvecs with fewer than 4 right-hand
+                                sides instead of evaluating exp, sincos and rsqrt per pair:
+                                0 off, 1 on, -1 automatic: on when the cache (32 bytes per pair and
+                                domain) takes at most a quarter of the free device memory [-1]    */
 } fmbem_options;
 
 void fmbem_default_options(fmbem_options *opt);

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
     _fields_ = [("node_mode", ctypes.c_int), ("p", ctypes.c_int), ("leaf_size", ctypes.c_int),
                 ("max_level", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("solve_precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("outer_precision", ctypes.c_int), ("m2l_rotation", ctypes.c_int),
-                ("profile_phases", ctypes.c_int)]
+                ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int)]
 
 
 class Mesh(ctypes.Structure):

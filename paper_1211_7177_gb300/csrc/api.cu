@@ -84,6 +84,7 @@ void fmbem_default_options(fmbem_options *o) {
     o->inner_tol = 1e-2;
     o->outer_precision = FMBEM_FP64;
     o->m2l_rotation = -1;
+    o->near_cache = -1;
     o->profile_phases = 0;
 }
 
@@ -108,7 +109,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32 && o.solve_precision != FMBEM_TF32) ||
         !(o.inner_tol > 0 && o.inner_tol < 1) ||
         (o.outer_precision != FMBEM_FP64 && o.outer_precision != FMBEM_FP32) || o.m2l_rotation < -1 ||
-        o.m2l_rotation > 1) {
+        o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
@@ -146,6 +147,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         }
         h->dcons = (c64 *)dev_alloc(h, sizeof(c64) * dc.size());
         CK(cudaMemcpyAsync(h->dcons, dc.data(), sizeof(c64) * dc.size(), cudaMemcpyHostToDevice, s));
+        build_near_cache(h, s);
         if (h->profile)
             for (auto &e : h->ev) CK(cudaEventCreate(&e));
         CK(cudaStreamSynchronize(s));

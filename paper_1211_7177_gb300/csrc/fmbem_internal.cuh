@@ -121,6 +121,10 @@ struct fmbem {
     int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;
     int4 *near_items = nullptr;  // warp work items of the near field (leaf, target offset, tg, nsl)
     int n_near_items = 0;
+    // near-field pair scalars (g, c) per leaf [side][source in the Neighbor list][target], double
+    // precision; near_base[leaf] = pairs of the leaves before it
+    void *near_cache64 = nullptr;
+    int64_t *near_base = nullptr;
     int32_t max_leaf = 0;                                 // largest leaf occupancy
     std::vector<int64_t> h_ff_count_level;
     // FF pairs of each level regrouped by translation offset, for the chunked M2L kernel:
@@ -245,6 +249,7 @@ void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
 void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s);
 void near_work_items(fmbem *h, cudaStream_t s);
+void build_near_cache(fmbem *h, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);

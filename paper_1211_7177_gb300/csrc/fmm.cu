@@ -710,7 +710,8 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                                               const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
                                               const int32_t *dom, const int32_t *perm, const cx<R> *dens,
                                               const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
-                                              const c64 *x, c64 *y) {
+                                              const c64 *x, c64 *y, const int64_t *cache_base,
+                                              const V4<R> *cache) {
     __shared__ NearSmem<R> S;
     __shared__ int rng_beg[32], rng_cum[33];
     SrcTile<R> &T = S.tile;
@@ -764,21 +765,41 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                 __syncthreads();
                 const int ns = min(128, nsrc - s0);
                 const R adom_r = (R)adom;
+                // cached pair scalars of this target: [side][source][target] within the leaf's block
+                const int NT = t1 - t0;
+                const V4<R> *cs0 = cache ? cache + 2 * cache_base[blockIdx.x] + (tb - t0 + tg) : nullptr;
                 if (active)
                     for (int u = slice; u < ns; u += nsl) {
                         const V4<R> pa = T.pa[u], pb = T.pb[u];
                         const V2<R> pn = T.pn[u];
                         R rx = pa.x - ax, ry = pa.y - ay, rz = pa.z - az;
                         if (DOUBLE_FLOAT) { rx += pb.x - alx; ry += pb.y - aly; rz += pb.z - alz; }
-                        R R2 = rx * rx + ry * ry + rz * rz;
-                        R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
-                        R Rr = R2 * inv;
                         cx<R> v[3], q[3];
                         {
                             const V4<R> a0 = T.dv[0][0][u], a1 = T.dv[0][1][u], a2 = T.dv[0][2][u];
                             v[0] = {a0.x, a0.y}; v[1] = {a0.z, a0.w}; v[2] = {a1.x, a1.y};
                             q[0] = {a1.z, a1.w}; q[1] = {a2.x, a2.y}; q[2] = {a2.z, a2.w};
                         }
+                        if (cs0) {
+                            // g and c from the cache; only the normal-dependent w = n x r and n.r here
+                            const int64_t e = s0 + u;
+                            const R w1[3] = {pn.x * rz - pn.y * ry, pn.y * rx - pb.w * rz, pb.w * ry - pn.x * rx};
+                            const R nr1 = pb.w * rx + pn.x * ry + pn.y * rz;
+                            const R w0[3] = {-w1[0], -w1[1], -w1[2]};
+                            const V4<R> s0v = cs0[e * NT];
+                            cross_apply<R>(w0, -nr1, cx<R>{s0v.x, s0v.y}, cx<R>{s0v.z, s0v.w}, v, q, acc0);
+                            if (pa.w == adom_r) {
+                                const V4<R> a0 = T.dv[1][0][u], a1 = T.dv[1][1][u], a2 = T.dv[1][2][u];
+                                v[0] = {a0.x, a0.y}; v[1] = {a0.z, a0.w}; v[2] = {a1.x, a1.y};
+                                q[0] = {a1.z, a1.w}; q[1] = {a2.x, a2.y}; q[2] = {a2.z, a2.w};
+                                const V4<R> s1v = cs0[((int64_t)nsrc + e) * NT];
+                                cross_apply<R>(w1, nr1, cx<R>{s1v.x, s1v.y}, cx<R>{s1v.z, s1v.w}, v, q, acc1);
+                            }
+                            continue;
+                        }
+                        R R2 = rx * rx + ry * ry + rz * rz;
+                        R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
+                        R Rr = R2 * inv;
                         pair_kernel<R>(rx, ry, rz, inv, Rr, kb, -pb.w, -pn.x, -pn.y, v, q, acc0);
                         if (pa.w == adom_r) {
                             const V4<R> a0 = T.dv[1][0][u], a1 = T.dv[1][1][u], a2 = T.dv[1][2][u];
@@ -814,6 +835,46 @@ __device__ __forceinline__ void pair_scalars(R inv, R Rr, cx<R> k, cx<R> &g, cx<
     g = {f * cs, f * sn};
     c = g * cx<R>{(-k.im - inv) * inv, k.re * inv};
 }
+// Near-field pair scalars of one leaf for the cache: for side 0 (domain 0) and side 1 (the
+// target's scatterer, zero where the source lies in another scatterer), every source e of the
+// leaf's Neighbor list (in k_near's order) and every target t of the leaf, g and c of
+// grad'g = c r (Eq. 2.12) at entry (side, e, t) of the leaf's block, in double precision.
+template <typename R>
+__global__ void k_near_cache(int64_t leaf_off, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                             const int32_t *nbr_idx, const double *pos, const int32_t *dom, const DomainConsts *dc,
+                             const int64_t *base, V4<R> *cache) {
+    __shared__ int rng_beg[32], rng_cum[33];
+    const int64_t g = leaf_off + blockIdx.x;
+    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        for (int q = 0; q < nnb; ++q) {
+            const int b = nbr_idx[nb0 + q];
+            rng_beg[q] = nbeg[b];
+            rng_cum[q] = cum;
+            cum += nend[b] - nbeg[b];
+        }
+        rng_cum[nnb] = cum;
+    }
+    __syncthreads();
+    const int nsrc = rng_cum[nnb], t0 = nbeg[g], nt = nend[g] - t0;
+    V4<R> *out = cache + 2 * base[blockIdx.x];
+    const int64_t total = 2 * (int64_t)nsrc * nt;
+    for (int64_t it = threadIdx.x; it < total; it += blockDim.x) {
+        const int side = (int)(it / ((int64_t)nsrc * nt));
+        const int rem = (int)(it - (int64_t)side * nsrc * nt), e = rem / nt, t = rem - e * nt;
+        const int q = source_range(rng_cum, nnb, e);
+        const int i = rng_beg[q] + (e - rng_cum[q]), a = t0 + t;
+        const double rx = pos[3 * i] - pos[3 * a], ry = pos[3 * i + 1] - pos[3 * a + 1], rz = pos[3 * i + 2] - pos[3 * a + 2];
+        const double R2 = rx * rx + ry * ry + rz * rz;
+        const double inv = R2 > 0.0 ? rsqrt_(R2) : 0.0;
+        const double Rr = R2 * inv;
+        c64 gs = {0, 0}, cs = {0, 0};
+        if (side == 0 || dom[i] == dom[a]) pair_scalars<double>(inv, Rr, dc[side == 0 ? 0 : dom[a]].k, gs, cs);
+        out[it] = V4<R>{(R)gs.re, (R)gs.im, (R)cs.re, (R)cs.im};
+    }
+}
+
 constexpr int NB_TILE = 64;  // sources per shared-memory tile in the blocked kernel
 template <typename R, int RB>
 struct SrcTileRB {
@@ -1292,6 +1353,43 @@ void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, 
                                               ") or azimuthal part not diagonal (" + std::to_string(off_max) + ")"};
 }
 
+// near-field pair-scalar cache (see k_near_cache): per leaf nt x nsrc pairs per side, double
+// precision (the single-precision kernels evaluate g and c faster than they could read them), built
+// when option near_cache asks for it (or, automatically, when it fits in a quarter of the free
+// device memory)
+void build_near_cache(fmbem *h, cudaStream_t s) {
+    if (h->opt.near_cache == 0) return;
+    const LevelInfo &L = h->lev[h->lmax];
+    std::vector<int32_t> nb(h->nbox), ne(h->nbox), ns(L.n + 1);
+    CK(cudaMemcpyAsync(nb.data(), h->box_nbeg, sizeof(int32_t) * h->nbox, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ne.data(), h->box_nend, sizeof(int32_t) * h->nbox, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ns.data(), h->nbr_start, sizeof(int32_t) * (L.n + 1), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> idx(ns[L.n]);
+    CK(cudaMemcpyAsync(idx.data(), h->nbr_idx, sizeof(int32_t) * idx.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int64_t> base(L.n + 1, 0);
+    for (int64_t lf = 0; lf < L.n; ++lf) {
+        int64_t nsrc = 0;
+        for (int q = ns[lf]; q < ns[lf + 1]; ++q) nsrc += ne[idx[q]] - nb[idx[q]];
+        base[lf + 1] = base[lf] + nsrc * (ne[L.off + lf] - nb[L.off + lf]);
+    }
+    const size_t pairs = (size_t)base[L.n];
+    const size_t bytes = 2 * pairs * sizeof(V4<double>);
+    if (h->opt.near_cache == -1) {
+        size_t freeb = 0, totb = 0;
+        CK(cudaMemGetInfo(&freeb, &totb));
+        if (bytes > freeb / 4) return;
+    }
+    h->near_base = (int64_t *)dev_alloc(h, sizeof(int64_t) * (L.n + 1));
+    CK(cudaMemcpyAsync(h->near_base, base.data(), sizeof(int64_t) * (L.n + 1), cudaMemcpyHostToDevice, s));
+    h->near_cache64 = dev_alloc(h, 2 * pairs * sizeof(V4<double>));
+    const DomainConsts *dc = (const DomainConsts *)h->dcons;
+    k_near_cache<double><<<(unsigned)L.n, 256, 0, s>>>(L.off, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, h->pos,
+                                                        h->dom, dc, h->near_base, (V4<double> *)h->near_cache64);
+    CKL("k_near_cache");
+    CK(cudaStreamSynchronize(s));
+}
+
 // warp work items of the near field (see k_near_w): per leaf of nt targets, the layout of W
 // warps x (tg targets x nsl slices) with the least lane time W / nsl, tg = ceil(nt / W) <= 32,
 // nsl the largest power of two with tg * nsl <= 32, up to 8 warps per leaf
@@ -1520,7 +1618,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
         else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
             k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                           h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens,
-                                                          dc, Bl2p, D, h->Mself, x, y);
+                                                          dc, Bl2p, D, h->Mself, x, y, nullptr, nullptr);
     } else if (nr >= 4) {
         constexpr int RBLK = 2;
         const size_t smn = sizeof(NearSmemRB<R, RBLK>);
@@ -1531,7 +1629,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     } else {
         k_near<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
                                                        h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D,
-                                                       h->Mself, x, y);
+                                                       h->Mself, x, y, h->near_base, (const V4<R> *)h->near_cache64);
     }
     CKL("k_near");
     if (timing) CK(cudaEventRecord(h->ev[4], s));

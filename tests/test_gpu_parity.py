@@ -174,6 +174,21 @@ def test_tf32_tensor_core_m2l(n_rhs, p):
         assert rel(ytc[r], y32[r]) < 1e-3
 
 
+@pytest.mark.parametrize("n_rhs", [1, 2])
+def test_near_cache_matches_direct_evaluation(n_rhs):
+    """The cached near-field pair scalars (computed once at create, FP64) give the same matvec as
+    the kernels that evaluate g and c per pair; FP32 matvecs do not use the cache."""
+    V, F, D = fi.icosphere(4)
+    args = ([1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5)
+    g_on = fm.FMBEM(V, F, D, *args, near_cache=1)
+    g_off = fm.FMBEM(V, F, D, *args, near_cache=0)
+    x = to_dev(fi.random_complex((n_rhs, g_on.N, 6), seed=23))
+    for prec, tol in ((fm.FP64, 1e-14), (fm.FP32, 2e-6)):
+        y_on = g_on.matvec(x, precision=prec).cpu().numpy()
+        y_off = g_off.matvec(x, precision=prec).cpu().numpy()
+        assert rel(y_on, y_off) < tol, (prec, rel(y_on, y_off))
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
