@@ -62,6 +62,8 @@ def _load():
             lib.oracle_precond_blocks.argtypes = [P, P]
             lib.oracle_matvec.argtypes = [P, i64, P, P]
             lib.oracle_matvec_rows.argtypes = [P, i64, i64, P, P, P]
+            lib.oracle_matvec_transpose.argtypes = [P, i64, P, P]
+            lib.oracle_matvec_transpose_rows.argtypes = [P, i64, i64, P, P, P]
             lib.oracle_precond_apply.argtypes = [P, i64, P, P]
             lib.oracle_plane_wave_rhs.argtypes = [P, i64, P, P, P]
             lib.oracle_gmres.restype = i32
@@ -161,6 +163,23 @@ class Oracle:
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         y = np.empty((x.shape[0], len(rows), 6), dtype=np.complex128)
         self._lib.oracle_matvec_rows(self._h, x.shape[0], len(rows), _ptr(rows), _ptr(x), _ptr(y))
+        return y[0] if squeeze else y
+
+    def matvec_transpose(self, x):
+        """y = A^T x (bilinear transpose); x [n_rhs, N, 6] (or [N, 6]) complex128."""
+        squeeze = np.ndim(x) == 2
+        x = self._vec(x)
+        y = np.empty_like(x)
+        self._lib.oracle_matvec_transpose(self._h, x.shape[0], _ptr(x), _ptr(y))
+        return y[0] if squeeze else y
+
+    def matvec_transpose_rows(self, x, rows):
+        """Entries of A^T x for the node indices ``rows``: [n_rhs, len(rows), 6]."""
+        squeeze = np.ndim(x) == 2
+        x = self._vec(x)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        y = np.empty((x.shape[0], len(rows), 6), dtype=np.complex128)
+        self._lib.oracle_matvec_transpose_rows(self._h, x.shape[0], len(rows), _ptr(rows), _ptr(x), _ptr(y))
         return y[0] if squeeze else y
 
     def precond_blocks(self):

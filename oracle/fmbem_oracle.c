@@ -22,6 +22,8 @@
  *     nodes of that domain summed directly with the one-point rule, plus the analytic self
  *     block.  The background domain uses the normal n0 = -n (outward from Omega_0) and the
  *     unknown n0 x curl E = -Psi (Psi is stored with the scatterer normal).
+ *   - The transposed product A^T x of the same operator (complex bilinear transpose, no
+ *     conjugation), gathered column by column from the transposed pair and self blocks.
  *   - The block-diagonal right preconditioner M = A_self of Eq. (3.2) (6x6 per node) and its
  *     exact application by Gaussian elimination with partial pivoting.
  *   - Right-preconditioned restarted GMRES, Eq. (3.1), with modified Gram-Schmidt and Givens
@@ -354,6 +356,108 @@ static void node_rows(const oracle_ctx *c, int64_t a, int64_t n_rhs, const cplx 
             for (int p = 0; p < 6; ++p) acc += M[q * 6 + p] * xa[p];
             out[6 * r + q] += acc;
         }
+    }
+}
+
+/* The transpose A^T (complex bilinear, no conjugation) applied to x: the result at column node b
+ * gathers, over every row node a != b, the transposed 6x6 block of node_rows' pair term, and the
+ * transposed self block.  With the bracket matrix Bk(n, a) v = n (a.v) - (n.a) v - a (n.v) of
+ * Eq. (2.12), Bk(n, a)^T u = a (n.u) - (n.a) u - n (a.u), and T_j is symmetric.  x: [n_rhs][N][6],
+ * out: [n_rhs][6] for node b. */
+static inline void bracket_t(const double *nn, const cplx *a, const cplx *u, cplx *out) {
+    cplx nu = nn[0] * u[0] + nn[1] * u[1] + nn[2] * u[2];
+    cplx na = nn[0] * a[0] + nn[1] * a[1] + nn[2] * a[2];
+    cplx au = a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
+    for (int q = 0; q < 3; ++q) out[q] = a[q] * nu - na * u[q] - nn[q] * au;
+}
+static void node_cols(const oracle_ctx *c, int64_t b, int64_t n_rhs, const cplx *x, cplx *out) {
+    const int64_t N = c->N;
+    const int j = c->dom[b];
+    const double *sb = c->s + 3 * b;
+    const double wb = c->w[b];
+    const double *nb = c->n + 3 * b;
+    const double n0[3] = {-nb[0], -nb[1], -nb[2]};
+    const cplx k0 = c->k[0], kj = c->k[j], gj = c->gam[j];
+    for (int64_t r = 0; r < n_rhs * 6; ++r) out[r] = 0;
+    for (int64_t a = 0; a < N; ++a) {
+        if (a == b) continue;
+        double rv[3]; sub3(sb, c->s + 3 * a, rv);            /* r = s_beta - s_alpha, as in node_rows */
+        double R = norm3(rv);
+        cplx g0 = cexp(I * k0 * R) / (4 * PI * R);
+        cplx c0 = g0 * (I * k0 - 1.0 / R) / R;
+        cplx a0[3] = {c0 * rv[0], c0 * rv[1], c0 * rv[2]};
+        int same = c->dom[a] == j;
+        cplx gj_ = 0, aj[3] = {0, 0, 0};
+        if (same) {
+            gj_ = cexp(I * kj * R) / (4 * PI * R);
+            cplx cj = gj_ * (I * kj - 1.0 / R) / R;
+            aj[0] = cj * rv[0]; aj[1] = cj * rv[1]; aj[2] = cj * rv[2];
+        }
+        for (int64_t r = 0; r < n_rhs; ++r) {
+            const cplx *xa = x + (r * N + a) * 6;
+            cplx B[3];
+            /* background rows of node a: blocks -w_b Bk(n0_b, a0) (Phi) and -w_b g0 I (Psi) */
+            bracket_t(n0, a0, xa, B);
+            for (int q = 0; q < 3; ++q) {
+                out[6 * r + q] += -wb * B[q];
+                out[6 * r + 3 + q] += -wb * g0 * xa[q];
+            }
+            if (same) {
+                /* scatterer rows: blocks -w_b Bk(n_b, aj) T_j(b) (Phi) and gamma_j w_b gj I (Psi) */
+                cplx TB[3];
+                bracket_t(nb, aj, xa + 3, B);
+                apply_T(c, j, nb, B, TB);
+                for (int q = 0; q < 3; ++q) {
+                    out[6 * r + q] += -wb * TB[q];
+                    out[6 * r + 3 + q] += gj * wb * gj_ * xa[3 + q];
+                }
+            }
+        }
+    }
+    const cplx *M = c->M + 36 * b;
+    for (int64_t r = 0; r < n_rhs; ++r) {
+        const cplx *xb = x + (r * N + b) * 6;
+        for (int p = 0; p < 6; ++p) {
+            cplx acc = 0;
+            for (int q = 0; q < 6; ++q) acc += M[q * 6 + p] * xb[q];
+            out[6 * r + p] += acc;
+        }
+    }
+}
+
+/* y = A^T x, x and y [n_rhs][N][6] complex */
+void oracle_matvec_transpose(const oracle_ctx *c, int64_t n_rhs, const double *x_, double *y_) {
+    const cplx *x = (const cplx *)x_;
+    cplx *y = (cplx *)y_;
+    const int64_t N = c->N;
+#pragma omp parallel
+    {
+        cplx *buf = malloc(sizeof(cplx) * 6 * n_rhs);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t b = 0; b < N; ++b) {
+            node_cols(c, b, n_rhs, x, buf);
+            for (int64_t r = 0; r < n_rhs; ++r)
+                for (int q = 0; q < 6; ++q) y[(r * N + b) * 6 + q] = buf[6 * r + q];
+        }
+        free(buf);
+    }
+}
+
+/* entries of A^T x for a subset of nodes: y [n_rhs][n_rows][6] */
+void oracle_matvec_transpose_rows(const oracle_ctx *c, int64_t n_rhs, int64_t n_rows, const int64_t *rows,
+                                  const double *x_, double *y_) {
+    const cplx *x = (const cplx *)x_;
+    cplx *y = (cplx *)y_;
+#pragma omp parallel
+    {
+        cplx *buf = malloc(sizeof(cplx) * 6 * n_rhs);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < n_rows; ++i) {
+            node_cols(c, rows[i], n_rhs, x, buf);
+            for (int64_t r = 0; r < n_rhs; ++r)
+                for (int q = 0; q < 6; ++q) y[(r * n_rows + i) * 6 + q] = buf[6 * r + q];
+        }
+        free(buf);
     }
 }
 
