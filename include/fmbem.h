@@ -172,6 +172,24 @@ fmbem_status fmbem_plane_wave_rhs(fmbem *h, int64_t n_rhs, const double *dir, co
  * demand, so the first call with a larger n_rhs allocates. */
 fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision, void *stream);
 
+/* y = A^T x, the transpose (complex bilinear, no conjugation) of the operator of Eq. (2.9) as
+ * fmbem_matvec evaluates it; A^H x is conj(A^T conj(x)).  The paper has no adjoint; it is the
+ * product an adjoint (gradient) solve needs.  Gathering the transposed blocks of Eq. (2.12) at a
+ * node b turns each domain's sum into the field of unweighted monopoles: with phi_i the
+ * potential of the strengths x_{a,i} of the d rows of x (g_d of Eq. 2.12),
+ *   Phi rows += w_b T_d(b) [-sum_i n'_i grad phi_i + n' div phi + (n'.grad) phi](s_b),
+ *   Psi rows += w_b sigma_d phi(s_b)   (n' = -n_b, sigma = -1 for the background; n' = n_b,
+ *                                       sigma = gamma_j for the node's scatterer),
+ * plus the transposed self block A_self^T x_b.  The far field of phi and grad phi runs through a
+ * monopole P2M, the same M2M, M2L and L2L translations, and L2P with the local basis and its
+ * gradient; the near field is summed directly over the Neighbor leaves.
+ *   x_dev, y_dev  device [n_rhs][N][6] complex128 (user order); x is read, y written; they
+ *                 must not overlap.
+ *   precision     FMBEM_FP64 or FMBEM_FP32 (as for fmbem_matvec; no tensor-core path).
+ * Uses the same handle-owned scratch as fmbem_matvec. */
+fmbem_status fmbem_adjoint_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,
+                                  void *stream);
+
 /* Solves A x = b (Eq. 2.9) by right-preconditioned restarted GMRES (Eq. 3.1) with the
  * block-diagonal preconditioner M = A_self (Eq. 3.2) applied exactly (6x6 LU per node), each
  * right-hand side in its own Krylov space, all right-hand sides batched through one matvec per

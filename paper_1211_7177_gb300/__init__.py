@@ -203,6 +203,17 @@ def fmbem_matvec(h, x, y=None, precision=FP64, stream=None):
     return y
 
 
+def fmbem_adjoint_matvec(h, x, y=None, precision=FP64, stream=None):
+    """y = A^T x (bilinear transpose of the operator; see include/fmbem.h)."""
+    import torch
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    y = torch.empty_like(x) if y is None else _dev(y, N, "y")
+    _check(h, load_library().fmbem_adjoint_matvec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                                  x.shape[0], int(precision), _stream(stream)))
+    return y
+
+
 def fmbem_solve(h, b, x=None, tol=1e-6, max_iter=1000, stream=None, raise_on_failure=False):
     """Returns (x, iters [n_rhs], relres [n_rhs], status)."""
     import torch
@@ -265,6 +276,9 @@ class FMBEM:
 
     def matvec(self, x, y=None, precision=FP64, stream=None):
         return fmbem_matvec(self.h, x, y, precision, stream)
+
+    def adjoint_matvec(self, x, y=None, precision=FP64, stream=None):
+        return fmbem_adjoint_matvec(self.h, x, y, precision, stream)
 
     def solve(self, b, x=None, tol=1e-6, max_iter=1000, stream=None):
         return fmbem_solve(self.h, b, x, tol, max_iter, stream)

@@ -142,6 +142,8 @@ struct fmbem {
     std::vector<double> lam;  // [(J+1)*(lmax+1)] scale lambda = |k_d| w_l
     c64 *B_p2m64 = nullptr, *B_l2p64 = nullptr;   // [2][N][4][p2], [2][N][p2] (side 0 bg, 1 own)
     c32 *B_p2m32 = nullptr, *B_l2p32 = nullptr;
+    c64 *B_l2pg64 = nullptr;                        // [2][N][3][p2] gradient of the L2P basis
+    c32 *B_l2pg32 = nullptr;
     c64 *T_m2l64 = nullptr, *T_mm64 = nullptr, *T_ll64 = nullptr;  // see tables.cu for layout
     c32 *T_m2l32 = nullptr, *T_mm32 = nullptr, *T_ll32 = nullptr;
     // tensor-core (tcgen05, TF32) M2L tables: real-form 128-byte-swizzled images, see m2l_tc.cu
@@ -243,6 +245,7 @@ void build_tables(fmbem *h, cudaStream_t s);
 // per-call operations
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
+void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);

@@ -1303,6 +1303,260 @@ __global__ void k_pack_rot_z(int p, int64_t nz, const cx<R> *Z, cx<R> *Zp) {
     Zp[idx] = Z[t * p2 * p2 + (int64_t)(n * n + n + m) * p2 + np * np + np + m];
 }
 
+// ---------------------------------------------------------------- adjoint (transposed) product
+// y = A^T x for the operator of Eq. (2.12) (complex bilinear transpose).  Gathering the transposed
+// pair blocks at a column node b gives, for each domain d of b's two equations (d = 0 and d = the
+// scatterer j of b),
+//   Phi rows:  w_b T_d(b) u,   u = -sum_i n'_i grad phi_i + n' div phi + (n'.grad) phi   at s_b,
+//   Psi rows:  w_b sigma_d phi(s_b),   sigma_0 = -1, sigma_j = gamma_j,
+// with n' = -n_b (d = 0) or n_b (d = j), T_0 = I, and phi_i(s) = sum_{a != b} g_d(|s - s_a|) x_{a,i}
+// the potential of unweighted monopoles taken from the d rows of x (rows 0-2 of every node for
+// d = 0, rows 3-5 of the nodes of scatterer j).  grad phi at s_b is sum_a c_d (s_b - s_a) x_a with
+// the c of grad'g = c r.  The far part of phi and grad phi comes from a monopole P2M, the usual
+// M2M, M2L and L2L, and L2P with the basis and its gradient; the transposed self block is added
+// in double precision.
+
+// dens[side][r][i][0..2] = x_{perm(i), 3 side + c}, unweighted, sorted order
+template <typename R>
+__global__ void k_prep_adj(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, cx<R> *dens) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = blockIdx.y;
+    if (i >= N) return;
+    const c64 *xa = x + (r * N + perm[i]) * 6;
+    for (int side = 0; side < 2; ++side) {
+        cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
+        for (int c = 0; c < 3; ++c) dn[c] = to<R>(xa[3 * side + c]);
+    }
+}
+
+// monopole P2M: C[d][leaf][3 r + c][q] = sum over the leaf's nodes of domain d of b0(i, q) x_{i,c},
+// with b0 the monopole row of the P2M basis (Eqs. 2.18-2.19)
+template <typename R>
+__global__ void k_p2m_adj(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+                          const int32_t *nend, const int32_t *dom, const cx<R> *dens, const cx<R> *Bp2m, cx<R> *C) {
+    const int64_t g = leaf_off + blockIdx.x;
+    const int d = blockIdx.y;
+    const int64_t r = blockIdx.z;
+    const int side = d == 0 ? 0 : 1;
+    const int i0 = nbeg[g], i1 = nend[g];
+    for (int q = threadIdx.x; q < p2; q += blockDim.x) {
+        cx<R> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int i = i0; i < i1; ++i) {
+            if (d > 0 && dom[i] != d) continue;
+            const cx<R> b0 = Bp2m[((int64_t)side * N + i) * 4 * p2 + q];
+            const cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cfma(acc[c], dn[c], b0);
+        }
+        for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
+    }
+}
+
+template <typename R>
+struct AdjTile {
+    V4<R> pa[128];      // position (high part) and scatterer id
+    V4<R> pb[128];      // position low part (double-float only)
+    cx<R> xv[3][128];   // the side's monopole strengths
+};
+template <typename R>
+union AdjSmem {
+    AdjTile<R> tile;
+    cx<R> red[12][128];  // per source slice: phi (3) and grad phi (9)
+};
+
+// near field, L2P (value and gradient), assembly and the transposed self block for one leaf;
+// threads split as (target, source slice) like k_near, both domains one after the other
+template <typename R, bool DOUBLE_FLOAT>
+__global__ void __launch_bounds__(128) k_near_adj(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                                  const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                                  const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
+                                                  const double *nrm, const double *w, const int32_t *dom,
+                                                  const int32_t *perm, const cx<R> *dens, const DomainConsts *dc,
+                                                  const cx<R> *Bl2p, const cx<R> *Bl2pg, const cx<R> *D,
+                                                  const c64 *Mself, const c64 *x, c64 *y, const int64_t *cache_base,
+                                                  const V4<R> *cache) {
+    __shared__ AdjSmem<R> S;
+    __shared__ int rng_beg[32], rng_cum[33];
+    AdjTile<R> &T = S.tile;
+    const int64_t g = leaf_off + blockIdx.x;
+    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        for (int q = 0; q < nnb; ++q) {
+            const int b = nbr_idx[nb0 + q];
+            rng_beg[q] = nbeg[b];
+            rng_cum[q] = cum;
+            cum += nend[b] - nbeg[b];
+        }
+        rng_cum[nnb] = cum;
+    }
+    __syncthreads();
+    const int nsrc = rng_cum[nnb];
+    const int t0 = nbeg[g], t1 = nend[g], NT = t1 - t0;
+    for (int64_t r = 0; r < nr; ++r) {
+        for (int tb = t0; tb < t1; tb += 128) {
+            const int nt = min(128, t1 - tb);
+            const int nsl = 128 / nt;
+            const int tg = threadIdx.x % nt, slice = threadIdx.x / nt;
+            const bool active = slice < nsl;
+            const int a = tb + tg;
+            const R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2];
+            R alx = 0, aly = 0, alz = 0;
+            if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
+            const int adom = dom[a];
+            const R adom_r = (R)adom;
+            const V4<R> *cs0 = cache ? cache + 2 * cache_base[blockIdx.x] + (tb - t0 + tg) : nullptr;
+            c64 yacc[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            for (int side = 0; side < 2; ++side) {
+                const int d = side == 0 ? 0 : adom;
+                const cx<R> k = to<R>(dc[d].k);
+                cx<R> phi[3], gphi[3][3];  // gphi[k][c] = d phi_c / d s_k
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    phi[c] = {0, 0};
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) gphi[kk][c] = {0, 0};
+                }
+                for (int s0 = 0; s0 < nsrc; s0 += 128) {
+                    __syncthreads();
+                    {
+                        const int e = s0 + threadIdx.x;
+                        if (e < nsrc) {
+                            const int q = source_range(rng_cum, nnb, e);
+                            const int i = rng_beg[q] + (e - rng_cum[q]);
+                            T.pa[threadIdx.x] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
+                            R lo[3] = {0, 0, 0};
+                            if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
+                            T.pb[threadIdx.x] = V4<R>{lo[0], lo[1], lo[2], 0};
+                            const cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
+                            for (int c = 0; c < 3; ++c) T.xv[c][threadIdx.x] = dn[c];
+                        }
+                    }
+                    __syncthreads();
+                    const int ns = min(128, nsrc - s0);
+                    if (active)
+                        for (int u = slice; u < ns; u += nsl) {
+                            const V4<R> pa = T.pa[u];
+                            if (side == 1 && pa.w != adom_r) continue;  // scatterer d sums over its own nodes
+                            const V4<R> pb = T.pb[u];
+                            R rx = pa.x - ax, ry = pa.y - ay, rz = pa.z - az;
+                            if (DOUBLE_FLOAT) { rx += pb.x - alx; ry += pb.y - aly; rz += pb.z - alz; }
+                            cx<R> gs, cs;
+                            if (cs0) {
+                                const V4<R> sv = cs0[((int64_t)side * nsrc + s0 + u) * NT];
+                                gs = {sv.x, sv.y};
+                                cs = {sv.z, sv.w};
+                            } else {
+                                const R R2 = rx * rx + ry * ry + rz * rz;
+                                const R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
+                                pair_scalars<R>(inv, R2 * inv, k, gs, cs);
+                            }
+                            // grad phi at the target: c (s_target - s_source) = -c r
+                            const cx<R> cr[3] = {-rx * cs, -ry * cs, -rz * cs};
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const cx<R> xc = T.xv[c][u];
+                                cfma(phi[c], gs, xc);
+#pragma unroll
+                                for (int kk = 0; kk < 3; ++kk) cfma(gphi[kk][c], cr[kk], xc);
+                            }
+                        }
+                }
+                // sum the source slices in a fixed order
+                __syncthreads();
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    S.red[c][threadIdx.x] = phi[c];
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) S.red[3 + 3 * kk + c][threadIdx.x] = gphi[kk][c];
+                }
+                __syncthreads();
+                if (threadIdx.x < nt) {
+                    c64 ph[3], gp[3][3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        cx<R> v = S.red[c][threadIdx.x];
+                        for (int sl = 1; sl < nsl; ++sl) v += S.red[c][sl * nt + threadIdx.x];
+                        ph[c] = c64{(double)v.re, (double)v.im};
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) {
+                            cx<R> t = S.red[3 + 3 * kk + c][threadIdx.x];
+                            for (int sl = 1; sl < nsl; ++sl) t += S.red[3 + 3 * kk + c][sl * nt + threadIdx.x];
+                            gp[kk][c] = c64{(double)t.re, (double)t.im};
+                        }
+                    }
+                    // far field: L2P of phi and grad phi from the leaf's local expansions
+                    const cx<R> *Dl = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r) * p2;
+                    const cx<R> *B = Bl2p + ((int64_t)side * N + a) * p2;
+                    const cx<R> *G = Bl2pg + ((int64_t)side * N + a) * 3 * p2;
+                    cx<R> fp[3] = {{0, 0}, {0, 0}, {0, 0}}, fg[3][3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) fg[kk][c] = {0, 0};
+                    for (int q = 0; q < p2; ++q) {
+                        const cx<R> b = B[q], gx = G[q], gy = G[p2 + q], gz = G[2 * p2 + q];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const cx<R> dq = Dl[c * p2 + q];
+                            cfma(fp[c], dq, b);
+                            cfma(fg[0][c], dq, gx);
+                            cfma(fg[1][c], dq, gy);
+                            cfma(fg[2][c], dq, gz);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        ph[c] += c64{(double)fp[c].re, (double)fp[c].im};
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) gp[kk][c] += c64{(double)fg[kk][c].re, (double)fg[kk][c].im};
+                    }
+                    // assembly in double precision
+                    const double sg = side == 0 ? -1.0 : 1.0;
+                    const double nb[3] = {nrm[3 * a], nrm[3 * a + 1], nrm[3 * a + 2]};
+                    const double np_[3] = {sg * nb[0], sg * nb[1], sg * nb[2]};
+                    const c64 div = gp[0][0] + gp[1][1] + gp[2][2];
+                    c64 u[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        c64 v = np_[c] * div;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) v -= np_[i] * gp[c][i];
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) v += np_[kk] * gp[kk][c];
+                        u[c] = v;
+                    }
+                    if (side == 1) {  // T_j u = u + t_j n (n.u), n the scatterer normal
+                        const c64 nu = nb[0] * u[0] + nb[1] * u[1] + nb[2] * u[2];
+                        const c64 tn = dc[d].t * nu;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) u[c] += nb[c] * tn;
+                    }
+                    const double wa = w[a];
+                    const c64 sig = side == 0 ? c64{-1.0, 0.0} : dc[d].gamma;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        yacc[c] += wa * u[c];
+                        yacc[3 + c] += (sig * ph[c]) * wa;
+                    }
+                }
+            }
+            if (threadIdx.x < nt) {  // transposed self block, stored in user order
+                const int64_t uu = perm[a];
+                const c64 *M = Mself + 36 * uu;
+                const c64 *xa = x + (r * N + uu) * 6;
+                c64 *ya = y + (r * N + uu) * 6;
+#pragma unroll
+                for (int pc = 0; pc < 6; ++pc) {
+                    c64 acc = yacc[pc];
+                    for (int q = 0; q < 6; ++q) cfma(acc, M[q * 6 + pc], xa[q]);
+                    ya[pc] = acc;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -1447,40 +1701,13 @@ static void ensure_scratch(fmbem *h, int64_t nr) {
     }
 }
 
+// M2M (Eq. 2.20) from level l_max up to level 2, on the multipole expansions in h->Cexp
 template <typename R>
-static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
-                        bool tensor_cores = false) {
-    const int64_t N = h->N;
+static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
     const int p2 = h->p2, lmax = h->lmax, J = h->J;
     const bool f32 = sizeof(R) == 4;
-    cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
-    const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
-    const cx<R> *Bl2p = f32 ? (const cx<R> *)h->B_l2p32 : (const cx<R> *)h->B_l2p64;
-    const cx<R> *Tm2l = f32 ? (const cx<R> *)h->T_m2l32 : (const cx<R> *)h->T_m2l64;
+    cx<R> *C = (cx<R> *)h->Cexp;
     const cx<R> *Tmm = f32 ? (const cx<R> *)h->T_mm32 : (const cx<R> *)h->T_mm64;
-    const cx<R> *Tll = f32 ? (const cx<R> *)h->T_ll32 : (const cx<R> *)h->T_ll64;
-    const bool timing = h->profile && h->ev[0] != nullptr;
-    if (timing) CK(cudaEventRecord(h->ev[0], s));
-
-    k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens);
-    CKL("k_prep");
-    const LevelInfo &L = h->lev[lmax];
-    const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
-    constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
-    if (nr >= 16) {
-        const int nthr = ((p2 + 3) / 4) * (P2M_MT / 4);
-        const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + P2M_MT);
-        CK(cudaFuncSetAttribute(k_p2m_gemm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
-        k_p2m_gemm<R><<<dim3((unsigned)L.n, J + 1, (unsigned)((3 * nr + P2M_MT - 1) / P2M_MT)), nthr, smp, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
-    } else if (nr >= 4)
-        k_p2m_rb<R, P2M_RB><<<dim3((unsigned)L.n, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
-    else
-        k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg,
-                                                                           h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
-    CKL("k_p2m");
-    if (timing) CK(cudaEventRecord(h->ev[1], s));
     const int ncc = (int)((3 * nr + CC - 1) / CC);
     const size_t sm = sizeof(cx<R>) * CC * p2;
     const int rows_pad = ((p2 + 31) / 32) * 32;
@@ -1490,7 +1717,19 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                                        h->box_cend, h->box_key, Tmm, C);
         CKL("k_m2m");
     }
-    if (timing) CK(cudaEventRecord(h->ev[2], s));
+}
+
+// downward pass (Eq. 2.21): M2L over the FF lists and L2L, h->Cexp -> h->Dexp, all levels
+template <typename R>
+static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_cores) {
+    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const bool f32 = sizeof(R) == 4;
+    cx<R> *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
+    const cx<R> *Tm2l = f32 ? (const cx<R> *)h->T_m2l32 : (const cx<R> *)h->T_m2l64;
+    const cx<R> *Tll = f32 ? (const cx<R> *)h->T_ll32 : (const cx<R> *)h->T_ll64;
+    const int rows_pad = ((p2 + 31) / 32) * 32;
+    const int ncc = (int)((3 * nr + CC - 1) / CC);  // column chunks of the fallback kernel
+    const size_t sm = sizeof(cx<R>) * CC * p2;
     // downward pass: offset-chunked M2L with a per-target reduction for few columns, the
     // target-major kernel (translation matrices reused across many columns) otherwise
     constexpr int MAXC = 24;
@@ -1590,6 +1829,42 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             CKL("k_down");
         }
     }
+}
+
+template <typename R>
+static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
+                        bool tensor_cores = false) {
+    const int64_t N = h->N;
+    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const bool f32 = sizeof(R) == 4;
+    cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
+    const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
+    const cx<R> *Bl2p = f32 ? (const cx<R> *)h->B_l2p32 : (const cx<R> *)h->B_l2p64;
+    const bool timing = h->profile && h->ev[0] != nullptr;
+    if (timing) CK(cudaEventRecord(h->ev[0], s));
+
+    k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens);
+    CKL("k_prep");
+    const LevelInfo &L = h->lev[lmax];
+    const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
+    constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
+    if (nr >= 16) {
+        const int nthr = ((p2 + 3) / 4) * (P2M_MT / 4);
+        const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + P2M_MT);
+        CK(cudaFuncSetAttribute(k_p2m_gemm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+        k_p2m_gemm<R><<<dim3((unsigned)L.n, J + 1, (unsigned)((3 * nr + P2M_MT - 1) / P2M_MT)), nthr, smp, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+    } else if (nr >= 4)
+        k_p2m_rb<R, P2M_RB><<<dim3((unsigned)L.n, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+    else
+        k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg,
+                                                                           h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+    CKL("k_p2m");
+    if (timing) CK(cudaEventRecord(h->ev[1], s));
+    upward_m2m<R>(h, nr, s);
+    if (timing) CK(cudaEventRecord(h->ev[2], s));
+    downward_pass<R>(h, nr, s, tensor_cores);
     if (timing) CK(cudaEventRecord(h->ev[3], s));
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
@@ -1633,6 +1908,48 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     }
     CKL("k_near");
     if (timing) CK(cudaEventRecord(h->ev[4], s));
+}
+
+// y = A^T x (see k_near_adj): monopole P2M, M2M, the downward pass, near field and assembly
+template <typename R>
+static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc) {
+    const int64_t N = h->N;
+    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const bool f32 = sizeof(R) == 4;
+    cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
+    const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
+    const cx<R> *Bl2p = f32 ? (const cx<R> *)h->B_l2p32 : (const cx<R> *)h->B_l2p64;
+    const cx<R> *Bl2pg = f32 ? (const cx<R> *)h->B_l2pg32 : (const cx<R> *)h->B_l2pg64;
+    k_prep_adj<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, dens);
+    CKL("k_prep_adj");
+    const LevelInfo &L = h->lev[lmax];
+    const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
+    k_p2m_adj<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg,
+                                                                           h->box_nend, h->dom, dens, Bp2m, C);
+    CKL("k_p2m_adj");
+    upward_m2m<R>(h, nr, s);
+    downward_pass<R>(h, nr, s, false);
+    const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
+    const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
+    const V4<R> *cache = f32 ? nullptr : (const V4<R> *)h->near_cache64;
+    if constexpr (sizeof(R) == 4)
+        k_near_adj<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+                                                          h->nbr_start, h->nbr_idx, ph, pl, h->nrm, h->w, h->dom,
+                                                          h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
+                                                          h->near_base, cache);
+    else
+        k_near_adj<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+                                                           h->nbr_start, h->nbr_idx, ph, pl, h->nrm, h->w, h->dom,
+                                                           h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
+                                                           h->near_base, cache);
+    CKL("k_near_adj");
+}
+
+void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
+    ensure_scratch(h, nr);
+    const DomainConsts *dc = (const DomainConsts *)h->dcons;
+    if (precision == FMBEM_FP32) adjoint_impl<float>(h, x, y, nr, s, dc);
+    else adjoint_impl<double>(h, x, y, nr, s, dc);
 }
 
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {

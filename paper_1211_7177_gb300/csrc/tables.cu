@@ -60,7 +60,7 @@ __global__ void k_to32(const c64 *a, c32 *b, int64_t n) {
 // per node and side: P2M basis (scaled, with the i k prefactor) and L2P basis
 __global__ void k_node_bases(int64_t N, int p, const double *pos, const int32_t *dom, const int32_t *node_leaf,
                              const double *box_ctr, const c64 *kd, const double *lam /* [J+1] at the leaf level */,
-                             c64 *Bp2m, c64 *Bl2p) {
+                             c64 *Bp2m, c64 *Bl2p, c64 *Bl2pg) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int side = blockIdx.y;
     if (i >= N) return;
@@ -76,6 +76,7 @@ __global__ void k_node_bases(int64_t N, int p, const double *pos, const int32_t 
     c64 ik = c64{-k.im, k.re};
     c64 *bp = Bp2m + ((int64_t)side * N + i) * 4 * p2;
     c64 *bl = Bl2p + ((int64_t)side * N + i) * p2;
+    c64 *bg = Bl2pg + ((int64_t)side * N + i) * 3 * p2;  // gradient of the L2P basis (adjoint product)
     double lpow = 1.0;  // lambda^n
     for (int n = 0; n < p; ++n) {
         double sm = 1.0 / (lpow * la);  // 1/lambda^(n+1)
@@ -88,6 +89,8 @@ __global__ void k_node_bases(int64_t N, int p, const double *pos, const int32_t 
             bp[2 * p2 + q] = (ik * g[1]) * sm;
             bp[3 * p2 + q] = (ik * g[2]) * sm;
             bl[q] = R[q] * (1.0 / lpow);
+            grad_regular(p, k, R, n, m, g);
+            for (int a = 0; a < 3; ++a) bg[a * p2 + q] = g[a] * (1.0 / lpow);
         }
         lpow *= la;
     }
@@ -211,15 +214,19 @@ void build_tables(fmbem *h, cudaStream_t s) {
     CK(cudaMemcpyAsync(dl, lleaf.data(), sizeof(double) * (J + 1), cudaMemcpyHostToDevice, s));
     h->B_p2m64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * 4 * p2);
     h->B_l2p64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * p2);
+    h->B_l2pg64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * 3 * p2);
     {
         dim3 grid(nblk(N, 64), 2);
-        k_node_bases<<<grid, 64, 0, s>>>(N, p, h->pos, h->dom, h->node_leaf, h->box_ctr, dk, dl, h->B_p2m64, h->B_l2p64);
+        k_node_bases<<<grid, 64, 0, s>>>(N, p, h->pos, h->dom, h->node_leaf, h->box_ctr, dk, dl, h->B_p2m64, h->B_l2p64,
+                                          h->B_l2pg64);
         CKL("k_node_bases");
     }
     h->B_p2m32 = (c32 *)dev_alloc(h, sizeof(c32) * 2 * N * 4 * p2);
     h->B_l2p32 = (c32 *)dev_alloc(h, sizeof(c32) * 2 * N * p2);
+    h->B_l2pg32 = (c32 *)dev_alloc(h, sizeof(c32) * 2 * N * 3 * p2);
     k_to32<<<nblk(2 * N * 4 * p2, 256), 256, 0, s>>>(h->B_p2m64, h->B_p2m32, 2 * N * 4 * p2);
     k_to32<<<nblk(2 * N * p2, 256), 256, 0, s>>>(h->B_l2p64, h->B_l2p32, 2 * N * p2);
+    k_to32<<<nblk(2 * N * 3 * p2, 256), 256, 0, s>>>(h->B_l2pg64, h->B_l2pg32, 2 * N * 3 * p2);
     CKL("k_to32");
 
     // ---- translation matrices

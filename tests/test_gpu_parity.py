@@ -189,6 +189,40 @@ def test_near_cache_matches_direct_evaluation(n_rhs):
         assert rel(y_on, y_off) < tol, (prec, rel(y_on, y_off))
 
 
+@pytest.mark.parametrize("precision", [fm.FP64, fm.FP32])
+def test_adjoint_matvec_matches_oracle_transpose(sphere_s4, precision):
+    """y = A^T x through the FMM (monopole P2M, the shared translations, L2P with its gradient)
+    against the oracle's dense transposed product, and the bilinear identity <y, A x> = <A^T y, x>
+    between the GPU forward and adjoint products."""
+    o, g = sphere_s4
+    x = fi.random_complex((2, o.N, 6), seed=51)
+    yt = g.adjoint_matvec(to_dev(x), precision=precision).cpu().numpy()
+    assert rel(yt, o.matvec_transpose(x)) < MATVEC_TOL
+    z = fi.random_complex((2, o.N, 6), seed=52)
+    lhs = np.sum(z * g.matvec(to_dev(x), precision=precision).cpu().numpy())
+    rhs = np.sum(g.adjoint_matvec(to_dev(z), precision=precision).cpu().numpy() * x)
+    assert abs(lhs - rhs) / abs(lhs) < MATVEC_TOL
+
+
+def test_adjoint_two_scatterers_and_rows_at_scale():
+    """Two scatterers with mu != 1 (full comparison), and 256 sampled rows of the silver sphere
+    (163842 nodes, p = 10)."""
+    m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
+    m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
+    o, g = case(fi.merge_meshes(m1, m2), [1.0, 2.25, -4 + 0.3j], [1.0, 1.3, 1.0], 1.2)
+    x = fi.random_complex((1, o.N, 6), seed=53)
+    for prec in (fm.FP64, fm.FP32):
+        assert rel(g.adjoint_matvec(to_dev(x), precision=prec).cpu().numpy(), o.matvec_transpose(x)) < MATVEC_TOL
+    V, F, D = fi.icosphere(7)
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    g7 = fm.FMBEM(V, F, D, eps, mu, k0, p=10)
+    o7 = oracle.Oracle(V, F, D, eps, mu, k0)
+    x7 = fi.random_complex((1, g7.N, 6), seed=54)
+    rows = fi.sample_rows(g7.N, 256, seed=55)
+    yt = g7.adjoint_matvec(to_dev(x7)).cpu().numpy()[:, rows]
+    assert rel(yt, o7.matvec_transpose_rows(x7, rows)) < MATVEC_TOL
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
