@@ -345,6 +345,22 @@ def run_ours(args):
         ms1 = e0.elapsed_time(e1) / 3
         other = dict(other or {}, fp64_single_rhs=dict(value=world * N / (ms1 * 1e-3), ms_per_step=ms1))
 
+    # the adjoint (transposed) product through the same tree and translations (no tensor-core path)
+    aprec = fm.FP64 if args.precision == "fp64" else fm.FP32
+    for _ in range(2):
+        g.adjoint_matvec(x, y, precision=aprec)
+    torch.cuda.synchronize()
+    a_ms = []
+    for k in range(3):
+        flush.fill_(float(k))
+        e0.record(stream)
+        g.adjoint_matvec(x, y, precision=aprec)
+        e1.record(stream)
+        e1.synchronize()
+        a_ms.append(e0.elapsed_time(e1))
+    adjoint = dict(precision="fp64" if aprec == fm.FP64 else "fp32", ms_per_step=statistics.mean(a_ms),
+                   value=world * N * nr / (statistics.mean(a_ms) * 1e-3))
+
     solve = None
     if not args.no_solve:
         solve = {}
@@ -386,7 +402,7 @@ def run_ours(args):
                             tree=info, parallelism=f"replicas x{world}",
                             l2="flushed (256 MiB write) before each step", setup_s=setup_s, wall_s=wall),
                 e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes),
-                roofline=roof, other_precision=other, solve=solve, cpu_baseline=cpu,
+                roofline=roof, other_precision=other, adjoint=adjoint, solve=solve, cpu_baseline=cpu,
                 gpu_launches=launches_per_step * args.steps, clocks=clk)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -208,6 +208,16 @@ fmbem_status fmbem_adjoint_matvec(fmbem *h, const void *x_dev, void *y_dev, int6
 fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
                          int32_t *iters_host, double *relres_host, void *stream);
 
+/* Solves A^T x = b, the adjoint (transposed) system of Eq. (2.9), the way fmbem_solve solves
+ * A x = b: right-preconditioned restarted GMRES with fmbem_adjoint_matvec as the operator and the
+ * transposed preconditioner M^T = A_self^T (applied exactly from the same 6x6 LU), honouring
+ * solve_precision, inner_tol and outer_precision (TF32 acts as FP32: the adjoint product has no
+ * tensor-core path).  The paper has no adjoint solve; an adjoint (gradient) computation needs it:
+ * for an objective J = L^T x with A x = b, dJ/dp = -lambda^T (dA/dp) x with A^T lambda = L.
+ * Arguments, layout, return values and errors as for fmbem_solve. */
+fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
+                                 int32_t *iters_host, double *relres_host, void *stream);
+
 /* z = M^{-1} v with M = A_self (Eq. 3.2), per node 6x6 complex LU; v_dev, z_dev device
  * [n_rhs][N][6] complex128 (may be the same buffer). */
 fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream);

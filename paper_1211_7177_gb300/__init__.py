@@ -74,6 +74,9 @@ def load_library(build_if_missing: bool = True):
         "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
         "fmbem_matvec": (i32, [P, P, P, i64, i32, P]),
         "fmbem_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
+        "fmbem_adjoint_matvec": (i32, [P, P, P, i64, i32, P]),
+        "fmbem_adjoint_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
+        "fmbem_matvec_noalloc": (i32, [P, P, P, i64, i32, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
     }
@@ -170,10 +173,17 @@ def fmbem_tree_info(h):
     return dict(l_max=lm.value, n_leaves=nl.value, n_boxes=nb.value, near_pairs=npairs.value, ff_pairs=nff.value)
 
 
-def _dev(t, N, name):
+def _dev(t, N, name, out=False):
+    """Checks a device vector [n_rhs, N, 6] complex128.  The library reads and writes raw device
+    memory, so lazily conjugated or negated tensors (PyTorch's conj/neg views) are materialised
+    when they are inputs and refused when they are outputs."""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if t.is_conj() or t.is_neg():
+        if out:
+            raise TypeError(f"{name} must not be a conjugate or negative view (it is written in place)")
+        t = t.resolve_conj().resolve_neg()
     if t.dim() == 2:
         t = t.unsqueeze(0)
     if t.dim() != 3 or t.shape[1] != N or t.shape[2] != 6:
@@ -197,7 +207,7 @@ def fmbem_matvec(h, x, y=None, precision=FP64, stream=None):
     import torch
     N = fmbem_num_nodes(h)
     x = _dev(x, N, "x")
-    y = torch.empty_like(x) if y is None else _dev(y, N, "y")
+    y = torch.empty_like(x) if y is None else _dev(y, N, "y", out=True)
     _check(h, load_library().fmbem_matvec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                           x.shape[0], int(precision), _stream(stream)))
     return y
@@ -208,7 +218,7 @@ def fmbem_adjoint_matvec(h, x, y=None, precision=FP64, stream=None):
     import torch
     N = fmbem_num_nodes(h)
     x = _dev(x, N, "x")
-    y = torch.empty_like(x) if y is None else _dev(y, N, "y")
+    y = torch.empty_like(x) if y is None else _dev(y, N, "y", out=True)
     _check(h, load_library().fmbem_adjoint_matvec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                                   x.shape[0], int(precision), _stream(stream)))
     return y
@@ -219,7 +229,7 @@ def fmbem_solve(h, b, x=None, tol=1e-6, max_iter=1000, stream=None, raise_on_fai
     import torch
     N = fmbem_num_nodes(h)
     b = _dev(b, N, "b")
-    x = torch.zeros_like(b) if x is None else _dev(x, N, "x")
+    x = torch.zeros_like(b) if x is None else _dev(x, N, "x", out=True)
     n = b.shape[0]
     it = np.zeros(n, dtype=np.int32)
     rr = np.zeros(n)
@@ -230,11 +240,27 @@ def fmbem_solve(h, b, x=None, tol=1e-6, max_iter=1000, stream=None, raise_on_fai
     return x, it, rr, st
 
 
+def fmbem_adjoint_solve(h, b, x=None, tol=1e-6, max_iter=1000, stream=None, raise_on_failure=False):
+    """Solves A^T x = b (see include/fmbem.h); returns (x, iters [n_rhs], relres [n_rhs], status)."""
+    import torch
+    N = fmbem_num_nodes(h)
+    b = _dev(b, N, "b")
+    x = torch.zeros_like(b) if x is None else _dev(x, N, "x", out=True)
+    n = b.shape[0]
+    it = np.zeros(n, dtype=np.int32)
+    rr = np.zeros(n)
+    st = load_library().fmbem_adjoint_solve(h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), n, float(tol),
+                                    int(max_iter), _ptr(it), _ptr(rr), _stream(stream))
+    if st not in (0, 5) or (raise_on_failure and st != 0):
+        raise FMBEMError(st, fmbem_last_error(h))
+    return x, it, rr, st
+
+
 def fmbem_precond_apply(h, v, z=None, stream=None):
     import torch
     N = fmbem_num_nodes(h)
     v = _dev(v, N, "v")
-    z = torch.empty_like(v) if z is None else _dev(z, N, "z")
+    z = torch.empty_like(v) if z is None else _dev(z, N, "z", out=True)
     _check(h, load_library().fmbem_precond_apply(h, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
                                                  v.shape[0], _stream(stream)))
     return z
@@ -283,6 +309,9 @@ class FMBEM:
     def solve(self, b, x=None, tol=1e-6, max_iter=1000, stream=None):
         return fmbem_solve(self.h, b, x, tol, max_iter, stream)
 
+    def adjoint_solve(self, b, x=None, tol=1e-6, max_iter=1000, stream=None):
+        return fmbem_adjoint_solve(self.h, b, x, tol, max_iter, stream)
+
     def precond_apply(self, v, z=None, stream=None):
         return fmbem_precond_apply(self.h, v, z, stream)
 
@@ -300,7 +329,7 @@ def fmbem_matvec_noalloc(h, x, y, precision=FP64, stream=None):
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
     N = fmbem_num_nodes(h)
     x = _dev(x, N, "x")
-    y = _dev(y, N, "y")
+    y = _dev(y, N, "y", out=True)
     _check(h, f(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.shape[0], int(precision),
                 _stream(stream)))
     return y

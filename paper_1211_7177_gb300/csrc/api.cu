@@ -255,6 +255,24 @@ fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs
     return res;
 }
 
+fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
+                                 int32_t *iters_host, double *relres_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || !b_dev || !x_dev || !(tol > 0) || max_iter < 1) {
+        h->err = "invalid argument";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    fmbem_status res = FMBEM_OK;
+    fmbem_status st = guarded(h, [&] {
+        res = run_solve(h, (const c64 *)b_dev, (c64 *)x_dev, n_rhs, tol, max_iter, iters_host, relres_host,
+                        (cudaStream_t)stream, true);
+    });
+    if (st != FMBEM_OK) return st;
+    if (res == FMBEM_ERR_NOT_CONVERGED) h->err = "GMRES did not reach the tolerance within max_iter";
+    if (res == FMBEM_ERR_BREAKDOWN) h->err = "GMRES produced a non-finite value";
+    return res;
+}
+
 fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (n_rhs < 1 || !v_dev || !z_dev) { h->err = "invalid argument"; return FMBEM_ERR_INVALID_ARGUMENT; }

@@ -254,7 +254,8 @@ void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, 
 void near_work_items(fmbem *h, cudaStream_t s);
 void build_near_cache(fmbem *h, cudaStream_t s);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
-void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
+void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s, bool transpose = false);
+void run_precond_t(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s);
 fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t n_rhs, double tol, int max_iter, int32_t *iters,
-                       double *relres, cudaStream_t s);
+                       double *relres, cudaStream_t s, bool transpose = false);

@@ -211,6 +211,44 @@ __global__ void k_precond(int64_t N, int64_t n_rhs, const c64 *LU, const int8_t 
     for (int q = 0; q < 6; ++q) z[6 * i + q] = b[q];
 }
 
+// z = M^-T v (the transposed preconditioner of the adjoint solve) from the LU factors PM = LU:
+// M^T = U^T L^T P, so U^T y = v (forward), L^T w = y (backward, unit diagonal), z = P^T w (the
+// row swaps undone in reverse order)
+__global__ void k_precond_t(int64_t N, int64_t n_rhs, const c64 *LU, const int8_t *piv, const c64 *v, c64 *z) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N * n_rhs) return;
+    const int64_t a = i % N;
+    const c64 *L = LU + 36 * a;
+    c64 b[6];
+    for (int q = 0; q < 6; ++q) b[q] = v[6 * i + q];
+    for (int r = 0; r < 6; ++r) {
+        c64 acc = b[r];
+        for (int c = 0; c < r; ++c) acc -= L[c * 6 + r] * b[c];
+        b[r] = cdiv(acc, L[r * 6 + r]);
+    }
+    for (int r = 5; r >= 0; --r)
+        for (int c = r + 1; c < 6; ++c) b[r] -= L[c * 6 + r] * b[c];
+    for (int c = 5; c >= 0; --c) {
+        const int pv = piv[6 * a + c];
+        if (pv != c) { c64 t = b[c]; b[c] = b[pv]; b[pv] = t; }
+    }
+    for (int q = 0; q < 6; ++q) z[6 * i + q] = b[q];
+}
+
+// z = M^-T v with the single-precision explicit inverse (adjoint inner iterations)
+__global__ void k_precond32_t(int64_t N, int64_t n_rhs, const c32 *Minv, const c32 *v, c64 *z) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N * n_rhs) return;
+    const c32 *M = Minv + 36 * (i % N);
+    c32 b[6];
+    for (int q = 0; q < 6; ++q) b[q] = v[6 * i + q];
+    for (int r = 0; r < 6; ++r) {
+        c32 acc = {0.f, 0.f};
+        for (int c = 0; c < 6; ++c) cfma(acc, M[6 * c + r], b[c]);
+        z[6 * i + r] = c64{(double)acc.re, (double)acc.im};
+    }
+}
+
 // explicit inverse of each node's 6x6 block M (Eq. 3.2) from its LU factors, column by column in
 // double precision, stored in single precision for the inner iterations of the refined solve
 __global__ void k_inverse32(int64_t N, const c64 *LU, const int8_t *piv, c32 *Minv) {
@@ -401,15 +439,22 @@ void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s) 
     CKL("k_precond");
 }
 
-void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s) {
+void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s, bool transpose) {
     if (h->Minv32 == nullptr) {
         h->Minv32 = (c32 *)dev_alloc(h, sizeof(c32) * 36 * h->N);
         k_inverse32<<<(unsigned)((h->N + 127) / 128), 128, 0, s>>>(h->N, h->Mlu, h->piv, h->Minv32);
         CKL("k_inverse32");
     }
     const int64_t n = h->N * n_rhs;
-    k_precond32<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(h->N, n_rhs, h->Minv32, v, z);
+    if (transpose) k_precond32_t<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(h->N, n_rhs, h->Minv32, v, z);
+    else k_precond32<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(h->N, n_rhs, h->Minv32, v, z);
     CKL("k_precond32");
+}
+
+void run_precond_t(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s) {
+    const int64_t n = h->N * n_rhs;
+    k_precond_t<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(h->N, n_rhs, h->Mlu, h->piv, v, z);
+    CKL("k_precond_t");
 }
 
 void run_plane_wave(fmbem *h, int64_t n_rhs, const double *dir, const fmbem_c64 *pol, c64 *b, cudaStream_t s) {

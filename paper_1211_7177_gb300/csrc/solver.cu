@@ -195,10 +195,20 @@ struct Work {
     }
 };
 
-// M^-1 applied to a basis vector: the LU of Eq. (3.2) in double precision for a double basis,
-// the single-precision explicit inverse for a single basis
-void precond(fmbem *h, const c64 *v, c64 *z, int64_t nr, cudaStream_t s) { run_precond(h, v, z, nr, s); }
-void precond(fmbem *h, const c32 *v, c64 *z, int64_t nr, cudaStream_t s) { run_precond32(h, v, z, nr, s); }
+// M^-1 (or M^-T for the adjoint solve) applied to a basis vector: the LU of Eq. (3.2) in double
+// precision for a double basis, the single-precision explicit inverse for a single basis
+void precond(fmbem *h, const c64 *v, c64 *z, int64_t nr, cudaStream_t s, bool tr) {
+    if (tr) run_precond_t(h, v, z, nr, s);
+    else run_precond(h, v, z, nr, s);
+}
+void precond(fmbem *h, const c32 *v, c64 *z, int64_t nr, cudaStream_t s, bool tr) { run_precond32(h, v, z, nr, s, tr); }
+
+// the operator of the solve: A (Eq. 2.9) or, for the adjoint solve, A^T (which has no tensor-core
+// path, so TF32 falls back to FP32)
+void apply_op(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s, bool tr) {
+    if (tr) run_adjoint_matvec(h, x, y, nr, precision == FMBEM_TF32 ? FMBEM_FP32 : precision, s);
+    else run_matvec(h, x, y, nr, precision, s);
+}
 
 // basis element type -> arithmetic of its vector operations
 template <typename TV>
@@ -217,8 +227,8 @@ struct ArithOf<c32> {
 // relative to ||rhs||.  V holds (m + 2) vectors of nr * n elements of TV (the last one is scratch
 // for the final combination); z and w are nr * n double vectors.
 template <typename TV>
-void gmres(fmbem *h, Work &W, int precision, const c64 *rhs, c64 *x, double tol, int max_iter, TV *V, c64 *z, c64 *w,
-           std::vector<int> &its, std::vector<double> &relres, std::vector<char> &conv, bool &breakdown) {
+void gmres(fmbem *h, Work &W, int precision, bool tr, const c64 *rhs, c64 *x, double tol, int max_iter, TV *V, c64 *z,
+           c64 *w, std::vector<int> &its, std::vector<double> &relres, std::vector<char> &conv, bool &breakdown) {
     using R = typename ArithOf<TV>::R;
     const int64_t n = W.n, nr = W.nr;
     const int m = std::max(1, h->opt.gmres_restart);
@@ -234,7 +244,7 @@ void gmres(fmbem *h, Work &W, int precision, const c64 *rhs, c64 *x, double tol,
     int total = 0;
     for (;;) {
         // true residual r = rhs - A x
-        run_matvec(h, x, w, nr, precision, s);
+        apply_op(h, x, w, nr, precision, s, tr);
         k_axpy<<<grid, 256, 0, s>>>(1, rhs, w, n, nr);
         CKL("k_axpy");
         W.norms<double>(w, rn);
@@ -257,8 +267,8 @@ void gmres(fmbem *h, Work &W, int precision, const c64 *rhs, c64 *x, double tol,
         for (int64_t r = 0; r < nr; ++r) g[r][0] = rn[r];
         int jdone = 0;
         for (int j = 0; j < m && total < max_iter; ++j) {
-            precond(h, V + (int64_t)j * nr * n, z, nr, s);
-            run_matvec(h, z, w, nr, precision, s);
+            precond(h, V + (int64_t)j * nr * n, z, nr, s, tr);
+            apply_op(h, z, w, nr, precision, s, tr);
             ++total;
             // classical Gram-Schmidt, twice
             std::vector<cd> hc(nr * (j + 1), cd(0, 0));
@@ -315,7 +325,7 @@ void gmres(fmbem *h, Work &W, int precision, const c64 *rhs, c64 *x, double tol,
         }
         k_combine<TV, R, TV><<<grid, 256, 0, s>>>(V, jdone, W.upload<R>(yc), tmp, n, nr);
         CKL("k_combine");
-        precond(h, tmp, z, nr, s);
+        precond(h, tmp, z, nr, s, tr);
         k_axpy<<<grid, 256, 0, s>>>(2, z, x, n, nr);
         CKL("k_axpy");
         if (breakdown) break;
@@ -328,7 +338,7 @@ size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
 
 fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, int max_iter, int32_t *iters,
-                       double *relres, cudaStream_t s) {
+                       double *relres, cudaStream_t s, bool transpose) {
     const int m = std::max(1, h->opt.gmres_restart);
     const int64_t n = 6 * h->N;
     const bool refine = h->opt.solve_precision != FMBEM_FP64;
@@ -363,7 +373,7 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
     const dim3 grid(nblk(n, 256), (unsigned)nr);
     try {
         if (!refine) {
-            gmres<c64>(h, W, FMBEM_FP64, b, x, tol, max_iter, (c64 *)base, z, w, its, rr, conv, breakdown);
+            gmres<c64>(h, W, FMBEM_FP64, transpose, b, x, tol, max_iter, (c64 *)base, z, w, its, rr, conv, breakdown);
         } else {
             // iterative refinement: r = b - A x (outer_precision passes, double vectors); solve
             // A' d = r to inner_tol with the FP32 or TF32 operator and a single-precision basis;
@@ -373,7 +383,7 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
             std::vector<double> bn;
             W.norms<double>(b, bn);
             for (int outer = 0;; ++outer) {
-                run_matvec(h, x, r, nr, h->opt.outer_precision, s);
+                apply_op(h, x, r, nr, h->opt.outer_precision, s, transpose);
                 k_axpy<<<grid, 256, 0, s>>>(1, b, r, n, nr);
                 CKL("k_axpy");
                 std::vector<double> rn;
@@ -394,8 +404,8 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
                 std::vector<double> ir;
                 std::vector<char> ic;
                 const double itol = std::max(h->opt.inner_tol, 0.5 * tol);
-                gmres<c32>(h, W, h->opt.solve_precision, r, d, itol, max_iter - used, (c32 *)base, z, w, ii, ir, ic,
-                           breakdown);
+                gmres<c32>(h, W, h->opt.solve_precision, transpose, r, d, itol, max_iter - used, (c32 *)base, z, w, ii,
+                           ir, ic, breakdown);
                 for (int64_t q = 0; q < nr; ++q) itot[q] += ii[q];
                 k_axpy<<<grid, 256, 0, s>>>(2, d, x, n, nr);
                 CKL("k_axpy");

@@ -70,3 +70,11 @@ def test_invalid_arguments_rejected():
     with pytest.raises(fm.FMBEMError) as e:
         _create(V, F, D, eps=(1.0, 0.0))
     assert e.value.status == 1
+
+
+def test_binding_declares_every_signature():
+    """Every entry point declared in include/fmbem.h gets its ctypes signature (argument types)
+    from the binding when the library is loaded, so scalars such as tolerances convert."""
+    lib = fm.load_library()
+    missing = [n for n in fm.header_functions() if getattr(lib, n).argtypes is None]
+    assert not missing, missing

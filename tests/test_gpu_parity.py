@@ -223,6 +223,54 @@ def test_adjoint_two_scatterers_and_rows_at_scale():
     assert rel(yt, o7.matvec_transpose_rows(x7, rows)) < MATVEC_TOL
 
 
+def test_adjoint_solve_duality_and_residual(sphere_s4):
+    """Adjoint GMRES (A^T x = b with M^T as right preconditioner): <b2, A^-1 b1> = <A^-T b2, b1>
+    between a forward and an adjoint solve, and the oracle's dense A^T residual of the adjoint
+    solution; also through the refined (FP32-inner) path."""
+    o, g = sphere_s4
+    b1 = fi.random_complex((1, o.N, 6), seed=61)
+    b2 = fi.random_complex((1, o.N, 6), seed=62)
+    xf, _, _, st1 = g.solve(to_dev(b1), tol=1e-8)
+    xa, its, rr, st2 = g.adjoint_solve(to_dev(b2), tol=1e-8)
+    assert st1 == 0 and st2 == 0, (st1, st2)
+    xf, xa = xf.cpu().numpy(), xa.cpu().numpy()
+    lhs, rhs = np.sum(b2 * xf), np.sum(xa * b1)
+    print(f"duality: {abs(lhs - rhs) / abs(lhs):.2e}")
+    assert abs(lhs - rhs) / abs(lhs) < 1e-3
+    res = rel(o.matvec_transpose(xa), b2)
+    print(f"adjoint solve: {int(its[0])} iterations, oracle A^T residual {res:.2e}")
+    assert res < 1e-3
+    V, F, D = fi.icosphere(4)
+    gr = fm.FMBEM(V, F, D, [1.0, 2.25], [1.0, 1.0], 1.0, solve_precision=fm.FP32, inner_tol=1e-3)
+    xr, _, rr2, st3 = gr.adjoint_solve(to_dev(b2), tol=1e-6)
+    assert st3 == 0 and rr2.max() <= 1e-6
+    assert rel(xr.cpu().numpy(), xa) < 1e-4
+
+
+def test_autograd_solve_and_matvec_gradients(sphere_s4):
+    """torch.autograd through the solve (backward = one adjoint solve) and the product (backward =
+    one adjoint product): the gradient of L = Re(c^T f(b)) matches the central difference of L
+    along a random complex direction (L is linear in b, so the difference is exact up to the
+    solver tolerance)."""
+    import torch
+    from paper_1211_7177_gb300 import autograd as fa
+    o, g = sphere_s4
+    c = to_dev(fi.random_complex((1, o.N, 6), seed=71))
+    b0 = to_dev(fi.random_complex((1, o.N, 6), seed=72))
+    dirn = to_dev(fi.random_complex((1, o.N, 6), seed=73))
+    for f in (lambda b: fa.solve(g, b, tol=1e-10), lambda b: fa.matvec(g, b)):
+        b = b0.clone().requires_grad_(True)
+        L = torch.real(torch.sum(c * f(b)))
+        L.backward()
+        slope = torch.real(torch.sum(torch.conj(b.grad) * dirn)).item()
+        h = 1e-3
+        with torch.no_grad():
+            Lp = torch.real(torch.sum(c * f(b0 + h * dirn))).item()
+            Lm = torch.real(torch.sum(c * f(b0 - h * dirn))).item()
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(slope - fd) <= 1e-6 * abs(fd), (slope, fd)
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
