@@ -54,37 +54,60 @@ __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm,
 }
 
 // ---------------------------------------------------------------- P2M (Eqs. 2.18-2.19)
-// grid (leaf, domain, rhs); thread per coefficient nm; C[d][g][3r+i][nm]
+// grid (leaf, domain, rhs); thread per coefficient nm; C[d][g][3r+i][nm].  The dipole and monopole
+// of component c enter as sum_k W_k(c) B_k with the node weights W_0 = q_c and
+// W_k = v_c n_k - n_c v_k + (n.v) delta_ck (m_c . grad R + q_c R, Eq. 2.18); the block forms them
+// once per node in shared memory, P2M_WN nodes at a time.
+constexpr int P2M_WN = 64;
 template <typename R>
 __global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
                       const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens, const cx<R> *Bp2m,
                       cx<R> *C) {
-    int64_t g = leaf_off + blockIdx.x;
-    int d = blockIdx.y;
-    int64_t r = blockIdx.z;
-    int side = d == 0 ? 0 : 1;
-    R sg = d == 0 ? (R)-1 : (R)1;
-    int i0 = nbeg[g], i1 = nend[g];
-    for (int q = threadIdx.x; q < p2; q += blockDim.x) {
-        cx<R> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-        for (int i = i0; i < i1; ++i) {
-            if (d > 0 && dom[i] != d) continue;
+    __shared__ cx<R> W[P2M_WN][4][3];
+    const int64_t g = leaf_off + blockIdx.x;
+    const int d = blockIdx.y;
+    const int64_t r = blockIdx.z;
+    const int side = d == 0 ? 0 : 1;
+    const R sg = d == 0 ? (R)-1 : (R)1;
+    const int i0 = nbeg[g], i1 = nend[g];
+    const int q = threadIdx.x;  // one thread per coefficient: blockDim >= p2
+    cx<R> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int ib = i0; ib < i1; ib += P2M_WN) {
+        const int nk = min(P2M_WN, i1 - ib);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 3 * nk; e += blockDim.x) {
+            const int il = e / 3, c = e - 3 * il, i = ib + il;
+            if (d > 0 && dom[i] != d) {
+                for (int k = 0; k < 4; ++k) W[il][k][c] = {0, 0};
+                continue;
+            }
             const cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
-            cx<R> v[3] = {dn[0], dn[1], dn[2]}, qq[3] = {dn[3], dn[4], dn[5]};
-            R n[3] = {sg * (R)nrm[3 * i], sg * (R)nrm[3 * i + 1], sg * (R)nrm[3 * i + 2]};
-            const cx<R> *B = Bp2m + ((int64_t)side * N + i) * 4 * p2;
-            cx<R> b0 = B[q], G[3] = {B[p2 + q], B[2 * p2 + q], B[3 * p2 + q]};
-            cx<R> nG = n[0] * G[0] + n[1] * G[1] + n[2] * G[2];
-            cx<R> nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
-            cx<R> vG = v[0] * G[0] + v[1] * G[1] + v[2] * G[2];
-            for (int c = 0; c < 3; ++c) {
-                // m_c . G = v_c (n.G) + (n.v) G_c - n_c (v.G), plus the monopole q_c R
-                cx<R> t = v[c] * nG + nv * G[c] - n[c] * vG + qq[c] * b0;
-                acc[c] += t;
+            const cx<R> v[3] = {dn[0], dn[1], dn[2]};
+            const R n[3] = {sg * (R)nrm[3 * i], sg * (R)nrm[3 * i + 1], sg * (R)nrm[3 * i + 2]};
+            const cx<R> nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+            W[il][0][c] = dn[3 + c];
+            const cx<R> vc = c == 0 ? v[0] : (c == 1 ? v[1] : v[2]);  // selects, not a local-memory index
+            const R nc = c == 0 ? n[0] : (c == 1 ? n[1] : n[2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                cx<R> t = n[k] * vc - nc * v[k];
+                if (k == c) t += nv;
+                W[il][1 + k][c] = t;
             }
         }
-        for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
+        __syncthreads();
+        if (q < p2)
+            for (int il = 0; il < nk; ++il) {
+                const cx<R> *B = Bp2m + ((int64_t)side * N + ib + il) * 4 * p2;
+                const cx<R> b[4] = {B[q], B[p2 + q], B[2 * p2 + q], B[3 * p2 + q]};
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cfma(acc[c], W[il][k][c], b[k]);
+            }
     }
+    if (q < p2)
+        for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
 }
 
 // P2M for blocks of RB right-hand sides: the basis values of a (node, coefficient) are read once
@@ -237,6 +260,7 @@ __global__ void k_p2m_gemm(int64_t leaf_off, int64_t N, int64_t nr, int p2, int6
 // acc[cc] += sum_c T[c][r] X[cc][c] for the thread's output row r; X in shared memory
 template <typename R, int CC>
 __device__ __forceinline__ void apply_T(const cx<R> *__restrict__ T, const cx<R> *X, int p2, int r, int ncol, cx<R> *acc) {
+#pragma unroll 4
     for (int c = 0; c < p2; ++c) {
         cx<R> t = T[(int64_t)c * p2 + r];
 #pragma unroll
@@ -248,26 +272,27 @@ __device__ __forceinline__ void apply_T(const cx<R> *__restrict__ T, const cx<R>
 constexpr int CC = 6;  // columns per CTA in the translation kernels
 
 // M2M (Eq. 2.20): parent multipole = sum over children S|S(child octant) child multipole
-// grid (parent box at level l-1, domain, column chunk)
-template <typename R>
+// grid (parent box at level l-1, domain, chunk of NC columns); NC = 3 for one right-hand side,
+// so that no multiply-add of the unrolled column loop is issued for an absent column
+template <typename R, int NC>
 __global__ void k_m2m(int64_t par_off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *cbeg,
                       const int32_t *cend, const uint64_t *key, const cx<R> *Tmm, cx<R> *C) {
     extern __shared__ unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
     int64_t g = par_off + blockIdx.x;
     int d = blockIdx.y;
-    int col0 = blockIdx.z * CC;
-    int ncol = min(CC, (int)(3 * nr) - col0);
+    int col0 = blockIdx.z * NC;
+    int ncol = min(NC, (int)(3 * nr) - col0);
     int r = threadIdx.x;
-    cx<R> acc[CC];
-    for (int cc = 0; cc < CC; ++cc) acc[cc] = {0, 0};
+    cx<R> acc[NC];
+    for (int cc = 0; cc < NC; ++cc) acc[cc] = {0, 0};
     for (int ch = cbeg[g]; ch < cend[g]; ++ch) {
         __syncthreads();
         for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
             X[e] = C[(((int64_t)d * nbox + ch) * 3 * nr + col0 + e / p2) * p2 + e % p2];
         __syncthreads();
         int o = (int)(key[ch] & 7);
-        if (r < p2) apply_T<R, CC>(Tmm + oct_matrix(d, l, o, lmax) * p2 * p2, X, p2, r, ncol, acc);
+        if (r < p2) apply_T<R, NC>(Tmm + oct_matrix(d, l, o, lmax) * p2 * p2, X, p2, r, ncol, acc);
     }
     if (r < p2)
         for (int cc = 0; cc < ncol; ++cc) C[(((int64_t)d * nbox + g) * 3 * nr + col0 + cc) * p2 + r] = acc[cc];
@@ -1708,13 +1733,16 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
     const bool f32 = sizeof(R) == 4;
     cx<R> *C = (cx<R> *)h->Cexp;
     const cx<R> *Tmm = f32 ? (const cx<R> *)h->T_mm32 : (const cx<R> *)h->T_mm64;
-    const int ncc = (int)((3 * nr + CC - 1) / CC);
-    const size_t sm = sizeof(cx<R>) * CC * p2;
     const int rows_pad = ((p2 + 31) / 32) * 32;
     for (int l = lmax; l >= 3; --l) {
         const LevelInfo &P = h->lev[l - 1];
-        k_m2m<R><<<dim3((unsigned)P.n, J + 1, ncc), rows_pad, sm, s>>>(P.off, l, lmax, nr, p2, h->nbox, h->box_cbeg,
-                                                                       h->box_cend, h->box_key, Tmm, C);
+        if (nr == 1)
+            k_m2m<R, 3><<<dim3((unsigned)P.n, J + 1, 1), rows_pad, sizeof(cx<R>) * 3 * p2, s>>>(
+                P.off, l, lmax, nr, p2, h->nbox, h->box_cbeg, h->box_cend, h->box_key, Tmm, C);
+        else
+            k_m2m<R, CC><<<dim3((unsigned)P.n, J + 1, (unsigned)((3 * nr + CC - 1) / CC)), rows_pad,
+                           sizeof(cx<R>) * CC * p2, s>>>(P.off, l, lmax, nr, p2, h->nbox, h->box_cbeg, h->box_cend,
+                                                         h->box_key, Tmm, C);
         CKL("k_m2m");
     }
 }
@@ -1857,9 +1885,9 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     } else if (nr >= 4)
         k_p2m_rb<R, P2M_RB><<<dim3((unsigned)L.n, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
             L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
-    else
-        k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg,
-                                                                           h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+    else  // one thread per coefficient
+        k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), ((p2 + 31) / 32) * 32, 0, s>>>(
+            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     CKL("k_p2m");
     if (timing) CK(cudaEventRecord(h->ev[1], s));
     upward_m2m<R>(h, nr, s);
