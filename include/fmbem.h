@@ -218,6 +218,24 @@ fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs
 fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
                                  int32_t *iters_host, double *relres_host, void *stream);
 
+/* Far-field amplitude of the scattered field of solutions x (Section 4; the representation
+ * formula of Appendix A in the far zone), with n0 = -n and Psi0 = -Psi the background's normal
+ * and unknown:
+ *   F(u) = 1/(4 pi) sum_b w_b exp(-i k0 u.s_b) { (-i k0)[n0 (u.Phi_b) - (n0.u) Phi_b - u (n0.Phi_b)]
+ *                                                 - Psi0_b },   E_sca ~ exp(i k0 r)/r F(u).
+ *   x_dev     device [n_rhs][N][6] complex128 (user order), read.
+ *   rhat      host [n_dir][3] unit directions.
+ *   F_host    host [n_rhs][n_dir][3] complex128, written.
+ * Extinction by the optical theorem is C_ext = (4 pi / k0) Im[e* . F(d)] for the plane wave
+ * (d, e); the scattering cross section is the integral of |F|^2 over the unit sphere. */
+fmbem_status fmbem_far_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_dir, const double *rhat,
+                             fmbem_c64 *F_host, void *stream);
+
+/* sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (host [n_rhs], written): with
+ * n x curl E = Psi the inward flux of the time-averaged Poynting vector, Eq. (4.2), gives the
+ * absorption cross section C_abs = -(1/k0) times this sum. */
+fmbem_status fmbem_absorption(fmbem *h, const void *x_dev, int64_t n_rhs, double *out_host, void *stream);
+
 /* z = M^{-1} v with M = A_self (Eq. 3.2), per node 6x6 complex LU; v_dev, z_dev device
  * [n_rhs][N][6] complex128 (may be the same buffer). */
 fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream);

@@ -77,6 +77,8 @@ def load_library(build_if_missing: bool = True):
         "fmbem_adjoint_matvec": (i32, [P, P, P, i64, i32, P]),
         "fmbem_adjoint_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
         "fmbem_matvec_noalloc": (i32, [P, P, P, i64, i32, P]),
+        "fmbem_far_field": (i32, [P, P, i64, i64, P, P, P]),
+        "fmbem_absorption": (i32, [P, P, i64, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
     }
@@ -224,6 +226,27 @@ def fmbem_adjoint_matvec(h, x, y=None, precision=FP64, stream=None):
     return y
 
 
+def fmbem_far_field(h, x, rhat, stream=None):
+    """Far-field amplitude F [n_rhs, n_dir, 3] complex128 (host) of solutions x in directions rhat."""
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    rhat = np.ascontiguousarray(np.atleast_2d(rhat), dtype=np.float64)
+    F = np.empty((x.shape[0], len(rhat), 3), dtype=np.complex128)
+    _check(h, load_library().fmbem_far_field(h, ctypes.c_void_p(x.data_ptr()), x.shape[0], len(rhat), _ptr(rhat),
+                                             _ptr(F), _stream(stream)))
+    return F
+
+
+def fmbem_absorption(h, x, stream=None):
+    """sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (C_abs = -this / k0)."""
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    out = np.empty(x.shape[0])
+    _check(h, load_library().fmbem_absorption(h, ctypes.c_void_p(x.data_ptr()), x.shape[0], _ptr(out),
+                                              _stream(stream)))
+    return out
+
+
 def fmbem_solve(h, b, x=None, tol=1e-6, max_iter=1000, stream=None, raise_on_failure=False):
     """Returns (x, iters [n_rhs], relres [n_rhs], status)."""
     import torch
@@ -279,6 +302,8 @@ class FMBEM:
         self.options = fmbem_default_options(**options)
         self.h = fmbem_create(V, F, D, eps, mu, k0, self.options, stream)
         self.N = fmbem_num_nodes(self.h)
+        # background wavenumber k0 sqrt(eps_0 mu_0) (real for the cross sections)
+        self.kb = complex(k0 * np.sqrt(complex(eps[0]) * complex(mu[0])))
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -311,6 +336,32 @@ class FMBEM:
 
     def adjoint_solve(self, b, x=None, tol=1e-6, max_iter=1000, stream=None):
         return fmbem_adjoint_solve(self.h, b, x, tol, max_iter, stream)
+
+    def far_field(self, x, rhat, stream=None):
+        return fmbem_far_field(self.h, x, rhat, stream)
+
+    def cross_sections(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
+        """(C_ext, C_sca, C_abs) per right-hand side for the plane waves (dirs[r], pols[r]) that
+        produced the solutions x[r]: extinction by the optical theorem, scattering as the
+        Gauss-Legendre (cos theta) x trapezoid (phi) integral of |F|^2, absorption by Eq. (4.2);
+        the far fields and the absorption sums are evaluated on the device."""
+        if self.kb.imag != 0:
+            raise ValueError("cross sections need a lossless background")
+        k0 = self.kb.real
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
+        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
+        ph = 2 * np.pi * np.arange(n_phi) / n_phi
+        MU, PH = np.meshgrid(mu, ph, indexing="ij")
+        ST = np.sqrt(1 - MU ** 2)
+        rq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
+        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel()
+        F = fmbem_far_field(self.h, x, np.concatenate([dirs, rq]), stream)
+        nr = F.shape[0]
+        cext = np.array([4 * np.pi / k0 * np.imag(np.vdot(pols[r], F[r, r])) for r in range(nr)])
+        csca = np.sum(wq[None, :] * np.sum(np.abs(F[:, len(dirs):]) ** 2, axis=2), axis=1)
+        cabs = -fmbem_absorption(self.h, x, stream) / k0
+        return cext, csca, cabs
 
     def precond_apply(self, v, z=None, stream=None):
         return fmbem_precond_apply(self.h, v, z, stream)

@@ -273,6 +273,27 @@ fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64
     return res;
 }
 
+fmbem_status fmbem_far_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_dir, const double *rhat,
+                             fmbem_c64 *F_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_dir < 1 || !x_dev || !rhat || !F_host || n_dir > 65535 || n_rhs > 65535) {
+        h->err = "invalid argument (n_rhs, n_dir in 1..65535, non-NULL pointers)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_far_field(h, (const c64 *)x_dev, n_rhs, n_dir, rhat, (c64 *)F_host, (cudaStream_t)stream);
+    });
+}
+
+fmbem_status fmbem_absorption(fmbem *h, const void *x_dev, int64_t n_rhs, double *out_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || !x_dev || !out_host) {
+        h->err = "invalid argument";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] { run_absorption(h, (const c64 *)x_dev, n_rhs, out_host, (cudaStream_t)stream); });
+}
+
 fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64_t n_rhs, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (n_rhs < 1 || !v_dev || !z_dev) { h->err = "invalid argument"; return FMBEM_ERR_INVALID_ARGUMENT; }

@@ -246,6 +246,9 @@ void build_tables(fmbem *h, cudaStream_t s);
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
+void run_far_field(fmbem *h, const c64 *x, int64_t n_rhs, int64_t n_dir, const double *rhat_host, c64 *F_host,
+                   cudaStream_t s);
+void run_absorption(fmbem *h, const c64 *x, int64_t n_rhs, double *out_host, cudaStream_t s);
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);

@@ -517,7 +517,8 @@ __global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, in
 }
 
 // D(l,q) = R|R D(parent) + sum of the target's M2L pair results (Eq. 2.21), columns col0..col0+ncol.
-// Threads: rows_pad x ct column threads; a thread owns columns c = ct_id, ct_id + ct, ...
+// Threads: rows_pad x ct column groups; a thread owns columns cid * L2L_CPT .. + L2L_CPT - 1.
+constexpr int L2L_CPT = 3;
 template <typename R>
 __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
                              int ct, const int32_t *parent, const uint64_t *key, const int32_t *ff_start,
@@ -537,10 +538,23 @@ __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, in
     }
     if (r >= p2) return;
     const int e0 = ff_start[g], e1 = ff_start[g + 1];
-    for (int c = cid; c < ncol; c += ct) {
-        cx<R> a0 = {0, 0}, a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
-        if (T)
-            for (int k = 0; k < p2; ++k) cfma(a0, T[(int64_t)k * p2 + r], X[c * p2 + k]);
+    // this thread's columns c0 .. c0 + L2L_CPT - 1: one read of T per row k feeds all of them
+    const int c0 = cid * L2L_CPT;
+    cx<R> lp[L2L_CPT];
+#pragma unroll
+    for (int j = 0; j < L2L_CPT; ++j) lp[j] = {0, 0};
+    if (T)
+        for (int k = 0; k < p2; ++k) {
+            const cx<R> t = T[(int64_t)k * p2 + r];
+#pragma unroll
+            for (int j = 0; j < L2L_CPT; ++j)
+                if (c0 + j < ncol) cfma(lp[j], t, X[(c0 + j) * p2 + k]);
+        }
+#pragma unroll
+    for (int j = 0; j < L2L_CPT; ++j) {
+        const int c = c0 + j;
+        if (c >= ncol) break;
+        cx<R> a0 = lp[j], a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
         const cx<R> *y = Y + ((e0 - e_first) * ncol + c) * p2 + r;
         const int64_t st = (int64_t)ncol * p2;
         int e = e0;
@@ -1786,11 +1800,15 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     auto rot_bytes = [&](int c) {
         return sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)c * RMAXC * p2);
     };
-    int cgr = std::max(1, std::min(4, fa_r.maxThreadsPerBlock / rows_pad));
+    // rotation kernel: in double precision groups of exactly p2 threads (a warp may straddle two
+    // column groups), so that no lane idles on a padded row in the FP64-bound stages; in single
+    // precision, where the kernel is latency-bound, rows padded to whole warps (more threads)
+    const int rows_rot = f32 ? rows_pad : p2;
+    int cgr = std::max(1, std::min(4, fa_r.maxThreadsPerBlock / rows_rot));
     while (cgr > 1 && rot_bytes(cgr) > budget) --cgr;
     const int pcr = std::min(M2L_CHUNK, cgr * RMAXC / ncol);
     const bool use_rot = chunked && h->m2l_rotation && h->R_D64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
-                         rows_pad <= fa_r.maxThreadsPerBlock;
+                         rows_rot <= fa_r.maxThreadsPerBlock;
     if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
         run_m2l_tc(h, (float *)C, (float *)D, nr, s);
     } else if (chunked) {
@@ -1811,7 +1829,7 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
                     const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
                     if (nch > 0) {
                         if (use_rot)
-                            k_m2l_rot<R, RMAXC><<<(unsigned)nch, rows_pad * cgr, rot_bytes(cgr), s>>>(
+                            k_m2l_rot<R, RMAXC><<<(unsigned)nch, rows_rot * cgr, rot_bytes(cgr), s>>>(
                                 c0, l, lmax, d, nr, pp, h->nbox, col0, nc, pcr, cgr, h->chunk_beg, h->chunk_cnt,
                                 h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD, RP, RZ, C, Y, e_first);
                         else if (tsm)
@@ -1824,7 +1842,7 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
                                 h->chunk_off, h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
                     }
                     CKL("k_m2l_chunks");
-                    const int ct = std::max(1, std::min(nc, 1024 / rows_pad));
+                    const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
                     k_l2l_reduce<R><<<(unsigned)Lv.n, rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
                         Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll,
                         Y, e_first, D);

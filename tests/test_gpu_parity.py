@@ -271,6 +271,26 @@ def test_autograd_solve_and_matvec_gradients(sphere_s4):
         assert abs(slope - fd) <= 1e-6 * abs(fd), (slope, fd)
 
 
+def test_far_field_and_cross_sections_match_oracle(sphere_s4):
+    """Far-field amplitude and the cross sections of a solved plane-wave problem evaluated on the
+    device against the oracle's evaluation of the same solution (sums in a different order)."""
+    o, g = sphere_s4
+    dirs, pols = fi.plane_wave_batch(2, seed=4)
+    b = g.plane_wave_rhs(dirs, pols)
+    x, _, _, st = g.solve(b, tol=1e-8)
+    assert st == 0
+    xh = x.cpu().numpy()
+    rh = fi.fibonacci_directions(7, seed=5)
+    F = g.far_field(x, rh)
+    for r in range(2):
+        np.testing.assert_allclose(F[r], o.far_field(xh[r], rh), rtol=1e-11, atol=1e-13 * np.abs(F[r]).max())
+    ce, cs, ca = g.cross_sections(x, dirs, pols, n_theta=24, n_phi=48)
+    for r in range(2):
+        ref = o.cross_sections(xh[r], dirs[r], pols[r], n_theta=24, n_phi=48)
+        np.testing.assert_allclose([ce[r], cs[r], ca[r]], ref, rtol=1e-9, atol=1e-12)
+        assert abs(ce[r] - cs[r] - ca[r]) < 0.1 * ce[r]  # optical theorem, to discretisation error
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
