@@ -204,7 +204,7 @@ def roofline(info, p, nr, n_dom, phases, precision):
     elif dom == "near_l2p_self":
         per_pair = NEAR_PAIR_CACHED if precision == "fp64" and nr < 4 else NEAR_PAIR
         flops = info["near_pairs"] * n_dom * (per_pair + NEAR_RHS * nr)
-        name = "near field + L2P + self (k_near)"
+        name = "near field + L2P + self (k_near / k_near_w)"
     else:
         flops, name = None, dom
     achieved = flops / (avg[dom] * 1e-3) / 1e12 if flops else None
@@ -229,15 +229,14 @@ def launches_per_matvec(lmax, nr, n_dom, precision):
     """Kernels per matvec: k_prep, P2M, k_m2m per level 3..l_max, the downward pass per level
     2..l_max (tensor path: k_round_tf32 then one k_m2l_tc per level; chunked: k_m2l_chunks or
     k_m2l_rot plus k_l2l_reduce per domain; many columns: k_m2l_multi), and the near field
-    (single precision with at least 4 right-hand sides: k_near_w and k_l2p_self; else one kernel)."""
+    (one kernel: k_near_w in single precision with at least 4 right-hand sides, else k_near*)."""
     if precision == "tf32" and tensor_path(nr):
         down = 1 + (lmax - 1)
     elif 3 * nr <= 24:
         down = (lmax - 1) * 2 * n_dom
     else:
         down = lmax - 1
-    near = 2 if precision != "fp64" and nr >= 4 else 1
-    return 2 + (lmax - 2) + down + near
+    return 2 + (lmax - 2) + down + 1
 
 
 def run_ours(args):

@@ -98,6 +98,7 @@ struct fmbem {
     double *pos = nullptr, *nrm = nullptr, *w = nullptr;  // [N][3], [N][3], [N]
     int32_t *dom = nullptr;                                // [N]
     float *pos_hi = nullptr, *pos_lo = nullptr, *nrm_f = nullptr;  // [N][3]
+    float4 *src_rec = nullptr;  // [N][3]: position hi + scatterer id, position lo + n_x, n_y n_z (k_near_w)
     // self blocks (user order): M = A_self [N][6][6], LU factors and pivots
     c64 *Mself = nullptr, *Mlu = nullptr;
     int8_t *piv = nullptr;
@@ -121,6 +122,7 @@ struct fmbem {
     int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;
     int4 *near_items = nullptr;  // warp work items of the near field (leaf, target offset, tg, nsl)
     int n_near_items = 0;
+    int *near_next = nullptr;    // unit counter of the persistent near-field kernel, reset per launch
     // near-field pair scalars (g, c) per leaf [side][source in the Neighbor list][target], double
     // precision; near_base[leaf] = pairs of the leaves before it
     void *near_cache64 = nullptr;

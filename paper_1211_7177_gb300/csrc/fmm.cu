@@ -1056,235 +1056,237 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
 }
 
 // ---------------------------------------------------------------- warp-independent near field
-// One warp owns one work item: a group of tg target nodes of one leaf, split over nsl source
-// slices (tg * nsl <= 32 lanes, nsl a power of two; lane = target + tg * slice), for one side
-// (domain 0, or the target's own scatterer) and one block of RB right-hand sides.  The items are
-// built once per tree (near_work_items) so that leaves of every size keep most lanes busy.  The
-// warp streams the sources of the leaf's Neighbor list through a warp-private shared-memory tile
-// of 32 (each lane stages one source: geometry and the RB densities of its side) and synchronises
-// only itself.  Per (source, target) pair it evaluates the kernel scalars once and applies them to
-// the RB right-hand sides; the slices are then summed by a fixed shuffle tree, and the slice-0 lane
-// of each target stores the side's three near-field rows (k_l2p_self adds the rest).
-template <typename R, int RB>
+// Steps 4-5 for many right-hand sides in single precision.  One warp owns one work item: a group
+// of tg target nodes of one leaf, split over nsl source slices (tg * nsl <= 32 lanes, nsl a power
+// of two; lane = target + tg * slice), for one side (domain 0, or the target's own scatterer) and
+// one block of RB right-hand sides.  The items are built once per tree (near_work_items) so that
+// leaves of every size keep most lanes busy.
+// - Near field: the warp streams the sources of the leaf's Neighbor list through two warp-private
+//   shared-memory tiles of NW_TS sources; while it computes on one, asynchronous copies (cp.async,
+//   16 bytes each: the 48-byte source record and the RB x 48 bytes of densities) fill the other,
+//   and the warp synchronises only itself.  Per (source, target) pair it evaluates the kernel
+//   scalars once and applies them to the RB right-hand sides.
+// - Far field (L2P, Eq. 2.23 first term): the leaf's local expansions of the block's 3 RB columns
+//   are staged in the same shared memory (in chunks of coefficients), and each slice adds the
+//   coefficients q = slice (mod nsl) of B_l2p[a][q] D[col][q] to its partial sums.
+// - The slices are summed by a fixed shuffle tree; the slice-0 lane of each target adds the side's
+//   rows of the analytic self block (App. B) applied to x in double precision and stores the
+//   side's three result rows.
+constexpr int NW_TS = 16;    // sources per tile
+static_assert(NW_TS == 16, "k_near_w stages a tile with two half-warps of 16 lanes");
+constexpr int NW_WARPS = 4;  // warps per block, one per SM sub-partition; each fetches its own units
+template <int RB>
 struct WarpTile {
-    V4<R> pa[32];           // position (high part) and scatterer id
-    V4<R> pb[32];           // position low part (double-float only) and n_x
-    V2<R> pn[32];           // n_y, n_z
-    V4<R> dv[RB][3][32];    // densities (v0, v1), (v2, q0), (q1, q2) of the side, per RHS
+    float4 geo[3][NW_TS];     // source record: position hi + scatterer id bits, position lo + n_x, n_y n_z
+    float4 dv[RB][3][NW_TS];  // densities (v0, v1), (v2, q0), (q1, q2) of the side, per RHS
 };
-constexpr int NW_WARPS = 4;  // warps (independent work items) per block
 
-template <typename R, bool DOUBLE_FLOAT, int RB>
-__global__ void __launch_bounds__(32 * NW_WARPS) k_near_w(
-    int64_t leaf_off, const int4 *__restrict__ items, int n_items, int64_t N, int64_t nr, int p2, int64_t nbox,
-    const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx, const R *pos_hi,
-    const R *pos_lo, const R *nrm, const int32_t *dom, const int32_t *perm, const cx<R> *dens, const DomainConsts *dc,
-    const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int RB>
+__global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
+    int64_t leaf_off, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N, int64_t nr,
+    const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
+    const float4 *__restrict__ rec, const cx<float> *dens, const DomainConsts *dc, const int32_t *perm, int p2,
+    int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
+    const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int rng_beg[NW_WARPS][32], rng_cum[NW_WARPS][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item_id = blockIdx.x * NW_WARPS + warp;
-    if (item_id >= n_items) return;  // no block-wide barrier below
-    WarpTile<R, RB> &T = reinterpret_cast<WarpTile<R, RB> *>(smem_raw)[warp];
+    WarpTile<RB> *T = reinterpret_cast<WarpTile<RB> *>(smem_raw) + 2 * warp;  // two buffers per warp
     int *rb_ = rng_beg[warp], *rc_ = rng_cum[warp];
-    const int4 it = items[item_id];
-    const int leaf = it.x, tg = it.z, nsl = it.w;
-    const int64_t g = leaf_off + leaf;
-    const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
-    if (lane == 0) {
-        int cum = 0;
-        for (int q = 0; q < nnb; ++q) {
-            const int b = nbr_idx[nb0 + q];
-            rb_[q] = nbeg[b];
-            rc_[q] = cum;
-            cum += nend[b] - nbeg[b];
+    // persistent warps: each takes the next unit (slab of side and RHS block, item) until none is
+    // left; units run slab by slab, so that a slab's densities stay in L2, and within a slab
+    // longest item first
+    for (;;) {
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(next_unit, 1);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= n_units) break;
+        const int yslab = unit / n_items, item_id = unit - yslab * n_items;
+        __syncwarp();  // the previous unit's shared-memory reads are done
+        const int4 it = items[item_id];
+        const int leaf = it.x, tg = it.z, nsl = it.w;
+        const int64_t g = leaf_off + leaf;
+        // the Neighbor leaves' node ranges and their running sum (a Neighbor list has at most 27 entries)
+        const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
+        {
+            int beg = 0, cnt = 0;
+            if (lane < nnb) {
+                const int b = nbr_idx[nb0 + lane];
+                beg = nbeg[b];
+                cnt = nend[b] - beg;
+            }
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane < nnb) { rb_[lane] = beg; rc_[lane] = incl - cnt; }
+            if (lane == nnb - 1) rc_[nnb] = incl;
         }
-        rc_[nnb] = cum;
-    }
-    __syncwarp();
-    const int side = blockIdx.y & 1;
-    const int64_t rb0 = (int64_t)(blockIdx.y >> 1) * RB;
-    const int nrb = (int)min((int64_t)RB, nr - rb0);
-    const int nsrc = rc_[nnb];
-    const int ti = lane % tg, sl = lane / tg;
-    const bool busy = sl < nsl;
-    const int a = nbeg[g] + it.y + ti;  // lanes past tg * nsl shadow a valid target and never store
-    const R sgn = side == 0 ? (R)-1 : (R)1;  // domain 0 sees the scatterer normal reversed
-    const R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2];
-    R alx = 0, aly = 0, alz = 0;
-    if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
-    const int adom = dom[a];
-    const R adom_r = (R)adom;
-    const cx<R> k = to<R>(dc[side == 0 ? 0 : adom].k);
-    cx<R> acc[RB][3];
-#pragma unroll
-    for (int rr = 0; rr < RB; ++rr)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[rr][c] = {0, 0};
-    for (int s0 = 0; s0 < nsrc; s0 += 32) {
+        const int side = yslab & 1;
+        const int64_t rb0 = (int64_t)(yslab >> 1) * RB;
+        const int nrb = (int)min((int64_t)RB, nr - rb0);
+        // densities of the RHS past the block's end stay zero in both tiles
+        for (int e = nrb * 3 * NW_TS + lane; e < RB * 3 * NW_TS; e += 32) {
+            (&T[0].dv[0][0][0])[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            (&T[1].dv[0][0][0])[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         __syncwarp();
-        {  // stage one source per lane
-            const int e = s0 + lane;
+        const int nsrc = rc_[nnb];
+        const int ti = lane % tg, sl = lane / tg;
+        const bool busy = sl < nsl;
+        const int a = nbeg[g] + it.y + ti;  // lanes past tg * nsl shadow a valid target and never store
+        const float sgn = side == 0 ? -1.f : 1.f;  // domain 0 sees the scatterer normal reversed
+        const float4 ra = rec[3 * a], rla = rec[3 * a + 1];
+        const int adom = __float_as_int(ra.w);
+        const cx<float> k = to<float>(dc[side == 0 ? 0 : adom].k);
+        const cx<float> *dside = dens + (side * nr + rb0) * N * 6;
+        // stage the tile of sources s0 .. s0 + NW_TS - 1 into buffer B: lane j (and j + 16) stages
+        // source j, the lower half the record and the first RB/2 right-hand sides' densities, the upper
+        // half the other RB/2; a lane's sources advance monotonically, so it follows its Neighbor range
+        const int j = lane & (NW_TS - 1), hh = lane >> 4;
+        const int64_t rstride = N * 6;
+        int qcur = 0;
+        auto stage = [&](WarpTile<RB> &B, int s0) {
+            const int e = s0 + j;
             if (e < nsrc) {
-                const int q = source_range(rc_, nnb, e);
-                const int i = rb_[q] + (e - rc_[q]);
-                T.pa[lane] = V4<R>{pos_hi[3 * i], pos_hi[3 * i + 1], pos_hi[3 * i + 2], (R)dom[i]};
-                R lo[3] = {0, 0, 0};
-                if (DOUBLE_FLOAT) { lo[0] = pos_lo[3 * i]; lo[1] = pos_lo[3 * i + 1]; lo[2] = pos_lo[3 * i + 2]; }
-                T.pb[lane] = V4<R>{lo[0], lo[1], lo[2], nrm[3 * i]};
-                T.pn[lane] = V2<R>{nrm[3 * i + 1], nrm[3 * i + 2]};
+                while (rc_[qcur + 1] <= e) ++qcur;
+                const int64_t i = rb_[qcur] + (e - rc_[qcur]);
+                if (hh == 0) {
+#pragma unroll
+                    for (int part = 0; part < 3; ++part) cp_async16(&B.geo[part][j], rec + 3 * i + part);
+                }
+                const cx<float> *src = dside + hh * (RB / 2) * rstride + 6 * i;
+#pragma unroll
+                for (int k = 0; k < RB / 2; ++k) {
+                    if (hh * (RB / 2) + k < nrb) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) cp_async16(&B.dv[hh * (RB / 2) + k][c][j], src + k * rstride + 2 * c);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        cx<float> acc[RB][3];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[rr][c] = {0, 0};
+        const int ntile = (nsrc + NW_TS - 1) / NW_TS;
+        stage(T[0], 0);
+        for (int t = 0; t < ntile; ++t) {
+            if (t + 1 < ntile) stage(T[(t + 1) & 1], (t + 1) * NW_TS);
+            else cp_async_commit();  // an empty group keeps "all but the newest group done" meaning tile t
+            cp_async_wait1();
+            __syncwarp();
+            const WarpTile<RB> &B = T[t & 1];
+            const int ns = busy ? min(NW_TS, nsrc - t * NW_TS) : 0;
+            for (int u = sl; u < ns; u += nsl) {
+                const float4 pa = B.geo[0][u], pb = B.geo[1][u], pc = B.geo[2][u];
+                if (side == 1 && __float_as_int(pa.w) != adom) continue;  // a scatterer's sum runs over its own nodes
+                const float rv3[3] = {(pa.x - ra.x) + (pb.x - rla.x), (pa.y - ra.y) + (pb.y - rla.y),
+                                      (pa.z - ra.z) + (pb.z - rla.z)};
+                const float R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
+                const float inv = R2 > 0.f ? rsqrt_(R2) : 0.f;  // the node itself drops out
+                const float Rr = R2 * inv;
+                const float nn[3] = {sgn * pb.w, sgn * pc.x, sgn * pc.y};
+                const float nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
+                const float w[3] = {nn[1] * rv3[2] - nn[2] * rv3[1], nn[2] * rv3[0] - nn[0] * rv3[2],
+                                    nn[0] * rv3[1] - nn[1] * rv3[0]};
+                cx<float> gs, cs;
+                pair_scalars<float>(inv, Rr, k, gs, cs);
 #pragma unroll
                 for (int rr = 0; rr < RB; ++rr) {
-                    if (rr < nrb) {
-                        const cx<R> *dn = dens + ((side * nr + rb0 + rr) * N + i) * 6;
+                    const float4 a0 = B.dv[rr][0][u], a1 = B.dv[rr][1][u], a2 = B.dv[rr][2][u];
+                    const cx<float> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
+                    const cx<float> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                    cross_apply<float>(w, nrv, gs, cs, v, qv, acc[rr]);
+                }
+            }
+            __syncwarp();  // the next stage overwrites this buffer
+        }
+        // far field: the local expansions of this side's domain at the leaf, for the block's columns
+        // 3 rb0 .. 3 (rb0 + nrb) - 1, staged through the tiles' shared memory in chunks of qc
+        // coefficients; on the scatterer side the warp's targets may lie in several scatterers, which
+        // are taken in turn
+        {
+            cx<float> *Ds = reinterpret_cast<cx<float> *>(T);
+            const int qc = min(p2, (int)(2 * sizeof(WarpTile<RB>) / sizeof(cx<float>)) / (3 * RB));
+            const int ncol = 3 * nrb;
+            const int64_t ncols = 3 * nr;
+            const int mydom = side == 0 ? 0 : adom;
+            const cx<float> *Ba = Bl2p + ((int64_t)side * N + a) * p2;
+            unsigned pending = 0xffffffffu;
+            while (pending) {
+                const int d = __shfl_sync(0xffffffffu, mydom, __ffs(pending) - 1);
+                const bool mine = mydom == d;
+                pending &= ~__ballot_sync(0xffffffffu, mine);
+                const cx<float> *Dg = D + ((int64_t)d * nbox + g) * ncols * p2 + 3 * rb0 * p2;
+                for (int q0 = 0; q0 < p2; q0 += qc) {
+                    const int qn = min(qc, p2 - q0);
+                    __syncwarp();
+                    for (int e = lane; e < ncol * qn; e += 32) {
+                        const int col = e / qn, qq = e - col * qn;
+                        Ds[col * qc + qq] = Dg[(int64_t)col * p2 + q0 + qq];
+                    }
+                    __syncwarp();
+                    if (busy && mine) {
+                        for (int qq = sl; qq < qn; qq += nsl) {
+                            const cx<float> bq = Ba[q0 + qq];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            T.dv[rr][c][lane] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
-                    } else {
+                            for (int rr = 0; rr < RB; ++rr) {
+                                if (rr < nrb) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) T.dv[rr][c][lane] = V4<R>{0, 0, 0, 0};
+                                    for (int c = 0; c < 3; ++c) cfma(acc[rr][c], bq, Ds[(3 * rr + c) * qc + qq]);
+                                }
+                            }
+                        }
                     }
                 }
             }
         }
-        __syncwarp();
-        const int ns = busy ? min(32, nsrc - s0) : 0;
-        for (int u = sl; u < ns; u += nsl) {
-            const V4<R> pa = T.pa[u], pb = T.pb[u];
-            const V2<R> pn = T.pn[u];
-            if (side == 1 && pa.w != adom_r) continue;  // a scatterer's sum runs over its own nodes
-            R rv3[3] = {pa.x - ax, pa.y - ay, pa.z - az};
-            if (DOUBLE_FLOAT) { rv3[0] += pb.x - alx; rv3[1] += pb.y - aly; rv3[2] += pb.z - alz; }
-            const R R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
-            const R inv = R2 > (R)0 ? rsqrt_(R2) : (R)0;  // the node itself drops out
-            const R Rr = R2 * inv;
-            const R nn[3] = {sgn * pb.w, sgn * pn.x, sgn * pn.y};
-            const R nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
-            const R w[3] = {nn[1] * rv3[2] - nn[2] * rv3[1], nn[2] * rv3[0] - nn[0] * rv3[2],
-                            nn[0] * rv3[1] - nn[1] * rv3[0]};
-            cx<R> gs, cs;
-            pair_scalars<R>(inv, Rr, k, gs, cs);
+        // sum the slices of each target: lane ti + tg * sl, fixed tree over sl
+        for (int off = nsl >> 1; off >= 1; off >>= 1) {
 #pragma unroll
-            for (int rr = 0; rr < RB; ++rr) {
-                const V4<R> a0 = T.dv[rr][0][u], a1 = T.dv[rr][1][u], a2 = T.dv[rr][2][u];
-                const cx<R> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
-                const cx<R> qv[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
-                cross_apply<R>(w, nrv, gs, cs, v, qv, acc[rr]);
-            }
-        }
-    }
-    // sum the slices of each target: lane ti + tg * sl, fixed tree over sl
-    for (int off = nsl >> 1; off >= 1; off >>= 1) {
+            for (int rr = 0; rr < RB; ++rr)
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const R re = __shfl_down_sync(0xffffffffu, acc[rr][c].re, off * tg);
-                const R im = __shfl_down_sync(0xffffffffu, acc[rr][c].im, off * tg);
-                if (sl < off) { acc[rr][c].re += re; acc[rr][c].im += im; }
-            }
-    }
-    if (sl == 0) {  // the side's near-field rows; k_l2p_self adds the far field and the self block
-        const int64_t u = perm[a];
-#pragma unroll
-        for (int rr = 0; rr < RB; ++rr) {
-            if (rr >= nrb) break;
-            c64 *ya = y + ((rb0 + rr) * N + u) * 6 + 3 * side;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ya[c] = c64{(double)acc[rr][c].re, (double)acc[rr][c].im};
-        }
-    }
-}
-
-// Far field (L2P, Eq. 2.23 first term) and self block (App. B) for many right-hand sides, added to
-// the near-field rows k_near_w stored: for one leaf, one side and a tile of L2P_MT columns,
-//   y[col][a][3 side + c] += sum_q B_l2p[side][a][q] D[d][leaf][col][q]
-//                            + sum_{c' < 3} M[a][3 side + c][c'] x[a][c'] + M[a][3 side + c][3 + c] x[a][3 + c]
-// (the Psi columns of each self block row are diagonal).  The L2P part is a (targets x p^2) by
-// (p^2 x columns) product: each thread owns targets tgr + 16 i and columns cgp + 12 j (i, j < 4),
-// with the shared rows padded to p^2 + 1 so that the 16 target rows a warp reads fall in distinct
-// banks.  The self part runs in double precision.  On the scatterer side d is each target's own
-// scatterer, so the leaf's scatterers are taken in turn.
-constexpr int L2P_MT = 48;  // columns per block (16 right-hand sides)
-constexpr int L2P_NT = 64;  // targets per pass
-template <typename R>
-__global__ void __launch_bounds__(192) k_l2p_self(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, int J,
-                                                  const int32_t *nbeg, const int32_t *nend, const int32_t *dom,
-                                                  const int32_t *perm, const cx<R> *Bl2p, const cx<R> *D,
-                                                  const c64 *Mself, const c64 *x, c64 *y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int ld = p2 + 1;                              // padded row length
-    cx<R> *Bs = reinterpret_cast<cx<R> *>(smem_raw);  // [L2P_NT][ld]
-    cx<R> *Ds = Bs + L2P_NT * ld;                       // [L2P_MT][ld]
-    __shared__ int present;
-    const int64_t g = leaf_off + blockIdx.x;
-    const int side = blockIdx.y;
-    const int ncols = (int)(3 * nr), col0 = blockIdx.z * L2P_MT;
-    const int nh = min(L2P_MT, ncols - col0);
-    const int t0 = nbeg[g], t1 = nend[g];
-    const int tgr = threadIdx.x % 16, cgp = threadIdx.x / 16;  // targets tgr + 16 i, columns cgp + 12 j
-    for (int tb = t0; tb < t1; tb += L2P_NT) {
-        const int nt = min(L2P_NT, t1 - tb);
-        for (int d = side == 0 ? 0 : 1; d <= (side == 0 ? 0 : J); ++d) {
-            __syncthreads();
-            if (threadIdx.x == 0) present = 0;
-            __syncthreads();
-            if (threadIdx.x < nt && (side == 0 || dom[tb + threadIdx.x] == d)) present = 1;
-            __syncthreads();
-            if (!present) continue;
-            for (int e = threadIdx.x; e < L2P_NT * p2; e += blockDim.x) {
-                const int t = e / p2, q = e - t * p2;
-                cx<R> v = {0, 0};
-                if (t < nt && (side == 0 || dom[tb + t] == d)) v = Bl2p[((int64_t)side * N + tb + t) * p2 + q];
-                Bs[t * ld + q] = v;
-            }
-            for (int e = threadIdx.x; e < L2P_MT * p2; e += blockDim.x) {
-                const int c = e / p2, q = e - c * p2;
-                Ds[c * ld + q] = c < nh ? D[(((int64_t)d * nbox + g) * ncols + col0 + c) * p2 + q] : cx<R>{0, 0};
-            }
-            __syncthreads();
-            cx<R> acc[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = {0, 0};
-#pragma unroll 4
-            for (int q = 0; q < p2; ++q) {
-                cx<R> bt[4], dc4[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) bt[i] = Bs[(tgr + 16 * i) * ld + q];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) dc4[j] = Ds[(cgp + 12 * j) * ld + q];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) cfma(acc[i][j], bt[i], dc4[j]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int t = tgr + 16 * i;
-                if (t >= nt) break;
-                const int a = tb + t;
-                if (side == 1 && dom[a] != d) continue;
-                const int64_t u = perm[a];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int col = cgp + 12 * j;
-                    if (col >= nh) break;
-                    const int64_t r = (col0 + col) / 3;
-                    const int c = (col0 + col) - 3 * (int)r, row = 3 * side + c;
-                    const c64 *M = Mself + 36 * u + 6 * row;
-                    const c64 *xa = x + (r * N + u) * 6;
-                    c64 *ya = y + (r * N + u) * 6 + row;
-                    c64 sacc = *ya;
-                    sacc += c64{(double)acc[i][j].re, (double)acc[i][j].im};
-                    cfma(sacc, M[0], xa[0]);
-                    cfma(sacc, M[1], xa[1]);
-                    cfma(sacc, M[2], xa[2]);
-                    cfma(sacc, M[3 + c], xa[3 + c]);
-                    *ya = sacc;
+                for (int c = 0; c < 3; ++c) {
+                    const float re = __shfl_down_sync(0xffffffffu, acc[rr][c].re, off * tg);
+                    const float im = __shfl_down_sync(0xffffffffu, acc[rr][c].im, off * tg);
+                    if (sl < off) { acc[rr][c].re += re; acc[rr][c].im += im; }
                 }
-            }
+        }
+        // the near + far sums of the slice-0 lanes go to shared memory (the tiles are free), and the
+        // whole warp adds the side's rows of the self block (its Psi columns are diagonal) in double
+        // precision and stores them, one (target, RHS, component) per lane and pass
+        cx<float> *Ys = reinterpret_cast<cx<float> *>(T);  // [target][RB][3]
+        __syncwarp();
+        if (sl == 0) {
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Ys[(ti * RB + rr) * 3 + c] = acc[rr][c];
+        }
+        __syncwarp();
+        for (int o = lane; o < tg * 3 * nrb; o += 32) {
+            const int t = o / (3 * nrb), rem = o - t * 3 * nrb, rr = rem / 3, c = rem - 3 * rr;
+            const int64_t u = perm[nbeg[g] + it.y + t];
+            const c64 *M = Mself + 36 * u + 18 * side + 6 * c;
+            const c64 *xa = x + ((rb0 + rr) * N + u) * 6;
+            const cx<float> f = Ys[(t * RB + rr) * 3 + c];
+            c64 v = {(double)f.re, (double)f.im};
+            cfma(v, M[0], xa[0]);
+            cfma(v, M[1], xa[1]);
+            cfma(v, M[2], xa[2]);
+            cfma(v, M[3 + c], xa[3 + c]);
+            y[((rb0 + rr) * N + u) * 6 + 3 * side + c] = v;
         }
     }
 }
@@ -1693,7 +1695,14 @@ void near_work_items(fmbem *h, cudaStream_t s) {
     CK(cudaMemcpyAsync(nb.data(), h->box_nbeg + L.off, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ne.data(), h->box_nend + L.off, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    std::vector<int32_t> ns(L.n + 1), ni;
+    CK(cudaMemcpyAsync(ns.data(), h->nbr_start, sizeof(int32_t) * (L.n + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ni.resize(std::max(ns[L.n], 1));
+    CK(cudaMemcpyAsync(ni.data(), h->nbr_idx, sizeof(int32_t) * ns[L.n], cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     std::vector<int4> items;
+    std::vector<int64_t> cost;  // a lane's pair count: the leaf's Neighbor sources over the slices
     for (int64_t leaf = 0; leaf < L.n; ++leaf) {
         const int nt = ne[leaf] - nb[leaf];
         if (nt <= 0) continue;
@@ -1707,10 +1716,23 @@ void near_work_items(fmbem *h, cudaStream_t s) {
             if ((double)W / p < best - 1e-12) { best = (double)W / p; bestW = W; bestP = p; }
         }
         const int tg = (nt + bestW - 1) / bestW;
-        for (int t = 0; t < nt; t += tg) items.push_back(int4{(int)leaf, t, std::min(tg, nt - t), bestP});
+        int64_t nsrc = 0;
+        for (int q = ns[leaf]; q < ns[leaf + 1]; ++q) nsrc += ne[ni[q] - L.off] - nb[ni[q] - L.off];
+        for (int t = 0; t < nt; t += tg) {
+            items.push_back(int4{(int)leaf, t, std::min(tg, nt - t), bestP});
+            cost.push_back((nsrc + bestP - 1) / bestP);
+        }
     }
+    // longest items first: blocks start in index order, so the last ones to start are short
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return cost[u] > cost[v]; });
+    std::vector<int4> sorted(items.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
+    items.swap(sorted);
     h->n_near_items = (int)items.size();
     h->near_items = (int4 *)dev_alloc(h, sizeof(int4) * items.size());
+    h->near_next = (int *)dev_alloc(h, sizeof(int));
     CK(cudaMemcpyAsync(h->near_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
 }
@@ -1920,22 +1942,26 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // double precision, the block-cooperative kernels (more threads per leaf, FP64 pipe busier)
     auto launch_w = [&](auto kern, int rb, size_t tile_bytes) {
         if (h->near_items == nullptr) throw fmbem_error{FMBEM_ERR_CUDA, "near-field work items were not built"};
-        const size_t smw = tile_bytes * NW_WARPS;
+        const size_t smw = 2 * tile_bytes * NW_WARPS;  // two tiles per warp
+        const int64_t units = (int64_t)h->n_near_items * 2 * ((nr + rb - 1) / rb);
+        if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
-        kern<<<dim3((unsigned)((h->n_near_items + NW_WARPS - 1) / NW_WARPS), (unsigned)(2 * ((nr + rb - 1) / rb))),
-               32 * NW_WARPS, smw, s>>>(L.off, h->near_items, h->n_near_items, N, nr, p2, h->nbox, h->box_nbeg,
-                                        h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc,
-                                        Bl2p, D, h->Mself, x, y);
+        int dev = 0, nsm = 0, per_sm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * NW_WARPS, smw));
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((units + NW_WARPS - 1) / NW_WARPS,
+                                                                    (int64_t)std::max(per_sm, 1) * nsm));
+        CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
+        kern<<<(unsigned)grid, 32 * NW_WARPS, smw, s>>>(
+            L.off, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
+            h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, dc, h->perm, p2, h->nbox,
+            (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_w");
-        const size_t sml = sizeof(cx<R>) * (size_t)(p2 + 1) * (L2P_NT + L2P_MT);
-        CK(cudaFuncSetAttribute(k_l2p_self<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml));
-        k_l2p_self<R><<<dim3((unsigned)L.n, 2, (unsigned)((3 * nr + L2P_MT - 1) / L2P_MT)), (L2P_NT / 4) * (L2P_MT / 4),
-                        sml, s>>>(L.off, N, nr, p2, h->nbox, J, h->box_nbeg, h->box_nend, h->dom, h->perm, Bl2p, D,
-                                  h->Mself, x, y);
     };
     if constexpr (sizeof(R) == 4) {
-        if (nr >= 8) launch_w(k_near_w<R, true, 8>, 8, sizeof(WarpTile<R, 8>));
-        else if (nr >= 4) launch_w(k_near_w<R, true, 4>, 4, sizeof(WarpTile<R, 4>));
+        if (nr >= 8) launch_w(k_near_w<8>, 8, sizeof(WarpTile<8>));
+        else if (nr >= 4) launch_w(k_near_w<4>, 4, sizeof(WarpTile<4>));
         else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
             k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                           h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens,

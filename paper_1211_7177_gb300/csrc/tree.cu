@@ -265,7 +265,7 @@ __global__ void k_farfield(int64_t nb, int64_t off, int l, const uint64_t *gkey,
 // sorted copies of the node geometry, double-float positions for the single-precision passes
 __global__ void k_sorted_geometry(int64_t N, const int32_t *perm, const double *upos, const double *unrm, const double *uw,
                                   const int32_t *udom, double *pos, double *nrm, double *w, int32_t *dom, int32_t *iperm,
-                                  float *hi, float *lo, float *nf) {
+                                  float *hi, float *lo, float *nf, float4 *rec) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     int32_t u = perm[i];
@@ -281,6 +281,11 @@ __global__ void k_sorted_geometry(int64_t N, const int32_t *perm, const double *
     }
     w[i] = uw[u];
     dom[i] = udom[u];
+    // the single-precision near field's 48-byte source record: (x_hi, y_hi, z_hi, scatterer id
+    // bits), (x_lo, y_lo, z_lo, n_x), (n_y, n_z, 0, 0)
+    rec[3 * i] = make_float4(hi[3 * i], hi[3 * i + 1], hi[3 * i + 2], __int_as_float(udom[u]));
+    rec[3 * i + 1] = make_float4(lo[3 * i], lo[3 * i + 1], lo[3 * i + 2], nf[3 * i]);
+    rec[3 * i + 2] = make_float4(nf[3 * i + 1], nf[3 * i + 2], 0.f, 0.f);
 }
 
 // target box of every FF CSR entry
@@ -524,8 +529,9 @@ void build_tree(fmbem *h, cudaStream_t s) {
     h->pos_hi = (float *)dev_alloc(h, sizeof(float) * 3 * N);
     h->pos_lo = (float *)dev_alloc(h, sizeof(float) * 3 * N);
     h->nrm_f = (float *)dev_alloc(h, sizeof(float) * 3 * N);
+    h->src_rec = (float4 *)dev_alloc(h, sizeof(float4) * 3 * N);
     k_sorted_geometry<<<nblk(N, TB), TB, 0, s>>>(N, h->perm, h->upos, h->unrm, h->uw, h->udom, h->pos, h->nrm, h->w, h->dom,
-                                                 h->iperm, h->pos_hi, h->pos_lo, h->nrm_f);
+                                                 h->iperm, h->pos_hi, h->pos_lo, h->nrm_f, h->src_rec);
     CKL("k_sorted_geometry");
     CK(cudaStreamSynchronize(s));
     for (int l = 0; l <= KEY_LEVELS; ++l) {
