@@ -122,7 +122,10 @@ struct fmbem {
     int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;
     int4 *near_items = nullptr;  // warp work items of the near field (leaf, target offset, tg, nsl)
     int n_near_items = 0;
-    int *near_next = nullptr;    // unit counter of the persistent near-field kernel, reset per launch
+    int *near_next = nullptr;    // unit counter of the persistent near-field kernels, reset per launch
+    int4 *near_groups = nullptr;  // target groups of the lane-per-RHS near field (leaf, target offset, count, -):
+                                  // n_near_groups in leaf order, then the same sorted by pair work
+    int n_near_groups = 0;
     // near-field pair scalars (g, c) per leaf [side][source in the Neighbor list][target], double
     // precision; near_base[leaf] = pairs of the leaves before it
     void *near_cache64 = nullptr;

@@ -53,6 +53,25 @@ __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm,
     }
 }
 
+// The single-precision densities node-major within blocks of 32 right-hand sides,
+// densT[side][block][node][32][6], for the lane-per-RHS near field (a source's 32 right-hand sides
+// are contiguous): grid (node tiles of 16, block, side), 32 x 16 entries of 48 bytes per block
+// through shared memory, read and written in whole rows.
+__global__ void __launch_bounds__(256) k_dens_node_major(int64_t N, int64_t nr, const float4 *dens, float4 *densT) {
+    __shared__ float4 t[32][16 * 3 + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * 16, rb = blockIdx.y, side = blockIdx.z, nb = gridDim.y;
+    const int ni = (int)min((int64_t)16, N - i0);
+    for (int e = threadIdx.x; e < 32 * 48; e += blockDim.x) {  // row r: 16 nodes x 3 float4
+        const int rl = e / 48, k = e - rl * 48;
+        if (k < 3 * ni) t[rl][k] = dens[((side * nr + rb * 32 + rl) * N + i0) * 3 + k];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 96; e += blockDim.x) {  // node i: 32 right-hand sides x 3 float4
+        const int il = e / 96, k = e - il * 96, rl = k / 3, c = k - rl * 3;
+        if (il < ni) densT[((side * nb + rb) * N + i0 + il) * 96 + k] = t[rl][il * 3 + c];
+    }
+}
+
 // ---------------------------------------------------------------- P2M (Eqs. 2.18-2.19)
 // grid (leaf, domain, rhs); thread per coefficient nm; C[d][g][3r+i][nm].  The dipole and monopole
 // of component c enter as sum_k W_k(c) B_k with the node weights W_0 = q_c and
@@ -1091,6 +1110,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 template <int RB>
 __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
     int64_t leaf_off, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N, int64_t nr,
+    int64_t rhs_base,
     const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
     const float4 *__restrict__ rec, const cx<float> *dens, const DomainConsts *dc, const int32_t *perm, int p2,
     int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
@@ -1131,7 +1151,7 @@ __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
             if (lane == nnb - 1) rc_[nnb] = incl;
         }
         const int side = yslab & 1;
-        const int64_t rb0 = (int64_t)(yslab >> 1) * RB;
+        const int64_t rb0 = rhs_base + (int64_t)(yslab >> 1) * RB;
         const int nrb = (int)min((int64_t)RB, nr - rb0);
         // densities of the RHS past the block's end stay zero in both tiles
         for (int e = nrb * 3 * NW_TS + lane; e < RB * 3 * NW_TS; e += 32) {
@@ -1238,8 +1258,10 @@ __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
                     }
                     __syncwarp();
                     if (busy && mine) {
+                        cx<float> bn = Ba[q0 + min(sl, qn - 1)];  // the next coefficient's load is in flight
                         for (int qq = sl; qq < qn; qq += nsl) {
-                            const cx<float> bq = Ba[q0 + qq];
+                            const cx<float> bq = bn;
+                            if (qq + nsl < qn) bn = Ba[q0 + qq + nsl];
 #pragma unroll
                             for (int rr = 0; rr < RB; ++rr) {
                                 if (rr < nrb) {
@@ -1287,6 +1309,213 @@ __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
             cfma(v, M[2], xa[2]);
             cfma(v, M[3 + c], xa[3 + c]);
             y[((rb0 + rr) * N + u) * 6 + 3 * side + c] = v;
+        }
+    }
+}
+
+// Steps 4-5 for 32 or more right-hand sides in single precision, one lane per right-hand side.
+// A warp owns one unit: a group of at most NR_TT targets of one leaf, one side and a block of 32
+// right-hand sides.  The sources of the leaf's Neighbor list go by in tiles of 32:
+// - pair phase: lane l takes source l of the tile and evaluates the kernel scalars (w = n x r,
+//   n.r, g, c) against every target of the group into shared memory (zero where the source lies in
+//   another scatterer on the scatterer side, or past the list's end);
+// - right-hand-side phase: every lane reads its own densities of each source (the next source's
+//   loads are in flight while the current one is applied) and applies the broadcast scalars of all
+//   targets, so a pair's scalars serve 32 right-hand sides and no lane idles.
+// Then L2P (Eq. 2.23 first term) from the lane's three columns of the leaf's local expansion, and
+// the side's rows of the analytic self block (App. B) in double precision; each lane stores its
+// right-hand side's rows.
+constexpr int NR_TT = 8;   // targets per unit
+constexpr int NR_WARPS = 4;
+struct RhsTile {
+    float4 ps[NR_TT][32][2];  // (w, n.r), (g, c) per target and source of the tile
+    float4 tp[NR_TT][2];      // target position hi + scatterer id bits, position lo
+    float2 tk[NR_TT];         // the wavenumber each target sees on this side
+};
+
+__global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
+    int64_t leaf_off, const int4 *__restrict__ groups, int n_groups, int n_units, int *next_unit, int64_t N,
+    int64_t nr, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
+    const float4 *__restrict__ rec, const cx<float> *densT, const DomainConsts *dc, const int32_t *perm, int p2,
+    int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
+    const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y) {
+    __shared__ RhsTile tiles[NR_WARPS];
+    __shared__ int rng_beg[NR_WARPS][32], rng_cum[NR_WARPS][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    RhsTile &S = tiles[warp];
+    int *rb_ = rng_beg[warp], *rc_ = rng_cum[warp];
+    for (;;) {
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(next_unit, 1);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= n_units) break;
+        const int slab = unit / n_groups, grp = unit - slab * n_groups;
+        const int side = slab & 1;
+        const int64_t r = (int64_t)(slab >> 1) * 32 + lane;  // this lane's right-hand side
+        __syncwarp();  // the previous unit's shared-memory reads are done
+        const int4 gi = groups[slab == 2 * (nr / 32) - 1 ? n_groups + grp : grp];  // last slab: longest first
+        const int leaf = gi.x, ntg = gi.z;
+        const int64_t g = leaf_off + leaf;
+        const int tbase = nbeg[g] + gi.y;
+        const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
+        {
+            int beg = 0, cnt = 0;
+            if (lane < nnb) {
+                const int b = nbr_idx[nb0 + lane];
+                beg = nbeg[b];
+                cnt = nend[b] - beg;
+            }
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane < nnb) { rb_[lane] = beg; rc_[lane] = incl - cnt; }
+            if (lane == nnb - 1) rc_[nnb] = incl;
+        }
+        if (lane < ntg) {
+            const int a = tbase + lane;
+            const float4 ta = rec[3 * a];
+            S.tp[lane][0] = ta;
+            S.tp[lane][1] = rec[3 * a + 1];
+            const cx<float> kt = to<float>(dc[side == 0 ? 0 : __float_as_int(ta.w)].k);
+            S.tk[lane] = make_float2(kt.re, kt.im);
+        }
+        __syncwarp();
+        const int nsrc = rc_[nnb];
+        const float sgn = side == 0 ? -1.f : 1.f;  // domain 0 sees the scatterer normal reversed
+        const int64_t nblk = nr / 32;  // node-major densities: this lane's of source i at dl + 96 i
+        const float4 *dl =
+            reinterpret_cast<const float4 *>(densT + (((side * nblk + (slab >> 1)) * N) * 32 + lane) * 6);
+        cx<float> acc[NR_TT][3];
+#pragma unroll
+        for (int t = 0; t < NR_TT; ++t)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[t][c] = {0, 0};
+        int qcur = 0;
+        for (int s0 = 0; s0 < nsrc; s0 += 32) {
+            // pair phase: source s0 + lane against the group's targets
+            const int e = s0 + lane;
+            const bool valid = e < nsrc;
+            int i = rb_[0];
+            if (valid) {
+                while (rc_[qcur + 1] <= e) ++qcur;
+                i = rb_[qcur] + (e - rc_[qcur]);
+            }
+            const float4 pa = rec[3 * i], pb = rec[3 * i + 1], pc = rec[3 * i + 2];
+            const int sdom = __float_as_int(pa.w);
+            const float nn[3] = {sgn * pb.w, sgn * pc.x, sgn * pc.y};
+#pragma unroll
+            for (int t = 0; t < NR_TT; ++t) {
+                if (t < ntg) {
+                    const float4 ta = S.tp[t][0], tl = S.tp[t][1];
+                    const float rv3[3] = {(pa.x - ta.x) + (pb.x - tl.x), (pa.y - ta.y) + (pb.y - tl.y),
+                                          (pa.z - ta.z) + (pb.z - tl.z)};
+                    const float R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
+                    const float inv = R2 > 0.f ? rsqrt_(R2) : 0.f;  // the node itself drops out
+                    const float Rr = R2 * inv;
+                    const float nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
+                    const float2 kt = S.tk[t];
+                    cx<float> gs, cs;
+                    pair_scalars<float>(inv, Rr, cx<float>{kt.x, kt.y}, gs, cs);
+                    if (!valid || (side == 1 && sdom != __float_as_int(ta.w))) gs = cs = cx<float>{0.f, 0.f};
+                    S.ps[t][lane][0] = make_float4(nn[1] * rv3[2] - nn[2] * rv3[1], nn[2] * rv3[0] - nn[0] * rv3[2],
+                                                   nn[0] * rv3[1] - nn[1] * rv3[0], nrv);
+                    S.ps[t][lane][1] = make_float4(gs.re, gs.im, cs.re, cs.im);
+                }
+            }
+            __syncwarp();
+            // right-hand-side phase
+            const int nsv = min(32, nsrc - s0);
+            int ic = __shfl_sync(0xffffffffu, i, 0);
+            float4 c0 = dl[96 * ic], c1 = dl[96 * ic + 1], c2 = dl[96 * ic + 2];
+            for (int sv = 0; sv < nsv; ++sv) {
+                float4 n0 = c0, n1 = c1, n2 = c2;
+                const int in = __shfl_sync(0xffffffffu, i, (sv + 1) & 31);
+                if (sv + 1 < nsv) { n0 = dl[96 * in]; n1 = dl[96 * in + 1]; n2 = dl[96 * in + 2]; }
+                const cx<float> v[3] = {{c0.x, c0.y}, {c0.z, c0.w}, {c1.x, c1.y}};
+                const cx<float> qv[3] = {{c1.z, c1.w}, {c2.x, c2.y}, {c2.z, c2.w}};
+#pragma unroll
+                for (int t = 0; t < NR_TT; ++t) {
+                    if (t < ntg) {
+                        const float4 p0 = S.ps[t][sv][0], p1 = S.ps[t][sv][1];
+                        const float w[3] = {p0.x, p0.y, p0.z};
+                        cross_apply<float>(w, p0.w, cx<float>{p1.x, p1.y}, cx<float>{p1.z, p1.w}, v, qv, acc[t]);
+                    }
+                }
+                c0 = n0; c1 = n1; c2 = n2;
+            }
+            __syncwarp();  // the next tile's pair phase overwrites the scalars
+        }
+        // far field: this lane's three columns of the leaf's local expansion of the side's domain
+        // (on the scatterer side each target's own scatterer: the group's scatterers in turn); the
+        // targets' L2P rows are staged in the scalars' shared memory, chunks of qc coefficients, and
+        // the lane's expansion coefficients are loaded two coefficients ahead
+        {
+            cx<float> *Bs = reinterpret_cast<cx<float> *>(&S.ps[0][0][0]);
+            constexpr int BS_CAP = (int)(sizeof(S.ps) / sizeof(cx<float>));
+            const int qc = min(p2, BS_CAP / NR_TT);
+            const int64_t ncols = 3 * nr;
+            unsigned pending = (1u << ntg) - 1u;
+            while (pending) {
+                const int d = side == 0 ? 0 : __float_as_int(S.tp[__ffs(pending) - 1][0].w);
+                unsigned mine = 0;
+                for (int t = 0; t < ntg; ++t)
+                    if (side == 0 || __float_as_int(S.tp[t][0].w) == d) mine |= 1u << t;
+                pending &= ~mine;
+                const cx<float> *Dr = D + (((int64_t)d * nbox + g) * ncols + 3 * r) * p2;
+                for (int q0 = 0; q0 < p2; q0 += qc) {
+                    const int qn = min(qc, p2 - q0);
+                    __syncwarp();
+                    for (int e = lane; e < ntg * qn; e += 32) {
+                        const int t = e / qn, qq = e - t * qn;
+                        Bs[t * qc + qq] = Bl2p[((int64_t)side * N + tbase + t) * p2 + q0 + qq];
+                    }
+                    __syncwarp();
+                    cx<float> d1[3], d2[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        d1[c] = Dr[c * p2 + q0];
+                        d2[c] = Dr[c * p2 + q0 + min(1, qn - 1)];
+                    }
+                    for (int qq = 0; qq < qn; ++qq) {
+                        const cx<float> dq[3] = {d1[0], d1[1], d1[2]};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            d1[c] = d2[c];
+                            if (qq + 2 < qn) d2[c] = Dr[c * p2 + q0 + qq + 2];
+                        }
+#pragma unroll
+                        for (int t = 0; t < NR_TT; ++t) {
+                            if ((mine >> t) & 1u) {
+                                const cx<float> b = Bs[t * qc + qq];
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) cfma(acc[t][c], b, dq[c]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // the side's rows of the self block (Psi columns diagonal) in double precision, stored
+#pragma unroll
+        for (int t = 0; t < NR_TT; ++t) {
+            if (t < ntg) {
+                const int64_t u = perm[tbase + t];
+                const c64 *M = Mself + 36 * u + 18 * side;
+                const c64 *xa = x + (r * N + u) * 6;
+                c64 *ya = y + (r * N + u) * 6 + 3 * side;
+                const c64 x0 = xa[0], x1 = xa[1], x2 = xa[2];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    c64 v = {(double)acc[t][c].re, (double)acc[t][c].im};
+                    cfma(v, M[6 * c], x0);
+                    cfma(v, M[6 * c + 1], x1);
+                    cfma(v, M[6 * c + 2], x2);
+                    cfma(v, M[6 * c + 3 + c], xa[3 + c]);
+                    ya[c] = v;
+                }
+            }
         }
     }
 }
@@ -1734,6 +1963,34 @@ void near_work_items(fmbem *h, cudaStream_t s) {
     h->near_items = (int4 *)dev_alloc(h, sizeof(int4) * items.size());
     h->near_next = (int *)dev_alloc(h, sizeof(int));
     CK(cudaMemcpyAsync(h->near_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+    // target groups of at most NR_TT targets per leaf for k_near_r, near-equal sizes: in leaf
+    // (Morton) order, so that concurrent units share sources in L2, and again with the most pair
+    // work first, for the last slab
+    std::vector<int4> groups;
+    std::vector<int64_t> gcost;
+    for (int64_t leaf = 0; leaf < L.n; ++leaf) {
+        const int nt = ne[leaf] - nb[leaf];
+        if (nt <= 0) continue;
+        int64_t nsrc = 0;
+        for (int q = ns[leaf]; q < ns[leaf + 1]; ++q) nsrc += ne[ni[q] - L.off] - nb[ni[q] - L.off];
+        const int ng = (nt + NR_TT - 1) / NR_TT;
+        for (int k = 0, t0 = 0; k < ng; ++k) {
+            const int cnt = nt / ng + (k < nt % ng ? 1 : 0);
+            groups.push_back(int4{(int)leaf, t0, cnt, 0});
+            gcost.push_back(nsrc * cnt);
+            t0 += cnt;
+        }
+    }
+    std::vector<int> gorder(groups.size());
+    for (size_t k = 0; k < gorder.size(); ++k) gorder[k] = (int)k;
+    std::stable_sort(gorder.begin(), gorder.end(), [&](int u, int v) { return gcost[u] > gcost[v]; });
+    std::vector<int4> gsorted(groups.size());
+    for (size_t k = 0; k < gorder.size(); ++k) gsorted[k] = groups[gorder[k]];
+    h->n_near_groups = (int)groups.size();
+    h->near_groups = (int4 *)dev_alloc(h, sizeof(int4) * 2 * std::max<size_t>(groups.size(), 1));
+    CK(cudaMemcpyAsync(h->near_groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->near_groups + groups.size(), gsorted.data(), sizeof(int4) * gsorted.size(),
+                       cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
 }
 
@@ -1911,8 +2168,17 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const bool timing = h->profile && h->ev[0] != nullptr;
     if (timing) CK(cudaEventRecord(h->ev[0], s));
 
+    // single precision with 32 or more right-hand sides: a node-major copy of the densities for
+    // k_near_r in the half of the density buffer that double precision would use
+    const int64_t nrT = f32 ? (nr / 32) * 32 : 0;
+    cx<R> *densT = nrT > 0 ? dens + 2 * nr * N * 6 : nullptr;
     k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens);
     CKL("k_prep");
+    if (densT != nullptr) {
+        k_dens_node_major<<<dim3((unsigned)((N + 15) / 16), (unsigned)(nrT / 32), 2), 256, 0, s>>>(
+            N, nr, (const float4 *)dens, (float4 *)densT);
+        CKL("k_dens_node_major");
+    }
     const LevelInfo &L = h->lev[lmax];
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
     constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
@@ -1940,29 +2206,49 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // near field: in single precision the warp-independent kernel with blocks of RB right-hand
     // sides (the pair scalars are shared by the block); for fewer than 4 right-hand sides, and in
     // double precision, the block-cooperative kernels (more threads per leaf, FP64 pipe busier)
-    auto launch_w = [&](auto kern, int rb, size_t tile_bytes) {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // k_near_w over the right-hand sides rhs_base .. nr - 1 in blocks of rb
+    auto launch_w = [&](auto kern, int rb, size_t tile_bytes, int64_t rhs_base) {
         if (h->near_items == nullptr) throw fmbem_error{FMBEM_ERR_CUDA, "near-field work items were not built"};
         const size_t smw = 2 * tile_bytes * NW_WARPS;  // two tiles per warp
-        const int64_t units = (int64_t)h->n_near_items * 2 * ((nr + rb - 1) / rb);
+        const int64_t units = (int64_t)h->n_near_items * 2 * ((nr - rhs_base + rb - 1) / rb);
         if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
-        int dev = 0, nsm = 0, per_sm = 0;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * NW_WARPS, smw));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((units + NW_WARPS - 1) / NW_WARPS,
                                                                     (int64_t)std::max(per_sm, 1) * nsm));
         CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
         kern<<<(unsigned)grid, 32 * NW_WARPS, smw, s>>>(
-            L.off, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
-            h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, dc, h->perm, p2, h->nbox,
+            L.off, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, rhs_base, h->box_nbeg,
+            h->box_nend, h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, dc, h->perm, p2, h->nbox,
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_w");
     };
+    // k_near_r over the right-hand sides 0 .. 32 nblk - 1
+    auto launch_r = [&](int64_t nblk) {
+        const int64_t units = (int64_t)h->n_near_groups * 2 * nblk;
+        if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_r, 32 * NR_WARPS, 0));
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((units + NR_WARPS - 1) / NR_WARPS,
+                                                                    (int64_t)std::max(per_sm, 1) * nsm));
+        CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
+        k_near_r<<<(unsigned)grid, 32 * NR_WARPS, 0, s>>>(
+            L.off, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
+            h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)densT, dc, h->perm, p2, h->nbox,
+            (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
+        CKL("k_near_r");
+    };
     if constexpr (sizeof(R) == 4) {
-        if (nr >= 8) launch_w(k_near_w<8>, 8, sizeof(WarpTile<8>));
-        else if (nr >= 4) launch_w(k_near_w<4>, 4, sizeof(WarpTile<4>));
-        else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
+        if (nr >= 4) {  // whole blocks of 32 right-hand sides one per lane, the rest by k_near_w
+            const int64_t nblk = nr / 32, rest = nr - 32 * nblk;
+            if (nblk > 0) launch_r(nblk);
+            if (rest >= 8) launch_w(k_near_w<8>, 8, sizeof(WarpTile<8>), 32 * nblk);
+            else if (rest > 0) launch_w(k_near_w<4>, 4, sizeof(WarpTile<4>), 32 * nblk);
+        } else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
             k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                           h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens,
                                                           dc, Bl2p, D, h->Mself, x, y, nullptr, nullptr);
@@ -2084,7 +2370,8 @@ template <typename R>
 static void matvec_static_scratch(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s) {
     const size_t S = sizeof(cx<R>);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t b_dens = up(S * 2 * nr * h->N * 6);
+    // single precision with 32 or more right-hand sides also keeps the node-major density copy
+    const size_t b_dens = up(S * 2 * nr * h->N * 6 * (sizeof(R) == 4 && nr >= 32 ? 2 : 1));
     const size_t b_exp = up(S * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
     size_t b_y = 0;
     if (3 * nr <= 24) {

@@ -302,6 +302,24 @@ def test_two_scatterers_and_permeability():
         assert rel(g.matvec(to_dev(x), precision=prec).cpu().numpy(), yo) < MATVEC_TOL
 
 
+@pytest.mark.parametrize("n_rhs", [35, 64])
+def test_batched_near_field_kernels(n_rhs):
+    """32 or more right-hand sides take the lane-per-RHS near-field kernel for whole blocks of 32
+    and the warp-item kernel for the rest (35 = 32 + 3).  Two spheres 0.05 apart make Neighbor
+    lists mix scatterers, so the scatterer-side sums must skip the other scatterer's nodes.  Every
+    right-hand side must match the oracle and the FP64 product."""
+    m1 = fi.icosphere(3, 0.5, (-0.525, 0, 0), domain=1)
+    m2 = fi.icosphere(3, 0.5, (0.525, 0.02, 0.0), domain=2)
+    o, g = case(fi.merge_meshes(m1, m2), [1.0, 2.25, -4 + 0.3j], [1.0, 1.0, 1.0], 1.2)
+    x = fi.random_complex((n_rhs, o.N, 6), seed=61)
+    yo = o.matvec(x)
+    y64 = g.matvec(to_dev(x), precision=fm.FP64).cpu().numpy()
+    y32 = g.matvec(to_dev(x), precision=fm.FP32).cpu().numpy()
+    assert rel(y32, yo) < MATVEC_TOL
+    for r in range(n_rhs):
+        assert rel(y32[r], y64[r]) < 2e-6, (r, rel(y32[r], y64[r]))
+
+
 def test_tiny_mesh():
     """42 nodes: every far pair is only two box widths apart, so p = 14 is needed for 1e-4."""
     o, g = case(fi.icosphere(1), [1.0, 2.25], [1.0, 1.0], 1.0, p=14)
