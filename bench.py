@@ -204,7 +204,7 @@ def roofline(info, p, nr, n_dom, phases, precision):
     elif dom == "near_l2p_self":
         per_pair = NEAR_PAIR_CACHED if precision == "fp64" and nr < 4 else NEAR_PAIR
         flops = info["near_pairs"] * n_dom * (per_pair + NEAR_RHS * nr)
-        name = "near field + L2P + self (k_near / k_near_w)"
+        name = "near field + L2P + self (k_near, k_near_w, k_near_r)"
     else:
         flops, name = None, dom
     achieved = flops / (avg[dom] * 1e-3) / 1e12 if flops else None
@@ -344,8 +344,8 @@ def run_ours(args):
         ms1 = e0.elapsed_time(e1) / 3
         other = dict(other or {}, fp64_single_rhs=dict(value=world * N / (ms1 * 1e-3), ms_per_step=ms1))
 
-    # the adjoint (transposed) product through the same tree and translations (no tensor-core path)
-    aprec = fm.FP64 if args.precision == "fp64" else fm.FP32
+    # the adjoint (transposed) product through the same tree and translations, in the bench's precision
+    aprec = {"fp64": fm.FP64, "fp32": fm.FP32, "tf32": fm.TF32}[args.precision]
     for _ in range(2):
         g.adjoint_matvec(x, y, precision=aprec)
     torch.cuda.synchronize()
@@ -357,7 +357,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         a_ms.append(e0.elapsed_time(e1))
-    adjoint = dict(precision="fp64" if aprec == fm.FP64 else "fp32", ms_per_step=statistics.mean(a_ms),
+    adjoint = dict(precision=args.precision, ms_per_step=statistics.mean(a_ms),
                    value=world * N * nr / (statistics.mean(a_ms) * 1e-3))
 
     solve = None

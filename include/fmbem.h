@@ -185,7 +185,8 @@ fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rh
  * gradient; the near field is summed directly over the Neighbor leaves.
  *   x_dev, y_dev  device [n_rhs][N][6] complex128 (user order); x is read, y written; they
  *                 must not overlap.
- *   precision     FMBEM_FP64 or FMBEM_FP32 (as for fmbem_matvec; no tensor-core path).
+ *   precision     fmbem_precision of the passes, as for fmbem_matvec (FMBEM_TF32 puts M2L and
+ *                 L2L on the tensor cores for at least 16 right-hand sides).
  * Uses the same handle-owned scratch as fmbem_matvec. */
 fmbem_status fmbem_adjoint_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,
                                   void *stream);

@@ -216,8 +216,8 @@ fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rh
 fmbem_status fmbem_adjoint_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,
                                   void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
-    if (n_rhs < 1 || !x_dev || !y_dev || x_dev == y_dev || (precision != FMBEM_FP64 && precision != FMBEM_FP32)) {
-        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64 or FP32)";
+    if (n_rhs < 1 || !x_dev || !y_dev || x_dev == y_dev || (precision != FMBEM_FP64 && precision != FMBEM_FP32 && precision != FMBEM_TF32)) {
+        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64, FP32 or TF32)";
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
     return guarded(h, [&] {

@@ -2270,7 +2270,8 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
 
 // y = A^T x (see k_near_adj): monopole P2M, M2M, the downward pass, near field and assembly
 template <typename R>
-static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc) {
+static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
+                         bool tensor_cores = false) {
     const int64_t N = h->N;
     const int p2 = h->p2, lmax = h->lmax, J = h->J;
     const bool f32 = sizeof(R) == 4;
@@ -2286,7 +2287,7 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
                                                                            h->box_nend, h->dom, dens, Bp2m, C);
     CKL("k_p2m_adj");
     upward_m2m<R>(h, nr, s);
-    downward_pass<R>(h, nr, s, false);
+    downward_pass<R>(h, nr, s, tensor_cores);
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
     const V4<R> *cache = f32 ? nullptr : (const V4<R> *)h->near_cache64;
@@ -2303,11 +2304,26 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
     CKL("k_near_adj");
 }
 
+// the bounded mbarrier waits of the tensor-core kernel report time-outs in h->tc_err
+static void check_tc_err(fmbem *h, cudaStream_t s) {
+    if (!h->tc_err) return;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (e) throw fmbem_error{FMBEM_ERR_CUDA, "tensor-core M2L: an mbarrier wait timed out"};
+}
+
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
     ensure_scratch(h, nr);
     const DomainConsts *dc = (const DomainConsts *)h->dcons;
-    if (precision == FMBEM_FP32) adjoint_impl<float>(h, x, y, nr, s, dc);
-    else adjoint_impl<double>(h, x, y, nr, s, dc);
+    if (precision == FMBEM_TF32) {
+        adjoint_impl<float>(h, x, y, nr, s, dc, true);
+        check_tc_err(h, s);
+    } else if (precision == FMBEM_FP32) {
+        adjoint_impl<float>(h, x, y, nr, s, dc);
+    } else {
+        adjoint_impl<double>(h, x, y, nr, s, dc);
+    }
 }
 
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
@@ -2316,12 +2332,7 @@ void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaS
     DomainConsts *dc = (DomainConsts *)h->dcons;
     if (precision == FMBEM_TF32) {
         matvec_impl<float>(h, x, y, nr, s, dc, true);
-        if (h->tc_err) {  // bounded mbarrier waits of the tensor-core kernel report time-outs here
-            int e = 0;
-            CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            if (e) throw fmbem_error{FMBEM_ERR_CUDA, "tensor-core M2L: an mbarrier wait timed out"};
-        }
+        check_tc_err(h, s);
     } else if (precision == FMBEM_FP32) {
         matvec_impl<float>(h, x, y, nr, s, dc);
     } else {

@@ -206,7 +206,7 @@ void precond(fmbem *h, const c32 *v, c64 *z, int64_t nr, cudaStream_t s, bool tr
 // the operator of the solve: A (Eq. 2.9) or, for the adjoint solve, A^T (which has no tensor-core
 // path, so TF32 falls back to FP32)
 void apply_op(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s, bool tr) {
-    if (tr) run_adjoint_matvec(h, x, y, nr, precision == FMBEM_TF32 ? FMBEM_FP32 : precision, s);
+    if (tr) run_adjoint_matvec(h, x, y, nr, precision, s);
     else run_matvec(h, x, y, nr, precision, s);
 }
 

@@ -223,6 +223,26 @@ def test_adjoint_two_scatterers_and_rows_at_scale():
     assert rel(yt, o7.matvec_transpose_rows(x7, rows)) < MATVEC_TOL
 
 
+def test_adjoint_tf32_tensor_core_path():
+    """The adjoint product with TF32 and 16 right-hand sides runs M2L and L2L on the tensor cores
+    (as the forward product does); it must stay close to the FP32 adjoint, to the oracle's
+    transposed rows, and satisfy the bilinear identity with the TF32 forward product."""
+    V, F, D = fi.icosphere(5)
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    o, g = case((V, F, D), eps, mu, k0)
+    assert g.tree_info()["l_max"] >= 3
+    x = fi.random_complex((16, o.N, 6), seed=57)
+    ytc = g.adjoint_matvec(to_dev(x), precision=fm.TF32).cpu().numpy()
+    y32 = g.adjoint_matvec(to_dev(x), precision=fm.FP32).cpu().numpy()
+    assert rel(ytc, y32) < 1e-3
+    rows = fi.sample_rows(o.N, 128, seed=58)
+    assert rel(ytc[:, rows], o.matvec_transpose_rows(x, rows)) < 1e-3
+    z = fi.random_complex((16, o.N, 6), seed=59)
+    lhs = np.sum(z * g.matvec(to_dev(x), precision=fm.TF32).cpu().numpy())
+    rhs = np.sum(g.adjoint_matvec(to_dev(z), precision=fm.TF32).cpu().numpy() * x)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-3
+
+
 def test_adjoint_solve_duality_and_residual(sphere_s4):
     """Adjoint GMRES (A^T x = b with M^T as right preconditioner): <b2, A^-1 b1> = <A^-T b2, b1>
     between a forward and an adjoint solve, and the oracle's dense A^T residual of the adjoint
