@@ -184,12 +184,14 @@ class ClockSampler:
 def m2l_flops_per_column(p, nr):
     """Algorithmic real flops of one S|R translation of one column: dense p^2 x p^2 complex matrix
     (8 p^4), or, in the rotation form the library uses for p >= 9 with at most 8 right-hand sides,
-    an azimuthal phase, a real polar rotation per degree block (real x complex, 4 flops per
-    entry), the complex coaxial S|R per order block, the real polar rotation back and a phase."""
+    an azimuthal phase and a fold into mirror-even/odd halves, a real polar rotation per degree on
+    the folded halves (real x complex, 4 flops per entry), the complex coaxial S|R per order block,
+    the folded polar rotation back, the unfold and a phase."""
     if p >= 9 and 3 * nr <= 24:
-        rot = p * (2 * p - 1) * (2 * p + 1) // 3
-        coax = p * (2 * p * p + 1) // 3
-        return 4.0 * 2 * rot + 8.0 * coax + 6.0 * 2 * p * p, "rotation form (phase, real polar rotation, coaxial S|R, back)"
+        rot = p * (2 * p * p + 1) // 3     # folded polar entries per rotation
+        coax = p * (2 * p * p + 1) // 3    # coaxial entries
+        return (4.0 * 2 * rot + 8.0 * coax + 6.0 * 2 * p * p + 4.0 * p * p,
+                "rotation form (phase, folded real polar rotation, coaxial S|R, back)")
     return 8.0 * p ** 4, "dense S|R matrices"
 
 

@@ -419,27 +419,70 @@ __global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr,
 // M2L on offset chunks in rotation form (S|R of Eq. 2.21 factored as T_o = B_o Z_{|t|} A_o):
 // C' = A_o C rotates each degree block into the frame whose z axis is the translation,
 // D' = Z C' translates along z (block-diagonal in the order m), Y = B_o D' rotates back.
-// Per column this costs sum_n (2n+1)^2 * 2 + sum_m (p-|m|)^2 complex multiply-adds instead of p^4.
-// The compact blocks of A_o, B_o and Z are staged in shared memory once per chunk; a thread owns
-// one output coefficient (n, m) for MAXC columns in each of the three stages.
-__device__ __forceinline__ int rot_off(int n) { return n * (2 * n - 1) * (2 * n + 1) / 3; }
+// A_o and B_o are a diagonal azimuthal phase and a real polar rotation per degree.  A rotation
+// about y commutes with the mirror y -> -y, which maps Y_n^m to Y_n^{-m} in this basis (the
+// normalisation depends on |m| only), so a polar block D obeys D[-m'][-m] = D[m'][m]; the coaxial
+// translation commutes with it too, so Z^{-m} = Z^m.  In the folded coordinates
+//   a_0 = x_0, a_m = x_m + x_{-m}, b_m = x_m - x_{-m}  (m >= 1)
+// a polar block splits into two half-size blocks, (D[m'][m] + D[m'][-m]) acting on a and
+// (D[m'][m] - D[m'][-m]) acting on b, and Z^m acts on both halves; the back rotation returns
+// P +- Q to the orders +-m'.  Per column this costs sum_n ((n+1)^2 + n^2) real-by-complex products
+// per rotation instead of sum_n (2n+1)^2, and sum_m (p-|m|)^2 complex products for Z.  The folded
+// blocks (pack_rot_factors) and Z are staged in shared memory once per chunk; a thread owns one
+// folded coefficient (degree n, slot s in 0..2n: a_s for s <= n, b_{s-n} after) for MAXC columns.
+__device__ __host__ __forceinline__ int rot_off(int n) { return n * (2 * n * n + 1) / 3; }  // folded blocks before degree n
+// The k-th folded slot (index n^2 + s) in order of its polar row length t = 1..p (stages 1 and 3):
+// length t holds the t a-slots of degree t-1 and the t b-slots of degree t.
+__device__ __forceinline__ int slot_by_rowlen(int p, int k) {
+    for (int t = 1; t <= p; ++t) {
+        if (k < t) return (t - 1) * (t - 1) + k;
+        k -= t;
+        if (t < p) {
+            if (k < t) return t * t + t + 1 + k;
+            k -= t;
+        }
+    }
+    return 0;
+}
+// The k-th folded slot in order of its coaxial row length p - |m| (stage 2), longest first: order
+// 0 holds the a-slots of degrees 0..p-1, order m >= 1 the a- and b-slots of degrees m..p-1.
+__device__ __forceinline__ int slot_by_order(int p, int k) {
+    for (int am = 0; am < p; ++am) {
+        const int cnt = p - am;
+        if (k < cnt) return (am + k) * (am + k) + am;
+        k -= cnt;
+        if (am > 0) {
+            if (k < cnt) return (am + k) * (am + k) + (am + k) + am;
+            k -= cnt;
+        }
+    }
+    return 0;
+}
 template <typename R, int MAXC>
-__global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox, int col0, int ncol,
-                          int pc, int cg, const int32_t *chunk_beg, const int32_t *chunk_cnt, const int16_t *chunk_off,
-                          const int32_t *pair_e, const int32_t *ff_src, const int8_t *tidx, int n_tlen,
-                          const R *RD, const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y,
-                          int64_t e_first) {
+__global__ void __launch_bounds__(512) k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox,
+                                                 int col0, int ncol, int pc, int cg, const int32_t *chunk_beg,
+                                                 const int32_t *chunk_cnt, const int16_t *chunk_off, const int32_t *pair_e,
+                                                 const int32_t *ff_src, const int8_t *tidx, int n_tlen, const R *RD,
+                                                 const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y,
+                                                 int64_t e_first) {
     const int p2 = p * p;
     const int nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *Df = reinterpret_cast<R *>(smem_raw);  // forward polar rotation, real degree blocks
-    R *Db = Df + nrot;                         // back polar rotation
+    R *Df = reinterpret_cast<R *>(smem_raw);  // forward polar rotation, folded real blocks
+    R *Db = Df + nrot;                         // back polar rotation, folded
     cx<R> *Pf = reinterpret_cast<cx<R> *>(Db + nrot);  // forward azimuthal phases [p2]
     cx<R> *Pb = Pf + p2;                                // back azimuthal phases [p2]
     cx<R> *Zb = Pb + p2;
     const int ncap = cg * MAXC;
     cx<R> *X = Zb + ncoax;       // [ncap][p2]
     cx<R> *U = X + ncap * p2;    // [ncap][p2]
+    short2 *itab = reinterpret_cast<short2 *>(U + ncap * p2);  // fold items: (degree n, order m >= 0)
+    const int nitem = p * (p + 1) / 2;
+    for (int i = threadIdx.x; i < nitem; i += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= i) ++n;
+        itab[i] = make_short2((short)n, (short)(i - n * (n + 1) / 2));
+    }
     const int64_t ck = chunk0 + blockIdx.x;
     const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
     const int o = chunk_off[ck];
@@ -452,84 +495,129 @@ __global__ void k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, in
     for (int i = threadIdx.x; i < ncoax; i += blockDim.x) Zb[i] = Z[i];
     const int rows_pad = blockDim.x / cg;
     const int r = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
-    int rn = (int)sqrtf((float)r);
+    int rn = (int)sqrtf((float)r);  // the natural coefficient (rn, r - rn^2 - rn) of the unfold
     while (rn * rn > r) --rn;
     while ((rn + 1) * (rn + 1) <= r) ++rn;
-    const int rm = r - rn * rn - rn;  // this thread's output coefficient (rn, rm)
+    // the folded slots of the three stages, ordered by row length so that the lanes of a warp
+    // run loops of (nearly) equal length; odd column groups take the order reversed, so that a
+    // warp straddling two groups still meets similar lengths
+    const int kk = (grp & 1) ? p2 - 1 - r : r;
+    const int r13 = r < p2 ? slot_by_rowlen(p, kk) : 0, r2 = r < p2 ? slot_by_order(p, kk) : 0;
+    int n1 = (int)sqrtf((float)r13);
+    while (n1 * n1 > r13) --n1;
+    while ((n1 + 1) * (n1 + 1) <= r13) ++n1;
+    const int sl1 = r13 - n1 * n1;
+    const bool plus1 = sl1 <= n1;
+    const int am1 = plus1 ? sl1 : sl1 - n1;
+    // folded polar rows of the stage 1 and 3 slot: a-block rows (n+1 long) or b-block rows (n long)
+    const int foff = rot_off(n1) + (plus1 ? sl1 * (n1 + 1) : (n1 + 1) * (n1 + 1) + (am1 - 1) * n1);
+    const int flen = plus1 ? n1 + 1 : n1, fin = plus1 ? n1 * n1 : n1 * n1 + n1 + 1;
+    int n2 = (int)sqrtf((float)r2);
+    while (n2 * n2 > r2) --n2;
+    while ((n2 + 1) * (n2 + 1) <= r2) ++n2;
+    const bool plus2 = r2 - n2 * n2 <= n2;
+    const int am2 = plus2 ? r2 - n2 * n2 : r2 - n2 * n2 - n2;
+    // coaxial block of the stage 2 slot's order am2 (Z^{-m} = Z^m): row n' - am2, columns n - am2
     int zbase = 0;
-    for (int m = -(p - 1); m < rm; ++m) zbase += (p - abs(m)) * (p - abs(m));
-    const int arm = abs(rm), zw = p - arm;
+    for (int m = -(p - 1); m < am2; ++m) zbase += (p - abs(m)) * (p - abs(m));
+    const int zw = p - am2;
     for (int b0 = 0; b0 < cnt; b0 += pc) {
         const int np = min(pc, cnt - b0);
         const int nct = np * ncol;
         __syncthreads();
-        for (int i = threadIdx.x; i < ncap * p2; i += blockDim.x) {
-            int j = i / p2, k = i - j * p2;
-            cx<R> v = {0, 0};
-            if (j < nct) {  // the azimuthal part of the forward rotation is diagonal: applied here
-                int pr = j / ncol, c = j - pr * ncol;
-                v = C[(((int64_t)d * nbox + ff_src[pair_e[beg + b0 + pr]]) * 3 * nr + col0 + c) * p2 + k] * Pf[k];
+        // load with the forward azimuthal phase and fold, one item (n, m >= 0) per thread: with
+        // the phase e of order m (that of -m is its conjugate, checked at packing),
+        // a_m = x_m e + x_{-m} conj(e) = Re(e) (x_m + x_{-m}) + i Im(e) (x_m - x_{-m}) and
+        // b_m = x_m e - x_{-m} conj(e) = Re(e) (x_m - x_{-m}) + i Im(e) (x_m + x_{-m})
+        for (int i = threadIdx.x; i < ncap * nitem; i += blockDim.x) {
+            const int j = i / nitem, it = i - j * nitem;
+            const short2 tn = itab[it];
+            const int n = tn.x, mm = tn.y, c0 = n * n + n;
+            cx<R> va = {0, 0}, vb = {0, 0};
+            if (j < nct) {
+                const int pr = j / ncol, c = j - pr * ncol;
+                const cx<R> *src = C + (((int64_t)d * nbox + ff_src[pair_e[beg + b0 + pr]]) * 3 * nr + col0 + c) * p2;
+                if (mm == 0) {
+                    va = src[c0] * Pf[c0];
+                } else {
+                    const cx<R> xp = src[c0 + mm], xm = src[c0 - mm], e = Pf[c0 + mm];
+                    const cx<R> sum = xp + xm, dif = xp - xm;
+                    va = cx<R>{e.re * sum.re - e.im * dif.im, e.re * sum.im + e.im * dif.re};
+                    vb = cx<R>{e.re * dif.re - e.im * sum.im, e.re * dif.im + e.im * sum.re};
+                }
             }
-            X[i] = v;
+            X[j * p2 + n * n + mm] = va;
+            if (mm > 0) X[j * p2 + n * n + n + mm] = vb;
         }
         __syncthreads();
         const int j0 = grp * MAXC, nj = min(MAXC, nct - j0);
         cx<R> acc[MAXC];
-        // stage 1: polar rotation into the translation frame, per degree (real blocks)
+        // stage 1: folded polar rotation into the translation frame
         if (r < p2 && nj > 0) {
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
-            const R *a = Df + rot_off(rn) + (rm + rn) * (2 * rn + 1);
-            for (int jj = 0; jj < 2 * rn + 1; ++jj) {
+            const R *a = Df + foff;
+            for (int jj = 0; jj < flen; ++jj) {
                 const R t = a[jj];
 #pragma unroll
                 for (int q = 0; q < MAXC; ++q) {
-                    const cx<R> xv = X[(j0 + q) * p2 + rn * rn + jj];
+                    const cx<R> xv = X[(j0 + q) * p2 + fin + jj];
                     acc[q].re = fma(t, xv.re, acc[q].re);
                     acc[q].im = fma(t, xv.im, acc[q].im);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < MAXC; ++q) U[(j0 + q) * p2 + r] = acc[q];
+            for (int q = 0; q < MAXC; ++q) U[(j0 + q) * p2 + r13] = acc[q];
         }
         __syncthreads();
-        // stage 2: coaxial translation along z, per order m
+        // stage 2: coaxial translation along z of order am2, on the a (or b) half
         if (r < p2 && nj > 0) {
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
-            const cx<R> *z = Zb + zbase + (rn - arm) * zw;
+            const cx<R> *z = Zb + zbase + (n2 - am2) * zw;
             for (int jj = 0; jj < zw; ++jj) {
                 const cx<R> t = z[jj];
-                const int n = arm + jj;
+                const int n = am2 + jj;
+                const int src = n * n + (plus2 ? am2 : n + am2);
 #pragma unroll
-                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, U[(j0 + q) * p2 + n * n + n + rm]);
+                for (int q = 0; q < MAXC; ++q) cfma(acc[q], t, U[(j0 + q) * p2 + src]);
             }
 #pragma unroll
-            for (int q = 0; q < MAXC; ++q) X[(j0 + q) * p2 + r] = acc[q];
+            for (int q = 0; q < MAXC; ++q) X[(j0 + q) * p2 + r2] = acc[q];
         }
         __syncthreads();
-        // stage 3: polar rotation back, per degree (real blocks), then the azimuthal phase; store
-        // at the pairs' CSR positions
+        // stage 3: folded polar rotation back: P (a half) and Q (b half)
         if (r < p2 && nj > 0) {
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) acc[q] = {0, 0};
-            const R *bb = Db + rot_off(rn) + (rm + rn) * (2 * rn + 1);
-            for (int jj = 0; jj < 2 * rn + 1; ++jj) {
+            const R *bb = Db + foff;
+            for (int jj = 0; jj < flen; ++jj) {
                 const R t = bb[jj];
 #pragma unroll
                 for (int q = 0; q < MAXC; ++q) {
-                    const cx<R> xv = X[(j0 + q) * p2 + rn * rn + jj];
+                    const cx<R> xv = X[(j0 + q) * p2 + fin + jj];
                     acc[q].re = fma(t, xv.re, acc[q].re);
                     acc[q].im = fma(t, xv.im, acc[q].im);
                 }
             }
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) U[(j0 + q) * p2 + r13] = acc[q];
+        }
+        __syncthreads();
+        // unfold, y_{+-m} = P_m +- Q_m, apply the back azimuthal phase and store at the pairs'
+        // CSR positions; here thread r owns the natural coefficient (rn, m = r - rn^2 - rn)
+        if (r < p2 && nj > 0) {
+            const int m = r - rn * rn - rn, mm = abs(m);
             const cx<R> ph = Pb[r];
 #pragma unroll
             for (int q = 0; q < MAXC; ++q)
                 if (q < nj) {
-                    int j = j0 + q, pr = j / ncol, c = j - pr * ncol;
-                    int64_t e = pair_e[beg + b0 + pr];
-                    Y[((e - e_first) * ncol + c) * p2 + r] = acc[q] * ph;
+                    const cx<R> *u = U + (j0 + q) * p2 + rn * rn;
+                    cx<R> v = u[mm];
+                    if (mm > 0) v = m > 0 ? v + u[rn + mm] : v - u[rn + mm];
+                    const int j = j0 + q, pr = j / ncol, c = j - pr * ncol;
+                    const int64_t e = pair_e[beg + b0 + pr];
+                    Y[((e - e_first) * ncol + c) * p2 + r] = v * ph;
                 }
         }
     }
@@ -1521,15 +1609,23 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
 }
 
 // Packed rotation-form tables, in the order k_m2l_rot reads them.  Polar rotations (per offset,
-// forward then back): the degree blocks n = 0..p-1 one after the other, each (2n+1) x (2n+1)
-// row-major with the row the output order m' + n and the column the input order m + n, real.
-// Azimuthal phases (per offset, forward then back): the diagonal, p2 complex.  Coaxial Z (per
-// domain, level and offset length): the order blocks m = -(p-1)..p-1, each (p-|m|) x (p-|m|)
-// row-major with the row the output degree n' - |m| and the column the input degree n - |m|.  The
-// dense projected tables are stored input-major, T[c][r] at c * p2 + r.  The polar factors must be
-// real and the azimuthal ones diagonal (to rounding); the largest departure is recorded in
-// dev[0] (imaginary parts) and dev[1] (off-diagonal entries) as the bit patterns of non-negative
-// doubles, so that atomicMax orders them.
+// forward then back): per degree n = 0..p-1 the folded blocks (see k_m2l_rot) one after the
+// other, each row-major, real: the a-block, (n+1) x (n+1) with rows m' = 0..n and columns
+// m = 0..n, then the b-block, n x n with rows and columns 1..n.  With D the dense polar block
+// (row = output order, column = input order):
+//   forward a-block: row 0: D[0][0], (D[0][m] + D[0][-m]) / 2; rows m' >= 1: 2 D[m'][0],
+//                    D[m'][m] + D[m'][-m];   b-block: D[m'][m] - D[m'][-m];
+//   back a-block:    row 0 as forward; rows m' >= 1: D[m'][0], (D[m'][m] + D[m'][-m]) / 2;
+//                    b-block: (D[m'][m] - D[m'][-m]) / 2,
+// so that the back rotation returns P + Q and P - Q for the orders +m' and -m'.  Azimuthal phases
+// (per offset, forward then back): the diagonal, p2 complex.  Coaxial Z (per domain, level and
+// offset length): the order blocks m = -(p-1)..p-1, each (p-|m|) x (p-|m|) row-major with the row
+// the output degree n' - |m| and the column the input degree n - |m|.  The dense projected tables
+// are stored input-major, T[c][r] at c * p2 + r.  The polar factors must be real, mirror
+// symmetric (D[-m'][-m] = D[m'][m]) and the azimuthal ones diagonal (to rounding); the largest
+// departures are recorded in dev[0] (imaginary parts), dev[1] (off-diagonal entries), dev[2]
+// (mirror asymmetry) and dev[3] (phases of orders -m that are not the conjugates of those of m)
+// as the bit patterns of non-negative doubles, so that atomicMax orders them.
 __global__ void k_pack_rot_d(int p, const c64 *Tf, const c64 *Tb, double *D64, float *D32, unsigned long long *dev) {
     const int p2 = p * p, nrot = rot_off(p);
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1538,11 +1634,24 @@ __global__ void k_pack_rot_d(int p, const c64 *Tf, const c64 *Tb, double *D64, f
     const int within = (int)(idx - o * 2 * nrot), fb = within / nrot, i = within - fb * nrot;
     int n = 0;
     while (rot_off(n + 1) <= i) ++n;
-    const int w = 2 * n + 1, loc = i - rot_off(n), row = loc / w, col = loc - row * w;
-    const c64 v = (fb == 0 ? Tf : Tb)[o * p2 * p2 + (int64_t)(n * n + col) * p2 + n * n + row];
-    D64[idx] = v.re;
-    D32[idx] = (float)v.re;
-    atomicMax(&dev[0], (unsigned long long)__double_as_longlong(fabs(v.im)));
+    const int loc = i - rot_off(n);
+    const bool ablk = loc < (n + 1) * (n + 1);
+    const int mp = ablk ? loc / (n + 1) : 1 + (loc - (n + 1) * (n + 1)) / n;
+    const int m = ablk ? loc % (n + 1) : 1 + (loc - (n + 1) * (n + 1)) % n;
+    const c64 *T = (fb == 0 ? Tf : Tb) + o * p2 * p2;
+    auto Dv = [&](int row, int col) { return T[(int64_t)(n * n + n + col) * p2 + n * n + n + row]; };
+    const c64 d1 = Dv(mp, m), d2 = Dv(mp, -m);
+    double v;
+    if (ablk && mp == 0) v = m == 0 ? d1.re : 0.5 * (d1.re + d2.re);
+    else if (ablk && m == 0) v = fb == 0 ? 2.0 * d1.re : d1.re;
+    else if (ablk) v = (fb == 0 ? 1.0 : 0.5) * (d1.re + d2.re);
+    else v = (fb == 0 ? 1.0 : 0.5) * (d1.re - d2.re);
+    D64[idx] = v;
+    D32[idx] = (float)v;
+    const c64 e1 = Dv(-mp, -m), e2 = Dv(-mp, m);
+    const double asym = fmax(fabs(e1.re - d1.re), fabs(e2.re - d2.re));
+    atomicMax(&dev[0], (unsigned long long)__double_as_longlong(fmax(fabs(d1.im), fabs(d2.im))));
+    atomicMax(&dev[2], (unsigned long long)__double_as_longlong(asym));
 }
 __global__ void k_pack_rot_p(int p, const c64 *Tf, const c64 *Tb, c64 *P64, c32 *P32, unsigned long long *dev) {
     const int p2 = p * p;
@@ -1555,6 +1664,11 @@ __global__ void k_pack_rot_p(int p, const c64 *Tf, const c64 *Tb, c64 *P64, c32 
     if (c == r) {
         P64[(o * 2 + fb) * p2 + r] = v;
         P32[(o * 2 + fb) * p2 + r] = c32{(float)v.re, (float)v.im};
+        int n = 0;  // the phase of order -m must be the conjugate of that of m
+        while ((n + 1) * (n + 1) <= r) ++n;
+        const int rm = 2 * (n * n + n) - r;
+        const c64 w = (fb == 0 ? Tf : Tb)[o * p2 * p2 + (int64_t)rm * p2 + rm];
+        atomicMax(&dev[3], (unsigned long long)__double_as_longlong(fmax(fabs(v.re - w.re), fabs(v.im + w.im))));
     } else {
         atomicMax(&dev[1], (unsigned long long)__double_as_longlong(sqrt(v.re * v.re + v.im * v.im)));
     }
@@ -1571,6 +1685,37 @@ __global__ void k_pack_rot_z(int p, int64_t nz, const cx<R> *Z, cx<R> *Zp) {
     const int am = abs(m), w = p - am, loc = i - base, row = loc / w, col = loc - row * w;
     const int np = am + row, n = am + col;  // output degree n', input degree n
     Zp[idx] = Z[t * p2 * p2 + (int64_t)(n * n + n + m) * p2 + np * np + np + m];
+}
+
+// Mirror check of the packed coaxial blocks (the folded rotation form applies Z^m to both
+// halves): k_z_scale records each table's largest |Z| in zmax[t], k_check_z_mirror the largest
+// |Z^{-m} - Z^m| / zmax[t]; both as bit patterns of non-negative doubles.
+template <typename R>
+__global__ void k_z_scale(int p, int64_t nz, const cx<R> *Zp, unsigned long long *zmax) {
+    const int ncoax = p * (2 * p * p + 1) / 3;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nz * ncoax) return;
+    const cx<R> a = Zp[idx];
+    atomicMax(&zmax[idx / ncoax], (unsigned long long)__double_as_longlong(sqrt((double)a.re * a.re + (double)a.im * a.im)));
+}
+template <typename R>
+__global__ void k_check_z_mirror(int p, int64_t nz, const cx<R> *Zp, const unsigned long long *zmax,
+                                 unsigned long long *dev) {
+    const int ncoax = p * (2 * p * p + 1) / 3;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nz * ncoax) return;
+    const int64_t t = idx / ncoax;
+    const int i = (int)(idx - t * ncoax);
+    int m = -(p - 1), base = 0;
+    while (base + (p - abs(m)) * (p - abs(m)) <= i) { base += (p - abs(m)) * (p - abs(m)); ++m; }
+    if (m >= 0) return;
+    int bm = base;  // block of order -m
+    for (int k = m; k < -m; ++k) bm += (p - abs(k)) * (p - abs(k));
+    const cx<R> a = Zp[t * ncoax + i], b = Zp[t * ncoax + bm + (i - base)];
+    const double dr = (double)a.re - (double)b.re, di = (double)a.im - (double)b.im;
+    const double scale = __longlong_as_double((long long)zmax[t]);
+    const double rel = scale > 0 ? sqrt(dr * dr + di * di) / scale : 0.0;
+    atomicMax(dev, (unsigned long long)__double_as_longlong(rel));
 }
 
 // ---------------------------------------------------------------- adjoint (transposed) product
@@ -1846,35 +1991,55 @@ void pack_rot_tables(fmbem *h, cudaStream_t s) {
     };
     pack(h->R_Z64);
     pack(h->R_Z32);
+    unsigned long long *dev = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long) * (nz + 1));
+    CK(cudaMemsetAsync(dev, 0, sizeof(unsigned long long) * (nz + 1), s));
+    const unsigned nb = (unsigned)((nz * ncoax + 255) / 256);
+    k_z_scale<<<nb, 256, 0, s>>>(p, nz, h->R_Z64, dev + 1);
+    CKL("k_z_scale");
+    k_check_z_mirror<<<nb, 256, 0, s>>>(p, nz, h->R_Z64, dev + 1, dev);
+    CKL("k_check_z_mirror");
+    unsigned long long hd = 0;
+    CK(cudaMemcpyAsync(&hd, dev, sizeof(hd), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dev_free(h, dev);
+    double zmax;
+    std::memcpy(&zmax, &hd, sizeof(double));
+    if (!(zmax < 1e-9))
+        throw fmbem_error{FMBEM_ERR_CUDA, "coaxial translations: Z^-m differs from Z^m (relative " +
+                                              std::to_string(zmax) + ")"};
 }
 
 // the packed rotation factors from the projected ones: forward T(Rz^T) (azimuthal), T(Ry^T)
 // (polar), back T(Ry) (polar), T(Rz) (azimuthal), each [316][p2][p2] input-major; fails loudly if
-// the polar factors are not real or the azimuthal ones not diagonal
+// the polar factors are not real or not mirror symmetric, or the azimuthal ones not diagonal
 void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s) {
     const int p = h->p, p2 = h->p2;
-    const int64_t nrot = p * (2 * p - 1) * (2 * p + 1) / 3;
+    const int64_t nrot = rot_off(p);  // folded polar entries per offset and direction
     h->R_D64 = (double *)dev_alloc(h, sizeof(double) * 316 * 2 * nrot);
     h->R_D32 = (float *)dev_alloc(h, sizeof(float) * 316 * 2 * nrot);
     h->R_P64 = (c64 *)dev_alloc(h, sizeof(c64) * 316 * 2 * p2);
     h->R_P32 = (c32 *)dev_alloc(h, sizeof(c32) * 316 * 2 * p2);
-    unsigned long long *dev = (unsigned long long *)dev_alloc(h, 2 * sizeof(unsigned long long));
-    CK(cudaMemsetAsync(dev, 0, 2 * sizeof(unsigned long long), s));
+    unsigned long long *dev = (unsigned long long *)dev_alloc(h, 4 * sizeof(unsigned long long));
+    CK(cudaMemsetAsync(dev, 0, 4 * sizeof(unsigned long long), s));
     k_pack_rot_d<<<(unsigned)((316 * 2 * nrot + 255) / 256), 256, 0, s>>>(p, Tyf, Tyb, h->R_D64, h->R_D32, dev);
     CKL("k_pack_rot_d");
     const int64_t np = (int64_t)316 * 2 * p2 * p2;
     k_pack_rot_p<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(p, Tzf, Tzb, h->R_P64, h->R_P32, dev);
     CKL("k_pack_rot_p");
-    unsigned long long hd[2];
+    unsigned long long hd[4];
     CK(cudaMemcpyAsync(hd, dev, sizeof(hd), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     dev_free(h, dev);
-    double im_max, off_max;
+    double im_max, off_max, asym_max, conj_max;
     std::memcpy(&im_max, &hd[0], sizeof(double));
     std::memcpy(&off_max, &hd[1], sizeof(double));
-    if (!(im_max < 1e-9) || !(off_max < 1e-9))
+    std::memcpy(&asym_max, &hd[2], sizeof(double));
+    std::memcpy(&conj_max, &hd[3], sizeof(double));
+    if (!(im_max < 1e-9) || !(off_max < 1e-9) || !(asym_max < 1e-9) || !(conj_max < 1e-9))
         throw fmbem_error{FMBEM_ERR_CUDA, "rotation factors: polar part not real (" + std::to_string(im_max) +
-                                              ") or azimuthal part not diagonal (" + std::to_string(off_max) + ")"};
+                                              "), not mirror symmetric (" + std::to_string(asym_max) +
+                                              "), azimuthal part not diagonal (" + std::to_string(off_max) +
+                                              ") or its orders -m not conjugate to m (" + std::to_string(conj_max) + ")"};
 }
 
 // near-field pair-scalar cache (see k_near_cache): per leaf nt x nsrc pairs per side, double
@@ -2073,11 +2238,12 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr && rows_pad <= max_thr;
     // rotation form of the chunked S|R (when its tables were built)
     constexpr int RMAXC = 12;
-    const int pp = h->p, nrot = pp * (2 * pp - 1) * (2 * pp + 1) / 3, ncoax = pp * (2 * pp * pp + 1) / 3;
+    const int pp = h->p, nrot = rot_off(pp), ncoax = pp * (2 * pp * pp + 1) / 3;
     cudaFuncAttributes fa_r{};
     CK(cudaFuncGetAttributes(&fa_r, k_m2l_rot<R, RMAXC>));
     auto rot_bytes = [&](int c) {
-        return sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)c * RMAXC * p2);
+        return sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)c * RMAXC * p2) +
+               sizeof(short2) * (size_t)(pp * (pp + 1) / 2);
     };
     // rotation kernel: in double precision groups of exactly p2 threads (a warp may straddle two
     // column groups), so that no lane idles on a padded row in the FP64-bound stages; in single
