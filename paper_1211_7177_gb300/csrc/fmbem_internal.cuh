@@ -164,6 +164,20 @@ struct fmbem {
     float *R_D32 = nullptr;
     c64 *R_P64 = nullptr, *R_Z64 = nullptr;
     c32 *R_P32 = nullptr, *R_Z32 = nullptr;
+    // the same form for M2M (S|S) and L2L (R|R) along the 8 child-parent diagonals, which share
+    // their rotation factors with the far-field offsets (+-2, +-2, +-2): coaxial S|S and R|R per
+    // (domain, level) [J+1][lmax+1][order blocks], and the child boxes of every level >= 3 in
+    // entries grouped by octant, in chunks of up to 32 (fmm.cu: build_rot_mm_lists)
+    c64 *R_Zmm64 = nullptr, *R_Zll64 = nullptr;
+    c32 *R_Zmm32 = nullptr, *R_Zll32 = nullptr;
+    int8_t *rot_zero = nullptr;                 // [316] zeros: one coaxial table per level
+    int32_t *rmm_iota = nullptr;                // [n_rmm] entry e -> e
+    int32_t *rmm_child = nullptr, *rmm_par = nullptr;  // [n_rmm] child box and its parent per entry
+    int32_t *rmm_entry = nullptr;               // [nbox] entry of a box of level >= 3 (else -1)
+    int32_t *rmm_chunk_beg = nullptr, *rmm_chunk_cnt = nullptr;
+    int16_t *rmm_chunk_mm = nullptr, *rmm_chunk_ll = nullptr;  // far-field offset code of the direction
+    std::vector<int64_t> h_rmm_first, h_rmm_chunk_first;      // per level: first entry, first chunk
+    int64_t n_rmm = 0;
 
     // scratch grown on demand
     int64_t scratch_rhs = 0;
@@ -258,6 +272,8 @@ bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
+void pack_rot_tables_mm(fmbem *h, cudaStream_t s);
+void build_rot_mm_lists(fmbem *h, cudaStream_t s);
 void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s);
 void near_work_items(fmbem *h, cudaStream_t s);
 void build_near_cache(fmbem *h, cudaStream_t s);

@@ -629,14 +629,15 @@ constexpr int L2L_CPT = 3;
 template <typename R>
 __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
                              int ct, const int32_t *parent, const uint64_t *key, const int32_t *ff_start,
-                             const cx<R> *Tll, const cx<R> *Y, int64_t e_first, cx<R> *D) {
+                             const cx<R> *Tll, const cx<R> *Y, int64_t e_first, cx<R> *D, const cx<R> *Yll,
+                             const int32_t *ll_entry, int64_t ll_first) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
     const int64_t g = off + blockIdx.x;
     const int rows_pad = blockDim.x / ct;
     const int r = threadIdx.x % rows_pad, cid = threadIdx.x / rows_pad;
     const cx<R> *T = nullptr;
-    if (l >= 3) {
+    if (l >= 3 && Yll == nullptr) {
         const int64_t P = parent[g];
         for (int e = threadIdx.x; e < ncol * p2; e += blockDim.x)
             X[e] = D[(((int64_t)d * nbox + P) * 3 * nr + col0 + e / p2) * p2 + e % p2];
@@ -657,6 +658,12 @@ __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, in
             for (int j = 0; j < L2L_CPT; ++j)
                 if (c0 + j < ncol) cfma(lp[j], t, X[(c0 + j) * p2 + k]);
         }
+    if (l >= 3 && Yll != nullptr) {  // R|R already applied in rotation form, per child entry
+        const cx<R> *yl = Yll + ((int64_t)(ll_entry[g] - ll_first) * ncol) * p2 + r;
+#pragma unroll
+        for (int j = 0; j < L2L_CPT; ++j)
+            if (c0 + j < ncol) lp[j] = yl[(c0 + j) * p2];
+    }
 #pragma unroll
     for (int j = 0; j < L2L_CPT; ++j) {
         const int c = c0 + j;
@@ -673,6 +680,22 @@ __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, in
         }
         for (; e < e1; ++e, y += st) a0 += y[0];
         D[(((int64_t)d * nbox + g) * 3 * nr + col0 + c) * p2 + r] = (a0 + a1) + (a2 + a3);
+    }
+}
+
+// Rotation-form M2M: the parent's multipole is the sum of its children's translated expansions,
+// C(g) = sum_{children ch} Y[entry(ch)], columns col0 .. col0 + ncol - 1 (Eq. 2.20).
+template <typename R>
+__global__ void k_mm_reduce(int64_t par_off, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
+                            const int32_t *cbeg, const int32_t *cend, const int32_t *entry, int64_t e_first,
+                            const cx<R> *Y, cx<R> *C) {
+    const int64_t g = par_off + blockIdx.x;
+    const int64_t nel = (int64_t)ncol * p2;
+    for (int64_t e = threadIdx.x; e < nel; e += blockDim.x) {
+        cx<R> a = {0, 0};
+        for (int ch = cbeg[g]; ch < cend[g]; ++ch) a += Y[(int64_t)(entry[ch] - e_first) * nel + e];
+        const int c = (int)(e / p2), q = (int)(e - (int64_t)c * p2);
+        C[(((int64_t)d * nbox + g) * 3 * nr + col0 + c) * p2 + q] = a;
     }
 }
 
@@ -1975,11 +1998,11 @@ __global__ void __launch_bounds__(128) k_near_adj(int64_t leaf_off, int64_t N, i
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// replace the dense coaxial tables R_Z (per domain, level and offset length) by their packed form
-void pack_rot_tables(fmbem *h, cudaStream_t s) {
+// replace dense coaxial tables (nz of them, p2 x p2 input-major) by their packed order blocks and
+// check Z^{-m} = Z^m, on which the folded rotation form relies
+static void pack_coax(fmbem *h, c64 *&Z64, c32 *&Z32, int64_t nz, cudaStream_t s) {
     const int p = h->p;
     const int64_t ncoax = p * (2 * p * p + 1) / 3;
-    const int64_t nz = (int64_t)(h->J + 1) * (h->lmax + 1) * h->n_tlen;
     auto pack = [&](auto *&Zd) {
         using T = std::remove_reference_t<decltype(*Zd)>;
         T *Zp = (T *)dev_alloc(h, sizeof(T) * nz * ncoax);
@@ -1989,14 +2012,14 @@ void pack_rot_tables(fmbem *h, cudaStream_t s) {
         dev_free(h, Zd);
         Zd = Zp;
     };
-    pack(h->R_Z64);
-    pack(h->R_Z32);
+    pack(Z64);
+    pack(Z32);
     unsigned long long *dev = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long) * (nz + 1));
     CK(cudaMemsetAsync(dev, 0, sizeof(unsigned long long) * (nz + 1), s));
     const unsigned nb = (unsigned)((nz * ncoax + 255) / 256);
-    k_z_scale<<<nb, 256, 0, s>>>(p, nz, h->R_Z64, dev + 1);
+    k_z_scale<<<nb, 256, 0, s>>>(p, nz, Z64, dev + 1);
     CKL("k_z_scale");
-    k_check_z_mirror<<<nb, 256, 0, s>>>(p, nz, h->R_Z64, dev + 1, dev);
+    k_check_z_mirror<<<nb, 256, 0, s>>>(p, nz, Z64, dev + 1, dev);
     CKL("k_check_z_mirror");
     unsigned long long hd = 0;
     CK(cudaMemcpyAsync(&hd, dev, sizeof(hd), cudaMemcpyDeviceToHost, s));
@@ -2004,9 +2027,27 @@ void pack_rot_tables(fmbem *h, cudaStream_t s) {
     dev_free(h, dev);
     double zmax;
     std::memcpy(&zmax, &hd, sizeof(double));
-    if (!(zmax < 1e-9))
-        throw fmbem_error{FMBEM_ERR_CUDA, "coaxial translations: Z^-m differs from Z^m (relative " +
-                                              std::to_string(zmax) + ")"};
+    // the projected tables carry quadrature rounding of about 1e-12..1e-8 of their largest entry;
+    // a convention error would show as an O(1) asymmetry
+    if (!(zmax < 1e-6)) {
+        char buf[64];
+        std::snprintf(buf, sizeof(buf), "%.3e", zmax);
+        throw fmbem_error{FMBEM_ERR_CUDA, std::string("coaxial translations: Z^-m differs from Z^m (relative ") + buf + ")"};
+    }
+}
+
+// the coaxial S|R tables R_Z (per domain, level and offset length)
+void pack_rot_tables(fmbem *h, cudaStream_t s) {
+    pack_coax(h, h->R_Z64, h->R_Z32, (int64_t)(h->J + 1) * (h->lmax + 1) * h->n_tlen, s);
+}
+
+// the coaxial S|S and R|R tables (per domain and level) and the octant-grouped child lists of the
+// rotation-form M2M and L2L
+void pack_rot_tables_mm(fmbem *h, cudaStream_t s) {
+    const int64_t nzl = (int64_t)(h->J + 1) * (h->lmax + 1);
+    pack_coax(h, h->R_Zmm64, h->R_Zmm32, nzl, s);
+    pack_coax(h, h->R_Zll64, h->R_Zll32, nzl, s);
+    build_rot_mm_lists(h, s);
 }
 
 // the packed rotation factors from the projected ones: forward T(Rz^T) (azimuthal), T(Ry^T)
@@ -2159,6 +2200,70 @@ void near_work_items(fmbem *h, cudaStream_t s) {
     CK(cudaStreamSynchronize(s));
 }
 
+// The child boxes of every level l >= 3 for the rotation-form M2M and L2L: entries grouped by
+// octant (the child-parent direction), in chunks of at most M2L_CHUNK that share it; each chunk
+// carries the far-field offset code of the same direction for M2M (child to parent, offset
+// (4o-2) per axis) and for L2L (parent to child, the opposite one).
+void build_rot_mm_lists(fmbem *h, cudaStream_t s) {
+    const int lmax = h->lmax;
+    std::vector<uint64_t> key(h->nbox);
+    std::vector<int32_t> par(h->nbox);
+    CK(cudaMemcpyAsync(key.data(), h->box_key, sizeof(uint64_t) * h->nbox, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(par.data(), h->box_parent, sizeof(int32_t) * h->nbox, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int32_t> child, parent, entry(h->nbox, -1), cbeg, ccnt;
+    std::vector<int16_t> cmm, cll;
+    h->h_rmm_first.assign(lmax + 2, 0);
+    h->h_rmm_chunk_first.assign(lmax + 2, 0);
+    for (int l = 0; l <= lmax + 1; ++l) {
+        h->h_rmm_first[l] = (int64_t)child.size();
+        h->h_rmm_chunk_first[l] = (int64_t)cbeg.size();
+        if (l < 3 || l > lmax) continue;
+        const LevelInfo &Lv = h->lev[l];
+        for (int o = 0; o < 8; ++o) {
+            const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;  // Morton bit order x, y, z
+            const int16_t mm = (int16_t)m2l_offset_code(4 * ox - 2, 4 * oy - 2, 4 * oz - 2);
+            const int16_t ll = (int16_t)m2l_offset_code(2 - 4 * ox, 2 - 4 * oy, 2 - 4 * oz);
+            int in_chunk = M2L_CHUNK;
+            for (int64_t g = Lv.off; g < Lv.off + Lv.n; ++g) {
+                if ((int)(key[g] & 7) != o) continue;
+                if (in_chunk == M2L_CHUNK) {
+                    cbeg.push_back((int32_t)child.size());
+                    ccnt.push_back(0);
+                    cmm.push_back(mm);
+                    cll.push_back(ll);
+                    in_chunk = 0;
+                }
+                entry[g] = (int32_t)child.size();
+                child.push_back((int32_t)g);
+                parent.push_back(par[g]);
+                ++ccnt.back();
+                ++in_chunk;
+            }
+        }
+    }
+    h->n_rmm = (int64_t)child.size();
+    if (h->n_rmm == 0) return;
+    std::vector<int32_t> iota(child.size());
+    for (size_t k = 0; k < iota.size(); ++k) iota[k] = (int32_t)k;
+    std::vector<int8_t> zero(316, 0);
+    auto up = [&](auto *&dst, const auto &v) {
+        using T = std::remove_reference_t<decltype(*dst)>;
+        dst = (T *)dev_alloc(h, sizeof(T) * std::max<size_t>(v.size(), 1));
+        CK(cudaMemcpyAsync(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+    };
+    up(h->rmm_iota, iota);
+    up(h->rmm_child, child);
+    up(h->rmm_par, parent);
+    up(h->rmm_entry, entry);
+    up(h->rmm_chunk_beg, cbeg);
+    up(h->rmm_chunk_cnt, ccnt);
+    up(h->rmm_chunk_mm, cmm);
+    up(h->rmm_chunk_ll, cll);
+    up(h->rot_zero, zero);
+    CK(cudaStreamSynchronize(s));
+}
+
 static void ensure_scratch(fmbem *h, int64_t nr) {
     const size_t cb = sizeof(c64);
     if (h->scratch_rhs < nr) {
@@ -2172,8 +2277,11 @@ static void ensure_scratch(fmbem *h, int64_t nr) {
     // sized by the columns of this call, so that a few-column call after a many-column one
     // still takes the chunked path
     if (3 * nr <= 24) {
-        int64_t mp = 1;
-        for (int l = 2; l <= h->lmax; ++l) mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l]);
+        int64_t mp = 1;  // a level's pair results, then (rotation form) its child entries
+        for (int l = 2; l <= h->lmax; ++l) {
+            const int64_t ne = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
+            mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l] + ne);
+        }
         const size_t need = cb * (size_t)mp * (size_t)(3 * nr) * h->p2;
         if (h->ybuf == nullptr || h->ybuf_bytes < need) {
             if (h->ybuf) dev_free(h, h->ybuf);
@@ -2184,6 +2292,38 @@ static void ensure_scratch(fmbem *h, int64_t nr) {
     }
 }
 
+// Launch shape of the rotation-form kernel k_m2l_rot for ncol columns: in double precision
+// groups of exactly p2 threads (a warp may straddle two column groups), so that no lane idles on
+// a padded row in the FP64-bound stages; in single precision, where the kernel is latency-bound,
+// rows padded to whole warps (more threads).  ok is false when the rotation tables were not built
+// or the shape does not fit.
+constexpr int ROT_MAXC = 12;
+struct RotLaunch {
+    bool ok = false;
+    int rows = 0, cg = 1, pc = 0;
+    size_t bytes = 0;
+};
+template <typename R>
+static RotLaunch rot_launch(fmbem *h, int ncol, size_t budget) {
+    RotLaunch rl;
+    if (!h->m2l_rotation || h->R_D64 == nullptr || ncol > 24) return rl;
+    const int p = h->p, p2 = h->p2, nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, k_m2l_rot<R, ROT_MAXC>));
+    auto bytes = [&](int c) {
+        return sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)c * ROT_MAXC * p2) +
+               sizeof(short2) * (size_t)(p * (p + 1) / 2);
+    };
+    rl.rows = sizeof(R) == 4 ? ((p2 + 31) / 32) * 32 : p2;
+    rl.cg = std::max(1, std::min(4, fa.maxThreadsPerBlock / rl.rows));
+    while (rl.cg > 1 && bytes(rl.cg) > budget) --rl.cg;
+    rl.pc = std::min(M2L_CHUNK, rl.cg * ROT_MAXC / ncol);
+    rl.bytes = bytes(rl.cg);
+    rl.ok = rl.pc >= 1 && rl.bytes <= budget && rl.rows * rl.cg <= fa.maxThreadsPerBlock;
+    if (rl.ok) CK(cudaFuncSetAttribute(k_m2l_rot<R, ROT_MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rl.bytes));
+    return rl;
+}
+
 // M2M (Eq. 2.20) from level l_max up to level 2, on the multipole expansions in h->Cexp
 template <typename R>
 static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
@@ -2192,6 +2332,33 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
     cx<R> *C = (cx<R> *)h->Cexp;
     const cx<R> *Tmm = f32 ? (const cx<R> *)h->T_mm32 : (const cx<R> *)h->T_mm64;
     const int rows_pad = ((p2 + 31) / 32) * 32;
+    // rotation form (p >= 9, few columns): the children of each level, by octant, translated to
+    // their parents' centres (folded rotation, coaxial S|S, rotation back), then summed per parent
+    const int ncol = (int)std::min<int64_t>(3 * nr, 24);
+    if (3 * nr <= 24 && h->rmm_chunk_beg != nullptr && h->ybuf != nullptr) {
+        const RotLaunch rl = rot_launch<R>(h, ncol, 200 * 1024);
+        if (rl.ok) {
+            const R *RD = f32 ? (const R *)h->R_D32 : (const R *)h->R_D64;
+            const cx<R> *RP = f32 ? (const cx<R> *)h->R_P32 : (const cx<R> *)h->R_P64;
+            const cx<R> *RZmm = f32 ? (const cx<R> *)h->R_Zmm32 : (const cx<R> *)h->R_Zmm64;
+            cx<R> *Y = (cx<R> *)h->ybuf;
+            for (int l = lmax; l >= 3; --l) {
+                const LevelInfo &P = h->lev[l - 1];
+                const int64_t c0 = h->h_rmm_chunk_first[l], nch = h->h_rmm_chunk_first[l + 1] - c0;
+                const int64_t e_first = h->h_rmm_first[l];
+                for (int d = 0; d <= J; ++d) {
+                    k_m2l_rot<R, ROT_MAXC><<<(unsigned)nch, rl.rows * rl.cg, rl.bytes, s>>>(
+                        c0, l, lmax, d, nr, h->p, h->nbox, 0, ncol, rl.pc, rl.cg, h->rmm_chunk_beg, h->rmm_chunk_cnt,
+                        h->rmm_chunk_mm, h->rmm_iota, h->rmm_child, h->rot_zero, 1, RD, RP, RZmm, C, Y, e_first);
+                    CKL("k_m2l_rot (M2M)");
+                    k_mm_reduce<R><<<(unsigned)P.n, 128, 0, s>>>(P.off, d, nr, p2, h->nbox, 0, ncol, h->box_cbeg,
+                                                                h->box_cend, h->rmm_entry, e_first, Y, C);
+                    CKL("k_mm_reduce");
+                }
+            }
+            return;
+        }
+    }
     for (int l = lmax; l >= 3; --l) {
         const LevelInfo &P = h->lev[l - 1];
         if (nr == 1)
@@ -2237,23 +2404,12 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     const int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
     const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr && rows_pad <= max_thr;
     // rotation form of the chunked S|R (when its tables were built)
-    constexpr int RMAXC = 12;
-    const int pp = h->p, nrot = rot_off(pp), ncoax = pp * (2 * pp * pp + 1) / 3;
-    cudaFuncAttributes fa_r{};
-    CK(cudaFuncGetAttributes(&fa_r, k_m2l_rot<R, RMAXC>));
-    auto rot_bytes = [&](int c) {
-        return sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)c * RMAXC * p2) +
-               sizeof(short2) * (size_t)(pp * (pp + 1) / 2);
-    };
-    // rotation kernel: in double precision groups of exactly p2 threads (a warp may straddle two
-    // column groups), so that no lane idles on a padded row in the FP64-bound stages; in single
-    // precision, where the kernel is latency-bound, rows padded to whole warps (more threads)
-    const int rows_rot = f32 ? rows_pad : p2;
-    int cgr = std::max(1, std::min(4, fa_r.maxThreadsPerBlock / rows_rot));
-    while (cgr > 1 && rot_bytes(cgr) > budget) --cgr;
-    const int pcr = std::min(M2L_CHUNK, cgr * RMAXC / ncol);
-    const bool use_rot = chunked && h->m2l_rotation && h->R_D64 != nullptr && pcr >= 1 && rot_bytes(cgr) <= budget &&
-                         rows_rot <= fa_r.maxThreadsPerBlock;
+    constexpr int RMAXC = ROT_MAXC;
+    const int pp = h->p;
+    const RotLaunch rl = rot_launch<R>(h, ncol, budget);
+    const int rows_rot = rl.rows, cgr = rl.cg, pcr = rl.pc;
+    auto rot_bytes = [&](int) { return rl.bytes; };
+    const bool use_rot = chunked && rl.ok;
     if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
         run_m2l_tc(h, (float *)C, (float *)D, nr, s);
     } else if (chunked) {
@@ -2264,6 +2420,8 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
         const R *RD = f32 ? (const R *)h->R_D32 : (const R *)h->R_D64;
         const cx<R> *RP = f32 ? (const cx<R> *)h->R_P32 : (const cx<R> *)h->R_P64;
         const cx<R> *RZ = f32 ? (const cx<R> *)h->R_Z32 : (const cx<R> *)h->R_Z64;
+        const cx<R> *RZll = f32 ? (const cx<R> *)h->R_Zll32 : (const cx<R> *)h->R_Zll64;
+        const bool use_rot_mm = use_rot && h->rmm_chunk_beg != nullptr;
         cx<R> *Y = (cx<R> *)h->ybuf;
         for (int l = 2; l <= lmax; ++l) {
             const LevelInfo &Lv = h->lev[l];
@@ -2287,10 +2445,23 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
                                 h->chunk_off, h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
                     }
                     CKL("k_m2l_chunks");
+                    // L2L in rotation form: the children of level l, by octant, from their parents'
+                    // local expansions, into the buffer after this level's pair results
+                    cx<R> *Yll = nullptr;
+                    int64_t ll_first = 0;
+                    if (use_rot_mm && l >= 3) {
+                        const int64_t lc0 = h->h_rmm_chunk_first[l], lnch = h->h_rmm_chunk_first[l + 1] - lc0;
+                        ll_first = h->h_rmm_first[l];
+                        Yll = Y + (h->h_pair_first[l + 1] - e_first) * nc * p2;
+                        k_m2l_rot<R, RMAXC><<<(unsigned)lnch, rows_rot * cgr, rot_bytes(cgr), s>>>(
+                            lc0, l, lmax, d, nr, pp, h->nbox, col0, nc, pcr, cgr, h->rmm_chunk_beg, h->rmm_chunk_cnt,
+                            h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP, RZll, D, Yll, ll_first);
+                        CKL("k_m2l_rot (L2L)");
+                    }
                     const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
                     k_l2l_reduce<R><<<(unsigned)Lv.n, rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
                         Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll,
-                        Y, e_first, D);
+                        Y, e_first, D, Yll, h->rmm_entry, ll_first);
                     CKL("k_l2l_reduce");
                 }
         }
@@ -2552,8 +2723,11 @@ static void matvec_static_scratch(fmbem *h, const c64 *x, c64 *y, int64_t nr, cu
     const size_t b_exp = up(S * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
     size_t b_y = 0;
     if (3 * nr <= 24) {
-        int64_t mp = 1;
-        for (int l = 2; l <= h->lmax; ++l) mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l]);
+        int64_t mp = 1;  // as in ensure_scratch: pair results, then the rotation form's child entries
+        for (int l = 2; l <= h->lmax; ++l) {
+            const int64_t ne = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
+            mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l] + ne);
+        }
         b_y = up(S * (size_t)mp * 3 * nr * h->p2);
     }
     const size_t need = b_dens + 2 * b_exp + b_y;

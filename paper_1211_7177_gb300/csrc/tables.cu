@@ -433,6 +433,36 @@ void build_tables(fmbem *h, cudaStream_t s) {
                 run_batch(true, false, h->k[d], w, tv, dz, h->R_Z64, h->R_Z32);
             }
         pack_rot_tables(h, s);
+        // coaxial S|S (M2M, child to parent) and R|R (L2L, parent to child) along z by the half
+        // diagonal sqrt(3) w / 2 of a child box, scaled like the dense S|S and R|R
+        const int64_t nzl = (int64_t)(J + 1) * (lmax + 1);
+        h->R_Zmm64 = (c64 *)dev_alloc(h, sizeof(c64) * nzl * p2 * p2);
+        h->R_Zmm32 = (c32 *)dev_alloc(h, sizeof(c32) * nzl * p2 * p2);
+        h->R_Zll64 = (c64 *)dev_alloc(h, sizeof(c64) * nzl * p2 * p2);
+        h->R_Zll32 = (c32 *)dev_alloc(h, sizeof(c32) * nzl * p2 * p2);
+        CK(cudaMemsetAsync(h->R_Zmm64, 0, sizeof(c64) * nzl * p2 * p2, s));
+        CK(cudaMemsetAsync(h->R_Zmm32, 0, sizeof(c32) * nzl * p2 * p2, s));
+        CK(cudaMemsetAsync(h->R_Zll64, 0, sizeof(c64) * nzl * p2 * p2, s));
+        CK(cudaMemsetAsync(h->R_Zll32, 0, sizeof(c32) * nzl * p2 * p2, s));
+        for (int d = 0; d <= J; ++d)
+            for (int l = 3; l <= lmax; ++l) {
+                const double w = h->lev[l].w, la = h->lam[d * (lmax + 1) + l], lp = h->lam[d * (lmax + 1) + l - 1];
+                const std::vector<double> tv = {0.0, 0.0, 0.5 * sqrt(3.0) * w};
+                const std::vector<int64_t> dz = {(int64_t)d * (lmax + 1) + l};
+                for (int q = 0; q < p2; ++q) {
+                    int n = nof(q);
+                    sr[q] = 1.0 / pow(lp, n + 1);  // output parent multipole
+                    sc[q] = pow(la, n + 1);        // input child multipole
+                }
+                run_batch(true, true, h->k[d], 2 * w, tv, dz, h->R_Zmm64, h->R_Zmm32);
+                for (int q = 0; q < p2; ++q) {
+                    int n = nof(q);
+                    sr[q] = pow(la, n);            // output child local
+                    sc[q] = 1.0 / pow(lp, n);      // input parent local
+                }
+                run_batch(false, false, h->k[d], w, tv, dz, h->R_Zll64, h->R_Zll32);
+            }
+        pack_rot_tables_mm(h, s);
     }
     dev_free(h, F);
     dev_free(h, Yc);

@@ -129,22 +129,27 @@ def test_matvec_options(opt):
         assert err < tol
 
 
-@pytest.mark.parametrize("p", [6, 9, 10])
-def test_m2l_rotation_form_matches_dense(p):
+@pytest.mark.parametrize("p,leaf", [(6, 64), (9, 64), (10, 64), (9, 12), (10, 12)])
+def test_m2l_rotation_form_matches_dense(p, leaf):
     """S|R as rotate - coaxial translate - rotate back must reproduce the dense S|R matrices
-    (both are exact translations of the truncated expansion) and meet the oracle bar."""
+    (both are exact translations of the truncated expansion) and meet the oracle bar.  With
+    leaf_size 12 the tree has level 3, so M2M (S|S) and L2L (R|R) run in the same folded
+    rotation form along the child-parent diagonals, for 1 and 3 right-hand sides."""
     V, F, D = fi.icosphere(4)
     eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
-    gd = fm.FMBEM(V, F, D, eps, mu, k0, p=p, m2l_rotation=0)
-    gr = fm.FMBEM(V, F, D, eps, mu, k0, p=p, m2l_rotation=1)
+    gd = fm.FMBEM(V, F, D, eps, mu, k0, p=p, leaf_size=leaf, m2l_rotation=0)
+    gr = fm.FMBEM(V, F, D, eps, mu, k0, p=p, leaf_size=leaf, m2l_rotation=1)
+    if leaf == 12:
+        assert gr.tree_info()["l_max"] >= 3
     o = oracle.Oracle(V, F, D, eps, mu, k0)
-    x = fi.random_complex((1, o.N, 6), seed=31)
-    yo = o.matvec(x)
-    for prec in (fm.FP64, fm.FP32):
-        yd = gd.matvec(to_dev(x), precision=prec).cpu().numpy()
-        yr = gr.matvec(to_dev(x), precision=prec).cpu().numpy()
-        assert rel(yr, yd) < (1e-10 if prec == fm.FP64 else 2e-6), (p, prec, rel(yr, yd))
-        assert rel(yr, yo) < (2e-4 if p == 6 else MATVEC_TOL)
+    for nr in ((1, 3) if leaf == 12 else (1,)):
+        x = fi.random_complex((nr, o.N, 6), seed=31)
+        yo = o.matvec(x)
+        for prec in (fm.FP64, fm.FP32):
+            yd = gd.matvec(to_dev(x), precision=prec).cpu().numpy()
+            yr = gr.matvec(to_dev(x), precision=prec).cpu().numpy()
+            assert rel(yr, yd) < (1e-10 if prec == fm.FP64 else 2e-6), (p, leaf, nr, prec, rel(yr, yd))
+            assert rel(yr, yo) < (2e-4 if p == 6 else MATVEC_TOL)
 
 
 @pytest.mark.parametrize("n_rhs,p", [(16, 8), (100, 8), (40, 6)])
