@@ -212,9 +212,10 @@ fmbem_status fmbem_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs
 /* Solves A^T x = b, the adjoint (transposed) system of Eq. (2.9), the way fmbem_solve solves
  * A x = b: right-preconditioned restarted GMRES with fmbem_adjoint_matvec as the operator and the
  * transposed preconditioner M^T = A_self^T (applied exactly from the same 6x6 LU), honouring
- * solve_precision, inner_tol and outer_precision (TF32 acts as FP32: the adjoint product has no
- * tensor-core path).  The paper has no adjoint solve; an adjoint (gradient) computation needs it:
- * for an objective J = L^T x with A x = b, dJ/dp = -lambda^T (dA/dp) x with A^T lambda = L.
+ * solve_precision, inner_tol and outer_precision (with TF32 the inner adjoint products run M2L
+ * and L2L on the tensor cores, as the forward ones do).  The paper has no adjoint solve; an
+ * adjoint (gradient) computation needs it: for an objective J = L^T x with A x = b,
+ * dJ/dp = -lambda^T (dA/dp) x with A^T lambda = L.
  * Arguments, layout, return values and errors as for fmbem_solve. */
 fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64_t n_rhs, double tol, int max_iter,
                                  int32_t *iters_host, double *relres_host, void *stream);
@@ -231,6 +232,24 @@ fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64
  * (d, e); the scattering cross section is the integral of |F|^2 over the unit sphere. */
 fmbem_status fmbem_far_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_dir, const double *rhat,
                              fmbem_c64 *F_host, void *stream);
+
+/* Total electric field at points outside every scatterer (Section 4; the representation formula
+ * of Appendix A for the background domain), for solutions x of plane-wave excitations:
+ *   E(r) = e exp(i k0 d.r) + sum_b w_b { n0 (a.Phi_b) - (n0.a) Phi_b - a (n0.Phi_b) + g Psi_b },
+ *   g = exp(i k0 R) / (4 pi R),  a = grad_s g = g (i k0 - 1/R) (s_b - r) / R,  R = |s_b - r|,
+ *   n0 = -n_b (the background's normal).
+ * Direct summation over the N nodes in double precision (no FMM: O(n_pts N) per right-hand side),
+ * for field maps and stress-tensor surfaces off the boundary; a point on or inside the surface
+ * gets no meaningful value.
+ *   x_dev     device [n_rhs][N][6] complex128 (user order), read.
+ *   pts       host [n_pts][3] points.
+ *   dir, pol  host [n_rhs][3] each: the plane waves (direction, polarisation) that produced x, for
+ *             the incident term; both NULL for the scattered field alone.
+ *   E_host    host [n_rhs][n_pts][3] complex128, written.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (n_rhs outside 1..65535, n_pts < 1, a NULL x, pts or E, or
+ * only one of dir and pol), FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
+fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
+                              const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, void *stream);
 
 /* sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (host [n_rhs], written): with
  * n x curl E = Psi the inward flux of the time-averaged Poynting vector, Eq. (4.2), gives the

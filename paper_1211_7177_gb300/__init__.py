@@ -79,6 +79,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_matvec_noalloc": (i32, [P, P, P, i64, i32, P]),
         "fmbem_far_field": (i32, [P, P, i64, i64, P, P, P]),
         "fmbem_absorption": (i32, [P, P, i64, P, P]),
+        "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
     }
@@ -237,6 +238,26 @@ def fmbem_far_field(h, x, rhat, stream=None):
     return F
 
 
+def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None):
+    """Total field E [n_rhs, n_pts, 3] complex128 (host) at exterior points of solutions x of the
+    plane waves (dirs[r], pols[r]); scattered field alone when dirs and pols are None."""
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    n = x.shape[0]
+    pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    if (dirs is None) != (pols is None):
+        raise ValueError("give both dirs and pols, or neither")
+    d = p = None
+    if dirs is not None:
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dirs, dtype=np.float64), (n, 3)))
+        p = np.ascontiguousarray(np.broadcast_to(np.asarray(pols, dtype=np.complex128), (n, 3)))
+    E = np.empty((n, len(pts), 3), dtype=np.complex128)
+    _check(h, load_library().fmbem_near_field(h, ctypes.c_void_p(x.data_ptr()), n, len(pts), _ptr(pts),
+                                              _ptr(d) if d is not None else None,
+                                              _ptr(p) if p is not None else None, _ptr(E), _stream(stream)))
+    return E
+
+
 def fmbem_absorption(h, x, stream=None):
     """sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (C_abs = -this / k0)."""
     N = fmbem_num_nodes(h)
@@ -339,6 +360,9 @@ class FMBEM:
 
     def far_field(self, x, rhat, stream=None):
         return fmbem_far_field(self.h, x, rhat, stream)
+
+    def near_field(self, x, points, dirs=None, pols=None, stream=None):
+        return fmbem_near_field(self.h, x, points, dirs, pols, stream)
 
     def cross_sections(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
         """(C_ext, C_sca, C_abs) per right-hand side for the plane waves (dirs[r], pols[r]) that

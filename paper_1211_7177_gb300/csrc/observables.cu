@@ -1,5 +1,6 @@
-// observables.cu -- quantities of a solution: the far-field amplitude of the scattered field and
-// the absorbed power (Section 4; representation formula of Appendix A in the far zone).
+// observables.cu -- quantities of a solution: the total field at exterior points and the far-field
+// amplitude of the scattered field (Section 4; representation formula of Appendix A, near and in
+// the far zone), and the absorbed power (Eq. 4.2).
 //
 // Far field: with n0 = -n (the outward normal of the background) and Psi0 = -Psi,
 //   F(u) = 1/(4 pi) sum_b w_b exp(-i k0 u.s_b) { (-i k0) [n0 (u.Phi_b) - (n0.u) Phi_b - u (n0.Phi_b)]
@@ -70,7 +71,90 @@ __global__ void __launch_bounds__(OB_TB) k_absorption(int64_t N, const double *w
     if (threadIdx.x == 0) out[r] = red[0];
 }
 
+// Total field at exterior points, direct summation over the nodes (see fmbem_near_field): one
+// thread per point, a block per (tile of OB_NT points, right-hand side), the nodes staged in
+// shared memory OB_NS at a time.  inc = 0: scattered field only.
+constexpr int OB_NT = 128, OB_NS = 64;
+__global__ void __launch_bounds__(OB_NT) k_near_field(int64_t N, const double *pos, const double *nrm, const double *w,
+                                                    const c64 *x, int64_t n_pts, const double *pts, c64 k0,
+                                                    const double *dir, const c64 *pol, c64 *E) {
+    __shared__ double sp[OB_NS][3], sn[OB_NS][3], sw[OB_NS];
+    __shared__ c64 sx[OB_NS][6];
+    const int64_t pt = blockIdx.x * (int64_t)OB_NT + threadIdx.x, r = blockIdx.y;
+    const bool valid = pt < n_pts;
+    const double t[3] = {valid ? pts[3 * pt] : 0.0, valid ? pts[3 * pt + 1] : 0.0, valid ? pts[3 * pt + 2] : 0.0};
+    c64 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (dir != nullptr && pol != nullptr) {  // incident plane wave e exp(i k0 d.r)
+        const double *d = dir + 3 * r;
+        const c64 ph = cexpd(c64{-k0.im, k0.re} * (d[0] * t[0] + d[1] * t[1] + d[2] * t[2]));
+        for (int q = 0; q < 3; ++q) acc[q] = pol[3 * r + q] * ph;
+    }
+    const c64 ik = {-k0.im, k0.re};
+    for (int64_t b0 = 0; b0 < N; b0 += OB_NS) {
+        const int nb = (int)min((int64_t)OB_NS, N - b0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+            const int64_t b = b0 + e;
+            for (int q = 0; q < 3; ++q) { sp[e][q] = pos[3 * b + q]; sn[e][q] = -nrm[3 * b + q]; }
+            sw[e] = w[b];
+        }
+        for (int e = threadIdx.x; e < 6 * nb; e += blockDim.x) sx[e / 6][e % 6] = x[(r * N + b0) * 6 + e];
+        __syncthreads();
+        if (!valid) continue;
+        for (int e = 0; e < nb; ++e) {
+            const double rv[3] = {sp[e][0] - t[0], sp[e][1] - t[1], sp[e][2] - t[2]};
+            const double R = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+            const c64 g = cexpd(ik * R) * (1.0 / (4.0 * FMBEM_PI * R));
+            const c64 c = g * (ik - c64{1.0 / R, 0}) * (1.0 / R);  // grad_s g = c (s - r)
+            const double *n0 = sn[e];
+            const c64 *Phi = sx[e], *Psi = sx[e] + 3;
+            const c64 rP = rv[0] * Phi[0] + rv[1] * Phi[1] + rv[2] * Phi[2];
+            const c64 nP = n0[0] * Phi[0] + n0[1] * Phi[1] + n0[2] * Phi[2];
+            const double nr = n0[0] * rv[0] + n0[1] * rv[1] + n0[2] * rv[2];
+            for (int q = 0; q < 3; ++q) {
+                // n0 (a.Phi) - (n0.a) Phi - a (n0.Phi) with a = c rv, plus g Psi
+                const c64 br = c * (n0[q] * rP - nr * Phi[q] - rv[q] * nP);
+                acc[q] += sw[e] * (br + g * Psi[q]);
+            }
+        }
+    }
+    if (valid)
+        for (int q = 0; q < 3; ++q) E[(r * n_pts + pt) * 3 + q] = acc[q];
+}
+
 }  // namespace
+
+void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host, const double *dir_host,
+                    const c64 *pol_host, c64 *E_host, cudaStream_t s) {
+    double *dp = (double *)dev_alloc(h, sizeof(double) * 3 * n_pts);
+    c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr);
+    double *dd = nullptr;
+    c64 *dpol = nullptr;
+    auto cleanup = [&] {
+        dev_free(h, dp);
+        dev_free(h, dE);
+        if (dd) dev_free(h, dd);
+        if (dpol) dev_free(h, dpol);
+    };
+    try {
+        CK(cudaMemcpyAsync(dp, pts_host, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, s));
+        if (dir_host && pol_host) {
+            dd = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
+            dpol = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
+            CK(cudaMemcpyAsync(dd, dir_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(dpol, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        }
+        k_near_field<<<dim3((unsigned)((n_pts + OB_NT - 1) / OB_NT), (unsigned)nr), OB_NT, 0, s>>>(
+            h->N, h->upos, h->unrm, h->uw, x, n_pts, dp, h->k[0], dd, dpol, dE);
+        CKL("k_near_field");
+        CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
 
 void run_far_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_dir, const double *rhat_host, c64 *F_host,
                    cudaStream_t s) {

@@ -316,6 +316,28 @@ def test_far_field_and_cross_sections_match_oracle(sphere_s4):
         assert abs(ce[r] - cs[r] - ca[r]) < 0.1 * ce[r]  # optical theorem, to discretisation error
 
 
+def test_near_field_matches_oracle(sphere_s4):
+    """Total field at exterior points (the circle of radius 2a of Fig. 4 and points off the axes)
+    from a solved plane-wave problem, evaluated on the device by direct summation against the
+    oracle's evaluation of the same solution; the scattered field alone is the total minus the
+    incident plane wave."""
+    o, g = sphere_s4
+    dirs, pols = fi.plane_wave_batch(2, seed=6)
+    x, _, _, st = g.solve(g.plane_wave_rhs(dirs, pols), tol=1e-8)
+    assert st == 0
+    xh = x.cpu().numpy()
+    th = np.linspace(0, 2 * np.pi, 37)[:-1]
+    pts = np.concatenate([2.0 * np.stack([np.cos(th), np.zeros_like(th), np.sin(th)], -1),
+                          [[1.3, 0.4, -0.2], [0.0, -3.0, 0.5], [5.0, 5.0, 5.0]]])
+    E = g.near_field(x, pts, dirs, pols)
+    Es = g.near_field(x, pts)
+    for r in range(2):
+        ref = o.near_field(xh[r], pts, dirs[r], pols[r])
+        np.testing.assert_allclose(E[r], ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+        inc = pols[r][None, :] * np.exp(1j * o.k[0] * (pts @ dirs[r]))[:, None]
+        np.testing.assert_allclose(Es[r], E[r] - inc, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
