@@ -53,8 +53,11 @@ UNIT = "points*RHS/s"
 NEAR_PAIR = 52
 NEAR_RHS = 78
 # FP64 with fewer than 4 right-hand sides reads g and c from the near-field cache built at create:
-# per (pair, domain) only r, w = n x r and n.r remain
-NEAR_PAIR_CACHED = 17
+# per pair only r, w = n x r and n.r remain (14 flops, shared by both domains), and the scatterer
+# domain's bracket is the background's plus s r (6 FFMA per RHS instead of u's 30 flops): per
+# (pair, domain) 7 + 69 per right-hand side, averaged over the two domains
+NEAR_PAIR_CACHED = 7
+NEAR_RHS_CACHED = 69
 PEAK_TFLOPS = {"fp64": 1.2, "fp32": 74.6}  # measured FMA throughput on GB300 (self-written probe)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor-core rate
 
@@ -204,8 +207,9 @@ def roofline(info, p, nr, n_dom, phases, precision):
         flops = per_col * 3 * nr * info["ff_pairs"] * n_dom
         name = f"M2L + L2L, {form}"
     elif dom == "near_l2p_self":
-        per_pair = NEAR_PAIR_CACHED if precision == "fp64" and nr < 4 else NEAR_PAIR
-        flops = info["near_pairs"] * n_dom * (per_pair + NEAR_RHS * nr)
+        cached = precision == "fp64" and nr < 4
+        per_pair, per_rhs = (NEAR_PAIR_CACHED, NEAR_RHS_CACHED) if cached else (NEAR_PAIR, NEAR_RHS)
+        flops = info["near_pairs"] * n_dom * (per_pair + per_rhs * nr)
         name = "near field + L2P + self (k_near, k_near_w, k_near_r)"
     else:
         flops, name = None, dom

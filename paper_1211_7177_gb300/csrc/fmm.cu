@@ -787,6 +787,7 @@ struct SrcTile {
     V4<R> pb[128];      // position low part (double-float only) and n_x
     V2<R> pn[128];      // n_y, n_z
     V4<R> dv[2][3][128];  // densities (v0, v1), (v2, q0), (q1, q2) of the current RHS, both sides
+    V2<R> sn[128];        // s = n.(v_side1 - v_side0): the scatterer's dipole density is v_0 + s n
 };
 template <typename R>
 union NearSmem {
@@ -929,6 +930,13 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                             for (int c = 0; c < 3; ++c)
                                 T.dv[sd][c][t] = V4<R>{dn[2 * c].re, dn[2 * c].im, dn[2 * c + 1].re, dn[2 * c + 1].im};
                         }
+                        if (cache) {  // the scatterer side's v differs from the background's along n only
+                            const cx<R> *d0 = dens + (r * N + i) * 6, *d1 = dens + ((nr + r) * N + i) * 6;
+                            const R nv[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+                            cx<R> sv = {0, 0};
+                            for (int c = 0; c < 3; ++c) sv += nv[c] * (d1[c] - d0[c]);
+                            T.sn[t] = V2<R>{sv.re, sv.im};
+                        }
                     }
                 }
                 __syncthreads();
@@ -950,19 +958,36 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                             q[0] = {a1.z, a1.w}; q[1] = {a2.x, a2.y}; q[2] = {a2.z, a2.w};
                         }
                         if (cs0) {
-                            // g and c from the cache; only the normal-dependent w = n x r and n.r here
+                            // g and c from the cache; only the normal-dependent part here.  With
+                            // w = n x r, U = w x v_0 + (n.r) v_0 is the background's bracket up to sign
+                            // (its normal is -n), and since (n x r) x n + (n.r) n = r for a unit n,
+                            // the scatterer side's bracket for v_0 + s n is U + s r
                             const int64_t e = s0 + u;
                             const R w1[3] = {pn.x * rz - pn.y * ry, pn.y * rx - pb.w * rz, pb.w * ry - pn.x * rx};
                             const R nr1 = pb.w * rx + pn.x * ry + pn.y * rz;
-                            const R w0[3] = {-w1[0], -w1[1], -w1[2]};
+                            const cx<R> U[3] = {w1[1] * v[2] - w1[2] * v[1] + nr1 * v[0],
+                                                w1[2] * v[0] - w1[0] * v[2] + nr1 * v[1],
+                                                w1[0] * v[1] - w1[1] * v[0] + nr1 * v[2]};
                             const V4<R> s0v = cs0[e * NT];
-                            cross_apply<R>(w0, -nr1, cx<R>{s0v.x, s0v.y}, cx<R>{s0v.z, s0v.w}, v, q, acc0);
+                            const cx<R> mc0 = {-s0v.z, -s0v.w}, g0 = {s0v.x, s0v.y};
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                cfma(acc0[c], mc0, U[c]);
+                                cfma(acc0[c], g0, q[c]);
+                            }
                             if (pa.w == adom_r) {
-                                const V4<R> a0 = T.dv[1][0][u], a1 = T.dv[1][1][u], a2 = T.dv[1][2][u];
-                                v[0] = {a0.x, a0.y}; v[1] = {a0.z, a0.w}; v[2] = {a1.x, a1.y};
-                                q[0] = {a1.z, a1.w}; q[1] = {a2.x, a2.y}; q[2] = {a2.z, a2.w};
+                                const V4<R> a1 = T.dv[1][1][u], a2 = T.dv[1][2][u];
+                                const cx<R> q1[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                                const V2<R> sv = T.sn[u];
+                                const cx<R> sc = {sv.x, sv.y};
+                                const R rr[3] = {rx, ry, rz};
                                 const V4<R> s1v = cs0[((int64_t)nsrc + e) * NT];
-                                cross_apply<R>(w1, nr1, cx<R>{s1v.x, s1v.y}, cx<R>{s1v.z, s1v.w}, v, q, acc1);
+                                const cx<R> c1 = {s1v.z, s1v.w}, g1 = {s1v.x, s1v.y};
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    cfma(acc1[c], c1, U[c] + rr[c] * sc);
+                                    cfma(acc1[c], g1, q1[c]);
+                                }
                             }
                             continue;
                         }
