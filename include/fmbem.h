@@ -233,6 +233,19 @@ fmbem_status fmbem_adjoint_solve(fmbem *h, const void *b_dev, void *x_dev, int64
 fmbem_status fmbem_far_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_dir, const double *rhat,
                              fmbem_c64 *F_host, void *stream);
 
+/* The far-field amplitude as a linear functional of the solution, for adjoint gradients of
+ * far-field observables: out[r] holds the coefficients of x -> c_r . F(u_r) (F as for
+ * fmbem_far_field, no conjugation), so that c_r . F(u_r) = sum_b out[r][b] . x[r][b].  With
+ * c = (4 pi / k0) conj(e) and u = d, Im of the functional is the extinction cross section of the
+ * plane wave (d, e); an adjoint solve with out as the right-hand side then gives its derivative
+ * with respect to any parameter p of A as -Im(lambda^T (dA/dp) x).
+ *   rhat   host [n_rhs][3] unit directions u_r.
+ *   coef   host [n_rhs][3] complex128 vectors c_r.
+ *   out_dev device [n_rhs][N][6] complex128 (user order), written.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (n_rhs outside 1..65535, NULL pointers), FMBEM_ERR_CUDA. */
+fmbem_status fmbem_far_field_functional(fmbem *h, int64_t n_rhs, const double *rhat, const fmbem_c64 *coef,
+                                        void *out_dev, void *stream);
+
 /* Total electric field at points outside every scatterer (Section 4; the representation formula
  * of Appendix A for the background domain), for solutions x of plane-wave excitations:
  *   E(r) = e exp(i k0 d.r) + sum_b w_b { n0 (a.Phi_b) - (n0.a) Phi_b - a (n0.Phi_b) + g Psi_b },

@@ -80,6 +80,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_far_field": (i32, [P, P, i64, i64, P, P, P]),
         "fmbem_absorption": (i32, [P, P, i64, P, P]),
         "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
+        "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
     }
@@ -258,6 +259,20 @@ def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None):
     return E
 
 
+def fmbem_far_field_functional(h, rhat, coef, stream=None):
+    """Coefficients [n, N, 6] complex128 (CUDA) of x -> coef[r] . F(rhat[r]) per right-hand side."""
+    import torch
+    N = fmbem_num_nodes(h)
+    rhat = np.ascontiguousarray(np.atleast_2d(rhat), dtype=np.float64)
+    coef = np.ascontiguousarray(np.atleast_2d(coef), dtype=np.complex128)
+    if rhat.shape != coef.shape or rhat.shape[1] != 3:
+        raise ValueError("rhat and coef must both be [n, 3]")
+    out = torch.empty((len(rhat), N, 6), dtype=torch.complex128, device="cuda")
+    _check(h, load_library().fmbem_far_field_functional(h, len(rhat), _ptr(rhat), _ptr(coef),
+                                                        ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
 def fmbem_absorption(h, x, stream=None):
     """sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (C_abs = -this / k0)."""
     N = fmbem_num_nodes(h)
@@ -363,6 +378,9 @@ class FMBEM:
 
     def near_field(self, x, points, dirs=None, pols=None, stream=None):
         return fmbem_near_field(self.h, x, points, dirs, pols, stream)
+
+    def far_field_functional(self, rhat, coef, stream=None):
+        return fmbem_far_field_functional(self.h, rhat, coef, stream)
 
     def cross_sections(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
         """(C_ext, C_sca, C_abs) per right-hand side for the plane waves (dirs[r], pols[r]) that

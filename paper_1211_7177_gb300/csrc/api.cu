@@ -298,6 +298,18 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
     });
 }
 
+fmbem_status fmbem_far_field_functional(fmbem *h, int64_t n_rhs, const double *rhat, const fmbem_c64 *coef,
+                                        void *out_dev, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_rhs > 65535 || !rhat || !coef || !out_dev) {
+        h->err = "invalid argument (n_rhs in 1..65535, non-NULL pointers)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_far_field_functional(h, n_rhs, rhat, (const c64 *)coef, (c64 *)out_dev, (cudaStream_t)stream);
+    });
+}
+
 fmbem_status fmbem_absorption(fmbem *h, const void *x_dev, int64_t n_rhs, double *out_host, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (n_rhs < 1 || !x_dev || !out_host) {

@@ -51,6 +51,29 @@ __global__ void __launch_bounds__(OB_TB) k_far_field(int64_t N, const double *po
     }
 }
 
+// Coefficients of the linear functional x -> c_r . F(u_r) of each right-hand side's solution:
+// out[r][b] = (d/dPhi_b, d/dPsi_b) of 1/(4 pi) w_b e_b { -i k0 [(c.n0)(u.Phi_b) - (n0.u)(c.Phi_b)
+// - (c.u)(n0.Phi_b)] + c.Psi_b }, e_b = exp(-i k0 u.s_b), so that c . F(u) = sum_b out[r][b] . x_b
+// (no conjugation).  One thread per (node, right-hand side), nodes in user order.
+__global__ void k_far_field_functional(int64_t N, int64_t nr, const double *pos, const double *nrm, const double *w,
+                                       const double *rhat, const c64 *coef, c64 k0, c64 *out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (b >= N) return;
+    const double u[3] = {rhat[3 * r], rhat[3 * r + 1], rhat[3 * r + 2]};
+    const c64 c[3] = {coef[3 * r], coef[3 * r + 1], coef[3 * r + 2]};
+    const double n0[3] = {-nrm[3 * b], -nrm[3 * b + 1], -nrm[3 * b + 2]};
+    const c64 mik = c64{k0.im, -k0.re};  // -i k0
+    const double us = u[0] * pos[3 * b] + u[1] * pos[3 * b + 1] + u[2] * pos[3 * b + 2];
+    const c64 f = cexpd(mik * us) * (w[b] / (4.0 * FMBEM_PI));
+    const c64 cn = c[0] * n0[0] + c[1] * n0[1] + c[2] * n0[2], cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+    const double nu = n0[0] * u[0] + n0[1] * u[1] + n0[2] * u[2];
+    c64 *o = out + (r * N + b) * 6;
+    for (int q = 0; q < 3; ++q) {
+        o[q] = f * mik * (cn * u[q] - nu * c[q] - cu * n0[q]);
+        o[3 + q] = f * c[q];
+    }
+}
+
 // out[r] = sum_b w_b Im(Phi_b . conj(Psi_b)); one block per right-hand side
 __global__ void __launch_bounds__(OB_TB) k_absorption(int64_t N, const double *w, const c64 *x, double *out) {
     __shared__ double red[OB_TB];
@@ -174,6 +197,26 @@ void run_far_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_dir, const doub
     }
     dev_free(h, dr);
     dev_free(h, dF);
+}
+
+void run_far_field_functional(fmbem *h, int64_t nr, const double *rhat_host, const c64 *coef_host, c64 *out,
+                              cudaStream_t s) {
+    double *dr = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
+    c64 *dc = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
+    try {
+        CK(cudaMemcpyAsync(dr, rhat_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dc, coef_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        k_far_field_functional<<<dim3((unsigned)((h->N + 127) / 128), (unsigned)nr), 128, 0, s>>>(
+            h->N, nr, h->upos, h->unrm, h->uw, dr, dc, h->k[0], out);
+        CKL("k_far_field_functional");
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        dev_free(h, dr);
+        dev_free(h, dc);
+        throw;
+    }
+    dev_free(h, dr);
+    dev_free(h, dc);
 }
 
 void run_absorption(fmbem *h, const c64 *x, int64_t nr, double *out_host, cudaStream_t s) {

@@ -338,6 +338,57 @@ def test_near_field_matches_oracle(sphere_s4):
         np.testing.assert_allclose(Es[r], E[r] - inc, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
 
 
+def test_far_field_functional_and_extinction_eps_gradient():
+    """The far-field functional reproduces c . F(u) of fmbem_far_field (bilinear identity); the
+    adjoint gradient of C_ext with respect to Re and Im of the sphere's permittivity matches
+    central finite differences (h = 1e-6) of C_ext from full GPU solves, and those of the
+    oracle's dense solves (to the FMM error)."""
+    from paper_1211_7177_gb300 import gradients as gr
+    V, F, D = fi.icosphere(3)
+    eps, mu, k0 = [1.0, -4.0 + 0.5j], [1.0, 1.0], 1.0
+    dirs, pols = fi.plane_wave_batch(1, seed=8)  # one direction, two polarisations
+    g = fm.FMBEM(V, F, D, eps, mu, k0)
+    x, _, _, st = g.solve(g.plane_wave_rhs(dirs, pols), tol=1e-12)
+    assert st == 0
+    c = fi.random_complex((2, 3), seed=9)
+    rh = fi.fibonacci_directions(2, seed=10)
+    L = g.far_field_functional(rh, c)
+    Fv = g.far_field(x, rh)
+    lhs = torch.sum(L * x, dim=(1, 2)).cpu().numpy()
+    for r in range(2):
+        assert abs(lhs[r] - np.dot(c[r], Fv[r, r])) < 1e-10 * abs(lhs[r])
+    cext, dre, dim_ = gr.extinction_eps_gradient(V, F, D, eps, mu, k0, dirs, pols, j=1, tol=1e-12)
+    np.testing.assert_allclose(cext, g.cross_sections(x, dirs, pols, n_theta=8, n_phi=16)[0], rtol=1e-12)
+    h = 1e-6
+
+    def cext_gpu(e1):
+        gg = fm.FMBEM(V, F, D, [1.0, e1], mu, k0)
+        xx, _, _, s_ = gg.solve(gg.plane_wave_rhs(dirs, pols), tol=1e-12)
+        assert s_ == 0
+        return gr.extinction(gg, xx, dirs, pols)
+
+    def cext_oracle(e1):
+        o = oracle.Oracle(V, F, D, [1.0, e1], mu, k0)
+        xo, _, _, conv = o.gmres(o.plane_wave_rhs(dirs, pols), tol=1e-12)
+        assert conv.all()
+        return np.array([o.cross_sections(xo[r], dirs[r], pols[r], n_theta=8, n_phi=16)[0] for r in range(2)])
+
+    e1 = eps[1]
+    fd_re = (cext_gpu(e1 + h) - cext_gpu(e1 - h)) / (2 * h)
+    fd_im = (cext_gpu(e1 + 1j * h) - cext_gpu(e1 - 1j * h)) / (2 * h)
+    print("C_ext", cext, "adjoint", dre, dim_, "FD", fd_re, fd_im)
+    np.testing.assert_allclose(dre, fd_re, rtol=1e-4, atol=1e-6 * np.abs(fd_re).max())
+    np.testing.assert_allclose(dim_, fd_im, rtol=1e-4, atol=1e-6 * np.abs(fd_im).max())
+    # against the dense operator the gradient differs by the FMM approximation (p = 8): compare
+    # the gradient (d/dRe, d/dIm) as a vector, relative to its length
+    or_re = (cext_oracle(e1 + h) - cext_oracle(e1 - h)) / (2 * h)
+    or_im = (cext_oracle(e1 + 1j * h) - cext_oracle(e1 - 1j * h)) / (2 * h)
+    print("oracle FD", or_re, or_im)
+    for r in range(2):
+        ga, go = np.array([dre[r], dim_[r]]), np.array([or_re[r], or_im[r]])
+        assert np.linalg.norm(ga - go) < 1e-3 * np.linalg.norm(go), (ga, go)
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
