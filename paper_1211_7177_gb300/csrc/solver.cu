@@ -22,7 +22,9 @@ namespace {
 
 using cd = std::complex<double>;
 constexpr int DOT_TB = 256;
-constexpr int MD_E = 4;  // elements of each vector per thread in the inner products
+// elements of each vector per thread in the inner products: 16 when that still gives several
+// blocks per SM (batches), 4 otherwise (a single right-hand side)
+constexpr int MD_E_BIG = 16, MD_E_SMALL = 4;
 constexpr int MD_G = 8;  // basis vectors per block reduction
 
 inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
@@ -37,7 +39,7 @@ __device__ __forceinline__ cx<R> load_as(const T *p, int64_t i) {
 // i = 0..nv-1 (V_i[r] at V + (i * nr + r) * n), in arithmetic R; the warps' sums are combined
 // in double precision.  The block keeps its slice of w in registers and walks the basis vectors
 // MD_G at a time, so w is read once and every basis vector once.
-template <typename TV, typename TW, typename R>
+template <typename TV, typename TW, typename R, int MD_E>
 __global__ void __launch_bounds__(DOT_TB) k_multidot(const TV *V, int nv, const TW *w, int64_t n, int64_t nr,
                                                     c64 *partial) {
     __shared__ double sre[MD_G][DOT_TB / 32], sim[MD_G][DOT_TB / 32];
@@ -153,7 +155,7 @@ struct Work {
     fmbem *h;
     cudaStream_t s;
     int64_t n, nr;
-    int nblocks;
+    int nblocks, md_e;
     c64 *partial, *dres;
     void *dcoef;
     std::vector<c64> hres;
@@ -161,7 +163,10 @@ struct Work {
     // dots[r][i] = <V_i[r], w[r]> for i < nv, arithmetic R
     template <typename R, typename TV, typename TW>
     void dots(const TV *V, int nv, const TW *w, std::vector<cd> &out) {
-        k_multidot<TV, TW, R><<<dim3(nblocks, (unsigned)nr), DOT_TB, 0, s>>>(V, nv, w, n, nr, partial);
+        if (md_e == MD_E_BIG)
+            k_multidot<TV, TW, R, MD_E_BIG><<<dim3(nblocks, (unsigned)nr), DOT_TB, 0, s>>>(V, nv, w, n, nr, partial);
+        else
+            k_multidot<TV, TW, R, MD_E_SMALL><<<dim3(nblocks, (unsigned)nr), DOT_TB, 0, s>>>(V, nv, w, n, nr, partial);
         CKL("k_multidot");
         const int64_t cnt = nr * nv;
         k_reduce_partials<<<nblk(cnt * 32, 256), 256, 0, s>>>(partial, nblocks, cnt, dres);
@@ -203,8 +208,7 @@ void precond(fmbem *h, const c64 *v, c64 *z, int64_t nr, cudaStream_t s, bool tr
 }
 void precond(fmbem *h, const c32 *v, c64 *z, int64_t nr, cudaStream_t s, bool tr) { run_precond32(h, v, z, nr, s, tr); }
 
-// the operator of the solve: A (Eq. 2.9) or, for the adjoint solve, A^T (which has no tensor-core
-// path, so TF32 falls back to FP32)
+// the operator of the solve: A (Eq. 2.9) or, for the adjoint solve, A^T
 void apply_op(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s, bool tr) {
     if (tr) run_adjoint_matvec(h, x, y, nr, precision, s);
     else run_matvec(h, x, y, nr, precision, s);
@@ -270,7 +274,8 @@ void gmres(fmbem *h, Work &W, int precision, bool tr, const c64 *rhs, c64 *x, do
             precond(h, V + (int64_t)j * nr * n, z, nr, s, tr);
             apply_op(h, z, w, nr, precision, s, tr);
             ++total;
-            // classical Gram-Schmidt, twice
+            // classical Gram-Schmidt, twice (a Daniel-Gragg-Kaufman-Stewart test for skipping the
+            // second pass found it needed in 199 of 202 iterations of the 128-RHS torus solve)
             std::vector<cd> hc(nr * (j + 1), cd(0, 0));
             for (int pass = 0; pass < 2; ++pass) {
                 std::vector<cd> d;
@@ -360,7 +365,8 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
     W.s = s;
     W.n = n;
     W.nr = nr;
-    W.nblocks = (int)nblk(n, DOT_TB * MD_E);
+    W.md_e = (int64_t)nr * nblk(n, DOT_TB * MD_E_BIG) >= 8 * 152 ? MD_E_BIG : MD_E_SMALL;
+    W.nblocks = (int)nblk(n, DOT_TB * W.md_e);
     const size_t pb = sizeof(c64) * (size_t)nr * (m + 1) * W.nblocks;
     W.partial = (c64 *)dev_alloc(h, pb);
     W.dres = (c64 *)dev_alloc(h, sizeof(c64) * nr * (m + 1));
