@@ -623,6 +623,161 @@ __global__ void __launch_bounds__(512) k_m2l_rot(int64_t chunk0, int l, int lmax
     }
 }
 
+// The same folded rotation form with the columns across the lanes (double precision, where the
+// FP64 pipe is the bound): the block takes up to ROTC_N columns (pc pairs x ncol) per pass and a
+// warp works one folded slot at a time with one column per lane, so that all lanes of a warp run
+// loops of the same length and read the broadcast table entries; the warps deal the slots,
+// ordered by loop length, in snake order.  Same arguments and results as k_m2l_rot (cg unused).
+constexpr int ROTC_N = 32;      // columns per pass (one per lane)
+constexpr int ROTC_S = ROTC_N + 1;  // row stride of the staged coefficients (conflict-free both ways)
+constexpr int ROTC_WARPS = 16;
+template <typename R>
+__global__ void __launch_bounds__(32 * ROTC_WARPS) k_m2l_rot_cols(
+    int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox, int col0, int ncol, int pc, int cg,
+    const int32_t *chunk_beg, const int32_t *chunk_cnt, const int16_t *chunk_off, const int32_t *pair_e,
+    const int32_t *ff_src, const int8_t *tidx, int n_tlen, const R *RD, const cx<R> *RP, const cx<R> *RZ,
+    const cx<R> *C, cx<R> *Y, int64_t e_first) {
+    const int p2 = p * p;
+    const int nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *Df = reinterpret_cast<R *>(smem_raw);
+    R *Db = Df + nrot;
+    cx<R> *Pf = reinterpret_cast<cx<R> *>(Db + nrot);
+    cx<R> *Pb = Pf + p2;
+    cx<R> *Zb = Pb + p2;
+    cx<R> *X = Zb + ncoax;         // [p2][ROTC_S]
+    cx<R> *U = X + p2 * ROTC_S;    // [p2][ROTC_S]
+    short2 *itab = reinterpret_cast<short2 *>(U + p2 * ROTC_S);
+    const int nitem = p * (p + 1) / 2;
+    for (int i = threadIdx.x; i < nitem; i += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= i) ++n;
+        itab[i] = make_short2((short)n, (short)(i - n * (n + 1) / 2));
+    }
+    const int64_t ck = chunk0 + blockIdx.x;
+    const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+    const int o = chunk_off[ck];
+    const R *D2 = RD + (int64_t)o * 2 * nrot;
+    const cx<R> *P2 = RP + (int64_t)o * 2 * p2;
+    const cx<R> *Z = RZ + (((int64_t)d * (lmax + 1) + l) * n_tlen + tidx[o]) * ncoax;
+    for (int i = threadIdx.x; i < 2 * nrot; i += blockDim.x) Df[i] = D2[i];
+    for (int i = threadIdx.x; i < 2 * p2; i += blockDim.x) Pf[i] = P2[i];
+    for (int i = threadIdx.x; i < ncoax; i += blockDim.x) Zb[i] = Z[i];
+    const int warp = threadIdx.x >> 5, c = threadIdx.x & 31;
+    for (int b0 = 0; b0 < cnt; b0 += pc) {
+        const int np = min(pc, cnt - b0);
+        const int nct = np * ncol;
+        __syncthreads();
+        // load with the forward phase and fold (as in k_m2l_rot), one (item, column) per thread
+        for (int i = threadIdx.x; i < nitem * ROTC_N; i += blockDim.x) {
+            const int it = i / ROTC_N, j = i - it * ROTC_N;
+            const short2 tn = itab[it];
+            const int n = tn.x, mm = tn.y, c0 = n * n + n;
+            cx<R> va = {0, 0}, vb = {0, 0};
+            if (j < nct) {
+                const int pr = j / ncol, cc = j - pr * ncol;
+                const cx<R> *src = C + (((int64_t)d * nbox + ff_src[pair_e[beg + b0 + pr]]) * 3 * nr + col0 + cc) * p2;
+                if (mm == 0) {
+                    va = src[c0] * Pf[c0];
+                } else {
+                    const cx<R> xp = src[c0 + mm], xm = src[c0 - mm], e = Pf[c0 + mm];
+                    const cx<R> sum = xp + xm, dif = xp - xm;
+                    va = cx<R>{e.re * sum.re - e.im * dif.im, e.re * sum.im + e.im * dif.re};
+                    vb = cx<R>{e.re * dif.re - e.im * sum.im, e.re * dif.im + e.im * sum.re};
+                }
+            }
+            X[(n * n + mm) * ROTC_S + j] = va;
+            if (mm > 0) X[(n * n + n + mm) * ROTC_S + j] = vb;
+        }
+        __syncthreads();
+        // stage 1: folded polar rotation; slot k (by loop length) goes to warp k in snake order
+        for (int k0 = 0; k0 < p2; k0 += ROTC_WARPS) {
+            const int k = k0 + (((k0 / ROTC_WARPS) & 1) ? ROTC_WARPS - 1 - warp : warp);
+            if (k >= p2) continue;
+            const int r13 = slot_by_rowlen(p, k);
+            int n1 = (int)sqrtf((float)r13);
+            while (n1 * n1 > r13) --n1;
+            while ((n1 + 1) * (n1 + 1) <= r13) ++n1;
+            const int sl1 = r13 - n1 * n1;
+            const bool plus1 = sl1 <= n1;
+            const int am1 = plus1 ? sl1 : sl1 - n1;
+            const R *a = Df + rot_off(n1) + (plus1 ? sl1 * (n1 + 1) : (n1 + 1) * (n1 + 1) + (am1 - 1) * n1);
+            const int flen = plus1 ? n1 + 1 : n1, fin = plus1 ? n1 * n1 : n1 * n1 + n1 + 1;
+            cx<R> acc = {0, 0};
+            for (int jj = 0; jj < flen; ++jj) {
+                const R t = a[jj];
+                const cx<R> xv = X[(fin + jj) * ROTC_S + c];
+                acc.re = fma(t, xv.re, acc.re);
+                acc.im = fma(t, xv.im, acc.im);
+            }
+            U[r13 * ROTC_S + c] = acc;
+        }
+        __syncthreads();
+        // stage 2: coaxial translation, slot k by coaxial row length
+        for (int k0 = 0; k0 < p2; k0 += ROTC_WARPS) {
+            const int k = k0 + (((k0 / ROTC_WARPS) & 1) ? ROTC_WARPS - 1 - warp : warp);
+            if (k >= p2) continue;
+            const int r2 = slot_by_order(p, k);
+            int n2 = (int)sqrtf((float)r2);
+            while (n2 * n2 > r2) --n2;
+            while ((n2 + 1) * (n2 + 1) <= r2) ++n2;
+            const bool plus2 = r2 - n2 * n2 <= n2;
+            const int am2 = plus2 ? r2 - n2 * n2 : r2 - n2 * n2 - n2;
+            int zbase = 0;
+            for (int m = -(p - 1); m < am2; ++m) zbase += (p - abs(m)) * (p - abs(m));
+            const int zw = p - am2;
+            const cx<R> *z = Zb + zbase + (n2 - am2) * zw;
+            cx<R> acc = {0, 0};
+            for (int jj = 0; jj < zw; ++jj) {
+                const int n = am2 + jj;
+                cfma(acc, z[jj], U[(n * n + (plus2 ? am2 : n + am2)) * ROTC_S + c]);
+            }
+            X[r2 * ROTC_S + c] = acc;
+        }
+        __syncthreads();
+        // stage 3: folded polar rotation back: P (a half) and Q (b half)
+        for (int k0 = 0; k0 < p2; k0 += ROTC_WARPS) {
+            const int k = k0 + (((k0 / ROTC_WARPS) & 1) ? ROTC_WARPS - 1 - warp : warp);
+            if (k >= p2) continue;
+            const int r13 = slot_by_rowlen(p, k);
+            int n1 = (int)sqrtf((float)r13);
+            while (n1 * n1 > r13) --n1;
+            while ((n1 + 1) * (n1 + 1) <= r13) ++n1;
+            const int sl1 = r13 - n1 * n1;
+            const bool plus1 = sl1 <= n1;
+            const int am1 = plus1 ? sl1 : sl1 - n1;
+            const R *bb = Db + rot_off(n1) + (plus1 ? sl1 * (n1 + 1) : (n1 + 1) * (n1 + 1) + (am1 - 1) * n1);
+            const int flen = plus1 ? n1 + 1 : n1, fin = plus1 ? n1 * n1 : n1 * n1 + n1 + 1;
+            cx<R> acc = {0, 0};
+            for (int jj = 0; jj < flen; ++jj) {
+                const R t = bb[jj];
+                const cx<R> xv = X[(fin + jj) * ROTC_S + c];
+                acc.re = fma(t, xv.re, acc.re);
+                acc.im = fma(t, xv.im, acc.im);
+            }
+            U[r13 * ROTC_S + c] = acc;
+        }
+        __syncthreads();
+        // unfold, back phase, store: one (column, coefficient) per thread, coefficients fastest
+        // so that the stores of a warp are contiguous
+        for (int i = threadIdx.x; i < p2 * nct; i += blockDim.x) {
+            const int j = i / p2, r = i - j * p2;
+            int rn = (int)sqrtf((float)r);
+            while (rn * rn > r) --rn;
+            while ((rn + 1) * (rn + 1) <= r) ++rn;
+            const int m = r - rn * rn - rn, mm = abs(m);
+            cx<R> v = U[(rn * rn + mm) * ROTC_S + j];
+            if (mm > 0) {
+                const cx<R> q = U[(rn * rn + rn + mm) * ROTC_S + j];
+                v = m > 0 ? v + q : v - q;
+            }
+            const int pr = j / ncol, cc = j - pr * ncol;
+            const int64_t e = pair_e[beg + b0 + pr];
+            Y[((e - e_first) * ncol + cc) * p2 + r] = v * Pb[r];
+        }
+    }
+}
+
 // D(l,q) = R|R D(parent) + sum of the target's M2L pair results (Eq. 2.21), columns col0..col0+ncol.
 // Threads: rows_pad x ct column groups; a thread owns columns cid * L2L_CPT .. + L2L_CPT - 1.
 constexpr int L2L_CPT = 3;
@@ -2324,7 +2479,7 @@ static void ensure_scratch(fmbem *h, int64_t nr) {
 // or the shape does not fit.
 constexpr int ROT_MAXC = 12;
 struct RotLaunch {
-    bool ok = false;
+    bool ok = false, cols = false;  // cols: the column-parallel kernel (double precision)
     int rows = 0, cg = 1, pc = 0;
     size_t bytes = 0;
 };
@@ -2333,6 +2488,19 @@ static RotLaunch rot_launch(fmbem *h, int ncol, size_t budget) {
     RotLaunch rl;
     if (!h->m2l_rotation || h->R_D64 == nullptr || ncol > 24) return rl;
     const int p = h->p, p2 = h->p2, nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
+    if (sizeof(R) == 8) {  // FP64-bound: one column per lane, loops of equal length in a warp
+        const size_t b = sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)p2 * ROTC_S) +
+                         sizeof(short2) * (size_t)(p * (p + 1) / 2);
+        if (b <= budget) {
+            rl.ok = rl.cols = true;
+            rl.rows = 32;
+            rl.cg = ROTC_WARPS;
+            rl.pc = std::min(M2L_CHUNK, ROTC_N / ncol);
+            rl.bytes = b;
+            CK(cudaFuncSetAttribute(k_m2l_rot_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            return rl;
+        }
+    }
     cudaFuncAttributes fa{};
     CK(cudaFuncGetAttributes(&fa, k_m2l_rot<R, ROT_MAXC>));
     auto bytes = [&](int c) {
@@ -2347,6 +2515,22 @@ static RotLaunch rot_launch(fmbem *h, int ncol, size_t budget) {
     rl.ok = rl.pc >= 1 && rl.bytes <= budget && rl.rows * rl.cg <= fa.maxThreadsPerBlock;
     if (rl.ok) CK(cudaFuncSetAttribute(k_m2l_rot<R, ROT_MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rl.bytes));
     return rl;
+}
+// one launch of the rotation-form kernel chosen by rot_launch over nch chunks
+template <typename R>
+static void launch_rot(const RotLaunch &rl, int64_t nch, cudaStream_t s, int64_t c0, int l, int lmax, int d, int64_t nr,
+                       int p, int64_t nbox, int col0, int nc, const int32_t *cbeg, const int32_t *ccnt,
+                       const int16_t *coff, const int32_t *pair_e, const int32_t *src, const int8_t *tidx, int n_tlen,
+                       const R *RD, const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y, int64_t e_first) {
+    if (nch <= 0) return;
+    if (rl.cols)
+        k_m2l_rot_cols<R><<<(unsigned)nch, 32 * ROTC_WARPS, rl.bytes, s>>>(c0, l, lmax, d, nr, p, nbox, col0, nc, rl.pc,
+                                                                          1, cbeg, ccnt, coff, pair_e, src, tidx, n_tlen,
+                                                                          RD, RP, RZ, C, Y, e_first);
+    else
+        k_m2l_rot<R, ROT_MAXC><<<(unsigned)nch, rl.rows * rl.cg, rl.bytes, s>>>(c0, l, lmax, d, nr, p, nbox, col0, nc,
+                                                                               rl.pc, rl.cg, cbeg, ccnt, coff, pair_e,
+                                                                               src, tidx, n_tlen, RD, RP, RZ, C, Y, e_first);
 }
 
 // M2M (Eq. 2.20) from level l_max up to level 2, on the multipole expansions in h->Cexp
@@ -2372,9 +2556,9 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
                 const int64_t c0 = h->h_rmm_chunk_first[l], nch = h->h_rmm_chunk_first[l + 1] - c0;
                 const int64_t e_first = h->h_rmm_first[l];
                 for (int d = 0; d <= J; ++d) {
-                    k_m2l_rot<R, ROT_MAXC><<<(unsigned)nch, rl.rows * rl.cg, rl.bytes, s>>>(
-                        c0, l, lmax, d, nr, h->p, h->nbox, 0, ncol, rl.pc, rl.cg, h->rmm_chunk_beg, h->rmm_chunk_cnt,
-                        h->rmm_chunk_mm, h->rmm_iota, h->rmm_child, h->rot_zero, 1, RD, RP, RZmm, C, Y, e_first);
+                    launch_rot<R>(rl, nch, s, c0, l, lmax, d, nr, h->p, h->nbox, 0, ncol, h->rmm_chunk_beg,
+                                  h->rmm_chunk_cnt, h->rmm_chunk_mm, h->rmm_iota, h->rmm_child, h->rot_zero, 1, RD, RP,
+                                  RZmm, C, Y, e_first);
                     CKL("k_m2l_rot (M2M)");
                     k_mm_reduce<R><<<(unsigned)P.n, 128, 0, s>>>(P.off, d, nr, p2, h->nbox, 0, ncol, h->box_cbeg,
                                                                 h->box_cend, h->rmm_entry, e_first, Y, C);
@@ -2429,19 +2613,14 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     const int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
     const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr && rows_pad <= max_thr;
     // rotation form of the chunked S|R (when its tables were built)
-    constexpr int RMAXC = ROT_MAXC;
     const int pp = h->p;
     const RotLaunch rl = rot_launch<R>(h, ncol, budget);
-    const int rows_rot = rl.rows, cgr = rl.cg, pcr = rl.pc;
-    auto rot_bytes = [&](int) { return rl.bytes; };
     const bool use_rot = chunked && rl.ok;
     if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
         run_m2l_tc(h, (float *)C, (float *)D, nr, s);
     } else if (chunked) {
         if (tsm) CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-        if (use_rot)
-            CK(cudaFuncSetAttribute(k_m2l_rot<R, RMAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_bytes(cgr)));
         const R *RD = f32 ? (const R *)h->R_D32 : (const R *)h->R_D64;
         const cx<R> *RP = f32 ? (const cx<R> *)h->R_P32 : (const cx<R> *)h->R_P64;
         const cx<R> *RZ = f32 ? (const cx<R> *)h->R_Z32 : (const cx<R> *)h->R_Z64;
@@ -2457,9 +2636,9 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
                     const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
                     if (nch > 0) {
                         if (use_rot)
-                            k_m2l_rot<R, RMAXC><<<(unsigned)nch, rows_rot * cgr, rot_bytes(cgr), s>>>(
-                                c0, l, lmax, d, nr, pp, h->nbox, col0, nc, pcr, cgr, h->chunk_beg, h->chunk_cnt,
-                                h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD, RP, RZ, C, Y, e_first);
+                            launch_rot<R>(rl, nch, s, c0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->chunk_beg,
+                                          h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD,
+                                          RP, RZ, C, Y, e_first);
                         else if (tsm)
                             k_m2l_chunks<R, MAXC, true><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
                                 c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt,
@@ -2478,9 +2657,9 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
                         const int64_t lc0 = h->h_rmm_chunk_first[l], lnch = h->h_rmm_chunk_first[l + 1] - lc0;
                         ll_first = h->h_rmm_first[l];
                         Yll = Y + (h->h_pair_first[l + 1] - e_first) * nc * p2;
-                        k_m2l_rot<R, RMAXC><<<(unsigned)lnch, rows_rot * cgr, rot_bytes(cgr), s>>>(
-                            lc0, l, lmax, d, nr, pp, h->nbox, col0, nc, pcr, cgr, h->rmm_chunk_beg, h->rmm_chunk_cnt,
-                            h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP, RZll, D, Yll, ll_first);
+                        launch_rot<R>(rl, lnch, s, lc0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->rmm_chunk_beg,
+                                      h->rmm_chunk_cnt, h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP,
+                                      RZll, D, Yll, ll_first);
                         CKL("k_m2l_rot (L2L)");
                     }
                     const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
