@@ -136,11 +136,11 @@ def split_ring(R: float, side: float, gap_deg: float, nu: int, nv_side: int,
     for k, uu in enumerate((u[0], u[-1])):
         caps.append([R * math.cos(uu), R * math.sin(uu), 0.0])
     V = np.concatenate([V, np.asarray(caps)])
-    for j in range(m):
+    for j in range(m):  # each cap runs its rim edges opposite to the side surface's
         a, b = j, (j + 1) % m
-        tris.append((base, b, a))
+        tris.append((base, a, b))
         a2, b2 = nu * m + j, nu * m + (j + 1) % m
-        tris.append((base + 1, a2, b2))
+        tris.append((base + 1, b2, a2))
     F = np.asarray(tris, dtype=np.int32)
     V = V + np.asarray(center, dtype=np.float64)
     # orient outward: flip if the signed volume is negative

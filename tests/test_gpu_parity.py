@@ -389,6 +389,53 @@ def test_far_field_functional_and_extinction_eps_gradient():
         assert np.linalg.norm(ga - go) < 1e-3 * np.linalg.norm(go), (ga, go)
 
 
+def test_autotune_picks_a_config_that_meets_the_target():
+    """The autotuner's choice of (p, leaf size) for a 1e-4 target must meet it against the dense
+    operator, and its error estimate must agree with the true error to within the reference's."""
+    from paper_1211_7177_gb300.autotune import autotune
+    V, F, D = fi.icosphere(4)
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    res = autotune(V, F, D, eps, mu, k0, tol=1e-4, p_candidates=(4, 6, 8), leaf_candidates=(32, 64), reps=2)
+    print(res)
+    assert len(res["table"]) == 6 and res["err"] <= 0.5e-4
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=res["p"], leaf_size=res["leaf_size"])
+    x = fi.random_complex((1, o.N, 6), seed=71)
+    err = rel(g.matvec(to_dev(x)).cpu().numpy(), o.matvec(x))
+    assert err <= 1e-4, err
+
+
+def test_uneven_batch_of_independent_problems():
+    """Five independent problems of uneven sizes and shapes (spheroids of aspect 2 and 4, tori of
+    R/r 4 and 2, a split ring) with the permittivities of the uneven-batch workload, 4 plane
+    waves each, run concurrently from a pool of host threads on separate streams: the batch's
+    products and solves must equal the one-at-a-time ones exactly, and each product must meet
+    the oracle bar."""
+    from paper_1211_7177_gb300.batch import Batch
+    meshes = [fi.spheroid(0.5, 1.0, 3), fi.spheroid(0.3, 1.2, 4), fi.torus(1.0, 0.25, 64, 16),
+              fi.split_ring(1.0, 0.2, 30.0, 48, 3), fi.torus(1.0, 0.5, 48, 24)]
+    eps = [2.25, -5 + 0.2j, -12 + 0.5j, 2.25, -5 + 0.2j]
+    k0s = [1.0, 1.5, 0.8, 2.0, 0.3]
+    probs = [dict(V=V, F=F, D=D, eps=[1.0, e], mu=[1.0, 1.0], k0=k) for (V, F, D), e, k in zip(meshes, eps, k0s)]
+    batch = Batch(probs, workers=3)
+    assert len(set(batch.sizes)) == 5
+    dirs, pols = fi.plane_wave_batch(2, seed=12)
+    bs = batch.plane_wave_rhs(dirs, pols)
+    xs = [to_dev(fi.random_complex((4, n, 6), seed=80 + i)) for i, n in enumerate(batch.sizes)]
+    ys = batch.matvec(xs, precision=fm.FP32)
+    for i, pr in enumerate(probs):
+        y1 = batch.handles[i].matvec(xs[i], precision=fm.FP32)
+        assert torch.equal(ys[i], y1), i
+        o = oracle.Oracle(pr["V"], pr["F"], pr["D"], pr["eps"], pr["mu"], pr["k0"])
+        assert rel(ys[i].cpu().numpy(), o.matvec(xs[i].cpu().numpy())) < MATVEC_TOL, i
+    sols = batch.solve(bs, tol=1e-6)
+    for i in range(len(probs)):
+        x, its, rr, st = sols[i]
+        assert st == 0 and rr.max() <= 1e-6, (i, st, rr)
+        x1, _, _, _ = batch.handles[i].solve(bs[i], tol=1e-6)
+        assert torch.equal(x, x1), i
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
