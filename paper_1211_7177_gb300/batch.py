@@ -5,6 +5,10 @@ threads take problems from a shared queue, each thread issuing its problem's ker
 CUDA stream: the products and GMRES solves of small problems, which occupy only a few SMs each,
 overlap on the device.  A handle is only ever used by one thread at a time.  Every step runs
 in the library's CUDA kernels; the threads only launch them (the C ABI releases the GIL).
+
+For repeated products on fixed buffers (an iteration driven from the host), capture() records
+every problem's FP64 or FP32 product into a CUDA graph once and replay() launches the graphs,
+one per problem on the workers' streams, without re-issuing the kernels one by one.
 """
 from __future__ import annotations
 
@@ -112,3 +116,37 @@ class Batch:
 
         self._run(len(self.handles), f)
         return out
+
+    def capture(self, xs, ys, precision=FP64):
+        """Record y_i = A_i x_i for the fixed buffers xs[i], ys[i] into one CUDA graph per problem
+        (FP64 or FP32: the TF32 product checks its tensor-core kernel on the host and cannot be
+        captured).  Each product runs once first, so that its scratch exists before capture."""
+        import torch
+        if precision not in (0, 1):
+            raise ValueError("capture supports FP64 and FP32 products")
+        self.graphs = [None] * len(self.handles)
+        self._graph_bufs = (xs, ys)
+        for i, h in enumerate(self.handles):
+            h.matvec(xs[i], ys[i], precision=precision)
+        torch.cuda.synchronize()
+        for i, h in enumerate(self.handles):  # capture from this thread, one graph per problem
+            st = self.streams[i % self.workers]
+            st.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                h.matvec(xs[i], ys[i], precision=precision)
+            self.graphs[i] = g
+        torch.cuda.synchronize()
+
+    def replay(self):
+        """Launch every captured product (after capture()); results land in the captured ys."""
+        import torch
+        cur = torch.cuda.current_stream()
+        for i, g in enumerate(self.graphs):
+            st = self.streams[i % self.workers]
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):
+                g.replay()
+        for st in self.streams:
+            cur.wait_stream(st)
+

@@ -409,8 +409,8 @@ def test_uneven_batch_of_independent_problems():
     """Five independent problems of uneven sizes and shapes (spheroids of aspect 2 and 4, tori of
     R/r 4 and 2, a split ring) with the permittivities of the uneven-batch workload, 4 plane
     waves each, run concurrently from a pool of host threads on separate streams: the batch's
-    products and solves must equal the one-at-a-time ones exactly, and each product must meet
-    the oracle bar."""
+    products (direct and replayed from CUDA graphs) and solves must equal the one-at-a-time ones
+    exactly, and each product must meet the oracle bar."""
     from paper_1211_7177_gb300.batch import Batch
     meshes = [fi.spheroid(0.5, 1.0, 3), fi.spheroid(0.3, 1.2, 4), fi.torus(1.0, 0.25, 64, 16),
               fi.split_ring(1.0, 0.2, 30.0, 48, 3), fi.torus(1.0, 0.5, 48, 24)]
@@ -428,6 +428,13 @@ def test_uneven_batch_of_independent_problems():
         assert torch.equal(ys[i], y1), i
         o = oracle.Oracle(pr["V"], pr["F"], pr["D"], pr["eps"], pr["mu"], pr["k0"])
         assert rel(ys[i].cpu().numpy(), o.matvec(xs[i].cpu().numpy())) < MATVEC_TOL, i
+    outs = [torch.empty_like(x) for x in xs]
+    batch.capture(xs, outs, precision=fm.FP32)  # CUDA-graph products on fixed buffers
+    for _ in range(2):
+        batch.replay()
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert torch.equal(outs[i], ys[i]), i
     sols = batch.solve(bs, tol=1e-6)
     for i in range(len(probs)):
         x, its, rr, st = sols[i]
