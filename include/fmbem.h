@@ -246,11 +246,15 @@ fmbem_status fmbem_far_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t
 fmbem_status fmbem_far_field_functional(fmbem *h, int64_t n_rhs, const double *rhat, const fmbem_c64 *coef,
                                         void *out_dev, void *stream);
 
-/* Total electric field at points outside every scatterer (Section 4; the representation formula
- * of Appendix A for the background domain), for solutions x of plane-wave excitations:
- *   E(r) = e exp(i k0 d.r) + sum_b w_b { n0 (a.Phi_b) - (n0.a) Phi_b - a (n0.Phi_b) + g Psi_b },
- *   g = exp(i k0 R) / (4 pi R),  a = grad_s g = g (i k0 - 1/R) (s_b - r) / R,  R = |s_b - r|,
- *   n0 = -n_b (the background's normal).
+/* Total electric (and magnetic) field at points outside every scatterer (Section 4; the
+ * representation formula of Appendix A for the background domain), for solutions x of
+ * plane-wave excitations:
+ *   E(r) = e exp(i k d.r) + sum_b w_b { n0 (a.Phi_b) - (n0.a) Phi_b - a (n0.Phi_b) + g Psi_b },
+ *   g = exp(i k R) / (4 pi R),  a = grad_s g = g (i k - 1/R) (s_b - r) / R,  R = |s_b - r|,
+ *   n0 = -n_b (the background's normal), k the background wavenumber;
+ *   H(r) = curl E / (i k0 mu_0) (omega = k0 with c = 1, mu_0 the background's permeability), where
+ *   the curl of the bracket is (K n0) x Phi_b + n0 x (K Phi_b) with K the Hessian of g in s_b,
+ *   and that of g Psi_b is -a x Psi_b; the incident wave contributes i k (d x e) exp(i k d.r).
  * Direct summation over the N nodes in double precision (no FMM: O(n_pts N) per right-hand side),
  * for field maps and stress-tensor surfaces off the boundary; a point on or inside the surface
  * gets no meaningful value.
@@ -259,10 +263,12 @@ fmbem_status fmbem_far_field_functional(fmbem *h, int64_t n_rhs, const double *r
  *   dir, pol  host [n_rhs][3] each: the plane waves (direction, polarisation) that produced x, for
  *             the incident term; both NULL for the scattered field alone.
  *   E_host    host [n_rhs][n_pts][3] complex128, written.
+ *   H_host    host [n_rhs][n_pts][3] complex128, written; NULL to skip the magnetic field.
  * Errors: FMBEM_ERR_INVALID_ARGUMENT (n_rhs outside 1..65535, n_pts < 1, a NULL x, pts or E, or
  * only one of dir and pol), FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
 fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
-                              const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, void *stream);
+                              const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, fmbem_c64 *H_host,
+                              void *stream);
 
 /* sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (host [n_rhs], written): with
  * n x curl E = Psi the inward flux of the time-averaged Poynting vector, Eq. (4.2), gives the

@@ -70,6 +70,7 @@ def _load():
             lib.oracle_gmres.argtypes = [P, P, P, dbl, i32, i32, i32, P, P]
             lib.oracle_far_field.argtypes = [P, P, i64, P, P]
             lib.oracle_near_field.argtypes = [P, P, i64, P, P, P, P]
+            lib.oracle_near_field_h.argtypes = [P, P, i64, P, P, P, P]
             lib.oracle_polygon_integrals.argtypes = [i32, P, P, P]
             lib.oracle_num_threads.restype = i32
             _lib = lib
@@ -238,6 +239,18 @@ class Oracle:
         E = np.empty((len(pts), 3), dtype=np.complex128)
         self._lib.oracle_near_field(self._h, _ptr(x), len(pts), _ptr(pts), _ptr(d), _ptr(e), _ptr(E))
         return E
+
+    def near_field_h(self, x, points, d, e):
+        """Total magnetic field H = curl E / (i k0 mu_0) at exterior points [P,3] (the curl of
+        the representation formula of near_field) for one solution x [N,6] of the plane wave
+        (d, e)."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        e = np.ascontiguousarray(e, dtype=np.complex128)
+        H = np.empty((len(pts), 3), dtype=np.complex128)
+        self._lib.oracle_near_field_h(self._h, _ptr(x), len(pts), _ptr(pts), _ptr(d), _ptr(e), _ptr(H))
+        return H
 
     def cross_sections(self, x, d, e, n_theta=48, n_phi=96):
         """(C_ext, C_sca, C_abs) of one solution x for the incident plane wave (d, e), |e| = 1.

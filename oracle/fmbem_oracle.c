@@ -694,6 +694,59 @@ void oracle_near_field(const oracle_ctx *c, const double *x_, int64_t np_, const
     }
 }
 
+/* Total magnetic field at exterior points, H = curl E / (i omega mu_0) with omega = k0 (c = 1)
+ * and mu_0 the background's relative permeability, from the curl of the representation formula
+ * used by oracle_near_field.  With a = grad_s g = g'(R) rhat (rhat = (s_b - r)/R) and the Hessian
+ * K = d^2 g / ds ds = g''(R) rhat rhat^T + g'(R)/R (I - rhat rhat^T),
+ * g' = g (i k - 1/R), g'' = g ((i k - 1/R)^2 + 1/R^2), the curl over r of the bracket
+ * n0 (a.Phi) - (n0.a) Phi - a (n0.Phi) is (K n0) x Phi + n0 x (K Phi) (curl_r a = 0, d a / d r = -K),
+ * and that of g Psi is -a x Psi.  The incident wave e exp(i k d.r) contributes
+ * (k / (omega mu_0)) d x e exp(i k d.r). */
+void oracle_near_field_h(const oracle_ctx *c, const double *x_, int64_t np_, const double *pts,
+                         const double *dir, const double *pol_, double *H_) {
+    const cplx *x = (const cplx *)x_;
+    const cplx *pol = (const cplx *)pol_;
+    cplx *H = (cplx *)H_;
+    const cplx k = c->k[0], mu0 = c->mu[0];
+    const cplx iwm = I * c->k0 * mu0;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < np_; ++p) {
+        const double *r = pts + 3 * p;
+        const cplx ph = cexp(I * k * dot3(dir, r));
+        cplx curl[3];
+        {
+            const cplx de[3] = {dir[1] * pol[2] - dir[2] * pol[1], dir[2] * pol[0] - dir[0] * pol[2],
+                                dir[0] * pol[1] - dir[1] * pol[0]};
+            for (int q = 0; q < 3; ++q) curl[q] = I * k * de[q] * ph;  /* curl of the incident wave */
+        }
+        for (int64_t b = 0; b < c->N; ++b) {
+            double rv[3]; sub3(c->s + 3 * b, r, rv);
+            const double R = norm3(rv);
+            const double rh[3] = {rv[0] / R, rv[1] / R, rv[2] / R};
+            const double *nb = c->n + 3 * b;
+            const double n0[3] = {-nb[0], -nb[1], -nb[2]};
+            const cplx g = cexp(I * k * R) / (4 * PI * R);
+            const cplx g1 = g * (I * k - 1.0 / R);
+            const cplx g2 = g * ((I * k - 1.0 / R) * (I * k - 1.0 / R) + 1.0 / (R * R));
+            const cplx *Phi = x + 6 * b, *Psi = x + 6 * b + 3;
+            /* K v = g'' rhat (rhat.v) + g'/R (v - rhat (rhat.v)) */
+            const double rn = dot3(rh, n0);
+            const cplx rP = rh[0] * Phi[0] + rh[1] * Phi[1] + rh[2] * Phi[2];
+            cplx Kn[3], KP[3], a[3];
+            for (int q = 0; q < 3; ++q) {
+                Kn[q] = g2 * rh[q] * rn + g1 / R * (n0[q] - rh[q] * rn);
+                KP[q] = g2 * rh[q] * rP + g1 / R * (Phi[q] - rh[q] * rP);
+                a[q] = g1 * rh[q];
+            }
+            const cplx t[3] = {Kn[1] * Phi[2] - Kn[2] * Phi[1] + n0[1] * KP[2] - n0[2] * KP[1] - (a[1] * Psi[2] - a[2] * Psi[1]),
+                               Kn[2] * Phi[0] - Kn[0] * Phi[2] + n0[2] * KP[0] - n0[0] * KP[2] - (a[2] * Psi[0] - a[0] * Psi[2]),
+                               Kn[0] * Phi[1] - Kn[1] * Phi[0] + n0[0] * KP[1] - n0[1] * KP[0] - (a[0] * Psi[1] - a[1] * Psi[0])};
+            for (int q = 0; q < 3; ++q) curl[q] += c->w[b] * t[q];
+        }
+        for (int q = 0; q < 3; ++q) H[3 * p + q] = curl[q] / iwm;
+    }
+}
+
 /* Appendix B integrals over an arbitrary planar polygon (vertices relative to O, counter-
  * clockwise about n, already in the plane): out = {I1, S, V1x, V1y, V1z, V3x, V3y, V3z}. */
 void oracle_polygon_integrals(int nv, const double *pts, const double *nrm, double *out) {

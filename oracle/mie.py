@@ -168,3 +168,36 @@ def cross_sections(k, a, eps_in, nmax=None):
     cext = 2 * np.pi / k ** 2 * np.sum((2 * n + 1) * (an + bn).real)
     csca = 2 * np.pi / k ** 2 * np.sum((2 * n + 1) * (abs(an) ** 2 + abs(bn) ** 2))
     return cext, csca, cext - csca
+
+
+def radiation_pressure(k, a, eps_in, nmax=None):
+    """Radiation-pressure cross section C_pr = C_ext - <cos theta> C_sca of the sphere, with the
+    asymmetry term from the Mie coefficients (Bohren & Huffman Eq. 4.74):
+    <cos theta> C_sca = (4 pi / k^2) sum_n [ n (n+2)/(n+1) Re(a_n a*_{n+1} + b_n b*_{n+1})
+                                             + (2n+1)/(n (n+1)) Re(a_n b*_n) ].
+    The time-averaged force on the sphere in a unit plane wave in vacuum is C_pr / 2 along d."""
+    x = k * a
+    an, bn, _, _ = coefficients(eps_in, x, nmax)
+    n = np.arange(1, len(an) + 1)
+    cext, csca, _ = cross_sections(k, a, eps_in, nmax)
+    t1 = n[:-1] * (n[:-1] + 2) / (n[:-1] + 1) * (an[:-1] * np.conj(an[1:]) + bn[:-1] * np.conj(bn[1:])).real
+    t2 = (2 * n + 1) / (n * (n + 1)) * (an * np.conj(bn)).real
+    gcsca = 4 * np.pi / k ** 2 * (np.sum(t1) + np.sum(t2))
+    return cext - gcsca
+
+
+def asymmetry_by_quadrature(k, a, eps_in, n_theta=400, nmax=None):
+    """<cos theta> C_sca by quadrature of the amplitude functions S1, S2 (Bohren & Huffman
+    Eqs. 4.74 in integral form): (pi / k^2) int (|S1|^2 + |S2|^2) cos theta sin theta dtheta, an
+    evaluation independent of the closed form in radiation_pressure."""
+    x = k * a
+    an, bn, _, _ = coefficients(eps_in, x, nmax)
+    nm = len(an)
+    n = np.arange(1, nm + 1)
+    mu, w = np.polynomial.legendre.leggauss(n_theta)
+    pi_n, tau_n = _angular(nm, mu)                     # [nmax, n_theta]
+    f = ((2 * n + 1) / (n * (n + 1)))[:, None]
+    S1 = np.sum(f * (an[:, None] * pi_n + bn[:, None] * tau_n), axis=0)
+    S2 = np.sum(f * (an[:, None] * tau_n + bn[:, None] * pi_n), axis=0)
+    return np.pi / k ** 2 * float(np.sum(w * (abs(S1) ** 2 + abs(S2) ** 2) * mu))
+

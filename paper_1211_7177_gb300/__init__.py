@@ -79,7 +79,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_matvec_noalloc": (i32, [P, P, P, i64, i32, P]),
         "fmbem_far_field": (i32, [P, P, i64, i64, P, P, P]),
         "fmbem_absorption": (i32, [P, P, i64, P, P]),
-        "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
+        "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P, P]),
         "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
@@ -239,9 +239,10 @@ def fmbem_far_field(h, x, rhat, stream=None):
     return F
 
 
-def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None):
+def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None, magnetic=False):
     """Total field E [n_rhs, n_pts, 3] complex128 (host) at exterior points of solutions x of the
-    plane waves (dirs[r], pols[r]); scattered field alone when dirs and pols are None."""
+    plane waves (dirs[r], pols[r]); scattered field alone when dirs and pols are None.  With
+    magnetic=True returns (E, H), H = curl E / (i k0 mu_0)."""
     N = fmbem_num_nodes(h)
     x = _dev(x, N, "x")
     n = x.shape[0]
@@ -253,10 +254,12 @@ def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None):
         d = np.ascontiguousarray(np.broadcast_to(np.asarray(dirs, dtype=np.float64), (n, 3)))
         p = np.ascontiguousarray(np.broadcast_to(np.asarray(pols, dtype=np.complex128), (n, 3)))
     E = np.empty((n, len(pts), 3), dtype=np.complex128)
+    H = np.empty((n, len(pts), 3), dtype=np.complex128) if magnetic else None
     _check(h, load_library().fmbem_near_field(h, ctypes.c_void_p(x.data_ptr()), n, len(pts), _ptr(pts),
                                               _ptr(d) if d is not None else None,
-                                              _ptr(p) if p is not None else None, _ptr(E), _stream(stream)))
-    return E
+                                              _ptr(p) if p is not None else None, _ptr(E),
+                                              _ptr(H) if H is not None else None, _stream(stream)))
+    return (E, H) if magnetic else E
 
 
 def fmbem_far_field_functional(h, rhat, coef, stream=None):
@@ -340,6 +343,7 @@ class FMBEM:
         self.N = fmbem_num_nodes(self.h)
         # background wavenumber k0 sqrt(eps_0 mu_0) (real for the cross sections)
         self.kb = complex(k0 * np.sqrt(complex(eps[0]) * complex(mu[0])))
+        self.eps0, self.mu0 = complex(eps[0]), complex(mu[0])
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -376,8 +380,59 @@ class FMBEM:
     def far_field(self, x, rhat, stream=None):
         return fmbem_far_field(self.h, x, rhat, stream)
 
-    def near_field(self, x, points, dirs=None, pols=None, stream=None):
-        return fmbem_near_field(self.h, x, points, dirs, pols, stream)
+    def near_field(self, x, points, dirs=None, pols=None, stream=None, magnetic=False):
+        return fmbem_near_field(self.h, x, points, dirs, pols, stream, magnetic)
+
+    def _vacuum_background(self):
+        if self.eps0 != 1 or self.mu0 != 1:
+            raise ValueError("the optical force here assumes a vacuum background (eps_0 = mu_0 = 1)")
+
+    def force_farfield(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
+        """Time-averaged force [n_rhs, 3] on all scatterers together in the unit plane waves
+        (dirs[r], pols[r]) (vacuum background, eps_0 = mu_0 = c = 1): momentum balance in the far
+        zone, F = (C_ext d - int |F(u)|^2 u dOmega) / 2, with the far fields on the device."""
+        self._vacuum_background()
+        k0 = self.kb.real
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
+        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
+        ph = 2 * np.pi * np.arange(n_phi) / n_phi
+        MU, PH = np.meshgrid(mu, ph, indexing="ij")
+        ST = np.sqrt(1 - MU ** 2)
+        rq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
+        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel()
+        F = fmbem_far_field(self.h, x, np.concatenate([dirs, rq]), stream)
+        nr = F.shape[0]
+        out = np.zeros((nr, 3))
+        for r in range(nr):
+            cext = 4 * np.pi / k0 * np.imag(np.vdot(pols[r], F[r, r]))
+            f2 = np.sum(np.abs(F[r, len(dirs):]) ** 2, axis=1)
+            out[r] = 0.5 * (cext * dirs[r] - np.sum((wq * f2)[:, None] * rq, axis=0))
+        return out
+
+    def force_stress(self, x, dirs, pols, center, radius, n_theta=32, n_phi=64, stream=None):
+        """Time-averaged force [n_rhs, 3] on the scatterers inside the sphere (center, radius) in
+        the unit plane waves (dirs[r], pols[r]) (vacuum background): the Maxwell stress tensor
+        T = Re[E E* + H H* - (|E|^2 + |H|^2) I / 2] / 2 integrated over the sphere (Gauss-Legendre
+        in cos theta x trapezoid in phi), E and H evaluated on the device."""
+        self._vacuum_background()
+        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
+        ph = 2 * np.pi * np.arange(n_phi) / n_phi
+        MU, PH = np.meshgrid(mu, ph, indexing="ij")
+        ST = np.sqrt(1 - MU ** 2)
+        nq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
+        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel() * radius ** 2
+        pts = np.asarray(center, dtype=np.float64)[None, :] + radius * nq
+        E, H = fmbem_near_field(self.h, x, pts, dirs, pols, stream, magnetic=True)
+        out = np.zeros((E.shape[0], 3))
+        for r in range(E.shape[0]):
+            e, hm = E[r], H[r]
+            en = np.sum(np.conj(e) * nq, axis=1)
+            hn = np.sum(np.conj(hm) * nq, axis=1)
+            u = np.sum(np.abs(e) ** 2 + np.abs(hm) ** 2, axis=1)
+            tn = 0.5 * np.real(e * en[:, None] + hm * hn[:, None] - 0.5 * u[:, None] * nq)
+            out[r] = np.sum(wq[:, None] * tn, axis=0)
+        return out
 
     def far_field_functional(self, rhat, coef, stream=None):
         return fmbem_far_field_functional(self.h, rhat, coef, stream)

@@ -94,25 +94,34 @@ __global__ void __launch_bounds__(OB_TB) k_absorption(int64_t N, const double *w
     if (threadIdx.x == 0) out[r] = red[0];
 }
 
-// Total field at exterior points, direct summation over the nodes (see fmbem_near_field): one
+// Total fields at exterior points, direct summation over the nodes (see fmbem_near_field): one
 // thread per point, a block per (tile of OB_NT points, right-hand side), the nodes staged in
-// shared memory OB_NS at a time.  inc = 0: scattered field only.
+// shared memory OB_NS at a time.  With the magnetic field, curl E is summed beside E (the curl
+// of the bracket is (K n0) x Phi + n0 x (K Phi) with K the Hessian of g in the source point, the
+// curl of g Psi is -grad_s g x Psi) and H = curl E / (i k0 mu_0).  No incident plane wave when
+// dir is null.
 constexpr int OB_NT = 128, OB_NS = 64;
+template <bool WITH_H>
 __global__ void __launch_bounds__(OB_NT) k_near_field(int64_t N, const double *pos, const double *nrm, const double *w,
                                                     const c64 *x, int64_t n_pts, const double *pts, c64 k0,
-                                                    const double *dir, const c64 *pol, c64 *E) {
+                                                    c64 iwmu, const double *dir, const c64 *pol, c64 *E, c64 *H) {
     __shared__ double sp[OB_NS][3], sn[OB_NS][3], sw[OB_NS];
     __shared__ c64 sx[OB_NS][6];
     const int64_t pt = blockIdx.x * (int64_t)OB_NT + threadIdx.x, r = blockIdx.y;
     const bool valid = pt < n_pts;
     const double t[3] = {valid ? pts[3 * pt] : 0.0, valid ? pts[3 * pt + 1] : 0.0, valid ? pts[3 * pt + 2] : 0.0};
-    c64 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    if (dir != nullptr && pol != nullptr) {  // incident plane wave e exp(i k0 d.r)
-        const double *d = dir + 3 * r;
-        const c64 ph = cexpd(c64{-k0.im, k0.re} * (d[0] * t[0] + d[1] * t[1] + d[2] * t[2]));
-        for (int q = 0; q < 3; ++q) acc[q] = pol[3 * r + q] * ph;
-    }
     const c64 ik = {-k0.im, k0.re};
+    c64 acc[3] = {{0, 0}, {0, 0}, {0, 0}}, cur[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (dir != nullptr && pol != nullptr) {  // incident plane wave e exp(i k0 d.r), curl i k0 d x e exp(..)
+        const double *d = dir + 3 * r;
+        const c64 *e = pol + 3 * r;
+        const c64 ph = cexpd(ik * (d[0] * t[0] + d[1] * t[1] + d[2] * t[2]));
+        for (int q = 0; q < 3; ++q) acc[q] = e[q] * ph;
+        if (WITH_H) {
+            const c64 de[3] = {d[1] * e[2] - d[2] * e[1], d[2] * e[0] - d[0] * e[2], d[0] * e[1] - d[1] * e[0]};
+            for (int q = 0; q < 3; ++q) cur[q] = ik * de[q] * ph;
+        }
+    }
     for (int64_t b0 = 0; b0 < N; b0 += OB_NS) {
         const int nb = (int)min((int64_t)OB_NS, N - b0);
         __syncthreads();
@@ -128,7 +137,8 @@ __global__ void __launch_bounds__(OB_NT) k_near_field(int64_t N, const double *p
             const double rv[3] = {sp[e][0] - t[0], sp[e][1] - t[1], sp[e][2] - t[2]};
             const double R = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
             const c64 g = cexpd(ik * R) * (1.0 / (4.0 * FMBEM_PI * R));
-            const c64 c = g * (ik - c64{1.0 / R, 0}) * (1.0 / R);  // grad_s g = c (s - r)
+            const c64 g1 = g * (ik - c64{1.0 / R, 0});  // dg/dR
+            const c64 c = g1 * (1.0 / R);                // grad_s g = c (s - r)
             const double *n0 = sn[e];
             const c64 *Phi = sx[e], *Psi = sx[e] + 3;
             const c64 rP = rv[0] * Phi[0] + rv[1] * Phi[1] + rv[2] * Phi[2];
@@ -139,23 +149,45 @@ __global__ void __launch_bounds__(OB_NT) k_near_field(int64_t N, const double *p
                 const c64 br = c * (n0[q] * rP - nr * Phi[q] - rv[q] * nP);
                 acc[q] += sw[e] * (br + g * Psi[q]);
             }
+            if (WITH_H) {
+                // K v = g'' rh (rh.v) + g'/R (v - rh (rh.v)), rh = rv / R
+                const double iR = 1.0 / R, rh[3] = {rv[0] * iR, rv[1] * iR, rv[2] * iR};
+                const c64 q1 = ik - c64{iR, 0};
+                const c64 g2 = g * (q1 * q1 + c64{iR * iR, 0});
+                const double rn = rh[0] * n0[0] + rh[1] * n0[1] + rh[2] * n0[2];
+                const c64 rhP = rP * iR;
+                c64 Kn[3], KP[3], av[3];
+                for (int q = 0; q < 3; ++q) {
+                    Kn[q] = g2 * (rh[q] * rn) + c * (n0[q] - rh[q] * rn);
+                    KP[q] = g2 * rhP * rh[q] + c * (Phi[q] - rhP * rh[q]);
+                    av[q] = g1 * rh[q];
+                }
+                cur[0] += sw[e] * (Kn[1] * Phi[2] - Kn[2] * Phi[1] + n0[1] * KP[2] - n0[2] * KP[1] - (av[1] * Psi[2] - av[2] * Psi[1]));
+                cur[1] += sw[e] * (Kn[2] * Phi[0] - Kn[0] * Phi[2] + n0[2] * KP[0] - n0[0] * KP[2] - (av[2] * Psi[0] - av[0] * Psi[2]));
+                cur[2] += sw[e] * (Kn[0] * Phi[1] - Kn[1] * Phi[0] + n0[0] * KP[1] - n0[1] * KP[0] - (av[0] * Psi[1] - av[1] * Psi[0]));
+            }
         }
     }
-    if (valid)
+    if (valid) {
         for (int q = 0; q < 3; ++q) E[(r * n_pts + pt) * 3 + q] = acc[q];
+        if (WITH_H)
+            for (int q = 0; q < 3; ++q) H[(r * n_pts + pt) * 3 + q] = cdiv(cur[q], iwmu);
+    }
 }
 
 }  // namespace
 
 void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host, const double *dir_host,
-                    const c64 *pol_host, c64 *E_host, cudaStream_t s) {
+                    const c64 *pol_host, c64 *E_host, c64 *H_host, cudaStream_t s) {
     double *dp = (double *)dev_alloc(h, sizeof(double) * 3 * n_pts);
     c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr);
+    c64 *dH = H_host ? (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr) : nullptr;
     double *dd = nullptr;
     c64 *dpol = nullptr;
     auto cleanup = [&] {
         dev_free(h, dp);
         dev_free(h, dE);
+        if (dH) dev_free(h, dH);
         if (dd) dev_free(h, dd);
         if (dpol) dev_free(h, dpol);
     };
@@ -167,10 +199,17 @@ void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const dou
             CK(cudaMemcpyAsync(dd, dir_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(dpol, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
         }
-        k_near_field<<<dim3((unsigned)((n_pts + OB_NT - 1) / OB_NT), (unsigned)nr), OB_NT, 0, s>>>(
-            h->N, h->upos, h->unrm, h->uw, x, n_pts, dp, h->k[0], dd, dpol, dE);
+        const dim3 grid((unsigned)((n_pts + OB_NT - 1) / OB_NT), (unsigned)nr);
+        const c64 iwmu = c64{0, h->k0} * h->mu[0];  // i omega mu_0 with omega = k0 (c = 1)
+        if (dH)
+            k_near_field<true><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, x, n_pts, dp, h->k[0], iwmu, dd, dpol,
+                                                      dE, dH);
+        else
+            k_near_field<false><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, x, n_pts, dp, h->k[0], iwmu, dd,
+                                                       dpol, dE, nullptr);
         CKL("k_near_field");
         CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
+        if (dH) CK(cudaMemcpyAsync(H_host, dH, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     } catch (...) {
         cleanup();
