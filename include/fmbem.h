@@ -270,6 +270,19 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
                               const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, fmbem_c64 *H_host,
                               void *stream);
 
+/* The exterior fields as linear functionals of the solution, for adjoint gradients of
+ * quantities built from them (the optical force of a Maxwell-stress surface): out[f] holds the
+ * coefficients of x -> sum_p ( cE[f][p] . E_sca(r_p) + cH[f][p] . H_sca(r_p) ) with E_sca, H_sca
+ * the scattered parts of fmbem_near_field's fields (no conjugation), so that the functional is
+ * sum_b out[f][b] . x_b.
+ *   pts      host [n_pts][3] points.
+ *   cE, cH   host [n_fun][n_pts][3] complex128; cH may be NULL (no magnetic part).
+ *   out_dev  device [n_fun][N][6] complex128 (user order), written.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (n_fun outside 1..65535, n_pts < 1, NULL pts, cE or out),
+ * FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
+fmbem_status fmbem_near_field_functional(fmbem *h, int64_t n_fun, int64_t n_pts, const double *pts,
+                                         const fmbem_c64 *cE, const fmbem_c64 *cH, void *out_dev, void *stream);
+
 /* sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (host [n_rhs], written): with
  * n x curl E = Psi the inward flux of the time-averaged Poynting vector, Eq. (4.2), gives the
  * absorption cross section C_abs = -(1/k0) times this sum. */

@@ -81,6 +81,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_absorption": (i32, [P, P, i64, P, P]),
         "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P, P]),
         "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
+        "fmbem_near_field_functional": (i32, [P, i64, i64, P, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
     }
@@ -276,6 +277,26 @@ def fmbem_far_field_functional(h, rhat, coef, stream=None):
     return out
 
 
+def fmbem_near_field_functional(h, points, cE, cH=None, stream=None):
+    """Coefficients [n_fun, N, 6] complex128 (CUDA) of x -> sum_p cE[f][p].E_sca(r_p) +
+    cH[f][p].H_sca(r_p) (cE, cH: [n_fun, n_pts, 3])."""
+    import torch
+    N = fmbem_num_nodes(h)
+    pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    cE = np.ascontiguousarray(cE, dtype=np.complex128)
+    if cE.ndim != 3 or cE.shape[1:] != (len(pts), 3):
+        raise ValueError("cE must be [n_fun, n_pts, 3]")
+    if cH is not None:
+        cH = np.ascontiguousarray(cH, dtype=np.complex128)
+        if cH.shape != cE.shape:
+            raise ValueError("cH must have the shape of cE")
+    out = torch.empty((cE.shape[0], N, 6), dtype=torch.complex128, device="cuda")
+    _check(h, load_library().fmbem_near_field_functional(h, cE.shape[0], len(pts), _ptr(pts), _ptr(cE),
+                                                         _ptr(cH) if cH is not None else None,
+                                                         ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
 def fmbem_absorption(h, x, stream=None):
     """sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (C_abs = -this / k0)."""
     N = fmbem_num_nodes(h)
@@ -436,6 +457,9 @@ class FMBEM:
 
     def far_field_functional(self, rhat, coef, stream=None):
         return fmbem_far_field_functional(self.h, rhat, coef, stream)
+
+    def near_field_functional(self, points, cE, cH=None, stream=None):
+        return fmbem_near_field_functional(self.h, points, cE, cH, stream)
 
     def cross_sections(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
         """(C_ext, C_sca, C_abs) per right-hand side for the plane waves (dirs[r], pols[r]) that

@@ -311,6 +311,19 @@ fmbem_status fmbem_far_field_functional(fmbem *h, int64_t n_rhs, const double *r
     });
 }
 
+fmbem_status fmbem_near_field_functional(fmbem *h, int64_t n_fun, int64_t n_pts, const double *pts,
+                                         const fmbem_c64 *cE, const fmbem_c64 *cH, void *out_dev, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_fun < 1 || n_fun > 65535 || n_pts < 1 || !pts || !cE || !out_dev) {
+        h->err = "invalid argument (n_fun in 1..65535, n_pts >= 1, non-NULL pts, cE and out)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_near_field_functional(h, n_fun, n_pts, pts, (const c64 *)cE, (const c64 *)cH, (c64 *)out_dev,
+                                  (cudaStream_t)stream);
+    });
+}
+
 fmbem_status fmbem_absorption(fmbem *h, const void *x_dev, int64_t n_rhs, double *out_host, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (n_rhs < 1 || !x_dev || !out_host) {

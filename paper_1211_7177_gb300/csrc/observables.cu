@@ -175,7 +175,114 @@ __global__ void __launch_bounds__(OB_NT) k_near_field(int64_t N, const double *p
     }
 }
 
+// Transposed near-field map (for adjoint gradients of quantities built from exterior fields):
+// out[f][b] = sum_p ( cE[f][p] . dE(r_p)/dx_b + cH[f][p] . dH(r_p)/dx_b ), with E, H as in
+// k_near_field (no incident part: it does not depend on x).  For c = cE[f][p]:
+//   c . dE/dPhi_b = w_b [ (c.n0) a - (n0.a) c - (c.a) n0 ],      c . dE/dPsi_b = w_b g c;
+// with c' = cH[f][p] / (i k0 mu_0) and K the Hessian of g in s_b (symmetric):
+//   c' . dH/dPhi_b = w_b [ c' x (K n0) + K (c' x n0) ],          c' . dH/dPsi_b = -w_b c' x a.
+// One thread per (node, functional); the points staged in shared memory OB_NS at a time.
+template <bool WITH_H>
+__global__ void __launch_bounds__(OB_NT) k_near_field_functional(int64_t N, const double *pos, const double *nrm,
+                                                               const double *w, int64_t n_pts, const double *pts,
+                                                               const c64 *cE, const c64 *cH, c64 k0, c64 iwmu,
+                                                               c64 *out) {
+    __shared__ double spt[OB_NS][3];
+    __shared__ c64 sce[OB_NS][3], sch[OB_NS][3];
+    const int64_t b = blockIdx.x * (int64_t)OB_NT + threadIdx.x, f = blockIdx.y;
+    const bool valid = b < N;
+    const double s[3] = {valid ? pos[3 * b] : 0.0, valid ? pos[3 * b + 1] : 0.0, valid ? pos[3 * b + 2] : 0.0};
+    const double n0[3] = {valid ? -nrm[3 * b] : 0.0, valid ? -nrm[3 * b + 1] : 0.0, valid ? -nrm[3 * b + 2] : 0.0};
+    const c64 ik = {-k0.im, k0.re};
+    c64 oP[3] = {{0, 0}, {0, 0}, {0, 0}}, oQ[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t p0 = 0; p0 < n_pts; p0 += OB_NS) {
+        const int np = (int)min((int64_t)OB_NS, n_pts - p0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            for (int q = 0; q < 3; ++q) {
+                spt[e][q] = pts[3 * (p0 + e) + q];
+                sce[e][q] = cE[(f * n_pts + p0 + e) * 3 + q];
+                if (WITH_H) sch[e][q] = cdiv(cH[(f * n_pts + p0 + e) * 3 + q], iwmu);
+            }
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int e = 0; e < np; ++e) {
+            const double rv[3] = {s[0] - spt[e][0], s[1] - spt[e][1], s[2] - spt[e][2]};
+            const double R = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]), iR = 1.0 / R;
+            const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
+            const c64 q1 = ik - c64{iR, 0};
+            const c64 g1 = g * q1, c = g1 * iR;
+            const double rh[3] = {rv[0] * iR, rv[1] * iR, rv[2] * iR};
+            const c64 a[3] = {g1 * rh[0], g1 * rh[1], g1 * rh[2]};
+            const c64 *ce = sce[e];
+            const c64 cn = ce[0] * n0[0] + ce[1] * n0[1] + ce[2] * n0[2];
+            const c64 na = a[0] * n0[0] + a[1] * n0[1] + a[2] * n0[2];
+            const c64 ca = ce[0] * a[0] + ce[1] * a[1] + ce[2] * a[2];
+            for (int q = 0; q < 3; ++q) {
+                oP[q] += cn * a[q] - na * ce[q] - ca * n0[q];
+                oQ[q] += g * ce[q];
+            }
+            if (WITH_H) {
+                const c64 *ch = sch[e];
+                const c64 g2 = g * (q1 * q1 + c64{iR * iR, 0});
+                const double rn = rh[0] * n0[0] + rh[1] * n0[1] + rh[2] * n0[2];
+                c64 Kn[3];
+                for (int q = 0; q < 3; ++q) Kn[q] = g2 * (rh[q] * rn) + c * (n0[q] - rh[q] * rn);
+                const c64 cxn[3] = {ch[1] * n0[2] - ch[2] * n0[1], ch[2] * n0[0] - ch[0] * n0[2], ch[0] * n0[1] - ch[1] * n0[0]};
+                const c64 rc = rh[0] * cxn[0] + rh[1] * cxn[1] + rh[2] * cxn[2];
+                const c64 cxK[3] = {ch[1] * Kn[2] - ch[2] * Kn[1], ch[2] * Kn[0] - ch[0] * Kn[2], ch[0] * Kn[1] - ch[1] * Kn[0]};
+                const c64 cxa[3] = {ch[1] * a[2] - ch[2] * a[1], ch[2] * a[0] - ch[0] * a[2], ch[0] * a[1] - ch[1] * a[0]};
+                for (int q = 0; q < 3; ++q) {
+                    // K (c' x n0) = g'' rh (rh.(c' x n0)) + g'/R ((c' x n0) - rh (rh.(c' x n0)))
+                    const c64 Kc = g2 * rc * rh[q] + c * (cxn[q] - rc * rh[q]);
+                    oP[q] += cxK[q] + Kc;
+                    oQ[q] += -cxa[q];
+                }
+            }
+        }
+    }
+    if (valid) {
+        c64 *o = out + (f * N + b) * 6;
+        for (int q = 0; q < 3; ++q) {
+            o[q] = oP[q] * w[b];
+            o[3 + q] = oQ[q] * w[b];
+        }
+    }
+}
+
 }  // namespace
+
+void run_near_field_functional(fmbem *h, int64_t nf, int64_t n_pts, const double *pts_host, const c64 *cE_host,
+                               const c64 *cH_host, c64 *out, cudaStream_t s) {
+    double *dp = (double *)dev_alloc(h, sizeof(double) * 3 * n_pts);
+    c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nf);
+    c64 *dH = cH_host ? (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nf) : nullptr;
+    auto cleanup = [&] {
+        dev_free(h, dp);
+        dev_free(h, dE);
+        if (dH) dev_free(h, dH);
+    };
+    try {
+        CK(cudaMemcpyAsync(dp, pts_host, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dE, cE_host, sizeof(c64) * 3 * n_pts * nf, cudaMemcpyHostToDevice, s));
+        if (dH) CK(cudaMemcpyAsync(dH, cH_host, sizeof(c64) * 3 * n_pts * nf, cudaMemcpyHostToDevice, s));
+        const dim3 grid((unsigned)((h->N + OB_NT - 1) / OB_NT), (unsigned)nf);
+        const c64 iwmu = c64{0, h->k0} * h->mu[0];
+        if (dH)
+            k_near_field_functional<true><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, n_pts, dp, dE, dH, h->k[0],
+                                                                 iwmu, out);
+        else
+            k_near_field_functional<false><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, n_pts, dp, dE, nullptr,
+                                                                  h->k[0], iwmu, out);
+        CKL("k_near_field_functional");
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
 
 void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host, const double *dir_host,
                     const c64 *pol_host, c64 *E_host, c64 *H_host, cudaStream_t s) {

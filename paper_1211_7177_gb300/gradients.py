@@ -1,4 +1,5 @@
-"""Adjoint gradients of the extinction cross section with respect to the permittivities.
+"""Adjoint gradients of the extinction cross section and of the optical force with respect to
+the permittivities.
 
 The extinction of a plane wave (d, e) is the imaginary part of a linear functional of the
 solution, C_ext = Im f(x) with f(x) = (4 pi / k0) conj(e) . F(d) (optical theorem, F the far-field
@@ -64,3 +65,65 @@ def extinction_eps_gradient(V, F, D, eps, mu, k0, dirs, pols, j, tol=1e-10, h=No
     dAx = (gp.matvec(x) - gm.matvec(x)) / (2 * step)
     df = -torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()
     return cext, df.imag, df.real
+
+
+def _sphere_points(center, radius, n_theta, n_phi):
+    mu, wmu = np.polynomial.legendre.leggauss(n_theta)
+    ph = 2 * np.pi * np.arange(n_phi) / n_phi
+    MU, PH = np.meshgrid(mu, ph, indexing="ij")
+    ST = np.sqrt(1 - MU ** 2)
+    nq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
+    wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel() * radius ** 2
+    return np.asarray(center, dtype=np.float64)[None, :] + radius * nq, nq, wq
+
+
+def force_eps_gradient(V, F, D, eps, mu, k0, d, e, j, center, radius, n_theta=24, n_phi=48, tol=1e-10, h=None,
+                       **options):
+    """(F [3], dF/dRe(eps_j) [3], dF/dIm(eps_j) [3]): the time-averaged Maxwell-stress force on the
+    particles inside the sphere (center, radius) in the unit plane wave (d, e) (vacuum
+    background), and its derivatives, by one forward solve, three adjoint solves (one per force
+    component) and the operator derivative of extinction_eps_gradient.
+
+    The force is a real quadratic form of the solution, F_i = sum_p w_p (T(E, H) n)_i, so
+    dF_i = 2 Re(L_i^T dx) with L_i the holomorphic (Wirtinger) derivative: for the point p,
+    dF_i/dE_j = w_p / 4 [delta_ij (conj(E).n) + conj(E_i) n_j - n_i conj(E_j)] (and likewise for
+    H), mapped to the unknowns by fmbem_near_field_functional.  With A^T lambda_i = L_i and
+    s_i = lambda_i^T (dA/deps_j) x: dF_i/dRe(eps_j) = -2 Re(s_i), dF_i/dIm(eps_j) = 2 Im(s_i)."""
+    import torch
+    eps = [complex(v) for v in eps]
+    if not 1 <= j < len(eps):
+        raise ValueError("j must index a scatterer (1..J)")
+    g = FMBEM(V, F, D, eps, mu, k0, **options)
+    g._vacuum_background()
+    d = np.asarray(d, dtype=np.float64).reshape(1, 3)
+    e = np.asarray(e, dtype=np.complex128).reshape(1, 3)
+    x, _, _, st = g.solve(g.plane_wave_rhs(d, e), tol=tol)
+    if st != 0:
+        raise FMBEMError(st, "forward solve did not converge")
+    pts, nq, wq = _sphere_points(center, radius, n_theta, n_phi)
+    E, H = g.near_field(x, pts, d, e, magnetic=True)
+    E, H = E[0], H[0]
+    en, hn = np.sum(np.conj(E) * nq, 1), np.sum(np.conj(H) * nq, 1)
+    u = np.sum(np.abs(E) ** 2 + np.abs(H) ** 2, 1)
+    force = np.sum(wq[:, None] * 0.5 * np.real(E * en[:, None] + H * hn[:, None] - 0.5 * u[:, None] * nq), 0)
+    eye = np.eye(3)
+
+    def wirtinger(Fv, fn):  # [3 (component i), P, 3 (field index j)]
+        c = (eye[:, None, :] * fn[None, :, None] + np.conj(Fv).T[:, :, None] * nq[None, :, :]
+             - nq.T[:, :, None] * np.conj(Fv)[None, :, :])
+        return 0.25 * wq[None, :, None] * c
+
+    L = g.near_field_functional(pts, wirtinger(E, en), wirtinger(H, hn))
+    lam, _, _, st = g.adjoint_solve(L, tol=tol)
+    if st != 0:
+        raise FMBEMError(st, "adjoint solve did not converge")
+    step = h if h is not None else 1e-5 * max(1.0, abs(eps[j]))
+    ep, em = list(eps), list(eps)
+    ep[j] += step
+    em[j] -= step
+    gp = FMBEM(V, F, D, ep, mu, k0, **options)
+    gm = FMBEM(V, F, D, em, mu, k0, **options)
+    dAx = (gp.matvec(x) - gm.matvec(x)) / (2 * step)
+    sv = torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()
+    return force, -2 * sv.real, 2 * sv.imag
+

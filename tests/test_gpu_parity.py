@@ -481,6 +481,40 @@ def test_optical_forces_match_oracle_and_mie(sphere_s4):
     assert np.linalg.norm(FA + FB - Ft) < 0.1 * np.linalg.norm(Ft)
 
 
+def test_force_eps_gradient_matches_finite_differences():
+    """Adjoint gradient of the Maxwell-stress force (three adjoint solves) with respect to Re and
+    Im of a permittivity against central differences (h = 1e-6) of the force from full GPU
+    solves: on one sphere, and on the smaller of two spheres with respect to the other's.  The
+    permittivities are lossy (Im > 0): k = k0 sqrt(eps mu) takes the root with Im k >= 0, which
+    jumps across the positive real eps axis, so a central difference in Im(eps) there would
+    straddle the branch cut."""
+    from paper_1211_7177_gb300 import gradients as gr
+    d = np.array([0.6, 0.0, 0.8])
+    e = np.array([0.8, 0.0, -0.6], dtype=np.complex128)
+    cases = [(fi.icosphere(3), [1.0, -4.0 + 0.5j], 1, np.zeros(3), 2.0),
+             (fi.merge_meshes(fi.icosphere(2, 0.5, (-1.0, 0, 0), domain=1), fi.icosphere(2, 0.3, (0.8, 0, 0), domain=2)),
+              [1.0, 2.25 + 0.1j, -4 + 0.3j], 1, np.array([0.8, 0, 0]), 0.45)]
+    for (V, F, D), eps, j, ctr, rad in cases:
+        mu = [1.0] * len(eps)
+        Fo, dre, dim_ = gr.force_eps_gradient(V, F, D, eps, mu, 1.5, d, e, j, ctr, rad, tol=1e-12)
+        h = 1e-6
+
+        def force(ej):
+            ee = list(eps)
+            ee[j] = ej
+            g = fm.FMBEM(V, F, D, ee, mu, 1.5)
+            x, _, _, st = g.solve(g.plane_wave_rhs(d[None], e[None]), tol=1e-12)
+            assert st == 0
+            return g.force_stress(x, d[None], e[None], ctr, rad, n_theta=24, n_phi=48)[0]
+
+        fd_re = (force(eps[j] + h) - force(eps[j] - h)) / (2 * h)
+        fd_im = (force(eps[j] + 1j * h) - force(eps[j] - 1j * h)) / (2 * h)
+        print("F", Fo, "adjoint", dre, dim_, "FD", fd_re, fd_im)
+        scale = np.linalg.norm(np.concatenate([fd_re, fd_im]))
+        assert np.linalg.norm(dre - fd_re) < 1e-5 * scale
+        assert np.linalg.norm(dim_ - fd_im) < 1e-5 * scale
+
+
 def test_two_scatterers_and_permeability():
     m1 = fi.icosphere(3, 0.6, (-0.8, 0, 0), domain=1)
     m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.05), domain=2)
