@@ -72,6 +72,10 @@ def _load():
             lib.oracle_near_field.argtypes = [P, P, i64, P, P, P, P]
             lib.oracle_near_field_h.argtypes = [P, P, i64, P, P, P, P]
             lib.oracle_polygon_integrals.argtypes = [i32, P, P, P]
+            lib.oracle_ibc_matvec.argtypes = [P, i64, P, P]
+            lib.oracle_ibc_precond_blocks.argtypes = [P, P]
+            lib.oracle_ibc_psi.argtypes = [P, i64, P, P]
+            lib.oracle_ibc_zeta.argtypes = [P, P]
             lib.oracle_num_threads.restype = i32
             _lib = lib
     return _lib
@@ -275,3 +279,71 @@ class Oracle:
         csca = float(np.sum(wq * np.sum(np.abs(F) ** 2, axis=1)))
         cabs = -1.0 / k * float(np.sum(self.w * np.imag(np.sum(x[:, :3] * np.conj(x[:, 3:]), axis=1))))
         return float(cext), csca, cabs
+
+    # ---------------------------------------------------------------- impedance boundary condition
+    # Section 2.3: scatterers modelled by Eq. (2.24) instead of their interior equations; the
+    # system is Eq. (2.25) in E_0 alone, vectors [n_rhs, N, 3].  Z_j = sqrt(mu_j / eps_j) of each
+    # scatterer's medium (principal root), zeta_j = i k0 mu_0 / Z_j.
+
+    def ibc_zeta(self):
+        """zeta_j = i k0 mu_0 / Z_j per scatterer, [J+1] (entry 0 unused)."""
+        z = np.zeros(self.J + 1, dtype=np.complex128)
+        self._lib.oracle_ibc_zeta(self._h, _ptr(z))
+        return z
+
+    def _vec3(self, x):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        if x.ndim == 2:
+            x = x[None]
+        assert x.shape[1:] == (self.N, 3), x.shape
+        return x
+
+    def ibc_matvec(self, x):
+        """y = A_IBC x, the operator of Eq. (2.25); x [n_rhs, N, 3] (or [N, 3])."""
+        squeeze = np.ndim(x) == 2
+        x = self._vec3(x)
+        y = np.empty_like(x)
+        self._lib.oracle_ibc_matvec(self._h, x.shape[0], _ptr(x), _ptr(y))
+        return y[0] if squeeze else y
+
+    def ibc_precond_blocks(self):
+        """The 3x3 self blocks of Eq. (2.25), [N, 3, 3]."""
+        M = np.zeros((self.N, 3, 3), dtype=np.complex128)
+        self._lib.oracle_ibc_precond_blocks(self._h, _ptr(M))
+        return M
+
+    def ibc_psi(self, E):
+        """Psi = n x curl E_0 implied by Eq. (2.24) for surface fields E [n_rhs, N, 3] (or [N, 3])."""
+        squeeze = np.ndim(E) == 2
+        E = self._vec3(E)
+        P = np.empty_like(E)
+        self._lib.oracle_ibc_psi(self._h, E.shape[0], _ptr(E), _ptr(P))
+        return P[0] if squeeze else P
+
+    def ibc_unknowns(self, E):
+        """The 6-vector (Phi, Psi) of Eq. (2.12) for an impedance solution E [.., N, 3], so that
+        the far field, near field and cross sections above apply to it."""
+        return np.concatenate([np.asarray(E), self.ibc_psi(E)], axis=-1)
+
+    def ibc_solve(self, b, tol=1e-10, restart=200, max_iter=2000):
+        """Solve Eq. (2.25) A_IBC x = b for each right-hand side b [n_rhs, N, 3] by right-
+        preconditioned GMRES (scipy's GMRES on A M^-1 with M the 3x3 self blocks; the residual it
+        measures is the true residual).  Returns (x, relres [n_rhs])."""
+        from scipy.sparse.linalg import LinearOperator, gmres
+        b = self._vec3(b)
+        Minv = np.linalg.inv(self.ibc_precond_blocks())
+        n = 3 * self.N
+
+        def apply(u):
+            z = np.einsum("aij,aj->ai", Minv, u.reshape(self.N, 3))
+            return self.ibc_matvec(z).reshape(n)
+
+        op = LinearOperator((n, n), matvec=apply, dtype=np.complex128)
+        xs, res = [], []
+        for r in range(b.shape[0]):
+            u, info = gmres(op, b[r].reshape(n), rtol=tol, atol=0.0, restart=restart, maxiter=max_iter)
+            x = np.einsum("aij,aj->ai", Minv, u.reshape(self.N, 3))
+            rr = np.linalg.norm(self.ibc_matvec(x) - b[r]) / np.linalg.norm(b[r])
+            xs.append(x)
+            res.append(rr)
+        return np.stack(xs), np.array(res)

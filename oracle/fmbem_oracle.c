@@ -31,6 +31,9 @@
  *   - Plane-wave right-hand sides (incident field at the nodes in the background rows, zero in
  *     the scatterer rows, Eq. (2.12) Phi_inc) and the far-field amplitude of the scattered field
  *     from the representation formula of Eqs. (A.4)/(A.8).
+ *   - The impedance-boundary-condition variant of Section 2.3: the 3N operator of Eq. (2.25)
+ *     (background equation with n0 x curl E_0 replaced through Eq. (2.24)), its 3x3 self blocks,
+ *     and the Psi that Eq. (2.24) implies for a given E_0.
  *
  * Layout of every vector: [n_rhs][N][6] complex128 (re, im interleaved), the 6 entries of a node
  * being (Phi_x, Phi_y, Phi_z, Psi_x, Psi_y, Psi_z) for unknowns and (background-domain x,y,z,
@@ -754,4 +757,122 @@ void oracle_polygon_integrals(int nv, const double *pts, const double *nrm, doub
     for (int e = 0; e < nv; ++e) edge_triangle(pts + 3 * e, pts + 3 * ((e + 1) % nv), nrm, &I1, &S, V1, V3);
     out[0] = I1; out[1] = S;
     for (int q = 0; q < 3; ++q) { out[2 + q] = V1[q]; out[5 + q] = V3[q]; }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Impedance boundary condition, Section 2.3.
+ * On a good conductor Eq. (2.24), n x E = Z n x (n x H), with n the scatterer's outward normal
+ * and Z = sqrt(mu_j / eps_j) the surface impedance relative to the vacuum impedance (principal
+ * root, Re Z >= 0), ties the tangential exterior fields together.  With curl E = i k0 mu_0 H (H
+ * in units of the vacuum impedance) it gives
+ *   n0 x curl E_0 = zeta n0 x (n0 x E_0),   zeta = i k0 mu_0 / Z,
+ * and the background equation (2.5) becomes Eq. (2.25), in E_0 alone (3 unknowns per node).
+ * Moved into the form of Eq. (2.12) (operator on the left, E_inc on the right) and discretised
+ * with the one-point rule of Eq. (2.8):
+ *   1/2 E(s_a) - sum_b w_b [n0 grad'g0 - (n0.grad'g0) I - grad'g0 n0] . E(s_b)
+ *              + sum_b w_b zeta_b g0 n0 x (n0 x E(s_b))  =  E_inc(s_a),
+ * n0 = -n_b, g0 = g_0(s_b, s_a); the b = a term from the background self-patch integrals of
+ * Appendix B.  Vectors are [n_rhs][N][3] complex. */
+static cplx ibc_zeta(const oracle_ctx *c, int j) { return I * c->k0 * c->mu[0] / csqrt(c->mu[j] / c->eps[j]); }
+
+/* n0 x (n0 x v) = n0 (n0.v) - v for a unit normal (the same for n and -n) */
+static inline void nxnx(const double *nn, const cplx *v, cplx *o) {
+    cplx nv = nn[0] * v[0] + nn[1] * v[1] + nn[2] * v[2];
+    for (int q = 0; q < 3; ++q) o[q] = nn[q] * nv - v[q];
+}
+
+static void ibc_node_rows(const oracle_ctx *c, int64_t a, int64_t n_rhs, const cplx *x, cplx *out) {
+    const int64_t N = c->N;
+    const double *sa = c->s + 3 * a;
+    const cplx k0 = c->k[0];
+    for (int64_t r = 0; r < n_rhs * 3; ++r) out[r] = 0;
+    for (int64_t b = 0; b < N; ++b) {
+        if (b == a) continue;
+        double rv[3]; sub3(c->s + 3 * b, sa, rv);
+        double R = norm3(rv);
+        const double wb = c->w[b];
+        const double *nb = c->n + 3 * b;
+        double n0[3] = {-nb[0], -nb[1], -nb[2]};
+        cplx g0 = cexp(I * k0 * R) / (4 * PI * R);
+        cplx c0 = g0 * (I * k0 - 1.0 / R) / R;
+        cplx a0[3] = {c0 * rv[0], c0 * rv[1], c0 * rv[2]};
+        cplx zg = ibc_zeta(c, c->dom[b]) * g0;
+        for (int64_t r = 0; r < n_rhs; ++r) {
+            const cplx *xb = x + (r * N + b) * 3;
+            cplx B[3], T[3];
+            bracket(n0, a0, xb, B);
+            nxnx(n0, xb, T);
+            for (int q = 0; q < 3; ++q) out[3 * r + q] += -wb * B[q] + wb * zg * T[q];
+        }
+    }
+    const double *na = c->n + 3 * a;
+    double n0a[3] = {-na[0], -na[1], -na[2]};
+    cplx zs = ibc_zeta(c, c->dom[a]) * c->Sg[2 * a];
+    for (int64_t r = 0; r < n_rhs; ++r) {
+        const cplx *xa = x + (r * N + a) * 3;
+        cplx B[3], T[3];
+        bracket(n0a, c->Sdg + 6 * a, xa, B);
+        nxnx(n0a, xa, T);
+        for (int q = 0; q < 3; ++q) out[3 * r + q] += 0.5 * xa[q] - B[q] + zs * T[q];
+    }
+}
+
+/* y = A_IBC x (Eq. 2.25), x and y [n_rhs][N][3] */
+void oracle_ibc_matvec(const oracle_ctx *c, int64_t n_rhs, const double *x_, double *y_) {
+    const cplx *x = (const cplx *)x_;
+    cplx *y = (cplx *)y_;
+    const int64_t N = c->N;
+#pragma omp parallel
+    {
+        cplx *buf = malloc(sizeof(cplx) * 3 * n_rhs);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t a = 0; a < N; ++a) {
+            ibc_node_rows(c, a, n_rhs, x, buf);
+            for (int64_t r = 0; r < n_rhs; ++r)
+                for (int q = 0; q < 3; ++q) y[(r * N + a) * 3 + q] = buf[3 * r + q];
+        }
+        free(buf);
+    }
+}
+
+/* 3x3 self block of Eq. (2.25) per node, row-major [N][3][3]: the preconditioner block of
+ * Eq. (3.2) for the impedance system */
+void oracle_ibc_precond_blocks(const oracle_ctx *c, double *M_) {
+    cplx *M = (cplx *)M_;
+    for (int64_t a = 0; a < c->N; ++a)
+        for (int col = 0; col < 3; ++col) {
+            cplx e[3] = {0, 0, 0};
+            e[col] = 1.0;
+            cplx y[3];
+            const double *na = c->n + 3 * a;
+            double n0a[3] = {-na[0], -na[1], -na[2]};
+            cplx B[3], T[3];
+            bracket(n0a, c->Sdg + 6 * a, e, B);
+            nxnx(n0a, e, T);
+            cplx zs = ibc_zeta(c, c->dom[a]) * c->Sg[2 * a];
+            for (int q = 0; q < 3; ++q) y[q] = 0.5 * e[q] - B[q] + zs * T[q];
+            for (int q = 0; q < 3; ++q) M[9 * a + 3 * q + col] = y[q];
+        }
+}
+
+/* The unknown Psi = n x curl E_0 of Eq. (2.12) (scatterer normal) implied by Eq. (2.24):
+ * Psi = -(n0 x curl E_0) = -zeta n0 x (n0 x E_0) = zeta (E_0 - n (n.E_0)).  E, Psi [n_rhs][N][3]. */
+void oracle_ibc_psi(const oracle_ctx *c, int64_t n_rhs, const double *E_, double *Psi_) {
+    const cplx *E = (const cplx *)E_;
+    cplx *Psi = (cplx *)Psi_;
+    for (int64_t r = 0; r < n_rhs; ++r)
+        for (int64_t a = 0; a < c->N; ++a) {
+            const cplx *e = E + (r * c->N + a) * 3;
+            cplx T[3];
+            nxnx(c->n + 3 * a, e, T);
+            cplx z = ibc_zeta(c, c->dom[a]);
+            for (int q = 0; q < 3; ++q) Psi[(r * c->N + a) * 3 + q] = -z * T[q];
+        }
+}
+
+/* zeta_j = i k0 mu_0 / Z_j of every scatterer, [J+1] complex (entry 0 unused, set to 0) */
+void oracle_ibc_zeta(const oracle_ctx *c, double *z_) {
+    cplx *z = (cplx *)z_;
+    z[0] = 0;
+    for (int j = 1; j <= c->J; ++j) z[j] = ibc_zeta(c, j);
 }

@@ -64,6 +64,32 @@ def coefficients(eps_in, x, nmax=None):
     return a, b, c, d
 
 
+def ibc_coefficients(eta, x, nmax=None):
+    """Scattering coefficients (a_n, b_n), n = 1..nmax, of a sphere whose surface obeys the
+    impedance condition of Eq. (2.24), n x E = Z n x (n x H), with eta = Z / Z_background.
+    From E_t = Z (r x H) at r = a with the total exterior field of Bohren & Huffman Eqs. (4.37),
+    (4.45): the theta and phi components give, per degree n,
+        b_n = (psi_n - i eta psi'_n) / (xi_n - i eta xi'_n),
+        a_n = (psi'_n + i eta psi_n) / (xi'_n + i eta xi_n)     (argument x = k a).
+    eta = 0 is the perfect conductor (a_n = psi'_n/xi'_n, b_n = psi_n/xi_n); eta = 1/m is the
+    large-|m| limit of the coefficients in ``coefficients``."""
+    if nmax is None:
+        nmax = default_nmax(x)
+    n = np.arange(1, nmax + 1)
+    px, dpx = _psi(n, x), _dpsi(n, x)
+    xx, dxx = _xi(n, x), _dxi(n, x)
+    a = (dpx + 1j * eta * px) / (dxx + 1j * eta * xx)
+    b = (px - 1j * eta * dpx) / (xx - 1j * eta * dxx)
+    return a, b
+
+
+def _scattering(eps_in, x, nmax, impedance):
+    if impedance is None:
+        a, b, _, _ = coefficients(eps_in, x, nmax)
+        return a, b
+    return ibc_coefficients(impedance, x, nmax)
+
+
 def _angular(nmax, mu):
     """pi_n, tau_n (n = 1..nmax) at mu = cos(theta); shapes [nmax, P]."""
     P = mu.shape[0]
@@ -116,14 +142,19 @@ def _spherical(points):
     return r, theta, phi
 
 
-def fields(points, k, a, eps_in, region="outside", nmax=None):
+def fields(points, k, a, eps_in, region="outside", nmax=None, impedance=None):
     """Electric field E and curl E at ``points`` [P,3] (must lie in ``region``: 'outside' gives the
     total exterior field E_inc + E_sca, 'inside' the internal field).  Returns (E, curlE),
-    each [P,3] complex."""
+    each [P,3] complex.  With ``impedance`` = eta the sphere obeys Eq. (2.24) with Z = eta
+    times the background impedance (``eps_in`` unused; 'outside' only)."""
     x = k * a
     if nmax is None:
         nmax = default_nmax(x) + 4
-    an, bn, cn, dn = coefficients(eps_in, x, nmax)
+    if impedance is not None:
+        assert region == "outside"
+        an, bn = ibc_coefficients(impedance, x, nmax)
+    else:
+        an, bn, cn, dn = coefficients(eps_in, x, nmax)
     n = np.arange(1, nmax + 1)
     En = (1j ** n) * (2 * n + 1) / (n * (n + 1))
     r, theta, phi = _spherical(np.asarray(points, dtype=np.float64))
@@ -152,18 +183,21 @@ def fields(points, k, a, eps_in, region="outside", nmax=None):
     return _to_cartesian(Ei, theta, phi), _to_cartesian(Ci, theta, phi)
 
 
-def surface_unknowns(points, normals, k, a, eps_in, nmax=None):
+def surface_unknowns(points, normals, k, a, eps_in, nmax=None, impedance=None):
     """The BEM unknowns of Eq. (2.12) from the Mie series at surface points: Phi = E_0 (total
     exterior field) and Psi = n x curl E_0 with the scatterer's outward normal n.  [P,6]."""
-    E, C = fields(points, k, a, eps_in, "outside", nmax)
+    E, C = fields(points, k, a, eps_in, "outside", nmax, impedance)
     Psi = np.cross(normals, C)
     return np.concatenate([E, Psi], axis=1)
 
 
-def cross_sections(k, a, eps_in, nmax=None):
-    """(C_ext, C_sca, C_abs) from the Mie coefficients (Bohren & Huffman Eqs. 4.61-4.62)."""
+def cross_sections(k, a, eps_in, nmax=None, impedance=None):
+    """(C_ext, C_sca, C_abs) from the Mie coefficients (Bohren & Huffman Eqs. 4.61-4.62); with
+    ``impedance`` = eta those of the impedance sphere (``ibc_coefficients``)."""
     x = k * a
-    an, bn, _, _ = coefficients(eps_in, x, nmax)
+    if nmax is None:
+        nmax = default_nmax(x)
+    an, bn = _scattering(eps_in, x, nmax, impedance)
     n = np.arange(1, len(an) + 1)
     cext = 2 * np.pi / k ** 2 * np.sum((2 * n + 1) * (an + bn).real)
     csca = 2 * np.pi / k ** 2 * np.sum((2 * n + 1) * (abs(an) ** 2 + abs(bn) ** 2))
