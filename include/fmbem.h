@@ -67,6 +67,22 @@ typedef enum { FMBEM_NODES_VERTEX = 0, FMBEM_NODES_CENTROID = 1 } fmbem_node_mod
  * on it should stop at a loose tolerance (1e-2) and let the outer refinement finish. */
 typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1, FMBEM_TF32 = 2 } fmbem_precision;
 
+/* How the scatterers are modelled (Section 2).
+ * PENETRABLE: the interior fields are unknowns too; Eqs. (2.5)-(2.13), 6N equations.
+ * IMPEDANCE: good conductors under the impedance boundary condition of Eq. (2.24),
+ *   n x E = Z n x (n x H), Z_j = sqrt(mu_j / eps_j) (relative to the vacuum impedance, principal
+ *   root) and n the scatterer's outward normal; the interior domains are not modelled
+ *   (Section 2.3).  The vectors keep the 6-entry layout, and the 6N system becomes
+ *     background rows of a node:  the background equation of Eq. (2.12), unchanged;
+ *     scatterer rows of a node:   Psi - zeta_j (Phi - n (n.Phi)) = 0, zeta_j = i k0 mu_0 / Z_j,
+ *   i.e. Eq. (2.24) itself written with Psi = n x curl E_0 = i k0 mu_0 (n x H_0).  Eliminating Psi
+ *   node by node gives exactly Eq. (2.25) in Phi = E_0 alone; GMRES on the 6N form with right-hand
+ *   sides whose scatterer rows are zero (as fmbem_plane_wave_rhs writes them) runs the same
+ *   iterations as GMRES on Eq. (2.25) with the node-block preconditioner, and its solution carries
+ *   the Psi that the far-field, near-field and cross-section routines take.  The fast multipole
+ *   passes run for the background domain only; eps_j, mu_j enter through Z_j alone. */
+typedef enum { FMBEM_BOUNDARY_PENETRABLE = 0, FMBEM_BOUNDARY_IMPEDANCE = 1 } fmbem_boundary;
+
 typedef struct { double re, im; } fmbem_c64;
 
 /* Closed, consistently oriented triangle mesh.  vertices [n_vertices][3] and triangles
@@ -108,6 +124,7 @@ typedef struct {
                                 sides instead of evaluating exp, sincos and rsqrt per pair:
                                 0 off, 1 on, -1 automatic: on when the cache (32 bytes per pair and
                                 domain) takes at most a quarter of the free device memory [-1]    */
+    int boundary;            /* fmbem_boundary: how the scatterers enter [PENETRABLE]             */
 } fmbem_options;
 
 void fmbem_default_options(fmbem_options *opt);

@@ -27,6 +27,8 @@ __all__ = [
 
 FP64, FP32, TF32 = 0, 1, 2
 NODES_VERTEX, NODES_CENTROID = 0, 1
+# boundary option: penetrable scatterers (Eqs. 2.5-2.13) or the impedance condition of Eq. (2.24)
+PENETRABLE, IMPEDANCE = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_MESH", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED", 6: "BREAKDOWN"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fmbem.h")
 
@@ -41,7 +43,7 @@ class Options(ctypes.Structure):
     _fields_ = [("node_mode", ctypes.c_int), ("p", ctypes.c_int), ("leaf_size", ctypes.c_int),
                 ("max_level", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("solve_precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("outer_precision", ctypes.c_int), ("m2l_rotation", ctypes.c_int),
-                ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int)]
+                ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class Mesh(ctypes.Structure):

@@ -71,6 +71,15 @@ static c64 root_with_nonneg_imag(c64 z) {
     return s;
 }
 
+// principal square root (Re >= 0): the surface impedance Z = sqrt(mu / eps) of Eq. (2.24)
+static c64 principal_root(c64 z) {
+    double r = cabsd(z);
+    double a = std::sqrt(std::max(0.0, 0.5 * (r + z.re)));
+    double b = std::sqrt(std::max(0.0, 0.5 * (r - z.re)));
+    if (z.im < 0) b = -b;
+    return {a, b};
+}
+
 extern "C" {
 
 void fmbem_default_options(fmbem_options *o) {
@@ -86,6 +95,7 @@ void fmbem_default_options(fmbem_options *o) {
     o->m2l_rotation = -1;
     o->near_cache = -1;
     o->profile_phases = 0;
+    o->boundary = FMBEM_BOUNDARY_PENETRABLE;
 }
 
 fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
@@ -109,7 +119,8 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32 && o.solve_precision != FMBEM_TF32) ||
         !(o.inner_tol > 0 && o.inner_tol < 1) ||
         (o.outer_precision != FMBEM_FP64 && o.outer_precision != FMBEM_FP32) || o.m2l_rotation < -1 ||
-        o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1) {
+        o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1 ||
+        (o.boundary != FMBEM_BOUNDARY_PENETRABLE && o.boundary != FMBEM_BOUNDARY_IMPEDANCE)) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
@@ -134,6 +145,23 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
             // Eq. (2.13): k_d = k0 sqrt(eps_d mu_d), gamma_d = mu_d / mu_0
             h->k[d] = k0 * root_with_nonneg_imag(h->eps[d] * h->mu[d]);
             h->gam[d] = d == 0 ? c64{1.0, 0.0} : cdiv(h->mu[d], h->mu[0]);
+        }
+        h->ibc = o.boundary == FMBEM_BOUNDARY_IMPEDANCE;
+        h->Jf = h->ibc ? 0 : h->J;
+        if (h->ibc) {
+            // Eq. (2.24): zeta_j = i k0 mu_0 / Z_j with Z_j = sqrt(mu_j / eps_j); the scatterers'
+            // interiors are not modelled, so their media become the background's (k_j = k_0,
+            // T_j = I, gamma_j = 1), which keeps every per-domain table finite and unused
+            h->zeta.assign(h->J + 1, c64{0, 0});
+            for (int d = 1; d <= h->J; ++d) {
+                h->zeta[d] = cdiv(c64{0.0, k0} * h->mu[0], principal_root(cdiv(h->mu[d], h->eps[d])));
+                h->eps[d] = h->eps[0];
+                h->mu[d] = h->mu[0];
+                h->k[d] = h->k[0];
+                h->gam[d] = {1.0, 0.0};
+            }
+            h->d_zeta = (c64 *)dev_alloc(h, sizeof(c64) * (h->J + 1));
+            CK(cudaMemcpyAsync(h->d_zeta, h->zeta.data(), sizeof(c64) * (h->J + 1), cudaMemcpyHostToDevice, s));
         }
         build_geometry(h, mesh, s);
         build_tree(h, s);

@@ -84,6 +84,13 @@ struct fmbem {
     int J = 0;
     double k0 = 0;
     std::vector<c64> eps, mu, k, gam;  // [J+1]
+    // impedance boundary condition (Section 2.3): the scatterer rows are Eq. (2.24) with
+    // zeta[j] = i k0 mu_0 / Z_j; the media of the scatterers are then the background's (their
+    // interiors are not modelled) and the multipole passes run over domains 0..Jf only
+    bool ibc = false;
+    int Jf = 0;
+    std::vector<c64> zeta;  // [J+1], entry 0 unused
+    c64 *d_zeta = nullptr;  // device copy
     int p = 0, p2 = 0;                 // truncation number and p^2 coefficients
 
     // host copies of geometry (user order)

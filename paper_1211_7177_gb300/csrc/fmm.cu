@@ -1936,14 +1936,14 @@ __global__ void k_check_z_mirror(int p, int64_t nz, const cx<R> *Zp, const unsig
 
 // dens[side][r][i][0..2] = x_{perm(i), 3 side + c}, unweighted, sorted order
 template <typename R>
-__global__ void k_prep_adj(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, cx<R> *dens) {
+__global__ void k_prep_adj(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, int sides, cx<R> *dens) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t r = blockIdx.y;
     if (i >= N) return;
     const c64 *xa = x + (r * N + perm[i]) * 6;
     for (int side = 0; side < 2; ++side) {
         cx<R> *dn = dens + ((side * nr + r) * N + i) * 6;
-        for (int c = 0; c < 3; ++c) dn[c] = to<R>(xa[3 * side + c]);
+        for (int c = 0; c < 3; ++c) dn[c] = side < sides ? to<R>(xa[3 * side + c]) : cx<R>{0, 0};
     }
 }
 
@@ -2536,7 +2536,7 @@ static void launch_rot(const RotLaunch &rl, int64_t nch, cudaStream_t s, int64_t
 // M2M (Eq. 2.20) from level l_max up to level 2, on the multipole expansions in h->Cexp
 template <typename R>
 static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
-    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const int p2 = h->p2, lmax = h->lmax, J = h->Jf;
     const bool f32 = sizeof(R) == 4;
     cx<R> *C = (cx<R> *)h->Cexp;
     const cx<R> *Tmm = f32 ? (const cx<R> *)h->T_mm32 : (const cx<R> *)h->T_mm64;
@@ -2584,7 +2584,7 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
 // downward pass (Eq. 2.21): M2L over the FF lists and L2L, h->Cexp -> h->Dexp, all levels
 template <typename R>
 static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_cores) {
-    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const int p2 = h->p2, lmax = h->lmax, J = h->Jf;
     const bool f32 = sizeof(R) == 4;
     cx<R> *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
     const cx<R> *Tm2l = f32 ? (const cx<R> *)h->T_m2l32 : (const cx<R> *)h->T_m2l64;
@@ -2697,11 +2697,34 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     }
 }
 
+// Impedance boundary (Section 2.3): the scatterer rows of every node are the local relation of
+// Eq. (2.24), y_s = M_s x with M_s the scatterer rows of the node's 6x6 block (Psi - zeta (Phi -
+// n (n.Phi))); they replace what the near-field kernel wrote there.  Thread per (rhs, node), user
+// order [nr][N][6].
+__global__ void k_local_rows(int64_t N, int64_t nr, const c64 *Mself, const c64 *x, c64 *y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N * nr) return;
+    const c64 *M = Mself + 36 * (i % N) + 18;
+    const c64 *xi = x + 6 * i;
+    for (int q = 0; q < 3; ++q) {
+        c64 acc = {0, 0};
+        for (int c = 0; c < 6; ++c) cfma(acc, M[6 * q + c], xi[c]);
+        y[6 * i + 3 + q] = acc;
+    }
+}
+
+// zero the local expansions of the domains Jf+1..J (not computed with an impedance boundary) in
+// the layout of an nr-column call, so that the near-field kernels read zeros there
+static void clear_unused_domains(fmbem *h, int64_t nr, size_t real_bytes, cudaStream_t s) {
+    const size_t per = 2 * real_bytes * (size_t)h->nbox * 3 * nr * h->p2;
+    if (h->J > h->Jf) CK(cudaMemsetAsync((char *)h->Dexp + per * (h->Jf + 1), 0, per * (h->J - h->Jf), s));
+}
+
 template <typename R>
 static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
                         bool tensor_cores = false) {
     const int64_t N = h->N;
-    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const int p2 = h->p2, lmax = h->lmax, J = h->Jf;  // multipole passes over domains 0..Jf
     const bool f32 = sizeof(R) == 4;
     cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
     const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
@@ -2713,6 +2736,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // k_near_r in the half of the density buffer that double precision would use
     const int64_t nrT = f32 ? (nr / 32) * 32 : 0;
     cx<R> *densT = nrT > 0 ? dens + 2 * nr * N * 6 : nullptr;
+    if (h->ibc) clear_unused_domains(h, nr, sizeof(R), s);
     k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens);
     CKL("k_prep");
     if (densT != nullptr) {
@@ -2806,6 +2830,10 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                        h->Mself, x, y, h->near_base, (const V4<R> *)h->near_cache64);
     }
     CKL("k_near");
+    if (h->ibc) {  // impedance boundary: the scatterer rows are the local relation of Eq. (2.24)
+        k_local_rows<<<nblk(N * nr, 128), 128, 0, s>>>(N, nr, h->Mself, x, y);
+        CKL("k_local_rows");
+    }
     if (timing) CK(cudaEventRecord(h->ev[4], s));
 }
 
@@ -2814,13 +2842,17 @@ template <typename R>
 static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
                          bool tensor_cores = false) {
     const int64_t N = h->N;
-    const int p2 = h->p2, lmax = h->lmax, J = h->J;
+    const int p2 = h->p2, lmax = h->lmax, J = h->Jf;  // multipole passes over domains 0..Jf
     const bool f32 = sizeof(R) == 4;
     cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
     const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
     const cx<R> *Bl2p = f32 ? (const cx<R> *)h->B_l2p32 : (const cx<R> *)h->B_l2p64;
     const cx<R> *Bl2pg = f32 ? (const cx<R> *)h->B_l2pg32 : (const cx<R> *)h->B_l2pg64;
-    k_prep_adj<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, dens);
+    // impedance boundary: the scatterer rows of A are local (Eq. 2.24), so the transposed product
+    // takes them from the transposed self blocks alone; the scatterer sources are zero, and so are
+    // the unused local expansions of the scatterer domains that the near-field kernel reads
+    if (h->ibc) clear_unused_domains(h, nr, sizeof(R), s);
+    k_prep_adj<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->ibc ? 1 : 2, dens);
     CKL("k_prep_adj");
     const LevelInfo &L = h->lev[lmax];
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);

@@ -60,9 +60,11 @@ __device__ void project_rel(const double *P, const double *O, const double *n, d
     for (int q = 0; q < 3; ++q) out[q] = d[q] - a * n[q];
 }
 
-// self blocks and LU for one node; ps are its patch integrals, n its outward normal
-__device__ void self_block(const PatchSums &ps, const double *n, c64 kb, c64 kj, c64 tj, c64 gj, c64 *M, c64 *LU,
-                           int8_t *piv) {
+// self blocks and LU for one node; ps are its patch integrals, n its outward normal.  With an
+// impedance boundary (ibc) the scatterer rows are the local relation of Eq. (2.24),
+// Psi - zeta (Phi - n (n.Phi)) = 0, zeta = i k0 mu_0 / Z.
+__device__ void self_block(const PatchSums &ps, const double *n, c64 kb, c64 kj, c64 tj, c64 gj, bool ibc, c64 zeta,
+                           c64 *M, c64 *LU, int8_t *piv) {
     const double inv4pi = 1.0 / (4.0 * FMBEM_PI), inv8pi = 1.0 / (8.0 * FMBEM_PI);
     for (int i = 0; i < 36; ++i) M[i] = {0, 0};
     for (int side = 0; side < 2; ++side) {
@@ -100,6 +102,14 @@ __device__ void self_block(const PatchSums &ps, const double *n, c64 kb, c64 kj,
         c64 dpsi = side == 0 ? -Sg : (gj * Sg);
         for (int q = 0; q < 3; ++q) M[(3 * side + q) * 6 + 3 + q] = dpsi;
     }
+    if (ibc)
+        for (int q = 0; q < 3; ++q)
+            for (int c = 0; c < 6; ++c) {
+                c64 v = {0, 0};
+                if (c < 3) v = zeta * (n[q] * n[c] - (q == c ? 1.0 : 0.0));
+                else if (c == 3 + q) v = {1.0, 0.0};
+                M[(3 + q) * 6 + c] = v;
+            }
     // LU with partial pivoting, row-major 6x6
     for (int i = 0; i < 36; ++i) LU[i] = M[i];
     for (int c = 0; c < 6; ++c) {
@@ -122,11 +132,12 @@ __device__ void self_block(const PatchSums &ps, const double *n, c64 kb, c64 kj,
 __device__ void domain_consts(const c64 *kd, const c64 *td, const c64 *gd, int j, c64 &kb, c64 &kj, c64 &tj, c64 &gj) {
     kb = kd[0]; kj = kd[j]; tj = td[j]; gj = gd[j];
 }
+__device__ c64 zeta_of(const c64 *zd, int j) { return zd ? zd[j] : c64{0, 0}; }
 
 // vertex nodes: weight 1/3 of incident areas, area-weighted normal, dual-cell patch
 __global__ void k_vertex_nodes(int64_t nv, const double *V, const int32_t *F, const int32_t *vt_start,
                                const int32_t *vt_tri, const int32_t *vdom, const c64 *kd, const c64 *td, const c64 *gd,
-                               double *pos, double *nrm, double *w, c64 *M, c64 *LU, int8_t *piv) {
+                               const c64 *zd, double *pos, double *nrm, double *w, c64 *M, c64 *LU, int8_t *piv) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const double *O = V + 3 * v;
@@ -161,13 +172,13 @@ __global__ void k_vertex_nodes(int64_t nv, const double *V, const int32_t *F, co
     w[v] = wsum;
     c64 kb, kj, tj, gj;
     domain_consts(kd, td, gd, vdom[v], kb, kj, tj, gj);
-    self_block(ps, n, kb, kj, tj, gj, M + 36 * v, LU + 36 * v, piv + 6 * v);
+    self_block(ps, n, kb, kj, tj, gj, zd != nullptr, zeta_of(zd, vdom[v]), M + 36 * v, LU + 36 * v, piv + 6 * v);
 }
 
 // centroid nodes: the triangle is its own patch
 __global__ void k_centroid_nodes(int64_t nt, const double *V, const int32_t *F, const int32_t *tdom, const c64 *kd,
-                                 const c64 *td, const c64 *gd, double *pos, double *nrm, double *w, c64 *M, c64 *LU,
-                                 int8_t *piv) {
+                                 const c64 *td, const c64 *gd, const c64 *zd, double *pos, double *nrm, double *w, c64 *M,
+                                 c64 *LU, int8_t *piv) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
     const double *A = V + 3 * F[3 * t], *B = V + 3 * F[3 * t + 1], *C = V + 3 * F[3 * t + 2];
@@ -187,7 +198,7 @@ __global__ void k_centroid_nodes(int64_t nt, const double *V, const int32_t *F, 
     w[t] = 0.5 * l;
     c64 kb, kj, tj, gj;
     domain_consts(kd, td, gd, tdom[t], kb, kj, tj, gj);
-    self_block(ps, n, kb, kj, tj, gj, M + 36 * t, LU + 36 * t, piv + 6 * t);
+    self_block(ps, n, kb, kj, tj, gj, zd != nullptr, zeta_of(zd, tdom[t]), M + 36 * t, LU + 36 * t, piv + 6 * t);
 }
 
 // z = M^{-1} v per node (Eq. 3.1-3.2), vectors in user order [n_rhs][N][6]
@@ -402,15 +413,15 @@ void build_geometry(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s) {
         int32_t *dvt = (int32_t *)dev_alloc(h, sizeof(int32_t) * 3 * nt);
         CK(cudaMemcpyAsync(dvs, vt_start.data(), sizeof(int32_t) * (nv + 1), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dvt, vt_tri.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
-        k_vertex_nodes<<<(unsigned)((nv + TB - 1) / TB), TB, 0, s>>>(nv, dV, dF, dvs, dvt, dDom, dk, dt, dg, upos, unrm, uw,
-                                                                   h->Mself, h->Mlu, h->piv);
+        k_vertex_nodes<<<(unsigned)((nv + TB - 1) / TB), TB, 0, s>>>(nv, dV, dF, dvs, dvt, dDom, dk, dt, dg, h->d_zeta, upos,
+                                                                   unrm, uw, h->Mself, h->Mlu, h->piv);
         CKL("k_vertex_nodes");
         CK(cudaStreamSynchronize(s));
         dev_free(h, dvs);
         dev_free(h, dvt);
     } else {
-        k_centroid_nodes<<<(unsigned)((nt + TB - 1) / TB), TB, 0, s>>>(nt, dV, dF, dDom, dk, dt, dg, upos, unrm, uw, h->Mself,
-                                                                     h->Mlu, h->piv);
+        k_centroid_nodes<<<(unsigned)((nt + TB - 1) / TB), TB, 0, s>>>(nt, dV, dF, dDom, dk, dt, dg, h->d_zeta, upos, unrm,
+                                                                     uw, h->Mself, h->Mlu, h->piv);
         CKL("k_centroid_nodes");
     }
     // host copies of the user-order geometry; the sorted copies are made by the tree build

@@ -393,7 +393,7 @@ void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s) {
         const LevelInfo &Lv = h->lev[l];
         const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), n, nsub, stages, tcols,
                         l < h->lmax ? 1 : 0};
-        k_m2l_tc<<<dim3((unsigned)Lv.n, h->J + 1, (unsigned)ntile), 128, smem, s>>>(
+        k_m2l_tc<<<dim3((unsigned)Lv.n, h->Jf + 1, (unsigned)ntile), 128, smem, s>>>(
             tmC, tmD, P, h->box_parent, h->box_key, h->ff_start, h->ff_src, h->ff_off, h->Atc, h->Lltc, D, h->tc_err);
         CKL("k_m2l_tc");
     }

@@ -589,3 +589,113 @@ def test_torus_sampled_rows_multi_rhs():
         err = rel(y, yo)
         print(f"torus precision={prec} rel L2 = {err:.3e}", g.tree_info())
         assert err < MATVEC_TOL
+
+
+# ------------------------------------------------------------------ impedance boundary (Section 2.3)
+@pytest.fixture(scope="module")
+def ibc_s4():
+    """Good conductor under the impedance condition (eps = 1 + 1e4 i, Z = 1/sqrt(eps)), sphere
+    a = 1, k0 a = 1, 2562 nodes, p = 10 (rotation-form translations).  On a near-perfect conductor
+    the field is nearly normal and Psi = zeta E_tan is ~1 % of zeta E, so a solve turns the
+    multipole error into a hundredfold larger relative error of Psi; p = 10 keeps that within the
+    1e-3 surface-field tolerance."""
+    V, F, D = fi.icosphere(4)
+    eps, mu = [1.0, 1 + 1e4j], [1.0, 1.0]
+    return oracle.Oracle(V, F, D, eps, mu, 1.0), fm.FMBEM(V, F, D, eps, mu, 1.0, p=10, boundary=fm.IMPEDANCE)
+
+
+@pytest.mark.parametrize("precision", [fm.FP64, fm.FP32])
+def test_ibc_matvec_matches_oracle(ibc_s4, precision):
+    """Background rows as the oracle's Eq. (2.12) rows, scatterer rows the local relation of
+    Eq. (2.24) (Psi - zeta (Phi - n (n.Phi))); with Psi eliminated through Eq. (2.24) the product is
+    the oracle's Eq. (2.25) operator."""
+    o, g = ibc_s4
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=(2, o.N, 6)) + 1j * rng.normal(size=(2, o.N, 6))
+    y = g.matvec(to_dev(x), precision=precision).cpu().numpy()
+    assert rel(y[..., :3], o.matvec(x)[..., :3]) < MATVEC_TOL
+    assert rel(y[..., 3:], x[..., 3:] - o.ibc_psi(x[..., :3])) < 1e-13
+    E = x[..., :3]
+    x6 = o.ibc_unknowns(E)
+    y2 = g.matvec(to_dev(x6), precision=precision).cpu().numpy()
+    assert rel(y2[..., :3], o.ibc_matvec(E)) < MATVEC_TOL
+    assert np.abs(y2[..., 3:]).max() < 1e-13 * np.abs(x6[..., 3:]).max()
+
+
+@pytest.mark.parametrize("precision", [fm.FP64, fm.FP32])
+def test_ibc_adjoint_matches_oracle(ibc_s4, precision):
+    """A^T of the impedance system [[A_00, A_0Psi], [-C, I]] (C = zeta (I - n n^T), symmetric):
+    the multipole part against the oracle's transpose of the background rows, the local part
+    exactly."""
+    o, g = ibc_s4
+    rng = np.random.default_rng(12)
+    x = rng.normal(size=(2, o.N, 6)) + 1j * rng.normal(size=(2, o.N, 6))
+    yt = g.adjoint_matvec(to_dev(x), precision=precision).cpu().numpy()
+    x0 = x.copy()
+    x0[..., 3:] = 0
+    far_near = yt.copy()
+    far_near[..., :3] += o.ibc_psi(x[..., 3:])
+    far_near[..., 3:] -= x[..., 3:]
+    assert rel(far_near, o.matvec_transpose(x0)) < MATVEC_TOL
+    z = rng.normal(size=(2, o.N, 6)) + 1j * rng.normal(size=(2, o.N, 6))
+    lhs = np.sum(z * g.matvec(to_dev(x), precision=precision).cpu().numpy())
+    rhs = np.sum(g.adjoint_matvec(to_dev(z), precision=precision).cpu().numpy() * x)
+    assert abs(lhs - rhs) < MATVEC_TOL * abs(lhs)
+
+
+def test_ibc_solve_matches_oracle(ibc_s4):
+    """GMRES on the 6N impedance system against the oracle's solve of Eq. (2.25); the Psi rows
+    of the solution are the Psi of Eq. (2.24), and the cross sections computed on the device
+    from it match the oracle's."""
+    o, g = ibc_s4
+    d = np.array([[0.0, 0.0, 1.0]])
+    e = np.array([[1.0, 0.0, 0.0]], dtype=np.complex128)
+    x, its, rr, st = g.solve(g.plane_wave_rhs(d, e), tol=1e-8)
+    assert st == 0 and rr.max() <= 1e-8
+    xg = x.cpu().numpy()[0]
+    xo, res = o.ibc_solve(o.plane_wave_rhs(d[0], e[0])[:, :, :3], tol=1e-10)
+    assert res[0] < 1e-9
+    assert rel(xg[:, :3], xo[0]) < SOLVE_TOL
+    assert rel(xg[:, 3:], o.ibc_psi(xo[0])) < SOLVE_TOL
+    cs = np.asarray(g.cross_sections(x, d, e))[:, 0]
+    cso = o.cross_sections(o.ibc_unknowns(xo[0]), d[0], e[0])
+    np.testing.assert_allclose(cs, cso, rtol=2e-3)
+
+
+def test_ibc_tf32_batch_matches_fp64():
+    """16 right-hand sides (M2L and L2L on the tensor cores) in the impedance mode, against the
+    FP64 product."""
+    V, F, D = fi.icosphere(4)
+    g = fm.FMBEM(V, F, D, [1.0, 1 + 1e4j], [1.0, 1.0], 1.0, boundary=fm.IMPEDANCE)
+    rng = np.random.default_rng(13)
+    x = to_dev(rng.normal(size=(16, g.N, 6)) + 1j * rng.normal(size=(16, g.N, 6)))
+    y64 = g.matvec(x).cpu().numpy()
+    ytc = g.matvec(x, precision=fm.TF32).cpu().numpy()
+    assert rel(ytc[..., :3], y64[..., :3]) < MATVEC_TOL
+    assert rel(ytc[..., 3:], y64[..., 3:]) < 1e-13
+
+
+def test_ibc_sphere_converges_to_mie_on_gpu():
+    """Lossy impedance sphere (Z = 1/sqrt(2.25 + 1i), k0 a = 1) at 10242 and 40962 nodes, sizes the
+    dense oracle does not reach: the surface-field error to the impedance-sphere series halves
+    (first order of the one-point rule; 0.255 at 2562 nodes in the oracle) and C_ext approaches
+    the series' value."""
+    from oracle import mie
+    eps = 2.25 + 1j
+    eta = 1 / np.sqrt(eps)
+    cext_m = mie.cross_sections(1.0, 1.0, None, impedance=eta)[0]
+    d = np.array([[0.0, 0.0, 1.0]])
+    e = np.array([[1.0, 0.0, 0.0]], dtype=np.complex128)
+    errs, dext = [], []
+    for sub in (5, 6):
+        V, F, D = fi.icosphere(sub)
+        g = fm.FMBEM(V, F, D, [1.0, eps], [1.0, 1.0], 1.0, boundary=fm.IMPEDANCE)
+        x, its, rr, st = g.solve(g.plane_wave_rhs(d, e), tol=1e-6)
+        assert st == 0
+        pos, nrm, w = g.node_geometry()
+        xm = mie.surface_unknowns(pos, nrm, 1.0, 1.0, None, impedance=eta)
+        errs.append(rel(x.cpu().numpy()[0, :, :3], xm[:, :3]))
+        dext.append(abs(np.asarray(g.cross_sections(x, d, e))[0][0] - cext_m) / cext_m)
+    print("surface-field error", errs, "C_ext error", dext)
+    assert errs[0] / errs[1] > 1.7 and errs[1] < 0.08, errs
+    assert dext[1] < dext[0] and dext[1] < 0.04, dext
