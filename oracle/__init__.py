@@ -73,6 +73,7 @@ def _load():
             lib.oracle_near_field_h.argtypes = [P, P, i64, P, P, P, P]
             lib.oracle_polygon_integrals.argtypes = [i32, P, P, P]
             lib.oracle_ibc_matvec.argtypes = [P, i64, P, P]
+            lib.oracle_interior_field.argtypes = [P, P, i64, P, P, P, P]
             lib.oracle_ibc_precond_blocks.argtypes = [P, P]
             lib.oracle_ibc_psi.argtypes = [P, i64, P, P]
             lib.oracle_ibc_zeta.argtypes = [P, P]
@@ -255,6 +256,20 @@ class Oracle:
         H = np.empty((len(pts), 3), dtype=np.complex128)
         self._lib.oracle_near_field_h(self._h, _ptr(x), len(pts), _ptr(pts), _ptr(d), _ptr(e), _ptr(H))
         return H
+
+    def interior_field(self, x, points, domain, magnetic=False):
+        """Fields inside the scatterers from the representation formula of each point's domain
+        (``domain`` [P] scatterer ids): E [P,3], and with magnetic=True (E, H), H = curl E /
+        (i k0 mu_j).  At a point outside its domain the same sum is the null-field integral."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        assert x.shape == (self.N, 6)
+        pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+        dom = np.ascontiguousarray(np.broadcast_to(np.asarray(domain, dtype=np.int32), (len(pts),)))
+        E = np.empty((len(pts), 3), dtype=np.complex128)
+        H = np.empty((len(pts), 3), dtype=np.complex128) if magnetic else None
+        self._lib.oracle_interior_field(self._h, _ptr(x), len(pts), _ptr(pts), _ptr(dom), _ptr(E),
+                                        _ptr(H) if H is not None else None)
+        return (E, H) if magnetic else E
 
     def cross_sections(self, x, d, e, n_theta=48, n_phi=96):
         """(C_ext, C_sca, C_abs) of one solution x for the incident plane wave (d, e), |e| = 1.

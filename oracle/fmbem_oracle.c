@@ -876,3 +876,64 @@ void oracle_ibc_zeta(const oracle_ctx *c, double *z_) {
     z[0] = 0;
     for (int j = 1; j <= c->J; ++j) z[j] = ibc_zeta(c, j);
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Fields inside the scatterers from the representation formula of domain j (Appendix A, the
+ * relation behind Eq. 2.5 at a point r inside Omega_j rather than on its boundary):
+ *   E_j(r) = sum_{b in j} w_b { [n_b (grad'g_j . v_b) - (n_b . grad'g_j) v_b - grad'g_j (n_b . v_b)]
+ *                               - g_j (n_b x curl E_j)(s_b) },
+ * n_b the scatterer's outward normal (outward from Omega_j), v_b = E_j(s_b) = T_j Phi_b (Eq. 2.6),
+ * n x curl E_j = gamma_j Psi_b (Eq. 2.7), g_j = g_j(s_b, r); no incident field inside.  The
+ * magnetic field H_j = curl E_j / (i k0 mu_j) is the curl of the same sum: (K n) x v + n x (K v)
+ * for the bracket (K the Hessian of g_j in the source point) and +grad'g_j x (gamma_j Psi) for the
+ * single layer.  At a point outside Omega_j the same sum is the extinction (null-field) integral,
+ * zero for exact data.  x one solution [N][6]; pts [np][3]; pdom [np] scatterer ids; E, H [np][3]
+ * (H may be NULL). */
+void oracle_interior_field(const oracle_ctx *c, const double *x_, int64_t np_, const double *pts, const int32_t *pdom,
+                           double *E_, double *H_) {
+    const cplx *x = (const cplx *)x_;
+    cplx *E = (cplx *)E_;
+    cplx *H = (cplx *)H_;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < np_; ++p) {
+        const double *r = pts + 3 * p;
+        const int j = pdom[p];
+        const cplx k = c->k[j], gam = c->gam[j];
+        cplx acc[3] = {0, 0, 0}, curl[3] = {0, 0, 0};
+        for (int64_t b = 0; b < c->N; ++b) {
+            if (c->dom[b] != j) continue;
+            double rv[3]; sub3(c->s + 3 * b, r, rv);
+            const double R = norm3(rv);
+            const double rh[3] = {rv[0] / R, rv[1] / R, rv[2] / R};
+            const double *nb = c->n + 3 * b;
+            const cplx g = cexp(I * k * R) / (4 * PI * R);
+            const cplx g1 = g * (I * k - 1.0 / R);
+            const cplx g2 = g * ((I * k - 1.0 / R) * (I * k - 1.0 / R) + 1.0 / (R * R));
+            cplx v[3], q[3];
+            apply_T(c, j, nb, x + 6 * b, v);
+            for (int i = 0; i < 3; ++i) q[i] = gam * x[6 * b + 3 + i];
+            cplx a[3] = {g1 * rh[0], g1 * rh[1], g1 * rh[2]};
+            cplx B[3];
+            bracket(nb, a, v, B);
+            for (int i = 0; i < 3; ++i) acc[i] += c->w[b] * (B[i] - g * q[i]);
+            if (H) {
+                const double rn = dot3(rh, nb);
+                const cplx rv_ = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+                cplx Kn[3], Kv[3];
+                for (int i = 0; i < 3; ++i) {
+                    Kn[i] = g2 * rh[i] * rn + g1 / R * (nb[i] - rh[i] * rn);
+                    Kv[i] = g2 * rh[i] * rv_ + g1 / R * (v[i] - rh[i] * rv_);
+                }
+                const cplx t[3] = {Kn[1] * v[2] - Kn[2] * v[1] + nb[1] * Kv[2] - nb[2] * Kv[1] + (a[1] * q[2] - a[2] * q[1]),
+                                   Kn[2] * v[0] - Kn[0] * v[2] + nb[2] * Kv[0] - nb[0] * Kv[2] + (a[2] * q[0] - a[0] * q[2]),
+                                   Kn[0] * v[1] - Kn[1] * v[0] + nb[0] * Kv[1] - nb[1] * Kv[0] + (a[0] * q[1] - a[1] * q[0])};
+                for (int i = 0; i < 3; ++i) curl[i] += c->w[b] * t[i];
+            }
+        }
+        for (int i = 0; i < 3; ++i) E[3 * p + i] = acc[i];
+        if (H) {
+            const cplx iwm = I * c->k0 * c->mu[j];
+            for (int i = 0; i < 3; ++i) H[3 * p + i] = curl[i] / iwm;
+        }
+    }
+}
