@@ -287,6 +287,24 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
                               const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, fmbem_c64 *H_host,
                               void *stream);
 
+/* Fields inside the scatterers: at each point r_p, inside scatterer domain[p] = j, the
+ * representation formula of domain j (Appendix A; Eq. 2.5 holds it on the boundary),
+ *   E_j(r) = sum over the nodes b of scatterer j of
+ *            w_b { [n_b (grad'g_j . v_b) - (n_b . grad'g_j) v_b - grad'g_j (n_b . v_b)]
+ *                  - g_j(s_b, r) gamma_j Psi_b },   v_b = T_j Phi_b (Eq. 2.6),
+ * with n_b the scatterer's outward normal and gamma_j Psi = n x curl E_j (Eq. 2.7); no incident
+ * field inside.  H_j = curl E_j / (i k0 mu_j), from the curl of the same sum.  Direct FP64
+ * summation over the scatterer's nodes (one thread per point), for field maps of moderate size.
+ *   x_dev    solutions [n_rhs][N][6] (device, user order).
+ *   pts      host [n_pts][3]; domain host [n_pts] scatterer ids 1..n_scatterers (a point outside
+ *            its domain gets the null-field integral, zero for exact data).
+ *   E_host   host [n_rhs][n_pts][3] complex128, written; H_host likewise, or NULL.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (counts, NULL pointers, a domain id out of range, or a
+ * handle created with the impedance boundary, which does not model the interiors),
+ * FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
+fmbem_status fmbem_interior_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
+                                  const int32_t *domain, fmbem_c64 *E_host, fmbem_c64 *H_host, void *stream);
+
 /* The exterior fields as linear functionals of the solution, for adjoint gradients of
  * quantities built from them (the optical force of a Maxwell-stress surface): out[f] holds the
  * coefficients of x -> sum_p ( cE[f][p] . E_sca(r_p) + cH[f][p] . H_sca(r_p) ) with E_sca, H_sca

@@ -83,6 +83,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_absorption": (i32, [P, P, i64, P, P]),
         "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P, P]),
         "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
+        "fmbem_interior_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
         "fmbem_near_field_functional": (i32, [P, i64, i64, P, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
@@ -265,6 +266,22 @@ def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None, magnetic=F
     return (E, H) if magnetic else E
 
 
+def fmbem_interior_field(h, x, points, domain, stream=None, magnetic=False):
+    """Field E [n_rhs, n_pts, 3] complex128 (host) inside the scatterers, at points whose
+    scatterer ids are ``domain`` [n_pts] (or one id for all); with magnetic=True returns (E, H),
+    H = curl E / (i k0 mu_j)."""
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    n = x.shape[0]
+    pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    dom = np.ascontiguousarray(np.broadcast_to(np.asarray(domain, dtype=np.int32), (len(pts),)))
+    E = np.empty((n, len(pts), 3), dtype=np.complex128)
+    H = np.empty((n, len(pts), 3), dtype=np.complex128) if magnetic else None
+    _check(h, load_library().fmbem_interior_field(h, ctypes.c_void_p(x.data_ptr()), n, len(pts), _ptr(pts), _ptr(dom),
+                                                  _ptr(E), _ptr(H) if H is not None else None, _stream(stream)))
+    return (E, H) if magnetic else E
+
+
 def fmbem_far_field_functional(h, rhat, coef, stream=None):
     """Coefficients [n, N, 6] complex128 (CUDA) of x -> coef[r] . F(rhat[r]) per right-hand side."""
     import torch
@@ -406,6 +423,9 @@ class FMBEM:
     def near_field(self, x, points, dirs=None, pols=None, stream=None, magnetic=False):
         return fmbem_near_field(self.h, x, points, dirs, pols, stream, magnetic)
 
+    def interior_field(self, x, points, domain, stream=None, magnetic=False):
+        return fmbem_interior_field(self.h, x, points, domain, stream, magnetic)
+
     def _vacuum_background(self):
         if self.eps0 != 1 or self.mu0 != 1:
             raise ValueError("the optical force here assumes a vacuum background (eps_0 = mu_0 = 1)")
@@ -456,6 +476,27 @@ class FMBEM:
             tn = 0.5 * np.real(e * en[:, None] + hm * hn[:, None] - 0.5 * u[:, None] * nq)
             out[r] = np.sum(wq[:, None] * tn, axis=0)
         return out
+
+    def dscs(self, x, rhat, pols=None, stream=None):
+        """Differential scattering cross section dC_sca/dOmega = |F(rhat)|^2 / |e|^2 [n_rhs, n_dir]
+        of solutions x of plane waves with polarisations ``pols`` [n_rhs, 3] (|e| = 1 when None), the
+        far-field amplitude F computed on the device (Appendix A in the far zone)."""
+        F = self.far_field(x, rhat, stream)
+        s = np.sum(np.abs(F) ** 2, axis=-1)
+        if pols is not None:
+            s = s / np.sum(np.abs(np.atleast_2d(pols)) ** 2, axis=-1)[:, None]
+        return s
+
+    def rcs(self, x, rhat, pols, receive=None, stream=None):
+        """Radar cross section 4 pi |p_r* . F(rhat)|^2 / |e|^2 [n_rhs, n_dir] of solutions x of the
+        plane waves with polarisations ``pols`` [n_rhs, 3]; ``receive`` [n_rhs, n_dir, 3] are the
+        receiving polarisations p_r (unit; None: all polarisations, 4 pi |F|^2 / |e|^2).  The
+        monostatic RCS takes rhat = -d and, for the vertical-vertical case, p_r = theta-hat."""
+        F = self.far_field(x, rhat, stream)
+        e2 = np.sum(np.abs(np.atleast_2d(pols)) ** 2, axis=-1)[:, None]
+        if receive is None:
+            return 4 * np.pi * np.sum(np.abs(F) ** 2, axis=-1) / e2
+        return 4 * np.pi * np.abs(np.sum(np.conj(np.asarray(receive)) * F, axis=-1)) ** 2 / e2
 
     def far_field_functional(self, rhat, coef, stream=None):
         return fmbem_far_field_functional(self.h, rhat, coef, stream)

@@ -327,6 +327,19 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
     });
 }
 
+fmbem_status fmbem_interior_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
+                                  const int32_t *domain, fmbem_c64 *E_host, fmbem_c64 *H_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_pts < 1 || !x_dev || !pts || !domain || !E_host || n_rhs > 65535) {
+        h->err = "invalid argument (n_rhs in 1..65535, n_pts >= 1, non-NULL x, pts, domain and E)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_interior_field(h, (const c64 *)x_dev, n_rhs, n_pts, pts, domain, (c64 *)E_host, (c64 *)H_host,
+                           (cudaStream_t)stream);
+    });
+}
+
 fmbem_status fmbem_far_field_functional(fmbem *h, int64_t n_rhs, const double *rhat, const fmbem_c64 *coef,
                                         void *out_dev, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;

@@ -274,6 +274,8 @@ void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int preci
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_near_field_functional(fmbem *h, int64_t nf, int64_t n_pts, const double *pts_host, const c64 *cE_host,
                                const c64 *cH_host, c64 *out, cudaStream_t s);
+void run_interior_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host,
+                        const int32_t *dom_host, c64 *E_host, c64 *H_host, cudaStream_t s);
 void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host, const double *dir_host,
                     const c64 *pol_host, c64 *E_host, c64 *H_host, cudaStream_t s);
 void run_far_field_functional(fmbem *h, int64_t nr, const double *rhat_host, const c64 *coef_host, c64 *out,

@@ -8,6 +8,9 @@
 // so that the scattered field behaves as E_sca ~ exp(i k0 r)/r F(u) in direction u.
 // Absorption: the inward flux of the time-averaged Poynting vector through the surface, Eq. (4.2),
 // with n x curl E = Psi, reduces to C_abs = -(1/k0) sum_b w_b Im(Phi_b . conj(Psi_b)).
+#include <string>
+#include <vector>
+
 #include "fmbem_internal.cuh"
 
 namespace {
@@ -175,6 +178,90 @@ __global__ void __launch_bounds__(OB_NT) k_near_field(int64_t N, const double *p
     }
 }
 
+// Fields inside the scatterers (see fmbem_interior_field): the representation formula of the
+// point's own scatterer domain j, summed over that scatterer's nodes,
+//   E = sum_b w_b { [n (a.v) - (n.a) v - a (n.v)] - g_j q },   v = T_j Phi_b (Eq. 2.6),
+//   q = gamma_j Psi_b (Eq. 2.7), n the scatterer's outward normal, a = grad_s g_j;
+// curl E sums (K n) x v + n x (K v) + a x q (K the Hessian of g_j in the source point), and
+// H = curl E / (i k0 mu_j).  Thread and staging layout as k_near_field: the nodes are staged with
+// v and q already formed, and each thread skips the nodes of the other scatterers.
+// dcon[4 d .. 4 d + 3] = (k_d, t_d, gamma_d, i k0 mu_d).
+template <bool WITH_H>
+__global__ void __launch_bounds__(OB_NT) k_interior_field(int64_t N, const double *pos, const double *nrm,
+                                                        const double *w, const int32_t *ndom, const c64 *x,
+                                                        int64_t n_pts, const double *pts, const int32_t *pdom,
+                                                        const c64 *dcon, c64 *E, c64 *H) {
+    __shared__ double sp[OB_NS][3], sn[OB_NS][3], sw[OB_NS];
+    __shared__ c64 sx[OB_NS][6];
+    __shared__ int sd[OB_NS];
+    const int64_t pt = blockIdx.x * (int64_t)OB_NT + threadIdx.x, r = blockIdx.y;
+    const bool valid = pt < n_pts;
+    const double t[3] = {valid ? pts[3 * pt] : 0.0, valid ? pts[3 * pt + 1] : 0.0, valid ? pts[3 * pt + 2] : 0.0};
+    const int j = valid ? pdom[pt] : -1;
+    const c64 k = valid ? dcon[4 * j] : c64{0, 0};
+    const c64 ik = {-k.im, k.re};
+    c64 acc[3] = {{0, 0}, {0, 0}, {0, 0}}, cur[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t b0 = 0; b0 < N; b0 += OB_NS) {
+        const int nb = (int)min((int64_t)OB_NS, N - b0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+            const int64_t b = b0 + e;
+            const int d = ndom[b];
+            const double n[3] = {nrm[3 * b], nrm[3 * b + 1], nrm[3 * b + 2]};
+            for (int q = 0; q < 3; ++q) { sp[e][q] = pos[3 * b + q]; sn[e][q] = n[q]; }
+            sw[e] = w[b];
+            sd[e] = d;
+            const c64 *xb = x + (r * N + b) * 6;
+            const c64 td = dcon[4 * d + 1], gd = dcon[4 * d + 2];
+            const c64 tn = td * (n[0] * xb[0] + n[1] * xb[1] + n[2] * xb[2]);
+            for (int q = 0; q < 3; ++q) {
+                sx[e][q] = xb[q] + n[q] * tn;
+                sx[e][3 + q] = gd * xb[3 + q];
+            }
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int e = 0; e < nb; ++e) {
+            if (sd[e] != j) continue;
+            const double rv[3] = {sp[e][0] - t[0], sp[e][1] - t[1], sp[e][2] - t[2]};
+            const double R = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+            const c64 g = cexpd(ik * R) * (1.0 / (4.0 * FMBEM_PI * R));
+            const c64 g1 = g * (ik - c64{1.0 / R, 0});  // dg/dR
+            const c64 c = g1 * (1.0 / R);                // grad_s g = c (s - r)
+            const double *n = sn[e];
+            const c64 *v = sx[e], *qv = sx[e] + 3;
+            const c64 rP = rv[0] * v[0] + rv[1] * v[1] + rv[2] * v[2];
+            const c64 nP = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+            const double nr = n[0] * rv[0] + n[1] * rv[1] + n[2] * rv[2];
+            for (int q = 0; q < 3; ++q) {
+                const c64 br = c * (n[q] * rP - nr * v[q] - rv[q] * nP);
+                acc[q] += sw[e] * (br - g * qv[q]);
+            }
+            if (WITH_H) {
+                const double iR = 1.0 / R, rh[3] = {rv[0] * iR, rv[1] * iR, rv[2] * iR};
+                const c64 q1 = ik - c64{iR, 0};
+                const c64 g2 = g * (q1 * q1 + c64{iR * iR, 0});
+                const double rn = rh[0] * n[0] + rh[1] * n[1] + rh[2] * n[2];
+                const c64 rhP = rP * iR;
+                c64 Kn[3], KP[3], av[3];
+                for (int q = 0; q < 3; ++q) {
+                    Kn[q] = g2 * (rh[q] * rn) + c * (n[q] - rh[q] * rn);
+                    KP[q] = g2 * rhP * rh[q] + c * (v[q] - rhP * rh[q]);
+                    av[q] = g1 * rh[q];
+                }
+                cur[0] += sw[e] * (Kn[1] * v[2] - Kn[2] * v[1] + n[1] * KP[2] - n[2] * KP[1] + (av[1] * qv[2] - av[2] * qv[1]));
+                cur[1] += sw[e] * (Kn[2] * v[0] - Kn[0] * v[2] + n[2] * KP[0] - n[0] * KP[2] + (av[2] * qv[0] - av[0] * qv[2]));
+                cur[2] += sw[e] * (Kn[0] * v[1] - Kn[1] * v[0] + n[0] * KP[1] - n[1] * KP[0] + (av[0] * qv[1] - av[1] * qv[0]));
+            }
+        }
+    }
+    if (valid) {
+        for (int q = 0; q < 3; ++q) E[(r * n_pts + pt) * 3 + q] = acc[q];
+        if (WITH_H)
+            for (int q = 0; q < 3; ++q) H[(r * n_pts + pt) * 3 + q] = cdiv(cur[q], dcon[4 * j + 3]);
+    }
+}
+
 // Transposed near-field map (for adjoint gradients of quantities built from exterior fields):
 // out[f][b] = sum_p ( cE[f][p] . dE(r_p)/dx_b + cH[f][p] . dH(r_p)/dx_b ), with E, H as in
 // k_near_field (no incident part: it does not depend on x).  For c = cE[f][p]:
@@ -315,6 +402,53 @@ void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const dou
             k_near_field<false><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, x, n_pts, dp, h->k[0], iwmu, dd,
                                                        dpol, dE, nullptr);
         CKL("k_near_field");
+        CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
+        if (dH) CK(cudaMemcpyAsync(H_host, dH, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+void run_interior_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host,
+                        const int32_t *dom_host, c64 *E_host, c64 *H_host, cudaStream_t s) {
+    if (h->ibc) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "the impedance boundary does not model the interiors"};
+    for (int64_t p = 0; p < n_pts; ++p)
+        if (dom_host[p] < 1 || dom_host[p] > h->J)
+            throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "point " + std::to_string(p) + ": domain outside 1..n_scatterers"};
+    std::vector<c64> dc(4 * (h->J + 1));
+    for (int d = 0; d <= h->J; ++d) {
+        dc[4 * d] = h->k[d];
+        dc[4 * d + 1] = d == 0 ? c64{0, 0} : cdiv(h->eps[0] - h->eps[d], h->eps[d]);  // T_d = I + t_d n n^T
+        dc[4 * d + 2] = h->gam[d];
+        dc[4 * d + 3] = c64{0, h->k0} * h->mu[d];  // i omega mu_d with omega = k0 (c = 1)
+    }
+    double *dp = (double *)dev_alloc(h, sizeof(double) * 3 * n_pts);
+    int32_t *dd = (int32_t *)dev_alloc(h, sizeof(int32_t) * n_pts);
+    c64 *dcon = (c64 *)dev_alloc(h, sizeof(c64) * dc.size());
+    c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr);
+    c64 *dH = H_host ? (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr) : nullptr;
+    auto cleanup = [&] {
+        dev_free(h, dp);
+        dev_free(h, dd);
+        dev_free(h, dcon);
+        dev_free(h, dE);
+        if (dH) dev_free(h, dH);
+    };
+    try {
+        CK(cudaMemcpyAsync(dp, pts_host, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dd, dom_host, sizeof(int32_t) * n_pts, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dcon, dc.data(), sizeof(c64) * dc.size(), cudaMemcpyHostToDevice, s));
+        const dim3 grid((unsigned)((n_pts + OB_NT - 1) / OB_NT), (unsigned)nr);
+        if (dH)
+            k_interior_field<true><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, h->udom, x, n_pts, dp, dd, dcon,
+                                                          dE, dH);
+        else
+            k_interior_field<false><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, h->udom, x, n_pts, dp, dd,
+                                                           dcon, dE, nullptr);
+        CKL("k_interior_field");
         CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
         if (dH) CK(cudaMemcpyAsync(H_host, dH, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

@@ -699,3 +699,81 @@ def test_ibc_sphere_converges_to_mie_on_gpu():
     print("surface-field error", errs, "C_ext error", dext)
     assert errs[0] / errs[1] > 1.7 and errs[1] < 0.08, errs
     assert dext[1] < dext[0] and dext[1] < 0.04, dext
+
+
+# ------------------------------------------------------------------ fields inside the scatterers
+def test_interior_field_matches_oracle(sphere_s4):
+    """E and H inside the sphere (representation formula of the scatterer domain) from the GPU
+    against the oracle's, for two random right-hand sides; then two scatterers with mu != 1."""
+    o, g = sphere_s4
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(2, o.N, 6)) + 1j * rng.normal(size=(2, o.N, 6))
+    P = rng.normal(size=(50, 3))
+    P *= (0.8 * rng.random((50, 1))) / np.linalg.norm(P, axis=1, keepdims=True)
+    E, H = g.interior_field(to_dev(x), P, 1, magnetic=True)
+    for r in range(2):
+        Eo, Ho = o.interior_field(x[r], P, 1, magnetic=True)
+        assert rel(E[r], Eo) < 1e-11 and rel(H[r], Ho) < 1e-11
+    m1 = fi.icosphere(3, 0.5, (-0.8, 0.0, 0.0), domain=1)
+    m2 = fi.icosphere(3, 0.4, (0.7, 0.1, 0.0), domain=2)
+    o2, g2 = case(fi.merge_meshes(m1, m2), [1.0, 3.0 + 0.2j, -2.0 + 0.5j], [1.0, 1.7, 1.0], 1.2)
+    x2 = rng.normal(size=(1, o2.N, 6)) + 1j * rng.normal(size=(1, o2.N, 6))
+    Q = np.concatenate([np.array([-0.8, 0, 0]) + 0.3 * rng.uniform(-1, 1, (20, 3)),
+                        np.array([0.7, 0.1, 0]) + 0.2 * rng.uniform(-1, 1, (20, 3))])
+    dom = np.repeat([1, 2], 20).astype(np.int32)
+    E2, H2 = g2.interior_field(to_dev(x2), Q, dom, magnetic=True)
+    Eo2, Ho2 = o2.interior_field(x2[0], Q, dom, magnetic=True)
+    assert rel(E2[0], Eo2) < 1e-11 and rel(H2[0], Ho2) < 1e-11
+    gi = fm.FMBEM(*fi.icosphere(2), [1.0, 1 + 1e4j], [1.0, 1.0], 1.0, boundary=fm.IMPEDANCE)
+    with pytest.raises(fm.FMBEMError):
+        gi.interior_field(to_dev(np.zeros((1, gi.N, 6))), P[:2], 1)
+
+
+def test_interior_field_of_a_solution_converges_to_mie():
+    """Dielectric sphere (eps = 2.25, k0 a = 1) solved on the GPU at 10242 nodes: the field
+    inside is within the one-point rule's first-order error of the Mie internal field (2.2 % at
+    2562 nodes in the oracle)."""
+    from oracle import mie
+    rng = np.random.default_rng(22)
+    P = rng.normal(size=(40, 3))
+    P *= (0.6 * rng.random((40, 1))) / np.linalg.norm(P, axis=1, keepdims=True)
+    Em, Cm = mie.fields(P, 1.0, 1.0, 2.25, "inside")
+    V, F, D = fi.icosphere(5)
+    g = fm.FMBEM(V, F, D, [1.0, 2.25], [1.0, 1.0], 1.0)
+    x, its, rr, st = g.solve(g.plane_wave_rhs(np.array([[0, 0, 1.0]]), np.array([[1.0, 0, 0]], dtype=complex)), tol=1e-8)
+    assert st == 0
+    E, H = g.interior_field(x, P, 1, magnetic=True)
+    eE, eH = rel(E[0], Em), rel(H[0], Cm / 1j)
+    print("interior field error at 10242 nodes", eE, eH)
+    assert eE < 0.015 and eH < 0.015
+
+
+def test_dscs_and_rcs_match_mie():
+    """DSCS |F|^2 and bistatic RCS from the device far field of the exact Mie surface data of the
+    2562-node sphere, against the Mie amplitude functions (Bohren & Huffman 4.74: |S1|^2 sin^2 phi
+    + |S2|^2 cos^2 phi over k^2 for x-polarised incidence along z), and the co-polarised monostatic
+    RCS 4 pi |S1(180)|^2 / k^2."""
+    from oracle import mie
+    V, F, D = fi.icosphere(4)
+    g = fm.FMBEM(V, F, D, [1.0, 2.25], [1.0, 1.0], 1.0)
+    pos, nrm, w = g.node_geometry()
+    xm = mie.surface_unknowns(pos, nrm, 1.0, 1.0, 2.25)
+    th = np.linspace(0.1, np.pi - 0.1, 9)
+    ph = 0.7
+    rh = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+    an, bn, _, _ = mie.coefficients(2.25, 1.0)
+    n = np.arange(1, len(an) + 1)
+    pi_n, tau_n = mie._angular(len(an), np.cos(th))
+    f = ((2 * n + 1) / (n * (n + 1)))[:, None]
+    S1 = np.sum(f * (an[:, None] * pi_n + bn[:, None] * tau_n), 0)
+    S2 = np.sum(f * (an[:, None] * tau_n + bn[:, None] * pi_n), 0)
+    dscs_m = np.abs(S1) ** 2 * np.sin(ph) ** 2 + np.abs(S2) ** 2 * np.cos(ph) ** 2
+    pol = np.array([[1.0, 0, 0]], dtype=complex)
+    d = g.dscs(to_dev(xm[None]), rh, pol)[0]
+    assert rel(d, dscs_m) < 0.01
+    np.testing.assert_allclose(g.rcs(to_dev(xm[None]), rh, pol)[0], 4 * np.pi * d, rtol=1e-12)
+    back = np.array([[0.0, 0.0, -1.0]])
+    mono = g.rcs(to_dev(xm[None]), back, pol, receive=pol[:, None, :])[0, 0]
+    pb, tb = mie._angular(len(an), np.array([-1.0]))
+    s1b = np.sum(f * (an[:, None] * pb + bn[:, None] * tb))                        # S1(180 deg)
+    assert abs(mono - 4 * np.pi * abs(s1b) ** 2) < 0.01 * mono
