@@ -287,6 +287,27 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
                               const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, fmbem_c64 *H_host,
                               void *stream);
 
+/* Gradient of a far-field functional with respect to the mesh vertex positions (vertex nodes,
+ * penetrable scatterers), by the adjoint method of the discrete system of Eq. (2.9).  For each
+ * right-hand side r, x_r solves A(V) x = b_r(V) with b_r the plane wave (dir[r], pol[r]) of
+ * fmbem_plane_wave_rhs, f_r = L_r(V)^T x_r is the functional coef[r] . F(rhat[r]) of
+ * fmbem_far_field_functional, and lambda_r solves A^T lambda = L_r (fmbem_adjoint_solve); then
+ *   out[r][v][c] = d/dV_vc [ L_r^T x_r + lambda_r^T b_r - lambda_r^T A x_r ]  (x, lambda fixed)
+ *               = d f_r / dV_vc.
+ * The vertex positions enter through the node positions, weights and normals of each vertex's
+ * 1-ring and through their self blocks (Appendix B); the pair blocks of Eq. (2.12) are summed
+ * directly (O(N^2) FP64 pair evaluations), all derivatives are FP64 central differences with
+ * steps of 1e-6 (the mean edge length for positions).  The extinction of the plane wave (d, e)
+ * is Im f with rhat = d and coef = (4 pi / k0) conj(e).
+ *   x_dev, lam_dev  device [n_rhs][N][6] complex128 (user order).
+ *   dir, rhat       host [n_rhs][3]; pol, coef host [n_rhs][3] complex128.
+ *   out_host        host [n_rhs][N][3] complex128 (N = number of vertices), written.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (counts, NULL pointers, centroid nodes, impedance boundary),
+ * FMBEM_ERR_INVALID_MESH (a vertex with more than 31 neighbours), FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
+fmbem_status fmbem_shape_gradient(fmbem *h, const void *x_dev, const void *lam_dev, int64_t n_rhs, const double *dir,
+                                  const fmbem_c64 *pol, const double *rhat, const fmbem_c64 *coef,
+                                  fmbem_c64 *out_host, void *stream);
+
 /* Fields inside the scatterers: at each point r_p, inside scatterer domain[p] = j, the
  * representation formula of domain j (Appendix A; Eq. 2.5 holds it on the boundary),
  *   E_j(r) = sum over the nodes b of scatterer j of

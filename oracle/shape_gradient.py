@@ -44,8 +44,9 @@ def dense_matrix(o):
     return o.matvec(np.eye(n, dtype=np.complex128).reshape(n, o.N, 6)).reshape(n, n).T
 
 
-def extinction_vertex_gradient(V, F, D, eps, mu, k0, d, e, h=1e-6):
-    """(C_ext, dC_ext/dV [nv, 3]) for the plane wave (d, e) by the dense adjoint formula above."""
+def extinction_vertex_gradient(V, F, D, eps, mu, k0, d, e, h=1e-6, return_state=False):
+    """(C_ext, dC_ext/dV [nv, 3]) for the plane wave (d, e) by the dense adjoint formula above;
+    with return_state also the dense solution x and adjoint lambda ([N, 6] each)."""
     V = np.asarray(V, dtype=np.float64)
     d = np.asarray(d, dtype=np.float64)
     e = np.asarray(e, dtype=np.complex128)
@@ -69,6 +70,8 @@ def extinction_vertex_gradient(V, F, D, eps, mu, k0, d, e, h=1e-6):
             Vp[v, c] += h
             Vm[v, c] -= h
             grad[v, c] = np.imag((G(Vp) - G(Vm)) / (2 * h))
+    if return_state:
+        return cext, grad, x, lam
     return cext, grad
 
 

@@ -84,6 +84,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P, P]),
         "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
         "fmbem_interior_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
+        "fmbem_shape_gradient": (i32, [P, P, P, i64, P, P, P, P, P, P]),
         "fmbem_near_field_functional": (i32, [P, i64, i64, P, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
@@ -280,6 +281,22 @@ def fmbem_interior_field(h, x, points, domain, stream=None, magnetic=False):
     _check(h, load_library().fmbem_interior_field(h, ctypes.c_void_p(x.data_ptr()), n, len(pts), _ptr(pts), _ptr(dom),
                                                   _ptr(E), _ptr(H) if H is not None else None, _stream(stream)))
     return (E, H) if magnetic else E
+
+
+def fmbem_shape_gradient(h, x, lam, dirs, pols, rhat, coef, stream=None):
+    """d/dV of the far-field functionals coef[r] . F(rhat[r]) of the solutions x (plane waves
+    (dirs, pols)) given their adjoints lam: complex128 [n_rhs, N_vertices, 3] (host)."""
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    lam = _dev(lam, N, "lam")
+    n = x.shape[0]
+    as_d = lambda a: np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (n, 3)))
+    as_c = lambda a: np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.complex128), (n, 3)))
+    d, p, rh, cf = as_d(dirs), as_c(pols), as_d(rhat), as_c(coef)
+    out = np.empty((n, N, 3), dtype=np.complex128)
+    _check(h, load_library().fmbem_shape_gradient(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(lam.data_ptr()), n,
+                                                  _ptr(d), _ptr(p), _ptr(rh), _ptr(cf), _ptr(out), _stream(stream)))
+    return out
 
 
 def fmbem_far_field_functional(h, rhat, coef, stream=None):
@@ -497,6 +514,9 @@ class FMBEM:
         if receive is None:
             return 4 * np.pi * np.sum(np.abs(F) ** 2, axis=-1) / e2
         return 4 * np.pi * np.abs(np.sum(np.conj(np.asarray(receive)) * F, axis=-1)) ** 2 / e2
+
+    def shape_gradient(self, x, lam, dirs, pols, rhat, coef, stream=None):
+        return fmbem_shape_gradient(self.h, x, lam, dirs, pols, rhat, coef, stream)
 
     def far_field_functional(self, rhat, coef, stream=None):
         return fmbem_far_field_functional(self.h, rhat, coef, stream)

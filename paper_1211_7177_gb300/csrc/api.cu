@@ -327,6 +327,20 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
     });
 }
 
+fmbem_status fmbem_shape_gradient(fmbem *h, const void *x_dev, const void *lam_dev, int64_t n_rhs, const double *dir,
+                                  const fmbem_c64 *pol, const double *rhat, const fmbem_c64 *coef,
+                                  fmbem_c64 *out_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_rhs > 65535 || !x_dev || !lam_dev || !dir || !pol || !rhat || !coef || !out_host) {
+        h->err = "invalid argument (n_rhs in 1..65535, non-NULL x, lambda, dir, pol, rhat, coef and out)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_shape_gradient(h, (const c64 *)x_dev, (const c64 *)lam_dev, n_rhs, dir, (const c64 *)pol, rhat,
+                           (const c64 *)coef, (c64 *)out_host, (cudaStream_t)stream);
+    });
+}
+
 fmbem_status fmbem_interior_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
                                   const int32_t *domain, fmbem_c64 *E_host, fmbem_c64 *H_host, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;

@@ -95,6 +95,7 @@ struct fmbem {
 
     // host copies of geometry (user order)
     std::vector<double> h_pos, h_nrm, h_w;
+    std::vector<int32_t> h_F, h_vt_start, h_vt_tri;  // triangles and vertex -> triangle lists (vertex nodes)
 
     // device geometry in user order (from the node set-up)
     double *upos = nullptr, *unrm = nullptr, *uw = nullptr;  // [N][3], [N][3], [N]
@@ -274,6 +275,11 @@ void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int preci
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_near_field_functional(fmbem *h, int64_t nf, int64_t n_pts, const double *pts_host, const c64 *cE_host,
                                const c64 *cH_host, c64 *out, cudaStream_t s);
+void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, const double *dir_host,
+                        const c64 *pol_host, const double *rhat_host, const c64 *coef_host, c64 *out_host,
+                        cudaStream_t s);
+void run_vertex_shape_grad(fmbem *h, int64_t nr, const c64 *x, const c64 *lam, const c64 *sens, double hv, c64 *out,
+                           cudaStream_t s);
 void run_interior_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host,
                         const int32_t *dom_host, c64 *E_host, c64 *H_host, cudaStream_t s);
 void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host, const double *dir_host,

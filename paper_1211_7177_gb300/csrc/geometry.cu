@@ -134,29 +134,43 @@ __device__ void domain_consts(const c64 *kd, const c64 *td, const c64 *gd, int j
 }
 __device__ c64 zeta_of(const c64 *zd, int j) { return zd ? zd[j] : c64{0, 0}; }
 
-// vertex nodes: weight 1/3 of incident areas, area-weighted normal, dual-cell patch
-__global__ void k_vertex_nodes(int64_t nv, const double *V, const int32_t *F, const int32_t *vt_start,
-                               const int32_t *vt_tri, const int32_t *vdom, const c64 *kd, const c64 *td, const c64 *gd,
-                               const c64 *zd, double *pos, double *nrm, double *w, c64 *M, c64 *LU, int8_t *piv) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    const double *O = V + 3 * v;
-    double nsum[3] = {0, 0, 0}, wsum = 0;
+// vertex positions read as stored, or with one vertex displaced (the shape gradient)
+struct PlainPos {
+    const double *V;
+    __device__ void operator()(int64_t i, double *o) const { o[0] = V[3 * i]; o[1] = V[3 * i + 1]; o[2] = V[3 * i + 2]; }
+};
+struct MovedPos {
+    const double *V;
+    int64_t moved;
+    double d[3];
+    __device__ void operator()(int64_t i, double *o) const {
+        for (int q = 0; q < 3; ++q) o[q] = V[3 * i + q] + (i == moved ? d[q] : 0.0);
+    }
+};
+
+// vertex node v: weight 1/3 of incident areas, area-weighted normal, dual-cell patch integrals
+template <class Pos>
+__device__ void vertex_geometry(int64_t v, const Pos &P, const int32_t *F, const int32_t *vt_start,
+                                const int32_t *vt_tri, double *O, double *n, double &wsum, PatchSums &ps) {
+    P(v, O);
+    double nsum[3] = {0, 0, 0};
+    wsum = 0;
     for (int q = vt_start[v]; q < vt_start[v + 1]; ++q) {
         int t = vt_tri[q];
-        const double *A = V + 3 * F[3 * t], *B = V + 3 * F[3 * t + 1], *C = V + 3 * F[3 * t + 2];
+        double A[3], B[3], C[3];
+        P(F[3 * t], A); P(F[3 * t + 1], B); P(F[3 * t + 2], C);
         double ab[3], ac[3], cr[3];
         sub3(B, A, ab); sub3(C, A, ac); cross3(ab, ac, cr);
         for (int i = 0; i < 3; ++i) nsum[i] += cr[i];
         wsum += sqrt(dot3(cr, cr)) / 6.0;
     }
     double ln = sqrt(dot3(nsum, nsum));
-    double n[3] = {nsum[0] / ln, nsum[1] / ln, nsum[2] / ln};
-    PatchSums ps;
+    for (int i = 0; i < 3; ++i) n[i] = nsum[i] / ln;
     for (int q = vt_start[v]; q < vt_start[v + 1]; ++q) {
         int t = vt_tri[q];
         int c0 = F[3 * t] == v ? 0 : (F[3 * t + 1] == v ? 1 : 2);
-        const double *A = V + 3 * F[3 * t + c0], *B = V + 3 * F[3 * t + (c0 + 1) % 3], *C = V + 3 * F[3 * t + (c0 + 2) % 3];
+        double A[3], B[3], C[3];
+        P(F[3 * t + c0], A); P(F[3 * t + (c0 + 1) % 3], B); P(F[3 * t + (c0 + 2) % 3], C);
         double mab[3], g[3], mac[3];
         for (int i = 0; i < 3; ++i) {
             mab[i] = 0.5 * (A[i] + B[i]);
@@ -168,11 +182,82 @@ __global__ void k_vertex_nodes(int64_t nv, const double *V, const int32_t *F, co
         patch_edge(pa, pg, n, ps);
         patch_edge(pg, pc, n, ps);
     }
+}
+
+__global__ void k_vertex_nodes(int64_t nv, const double *V, const int32_t *F, const int32_t *vt_start,
+                               const int32_t *vt_tri, const int32_t *vdom, const c64 *kd, const c64 *td, const c64 *gd,
+                               const c64 *zd, double *pos, double *nrm, double *w, c64 *M, c64 *LU, int8_t *piv) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double O[3], n[3], wsum;
+    PatchSums ps;
+    vertex_geometry(v, PlainPos{V}, F, vt_start, vt_tri, O, n, wsum, ps);
     for (int i = 0; i < 3; ++i) { pos[3 * v + i] = O[i]; nrm[3 * v + i] = n[i]; }
     w[v] = wsum;
     c64 kb, kj, tj, gj;
     domain_consts(kd, td, gd, vdom[v], kb, kj, tj, gj);
     self_block(ps, n, kb, kj, tj, gj, zd != nullptr, zeta_of(zd, vdom[v]), M + 36 * v, LU + 36 * v, piv + 6 * v);
+}
+
+// Shape gradient, local part (vertex nodes): for vertex v and coordinate c, the central
+// difference (step hv) of everything in G = L^T x + lambda^T b - lambda^T A x that depends on
+// vertex v through the node data of the nodes u of its 1-ring S_v (v and the other vertices of
+// the triangles at v): the node data themselves enter through the sensitivities sens[r][u] =
+// dG/d(s_u, w_u, n_u) (pair terms, functional and right-hand side, from k_node_sens), and the self
+// blocks M_u (Appendix B) directly: out[r][v][c] = sum_u [sens_u . d(s,w,n)_u - lambda_u^T dM_u x_u].
+// One thread per vertex; err is set when a 1-ring has more than SG_RING nodes.
+constexpr int SG_RING = 32;
+__global__ void k_vertex_shape_grad(int64_t nv, int64_t nr, const double *V, const int32_t *F, const int32_t *vt_start,
+                                    const int32_t *vt_tri, const int32_t *vdom, const c64 *kd, const c64 *td,
+                                    const c64 *gd, const c64 *x, const c64 *lam, const c64 *sens, double hv, c64 *out,
+                                    int *err) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    int64_t ring[SG_RING];
+    int nring = 0;
+    for (int q = vt_start[v]; q < vt_start[v + 1]; ++q)
+        for (int a = 0; a < 3; ++a) {
+            const int64_t u = F[3 * vt_tri[q] + a];
+            bool seen = false;
+            for (int i = 0; i < nring; ++i) seen |= ring[i] == u;
+            if (seen) continue;
+            if (nring == SG_RING) { atomicExch(err, 1); return; }
+            ring[nring++] = u;
+        }
+    for (int c = 0; c < 3; ++c) {
+        for (int64_t r = 0; r < nr; ++r) out[(r * nv + v) * 3 + c] = {0, 0};
+        for (int i = 0; i < nring; ++i) {
+            const int64_t u = ring[i];
+            double Op[3], Om[3], np_[3], nm[3], wp, wm;
+            PatchSums pp, pm;
+            MovedPos Pp{V, v, {0, 0, 0}}, Pm{V, v, {0, 0, 0}};
+            Pp.d[c] = hv;
+            Pm.d[c] = -hv;
+            vertex_geometry(u, Pp, F, vt_start, vt_tri, Op, np_, wp, pp);
+            vertex_geometry(u, Pm, F, vt_start, vt_tri, Om, nm, wm, pm);
+            c64 kb, kj, tj, gj;
+            domain_consts(kd, td, gd, vdom[u], kb, kj, tj, gj);
+            c64 Mp[36], Mm[36], LU[36];
+            int8_t piv[6];
+            self_block(pp, np_, kb, kj, tj, gj, false, c64{0, 0}, Mp, LU, piv);
+            self_block(pm, nm, kb, kj, tj, gj, false, c64{0, 0}, Mm, LU, piv);
+            const double inv2h = 1.0 / (2.0 * hv);
+            for (int64_t r = 0; r < nr; ++r) {
+                const c64 *su = sens + (r * nv + u) * 7;
+                const c64 *xu = x + (r * nv + u) * 6, *lu = lam + (r * nv + u) * 6;
+                c64 acc = {0, 0};
+                for (int q = 0; q < 3; ++q) acc += su[q] * ((Op[q] - Om[q]) * inv2h);
+                acc += su[3] * ((wp - wm) * inv2h);
+                for (int q = 0; q < 3; ++q) acc += su[4 + q] * ((np_[q] - nm[q]) * inv2h);
+                for (int a = 0; a < 6; ++a) {
+                    c64 row = {0, 0};
+                    for (int b = 0; b < 6; ++b) row += (Mp[6 * a + b] - Mm[6 * a + b]) * xu[b];
+                    acc -= lu[a] * row * inv2h;
+                }
+                out[(r * nv + v) * 3 + c] += acc;
+            }
+        }
+    }
 }
 
 // centroid nodes: the triangle is its own patch
@@ -424,6 +509,11 @@ void build_geometry(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s) {
                                                                      uw, h->Mself, h->Mlu, h->piv);
         CKL("k_centroid_nodes");
     }
+    if (vertex) {  // kept for the shape gradient
+        h->h_F.assign(F, F + 3 * nt);
+        h->h_vt_start = vt_start;
+        h->h_vt_tri = vt_tri;
+    }
     // host copies of the user-order geometry; the sorted copies are made by the tree build
     h->h_pos.resize(3 * N);
     h->h_nrm.resize(3 * N);
@@ -442,6 +532,46 @@ void build_geometry(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s) {
     dev_free(h, dk);
     dev_free(h, dt);
     dev_free(h, dg);
+}
+
+void run_vertex_shape_grad(fmbem *h, int64_t nr, const c64 *x, const c64 *lam, const c64 *sens, double hv, c64 *out,
+                           cudaStream_t s) {
+    const int64_t nv = h->N, nt = (int64_t)h->h_F.size() / 3;
+    std::vector<c64> kd(h->J + 1), td(h->J + 1), gd(h->J + 1);
+    for (int d = 0; d <= h->J; ++d) {
+        kd[d] = h->k[d];
+        td[d] = d == 0 ? c64{0, 0} : cdiv(h->eps[0] - h->eps[d], h->eps[d]);
+        gd[d] = h->gam[d];
+    }
+    int32_t *dF = (int32_t *)dev_alloc(h, sizeof(int32_t) * 3 * nt);
+    int32_t *dvs = (int32_t *)dev_alloc(h, sizeof(int32_t) * (nv + 1));
+    int32_t *dvt = (int32_t *)dev_alloc(h, sizeof(int32_t) * 3 * nt);
+    c64 *dk = (c64 *)dev_alloc(h, sizeof(c64) * 3 * (h->J + 1));
+    int *derr = (int *)dev_alloc(h, sizeof(int));
+    auto cleanup = [&] {
+        for (void *p : {(void *)dF, (void *)dvs, (void *)dvt, (void *)dk, (void *)derr}) dev_free(h, p);
+    };
+    try {
+        CK(cudaMemcpyAsync(dF, h->h_F.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dvs, h->h_vt_start.data(), sizeof(int32_t) * (nv + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dvt, h->h_vt_tri.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dk, kd.data(), sizeof(c64) * (h->J + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dk + (h->J + 1), td.data(), sizeof(c64) * (h->J + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dk + 2 * (h->J + 1), gd.data(), sizeof(c64) * (h->J + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
+        k_vertex_shape_grad<<<(unsigned)((nv + 63) / 64), 64, 0, s>>>(nv, nr, h->upos, dF, dvs, dvt, h->udom, dk,
+                                                                   dk + (h->J + 1), dk + 2 * (h->J + 1), x, lam, sens,
+                                                                   hv, out, derr);
+        CKL("k_vertex_shape_grad");
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (e) throw fmbem_error{FMBEM_ERR_INVALID_MESH, "a vertex 1-ring holds more than 32 vertices"};
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
 }
 
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s) {

@@ -1,0 +1,249 @@
+// shapegrad.cu -- gradient of a linear functional of the solution with respect to the mesh
+// vertex positions (vertex nodes), by the adjoint method of the discrete system of Eq. (2.9).
+//
+// For A(V) x = b(V), a functional f = L(V)^T x and the adjoint A^T lambda = L,
+//   df/dtheta = d/dtheta [ L^T x + lambda^T b - lambda^T A x ]   at fixed x and lambda
+// for every vertex coordinate theta.  The vertex positions enter through the node data (position
+// s_u, weight w_u, normal n_u) of the nodes of the vertex's 1-ring and through their self blocks
+// (Appendix B).  Here the sensitivities of G = L^T x + lambda^T b - lambda^T A x to the node data
+// of every node are summed over all partners (the pair blocks of Eq. 2.12 depend on s_a, s_b,
+// w_b and n_b), by central differences in FP64, O(N^2) pair evaluations in all;
+// k_vertex_shape_grad (geometry.cu) then chains them with the node data of each vertex's 1-ring
+// and adds the self blocks' change.
+#include <algorithm>
+
+#include "fmbem_internal.cuh"
+
+namespace {
+
+struct DomainC {  // per domain, as in the matvec: k, t = (eps_0 - eps_d)/eps_d, gamma
+    c64 k, t, gamma;
+};
+
+__device__ __forceinline__ double dot3d(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// lambda_a . (pair block of Eq. 2.12 for target a, source b) x_b with r = s_b - s_a: the background
+// side always (normal -n_b, Psi^(0) = -Psi), the scatterer side when a and b share scatterer j
+__device__ c64 pair_val(const double *r, double wb, const double *nb, bool same, c64 k0, c64 kj, c64 tj, c64 gj,
+                        const c64 *la, const c64 *xb) {
+    const double R = sqrt(dot3d(r, r));
+    const double iR = 1.0 / R;
+    const c64 *Phi = xb, *Psi = xb + 3;
+    const double nr = dot3d(nb, r);
+    c64 val = {0, 0};
+    {
+        const c64 ik = {-k0.im, k0.re};
+        const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
+        const c64 c = g * (ik - c64{iR, 0}) * iR;
+        const c64 rP = r[0] * Phi[0] + r[1] * Phi[1] + r[2] * Phi[2];
+        const c64 nP = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
+        for (int q = 0; q < 3; ++q) {
+            // bracket with the background normal -n_b: -n (a.Phi) + (n.a) Phi + a (n.Phi), a = c r
+            const c64 B = c * (-nb[q] * rP + nr * Phi[q] + r[q] * nP);
+            val += la[q] * (-wb * (B + g * Psi[q]));
+        }
+    }
+    if (same) {
+        const c64 ik = {-kj.im, kj.re};
+        const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
+        const c64 c = g * (ik - c64{iR, 0}) * iR;
+        const c64 nP0 = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
+        c64 v[3];
+        for (int q = 0; q < 3; ++q) v[q] = Phi[q] + nb[q] * (tj * nP0);  // T_j Phi (Eq. 2.13)
+        const c64 rv = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+        const c64 nv = nb[0] * v[0] + nb[1] * v[1] + nb[2] * v[2];
+        for (int q = 0; q < 3; ++q) {
+            const c64 B = c * (nb[q] * rv - nr * v[q] - r[q] * nv);
+            val += la[3 + q] * (-wb * B + (gj * g) * (wb * 1.0) * Psi[q]);
+        }
+    }
+    return val;
+}
+
+// partial sensitivities of G's pair part over one slice of partners:
+// part[slice][r][u][7] = dG/d(s_u (3), w_u, n_u (3)); grid (node tiles, slices, rhs)
+constexpr int SG_NT = 128, SG_NS = 32;
+__global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, const double *pos, const double *nrm,
+                                                   const double *w, const int32_t *dom, const DomainC *dc,
+                                                   const c64 *x, const c64 *lam, double hs, double hn,
+                                                   int64_t slice_len, c64 *part) {
+    __shared__ double sp[SG_NS][3], sn[SG_NS][3], sw[SG_NS];
+    __shared__ int sd[SG_NS];
+    __shared__ c64 sx[SG_NS][6], sl[SG_NS][6];
+    const int64_t u = blockIdx.x * (int64_t)SG_NT + threadIdx.x, slice = blockIdx.y, r = blockIdx.z;
+    const bool valid = u < N;
+    double su[3] = {0, 0, 0}, nu[3] = {0, 0, 1}, wu = 1;
+    int du = 0;
+    c64 xu[6], lu[6];
+    for (int q = 0; q < 6; ++q) { xu[q] = {0, 0}; lu[q] = {0, 0}; }
+    if (valid) {
+        for (int q = 0; q < 3; ++q) { su[q] = pos[3 * u + q]; nu[q] = nrm[3 * u + q]; }
+        wu = w[u];
+        du = dom[u];
+        for (int q = 0; q < 6; ++q) { xu[q] = x[(r * N + u) * 6 + q]; lu[q] = lam[(r * N + u) * 6 + q]; }
+    }
+    const c64 k0 = dc[0].k, kj = dc[du].k, tj = dc[du].t, gj = dc[du].gamma;
+    const int64_t b0s = slice * slice_len, b1s = min(N, b0s + slice_len);
+    c64 acc[7];
+    for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
+    const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
+    for (int64_t b0 = b0s; b0 < b1s; b0 += SG_NS) {
+        const int nb = (int)min((int64_t)SG_NS, b1s - b0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+            const int64_t m = b0 + e;
+            for (int q = 0; q < 3; ++q) { sp[e][q] = pos[3 * m + q]; sn[e][q] = nrm[3 * m + q]; }
+            sw[e] = w[m];
+            sd[e] = dom[m];
+            for (int q = 0; q < 6; ++q) { sx[e][q] = x[(r * N + m) * 6 + q]; sl[e][q] = lam[(r * N + m) * 6 + q]; }
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int e = 0; e < nb; ++e) {
+            if (b0 + e == u) continue;
+            const bool same = sd[e] == du;
+            const double rt[3] = {sp[e][0] - su[0], sp[e][1] - su[1], sp[e][2] - su[2]};
+            // u as the target: r = s_m - s_u, dG/ds_u = +dt/dr (G holds -t)
+            for (int c = 0; c < 3; ++c) {
+                double rp[3] = {rt[0], rt[1], rt[2]}, rm[3] = {rt[0], rt[1], rt[2]};
+                rp[c] += hs;
+                rm[c] -= hs;
+                acc[c] += (pair_val(rp, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e]) -
+                           pair_val(rm, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e])) * i2s;
+            }
+            // u as the source: r = s_u - s_m, dG/ds_u = -dsigma/dr, dG/dn_u, dG/dw_u = -sigma / w_u
+            const double rs[3] = {-rt[0], -rt[1], -rt[2]};
+            for (int c = 0; c < 3; ++c) {
+                double rp[3] = {rs[0], rs[1], rs[2]}, rm[3] = {rs[0], rs[1], rs[2]};
+                rp[c] += hs;
+                rm[c] -= hs;
+                acc[c] -= (pair_val(rp, wu, nu, same, k0, kj, tj, gj, sl[e], xu) -
+                           pair_val(rm, wu, nu, same, k0, kj, tj, gj, sl[e], xu)) * i2s;
+                double np_[3] = {nu[0], nu[1], nu[2]}, nm[3] = {nu[0], nu[1], nu[2]};
+                np_[c] += hn;
+                nm[c] -= hn;
+                acc[4 + c] -= (pair_val(rs, wu, np_, same, k0, kj, tj, gj, sl[e], xu) -
+                               pair_val(rs, wu, nm, same, k0, kj, tj, gj, sl[e], xu)) * i2n;
+            }
+            acc[3] -= pair_val(rs, wu, nu, same, k0, kj, tj, gj, sl[e], xu) * (1.0 / wu);
+        }
+    }
+    if (valid)
+        for (int q = 0; q < 7; ++q) part[((slice * nr + r) * N + u) * 7 + q] = acc[q];
+}
+
+// far-field functional value L_u(s, w, n) . x_u (the coefficients of fmbem_far_field_functional)
+__device__ c64 ff_functional(const double *s, double w, const double *n, c64 k0, const double *u, const c64 *c,
+                             const c64 *xu) {
+    const c64 mik = {k0.im, -k0.re};  // -i k0
+    const double n0[3] = {-n[0], -n[1], -n[2]};
+    const c64 f = cexpd(mik * dot3d(u, s)) * (w / (4.0 * FMBEM_PI));
+    const c64 cn = c[0] * n0[0] + c[1] * n0[1] + c[2] * n0[2], cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+    const double nu = dot3d(n0, u);
+    c64 val = {0, 0};
+    for (int q = 0; q < 3; ++q) val += f * (mik * (cn * u[q] - nu * c[q] - cu * n0[q]) * xu[q] + c[q] * xu[3 + q]);
+    return val;
+}
+
+// sens[r][u] = sum over slices + the local terms of G: the functional L_u . x_u and the right-
+// hand side lambda_u . e exp(i k0 d.s_u) (background rows, Eq. 2.12); thread per (node, rhs)
+__global__ void k_node_sens_reduce(int64_t N, int64_t nr, int n_slices, const c64 *part, const double *pos,
+                                   const double *nrm, const double *w, c64 k0, const double *dir, const c64 *pol,
+                                   const double *rhat, const c64 *coef, const c64 *x, const c64 *lam, double hs,
+                                   double hn, c64 *sens) {
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (u >= N) return;
+    c64 acc[7];
+    for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
+    for (int sl = 0; sl < n_slices; ++sl)
+        for (int q = 0; q < 7; ++q) acc[q] += part[(((int64_t)sl * nr + r) * N + u) * 7 + q];
+    const double s[3] = {pos[3 * u], pos[3 * u + 1], pos[3 * u + 2]}, n[3] = {nrm[3 * u], nrm[3 * u + 1], nrm[3 * u + 2]};
+    const double wu = w[u];
+    const c64 *xu = x + (r * N + u) * 6, *lu = lam + (r * N + u) * 6;
+    {  // right-hand side
+        const double *d = dir + 3 * r;
+        const c64 *e = pol + 3 * r;
+        const c64 ik = {-k0.im, k0.re};
+        const c64 ph = cexpd(ik * dot3d(d, s));
+        const c64 le = lu[0] * e[0] + lu[1] * e[1] + lu[2] * e[2];
+        for (int c = 0; c < 3; ++c) acc[c] += ik * le * ph * d[c];
+    }
+    {  // functional
+        const double *ud = rhat + 3 * r;
+        const c64 *cf = coef + 3 * r;
+        const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
+        for (int c = 0; c < 3; ++c) {
+            double sp_[3] = {s[0], s[1], s[2]}, sm[3] = {s[0], s[1], s[2]};
+            sp_[c] += hs;
+            sm[c] -= hs;
+            acc[c] += (ff_functional(sp_, wu, n, k0, ud, cf, xu) - ff_functional(sm, wu, n, k0, ud, cf, xu)) * i2s;
+            double np_[3] = {n[0], n[1], n[2]}, nm[3] = {n[0], n[1], n[2]};
+            np_[c] += hn;
+            nm[c] -= hn;
+            acc[4 + c] += (ff_functional(s, wu, np_, k0, ud, cf, xu) - ff_functional(s, wu, nm, k0, ud, cf, xu)) * i2n;
+        }
+        acc[3] += ff_functional(s, wu, n, k0, ud, cf, xu) * (1.0 / wu);
+    }
+    for (int q = 0; q < 7; ++q) sens[(r * N + u) * 7 + q] = acc[q];
+}
+
+}  // namespace
+
+void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, const double *dir_host,
+                        const c64 *pol_host, const double *rhat_host, const c64 *coef_host, c64 *out_host,
+                        cudaStream_t s) {
+    if (h->opt.node_mode != FMBEM_NODES_VERTEX)
+        throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "the shape gradient needs vertex nodes"};
+    if (h->ibc) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "the shape gradient is for penetrable scatterers"};
+    const int64_t N = h->N;
+    // finite-difference steps: positions 1e-6 of the mean edge length, normals 1e-6
+    double ledge = 0;
+    const int64_t nt = (int64_t)h->h_F.size() / 3;
+    for (int64_t t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) {
+            const double *A = &h->h_pos[3 * h->h_F[3 * t + a]], *B = &h->h_pos[3 * h->h_F[3 * t + (a + 1) % 3]];
+            ledge += std::sqrt((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]));
+        }
+    ledge /= (double)(3 * nt);
+    const double hs = 1e-6 * ledge, hn = 1e-6;
+    const int64_t ntile = (N + SG_NT - 1) / SG_NT;
+    const int n_slices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (4 * 152 + ntile * nr - 1) / (ntile * nr)));
+    const int64_t slice_len = (N + n_slices - 1) / n_slices;
+    std::vector<c64> dch(3 * (h->J + 1));
+    for (int d = 0; d <= h->J; ++d) {
+        dch[3 * d] = h->k[d];
+        dch[3 * d + 1] = d == 0 ? c64{0, 0} : cdiv(h->eps[0] - h->eps[d], h->eps[d]);
+        dch[3 * d + 2] = h->gam[d];
+    }
+    DomainC *ddc = (DomainC *)dev_alloc(h, sizeof(c64) * dch.size());
+    c64 *part = (c64 *)dev_alloc(h, sizeof(c64) * 7 * N * nr * n_slices);
+    c64 *sens = (c64 *)dev_alloc(h, sizeof(c64) * 7 * N * nr);
+    double *dd = (double *)dev_alloc(h, sizeof(double) * 3 * nr), *dr = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
+    c64 *dp = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr), *dcf = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
+    c64 *dout = (c64 *)dev_alloc(h, sizeof(c64) * 3 * N * nr);
+    auto cleanup = [&] {
+        for (void *p : {(void *)ddc, (void *)part, (void *)sens, (void *)dd, (void *)dr, (void *)dp, (void *)dcf,
+                        (void *)dout})
+            dev_free(h, p);
+    };
+    try {
+        CK(cudaMemcpyAsync(ddc, dch.data(), sizeof(c64) * dch.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dd, dir_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dr, rhat_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dp, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dcf, coef_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        k_node_sens<<<dim3((unsigned)ntile, (unsigned)n_slices, (unsigned)nr), SG_NT, 0, s>>>(
+            N, nr, h->upos, h->unrm, h->uw, h->udom, ddc, x, lam, hs, hn, slice_len, part);
+        CKL("k_node_sens");
+        k_node_sens_reduce<<<dim3((unsigned)((N + 127) / 128), (unsigned)nr), 128, 0, s>>>(
+            N, nr, n_slices, part, h->upos, h->unrm, h->uw, h->k[0], dd, dp, dr, dcf, x, lam, hs, hn, sens);
+        CKL("k_node_sens_reduce");
+        run_vertex_shape_grad(h, nr, x, lam, sens, hs, dout, s);
+        CK(cudaMemcpyAsync(out_host, dout, sizeof(c64) * 3 * N * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}

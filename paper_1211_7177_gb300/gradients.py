@@ -1,5 +1,5 @@
 """Adjoint gradients of the extinction cross section and of the optical force with respect to
-the permittivities.
+the permittivities, and of the extinction with respect to the mesh vertex positions.
 
 The extinction of a plane wave (d, e) is the imaginary part of a linear functional of the
 solution, C_ext = Im f(x) with f(x) = (4 pi / k0) conj(e) . F(d) (optical theorem, F the far-field
@@ -65,6 +65,28 @@ def extinction_eps_gradient(V, F, D, eps, mu, k0, dirs, pols, j, tol=1e-10, h=No
     dAx = (gp.matvec(x) - gm.matvec(x)) / (2 * step)
     df = -torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()
     return cext, df.imag, df.real
+
+
+def extinction_vertex_gradient(V, F, D, eps, mu, k0, dirs, pols, tol=1e-10, **options):
+    """(C_ext [n_rhs], dC_ext/dV [n_rhs, nv, 3]) for the plane waves (dirs[r], pols[r]) on the mesh
+    (V, F, D) (vertex nodes): one forward and one adjoint GMRES solve through the FMM, then the
+    vertex derivative of L^T x + lambda^T b - lambda^T A x at fixed x and lambda
+    (fmbem_shape_gradient), whose imaginary part is the extinction's."""
+    import torch
+    g = FMBEM(V, F, D, eps, mu, k0, **options)
+    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+    pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
+    x, _, _, st = g.solve(g.plane_wave_rhs(dirs, pols), tol=tol)
+    if st != 0:
+        raise FMBEMError(st, "forward solve did not converge")
+    coef = 4 * np.pi / g.kb.real * np.conj(pols)
+    L = g.far_field_functional(dirs, coef)
+    cext = torch.sum(L * x, dim=(1, 2)).imag.cpu().numpy()
+    lam, _, _, st = g.adjoint_solve(L, tol=tol)
+    if st != 0:
+        raise FMBEMError(st, "adjoint solve did not converge")
+    grad = g.shape_gradient(x, lam, dirs, pols, dirs, coef)
+    return cext, grad.imag
 
 
 def _sphere_points(center, radius, n_theta, n_phi):
