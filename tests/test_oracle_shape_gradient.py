@@ -45,3 +45,25 @@ def test_two_scatterers_with_mu():
         fd = (sg.extinction(Vp, F, D, eps, mu, k0, d, e) - sg.extinction(Vm, F, D, eps, mu, k0, d, e)) / (2 * h)
         assert abs(g[v, cc] - fd) < 1e-7 * np.abs(g).max(), (v, cc, g[v, cc], fd)
     assert np.abs(g.sum(0)).max() < 1e-7 * np.abs(g).max()
+
+
+def test_force_gradient_matches_full_solves():
+    """The Maxwell-stress force on the smaller of two spheres: its dense adjoint vertex gradient
+    against central differences of the force from full dense solves, for vertices of both
+    spheres."""
+    m1 = fi.icosphere(1, 0.5, (-0.6, 0.0, 0.0), domain=1)
+    m2 = fi.icosphere(1, 0.3, (0.5, 0.1, 0.0), domain=2)
+    V, F, D = fi.merge_meshes(m1, m2)
+    eps, mu, k0 = [1.0, 2.25 + 0.1j, -4.0 + 0.5j], [1.0, 1.0, 1.0], 1.5
+    d = np.array([0.6, 0.0, 0.8])
+    e = np.array([0.8, 0.0, -0.6], dtype=np.complex128)
+    ctr, rad = np.array([0.5, 0.1, 0.0]), 0.42
+    Fo, g = sg.force_vertex_gradient(V, F, D, eps, mu, k0, d, e, ctr, rad)
+    assert np.allclose(Fo, sg.force(V, F, D, eps, mu, k0, d, e, ctr, rad), rtol=1e-12, atol=1e-15)
+    h = 1e-6
+    for v, cc in ((50, 0), (60, 2), (3, 1)):
+        Vp, Vm = V.copy(), V.copy()
+        Vp[v, cc] += h
+        Vm[v, cc] -= h
+        fd = (sg.force(Vp, F, D, eps, mu, k0, d, e, ctr, rad) - sg.force(Vm, F, D, eps, mu, k0, d, e, ctr, rad)) / (2 * h)
+        assert np.abs(g[:, v, cc] - fd).max() < 1e-7 * np.abs(g).max(), (v, cc, g[:, v, cc], fd)
