@@ -308,6 +308,18 @@ fmbem_status fmbem_shape_gradient(fmbem *h, const void *x_dev, const void *lam_d
                                   const fmbem_c64 *pol, const double *rhat, const fmbem_c64 *coef,
                                   fmbem_c64 *out_host, void *stream);
 
+/* As fmbem_shape_gradient, for the near-field functionals
+ *   f_r = sum_p cE[r][p] . E_sca(r_p) + cH[r][p] . H_sca(r_p)
+ * of fmbem_near_field_functional (E_sca, H_sca the scattered parts of fmbem_near_field's fields at
+ * the fixed points pts) in place of the far-field ones: with A^T lambda_r = N_r (the functional's
+ * coefficients), out[r][v][c] = d f_r / dV_vc.  The gradient of the Maxwell-stress force takes
+ * the Wirtinger coefficients of each force component as cE, cH (F_i = 2 Re ... to first order).
+ *   pts host [n_pts][3]; cE, cH host [n_rhs][n_pts][3] complex128 (cH may be NULL).
+ * Errors as fmbem_shape_gradient. */
+fmbem_status fmbem_shape_gradient_near(fmbem *h, const void *x_dev, const void *lam_dev, int64_t n_rhs,
+                                       const double *dir, const fmbem_c64 *pol, int64_t n_pts, const double *pts,
+                                       const fmbem_c64 *cE, const fmbem_c64 *cH, fmbem_c64 *out_host, void *stream);
+
 /* Fields inside the scatterers: at each point r_p, inside scatterer domain[p] = j, the
  * representation formula of domain j (Appendix A; Eq. 2.5 holds it on the boundary),
  *   E_j(r) = sum over the nodes b of scatterer j of

@@ -106,8 +106,10 @@ def stress_force(o, x, d, e, center, radius, n_theta=12, n_phi=24):
     return np.sum(wq[:, None] * 0.5 * np.real(E * en[:, None] + H * hn[:, None] - 0.5 * u[:, None] * nq), 0)
 
 
-def force_vertex_gradient(V, F, D, eps, mu, k0, d, e, center, radius, n_theta=12, n_phi=24, h=1e-6):
-    """(F [3], dF/dV [3, nv, 3]) of the Maxwell-stress force by the dense adjoint formula.
+def force_vertex_gradient(V, F, D, eps, mu, k0, d, e, center, radius, n_theta=12, n_phi=24, h=1e-6,
+                          return_state=False):
+    """(F [3], dF/dV [3, nv, 3]) of the Maxwell-stress force by the dense adjoint formula (with
+    return_state also x, lambda [3, N, 6], the stress points and the coefficients cE, cH).
 
     F_i is a real quadratic form of the fields on the stress sphere, so dF_i = 2 Re(sum_p cE_p . dE_p
     + cH_p . dH_p) with the holomorphic (Wirtinger) coefficients cE, cH of F_i at the current
@@ -165,6 +167,8 @@ def force_vertex_gradient(V, F, D, eps, mu, k0, d, e, center, radius, n_theta=12
                 Gs.append([functional(op, x, i) + np.sum(lam[i] * bx) - np.sum(lam[i] * Ax) for i in range(3)])
             for i in range(3):
                 grad[i, v, c] = 2 * np.real((Gs[0][i] - Gs[1][i]) / (2 * h))
+    if return_state:  # the dense solution, adjoints [3, N, 6], stress points and coefficients
+        return force, grad, x, np.stack(lam), pts, cE, cH
     return force, grad
 
 

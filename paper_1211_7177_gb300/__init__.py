@@ -85,6 +85,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
         "fmbem_interior_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
         "fmbem_shape_gradient": (i32, [P, P, P, i64, P, P, P, P, P, P]),
+        "fmbem_shape_gradient_near": (i32, [P, P, P, i64, P, P, i64, P, P, P, P, P]),
         "fmbem_near_field_functional": (i32, [P, i64, i64, P, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
@@ -296,6 +297,30 @@ def fmbem_shape_gradient(h, x, lam, dirs, pols, rhat, coef, stream=None):
     out = np.empty((n, N, 3), dtype=np.complex128)
     _check(h, load_library().fmbem_shape_gradient(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(lam.data_ptr()), n,
                                                   _ptr(d), _ptr(p), _ptr(rh), _ptr(cf), _ptr(out), _stream(stream)))
+    return out
+
+
+def fmbem_shape_gradient_near(h, x, lam, dirs, pols, points, cE, cH=None, stream=None):
+    """d/dV of the near-field functionals sum_p cE[r][p] . E_sca(r_p) + cH[r][p] . H_sca(r_p) of the
+    solutions x (plane waves (dirs, pols)) given their adjoints lam: [n_rhs, N_vertices, 3] (host)."""
+    N = fmbem_num_nodes(h)
+    x = _dev(x, N, "x")
+    lam = _dev(lam, N, "lam")
+    n = x.shape[0]
+    d = np.ascontiguousarray(np.broadcast_to(np.asarray(dirs, dtype=np.float64), (n, 3)))
+    p = np.ascontiguousarray(np.broadcast_to(np.asarray(pols, dtype=np.complex128), (n, 3)))
+    pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    cE = np.ascontiguousarray(cE, dtype=np.complex128)
+    if cE.shape != (n, len(pts), 3):
+        raise ValueError("cE must be [n_rhs, n_pts, 3]")
+    if cH is not None:
+        cH = np.ascontiguousarray(cH, dtype=np.complex128)
+        if cH.shape != cE.shape:
+            raise ValueError("cH must have the shape of cE")
+    out = np.empty((n, N, 3), dtype=np.complex128)
+    _check(h, load_library().fmbem_shape_gradient_near(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                                       n, _ptr(d), _ptr(p), len(pts), _ptr(pts), _ptr(cE),
+                                                       _ptr(cH) if cH is not None else None, _ptr(out), _stream(stream)))
     return out
 
 
@@ -517,6 +542,9 @@ class FMBEM:
 
     def shape_gradient(self, x, lam, dirs, pols, rhat, coef, stream=None):
         return fmbem_shape_gradient(self.h, x, lam, dirs, pols, rhat, coef, stream)
+
+    def shape_gradient_near(self, x, lam, dirs, pols, points, cE, cH=None, stream=None):
+        return fmbem_shape_gradient_near(self.h, x, lam, dirs, pols, points, cE, cH, stream)
 
     def far_field_functional(self, rhat, coef, stream=None):
         return fmbem_far_field_functional(self.h, rhat, coef, stream)

@@ -337,7 +337,21 @@ fmbem_status fmbem_shape_gradient(fmbem *h, const void *x_dev, const void *lam_d
     }
     return guarded(h, [&] {
         run_shape_gradient(h, (const c64 *)x_dev, (const c64 *)lam_dev, n_rhs, dir, (const c64 *)pol, rhat,
-                           (const c64 *)coef, (c64 *)out_host, (cudaStream_t)stream);
+                           (const c64 *)coef, 0, nullptr, nullptr, nullptr, (c64 *)out_host, (cudaStream_t)stream);
+    });
+}
+
+fmbem_status fmbem_shape_gradient_near(fmbem *h, const void *x_dev, const void *lam_dev, int64_t n_rhs,
+                                       const double *dir, const fmbem_c64 *pol, int64_t n_pts, const double *pts,
+                                       const fmbem_c64 *cE, const fmbem_c64 *cH, fmbem_c64 *out_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_rhs > 65535 || n_pts < 1 || !x_dev || !lam_dev || !dir || !pol || !pts || !cE || !out_host) {
+        h->err = "invalid argument (n_rhs in 1..65535, n_pts >= 1, non-NULL x, lambda, dir, pol, pts, cE and out)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_shape_gradient(h, (const c64 *)x_dev, (const c64 *)lam_dev, n_rhs, dir, (const c64 *)pol, nullptr, nullptr,
+                           n_pts, pts, (const c64 *)cE, (const c64 *)cH, (c64 *)out_host, (cudaStream_t)stream);
     });
 }
 

@@ -276,7 +276,8 @@ void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int preci
 void run_near_field_functional(fmbem *h, int64_t nf, int64_t n_pts, const double *pts_host, const c64 *cE_host,
                                const c64 *cH_host, c64 *out, cudaStream_t s);
 void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, const double *dir_host,
-                        const c64 *pol_host, const double *rhat_host, const c64 *coef_host, c64 *out_host,
+                        const c64 *pol_host, const double *rhat_host, const c64 *coef_host, int64_t n_pts,
+                        const double *pts_host, const c64 *cE_host, const c64 *cH_host, c64 *out_host,
                         cudaStream_t s);
 void run_vertex_shape_grad(fmbem *h, int64_t nr, const c64 *x, const c64 *lam, const c64 *sens, double hv, c64 *out,
                            cudaStream_t s);

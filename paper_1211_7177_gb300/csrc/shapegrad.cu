@@ -168,7 +168,7 @@ __global__ void k_node_sens_reduce(int64_t N, int64_t nr, int n_slices, const c6
         const c64 le = lu[0] * e[0] + lu[1] * e[1] + lu[2] * e[2];
         for (int c = 0; c < 3; ++c) acc[c] += ik * le * ph * d[c];
     }
-    {  // functional
+    if (rhat != nullptr) {  // far-field functional
         const double *ud = rhat + 3 * r;
         const c64 *cf = coef + 3 * r;
         const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
@@ -187,10 +187,104 @@ __global__ void k_node_sens_reduce(int64_t N, int64_t nr, int n_slices, const c6
     for (int q = 0; q < 7; ++q) sens[(r * N + u) * 7 + q] = acc[q];
 }
 
+// node u's part of sum_p cE_p . E_sca(r_p) + cH_p . H_sca(r_p) with its own data (s, w, n): the
+// representation formula of fmbem_near_field (background normal -n, Psi^(0) = -Psi) and its curl
+__device__ c64 nf_val(const double *t, const double *s, double w, const double *n, const c64 *xu, c64 k0, c64 iwmu,
+                      const c64 *cE, const c64 *cH) {
+    const double rv[3] = {s[0] - t[0], s[1] - t[1], s[2] - t[2]};
+    const double R = sqrt(dot3d(rv, rv)), iR = 1.0 / R;
+    const c64 ik = {-k0.im, k0.re};
+    const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
+    const c64 g1 = g * (ik - c64{iR, 0});
+    const c64 c = g1 * iR;
+    const double n0[3] = {-n[0], -n[1], -n[2]};
+    const c64 *Phi = xu, *Psi = xu + 3;
+    const c64 rP = rv[0] * Phi[0] + rv[1] * Phi[1] + rv[2] * Phi[2];
+    const c64 nP = n0[0] * Phi[0] + n0[1] * Phi[1] + n0[2] * Phi[2];
+    const double nr = dot3d(n0, rv);
+    c64 val = {0, 0};
+    for (int q = 0; q < 3; ++q) val += cE[q] * (w * (c * (n0[q] * rP - nr * Phi[q] - rv[q] * nP) + g * Psi[q]));
+    if (cH != nullptr) {
+        const double rh[3] = {rv[0] * iR, rv[1] * iR, rv[2] * iR};
+        const c64 q1 = ik - c64{iR, 0};
+        const c64 g2 = g * (q1 * q1 + c64{iR * iR, 0});
+        const double rn = dot3d(rh, n0);
+        const c64 rhP = rP * iR;
+        c64 Kn[3], KP[3], av[3];
+        for (int q = 0; q < 3; ++q) {
+            Kn[q] = g2 * (rh[q] * rn) + c * (n0[q] - rh[q] * rn);
+            KP[q] = g2 * rhP * rh[q] + c * (Phi[q] - rhP * rh[q]);
+            av[q] = g1 * rh[q];
+        }
+        const c64 cur[3] = {Kn[1] * Phi[2] - Kn[2] * Phi[1] + n0[1] * KP[2] - n0[2] * KP[1] - (av[1] * Psi[2] - av[2] * Psi[1]),
+                            Kn[2] * Phi[0] - Kn[0] * Phi[2] + n0[2] * KP[0] - n0[0] * KP[2] - (av[2] * Psi[0] - av[0] * Psi[2]),
+                            Kn[0] * Phi[1] - Kn[1] * Phi[0] + n0[0] * KP[1] - n0[1] * KP[0] - (av[0] * Psi[1] - av[1] * Psi[0])};
+        for (int q = 0; q < 3; ++q) val += cH[q] * cdiv(cur[q] * w, iwmu);
+    }
+    return val;
+}
+
+// adds to sens[r][u] the derivatives of node u's part of the near-field functional of right-hand
+// side r with respect to its position, weight and normal; thread per (node, rhs), the points
+// staged in shared memory SG_NS at a time
+__global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr, const double *pos,
+                                                        const double *nrm, const double *w, const c64 *x,
+                                                        int64_t n_pts, const double *pts, const c64 *cE,
+                                                        const c64 *cH, c64 k0, c64 iwmu, double hs, double hn,
+                                                        c64 *sens) {
+    __shared__ double spt[SG_NS][3];
+    __shared__ c64 sce[SG_NS][3], sch[SG_NS][3];
+    const int64_t u = blockIdx.x * (int64_t)SG_NT + threadIdx.x, r = blockIdx.y;
+    const bool valid = u < N;
+    double s[3] = {0, 0, 0}, n[3] = {0, 0, 1}, wu = 1;
+    c64 xu[6];
+    for (int q = 0; q < 6; ++q) xu[q] = {0, 0};
+    if (valid) {
+        for (int q = 0; q < 3; ++q) { s[q] = pos[3 * u + q]; n[q] = nrm[3 * u + q]; }
+        wu = w[u];
+        for (int q = 0; q < 6; ++q) xu[q] = x[(r * N + u) * 6 + q];
+    }
+    c64 acc[7];
+    for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
+    const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
+    for (int64_t p0 = 0; p0 < n_pts; p0 += SG_NS) {
+        const int np = (int)min((int64_t)SG_NS, n_pts - p0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            for (int q = 0; q < 3; ++q) {
+                spt[e][q] = pts[3 * (p0 + e) + q];
+                sce[e][q] = cE[(r * n_pts + p0 + e) * 3 + q];
+                sch[e][q] = cH ? cH[(r * n_pts + p0 + e) * 3 + q] : c64{0, 0};
+            }
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int e = 0; e < np; ++e) {
+            const c64 *ch = cH ? sch[e] : nullptr;
+            for (int c = 0; c < 3; ++c) {
+                double sp_[3] = {s[0], s[1], s[2]}, sm[3] = {s[0], s[1], s[2]};
+                sp_[c] += hs;
+                sm[c] -= hs;
+                acc[c] += (nf_val(spt[e], sp_, wu, n, xu, k0, iwmu, sce[e], ch) -
+                           nf_val(spt[e], sm, wu, n, xu, k0, iwmu, sce[e], ch)) * i2s;
+                double np_[3] = {n[0], n[1], n[2]}, nm[3] = {n[0], n[1], n[2]};
+                np_[c] += hn;
+                nm[c] -= hn;
+                acc[4 + c] += (nf_val(spt[e], s, wu, np_, xu, k0, iwmu, sce[e], ch) -
+                               nf_val(spt[e], s, wu, nm, xu, k0, iwmu, sce[e], ch)) * i2n;
+            }
+            acc[3] += nf_val(spt[e], s, wu, n, xu, k0, iwmu, sce[e], ch) * (1.0 / wu);
+        }
+    }
+    if (valid)
+        for (int q = 0; q < 7; ++q) sens[(r * N + u) * 7 + q] += acc[q];
+}
+
 }  // namespace
 
 void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, const double *dir_host,
-                        const c64 *pol_host, const double *rhat_host, const c64 *coef_host, c64 *out_host,
+                        const c64 *pol_host, const double *rhat_host, const c64 *coef_host, int64_t n_pts,
+                        const double *pts_host, const c64 *cE_host, const c64 *cH_host, c64 *out_host,
                         cudaStream_t s) {
     if (h->opt.node_mode != FMBEM_NODES_VERTEX)
         throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "the shape gradient needs vertex nodes"};
@@ -221,23 +315,41 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
     double *dd = (double *)dev_alloc(h, sizeof(double) * 3 * nr), *dr = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
     c64 *dp = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr), *dcf = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
     c64 *dout = (c64 *)dev_alloc(h, sizeof(c64) * 3 * N * nr);
+    const bool nearf = pts_host != nullptr;
+    double *dpt = nearf ? (double *)dev_alloc(h, sizeof(double) * 3 * n_pts) : nullptr;
+    c64 *dcE = nearf ? (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr) : nullptr;
+    c64 *dcH = nearf && cH_host ? (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr) : nullptr;
     auto cleanup = [&] {
         for (void *p : {(void *)ddc, (void *)part, (void *)sens, (void *)dd, (void *)dr, (void *)dp, (void *)dcf,
-                        (void *)dout})
-            dev_free(h, p);
+                        (void *)dout, (void *)dpt, (void *)dcE, (void *)dcH})
+            if (p) dev_free(h, p);
     };
     try {
         CK(cudaMemcpyAsync(ddc, dch.data(), sizeof(c64) * dch.size(), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dd, dir_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(dr, rhat_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dp, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(dcf, coef_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        if (rhat_host) {
+            CK(cudaMemcpyAsync(dr, rhat_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(dcf, coef_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        }
+        if (nearf) {
+            CK(cudaMemcpyAsync(dpt, pts_host, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(dcE, cE_host, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyHostToDevice, s));
+            if (dcH) CK(cudaMemcpyAsync(dcH, cH_host, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyHostToDevice, s));
+        }
         k_node_sens<<<dim3((unsigned)ntile, (unsigned)n_slices, (unsigned)nr), SG_NT, 0, s>>>(
             N, nr, h->upos, h->unrm, h->uw, h->udom, ddc, x, lam, hs, hn, slice_len, part);
         CKL("k_node_sens");
         k_node_sens_reduce<<<dim3((unsigned)((N + 127) / 128), (unsigned)nr), 128, 0, s>>>(
-            N, nr, n_slices, part, h->upos, h->unrm, h->uw, h->k[0], dd, dp, dr, dcf, x, lam, hs, hn, sens);
+            N, nr, n_slices, part, h->upos, h->unrm, h->uw, h->k[0], dd, dp, rhat_host ? dr : nullptr, dcf, x, lam, hs,
+            hn, sens);
         CKL("k_node_sens_reduce");
+        if (nearf) {
+            const c64 iwmu = c64{0, h->k0} * h->mu[0];  // i omega mu_0 with omega = k0 (c = 1)
+            k_node_sens_near<<<dim3((unsigned)ntile, (unsigned)nr), SG_NT, 0, s>>>(
+                N, nr, h->upos, h->unrm, h->uw, x, n_pts, dpt, dcE, dcH, h->k[0], iwmu, hs, hn, sens);
+            CKL("k_node_sens_near");
+        }
         run_vertex_shape_grad(h, nr, x, lam, sens, hs, dout, s);
         CK(cudaMemcpyAsync(out_host, dout, sizeof(c64) * 3 * N * nr, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

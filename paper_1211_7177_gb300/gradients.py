@@ -99,6 +99,34 @@ def _sphere_points(center, radius, n_theta, n_phi):
     return np.asarray(center, dtype=np.float64)[None, :] + radius * nq, nq, wq
 
 
+def _force_adjoint(g, d, e, center, radius, n_theta, n_phi, tol):
+    """Forward solve, the Maxwell-stress force on the sphere (center, radius), the Wirtinger
+    coefficients cE, cH [3, P, 3] of its components and their adjoints lambda [3, N, 6]."""
+    g._vacuum_background()
+    x, _, _, st = g.solve(g.plane_wave_rhs(d, e), tol=tol)
+    if st != 0:
+        raise FMBEMError(st, "forward solve did not converge")
+    pts, nq, wq = _sphere_points(center, radius, n_theta, n_phi)
+    E, H = g.near_field(x, pts, d, e, magnetic=True)
+    E, H = E[0], H[0]
+    en, hn = np.sum(np.conj(E) * nq, 1), np.sum(np.conj(H) * nq, 1)
+    u = np.sum(np.abs(E) ** 2 + np.abs(H) ** 2, 1)
+    force = np.sum(wq[:, None] * 0.5 * np.real(E * en[:, None] + H * hn[:, None] - 0.5 * u[:, None] * nq), 0)
+    eye = np.eye(3)
+
+    def wirtinger(Fv, fn):  # [3 (component i), P, 3 (field index j)]
+        c = (eye[:, None, :] * fn[None, :, None] + np.conj(Fv).T[:, :, None] * nq[None, :, :]
+             - nq.T[:, :, None] * np.conj(Fv)[None, :, :])
+        return 0.25 * wq[None, :, None] * c
+
+    cE, cH = wirtinger(E, en), wirtinger(H, hn)
+    L = g.near_field_functional(pts, cE, cH)
+    lam, _, _, st = g.adjoint_solve(L, tol=tol)
+    if st != 0:
+        raise FMBEMError(st, "adjoint solve did not converge")
+    return x, force, pts, cE, cH, lam
+
+
 def force_eps_gradient(V, F, D, eps, mu, k0, d, e, j, center, radius, n_theta=24, n_phi=48, tol=1e-10, h=None,
                        **options):
     """(F [3], dF/dRe(eps_j) [3], dF/dIm(eps_j) [3]): the time-averaged Maxwell-stress force on the
@@ -116,29 +144,9 @@ def force_eps_gradient(V, F, D, eps, mu, k0, d, e, j, center, radius, n_theta=24
     if not 1 <= j < len(eps):
         raise ValueError("j must index a scatterer (1..J)")
     g = FMBEM(V, F, D, eps, mu, k0, **options)
-    g._vacuum_background()
     d = np.asarray(d, dtype=np.float64).reshape(1, 3)
     e = np.asarray(e, dtype=np.complex128).reshape(1, 3)
-    x, _, _, st = g.solve(g.plane_wave_rhs(d, e), tol=tol)
-    if st != 0:
-        raise FMBEMError(st, "forward solve did not converge")
-    pts, nq, wq = _sphere_points(center, radius, n_theta, n_phi)
-    E, H = g.near_field(x, pts, d, e, magnetic=True)
-    E, H = E[0], H[0]
-    en, hn = np.sum(np.conj(E) * nq, 1), np.sum(np.conj(H) * nq, 1)
-    u = np.sum(np.abs(E) ** 2 + np.abs(H) ** 2, 1)
-    force = np.sum(wq[:, None] * 0.5 * np.real(E * en[:, None] + H * hn[:, None] - 0.5 * u[:, None] * nq), 0)
-    eye = np.eye(3)
-
-    def wirtinger(Fv, fn):  # [3 (component i), P, 3 (field index j)]
-        c = (eye[:, None, :] * fn[None, :, None] + np.conj(Fv).T[:, :, None] * nq[None, :, :]
-             - nq.T[:, :, None] * np.conj(Fv)[None, :, :])
-        return 0.25 * wq[None, :, None] * c
-
-    L = g.near_field_functional(pts, wirtinger(E, en), wirtinger(H, hn))
-    lam, _, _, st = g.adjoint_solve(L, tol=tol)
-    if st != 0:
-        raise FMBEMError(st, "adjoint solve did not converge")
+    x, force, _, _, _, lam = _force_adjoint(g, d, e, center, radius, n_theta, n_phi, tol)
     step = h if h is not None else 1e-5 * max(1.0, abs(eps[j]))
     ep, em = list(eps), list(eps)
     ep[j] += step
@@ -149,3 +157,17 @@ def force_eps_gradient(V, F, D, eps, mu, k0, d, e, j, center, radius, n_theta=24
     sv = torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()
     return force, -2 * sv.real, 2 * sv.imag
 
+
+def force_vertex_gradient(V, F, D, eps, mu, k0, d, e, center, radius, n_theta=24, n_phi=48, tol=1e-10, **options):
+    """(F [3], dF/dV [3, nv, 3]): the Maxwell-stress force of force_eps_gradient and its gradient
+    with respect to the mesh vertex positions (vertex nodes; the stress sphere stays fixed), by
+    one forward and three adjoint solves: dF_i/dV = 2 Re d/dV [N_i^T x + lambda_i^T b -
+    lambda_i^T A x] at fixed x and lambda_i, N_i the near-field functional of F_i's Wirtinger
+    coefficients (fmbem_shape_gradient_near)."""
+    g = FMBEM(V, F, D, eps, mu, k0, **options)
+    d = np.asarray(d, dtype=np.float64).reshape(1, 3)
+    e = np.asarray(e, dtype=np.complex128).reshape(1, 3)
+    x, force, pts, cE, cH, lam = _force_adjoint(g, d, e, center, radius, n_theta, n_phi, tol)
+    x3 = x.expand(3, -1, -1).contiguous()
+    out = g.shape_gradient_near(x3, lam, np.repeat(d, 3, 0), np.repeat(e, 3, 0), pts, cE, cH)
+    return force, 2 * out.real

@@ -841,3 +841,30 @@ def test_shape_gradient_matches_finite_differences_of_gpu_solves():
         fd = (cext(Vp) - cext(Vm)) / (2 * hstep)
         print("vertex", v, cc, g[0, v, cc], fd)
         assert abs(g[0, v, cc] - fd) < 2e-3 * np.abs(g[0]).max()
+
+
+def test_force_shape_gradient_matches_dense_reference():
+    """Maxwell-stress force on the smaller of two spheres: fmbem_shape_gradient_near given the
+    dense oracle's x, lambda_i and Wirtinger coefficients reproduces the oracle's adjoint vertex
+    gradient to the finite-difference error; the whole chain (forward and three adjoint FMM
+    solves at p = 12) to 1e-3 of the largest component."""
+    from oracle import shape_gradient as sg
+    from paper_1211_7177_gb300 import gradients as gr
+    m1 = fi.icosphere(1, 0.5, (-0.6, 0.0, 0.0), domain=1)
+    m2 = fi.icosphere(1, 0.3, (0.5, 0.1, 0.0), domain=2)
+    V, F, D = fi.merge_meshes(m1, m2)
+    eps, mu, k0 = [1.0, 2.25 + 0.1j, -4.0 + 0.5j], [1.0, 1.0, 1.0], 1.5
+    d = np.array([0.6, 0.0, 0.8])
+    e = np.array([0.8, 0.0, -0.6], dtype=np.complex128)
+    ctr, rad = np.array([0.5, 0.1, 0.0]), 0.42
+    Fo, go, xo, lo, pts, cE, cH = sg.force_vertex_gradient(V, F, D, eps, mu, k0, d, e, ctr, rad, return_state=True)
+    g = fm.FMBEM(V, F, D, eps, mu, k0)
+    out = g.shape_gradient_near(to_dev(np.repeat(xo[None], 3, 0)), to_dev(lo), np.repeat(d[None], 3, 0),
+                                np.repeat(e[None], 3, 0), pts, cE, cH)
+    ek = np.abs(2 * out.real - go).max() / np.abs(go).max()
+    Fg, gg = gr.force_vertex_gradient(V, F, D, eps, mu, k0, d, e, ctr, rad, n_theta=12, n_phi=24, tol=1e-12, p=12)
+    eg = np.abs(gg - go).max() / np.abs(go).max()
+    print("force", Fg, Fo, "gradient error: kernels", ek, "whole chain", eg)
+    assert ek < 1e-6
+    assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
+    assert eg < 1e-3
