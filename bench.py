@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-impedance", action="store_true", help="skip the impedance-boundary product")
+    ap.add_argument("--gradients", action="store_true",
+                    help="also time the adjoint gradients on the torus + sphere differentiation case")
     ap.add_argument("--restart", type=int, default=50, help="GMRES restart length of the timed solves")
     ap.add_argument("--n-rhs", type=int, default=0, help="right-hand sides (0 = the workload's)")
     return ap.parse_args()
@@ -244,6 +246,52 @@ def launches_per_matvec(lmax, nr, n_dom, precision):
     else:
         down = lmax - 1
     return 2 + (lmax - 2) + down + 1
+
+
+def run_gradients():
+    """Differentiation case: a silver-like torus (R = 1, r = 0.25, 256 x 64 grid, 32768 triangles,
+    eps = -10 + 0.4i) and a dielectric sphere (a = 0.1, eps = 2.5, 1280 triangles) a seeded gap
+    above the tube, k0 R = 1.5, one plane wave along -z.  Times the extinction's gradient with
+    respect to eps and to every vertex, and the Maxwell-stress force on the sphere with its vertex
+    gradient (forward and adjoint FMM solves included), and checks one sphere vertex of the force
+    gradient against central differences of full GPU solves."""
+    import torch
+
+    from paper_1211_7177_gb300 import gradients as gr
+    rng = np.random.default_rng(4)
+    gap, a = 0.05 + 0.25 * float(rng.random()), 0.1
+    ctr = np.array([1.0, 0.0, 0.25 + gap + a])
+    V, F, D = fi.merge_meshes(fi.torus(1.0, 0.25, 256, 64, domain=1), fi.icosphere(3, a, tuple(ctr), domain=2))
+    eps, mu, k0 = [1.0, -10 + 0.4j, 2.5], [1.0, 1.0, 1.0], 1.5
+    d = np.array([0.0, 0.0, -1.0])
+    e = np.array([1.0, 0.0, 0.0], dtype=np.complex128)
+    rad = a + 0.5 * gap
+    out = dict(nodes=len(V), gap=gap, stress_sphere_radius=rad)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c, de_re, de_im = gr.extinction_eps_gradient(V, F, D, eps, mu, k0, d[None], e[None], j=2, tol=1e-8)
+    torch.cuda.synchronize()
+    out["extinction_eps_gradient_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c, gV = gr.extinction_vertex_gradient(V, F, D, eps, mu, k0, d[None], e[None], tol=1e-8)
+    torch.cuda.synchronize()
+    out["extinction_vertex_gradient_s"] = time.perf_counter() - t0
+    out["cext"] = float(c[0])
+    t0 = time.perf_counter()
+    Fo, gF = gr.force_vertex_gradient(V, F, D, eps, mu, k0, d, e, ctr, rad, tol=1e-10)
+    torch.cuda.synchronize()
+    out["force_vertex_gradient_s"] = time.perf_counter() - t0
+    out["force"] = [float(v) for v in Fo]
+    # central difference of the force for one vertex of the sphere (its vertices follow the torus')
+    v, h = len(V) - 5, 1e-6
+    fd = []
+    for sgn in (1, -1):
+        Vx = V.copy()
+        Vx[v, 2] += sgn * h
+        fd.append(gr.force_vertex_gradient(Vx, F, D, eps, mu, k0, d, e, ctr, rad, tol=1e-12)[0])
+    out["force_fd_check"] = dict(vertex=int(v), coordinate="z", adjoint=[float(q) for q in gF[:, v, 2]],
+                                 central_difference=[float(q) for q in (fd[0] - fd[1]) / (2 * h)])
+    return out
 
 
 def run_ours(args):
@@ -413,6 +461,8 @@ def run_ours(args):
                                 relres=float(rr.max()), status=int(st), restart=args.restart, inner_tol=itol)
             h2.close()
 
+    gradients = run_gradients() if args.gradients and rank == 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rows = 1024 if nr == 1 else 16
@@ -430,7 +480,7 @@ def run_ours(args):
                             l2="flushed (256 MiB write) before each step", setup_s=setup_s, wall_s=wall),
                 e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes),
                 roofline=roof, other_precision=other, adjoint=adjoint, impedance=impedance, solve=solve,
-                cpu_baseline=cpu,
+                gradients=gradients, cpu_baseline=cpu,
                 gpu_launches=launches_per_step * args.steps, clocks=clk)
     if rank == 0:
         print(json.dumps(line), flush=True)
