@@ -97,6 +97,22 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value, device):
+    """The largest of the ranks' values (all ranks get it); the value itself with one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job rate: the units every rank processed in ms milliseconds (the slowest rank's)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def rhs_batch(n_rhs):
     if n_rhs == 1:
         return np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]], dtype=np.complex128)
@@ -344,15 +360,11 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         clk = sampler.stop() if sampler else None
-        ms = statistics.mean(a.elapsed_time(bb) for a, bb in ev)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(statistics.mean(a.elapsed_time(bb) for a, bb in ev), "cuda")
         return ms, phases, wall, clk
 
     ms_step, phases, wall, clk = timed(prec, args.steps, args.warmup, clocks=True)
-    value = world * N * nr / (ms_step * 1e-3)
+    value = job_throughput(N * nr, world, ms_step)
     roof = roofline(info, p, nr, n_dom, phases, args.precision)
 
     # e2e through the C ABI: pinned host x -> device, matvec, device -> pinned host y
