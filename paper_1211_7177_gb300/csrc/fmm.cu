@@ -1036,7 +1036,7 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                                               const int32_t *dom, const int32_t *perm, const cx<R> *dens,
                                               const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
                                               const c64 *x, c64 *y, const int64_t *cache_base,
-                                              const V4<R> *cache) {
+                                              const V4<R> *cache, bool side1) {
     __shared__ NearSmem<R> S;
     __shared__ int rng_beg[32], rng_cum[33];
     SrcTile<R> &T = S.tile;
@@ -1096,7 +1096,7 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                 }
                 __syncthreads();
                 const int ns = min(128, nsrc - s0);
-                const R adom_r = (R)adom;
+                const R adom_r = side1 ? (R)adom : (R)-1;  // -1: no scatterer-side pairs (impedance boundary)
                 // cached pair scalars of this target: [side][source][target] within the leaf's block
                 const int NT = t1 - t0;
                 const V4<R> *cs0 = cache ? cache + 2 * cache_base[blockIdx.x] + (tb - t0 + tg) : nullptr;
@@ -1244,7 +1244,8 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
                                                  const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
                                                  const R *nrm, const int32_t *dom, const int32_t *perm,
                                                  const cx<R> *dens, const DomainConsts *dc, const cx<R> *Bl2p,
-                                                 const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y) {
+                                                 const cx<R> *D, const c64 *Mself, const c64 *x, c64 *y,
+                                                 bool side1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     NearSmemRB<R, RB> &S = *reinterpret_cast<NearSmemRB<R, RB> *>(smem_raw);
     SrcTileRB<R, RB> &T = S.tile;
@@ -1276,7 +1277,7 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
             R ax = pos_hi[3 * a], ay = pos_hi[3 * a + 1], az = pos_hi[3 * a + 2], alx = 0, aly = 0, alz = 0;
             if (DOUBLE_FLOAT) { alx = pos_lo[3 * a]; aly = pos_lo[3 * a + 1]; alz = pos_lo[3 * a + 2]; }
             const int adom = dom[a];
-            const R adom_r = (R)adom;
+            const R adom_r = side1 ? (R)adom : (R)-1;
             const cx<R> kb = to<R>(dc[0].k), kj = to<R>(dc[adom].k);
             cx<R> acc0[RB][3], acc1[RB][3];
 #pragma unroll
@@ -2816,18 +2817,19 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
         } else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
             k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                           h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens,
-                                                          dc, Bl2p, D, h->Mself, x, y, nullptr, nullptr);
+                                                          dc, Bl2p, D, h->Mself, x, y, nullptr, nullptr, !h->ibc);
     } else if (nr >= 4) {
         constexpr int RBLK = 2;
         const size_t smn = sizeof(NearSmemRB<R, RBLK>);
         CK(cudaFuncSetAttribute(k_near_rb<R, false, RBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn));
         k_near_rb<R, false, RBLK><<<dim3((unsigned)L.n, (unsigned)((nr + RBLK - 1) / RBLK)), 128, smn, s>>>(
             L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm,
-            dens, dc, Bl2p, D, h->Mself, x, y);
+            dens, dc, Bl2p, D, h->Mself, x, y, !h->ibc);
     } else {
         k_near<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
                                                        h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D,
-                                                       h->Mself, x, y, h->near_base, (const V4<R> *)h->near_cache64);
+                                                       h->Mself, x, y, h->near_base, (const V4<R> *)h->near_cache64,
+                                                       !h->ibc);
     }
     CKL("k_near");
     if (h->ibc) {  // impedance boundary: the scatterer rows are the local relation of Eq. (2.24)
