@@ -338,6 +338,17 @@ fmbem_status fmbem_shape_gradient_near(fmbem *h, const void *x_dev, const void *
 fmbem_status fmbem_interior_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
                                   const int32_t *domain, fmbem_c64 *E_host, fmbem_c64 *H_host, void *stream);
 
+/* The fields of fmbem_near_field through the fast multipole passes, for maps with many points:
+ * one FP64 product of x (Eqs. 2.18-2.21) leaves the local expansions of the background domain
+ * at every leaf; a point inside a leaf takes the far sources from that leaf's expansion (first
+ * term of Eq. 2.23 at the point, and its gradient for H) and the sources of the leaf and its
+ * Neighbor leaves directly; a point outside every (non-empty) leaf sums all nodes directly.
+ * Arguments, layout and errors as fmbem_near_field; the result differs from it by the multipole
+ * truncation error. */
+fmbem_status fmbem_near_field_fmm(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
+                                  const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, fmbem_c64 *H_host,
+                                  void *stream);
+
 /* The exterior fields as linear functionals of the solution, for adjoint gradients of
  * quantities built from them (the optical force of a Maxwell-stress surface): out[f] holds the
  * coefficients of x -> sum_p ( cE[f][p] . E_sca(r_p) + cH[f][p] . H_sca(r_p) ) with E_sca, H_sca

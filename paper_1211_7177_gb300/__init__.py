@@ -82,6 +82,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_far_field": (i32, [P, P, i64, i64, P, P, P]),
         "fmbem_absorption": (i32, [P, P, i64, P, P]),
         "fmbem_near_field": (i32, [P, P, i64, i64, P, P, P, P, P, P]),
+        "fmbem_near_field_fmm": (i32, [P, P, i64, i64, P, P, P, P, P, P]),
         "fmbem_far_field_functional": (i32, [P, i64, P, P, P, P]),
         "fmbem_interior_field": (i32, [P, P, i64, i64, P, P, P, P, P]),
         "fmbem_shape_gradient": (i32, [P, P, P, i64, P, P, P, P, P, P]),
@@ -245,10 +246,11 @@ def fmbem_far_field(h, x, rhat, stream=None):
     return F
 
 
-def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None, magnetic=False):
+def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None, magnetic=False, fmm=False):
     """Total field E [n_rhs, n_pts, 3] complex128 (host) at exterior points of solutions x of the
     plane waves (dirs[r], pols[r]); scattered field alone when dirs and pols are None.  With
-    magnetic=True returns (E, H), H = curl E / (i k0 mu_0)."""
+    magnetic=True returns (E, H), H = curl E / (i k0 mu_0).  fmm=True evaluates through the fast
+    multipole passes (fmbem_near_field_fmm) instead of the direct sum."""
     N = fmbem_num_nodes(h)
     x = _dev(x, N, "x")
     n = x.shape[0]
@@ -261,10 +263,9 @@ def fmbem_near_field(h, x, points, dirs=None, pols=None, stream=None, magnetic=F
         p = np.ascontiguousarray(np.broadcast_to(np.asarray(pols, dtype=np.complex128), (n, 3)))
     E = np.empty((n, len(pts), 3), dtype=np.complex128)
     H = np.empty((n, len(pts), 3), dtype=np.complex128) if magnetic else None
-    _check(h, load_library().fmbem_near_field(h, ctypes.c_void_p(x.data_ptr()), n, len(pts), _ptr(pts),
-                                              _ptr(d) if d is not None else None,
-                                              _ptr(p) if p is not None else None, _ptr(E),
-                                              _ptr(H) if H is not None else None, _stream(stream)))
+    fn = load_library().fmbem_near_field_fmm if fmm else load_library().fmbem_near_field
+    _check(h, fn(h, ctypes.c_void_p(x.data_ptr()), n, len(pts), _ptr(pts), _ptr(d) if d is not None else None,
+                 _ptr(p) if p is not None else None, _ptr(E), _ptr(H) if H is not None else None, _stream(stream)))
     return (E, H) if magnetic else E
 
 
@@ -462,8 +463,8 @@ class FMBEM:
     def far_field(self, x, rhat, stream=None):
         return fmbem_far_field(self.h, x, rhat, stream)
 
-    def near_field(self, x, points, dirs=None, pols=None, stream=None, magnetic=False):
-        return fmbem_near_field(self.h, x, points, dirs, pols, stream, magnetic)
+    def near_field(self, x, points, dirs=None, pols=None, stream=None, magnetic=False, fmm=False):
+        return fmbem_near_field(self.h, x, points, dirs, pols, stream, magnetic, fmm)
 
     def interior_field(self, x, points, domain, stream=None, magnetic=False):
         return fmbem_interior_field(self.h, x, points, domain, stream, magnetic)

@@ -355,6 +355,20 @@ fmbem_status fmbem_shape_gradient_near(fmbem *h, const void *x_dev, const void *
     });
 }
 
+fmbem_status fmbem_near_field_fmm(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
+                                  const double *dir, const fmbem_c64 *pol, fmbem_c64 *E_host, fmbem_c64 *H_host,
+                                  void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_pts < 1 || !x_dev || !pts || !E_host || n_rhs > 65535 || (!dir) != (!pol)) {
+        h->err = "invalid argument (n_rhs in 1..65535, n_pts >= 1, non-NULL x, pts and E; dir and pol both or neither)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_near_field_fmm(h, (const c64 *)x_dev, n_rhs, n_pts, pts, dir, (const c64 *)pol, (c64 *)E_host,
+                           (c64 *)H_host, (cudaStream_t)stream);
+    });
+}
+
 fmbem_status fmbem_interior_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_t n_pts, const double *pts,
                                   const int32_t *domain, fmbem_c64 *E_host, fmbem_c64 *H_host, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;

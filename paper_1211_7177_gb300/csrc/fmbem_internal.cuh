@@ -281,6 +281,9 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
                         cudaStream_t s);
 void run_vertex_shape_grad(fmbem *h, int64_t nr, const c64 *x, const c64 *lam, const c64 *sens, double hv, c64 *out,
                            cudaStream_t s);
+void run_near_field_fmm(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host,
+                        const double *dir_host, const c64 *pol_host, c64 *E_host, c64 *H_host, cudaStream_t s);
+void run_locate_leaves(fmbem *h, const double *pts_dev, int64_t n, int32_t *leaf_dev, cudaStream_t s);
 void run_interior_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host,
                         const int32_t *dom_host, c64 *E_host, c64 *H_host, cudaStream_t s);
 void run_near_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host, const double *dir_host,

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fmbem_internal.cuh"
+#include "special.cuh"
 
 namespace {
 
@@ -262,6 +263,119 @@ __global__ void __launch_bounds__(OB_NT) k_interior_field(int64_t N, const doubl
     }
 }
 
+// one source node's term of the exterior representation formula at the point t (and its curl):
+// w [n0 (a.Phi) - (n0.a) Phi - a (n0.Phi) + g Psi], n0 = -n, a = grad_s g (as k_near_field)
+template <bool WITH_H>
+__device__ void exterior_term(const double *t, const double *s, const double *n, double w, const c64 *Phi,
+                              const c64 *Psi, c64 ik, c64 *acc, c64 *cur) {
+    const double rv[3] = {s[0] - t[0], s[1] - t[1], s[2] - t[2]};
+    const double R = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+    const c64 g = cexpd(ik * R) * (1.0 / (4.0 * FMBEM_PI * R));
+    const c64 g1 = g * (ik - c64{1.0 / R, 0});
+    const c64 c = g1 * (1.0 / R);
+    const double n0[3] = {-n[0], -n[1], -n[2]};
+    const c64 rP = rv[0] * Phi[0] + rv[1] * Phi[1] + rv[2] * Phi[2];
+    const c64 nP = n0[0] * Phi[0] + n0[1] * Phi[1] + n0[2] * Phi[2];
+    const double nr = n0[0] * rv[0] + n0[1] * rv[1] + n0[2] * rv[2];
+    for (int q = 0; q < 3; ++q) acc[q] += w * (c * (n0[q] * rP - nr * Phi[q] - rv[q] * nP) + g * Psi[q]);
+    if (WITH_H) {
+        const double iR = 1.0 / R, rh[3] = {rv[0] * iR, rv[1] * iR, rv[2] * iR};
+        const c64 q1 = ik - c64{iR, 0};
+        const c64 g2 = g * (q1 * q1 + c64{iR * iR, 0});
+        const double rn = rh[0] * n0[0] + rh[1] * n0[1] + rh[2] * n0[2];
+        const c64 rhP = rP * iR;
+        c64 Kn[3], KP[3], av[3];
+        for (int q = 0; q < 3; ++q) {
+            Kn[q] = g2 * (rh[q] * rn) + c * (n0[q] - rh[q] * rn);
+            KP[q] = g2 * rhP * rh[q] + c * (Phi[q] - rhP * rh[q]);
+            av[q] = g1 * rh[q];
+        }
+        cur[0] += w * (Kn[1] * Phi[2] - Kn[2] * Phi[1] + n0[1] * KP[2] - n0[2] * KP[1] - (av[1] * Psi[2] - av[2] * Psi[1]));
+        cur[1] += w * (Kn[2] * Phi[0] - Kn[0] * Phi[2] + n0[2] * KP[0] - n0[0] * KP[2] - (av[2] * Psi[0] - av[0] * Psi[2]));
+        cur[2] += w * (Kn[0] * Phi[1] - Kn[1] * Phi[0] + n0[0] * KP[1] - n0[1] * KP[0] - (av[0] * Psi[1] - av[1] * Psi[0]));
+    }
+}
+
+// Exterior fields through the fast multipole passes (see fmbem_near_field_fmm): a point in leaf g
+// takes the far sources from g's local expansion of the background domain (the matvec's D, whose
+// L2P gives minus the scattered field: the background rows carry the representation formula with
+// the opposite sign), and the sources of g and its Neighbor leaves directly; a point outside
+// every leaf sums all nodes directly.  Thread per (point, rhs).
+constexpr int FF_PMAX = 20;
+template <bool WITH_H>
+__global__ void __launch_bounds__(128) k_field_fmm(int64_t N, int64_t nr, int p, int64_t nbox, int64_t leaf_off,
+                                                 const int32_t *leaf_of, const double *box_ctr,
+                                                 const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                                 const int32_t *nbr_idx, const double *spos, const double *snrm,
+                                                 const double *sw, const int32_t *perm, const double *upos,
+                                                 const double *unrm, const double *uw, const c64 *x, const c64 *D,
+                                                 double lam, int64_t n_pts, const double *pts, c64 k0, c64 iwmu,
+                                                 const double *dir, const c64 *pol, c64 *E, c64 *H) {
+    const int64_t pt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (pt >= n_pts) return;
+    const double t[3] = {pts[3 * pt], pts[3 * pt + 1], pts[3 * pt + 2]};
+    const c64 ik = {-k0.im, k0.re};
+    c64 acc[3] = {{0, 0}, {0, 0}, {0, 0}}, cur[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (dir != nullptr && pol != nullptr) {
+        const double *d = dir + 3 * r;
+        const c64 *e = pol + 3 * r;
+        const c64 ph = cexpd(ik * (d[0] * t[0] + d[1] * t[1] + d[2] * t[2]));
+        for (int q = 0; q < 3; ++q) acc[q] = e[q] * ph;
+        if (WITH_H) {
+            const c64 de[3] = {d[1] * e[2] - d[2] * e[1], d[2] * e[0] - d[0] * e[2], d[0] * e[1] - d[1] * e[0]};
+            for (int q = 0; q < 3; ++q) cur[q] = ik * de[q] * ph;
+        }
+    }
+    const int32_t lf = leaf_of[pt];
+    if (lf < 0) {
+        for (int64_t b = 0; b < N; ++b)
+            exterior_term<WITH_H>(t, upos + 3 * b, unrm + 3 * b, uw[b], x + (r * N + b) * 6, x + (r * N + b) * 6 + 3, ik,
+                                  acc, cur);
+    } else {
+        const int64_t g = leaf_off + lf;
+        for (int q = nbr_start[lf]; q < nbr_start[lf + 1]; ++q) {
+            const int32_t bx = nbr_idx[q];
+            for (int i = nbeg[bx]; i < nend[bx]; ++i) {
+                const c64 *xb = x + (r * N + perm[i]) * 6;
+                exterior_term<WITH_H>(t, spos + 3 * i, snrm + 3 * i, sw[i], xb, xb + 3, ik, acc, cur);
+            }
+        }
+        // L2P: sum_q D_q R_q(t - c) / lambda^n (and its gradient), subtracted
+        const double *c = box_ctr + 3 * g;
+        const double rl[3] = {t[0] - c[0], t[1] - c[1], t[2] - c[2]};
+        c64 R[(FF_PMAX + 1) * (FF_PMAX + 1)], rad[FF_PMAX + 2];
+        double Pb[(FF_PMAX + 2) * (FF_PMAX + 3) / 2];
+        wave_functions<false>(p, k0, rl, R, rad, Pb);
+        const int p2 = p * p;
+        const c64 *Dg = D + (g * 3 * nr + 3 * r) * p2;  // background domain (d = 0)
+        c64 grad[3][3] = {{{0, 0}, {0, 0}, {0, 0}}, {{0, 0}, {0, 0}, {0, 0}}, {{0, 0}, {0, 0}, {0, 0}}};  // [component][axis]
+        double lpow = 1.0;
+        for (int n = 0; n < p; ++n) {
+            const double sc = 1.0 / lpow;
+            for (int m = -n; m <= n; ++m) {
+                const int qi = n * n + n + m;
+                c64 gr[3];
+                if (WITH_H) grad_regular(p, k0, R, n, m, gr);
+                for (int comp = 0; comp < 3; ++comp) {
+                    const c64 dq = Dg[comp * p2 + qi] * sc;
+                    acc[comp] -= dq * R[qi];
+                    if (WITH_H)
+                        for (int a = 0; a < 3; ++a) grad[comp][a] += dq * gr[a];
+                }
+            }
+            lpow *= lam;
+        }
+        if (WITH_H) {  // curl of -sum: subtract the curl of the expansion's field
+            cur[0] -= grad[2][1] - grad[1][2];
+            cur[1] -= grad[0][2] - grad[2][0];
+            cur[2] -= grad[1][0] - grad[0][1];
+        }
+    }
+    for (int q = 0; q < 3; ++q) E[(r * n_pts + pt) * 3 + q] = acc[q];
+    if (WITH_H)
+        for (int q = 0; q < 3; ++q) H[(r * n_pts + pt) * 3 + q] = cdiv(cur[q], iwmu);
+}
+
 // Transposed near-field map (for adjoint gradients of quantities built from exterior fields):
 // out[f][b] = sum_p ( cE[f][p] . dE(r_p)/dx_b + cH[f][p] . dH(r_p)/dx_b ), with E, H as in
 // k_near_field (no incident part: it does not depend on x).  For c = cE[f][p]:
@@ -449,6 +563,56 @@ void run_interior_field(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const
             k_interior_field<false><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, h->udom, x, n_pts, dp, dd,
                                                            dcon, dE, nullptr);
         CKL("k_interior_field");
+        CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
+        if (dH) CK(cudaMemcpyAsync(H_host, dH, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+void run_near_field_fmm(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const double *pts_host,
+                        const double *dir_host, const c64 *pol_host, c64 *E_host, c64 *H_host, cudaStream_t s) {
+    if (h->p > FF_PMAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "p above the supported maximum"};
+    c64 *yscr = (c64 *)dev_alloc(h, sizeof(c64) * 6 * h->N * nr);
+    double *dp = (double *)dev_alloc(h, sizeof(double) * 3 * n_pts);
+    int32_t *dl = (int32_t *)dev_alloc(h, sizeof(int32_t) * n_pts);
+    c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr);
+    c64 *dH = H_host ? (c64 *)dev_alloc(h, sizeof(c64) * 3 * n_pts * nr) : nullptr;
+    double *dd = nullptr;
+    c64 *dpol = nullptr;
+    auto cleanup = [&] {
+        for (void *q : {(void *)yscr, (void *)dp, (void *)dl, (void *)dE, (void *)dH, (void *)dd, (void *)dpol})
+            if (q) dev_free(h, q);
+    };
+    try {
+        // the passes of one FP64 product leave the local expansions of x's background sums in D
+        run_matvec(h, x, yscr, nr, FMBEM_FP64, s);
+        CK(cudaMemcpyAsync(dp, pts_host, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, s));
+        if (dir_host && pol_host) {
+            dd = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
+            dpol = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
+            CK(cudaMemcpyAsync(dd, dir_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(dpol, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        }
+        run_locate_leaves(h, dp, n_pts, dl, s);
+        const LevelInfo &L = h->lev[h->lmax];
+        const double lam = h->lam[h->lmax];  // domain 0, leaf level
+        const c64 iwmu = c64{0, h->k0} * h->mu[0];
+        const dim3 grid((unsigned)((n_pts + 127) / 128), (unsigned)nr);
+        if (dH)
+            k_field_fmm<true><<<grid, 128, 0, s>>>(h->N, nr, h->p, h->nbox, L.off, dl, h->box_ctr, h->box_nbeg,
+                                                   h->box_nend, h->nbr_start, h->nbr_idx, h->pos, h->nrm, h->w,
+                                                   h->perm, h->upos, h->unrm, h->uw, x, (const c64 *)h->Dexp, lam,
+                                                   n_pts, dp, h->k[0], iwmu, dd, dpol, dE, dH);
+        else
+            k_field_fmm<false><<<grid, 128, 0, s>>>(h->N, nr, h->p, h->nbox, L.off, dl, h->box_ctr, h->box_nbeg,
+                                                    h->box_nend, h->nbr_start, h->nbr_idx, h->pos, h->nrm, h->w,
+                                                    h->perm, h->upos, h->unrm, h->uw, x, (const c64 *)h->Dexp, lam,
+                                                    n_pts, dp, h->k[0], iwmu, dd, dpol, dE, nullptr);
+        CKL("k_field_fmm");
         CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
         if (dH) CK(cudaMemcpyAsync(H_host, dH, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

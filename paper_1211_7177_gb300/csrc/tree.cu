@@ -312,7 +312,45 @@ __global__ void k_add_offset(int32_t *a, int64_t n, int32_t off) {
 
 inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
+// the leaf (index within level lmax) containing each point, or -1 when the point lies outside
+// the root cube or in an empty box: the key of the point's box at level lmax (as k_keys, without
+// clamping) looked up by bisection among the sorted leaf keys
+__global__ void k_locate_leaf(int64_t n, const double *pts, double x0, double y0, double z0, double inv_w,
+                              int shift, const uint64_t *leaf_key, int64_t nleaf, int32_t *leaf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int M = 1 << KEY_LEVELS;
+    const double o[3] = {x0, y0, z0};
+    uint32_t c[3];
+    bool inside = true;
+    for (int q = 0; q < 3; ++q) {
+        const double t = floor((pts[3 * i + q] - o[q]) * inv_w);
+        inside = inside && t >= 0.0 && t < (double)M;
+        c[q] = inside ? (uint32_t)t : 0u;
+    }
+    int32_t found = -1;
+    if (inside) {
+        const uint64_t key = morton(c[0], c[1], c[2]) >> shift;
+        int64_t lo = 0, hi = nleaf;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (leaf_key[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nleaf && leaf_key[lo] == key) found = (int32_t)lo;
+    }
+    leaf[i] = found;
+}
+
 }  // namespace
+
+void run_locate_leaves(fmbem *h, const double *pts_dev, int64_t n, int32_t *leaf_dev, cudaStream_t s) {
+    const LevelInfo &L = h->lev[h->lmax];
+    k_locate_leaf<<<nblk(n, 128), 128, 0, s>>>(n, pts_dev, h->root_min[0], h->root_min[1], h->root_min[2],
+                                               (double)(1 << KEY_LEVELS) / h->root_w, 3 * (KEY_LEVELS - h->lmax),
+                                               h->box_key + L.off, L.n, leaf_dev);
+    CKL("k_locate_leaf");
+}
 
 void build_tree(fmbem *h, cudaStream_t s) {
     const int64_t N = h->N;

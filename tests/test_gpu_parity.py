@@ -868,3 +868,27 @@ def test_force_shape_gradient_matches_dense_reference():
     assert ek < 1e-6
     assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
     assert eg < 1e-3
+
+
+def test_near_field_through_the_fmm_matches_direct_sum(sphere_s4):
+    """Exterior E and H through the multipole passes (leaf local expansions + the leaf's Neighbor
+    sources) against the direct FP64 sum, for points 3 % off the surface (inside the leaves) and
+    points outside the root cube (direct fallback), two right-hand sides; also at p = 10 (the
+    rotation-form translations) on the same sphere."""
+    o, g = sphere_s4
+    rng = np.random.default_rng(41)
+    pos, nrm, w = g.node_geometry()
+    near = 1.03 * pos[rng.choice(len(pos), 200, replace=False)]
+    far = rng.normal(size=(20, 3))
+    far *= 3.0 / np.linalg.norm(far, axis=1, keepdims=True)
+    pts = np.concatenate([near, far])
+    dirs, pols = fi.plane_wave_batch(1, seed=5)
+    x, _, _, st = g.solve(g.plane_wave_rhs(dirs, pols), tol=1e-8)
+    assert st == 0
+    for h in (g, fm.FMBEM(*fi.icosphere(4), [1.0, 2.25], [1.0, 1.0], 1.0, p=10)):
+        E0, H0 = h.near_field(x, pts, dirs, pols, magnetic=True)
+        E1, H1 = h.near_field(x, pts, dirs, pols, magnetic=True, fmm=True)
+        Es0 = h.near_field(x, pts, magnetic=False)
+        Es1 = h.near_field(x, pts, magnetic=False, fmm=True)
+        print("FMM near field: E", rel(E1, E0), "H", rel(H1, H0), "scattered", rel(Es1, Es0))
+        assert rel(E1, E0) < MATVEC_TOL and rel(H1, H0) < MATVEC_TOL and rel(Es1, Es0) < MATVEC_TOL
