@@ -72,6 +72,28 @@ def test_invalid_arguments_rejected():
     assert e.value.status == 1
 
 
+def test_boundary_option_and_null_handles_rejected():
+    """The boundary option defaults to the penetrable formulation and an unknown value is refused
+    before any device work; every entry point that takes a handle refuses NULL."""
+    o = fm.fmbem_default_options()
+    assert o.boundary == fm.PENETRABLE
+    V, F, D = fi.icosphere(1)
+    with pytest.raises(fm.FMBEMError) as e:
+        _create(V, F, D, boundary=7)
+    assert e.value.status == 1
+    lib = fm.load_library()
+    N = None
+    z = np.zeros(3)
+    zc = np.zeros(3, dtype=np.complex128)
+    p3 = z.ctypes.data
+    pc = zc.ctypes.data
+    assert lib.fmbem_shape_gradient(N, 1, 1, 1, p3, pc, p3, pc, pc, None) == 1
+    assert lib.fmbem_shape_gradient_near(N, 1, 1, 1, p3, pc, 1, p3, pc, None, pc, None) == 1
+    assert lib.fmbem_interior_field(N, 1, 1, 1, p3, p3, pc, None, None) == 1
+    assert lib.fmbem_near_field_fmm(N, 1, 1, 1, p3, None, None, pc, None, None) == 1
+    assert lib.fmbem_near_field(N, 1, 1, 1, p3, None, None, pc, None, None) == 1
+
+
 def test_binding_declares_every_signature():
     """Every entry point declared in include/fmbem.h gets its ctypes signature (argument types)
     from the binding when the library is loaded, so scalars such as tolerances convert."""
