@@ -129,6 +129,13 @@ typedef struct {
 
 void fmbem_default_options(fmbem_options *opt);
 
+/* Fault injection for tests of the out-of-memory paths: after this call, device allocations
+ * of the library (all handles, all threads) may take `bytes` more bytes in total; one that would
+ * exceed the budget fails as if cudaMalloc had, and the call that made it returns FMBEM_ERR_OOM
+ * with the handle's resources released (fmbem_create) or left as before the call.  A negative
+ * value removes the budget (the default). */
+void fmbem_debug_set_device_budget(int64_t bytes);
+
 typedef struct fmbem fmbem;  /* opaque handle */
 
 /* Builds everything that depends on geometry and frequency, Sections 2.1-2.2 and Appendices

@@ -67,6 +67,7 @@ def load_library(build_if_missing: bool = True):
     P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     sig = {
         "fmbem_default_options": (None, [ctypes.POINTER(Options)]),
+        "fmbem_debug_set_device_budget": (None, [i64]),
         "fmbem_create": (i32, [ctypes.POINTER(Mesh), P, P, dbl, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
         "fmbem_destroy": (None, [P]),
         "fmbem_last_error": (ctypes.c_char_p, [P]),

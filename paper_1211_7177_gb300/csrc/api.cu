@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/fmbem.h: argument checks, handle life cycle and error capture.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -12,9 +13,20 @@ std::string cuda_msg(cudaError_t e, const char *what) {
     return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
 }
 
+// device bytes that later allocations may still take (fault injection, fmbem_debug_set_device_budget);
+// negative: unlimited
+static std::atomic<int64_t> g_device_budget{-1};
+
 void *dev_alloc(fmbem *h, size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    for (int64_t left = g_device_budget.load(); left >= 0;) {
+        if ((int64_t)bytes > left)
+            throw fmbem_error{FMBEM_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                                 " bytes refused: the injected budget has " + std::to_string(left) +
+                                                 " bytes left"};
+        if (g_device_budget.compare_exchange_weak(left, left - (int64_t)bytes)) break;
+    }
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -81,6 +93,8 @@ static c64 principal_root(c64 z) {
 }
 
 extern "C" {
+
+void fmbem_debug_set_device_budget(int64_t bytes) { g_device_budget.store(bytes < 0 ? -1 : bytes); }
 
 void fmbem_default_options(fmbem_options *o) {
     if (!o) return;

@@ -94,6 +94,21 @@ def test_boundary_option_and_null_handles_rejected():
     assert lib.fmbem_near_field(N, 1, 1, 1, p3, None, None, pc, None, None) == 1
 
 
+def test_injected_device_budget_fails_create_with_oom():
+    """Fault injection on the host: with a device budget smaller than the first allocation,
+    fmbem_create fails with FMBEM_ERR_OOM and a message naming the budget, after the mesh has
+    been validated and before any device work."""
+    V, F, D = fi.icosphere(1)
+    lib = fm.load_library()
+    lib.fmbem_debug_set_device_budget(0)
+    try:
+        with pytest.raises(fm.FMBEMError) as e:
+            _create(V, F, D)
+        assert e.value.status == 3 and "budget" in str(e.value)
+    finally:
+        lib.fmbem_debug_set_device_budget(-1)
+
+
 def test_binding_declares_every_signature():
     """Every entry point declared in include/fmbem.h gets its ctypes signature (argument types)
     from the binding when the library is loaded, so scalars such as tolerances convert."""
