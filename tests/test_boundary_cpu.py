@@ -115,3 +115,45 @@ def test_binding_declares_every_signature():
     lib = fm.load_library()
     missing = [n for n in fm.header_functions() if getattr(lib, n).argtypes is None]
     assert not missing, missing
+
+
+def test_header_is_plain_c_and_a_c_program_links(tmp_path):
+    """include/fmbem.h compiles as C99 (no C++ types in the signatures), and a C program linked
+    against the library runs the host-side entry points: default options, and the refusal of an
+    open mesh before any device work."""
+    import os
+    import shutil
+    import subprocess
+    from paper_1211_7177_gb300 import build as b
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    fm.load_library()
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "fmbem.h"
+int main(void) {
+    fmbem_options o;
+    fmbem_default_options(&o);
+    double V[12] = {0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1};
+    int32_t F[9] = {0, 2, 1, 0, 1, 3, 0, 3, 2};   /* three faces of a tetrahedron: open */
+    int32_t D[3] = {1, 1, 1};
+    fmbem_mesh m = {4, V, 3, F, D, 1};
+    fmbem_c64 eps[2] = {{1.0, 0.0}, {2.25, 0.0}}, mu[2] = {{1.0, 0.0}, {1.0, 0.0}};
+    fmbem *h = NULL;
+    fmbem_status st = fmbem_create(&m, eps, mu, 1.0, &o, NULL, &h);
+    printf("%d %d %d %d %s\n", o.p, o.leaf_size, (int)st, h == NULL, fmbem_last_error(NULL));
+    return 0;
+}
+""")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(b.LIB)
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", include, str(src), "-o", str(exe), b.LIB,
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    p, leaf, st, null, *msg = out.stdout.split(maxsplit=4)
+    assert (p, leaf, st, null) == ("8", "64", "2", "1"), out.stdout
