@@ -274,10 +274,8 @@ def run_gradients():
     import torch
 
     from paper_1211_7177_gb300 import gradients as gr
-    rng = np.random.default_rng(4)
-    gap, a = 0.05 + 0.25 * float(rng.random()), 0.1
-    ctr = np.array([1.0, 0.0, 0.25 + gap + a])
-    V, F, D = fi.merge_meshes(fi.torus(1.0, 0.25, 256, 64, domain=1), fi.icosphere(3, a, tuple(ctr), domain=2))
+    a = 0.1
+    (V, F, D), gap, ctr = fi.torus_and_sphere(seed=4, a=a)
     eps, mu, k0 = [1.0, -10 + 0.4j, 2.5], [1.0, 1.0, 1.0], 1.5
     d = np.array([0.0, 0.0, -1.0])
     e = np.array([1.0, 0.0, 0.0], dtype=np.complex128)

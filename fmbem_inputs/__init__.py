@@ -162,6 +162,17 @@ def merge_meshes(*meshes):
     return np.concatenate(Vs), np.concatenate(Fs).astype(np.int32), np.concatenate(Ds).astype(np.int32)
 
 
+def torus_and_sphere(seed: int = 4, nu: int = 256, nv: int = 64, a: float = 0.1, sphere_subdiv: int = 3):
+    """The differentiation case: a torus (R = 1, r = 0.25, ``nu x nv`` grid, domain 1) and a sphere
+    of radius ``a`` (domain 2) centred above the top of the tube at a seeded gap, uniform in
+    0.05-0.3.  Returns ((V, F, D), gap, centre of the sphere)."""
+    rng = np.random.default_rng(seed)
+    gap = 0.05 + 0.25 * float(rng.random())
+    ctr = (1.0, 0.0, 0.25 + gap + a)
+    mesh = merge_meshes(torus(1.0, 0.25, nu, nv, domain=1), icosphere(sphere_subdiv, a, ctr, domain=2))
+    return mesh, gap, np.asarray(ctr)
+
+
 def _random_rotation(rng):
     q = rng.normal(size=4)
     q /= np.linalg.norm(q)
