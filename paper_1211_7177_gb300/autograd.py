@@ -1,4 +1,5 @@
-"""Differentiable wrappers of the FMM-BEM product and solve for torch.autograd.
+"""Differentiable wrappers of the FMM-BEM product and solve, and of the extinction cross section
+as a function of the vertex positions and permittivities, for torch.autograd.
 
 The operator A (Eq. 2.9) is fixed by the handle; these functions are differentiable with respect
 to their vector argument.  PyTorch's convention for complex tensors makes the gradient of a real
@@ -53,3 +54,67 @@ def matvec(handle, x, precision=FP64):
 def solve(handle, b, tol=1e-8, max_iter=1000):
     """x = A^-1 b by GMRES, differentiable in b; the backward pass is one adjoint solve."""
     return _Solve.apply(b, handle, tol, max_iter)
+
+
+class _Extinction(torch.autograd.Function):
+    """C_ext [n_rhs] of the plane waves (dirs, pols) on the mesh with vertex positions V and
+    permittivities eps; differentiable in V (through fmbem_shape_gradient) and in eps (through
+    the operator's central difference in each eps_j, as gradients.extinction_eps_gradient)."""
+
+    @staticmethod
+    def forward(ctx, V, eps, F, D, mu, k0, dirs, pols, options):
+        import numpy as np
+
+        from . import FMBEM
+        Vn = V.detach().cpu().numpy().astype(np.float64)
+        en = [complex(v) for v in eps.detach().cpu().numpy()]
+        g = FMBEM(Vn, F, D, en, mu, k0, **options)
+        x, _, _, st = g.solve(g.plane_wave_rhs(dirs, pols), tol=1e-10)
+        if st != 0:
+            raise FMBEMError(st, "forward solve did not converge")
+        coef = 4 * np.pi / g.kb.real * np.conj(pols)
+        L = g.far_field_functional(dirs, coef)
+        cext = torch.sum(L * x, dim=(1, 2)).imag
+        ctx.state = (g, x, L, coef, Vn, en, F, D, mu, k0, dirs, pols, options)
+        ctx.devices = (V.device, eps.device)
+        return cext.to(device=V.device, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, go):
+        import numpy as np
+
+        from . import FMBEM
+        g, x, L, coef, Vn, en, F, D, mu, k0, dirs, pols, options = ctx.state
+        lam, _, _, st = g.adjoint_solve(L, tol=1e-10)
+        if st != 0:
+            raise FMBEMError(st, "adjoint solve did not converge")
+        w = go.detach().cpu().numpy().astype(np.float64)  # dLoss/dC_ext[r]
+        gV = geps = None
+        if ctx.needs_input_grad[0]:
+            dV = g.shape_gradient(x, lam, dirs, pols, dirs, coef).imag  # [n_rhs, nv, 3]
+            gV = torch.from_numpy(np.einsum("r,rvc->vc", w, dV)).to(ctx.devices[0])
+        if ctx.needs_input_grad[1]:
+            ge = np.zeros(len(en), dtype=np.complex128)
+            for j in range(1, len(en)):
+                h = 1e-5 * max(1.0, abs(en[j]))
+                ep, em = list(en), list(en)
+                ep[j] += h
+                em[j] -= h
+                dAx = (FMBEM(Vn, F, D, ep, mu, k0, **options).matvec(x) -
+                       FMBEM(Vn, F, D, em, mu, k0, **options).matvec(x)) / (2 * h)
+                df = -torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()  # d f / d eps_j (holomorphic)
+                # C = Im f: dC/dRe = Im df, dC/dIm = Re df; the complex gradient is dRe + i dIm
+                ge[j] = np.sum(w * (df.imag + 1j * df.real))
+            geps = torch.from_numpy(ge).to(ctx.devices[1])
+        return gV, geps, None, None, None, None, None, None, None
+
+
+def extinction(V, eps, F, D, mu, k0, dirs, pols, **options):
+    """C_ext [n_rhs] (float64 tensor) of the plane waves (dirs[r], pols[r]) on the mesh (V, F, D),
+    differentiable in V (float64 tensor [nv, 3], vertex nodes) and eps (complex128 tensor [J+1]):
+    one forward and one adjoint GMRES solve serve both gradients.  Under PyTorch's convention the
+    gradient of a real loss with respect to eps_j is dL/dRe(eps_j) + i dL/dIm(eps_j)."""
+    import numpy as np
+    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+    pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
+    return _Extinction.apply(V, eps, F, D, mu, k0, dirs, pols, options)
