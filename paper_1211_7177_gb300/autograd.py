@@ -118,3 +118,61 @@ def extinction(V, eps, F, D, mu, k0, dirs, pols, **options):
     dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
     pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
     return _Extinction.apply(V, eps, F, D, mu, k0, dirs, pols, options)
+
+
+class _Force(torch.autograd.Function):
+    """Maxwell-stress force [3] on the particles inside the sphere (center, radius) in the plane
+    wave (d, e) (vacuum background); differentiable in the vertex positions V (fmbem_shape_
+    gradient_near) and the permittivities eps (operator central differences), each force
+    component's gradient being 2 Re of its Wirtinger functional's (see gradients.py)."""
+
+    @staticmethod
+    def forward(ctx, V, eps, F, D, mu, k0, d, e, center, radius, n_theta, n_phi, options):
+        import numpy as np
+
+        from . import FMBEM
+        from .gradients import _force_adjoint
+        Vn = V.detach().cpu().numpy().astype(np.float64)
+        en = [complex(v) for v in eps.detach().cpu().numpy()]
+        g = FMBEM(Vn, F, D, en, mu, k0, **options)
+        x, force, pts, cE, cH, lam = _force_adjoint(g, d, e, center, radius, n_theta, n_phi, 1e-10)
+        ctx.state = (g, x, pts, cE, cH, lam, Vn, en, F, D, mu, k0, d, e, options)
+        ctx.devices = (V.device, eps.device)
+        return torch.as_tensor(np.asarray(force, dtype=np.float64), device=V.device)
+
+    @staticmethod
+    def backward(ctx, go):
+        import numpy as np
+
+        from . import FMBEM
+        g, x, pts, cE, cH, lam, Vn, en, F, D, mu, k0, d, e, options = ctx.state
+        w = go.detach().cpu().numpy().astype(np.float64)  # dLoss/dF_i
+        gV = geps = None
+        if ctx.needs_input_grad[0]:
+            x3 = x.expand(3, -1, -1).contiguous()
+            out = g.shape_gradient_near(x3, lam, np.repeat(d, 3, 0), np.repeat(e, 3, 0), pts, cE, cH)
+            gV = torch.from_numpy(np.einsum("i,ivc->vc", w, 2 * out.real)).to(ctx.devices[0])
+        if ctx.needs_input_grad[1]:
+            ge = np.zeros(len(en), dtype=np.complex128)
+            for j in range(1, len(en)):
+                h = 1e-5 * max(1.0, abs(en[j]))
+                ep, em = list(en), list(en)
+                ep[j] += h
+                em[j] -= h
+                dAx = (FMBEM(Vn, F, D, ep, mu, k0, **options).matvec(x) -
+                       FMBEM(Vn, F, D, em, mu, k0, **options).matvec(x)) / (2 * h)
+                sv = torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()  # s_i = lambda_i^T (dA/deps_j) x
+                ge[j] = np.sum(w * (-2 * sv.real + 1j * 2 * sv.imag))  # dF_i/dRe + i dF_i/dIm
+            geps = torch.from_numpy(ge).to(ctx.devices[1])
+        return gV, geps, None, None, None, None, None, None, None, None, None, None, None
+
+
+def force(V, eps, F, D, mu, k0, d, e, center, radius, n_theta=24, n_phi=48, **options):
+    """The Maxwell-stress force [3] (float64 tensor) of gradients.force_eps_gradient, differentiable
+    in V (float64 tensor [nv, 3], vertex nodes; the stress sphere stays fixed) and eps (complex128
+    tensor [J+1]): one forward and three adjoint solves serve both gradients."""
+    import numpy as np
+    d = np.asarray(d, dtype=np.float64).reshape(1, 3)
+    e = np.asarray(e, dtype=np.complex128).reshape(1, 3)
+    return _Force.apply(V, eps, F, D, mu, k0, d, e, np.asarray(center, dtype=np.float64), float(radius), n_theta,
+                        n_phi, options)
