@@ -11,7 +11,15 @@ Also reported: e2e (same metric through the C ABI with pinned host buffers and t
 copies inside the timed region), the roofline of the dominant kernel, the same matvec in FP32
 arithmetic, the solve time to a 1e-4 relative residual for the plain FP64 solve and for the
 FP32-inner / FP64-outer refined solve, and the FP64 CPU oracle timed on a bounded sample of rows
-(cpu_baseline).  ``--workload torus_512x128`` runs the 128-right-hand-side batch.
+(cpu_baseline).
+
+The default run adds a ``batched`` object: the batched mixed-precision form on the torus
+R=1, r=0.25 (512x128 grid, 65536 nodes, eps=-10+0.4i, k0 R=1.5) with 128 plane waves -- the
+128-RHS matvec with M2L + L2L on the TF32 tensor cores (device time and e2e, per-phase rooflines),
+the FP64 single-RHS matvec on the same mesh, the plain FP64 single-RHS solve and the batched solve
+(TF32 inner GMRES, FP64-operator true residual) to 1e-4, and the FP64 oracle on sampled rows
+(timed, with the matvec error and the batched solution's residual against the dense operator).
+``--workload torus_512x128`` runs the 128-right-hand-side batch as the main line instead.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm of this comparison).
 """
@@ -90,6 +98,8 @@ def parse():
                     help="also time the adjoint gradients on the torus + sphere differentiation case")
     ap.add_argument("--restart", type=int, default=50, help="GMRES restart length of the timed solves")
     ap.add_argument("--n-rhs", type=int, default=0, help="right-hand sides (0 = the workload's)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched leg (128-RHS torus, TF32 M2L, FP64-refined solve) of the default run")
     return ap.parse_args()
 
 
@@ -308,6 +318,203 @@ def run_gradients():
     return out
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one matvec phase, from ncu
+# captures summarised under profiles/, keyed by (workload, precision, n_rhs, phase); each entry
+# records the SHA-256 prefix of the kernel source it was taken with, and the bench reports null
+# once that source has changed.
+TRAFFIC = {}
+
+
+def _src_sha(name):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1211_7177_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def phase_traffic(workload, precision, nr, phase):
+    t = TRAFFIC.get((workload, precision, nr, phase))
+    if t is None:
+        return None
+    if any(_src_sha(f) != h for f, h in t["src"].items()):
+        return None
+    return t["bytes"]
+
+
+def phase_rooflines(info, p, nr, n_dom, N, phases, workload):
+    """Per-phase roofline of the TF32 batched matvec: near field against the FP32 ALU peak,
+    M2L + L2L against the TF32 tensor peak, P2M and M2M against the FP32 ALU peak."""
+    keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
+    avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
+    tpk, tsrc = tensor_peak_tf32()
+    cols = 3 * nr * n_dom
+    flops = {
+        # per (near pair, domain): the kernel scalars; per (pair, domain, RHS): the bracket and g q
+        "near_l2p_self": info["near_pairs"] * n_dom * (NEAR_PAIR + NEAR_RHS * nr),
+        # dense S|R in real form on the tensor cores: 8 p^4 per (FF pair, column)
+        "m2l_l2l": 8.0 * p ** 4 * info["ff_pairs"] * cols,
+        # per (node, side, coefficient, column): a dipole/monopole weight times the basis, 4 complex MACs
+        "p2m": 32.0 * N * 2 * p * p * 3 * nr,
+        # dense S|S per (child box, column), every box below level 2 has a parent
+        "m2m": 8.0 * p ** 4 * max(info["n_boxes"] - 64, 0) * cols,
+    }
+    out = {}
+    for k in keys:
+        tensor = k == "m2l_l2l"
+        peak = tpk if tensor else PEAK_TFLOPS["fp32"]
+        ach = flops[k] / (avg[k] * 1e-3) / 1e12
+        out[k] = dict(bound="tensor" if tensor else "alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                      ms=avg[k], algorithmic_flops=flops[k],
+                      traffic=phase_traffic(workload, "tf32", nr, k),
+                      peak_source=tsrc if tensor else "measured FP32 FMA throughput of GB300 (self-written probe)")
+    return out, avg
+
+
+def run_batched(args, world, flush):
+    """Batched, mixed-precision form on the torus: R = 1, r = 0.25, 512 x 128 grid (65536 nodes),
+    eps = -10 + 0.4i, k0 R = 1.5, 128 plane waves (64 Fibonacci directions x 2 polarisations),
+    p = 8.  Times the 128-RHS matvec with the M2L on the TF32 tensor cores (device and e2e), the
+    FP64 single-RHS matvec on the same mesh, the plain FP64 single-RHS solve and the batched solve
+    (TF32-operator inner GMRES, FP64-operator true residual) to 1e-4; on rank 0 the FP64 oracle
+    evaluates sampled rows, timed, giving the matvec error and the solve's residual against the
+    dense operator."""
+    import torch
+
+    import paper_1211_7177_gb300 as fm
+    name = "torus_512x128"
+    wl = WORKLOADS[name]
+    p, nr, restart = wl["p"], wl["n_rhs"], 100
+    rank = dist_env()[0]
+    V, F, D = wl["mesh"]()
+    t0 = time.perf_counter()
+    g = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, profile_phases=1,
+                 m2l_rotation=1, gmres_restart=restart)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = g.tree_info()
+    N, n_dom = g.N, len(wl["eps"])
+    dirs, pols = rhs_batch(nr)
+    b = g.plane_wave_rhs(dirs, pols)
+    noise = torch.from_numpy(fi.random_complex((nr, N, 6), seed=13)).cuda()
+    x = b + 0.1 * noise
+    del noise
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def time_matvec(xx, yy, prec, steps, warmup, with_phases=True):
+        for _ in range(warmup):
+            g.matvec(xx, yy, precision=prec)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        ph = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            g.matvec(xx, yy, precision=prec)
+            ev[k][1].record(stream)
+            if with_phases:
+                ph.append(g.last_matvec_times())
+        torch.cuda.synchronize()
+        return max_over_ranks(statistics.mean(a.elapsed_time(bb) for a, bb in ev), "cuda"), ph
+
+    ms, phases = time_matvec(x, y, fm.TF32, args.steps, args.warmup)
+    roof, avg = phase_rooflines(info, p, nr, n_dom, N, phases, name)
+    dom = max(avg, key=avg.get)
+    out = dict(workload=name, desc=wl["desc"], nodes=N, n_rhs=nr, p=p, leaf_size=args.leaf, tree=info,
+               dtype="f32 (M2L on TF32 tensor cores)", setup_s=setup_s,
+               l2="inputs larger than L2 and L2 flushed (256 MiB write) before each step",
+               value=job_throughput(N * nr, world, ms), unit=UNIT, ms_per_step=ms, steps=args.steps,
+               roofline=dict(roof[dom], kernel=dom), phase_roofline=roof)
+
+    # e2e through the C ABI: pinned host x -> device, matvec, device -> pinned host y
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        e0.record(stream)
+        x.copy_(xh, non_blocking=True)
+        g.matvec(x, y, precision=fm.TF32)
+        yh.copy_(y, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    nbytes = x.numel() * 16
+    out["e2e"] = dict(value=world * N * nr / (statistics.mean(e2e_ms) * 1e-3), unit=UNIT,
+                      h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes)
+    y_tf32 = yh.numpy().copy()
+
+    # the plain method's form on the same mesh: FP64 arithmetic, one right-hand side per matvec
+    x1, y1 = x[:1].contiguous(), y[:1].contiguous()
+    ms1, _ = time_matvec(x1, y1, fm.FP64, 3, 2, with_phases=False)
+    out["fp64_single_rhs"] = dict(value=world * N / (ms1 * 1e-3), unit=UNIT, ms_per_step=ms1)
+    out["speedup_vs_fp64_single_rhs"] = out["value"] / out["fp64_single_rhs"]["value"]
+
+    solve = {}
+    if not args.no_solve:
+        # plain: FP64 GMRES(100) on one right-hand side
+        gp = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, m2l_rotation=1,
+                      gmres_restart=restart)
+        b1 = b[:1].contiguous()
+        xs1 = torch.zeros_like(b1)
+        gp.solve(b1, xs1, tol=1e-4, max_iter=2)  # warm-up: allocates the Krylov basis
+        xs1.zero_()
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        _, its, rr, st = gp.solve(b1, xs1, tol=1e-4, max_iter=1000)
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - s0
+        solve["plain_fp64_single_rhs"] = dict(tol=1e-4, ms=1e3 * t_plain, iters=int(its.max()), relres=float(rr.max()),
+                                              status=int(st), restart=restart)
+        gp.close()
+        del gp
+        # batched: inner GMRES(100) with the TF32 tensor-core operator to 1e-2 (above the floor its
+        # input rounding sets) and a single-precision basis; outer true residual b - A x with the
+        # FP64 operator and FP64 vectors, repeated until it is <= 1e-4
+        gb = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, m2l_rotation=1,
+                      gmres_restart=restart, solve_precision=fm.TF32, inner_tol=1e-2, outer_precision=fm.FP64)
+        xs = torch.zeros_like(b)
+        gb.solve(b, xs, tol=1e-4, max_iter=2)  # warm-up
+        xs.zero_()
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        _, its, rr, st = gb.solve(b, xs, tol=1e-4, max_iter=2000)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - s0
+        solve["batched_tf32_inner_fp64_outer"] = dict(
+            tol=1e-4, ms=1e3 * t_b, ms_per_rhs=1e3 * t_b / nr, iters=int(its.max()), relres_fp64_true=float(rr.max()),
+            status=int(st), restart=restart, inner_tol=1e-2, n_rhs=nr)
+        solve["per_rhs_speedup_vs_plain"] = t_plain / (t_b / nr)
+        xs_h = xs.cpu().numpy()
+        gb.close()
+        del gb
+    out["solve"] = solve
+
+    if rank == 0 and not args.no_cpu_baseline:
+        # the FP64 CPU oracle on 32 seeded node rows for all 128 right-hand sides (timed: the
+        # batched leg's cpu_baseline); the same rows give the TF32 matvec's error and the refined
+        # solution's true residual against the dense FP64 operator
+        import oracle
+        o = oracle.Oracle(V, F, D, wl["eps"], wl["mu"], wl["k0"])
+        rows = fi.sample_rows(N, 32, seed=2)
+        xh_np = xh.numpy()
+        t0 = time.perf_counter()
+        yo = o.matvec_rows(xh_np, rows)
+        t_or = time.perf_counter() - t0
+        out["cpu_baseline"] = dict(value=len(rows) * nr / t_or, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                                   sample=f"{len(rows)} seeded node rows x {nr} RHS of the {N}-node dense FP64 operator")
+        yg = y_tf32[:, rows]
+        acc = dict(rows=len(rows), matvec_rel_l2_vs_oracle=float(np.linalg.norm(yg - yo) / np.linalg.norm(yo)))
+        if solve:
+            bo = o.plane_wave_rhs(dirs, pols)[:, rows]
+            ro = o.matvec_rows(xs_h, rows) - bo
+            acc["solve_rel_residual_vs_oracle"] = float(np.linalg.norm(ro) / np.linalg.norm(bo))
+        out["accuracy"] = acc
+    g.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -452,14 +659,14 @@ def run_ours(args):
         if nr == 1:
             kinds = (("plain_fp64", fm.FP64, 0.5e-4), ("fp32_inner_fp64_refined", fm.FP32, 0.5e-4))
         else:
-            kinds = (("fp32_inner_fp32_refined", fm.FP32, 0.5e-4),) + \
-                ((("tf32_inner_fp32_refined", fm.TF32, 1e-2),) if tensor_path(nr) else ())
+            kinds = (("fp32_inner_fp64_refined", fm.FP32, 0.5e-4),) + \
+                ((("tf32_inner_fp64_refined", fm.TF32, 1e-2),) if tensor_path(nr) else ())
         for label, sp, itol in kinds:
             # refined solve: FP32 inner GMRES to half the tolerance (TF32 tensor-core M2L: to 1e-2,
-            # above the floor its input rounding sets), true residual with FP64 vectors (FP64
-            # passes for one right-hand side, FP32 passes with FP64 accumulation for batches)
+            # above the floor its input rounding sets), true residual with the FP64 operator and
+            # FP64 vectors
             h2 = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, gmres_restart=args.restart,
-                          solve_precision=sp, inner_tol=itol, outer_precision=fm.FP64 if nr == 1 else fm.FP32)
+                          solve_precision=sp, inner_tol=itol, outer_precision=fm.FP64, m2l_rotation=1 if nr > 8 else -1)
             xs = torch.zeros_like(b)
             h2.solve(b, xs, tol=1e-4, max_iter=1000)  # warm-up (allocates the Krylov basis)
             xs.zero_()
@@ -480,6 +687,11 @@ def run_ours(args):
         cpu = dict(value=rows * nr / min(times), unit=UNIT, cores=cores, kind="oracle",
                    sample=f"{rows} seeded node rows x {nr} RHS of the {Nn}-node dense FP64 operator, best of 2")
 
+    g.close()
+    batched = None
+    if args.workload == "silver_sphere_s7" and not args.no_batched:
+        batched = run_batched(args, world, flush)
+
     launches_per_step = launches_per_matvec(info["l_max"], nr, n_dom, args.precision)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -490,11 +702,10 @@ def run_ours(args):
                             l2="flushed (256 MiB write) before each step", setup_s=setup_s, wall_s=wall),
                 e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes),
                 roofline=roof, other_precision=other, adjoint=adjoint, impedance=impedance, solve=solve,
-                gradients=gradients, cpu_baseline=cpu,
+                gradients=gradients, cpu_baseline=cpu, batched=batched,
                 gpu_launches=launches_per_step * args.steps, clocks=clk)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 

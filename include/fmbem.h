@@ -51,7 +51,11 @@ typedef enum {
     FMBEM_ERR_OOM = 3,              /* a device allocation failed                              */
     FMBEM_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed             */
     FMBEM_ERR_NOT_CONVERGED = 5,    /* fmbem_solve reached max_iter above the tolerance        */
-    FMBEM_ERR_BREAKDOWN = 6         /* GMRES produced a non-finite value                       */
+    FMBEM_ERR_BREAKDOWN = 6,        /* GMRES produced a non-finite value                       */
+    FMBEM_ERR_DEVICE_TIMEOUT = 7    /* a bounded wait inside a kernel ran out (a pipeline stage
+                                       or a work item never became ready); the kernel stopped,
+                                       released what it held and returned, the context stays
+                                       usable and the call's outputs are undefined              */
 } fmbem_status;
 
 typedef enum { FMBEM_NODES_VERTEX = 0, FMBEM_NODES_CENTROID = 1 } fmbem_node_mode;
@@ -383,8 +387,9 @@ fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64
  * capture), code whose device memory is owned by a framework allocator, or callbacks that must
  * not trigger the implicit device synchronisation of cudaMalloc/cudaFree.  The paper has no
  * counterpart; this is a library-level variant of fmbem_matvec.
- * Same arguments, layouts, kernels and results as fmbem_matvec, but the scratch (source
- * densities, expansion coefficients, per-pair M2L results) lives in one file-scope device array
+ * Same arguments, layouts, kernels and results as fmbem_matvec, except that precision must be
+ * FMBEM_FP64 or FMBEM_FP32 (FMBEM_TF32 is refused with FMBEM_ERR_INVALID_ARGUMENT).  The scratch
+ * (source densities, expansion coefficients, per-pair M2L results) lives in one file-scope device array
  * of 32 MiB that every GPU loading the library holds until the process exits; no cudaMalloc,
  * cudaFree or allocating library routine is called.  Problems whose scratch for the given n_rhs
  * and precision exceeds 32 MiB (roughly a few thousand nodes at p = 8 and one right-hand side)

@@ -29,7 +29,8 @@ FP64, FP32, TF32 = 0, 1, 2
 NODES_VERTEX, NODES_CENTROID = 0, 1
 # boundary option: penetrable scatterers (Eqs. 2.5-2.13) or the impedance condition of Eq. (2.24)
 PENETRABLE, IMPEDANCE = 0, 1
-STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_MESH", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED", 6: "BREAKDOWN"}
+STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_MESH", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED", 6: "BREAKDOWN",
+          7: "DEVICE_TIMEOUT"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fmbem.h")
 
 
@@ -587,12 +588,17 @@ class FMBEM:
 def fmbem_matvec_noalloc(h, x, y, precision=FP64, stream=None):
     """Allocation-free y = A x (see include/fmbem.h): for callers that cannot allocate device
     memory when they need the product, e.g. while a CUDA graph is being captured.  x and y are
-    preallocated complex128 CUDA tensors [n_rhs, N, 6]; y is written in place and returned."""
+    preallocated complex128 CUDA tensors [n_rhs, N, 6]; y is written in place and returned.
+    precision is FP64 or FP32.  A lazily conjugated or negated x (PyTorch's conj/neg views) is
+    refused rather than materialised, since materialising it would allocate."""
+    import torch
     lib = load_library()
     f = lib.fmbem_matvec_noalloc
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
     N = fmbem_num_nodes(h)
+    if isinstance(x, torch.Tensor) and (x.is_conj() or x.is_neg()):
+        raise TypeError("x must not be a conjugate or negative view (resolving it would allocate)")
     x = _dev(x, N, "x")
     y = _dev(y, N, "y", out=True)
     _check(h, f(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.shape[0], int(precision),

@@ -94,7 +94,11 @@ class _Extinction(torch.autograd.Function):
             dV = g.shape_gradient(x, lam, dirs, pols, dirs, coef).imag  # [n_rhs, nv, 3]
             gV = torch.from_numpy(np.einsum("r,rvc->vc", w, dV)).to(ctx.devices[0])
         if ctx.needs_input_grad[1]:
+            # eps_0 (the background) is held fixed: it also enters the incident field and the
+            # optical theorem's prefactor, which this adjoint does not differentiate, so its entry
+            # is NaN rather than a silent zero
             ge = np.zeros(len(en), dtype=np.complex128)
+            ge[0] = complex(np.nan, np.nan)
             for j in range(1, len(en)):
                 h = 1e-5 * max(1.0, abs(en[j]))
                 ep, em = list(en), list(en)
@@ -113,7 +117,9 @@ def extinction(V, eps, F, D, mu, k0, dirs, pols, **options):
     """C_ext [n_rhs] (float64 tensor) of the plane waves (dirs[r], pols[r]) on the mesh (V, F, D),
     differentiable in V (float64 tensor [nv, 3], vertex nodes) and eps (complex128 tensor [J+1]):
     one forward and one adjoint GMRES solve serve both gradients.  Under PyTorch's convention the
-    gradient of a real loss with respect to eps_j is dL/dRe(eps_j) + i dL/dIm(eps_j)."""
+    gradient of a real loss with respect to eps_j is dL/dRe(eps_j) + i dL/dIm(eps_j).  Only the
+    scatterers' permittivities eps[1:] are differentiated: the background eps[0] is held fixed and
+    its gradient entry is NaN (slice eps[1:] into a leaf tensor to optimise the scatterers)."""
     import numpy as np
     dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
     pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
@@ -154,6 +160,7 @@ class _Force(torch.autograd.Function):
             gV = torch.from_numpy(np.einsum("i,ivc->vc", w, 2 * out.real)).to(ctx.devices[0])
         if ctx.needs_input_grad[1]:
             ge = np.zeros(len(en), dtype=np.complex128)
+            ge[0] = complex(np.nan, np.nan)  # eps_0 held fixed (see _Extinction.backward)
             for j in range(1, len(en)):
                 h = 1e-5 * max(1.0, abs(en[j]))
                 ep, em = list(en), list(en)
@@ -170,7 +177,8 @@ class _Force(torch.autograd.Function):
 def force(V, eps, F, D, mu, k0, d, e, center, radius, n_theta=24, n_phi=48, **options):
     """The Maxwell-stress force [3] (float64 tensor) of gradients.force_eps_gradient, differentiable
     in V (float64 tensor [nv, 3], vertex nodes; the stress sphere stays fixed) and eps (complex128
-    tensor [J+1]): one forward and three adjoint solves serve both gradients."""
+    tensor [J+1]): one forward and three adjoint solves serve both gradients.  As for extinction,
+    the background eps[0] is held fixed and its gradient entry is NaN."""
     import numpy as np
     d = np.asarray(d, dtype=np.float64).reshape(1, 3)
     e = np.asarray(e, dtype=np.complex128).reshape(1, 3)

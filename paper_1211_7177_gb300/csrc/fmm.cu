@@ -2445,7 +2445,30 @@ void build_rot_mm_lists(fmbem *h, cudaStream_t s) {
     CK(cudaStreamSynchronize(s));
 }
 
-static void ensure_scratch(fmbem *h, int64_t nr) {
+// Columns per window of the FP64 rotation-form M2L when a call has more than 24 columns: one
+// column per lane of k_m2l_rot_cols (32), unless the per-target reduction k_l2l_reduce would then
+// need more than 1024 threads (p > 8), where it stays at 24.
+static int rot_many_cols(const fmbem *h) {
+    const int rows_pad = ((h->p2 + 31) / 32) * 32;
+    return rows_pad * ((ROTC_N + L2L_CPT - 1) / L2L_CPT) <= 1024 ? ROTC_N : 24;
+}
+// FP64 calls with more than 24 columns run the rotation form in column windows when its tables
+// were built (the dense target-major kernel otherwise)
+static bool rot_many_path(const fmbem *h, int64_t nr, bool fp64) {
+    return fp64 && 3 * nr > 24 && h->m2l_rotation && h->R_D64 != nullptr;
+}
+// bytes of the per-pair M2L result buffer for ncol columns: the largest level's pair results,
+// then (rotation form) its child entries
+static size_t ybuf_need(const fmbem *h, int64_t ncol, size_t elem) {
+    int64_t mp = 1;
+    for (int l = 2; l <= h->lmax; ++l) {
+        const int64_t ne = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
+        mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l] + ne);
+    }
+    return elem * (size_t)mp * (size_t)ncol * h->p2;
+}
+
+static void ensure_scratch(fmbem *h, int64_t nr, int precision) {
     const size_t cb = sizeof(c64);
     if (h->scratch_rhs < nr) {
         if (h->dens) { dev_free(h, h->dens); dev_free(h, h->Cexp); dev_free(h, h->Dexp); }
@@ -2454,16 +2477,12 @@ static void ensure_scratch(fmbem *h, int64_t nr) {
         h->Dexp = dev_alloc(h, cb * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
         h->scratch_rhs = nr;
     }
-    // per-pair M2L results of one level, one domain and up to 24 columns (chunked path only);
-    // sized by the columns of this call, so that a few-column call after a many-column one
-    // still takes the chunked path
-    if (3 * nr <= 24) {
-        int64_t mp = 1;  // a level's pair results, then (rotation form) its child entries
-        for (int l = 2; l <= h->lmax; ++l) {
-            const int64_t ne = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
-            mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l] + ne);
-        }
-        const size_t need = cb * (size_t)mp * (size_t)(3 * nr) * h->p2;
+    // per-pair M2L results of one level, one domain and up to 24 columns (chunked path only;
+    // one column window of the FP64 rotation form for more columns); sized by the columns of
+    // this call, so that a few-column call after a many-column one still takes the chunked path
+    const bool many = rot_many_path(h, nr, precision == FMBEM_FP64);
+    if (3 * nr <= 24 || many) {
+        const size_t need = ybuf_need(h, many ? rot_many_cols(h) : 3 * nr, cb);
         if (h->ybuf == nullptr || h->ybuf_bytes < need) {
             if (h->ybuf) dev_free(h, h->ybuf);
             h->ybuf = nullptr;
@@ -2487,7 +2506,7 @@ struct RotLaunch {
 template <typename R>
 static RotLaunch rot_launch(fmbem *h, int ncol, size_t budget) {
     RotLaunch rl;
-    if (!h->m2l_rotation || h->R_D64 == nullptr || ncol > 24) return rl;
+    if (!h->m2l_rotation || h->R_D64 == nullptr || ncol > (sizeof(R) == 8 ? ROTC_N : 24)) return rl;
     const int p = h->p, p2 = h->p2, nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
     if (sizeof(R) == 8) {  // FP64-bound: one column per lane, loops of equal length in a warp
         const size_t b = sizeof(R) * 2 * (size_t)nrot + sizeof(cx<R>) * ((size_t)(2 * p2 + ncoax) + 2 * (size_t)p2 * ROTC_S) +
@@ -2502,6 +2521,7 @@ static RotLaunch rot_launch(fmbem *h, int ncol, size_t budget) {
             return rl;
         }
     }
+    if (ncol > 24) return rl;  // wider windows only in the column-parallel kernel
     cudaFuncAttributes fa{};
     CK(cudaFuncGetAttributes(&fa, k_m2l_rot<R, ROT_MAXC>));
     auto bytes = [&](int c) {
@@ -2596,7 +2616,9 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     // downward pass: offset-chunked M2L with a per-target reduction for few columns, the
     // target-major kernel (translation matrices reused across many columns) otherwise
     constexpr int MAXC = 24;
-    const int ncol = (int)std::min<int64_t>(3 * nr, MAXC);
+    // FP64 with more than MAXC columns and rotation tables: the rotation form in column windows
+    const bool rot_many = rot_many_path(h, nr, !f32);
+    const int ncol = rot_many ? rot_many_cols(h) : (int)std::min<int64_t>(3 * nr, MAXC);
     const size_t tbytes = sizeof(cx<R>) * p2 * p2;
     const size_t budget = 200 * 1024;
     auto xs_bytes = [&](int c) { return sizeof(cx<R>) * c * MAXC * p2; };
@@ -2612,10 +2634,13 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
     while (cg > 1 && (tsm ? tbytes : 0) + xs_bytes(cg) > budget) --cg;
     const size_t smc = (tsm ? tbytes : 0) + xs_bytes(cg);
     const int pc = std::min(M2L_CHUNK, cg * MAXC / ncol);
-    const bool chunked = 3 * nr <= MAXC && pc >= 1 && smc <= budget && h->ybuf != nullptr && rows_pad <= max_thr;
     // rotation form of the chunked S|R (when its tables were built)
     const int pp = h->p;
     const RotLaunch rl = rot_launch<R>(h, ncol, budget);
+    const bool chunked =
+        (3 * nr <= MAXC ? pc >= 1 && smc <= budget
+                        : rot_many && rl.ok && h->ybuf_bytes >= ybuf_need(h, ncol, sizeof(cx<R>))) &&
+        h->ybuf != nullptr && rows_pad <= max_thr;
     const bool use_rot = chunked && rl.ok;
     if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
         run_m2l_tc(h, (float *)C, (float *)D, nr, s);
@@ -2885,11 +2910,14 @@ static void check_tc_err(fmbem *h, cudaStream_t s) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (e) throw fmbem_error{FMBEM_ERR_CUDA, "tensor-core M2L: an mbarrier wait timed out"};
+    if (e) {
+        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+        throw fmbem_error{FMBEM_ERR_DEVICE_TIMEOUT, "tensor-core M2L: an mbarrier wait timed out"};
+    }
 }
 
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
-    ensure_scratch(h, nr);
+    ensure_scratch(h, nr, precision);
     const DomainConsts *dc = (const DomainConsts *)h->dcons;
     if (precision == FMBEM_TF32) {
         adjoint_impl<float>(h, x, y, nr, s, dc, true);
@@ -2902,7 +2930,7 @@ void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precisio
 }
 
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
-    ensure_scratch(h, nr);
+    ensure_scratch(h, nr, precision);
     static_assert(sizeof(DomainConsts) == 3 * sizeof(c64), "layout");
     DomainConsts *dc = (DomainConsts *)h->dcons;
     if (precision == FMBEM_TF32) {

@@ -36,6 +36,8 @@ def test_extinction_gradients_match_central_differences(fake):
     V = torch.tensor(V0, requires_grad=True)
     eps = torch.tensor(eps0, dtype=torch.complex128, requires_grad=True)
     loss(V, eps).backward()
+    # the background permittivity is held fixed: its entry is NaN, never a silent zero
+    assert torch.isnan(eps.grad[0].real) and torch.isnan(eps.grad[0].imag)
     h = 1e-6
     with torch.no_grad():
         for v, c in ((0, 0), (2, 1), (3, 2)):
@@ -71,6 +73,8 @@ def test_force_gradients_match_central_differences(fake):
     V = torch.tensor(V0, requires_grad=True)
     eps = torch.tensor(eps0, dtype=torch.complex128, requires_grad=True)
     loss(V, eps).backward()
+    # the background permittivity is held fixed: its entry is NaN, never a silent zero
+    assert torch.isnan(eps.grad[0].real) and torch.isnan(eps.grad[0].imag)
     h = 1e-6
     with torch.no_grad():
         for v, c in ((0, 2), (1, 0), (3, 1)):

@@ -52,3 +52,36 @@ def test_noalloc_rejects_oversized_scratch(handle):
     with pytest.raises(fm.FMBEMError) as e:
         fm.fmbem_matvec_noalloc(g.h, x, y)
     assert e.value.status == 1 and "bytes" in str(e.value)
+
+
+def test_noalloc_allocates_nothing_batched_and_impedance():
+    """With the library's device-allocation budget set to zero (fault injection: any further
+    allocation fails as cudaMalloc would), the allocation-free product must still run, after a
+    first call that looked up the static array's address: four right-hand sides in FP32 (the
+    blocked P2M and the warp near-field kernel) on a 642-node sphere, and one right-hand side on an
+    impedance-boundary handle (whose unused scatterer expansions are cleared inside the array).
+    Each result must equal fmbem_matvec's, computed before the budget is set."""
+    lib = fm.load_library()
+    V, F, D = fi.icosphere(3)
+    cases = [(fm.FMBEM(V, F, D, [1.0, 2.25], [1.0, 1.0], 1.0), 4, fm.FP32),
+             (fm.FMBEM(V, F, D, [1.0, 1.0 + 1e4j], [1.0, 1.0], 1.0, boundary=fm.IMPEDANCE, p=10), 1, fm.FP64)]
+    try:
+        work = []
+        for g, nr, prec in cases:
+            x = torch.from_numpy(fi.random_complex((nr, g.N, 6), seed=31)).cuda()
+            y = torch.empty_like(x)
+            ref = g.matvec(x, precision=prec)
+            fm.fmbem_matvec_noalloc(g.h, x, y, precision=prec)  # first call: address look-up
+            torch.cuda.synchronize()
+            work.append((g, x, y, ref, prec))
+        lib.fmbem_debug_set_device_budget(0)
+        for g, x, y, ref, prec in work:
+            for _ in range(2):
+                y.zero_()
+                fm.fmbem_matvec_noalloc(g.h, x, y, precision=prec)
+                torch.cuda.synchronize()
+                assert rel(y, ref) < TOL[prec]
+    finally:
+        lib.fmbem_debug_set_device_budget(-1)
+        for g, *_ in cases:
+            g.close()
