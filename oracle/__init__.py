@@ -77,6 +77,8 @@ def _load():
             lib.oracle_ibc_precond_blocks.argtypes = [P, P]
             lib.oracle_ibc_psi.argtypes = [P, i64, P, P]
             lib.oracle_ibc_zeta.argtypes = [P, P]
+            lib.oracle_set_near_singular.argtypes = [P, dbl, i32]
+            lib.oracle_patch_integral.argtypes = [P, i64, P, dbl, dbl, i32, P]
             lib.oracle_num_threads.restype = i32
             _lib = lib
     return _lib
@@ -107,7 +109,7 @@ class Oracle:
     ``eps``/``mu``: relative permittivity/permeability of the background (index 0) and of
     scatterers 1..J; ``k0``: vacuum wavenumber; ``mode``: 'vertex' or 'centroid' nodes."""
 
-    def __init__(self, V, F, D, eps, mu, k0, mode="vertex"):
+    def __init__(self, V, F, D, eps, mu, k0, mode="vertex", near_singular_radius=0.0, near_singular_levels=3):
         lib = _load()
         self.V = np.ascontiguousarray(V, dtype=np.float64)
         self.F = np.ascontiguousarray(F, dtype=np.int32)
@@ -140,6 +142,12 @@ class Oracle:
         k = np.zeros(self.J + 1, dtype=np.complex128)
         lib.oracle_wavenumbers(self._h, _ptr(k))
         self.k = k
+        # near-singular correction (off at radius 0, the paper's operator): a source node within
+        # R < radius * sqrt(w) of the target contributes the integral of the kernel over its patch
+        # (4^levels sub-triangles per flat piece, centroid rule) instead of the one-point term
+        self.near_singular_radius = float(near_singular_radius)
+        self.near_singular_levels = int(near_singular_levels)
+        lib.oracle_set_near_singular(self._h, self.near_singular_radius, self.near_singular_levels)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -161,6 +169,17 @@ class Oracle:
         y = np.empty_like(x)
         self._lib.oracle_matvec(self._h, x.shape[0], _ptr(x), _ptr(y))
         return y[0] if squeeze else y
+
+    def patch_integral(self, b, point, k, levels=None):
+        """(int g dA', int grad' g dA' [3]) over node b's patch seen from ``point`` with wavenumber
+        k, by the subdivision rule of the near-singular correction (``levels`` defaults to the
+        instance's)."""
+        L = self.near_singular_levels if levels is None else int(levels)
+        pt = np.ascontiguousarray(point, dtype=np.float64)
+        out = np.zeros(8)
+        k = complex(k)
+        self._lib.oracle_patch_integral(self._h, int(b), _ptr(pt), k.real, k.imag, L, _ptr(out))
+        return complex(out[0], out[1]), out[2::2] + 1j * out[3::2]
 
     def matvec_rows(self, x, rows):
         """Rows of A x for the node indices ``rows``: [n_rhs, len(rows), 6]."""

@@ -24,6 +24,12 @@
  *     unknown n0 x curl E = -Psi (Psi is stored with the scatterer normal).
  *   - The transposed product A^T x of the same operator (complex bilinear transpose, no
  *     conjugation), gathered column by column from the transposed pair and self blocks.
+ *   - Optionally (radius rho > 0; rho = 0 is the paper's operator), a near-singular correction:
+ *     a source node beta within R < rho sqrt(w_beta) of the target contributes the integral of
+ *     the pair kernel over its patch, with its density and normal held constant, instead of the
+ *     one-point term of Eq. (2.8); the patch is the triangle (centroid nodes) or the unprojected
+ *     barycentric dual cell (vertex nodes), each flat piece split L times into four by its edge
+ *     midpoints and integrated with the centroid rule.
  *   - The block-diagonal right preconditioner M = A_self of Eq. (3.2) (6x6 per node) and its
  *     exact application by Gaussian elimination with partial pivoting.
  *   - Right-preconditioned restarted GMRES, Eq. (3.1), with modified Gram-Schmidt and Givens
@@ -65,6 +71,12 @@ typedef struct {
     cplx *Sg;                /* [N][2]: self integral of g for (background, own scatterer) */
     cplx *Sdg;               /* [N][2][3]: self integral of grad' g */
     cplx *M;                 /* [N][6][6] preconditioner blocks, row-major */
+    /* near-singular correction (off while ns_rho == 0): the flat pieces of each node's patch,
+     * pieces pc_beg[a] .. pc_beg[a+1]-1, 9 doubles (three corners) each */
+    double ns_rho;
+    int ns_L;
+    int64_t *pc_beg;
+    double *pc_tri;
     char err[256];
 } oracle_ctx;
 
@@ -203,6 +215,109 @@ static int build_nodes(oracle_ctx *c, int64_t nv, const double *V, int64_t nt, c
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* near-singular correction (reading of the option "near_singular_radius"; the paper itself uses
+ * the one-point rule of Eq. (2.8) for every pair beta != alpha).  The patch of a node is the part
+ * of the surface its one-point weight stands for: the triangle itself for centroid nodes; for a
+ * vertex node the barycentric dual cell, i.e. in every incident triangle (A = the vertex, B, C)
+ * the quadrilateral A -> mid(AB) -> centroid -> mid(AC), taken as the two flat pieces
+ * (A, mid(AB), G) and (A, G, mid(AC)) on the triangle itself (not projected).  Their areas add up
+ * to one third of every incident triangle, i.e. exactly to the node weight w.                */
+static void build_patches(oracle_ctx *c, int64_t nv, const double *V, int64_t nt, const int32_t *F) {
+    const int64_t N = c->N;
+    c->pc_beg = calloc(N + 1, sizeof(int64_t));
+    if (c->mode == 1) {
+        c->pc_tri = malloc(sizeof(double) * 9 * nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            c->pc_beg[t + 1] = t + 1;
+            for (int a = 0; a < 3; ++a)
+                for (int k = 0; k < 3; ++k) c->pc_tri[9 * t + 3 * a + k] = V[3 * F[3 * t + a] + k];
+        }
+        return;
+    }
+    (void)nv;
+    for (int64_t t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) c->pc_beg[F[3 * t + a] + 1] += 2;
+    for (int64_t i = 0; i < N; ++i) c->pc_beg[i + 1] += c->pc_beg[i];
+    c->pc_tri = malloc(sizeof(double) * 9 * c->pc_beg[N]);
+    int64_t *fill = calloc(N, sizeof(int64_t));
+    for (int64_t t = 0; t < nt; ++t) {
+        for (int a = 0; a < 3; ++a) {
+            const int32_t v = F[3 * t + a];
+            const double *A = V + 3 * F[3 * t + a], *B = V + 3 * F[3 * t + (a + 1) % 3], *C = V + 3 * F[3 * t + (a + 2) % 3];
+            double mab[3], g[3], mac[3];
+            for (int k = 0; k < 3; ++k) { mab[k] = 0.5 * (A[k] + B[k]); mac[k] = 0.5 * (A[k] + C[k]); g[k] = (A[k] + B[k] + C[k]) / 3.0; }
+            double *p1 = c->pc_tri + 9 * (c->pc_beg[v] + fill[v]++);
+            double *p2 = c->pc_tri + 9 * (c->pc_beg[v] + fill[v]++);
+            for (int k = 0; k < 3; ++k) {
+                p1[k] = A[k]; p1[3 + k] = mab[k]; p1[6 + k] = g[k];
+                p2[k] = A[k]; p2[3 + k] = g[k]; p2[6 + k] = mac[k];
+            }
+        }
+    }
+    free(fill);
+}
+
+/* int g dA' and int grad' g dA' over the triangle (P0, P1, P2) seen from the point sa, with
+ * g = exp(i k R)/(4 pi R), R = |s' - sa|, grad' g = g (i k - 1/R) (s' - sa)/R: the triangle is
+ * split into four by its edge midpoints L times, and each of the 4^L pieces contributes its area
+ * times the integrand at its centroid. */
+static void piece_integral(const double *P0, const double *P1, const double *P2, int L, const double *sa, cplx k,
+                           cplx *G, cplx *A) {
+    if (L > 0) {
+        double m01[3], m12[3], m20[3];
+        for (int q = 0; q < 3; ++q) {
+            m01[q] = 0.5 * (P0[q] + P1[q]);
+            m12[q] = 0.5 * (P1[q] + P2[q]);
+            m20[q] = 0.5 * (P2[q] + P0[q]);
+        }
+        piece_integral(P0, m01, m20, L - 1, sa, k, G, A);
+        piece_integral(m01, P1, m12, L - 1, sa, k, G, A);
+        piece_integral(m20, m12, P2, L - 1, sa, k, G, A);
+        piece_integral(m12, m20, m01, L - 1, sa, k, G, A);
+        return;
+    }
+    double e1[3], e2[3], cr[3], r[3];
+    sub3(P1, P0, e1); sub3(P2, P0, e2); cross3(e1, e2, cr);
+    const double area = 0.5 * norm3(cr);
+    for (int q = 0; q < 3; ++q) r[q] = (P0[q] + P1[q] + P2[q]) / 3.0 - sa[q];
+    const double R = norm3(r);
+    const cplx g = cexp(I * k * R) / (4 * PI * R);
+    const cplx cc = g * (I * k - 1.0 / R) / R;
+    *G += area * g;
+    for (int q = 0; q < 3; ++q) A[q] += area * cc * r[q];
+}
+
+/* the patch integrals of node b seen from sa, summed over its pieces */
+static void patch_integral(const oracle_ctx *c, int64_t b, const double *sa, cplx k, int L, cplx *G, cplx *A) {
+    *G = 0;
+    A[0] = A[1] = A[2] = 0;
+    for (int64_t p = c->pc_beg[b]; p < c->pc_beg[b + 1]; ++p) {
+        const double *T = c->pc_tri + 9 * p;
+        piece_integral(T, T + 3, T + 6, L, sa, k, G, A);
+    }
+}
+
+/* does source b take its patch integral instead of the one-point rule for target distance R? */
+static inline int near_singular(const oracle_ctx *c, int64_t b, double R) {
+    return c->ns_rho > 0 && R < c->ns_rho * sqrt(c->w[b]);
+}
+
+void oracle_set_near_singular(oracle_ctx *c, double rho, int levels) {
+    c->ns_rho = rho;
+    c->ns_L = levels;
+}
+
+/* int g dA' (out[0..1]) and int grad' g dA' (out[2..7]) over node b's patch from the point pt,
+ * wavenumber (kre, kim), L subdivision levels */
+void oracle_patch_integral(const oracle_ctx *c, int64_t b, const double *pt, double kre, double kim, int L,
+                           double *out) {
+    cplx G, A[3];
+    patch_integral(c, b, pt, kre + I * kim, L, &G, A);
+    out[0] = creal(G); out[1] = cimag(G);
+    for (int q = 0; q < 3; ++q) { out[2 + 2 * q] = creal(A[q]); out[3 + 2 * q] = cimag(A[q]); }
+}
+
 /* Self integrals of g and grad' g over the patch with the paper's Taylor truncations:
  * Eq. (B.2)  int g dA      ~ (I1 + i k S) / (4 pi)
  * Eq. (B.4)  int grad g dA ~ -k^2/(8 pi) int r/r dA - 1/(4 pi) CPV int r/r^3 dA             */
@@ -278,6 +393,7 @@ oracle_ctx *oracle_create(int mode, int64_t nv, const double *V, int64_t nt, con
         if (errbuf) snprintf(errbuf, errlen, "%s", c->err);
         return NULL;  /* leaks on the error path; test infrastructure */
     }
+    build_patches(c, nv, V, nt, F);
     self_terms(c);
     build_precond(c);
     return c;
@@ -287,6 +403,7 @@ void oracle_destroy(oracle_ctx *c) {
     if (!c) return;
     free(c->s); free(c->n); free(c->w); free(c->dom); free(c->I1); free(c->S); free(c->V1); free(c->V3);
     free(c->eps); free(c->mu); free(c->k); free(c->gam); free(c->Sg); free(c->Sdg); free(c->M);
+    free(c->pc_beg); free(c->pc_tri);
     free(c);
 }
 
@@ -326,6 +443,28 @@ static void node_rows(const oracle_ctx *c, int64_t a, int64_t n_rhs, const cplx 
         const double wb = c->w[b];
         const double *nb = c->n + 3 * b;
         double n0[3] = {-nb[0], -nb[1], -nb[2]};
+        if (near_singular(c, b, R)) {
+            /* the patch integrals of g and grad' g replace w_b g and w_b grad' g (the density of
+             * node b and its normal held constant over the patch, so the bracket of Eq. (2.12)
+             * takes the integrated gradient) */
+            cplx G0, A0[3], Gj = 0, Aj[3] = {0, 0, 0};
+            patch_integral(c, b, sa, k0, c->ns_L, &G0, A0);
+            const int same_ns = c->dom[b] == j;
+            if (same_ns) patch_integral(c, b, sa, kj, c->ns_L, &Gj, Aj);
+            for (int64_t r = 0; r < n_rhs; ++r) {
+                const cplx *xb = x + (r * N + b) * 6;
+                cplx B[3];
+                bracket(n0, A0, xb, B);
+                for (int q = 0; q < 3; ++q) out[6 * r + q] += -B[q] + G0 * (-xb[3 + q]);
+                if (same_ns) {
+                    cplx Tv[3];
+                    apply_T(c, j, nb, xb, Tv);
+                    bracket(nb, Aj, Tv, B);
+                    for (int q = 0; q < 3; ++q) out[6 * r + 3 + q] += -B[q] + gj * Gj * xb[3 + q];
+                }
+            }
+            continue;
+        }
         /* background domain: every node is a source */
         cplx g0 = cexp(I * k0 * R) / (4 * PI * R);
         cplx c0 = g0 * (I * k0 - 1.0 / R) / R;                /* grad' g = c0 r */
@@ -386,6 +525,32 @@ static void node_cols(const oracle_ctx *c, int64_t b, int64_t n_rhs, const cplx 
         if (a == b) continue;
         double rv[3]; sub3(sb, c->s + 3 * a, rv);            /* r = s_beta - s_alpha, as in node_rows */
         double R = norm3(rv);
+        if (near_singular(c, b, R)) {
+            /* transposed patch-integral blocks of node_rows' near-singular branch */
+            cplx G0, A0[3], Gj = 0, Aj[3] = {0, 0, 0};
+            patch_integral(c, b, c->s + 3 * a, k0, c->ns_L, &G0, A0);
+            const int same_ns = c->dom[a] == j;
+            if (same_ns) patch_integral(c, b, c->s + 3 * a, kj, c->ns_L, &Gj, Aj);
+            for (int64_t r = 0; r < n_rhs; ++r) {
+                const cplx *xa = x + (r * N + a) * 6;
+                cplx B[3];
+                bracket_t(n0, A0, xa, B);
+                for (int q = 0; q < 3; ++q) {
+                    out[6 * r + q] += -B[q];
+                    out[6 * r + 3 + q] += -G0 * xa[q];
+                }
+                if (same_ns) {
+                    cplx TB[3];
+                    bracket_t(nb, Aj, xa + 3, B);
+                    apply_T(c, j, nb, B, TB);
+                    for (int q = 0; q < 3; ++q) {
+                        out[6 * r + q] += -TB[q];
+                        out[6 * r + 3 + q] += gj * Gj * xa[3 + q];
+                    }
+                }
+            }
+            continue;
+        }
         cplx g0 = cexp(I * k0 * R) / (4 * PI * R);
         cplx c0 = g0 * (I * k0 - 1.0 / R) / R;
         cplx a0[3] = {c0 * rv[0], c0 * rv[1], c0 * rv[2]};
