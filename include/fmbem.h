@@ -129,6 +129,20 @@ typedef struct {
                                 0 off, 1 on, -1 automatic: on when the cache (32 bytes per pair and
                                 domain) takes at most a quarter of the free device memory [-1]    */
     int boundary;            /* fmbem_boundary: how the scatterers enter [PENETRABLE]             */
+    double near_singular_radius; /* near-singular correction of the pair terms of Eq. (2.12) [0]:
+                                0 keeps the paper's one-point rule (Eq. 2.8) for every pair;
+                                rho > 0 replaces, for every source node beta within
+                                |s_beta - s_alpha| < rho sqrt(w_beta) of the target, w_beta times the
+                                kernel at s_beta by the integral of the kernel over beta's patch (its
+                                density and normal held constant): the triangle (CENTROID nodes) or
+                                the unprojected barycentric dual cell (VERTEX nodes), each flat piece
+                                cut into 4^near_singular_levels triangles with the centroid rule.
+                                The corrections are computed at create in FP64 and applied in FP64
+                                by every product (either precision) and its transpose.  Needs the
+                                penetrable boundary and rho sqrt(max w) <= the leaf box width
+                                (FMBEM_ERR_INVALID_ARGUMENT otherwise); the vertex-position
+                                gradients refuse handles with rho > 0                            */
+    int near_singular_levels;    /* subdivision levels L of the correction, 0..6 [3]              */
 } fmbem_options;
 
 void fmbem_default_options(fmbem_options *opt);
@@ -175,6 +189,10 @@ int64_t fmbem_num_nodes(const fmbem *h);
 /* Node positions [N][3], outward normals [N][3] and weights [N], host arrays in user order
  * (any of them may be NULL).  Eq. (2.8). */
 fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, double *weight);
+
+/* Number of (target, source) node pairs that take the near-singular correction (0 when
+ * near_singular_radius is 0). */
+int64_t fmbem_num_near_singular_pairs(const fmbem *h);
 
 /* Octree summary: l_max, number of leaves, total number of boxes on levels 2..l_max, and the
  * number of near-field (source, target) node pairs and of far-field box pairs (S|R

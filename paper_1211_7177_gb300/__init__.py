@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
     _fields_ = [("node_mode", ctypes.c_int), ("p", ctypes.c_int), ("leaf_size", ctypes.c_int),
                 ("max_level", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("solve_precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("outer_precision", ctypes.c_int), ("m2l_rotation", ctypes.c_int),
-                ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("near_singular_radius", ctypes.c_double), ("near_singular_levels", ctypes.c_int)]
 
 
 class Mesh(ctypes.Structure):
@@ -73,6 +74,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_destroy": (None, [P]),
         "fmbem_last_error": (ctypes.c_char_p, [P]),
         "fmbem_num_nodes": (i64, [P]),
+        "fmbem_num_near_singular_pairs": (i64, [P]),
         "fmbem_node_geometry": (i32, [P, P, P, P]),
         "fmbem_tree_info": (i32, [P, P, P, P, P, P]),
         "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
@@ -169,6 +171,10 @@ def fmbem_last_error(h):
 
 def fmbem_num_nodes(h):
     return int(load_library().fmbem_num_nodes(h))
+
+
+def fmbem_num_near_singular_pairs(h):
+    return int(load_library().fmbem_num_near_singular_pairs(h))
 
 
 def fmbem_node_geometry(h):
@@ -446,6 +452,9 @@ class FMBEM:
 
     def tree_info(self):
         return fmbem_tree_info(self.h)
+
+    def num_near_singular_pairs(self):
+        return fmbem_num_near_singular_pairs(self.h)
 
     def plane_wave_rhs(self, dirs, pols, out=None, stream=None):
         return fmbem_plane_wave_rhs(self.h, dirs, pols, out, stream)

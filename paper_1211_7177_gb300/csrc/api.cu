@@ -110,6 +110,8 @@ void fmbem_default_options(fmbem_options *o) {
     o->near_cache = -1;
     o->profile_phases = 0;
     o->boundary = FMBEM_BOUNDARY_PENETRABLE;
+    o->near_singular_radius = 0.0;
+    o->near_singular_levels = 3;
 }
 
 fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
@@ -134,7 +136,9 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         !(o.inner_tol > 0 && o.inner_tol < 1) ||
         (o.outer_precision != FMBEM_FP64 && o.outer_precision != FMBEM_FP32) || o.m2l_rotation < -1 ||
         o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1 ||
-        (o.boundary != FMBEM_BOUNDARY_PENETRABLE && o.boundary != FMBEM_BOUNDARY_IMPEDANCE)) {
+        (o.boundary != FMBEM_BOUNDARY_PENETRABLE && o.boundary != FMBEM_BOUNDARY_IMPEDANCE) ||
+        !(o.near_singular_radius >= 0 && std::isfinite(o.near_singular_radius)) || o.near_singular_levels < 0 ||
+        o.near_singular_levels > 6) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
@@ -190,6 +194,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         h->dcons = (c64 *)dev_alloc(h, sizeof(c64) * dc.size());
         CK(cudaMemcpyAsync(h->dcons, dc.data(), sizeof(c64) * dc.size(), cudaMemcpyHostToDevice, s));
         build_near_cache(h, s);
+        build_near_singular(h, mesh, s);
         if (h->profile)
             for (auto &e : h->ev) CK(cudaEventCreate(&e));
         CK(cudaStreamSynchronize(s));
@@ -214,6 +219,8 @@ void fmbem_destroy(fmbem *h) {
 const char *fmbem_last_error(const fmbem *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 int64_t fmbem_num_nodes(const fmbem *h) { return h ? h->N : 0; }
+
+int64_t fmbem_num_near_singular_pairs(const fmbem *h) { return h ? h->ns_pairs : 0; }
 
 fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, double *weight) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
@@ -349,6 +356,10 @@ fmbem_status fmbem_shape_gradient(fmbem *h, const void *x_dev, const void *lam_d
         h->err = "invalid argument (n_rhs in 1..65535, non-NULL x, lambda, dir, pol, rhat, coef and out)";
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
+    if (h->ns_pairs > 0) {
+        h->err = "the vertex-position gradient does not differentiate the near-singular correction (near_singular_radius > 0)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
     return guarded(h, [&] {
         run_shape_gradient(h, (const c64 *)x_dev, (const c64 *)lam_dev, n_rhs, dir, (const c64 *)pol, rhat,
                            (const c64 *)coef, 0, nullptr, nullptr, nullptr, (c64 *)out_host, (cudaStream_t)stream);
@@ -361,6 +372,10 @@ fmbem_status fmbem_shape_gradient_near(fmbem *h, const void *x_dev, const void *
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (n_rhs < 1 || n_rhs > 65535 || n_pts < 1 || !x_dev || !lam_dev || !dir || !pol || !pts || !cE || !out_host) {
         h->err = "invalid argument (n_rhs in 1..65535, n_pts >= 1, non-NULL x, lambda, dir, pol, pts, cE and out)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    if (h->ns_pairs > 0) {
+        h->err = "the vertex-position gradient does not differentiate the near-singular correction (near_singular_radius > 0)";
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
     return guarded(h, [&] {

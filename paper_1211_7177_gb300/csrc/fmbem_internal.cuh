@@ -138,6 +138,13 @@ struct fmbem {
     // precision; near_base[leaf] = pairs of the leaves before it
     void *near_cache64 = nullptr;
     int64_t *near_base = nullptr;
+    // near-singular correction (nearsing.cu): pairs by target [ns_start[a], ns_start[a+1]) with
+    // user-order target and source, 8 complex coefficients each (dS, dA for the background and
+    // the scatterer side), and the pairs by source for the transposed product
+    int64_t ns_pairs = 0;
+    int64_t *ns_start = nullptr, *ns_tstart = nullptr, *ns_tpair = nullptr;
+    int32_t *ns_tgt = nullptr, *ns_src = nullptr;
+    c64 *ns_coef = nullptr;
     int32_t max_leaf = 0;                                 // largest leaf occupancy
     std::vector<int64_t> h_ff_count_level;
     // FF pairs of each level regrouped by translation offset, for the chunked M2L kernel:
@@ -302,6 +309,8 @@ void build_rot_mm_lists(fmbem *h, cudaStream_t s);
 void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s);
 void near_work_items(fmbem *h, cudaStream_t s);
 void build_near_cache(fmbem *h, cudaStream_t s);
+void build_near_singular(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s);
+void apply_near_singular(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, bool transpose);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);
 void run_precond32(fmbem *h, const c32 *v, c64 *z, int64_t n_rhs, cudaStream_t s, bool transpose = false);
 void run_precond_t(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);

@@ -2861,6 +2861,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
         k_local_rows<<<nblk(N * nr, 128), 128, 0, s>>>(N, nr, h->Mself, x, y);
         CKL("k_local_rows");
     }
+    apply_near_singular(h, x, y, nr, s, false);  // near-singular pair corrections (option), FP64
     if (timing) CK(cudaEventRecord(h->ev[4], s));
 }
 
@@ -2902,6 +2903,7 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
                                                            h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
                                                            h->near_base, cache);
     CKL("k_near_adj");
+    apply_near_singular(h, x, y, nr, s, true);  // transposed near-singular pair corrections (option)
 }
 
 // the bounded mbarrier waits of the tensor-core kernel report time-outs in h->tc_err

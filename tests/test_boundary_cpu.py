@@ -157,3 +157,18 @@ int main(void) {
     assert out.returncode == 0, out.stderr
     p, leaf, st, null, *msg = out.stdout.split(maxsplit=4)
     assert (p, leaf, st, null) == ("8", "64", "2", "1"), out.stdout
+
+
+def test_near_singular_options_validated_before_device_work():
+    """The near-singular correction is off by default (radius 0, the paper's one-point rule);
+    a negative or non-finite radius and subdivision levels outside 0..6 are refused before any
+    device work; fmbem_num_near_singular_pairs takes a NULL handle as zero pairs."""
+    o = fm.fmbem_default_options()
+    assert o.near_singular_radius == 0.0 and o.near_singular_levels == 3
+    V, F, D = fi.icosphere(1)
+    for kw in (dict(near_singular_radius=-1.0), dict(near_singular_radius=float("nan")),
+               dict(near_singular_radius=1.5, near_singular_levels=7), dict(near_singular_levels=-1)):
+        with pytest.raises(fm.FMBEMError) as e:
+            _create(V, F, D, **kw)
+        assert e.value.status == 1, kw
+    assert fm.load_library().fmbem_num_near_singular_pairs(None) == 0
