@@ -15,9 +15,10 @@ FP32-inner / FP64-outer refined solve, and the FP64 CPU oracle timed on a bounde
 
 The default run adds a ``batched`` object: the batched mixed-precision form on the torus
 R=1, r=0.25 (512x128 grid, 65536 nodes, eps=-10+0.4i, k0 R=1.5) with 128 plane waves -- the
-128-RHS matvec with M2L + L2L on the TF32 tensor cores (device time and e2e, per-phase rooflines),
+128-RHS matvec with M2L + L2L on the tensor cores in the BF16x3 form (bf16 hi/lo split operands,
+three products per step; device time and e2e, per-phase rooflines; the TF32 form's time beside it),
 the FP64 single-RHS matvec on the same mesh, the plain FP64 single-RHS solve and the batched solve
-(TF32 inner GMRES, FP64-operator true residual) to 1e-4, and the FP64 oracle on sampled rows
+(BF16x3 inner GMRES, FP64-operator true residual) to 1e-4, and the FP64 oracle on sampled rows
 (timed, with the matvec error and the batched solution's residual against the dense operator).
 ``--workload torus_512x128`` runs the 128-right-hand-side batch as the main line instead.
 
@@ -99,7 +100,7 @@ def parse():
     ap.add_argument("--restart", type=int, default=50, help="GMRES restart length of the timed solves")
     ap.add_argument("--n-rhs", type=int, default=0, help="right-hand sides (0 = the workload's)")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batched leg (128-RHS torus, TF32 M2L, FP64-refined solve) of the default run")
+                    help="skip the batched leg (128-RHS torus, BF16x3 tensor-core M2L, FP64-refined solve) of the default run")
     return ap.parse_args()
 
 
@@ -340,12 +341,24 @@ def phase_traffic(workload, precision, nr, phase):
     return t["bytes"]
 
 
-def phase_rooflines(info, p, nr, n_dom, N, phases, workload):
-    """Per-phase roofline of the TF32 batched matvec: near field against the FP32 ALU peak,
-    M2L + L2L against the TF32 tensor peak, P2M and M2M against the FP32 ALU peak."""
+def tensor_peak_bf16x3():
+    """Effective tensor peak of the BF16x3 form: the measured cuBLAS BF16 burst rate over the three
+    bf16 products that carry one algorithmic product."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16, src = float(json.load(f)["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1900.0, "of fallback"
+    return bf16 / 3, f"{src} BF16 GEMM burst rate / 3 (three bf16 products per algorithmic product)"
+
+
+def phase_rooflines(info, p, nr, n_dom, N, phases, workload, form="bf16x3"):
+    """Per-phase roofline of the batched matvec: near field against the FP32 ALU peak, M2L + L2L
+    (algorithmic flops of the dense complex contraction) against the tensor peak of the form
+    (BF16x3: the BF16 rate over three; TF32), P2M and M2M against the FP32 ALU peak."""
     keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
     avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
-    tpk, tsrc = tensor_peak_tf32()
+    tpk, tsrc = tensor_peak_bf16x3() if form == "bf16x3" else tensor_peak_tf32()
     cols = 3 * nr * n_dom
     flops = {
         # per (near pair, domain): the kernel scalars; per (pair, domain, RHS): the bracket and g q
@@ -364,7 +377,7 @@ def phase_rooflines(info, p, nr, n_dom, N, phases, workload):
         ach = flops[k] / (avg[k] * 1e-3) / 1e12
         out[k] = dict(bound="tensor" if tensor else "alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                       ms=avg[k], algorithmic_flops=flops[k],
-                      traffic=phase_traffic(workload, "tf32", nr, k),
+                      traffic=phase_traffic(workload, form, nr, k),
                       peak_source=tsrc if tensor else "measured FP32 FMA throughput of GB300 (self-written probe)")
     return out, avg
 
@@ -372,9 +385,10 @@ def phase_rooflines(info, p, nr, n_dom, N, phases, workload):
 def run_batched(args, world, flush):
     """Batched, mixed-precision form on the torus: R = 1, r = 0.25, 512 x 128 grid (65536 nodes),
     eps = -10 + 0.4i, k0 R = 1.5, 128 plane waves (64 Fibonacci directions x 2 polarisations),
-    p = 8.  Times the 128-RHS matvec with the M2L on the TF32 tensor cores (device and e2e), the
+    p = 8.  Times the 128-RHS matvec with the M2L on the tensor cores in the BF16x3 form (device
+    and e2e; the TF32 form beside it), the
     FP64 single-RHS matvec on the same mesh, the plain FP64 single-RHS solve and the batched solve
-    (TF32-operator inner GMRES, FP64-operator true residual) to 1e-4; on rank 0 the FP64 oracle
+    (BF16x3-operator inner GMRES, FP64-operator true residual) to 1e-4; on rank 0 the FP64 oracle
     evaluates sampled rows, timed, giving the matvec error and the solve's residual against the
     dense operator."""
     import torch
@@ -416,11 +430,12 @@ def run_batched(args, world, flush):
         torch.cuda.synchronize()
         return max_over_ranks(statistics.mean(a.elapsed_time(bb) for a, bb in ev), "cuda"), ph
 
-    ms, phases = time_matvec(x, y, fm.TF32, args.steps, args.warmup)
+    ms, phases = time_matvec(x, y, fm.BF16X3, args.steps, args.warmup)
     roof, avg = phase_rooflines(info, p, nr, n_dom, N, phases, name)
     dom = max(avg, key=avg.get)
     out = dict(workload=name, desc=wl["desc"], nodes=N, n_rhs=nr, p=p, leaf_size=args.leaf, tree=info,
-               dtype="f32 (M2L on TF32 tensor cores)", setup_s=setup_s,
+               dtype="f32 (M2L + L2L on the tensor cores: bf16 hi/lo split operands, three products, FP32 "
+                     "accumulation)", setup_s=setup_s,
                l2="inputs larger than L2 and L2 flushed (256 MiB write) before each step",
                value=job_throughput(N * nr, world, ms), unit=UNIT, ms_per_step=ms, steps=args.steps,
                roofline=dict(roof[dom], kernel=dom), phase_roofline=roof)
@@ -434,7 +449,7 @@ def run_batched(args, world, flush):
         flush.fill_(float(k))
         e0.record(stream)
         x.copy_(xh, non_blocking=True)
-        g.matvec(x, y, precision=fm.TF32)
+        g.matvec(x, y, precision=fm.BF16X3)
         yh.copy_(y, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
@@ -443,7 +458,11 @@ def run_batched(args, world, flush):
     nbytes = x.numel() * 16
     out["e2e"] = dict(value=world * N * nr / (statistics.mean(e2e_ms) * 1e-3), unit=UNIT,
                       h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes)
-    y_tf32 = yh.numpy().copy()
+    y_bf3 = yh.numpy().copy()
+    # the TF32 operand form of the same product, for comparison (faster rounding, less accurate)
+    ms_tf, _ = time_matvec(x, y, fm.TF32, args.steps, 2, with_phases=False)
+    y_tf32 = y.cpu().numpy()
+    out["tf32_form"] = dict(value=job_throughput(N * nr, world, ms_tf), unit=UNIT, ms_per_step=ms_tf)
 
     # the plain method's form on the same mesh: FP64 arithmetic, one right-hand side per matvec
     x1, y1 = x[:1].contiguous(), y[:1].contiguous()
@@ -469,11 +488,11 @@ def run_batched(args, world, flush):
                                               status=int(st), restart=restart)
         gp.close()
         del gp
-        # batched: inner GMRES(100) with the TF32 tensor-core operator to 1e-2 (above the floor its
-        # input rounding sets) and a single-precision basis; outer true residual b - A x with the
-        # FP64 operator and FP64 vectors, repeated until it is <= 1e-4
+        # batched: inner GMRES(100) with the BF16x3 tensor-core operator to 1e-2 and a
+        # single-precision basis; outer true residual b - A x with the FP64 operator and FP64
+        # vectors, repeated until it is <= 1e-4
         gb = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, m2l_rotation=1,
-                      gmres_restart=restart, solve_precision=fm.TF32, inner_tol=1e-2, outer_precision=fm.FP64)
+                      gmres_restart=restart, solve_precision=fm.BF16X3, inner_tol=1e-2, outer_precision=fm.FP64)
         xs = torch.zeros_like(b)
         gb.solve(b, xs, tol=1e-4, max_iter=2)  # warm-up
         xs.zero_()
@@ -482,7 +501,7 @@ def run_batched(args, world, flush):
         _, its, rr, st = gb.solve(b, xs, tol=1e-4, max_iter=2000)
         torch.cuda.synchronize()
         t_b = time.perf_counter() - s0
-        solve["batched_tf32_inner_fp64_outer"] = dict(
+        solve["batched_bf16x3_inner_fp64_outer"] = dict(
             tol=1e-4, ms=1e3 * t_b, ms_per_rhs=1e3 * t_b / nr, iters=int(its.max()), relres_fp64_true=float(rr.max()),
             status=int(st), restart=restart, inner_tol=1e-2, n_rhs=nr)
         solve["per_rhs_speedup_vs_plain"] = t_plain / (t_b / nr)
@@ -493,7 +512,7 @@ def run_batched(args, world, flush):
 
     if rank == 0 and not args.no_cpu_baseline:
         # the FP64 CPU oracle on 32 seeded node rows for all 128 right-hand sides (timed: the
-        # batched leg's cpu_baseline); the same rows give the TF32 matvec's error and the refined
+        # batched leg's cpu_baseline); the same rows give the tensor-core matvecs' errors and the refined
         # solution's true residual against the dense FP64 operator
         import oracle
         o = oracle.Oracle(V, F, D, wl["eps"], wl["mu"], wl["k0"])
@@ -504,8 +523,8 @@ def run_batched(args, world, flush):
         t_or = time.perf_counter() - t0
         out["cpu_baseline"] = dict(value=len(rows) * nr / t_or, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
                                    sample=f"{len(rows)} seeded node rows x {nr} RHS of the {N}-node dense FP64 operator")
-        yg = y_tf32[:, rows]
-        acc = dict(rows=len(rows), matvec_rel_l2_vs_oracle=float(np.linalg.norm(yg - yo) / np.linalg.norm(yo)))
+        err = lambda a: float(np.linalg.norm(a[:, rows] - yo) / np.linalg.norm(yo))
+        acc = dict(rows=len(rows), matvec_rel_l2_vs_oracle=err(y_bf3), tf32_form_rel_l2_vs_oracle=err(y_tf32))
         if solve:
             bo = o.plane_wave_rhs(dirs, pols)[:, rows]
             ro = o.matvec_rows(xs_h, rows) - bo

@@ -68,8 +68,13 @@ typedef enum { FMBEM_NODES_VERTEX = 0, FMBEM_NODES_CENTROID = 1 } fmbem_node_mod
  * L2L products run on the tensor cores (tcgen05.mma, inputs rounded to TF32, FP32 accumulation
  * in tensor memory); meant for the inner iterations of the refined solve.  The rounding adds a
  * relative error of about 1e-5 to a matvec and makes it slightly nonlinear, so an inner GMRES
- * on it should stop at a loose tolerance (1e-2) and let the outer refinement finish. */
-typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1, FMBEM_TF32 = 2 } fmbem_precision;
+ * on it should stop at a loose tolerance (1e-2) and let the outer refinement finish.
+ * BF16X3: as TF32, except that the tensor-core M2L and L2L products run on bf16 operands split
+ * into hi and lo parts (x = x_hi + x_lo, each bf16) and accumulate A_hi B_hi + A_hi B_lo +
+ * A_lo B_hi in FP32 (tcgen05.mma kind::f16): three times the MMAs of TF32 at twice its rate, the
+ * same bytes, and a rounding error of ~2^-16 instead of ~2^-11 per product, so the product stays
+ * within the FP32 path's accuracy (FP32 itself below 16 right-hand sides). */
+typedef enum { FMBEM_FP64 = 0, FMBEM_FP32 = 1, FMBEM_TF32 = 2, FMBEM_BF16X3 = 3 } fmbem_precision;
 
 /* How the scatterers are modelled (Section 2).
  * PENETRABLE: the interior fields are unknowns too; Eqs. (2.5)-(2.13), 6N equations.

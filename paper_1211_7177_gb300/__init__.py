@@ -25,7 +25,7 @@ __all__ = [
     "fmbem_solve", "fmbem_precond_apply", "fmbem_last_matvec_times", "FP64", "FP32", "FMBEMError",
 ]
 
-FP64, FP32, TF32 = 0, 1, 2
+FP64, FP32, TF32, BF16X3 = 0, 1, 2, 3
 NODES_VERTEX, NODES_CENTROID = 0, 1
 # boundary option: penetrable scatterers (Eqs. 2.5-2.13) or the impedance condition of Eq. (2.24)
 PENETRABLE, IMPEDANCE = 0, 1

@@ -132,7 +132,8 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
     const fmbem_options &o = h->opt;
     if ((o.node_mode != FMBEM_NODES_VERTEX && o.node_mode != FMBEM_NODES_CENTROID) || o.p < 2 || o.p > 20 ||
         o.leaf_size < 1 || o.max_level < 2 || o.gmres_restart < 1 || o.gmres_restart > 500 ||
-        (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32 && o.solve_precision != FMBEM_TF32) ||
+        (o.solve_precision != FMBEM_FP64 && o.solve_precision != FMBEM_FP32 && o.solve_precision != FMBEM_TF32 &&
+         o.solve_precision != FMBEM_BF16X3) ||
         !(o.inner_tol > 0 && o.inner_tol < 1) ||
         (o.outer_precision != FMBEM_FP64 && o.outer_precision != FMBEM_FP32) || o.m2l_rotation < -1 ||
         o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1 ||
@@ -255,8 +256,8 @@ fmbem_status fmbem_plane_wave_rhs(fmbem *h, int64_t n_rhs, const double *dir, co
 fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision, void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (n_rhs < 1 || !x_dev || !y_dev || x_dev == y_dev ||
-        (precision != FMBEM_FP64 && precision != FMBEM_FP32 && precision != FMBEM_TF32)) {
-        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64, FP32 or TF32)";
+        (precision != FMBEM_FP64 && precision != FMBEM_FP32 && precision != FMBEM_TF32 && precision != FMBEM_BF16X3)) {
+        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64, FP32, TF32 or BF16X3)";
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
     return guarded(h, [&] { run_matvec(h, (const c64 *)x_dev, (c64 *)y_dev, n_rhs, precision, (cudaStream_t)stream); });
@@ -265,8 +266,9 @@ fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rh
 fmbem_status fmbem_adjoint_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,
                                   void *stream) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
-    if (n_rhs < 1 || !x_dev || !y_dev || x_dev == y_dev || (precision != FMBEM_FP64 && precision != FMBEM_FP32 && precision != FMBEM_TF32)) {
-        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64, FP32 or TF32)";
+    if (n_rhs < 1 || !x_dev || !y_dev || x_dev == y_dev ||
+        (precision != FMBEM_FP64 && precision != FMBEM_FP32 && precision != FMBEM_TF32 && precision != FMBEM_BF16X3)) {
+        h->err = "invalid argument (n_rhs >= 1, distinct non-NULL x and y, precision FP64, FP32, TF32 or BF16X3)";
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
     return guarded(h, [&] {

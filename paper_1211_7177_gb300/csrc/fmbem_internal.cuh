@@ -168,6 +168,7 @@ struct fmbem {
     c32 *T_m2l32 = nullptr, *T_mm32 = nullptr, *T_ll32 = nullptr;
     // tensor-core (tcgen05, TF32) M2L tables: real-form 128-byte-swizzled images, see m2l_tc.cu
     float *Atc = nullptr, *Lltc = nullptr;
+    float *Abf = nullptr, *Llbf = nullptr;  // the same matrices as bf16 hi/lo images (BF16x3)
     int *tc_err = nullptr;
     bool m2l_rotation = false;
     int n_tlen = 0;
@@ -302,7 +303,7 @@ void run_far_field(fmbem *h, const c64 *x, int64_t n_rhs, int64_t n_dir, const d
 void run_absorption(fmbem *h, const c64 *x, int64_t n_rhs, double *out_host, cudaStream_t s);
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
-void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s);
+void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
 void pack_rot_tables_mm(fmbem *h, cudaStream_t s);
 void build_rot_mm_lists(fmbem *h, cudaStream_t s);

@@ -2604,7 +2604,8 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
 
 // downward pass (Eq. 2.21): M2L over the FF lists and L2L, h->Cexp -> h->Dexp, all levels
 template <typename R>
-static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_cores) {
+// tensor_mode: 0 CUDA cores, 1 TF32 tensor cores, 2 BF16x3 tensor cores (many columns)
+static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode) {
     const int p2 = h->p2, lmax = h->lmax, J = h->Jf;
     const bool f32 = sizeof(R) == 4;
     cx<R> *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
@@ -2642,8 +2643,8 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, bool tensor_core
                         : rot_many && rl.ok && h->ybuf_bytes >= ybuf_need(h, ncol, sizeof(cx<R>))) &&
         h->ybuf != nullptr && rows_pad <= max_thr;
     const bool use_rot = chunked && rl.ok;
-    if (tensor_cores && f32 && h->Atc != nullptr && 3 * nr >= 48) {
-        run_m2l_tc(h, (float *)C, (float *)D, nr, s);
+    if (tensor_mode && f32 && h->Atc != nullptr && 3 * nr >= 48) {
+        run_m2l_tc(h, (float *)C, (float *)D, nr, s, tensor_mode == 2);
     } else if (chunked) {
         if (tsm) CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
@@ -2748,7 +2749,7 @@ static void clear_unused_domains(fmbem *h, int64_t nr, size_t real_bytes, cudaSt
 
 template <typename R>
 static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
-                        bool tensor_cores = false) {
+                        int tensor_mode = 0) {
     const int64_t N = h->N;
     const int p2 = h->p2, lmax = h->lmax, J = h->Jf;  // multipole passes over domains 0..Jf
     const bool f32 = sizeof(R) == 4;
@@ -2789,7 +2790,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     if (timing) CK(cudaEventRecord(h->ev[1], s));
     upward_m2m<R>(h, nr, s);
     if (timing) CK(cudaEventRecord(h->ev[2], s));
-    downward_pass<R>(h, nr, s, tensor_cores);
+    downward_pass<R>(h, nr, s, tensor_mode);
     if (timing) CK(cudaEventRecord(h->ev[3], s));
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
@@ -2868,7 +2869,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
 // y = A^T x (see k_near_adj): monopole P2M, M2M, the downward pass, near field and assembly
 template <typename R>
 static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
-                         bool tensor_cores = false) {
+                         int tensor_mode = 0) {
     const int64_t N = h->N;
     const int p2 = h->p2, lmax = h->lmax, J = h->Jf;  // multipole passes over domains 0..Jf
     const bool f32 = sizeof(R) == 4;
@@ -2888,7 +2889,7 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
                                                                            h->box_nend, h->dom, dens, Bp2m, C);
     CKL("k_p2m_adj");
     upward_m2m<R>(h, nr, s);
-    downward_pass<R>(h, nr, s, tensor_cores);
+    downward_pass<R>(h, nr, s, tensor_mode);
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
     const V4<R> *cache = f32 ? nullptr : (const V4<R> *)h->near_cache64;
@@ -2921,8 +2922,8 @@ static void check_tc_err(fmbem *h, cudaStream_t s) {
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
     ensure_scratch(h, nr, precision);
     const DomainConsts *dc = (const DomainConsts *)h->dcons;
-    if (precision == FMBEM_TF32) {
-        adjoint_impl<float>(h, x, y, nr, s, dc, true);
+    if (precision == FMBEM_TF32 || precision == FMBEM_BF16X3) {
+        adjoint_impl<float>(h, x, y, nr, s, dc, precision == FMBEM_TF32 ? 1 : 2);
         check_tc_err(h, s);
     } else if (precision == FMBEM_FP32) {
         adjoint_impl<float>(h, x, y, nr, s, dc);
@@ -2935,8 +2936,8 @@ void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaS
     ensure_scratch(h, nr, precision);
     static_assert(sizeof(DomainConsts) == 3 * sizeof(c64), "layout");
     DomainConsts *dc = (DomainConsts *)h->dcons;
-    if (precision == FMBEM_TF32) {
-        matvec_impl<float>(h, x, y, nr, s, dc, true);
+    if (precision == FMBEM_TF32 || precision == FMBEM_BF16X3) {
+        matvec_impl<float>(h, x, y, nr, s, dc, precision == FMBEM_TF32 ? 1 : 2);
         check_tc_err(h, s);
     } else if (precision == FMBEM_FP32) {
         matvec_impl<float>(h, x, y, nr, s, dc);

@@ -22,7 +22,16 @@
 // four warps read the accumulators with tcgen05.ld and write D.  Every mbarrier wait is bounded (2 s by
 // %globaltimer); on time-out the kernel raises an error flag, stops issuing work, waits (bounded)
 // for its own copies and MMAs in flight, frees its tensor memory and returns.
+//
+// The BF16x3 form (precision FMBEM_BF16X3) runs the same chain with kind::f16 MMAs on bf16
+// operands: every real-form value x is split into x_hi = bf16(x) and x_lo = bf16(x - x_hi), and
+// each product is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is
+// ~2^-16 of the product), which brings the rounding error from TF32's ~2^-11 to ~2^-16 per
+// product while moving the same bytes: a 32-element K block of hi and lo bf16 rows is 64 + 64
+// bytes, staged with the 64-byte swizzle.  The expansions C are split once before the pass and
+// the local expansions of non-leaf levels are split in the epilogue for the next level's L2L.
 #include <cuda.h>  // CUtensorMap and its enums; the encoder itself is looked up at run time
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <string>
@@ -59,6 +68,26 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
 // instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = n
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+// instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+// bf16 index of element (row, k) of one K block (32 bf16 = 64 bytes per row) in the 64-byte-swizzled
+// K-major layout: the 16-byte chunk c of row m stored at chunk c ^ ((m / 2) mod 4)
+__host__ __device__ __forceinline__ int sw64_index(int row, int k) {
+    return row * KBLK + ((((k >> 3) ^ (row >> 1)) & 3) << 3) + (k & 7);
+}
+
+// shared-memory matrix descriptor, K-major, 64-byte swizzle: 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;           // descriptor version of the sm_100 family
+    d |= (uint64_t)4 << 61;           // 64-byte swizzle
+    return d;
 }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -119,6 +148,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *m) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(m))
                  : "memory");
@@ -135,11 +172,17 @@ struct TcLevel {
     int round_out;        // round D to TF32 (it feeds the next level's L2L product)
 };
 
+// BF3 = false: TF32 operands (tmC, tmD over the TF32-rounded FP32 expansions, A images of TF32
+// values).  BF3 = true: bf16 hi/lo operands (tmC/tmD over the hi parts, tmC2/tmD2 over the lo
+// parts, A images of [hi | lo] 8 KiB halves per K block), three products per K step, and on
+// non-leaf levels the epilogue also writes the hi/lo split of D (Dh, Dl) for the next level.
+template <bool BF3>
 __global__ void __launch_bounds__(128, 1)
-    k_m2l_tc(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmD, const TcLevel P,
+    k_m2l_tc(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmD,
+             const __grid_constant__ CUtensorMap tmC2, const __grid_constant__ CUtensorMap tmD2, const TcLevel P,
              const int32_t *__restrict__ parent, const uint64_t *__restrict__ key, const int32_t *__restrict__ ff_start,
              const int32_t *__restrict__ ff_src, const int16_t *__restrict__ ff_off, const float *__restrict__ Atc,
-             const float *__restrict__ Lltc, float *D, int *err) {
+             const float *__restrict__ Lltc, float *D, __nv_bfloat16 *Dh, __nv_bfloat16 *Dl, int *err) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[MAX_STAGES], empty[MAX_STAGES], done;
     __shared__ uint32_t tmem_slot;
@@ -163,6 +206,10 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmD)) : "memory");
+        if (BF3) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC2)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmD2)) : "memory");
+        }
     }
     if (warp == 0)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -190,40 +237,60 @@ __global__ void __launch_bounds__(128, 1)
             if (s_abort || *(volatile int *)err) break;
             const int i = u / P.kblocks, kb = u - i * P.kblocks;
             const float *Asrc;
-            const CUtensorMap *tm;
+            const CUtensorMap *tm, *tm2;
             int y;
             if (has_l2l && i == 0) {
                 Asrc = Lltc + (tbl * 8 + (int)(key[g] & 7)) * a_mat;
                 tm = &tmD;
+                tm2 = &tmD2;
                 y = (int)(((int64_t)d * P.nbox + parent[g]) * P.ncols + col0);
             } else {
                 const int e = e0 + i - has_l2l;
                 Asrc = Atc + (tbl * 316 + ff_off[e]) * a_mat;
                 tm = &tmC;
+                tm2 = &tmC2;
                 y = (int)(((int64_t)d * P.nbox + ff_src[e]) * P.ncols + col0);
             }
             const uint32_t sA = sbase + (uint32_t)s * stage_bytes, sB = sA + A_KB_BYTES;
             mbar_arrive_expect_tx(&full[s], stage_bytes);
             bulk_load(sA, Asrc + (int64_t)kb * (A_KB_BYTES / 4), A_KB_BYTES, &full[s]);
-            for (int j = 0; j < P.nsub; ++j) tma_load_2d(sB + j * b_bytes, tm, kb * KBLK, y + j * P.n, &full[s]);
+            for (int j = 0; j < P.nsub; ++j) {
+                tma_load_2d(sB + j * b_bytes, tm, kb * KBLK, y + j * P.n, &full[s]);
+                // bf16: the lo rows follow the n hi rows of 64 bytes
+                if (BF3) tma_load_2d(sB + j * b_bytes + (uint32_t)P.n * 64u, tm2, kb * KBLK, y + j * P.n, &full[s]);
+            }
             ++issued;
             if (++s == P.stages) { s = 0; ++q; }
         }
         if (!ok) { atomicExch(err, 1); s_abort = 1; }
     } else if (threadIdx.x == 32 && nunits > 0) {
         // ------------------------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_tf32(P.n);
+        const uint32_t idesc = BF3 ? idesc_bf16(P.n) : idesc_tf32(P.n);
         bool ok = true;
         int s = 0, q = 0;
         for (int u = 0; u < nunits && !s_abort; ++u) {
             if (!mbar_wait(&full[s], (uint32_t)q & 1u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sA = sbase + (uint32_t)s * stage_bytes, sB = sA + A_KB_BYTES;
-            for (int t = 0; t < P.nsub; ++t)  // one accumulator of n TMEM columns per sub-tile
+            for (int t = 0; t < P.nsub; ++t) {  // one accumulator of n TMEM columns per sub-tile
+                const uint32_t acc = tmem + (uint32_t)(t * P.n);
+                if (BF3) {
 #pragma unroll
-                for (int j = 0; j < KBLK / 8; ++j)  // K = 8 TF32 per MMA = 32 bytes along the swizzled row
-                    mma_tf32(tmem + (uint32_t)(t * P.n), smem_desc_sw128(sA + 32u * j),
-                             smem_desc_sw128(sB + t * b_bytes + 32u * j), idesc, (u > 0 || j > 0) ? 1u : 0u);
+                    for (int j = 0; j < 2; ++j) {  // K = 16 bf16 per MMA = 32 bytes along the 64-byte row
+                        const uint64_t ah = smem_desc_sw64(sA + 32u * j), al = smem_desc_sw64(sA + 8192u + 32u * j);
+                        const uint64_t bh = smem_desc_sw64(sB + t * b_bytes + 32u * j);
+                        const uint64_t bl = smem_desc_sw64(sB + t * b_bytes + (uint32_t)P.n * 64u + 32u * j);
+                        mma_bf16(acc, ah, bh, idesc, (u > 0 || j > 0) ? 1u : 0u);
+                        mma_bf16(acc, ah, bl, idesc, 1u);
+                        mma_bf16(acc, al, bh, idesc, 1u);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < KBLK / 8; ++j)  // K = 8 TF32 per MMA = 32 bytes along the swizzled row
+                        mma_tf32(acc, smem_desc_sw128(sA + 32u * j), smem_desc_sw128(sB + t * b_bytes + 32u * j), idesc,
+                                 (u > 0 || j > 0) ? 1u : 0u);
+                }
+            }
             mma_commit(&empty[s]);
             if (++s == P.stages) { s = 0; ++q; }
         }
@@ -244,6 +311,13 @@ __global__ void __launch_bounds__(128, 1)
     float *Dout = D + (((int64_t)d * P.nbox + g) * P.ncols + col0) * 2 * P.p2;
     if (nprod == 0) {  // no translation reaches this box: its local expansion is zero
         for (int i = threadIdx.x; i < nh * 2 * P.p2; i += blockDim.x) Dout[i] = 0.f;
+        if (BF3 && P.round_out) {
+            const int64_t ob = (((int64_t)d * P.nbox + g) * P.ncols + col0) * 2 * P.p2;
+            for (int i = threadIdx.x; i < nh * 2 * P.p2; i += blockDim.x) {
+                Dh[ob + i] = __float2bfloat16_rn(0.f);
+                Dl[ob + i] = __float2bfloat16_rn(0.f);
+            }
+        }
     } else if (s_fin) {
         // warp w owns accumulator lanes 32w..32w+31 = real-form rows R = 2r + a; sub-tile t sits
         // in TMEM columns t n .. t n + n - 1, so tile column c is TMEM column c
@@ -263,7 +337,18 @@ __global__ void __launch_bounds__(128, 1)
                 for (int j = 0; j < 16; ++j)
                     if (c0 + j < nh) {
                         const float x = __uint_as_float(v[j]);
-                        Dout[(int64_t)(c0 + j) * 2 * P.p2 + R] = P.round_out ? to_tf32(x) : x;
+                        const int64_t o = (int64_t)(c0 + j) * 2 * P.p2 + R;
+                        if (BF3) {
+                            Dout[o] = x;
+                            if (P.round_out) {  // the hi/lo split the next level's L2L reads
+                                const int64_t ob = (((int64_t)d * P.nbox + g) * P.ncols + col0) * 2 * P.p2 + o;
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                                Dh[ob] = hi;
+                                Dl[ob] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                            }
+                        } else {
+                            Dout[o] = P.round_out ? to_tf32(x) : x;
+                        }
                     }
         }
     }
@@ -298,6 +383,39 @@ __global__ void k_build_tc_tables(const c64 *T, int64_t nmat, int p2, int kblock
         v = to_tf32((float)x);
     }
     out[m * per + (int64_t)kb * TC_M * KBLK + sw128_index(R, kk)] = v;
+}
+
+// bf16 hi/lo image of the same matrices: per K block, 128 rows x 32 of hi then of lo, each in the
+// 64-byte-swizzled K-major layout (8 KiB + 8 KiB, the byte size of one TF32 K block)
+__global__ void k_build_bf3_tables(const c64 *T, int64_t nmat, int p2, int kblocks, __nv_bfloat16 *out) {
+    const int64_t per = (int64_t)kblocks * TC_M * KBLK;  // elements of one matrix, per half
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nmat * per) return;
+    const int64_t m = idx / per;
+    const int rem = (int)(idx % per);
+    const int kb = rem / (TC_M * KBLK), R = (rem % (TC_M * KBLK)) / KBLK, kk = rem % KBLK;
+    const int K = kb * KBLK + kk;
+    const int r = R >> 1, a = R & 1, k = K >> 1, b = K & 1;
+    double x = 0.0;
+    if (r < p2 && k < p2) {
+        const c64 t = T[(m * p2 + k) * p2 + r];
+        x = (a == 0) ? (b == 0 ? t.re : -t.im) : (b == 0 ? t.im : t.re);  // [[Re, -Im], [Im, Re]]
+    }
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+    __nv_bfloat16 *blk = out + m * 2 * per + (int64_t)kb * 2 * TC_M * KBLK;
+    blk[sw64_index(R, kk)] = hi;
+    blk[TC_M * KBLK + sw64_index(R, kk)] = lo;
+}
+
+// hi/lo bf16 split of a float array (the expansions the BF16x3 products read as B)
+__global__ void k_split_bf16(const float *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
 }
 
 // round a float array to TF32 in place (the expansions the tensor-core products read as B)
@@ -338,6 +456,22 @@ CUtensorMap make_column_map(const float *base, int64_t rows, int p2, int n) {
     return tm;
 }
 
+// bf16 rows of 2 p^2 values (one column's coefficients, hi or lo part), boxes of 32 x n rows,
+// 64-byte swizzle
+CUtensorMap make_column_map_bf16(const __nv_bfloat16 *base, int64_t rows, int p2, int n) {
+    CUtensorMap tm;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * p2), (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * p2) * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)n};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims,
+                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        throw fmbem_error{FMBEM_ERR_CUDA, "cuTensorMapEncodeTiled (bf16) failed with code " + std::to_string((int)r)};
+    return tm;
+}
+
 int tc_kblocks(int p2) { return (2 * p2 + KBLK - 1) / KBLK; }
 
 }  // namespace
@@ -357,6 +491,15 @@ void build_tc_tables(fmbem *h, cudaStream_t s) {
     CKL("k_build_tc_tables");
     k_build_tc_tables<<<(unsigned)((n_oct * per + tb - 1) / tb), tb, 0, s>>>(h->T_ll64, n_oct, p2, kb, h->Lltc);
     CKL("k_build_tc_tables");
+    // the bf16 hi/lo images take the bytes of the TF32 ones
+    h->Abf = (float *)dev_alloc(h, sizeof(float) * per * n_m2l);
+    h->Llbf = (float *)dev_alloc(h, sizeof(float) * per * n_oct);
+    k_build_bf3_tables<<<(unsigned)((n_m2l * per + tb - 1) / tb), tb, 0, s>>>(h->T_m2l64, n_m2l, p2, kb,
+                                                                            (__nv_bfloat16 *)h->Abf);
+    CKL("k_build_bf3_tables");
+    k_build_bf3_tables<<<(unsigned)((n_oct * per + tb - 1) / tb), tb, 0, s>>>(h->T_ll64, n_oct, p2, kb,
+                                                                            (__nv_bfloat16 *)h->Llbf);
+    CKL("k_build_bf3_tables");
     h->tc_err = (int *)dev_alloc(h, sizeof(int));
     CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
 }
@@ -373,12 +516,21 @@ void tc_tile_shape(int64_t ncols, int *n, int *nsub, int *ntile) {
 }
 
 // downward pass for all levels: the multipole expansions C are rounded to TF32 in place first
-// (from here on only these products read them), then one launch per level
-void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s) {
+// (TF32), or split into bf16 hi/lo parts in the second half of their buffer (BF16x3; the handle's
+// expansion buffers hold double-precision complex values, so single precision leaves that half
+// free); from here on only these products read them.  Then one launch per level.
+void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3) {
     const int64_t ncols = 3 * nr;
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
-    k_round_tf32<<<152 * 8, 256, 0, s>>>(C, nfloat);
-    CKL("k_round_tf32");
+    __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
+    __nv_bfloat16 *Dhi = (__nv_bfloat16 *)(D + nfloat), *Dlo = Dhi + nfloat;
+    if (bf3) {
+        k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
+        CKL("k_split_bf16");
+    } else {
+        k_round_tf32<<<152 * 8, 256, 0, s>>>(C, nfloat);
+        CKL("k_round_tf32");
+    }
     int n, nsub, ntile;
     tc_tile_shape(ncols, &n, &nsub, &ntile);
     const int stage = A_KB_BYTES + nsub * n * 128;
@@ -386,15 +538,31 @@ void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s) {
     const size_t smem = (size_t)stages * stage + 1024;  // + slack to align the stages to 1024 bytes
     uint32_t tcols = 32;
     while ((int)tcols < nsub * n) tcols <<= 1;
-    CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t rows = (int64_t)(h->J + 1) * h->nbox * ncols;
-    const CUtensorMap tmC = make_column_map(C, rows, h->p2, n), tmD = make_column_map(D, rows, h->p2, n);
+    CUtensorMap tmC, tmD, tmC2, tmD2;
+    if (bf3) {
+        CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tmC = make_column_map_bf16(Chi, rows, h->p2, n);
+        tmC2 = make_column_map_bf16(Clo, rows, h->p2, n);
+        tmD = make_column_map_bf16(Dhi, rows, h->p2, n);
+        tmD2 = make_column_map_bf16(Dlo, rows, h->p2, n);
+    } else {
+        CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tmC = tmC2 = make_column_map(C, rows, h->p2, n);
+        tmD = tmD2 = make_column_map(D, rows, h->p2, n);
+    }
     for (int l = 2; l <= h->lmax; ++l) {
         const LevelInfo &Lv = h->lev[l];
         const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), n, nsub, stages, tcols,
                         l < h->lmax ? 1 : 0};
-        k_m2l_tc<<<dim3((unsigned)Lv.n, h->Jf + 1, (unsigned)ntile), 128, smem, s>>>(
-            tmC, tmD, P, h->box_parent, h->box_key, h->ff_start, h->ff_src, h->ff_off, h->Atc, h->Lltc, D, h->tc_err);
+        const dim3 grid((unsigned)Lv.n, h->Jf + 1, (unsigned)ntile);
+        if (bf3)
+            k_m2l_tc<true><<<grid, 128, smem, s>>>(tmC, tmD, tmC2, tmD2, P, h->box_parent, h->box_key, h->ff_start,
+                                                   h->ff_src, h->ff_off, h->Abf, h->Llbf, D, Dhi, Dlo, h->tc_err);
+        else
+            k_m2l_tc<false><<<grid, 128, smem, s>>>(tmC, tmD, tmC2, tmD2, P, h->box_parent, h->box_key, h->ff_start,
+                                                    h->ff_src, h->ff_off, h->Atc, h->Lltc, D, nullptr, nullptr,
+                                                    h->tc_err);
         CKL("k_m2l_tc");
     }
 }

