@@ -59,7 +59,7 @@ def test_bf16x3_tensor_core_m2l_matches_fp32(n_rhs, p):
     assert rel(yb, y32) < 0.3 * rel(ytf, y32)
     for r in (0, n_rhs - 1):
         assert rel(yb[r], y32[r]) < 2e-5
-    tol = 1e-2 if p == 4 else MATVEC_TOL
+    tol = {4: 1e-2, 6: 1e-3}.get(p, MATVEC_TOL)  # the truncation error of low p
     assert rel(yb[:, rows], yo) < tol
     # the transposed product takes the same tensor-core pass
     ybt = g.adjoint_matvec(xd, precision=fm.BF16X3).cpu().numpy()
