@@ -22,6 +22,11 @@ the FP64 single-RHS matvec on the same mesh, the plain FP64 single-RHS solve and
 (timed, with the matvec error and the batched solution's residual against the dense operator).
 ``--workload torus_512x128`` runs the 128-right-hand-side batch as the main line instead.
 
+It also adds ``uneven_batch``: 256 seeded particles (spheroids, tori, split rings of 2k-60k
+triangles, 4 plane waves each) whose products run in ONE persistent kernel launch with a device
+work queue, timed beside the same products issued one problem at a time, with the oracle's error
+on sampled rows of 16 of the particles.
+
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm of this comparison).
 """
 from __future__ import annotations
@@ -101,6 +106,8 @@ def parse():
     ap.add_argument("--n-rhs", type=int, default=0, help="right-hand sides (0 = the workload's)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched leg (128-RHS torus, BF16x3 tensor-core M2L, FP64-refined solve) of the default run")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the uneven-batch leg (256 particles in one persistent launch) of the default run")
     return ap.parse_args()
 
 
@@ -534,6 +541,87 @@ def run_batched(args, world, flush):
     return out
 
 
+def run_uneven_batch(args, world, flush):
+    """Uneven batch of 256 independent particles (seeded spheroids, tori and split rings of 2k-60k
+    triangles, eps from {2.25, -5+0.2i, -12+0.5i}, k0 size 0.3-3, 4 plane waves each): all 256
+    products in ONE persistent kernel launch (device work queue, bounded waits), FP32 passes,
+    p = 8; beside it the same products issued one problem after another through fmbem_matvec.
+    On rank 0 the FP64 oracle evaluates 16 seeded rows of 16 seeded problems (timed: this leg's
+    cpu_baseline), giving the batch's error against the dense operators."""
+    import torch
+
+    import paper_1211_7177_gb300 as fm
+    from paper_1211_7177_gb300.batch import PersistentBatch
+    nr = 4
+    probs = fi.particle_batch(256, seed=5)
+    free0 = torch.cuda.mem_get_info()[0]
+    t0 = time.perf_counter()
+    hs = [fm.FMBEM(p["V"], p["F"], p["D"], p["eps"], p["mu"], p["k0"], p=8, leaf_size=args.leaf, fp32_only=1)
+          for p in probs]
+    dirs, pols = fi.plane_wave_batch(2, seed=15)
+    xs = [h.plane_wave_rhs(dirs, pols) for h in hs]
+    ys = [torch.empty_like(x) for x in xs]
+    b = PersistentBatch(hs, nr)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    mem_gb = (free0 - torch.cuda.mem_get_info()[0]) / 2 ** 30
+    stream = torch.cuda.current_stream()
+    nodes = sum(h.N for h in hs)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(statistics.mean(a.elapsed_time(bb) for a, bb in ev), "cuda")
+
+    ms = timed(lambda: b.matvec(xs, ys), args.steps, args.warmup)
+    y_batch = [y.clone() for y in ys]
+
+    def one_by_one():
+        for h, x, y in zip(hs, xs, ys):
+            h.matvec(x, y, precision=fm.FP32)
+
+    ms_seq = timed(one_by_one, max(2, args.steps // 4), 2)
+    dev = max(float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c)) for a, c in zip(y_batch, ys))
+    out = dict(workload="particle_batch_256", n_problems=len(hs), nodes_total=nodes, n_rhs=nr,
+               triangles=[int(min(len(p["F"]) for p in probs)), int(max(len(p["F"]) for p in probs))],
+               p=8, dtype="f32", setup_s=setup_s, device_memory_gb=mem_gb, work_items=b.num_items,
+               l2="inputs larger than L2 (1.26 GB of right-hand sides) and L2 flushed before each step",
+               value=job_throughput(nodes * nr, world, ms), unit=UNIT, ms_per_step=ms, steps=args.steps,
+               one_by_one=dict(value=job_throughput(nodes * nr, world, ms_seq), unit=UNIT, ms_per_step=ms_seq,
+                               max_rel_diff_to_batch=dev))
+    if dist_env()[0] == 0 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(17)
+        pick = sorted(rng.choice(len(hs), 16, replace=False).tolist())
+        errs, t_or, nrows = [], 0.0, 0
+        for i in pick:
+            p = probs[i]
+            o = oracle.Oracle(p["V"], p["F"], p["D"], p["eps"], p["mu"], p["k0"])
+            rows = fi.sample_rows(hs[i].N, 16, seed=i)
+            xh = xs[i].cpu().numpy()
+            s0 = time.perf_counter()
+            yo = o.matvec_rows(xh, rows)
+            t_or += time.perf_counter() - s0
+            nrows += len(rows)
+            errs.append(float(np.linalg.norm(y_batch[i].cpu().numpy()[:, rows] - yo) / np.linalg.norm(yo)))
+        out["cpu_baseline"] = dict(value=nrows * nr / t_or, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                                   sample=f"16 seeded rows x {nr} RHS of 16 seeded problems of the batch, dense FP64")
+        out["accuracy"] = dict(problems=len(pick), rows_each=16, max_rel_l2_vs_oracle=max(errs),
+                               median_rel_l2_vs_oracle=float(np.median(errs)))
+    b.close()
+    for h in hs:
+        h.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -710,6 +798,9 @@ def run_ours(args):
     batched = None
     if args.workload == "silver_sphere_s7" and not args.no_batched:
         batched = run_batched(args, world, flush)
+    uneven = None
+    if args.workload == "silver_sphere_s7" and not args.no_uneven:
+        uneven = run_uneven_batch(args, world, flush)
 
     launches_per_step = launches_per_matvec(info["l_max"], nr, n_dom, args.precision)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -721,7 +812,7 @@ def run_ours(args):
                             l2="flushed (256 MiB write) before each step", setup_s=setup_s, wall_s=wall),
                 e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes),
                 roofline=roof, other_precision=other, adjoint=adjoint, impedance=impedance, solve=solve,
-                gradients=gradients, cpu_baseline=cpu, batched=batched,
+                gradients=gradients, cpu_baseline=cpu, batched=batched, uneven_batch=uneven,
                 gpu_launches=launches_per_step * args.steps, clocks=clk)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -227,6 +227,43 @@ def random_complex(shape, seed: int):
     return (rng.normal(size=shape) + 1j * rng.normal(size=shape)) / math.sqrt(2.0)
 
 
+def particle_batch(n: int = 256, seed: int = 5, tri_range=(2000, 60000)):
+    """Uneven batch of independent particles: seeded spheroids (aspect U(1, 4)), tori (R/r U(2, 6))
+    and split rings (square cross-section 0.2 of the ring radius, gap U(10, 40) degrees), each
+    scaled to a largest dimension of 1, with a triangle count drawn from U(tri_range) and met by the
+    grid resolution (the nearest icosphere subdivision for spheroids), eps drawn from {2.25,
+    -5+0.2i, -12+0.5i}, k0 (= k0 times the size) from U(0.3, 3).  Returns a list of dicts with V, F,
+    D, eps, mu, k0, kind."""
+    rng = np.random.default_rng(seed)
+    eps_set = [2.25, -5 + 0.2j, -12 + 0.5j]
+    out = []
+    for _ in range(n):
+        kind = ("spheroid", "torus", "split_ring")[int(rng.integers(3))]
+        T = rng.uniform(*tri_range)
+        e = eps_set[int(rng.integers(3))]
+        k0 = rng.uniform(0.3, 3.0)
+        if kind == "spheroid":
+            asp = rng.uniform(1.0, 4.0)
+            sub = int(np.clip(np.rint(np.log(T / 20.0) / np.log(4.0)), 3, 5))
+            V, F, D = spheroid(1.0, asp, sub)
+            V = V / (2.0 * max(1.0, asp))
+        elif kind == "torus":
+            ratio = rng.uniform(2.0, 6.0)
+            nv = max(6, int(round(np.sqrt(T / (2.0 * ratio)))))
+            nu = max(12, int(round(ratio * nv)))
+            r = 0.5 / (ratio + 1.0)
+            V, F, D = torus(ratio * r, r, nu, nv)
+        else:
+            gap = rng.uniform(10.0, 40.0)
+            frac = 1.0 - gap / 360.0
+            nvs = max(2, int(round(np.sqrt(T / (8.0 * 31.4 * frac)))))
+            nu = max(8, int(round(nvs * 31.4 * frac)))
+            V, F, D = split_ring(1.0, 0.2, gap, nu, nvs)
+            V = V / (2.0 * 1.1)
+        out.append(dict(V=V, F=F, D=D, eps=[1.0, e], mu=[1.0, 1.0], k0=k0, kind=kind))
+    return out
+
+
 def sample_rows(n: int, k: int, seed: int):
     """``k`` distinct node indices drawn without replacement from range(n), sorted."""
     rng = np.random.default_rng(seed)

@@ -148,6 +148,11 @@ typedef struct {
                                 (FMBEM_ERR_INVALID_ARGUMENT otherwise); the vertex-position
                                 gradients refuse handles with rho > 0                            */
     int near_singular_levels;    /* subdivision levels L of the correction, 0..6 [3]              */
+    int fp32_only;           /* non-zero: keep only the single-precision bases and translation
+                                matrices (about a third of the device memory of a handle, for many
+                                small problems on one GPU, e.g. fmbem_batch_*); products, solves and
+                                observables that need FP64, TF32 or BF16X3 passes are then refused
+                                with FMBEM_ERR_INVALID_ARGUMENT, and the near-field cache is off [0] */
 } fmbem_options;
 
 void fmbem_default_options(fmbem_options *opt);
@@ -423,6 +428,43 @@ fmbem_status fmbem_precond_apply(fmbem *h, const void *v_dev, void *z_dev, int64
  * calls, because every scratch element a call reads is written earlier in the same call. */
 fmbem_status fmbem_matvec_noalloc(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,
                                   void *stream);
+
+/* One persistent kernel launch over many independent problems of uneven size (no counterpart in
+ * the paper, which treats one problem at a time): the products y_i = A_i x_i of n_problems
+ * handles, each with n_rhs right-hand sides, in FP32 passes.  A plan lays out, once, the work items
+ * of every problem -- source densities per (node block, right-hand side), P2M per (leaf, domain,
+ * right-hand side), M2M per (parent box, domain, column chunk) level by level upwards, M2L + L2L
+ * per (box, domain, column chunk) level by level downwards (dense S|S, S|R, R|R), near field +
+ * L2P + self per leaf -- in stage order, with the number of items of every stage of every
+ * problem.  Each fmbem_batch_matvec is one launch of as many 128-thread blocks as can be
+ * resident; a block takes the next item from a device queue counter, waits (bounded spin) until
+ * the stages its item reads are complete for its problem, runs it and counts it complete.  Items
+ * only wait for stages that come earlier in the queue, so the earliest unfinished item can always
+ * proceed; a wait that runs out (2 s, see fmbem_debug_set_batch_wait) stops the launch and the
+ * call returns FMBEM_ERR_DEVICE_TIMEOUT (outputs undefined, the context stays usable).
+ *   handles     host [n_problems] handles (penetrable boundary, near_singular_radius 0, p <= 11);
+ *               they must outlive the plan, and a handle must not run other work while a batch
+ *               product that includes it is in flight.
+ *   n_rhs       right-hand sides per problem, 1..64.  precision: FMBEM_FP32 only.
+ *   x_dev, y_dev  host [n_problems] arrays of device pointers, problem i's [n_rhs][N_i][6]
+ *               complex128 vectors (user order); x read, y written.
+ * The plan's work items live in device memory allocated by fmbem_batch_create (cudaMalloc) and
+ * freed by fmbem_batch_destroy; each handle's own scratch is grown for n_rhs if needed.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT, FMBEM_ERR_OOM, FMBEM_ERR_CUDA, FMBEM_ERR_DEVICE_TIMEOUT. */
+typedef struct fmbem_batch fmbem_batch;
+fmbem_status fmbem_batch_create(fmbem *const *handles, int32_t n_problems, int64_t n_rhs, int precision,
+                                fmbem_batch **out);
+fmbem_status fmbem_batch_matvec(fmbem_batch *b, const void *const *x_dev, void *const *y_dev, void *stream);
+int64_t fmbem_batch_num_items(const fmbem_batch *b);
+void fmbem_batch_destroy(fmbem_batch *b);
+/* Message of the last failure of a plan ("" if none); NULL: the last fmbem_batch_create failure
+ * of the calling thread. */
+const char *fmbem_batch_last_error(const fmbem_batch *b);
+/* Fault injection for tests of the bounded waits, process-wide: wait_ns sets the spin limit of
+ * the batch kernel's waits (0 restores 2 s); stall_problem >= 0 makes the next launches withhold
+ * the completion count of that problem's P2M items, so that its later items wait until the limit
+ * and the call returns FMBEM_ERR_DEVICE_TIMEOUT; -1 turns it off. */
+void fmbem_debug_set_batch_wait(uint64_t wait_ns, int32_t stall_problem);
 
 /* Wall-clock milliseconds of the phases of the last fmbem_matvec call, measured with CUDA
  * events on its stream: [0] source densities + P2M, [1] M2M, [2] M2L + L2L, [3] near field

@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("max_level", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("solve_precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("outer_precision", ctypes.c_int), ("m2l_rotation", ctypes.c_int),
                 ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("near_singular_radius", ctypes.c_double), ("near_singular_levels", ctypes.c_int)]
+                ("near_singular_radius", ctypes.c_double), ("near_singular_levels", ctypes.c_int),
+                ("fp32_only", ctypes.c_int)]
 
 
 class Mesh(ctypes.Structure):
@@ -94,6 +95,12 @@ def load_library(build_if_missing: bool = True):
         "fmbem_near_field_functional": (i32, [P, i64, i64, P, P, P, P, P]),
         "fmbem_precond_apply": (i32, [P, P, P, i64, P]),
         "fmbem_last_matvec_times": (i32, [P, P]),
+        "fmbem_batch_create": (i32, [P, i32, i64, i32, ctypes.POINTER(P)]),
+        "fmbem_batch_matvec": (i32, [P, P, P, P]),
+        "fmbem_batch_num_items": (i64, [P]),
+        "fmbem_batch_destroy": (None, [P]),
+        "fmbem_batch_last_error": (ctypes.c_char_p, [P]),
+        "fmbem_debug_set_batch_wait": (None, [ctypes.c_uint64, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -150,3 +150,69 @@ class Batch:
         for st in self.streams:
             cur.wait_stream(st)
 
+
+
+class PersistentBatch:
+    """Products of many independent problems in ONE persistent kernel launch (fmbem_batch_* of the
+    C ABI): the handles' work items (densities, P2M, M2M, M2L + L2L, near field) sit in one device
+    queue in stage order; blocks take items and wait, with a bounded spin, for the stages their
+    item reads.  FP32 passes; handles with the penetrable boundary and p <= 11 (fp32_only handles
+    keep their memory small).  The handles must stay alive while the batch is used."""
+
+    def __init__(self, handles, n_rhs, precision=1):
+        import ctypes
+
+        from . import FMBEMError, load_library
+        lib = load_library()
+        self._lib = lib
+        self.handles = list(handles)
+        self.n_rhs = int(n_rhs)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.h.value for h in self.handles])
+        out = ctypes.c_void_p()
+        st = lib.fmbem_batch_create(arr, len(self.handles), self.n_rhs, int(precision), ctypes.byref(out))
+        if st != 0:
+            raise FMBEMError(st, lib.fmbem_batch_last_error(None).decode())
+        self.b = out
+
+    @property
+    def num_items(self):
+        return int(self._lib.fmbem_batch_num_items(self.b))
+
+    def matvec(self, xs, ys=None, stream=None):
+        """ys[i] = A_i xs[i] (CUDA complex128 tensors [n_rhs, N_i, 6]); returns ys."""
+        import ctypes
+
+        import torch
+
+        from . import FMBEMError, _stream
+        if ys is None:
+            ys = [torch.empty_like(x) for x in xs]
+        for i, (h, x, y) in enumerate(zip(self.handles, xs, ys)):
+            for t, nm in ((x, "x"), (y, "y")):
+                if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()
+                        and tuple(t.shape) == (self.n_rhs, h.N, 6)) or t.is_conj() or t.is_neg():
+                    raise TypeError(f"{nm}[{i}] must be a contiguous complex128 CUDA tensor [{self.n_rhs}, {h.N}, 6]")
+        xa = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        st = self._lib.fmbem_batch_matvec(self.b, xa, ya, _stream(stream))
+        if st != 0:
+            raise FMBEMError(st, self._lib.fmbem_batch_last_error(self.b).decode())
+        return ys
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            self._lib.fmbem_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_batch_wait(wait_ns=0, stall_problem=-1):
+    """Fault injection for tests (fmbem_debug_set_batch_wait): the spin limit of the persistent
+    batch kernel's waits (0: the default 2 s) and a problem whose P2M completion is withheld."""
+    from . import load_library
+    load_library().fmbem_debug_set_batch_wait(int(wait_ns), int(stall_problem))

@@ -112,6 +112,7 @@ void fmbem_default_options(fmbem_options *o) {
     o->boundary = FMBEM_BOUNDARY_PENETRABLE;
     o->near_singular_radius = 0.0;
     o->near_singular_levels = 3;
+    o->fp32_only = 0;
 }
 
 fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
@@ -139,11 +140,12 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1 ||
         (o.boundary != FMBEM_BOUNDARY_PENETRABLE && o.boundary != FMBEM_BOUNDARY_IMPEDANCE) ||
         !(o.near_singular_radius >= 0 && std::isfinite(o.near_singular_radius)) || o.near_singular_levels < 0 ||
-        o.near_singular_levels > 6) {
+        o.near_singular_levels > 6 || o.fp32_only < 0 || o.fp32_only > 1) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
+    if (h->opt.fp32_only) h->opt.near_cache = 0;  // the cache serves FP64 products only
     cudaStream_t s = (cudaStream_t)stream;
     fmbem_status st = guarded(h, [&] {
         h->J = mesh->n_scatterers;

@@ -310,6 +310,43 @@ void build_rot_mm_lists(fmbem *h, cudaStream_t s);
 void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s);
 void near_work_items(fmbem *h, cudaStream_t s);
 void build_near_cache(fmbem *h, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// one persistent launch over many problems (batch.cu, kernel in fmm.cu)
+constexpr int BATCH_MAX_LEVEL = 10;
+constexpr int BATCH_COUNTERS = 24;  // per problem: prep, up[0..10], down[0..10], near
+constexpr int BATCH_CHUNK_COLS = 6;  // columns per M2M / M2L item (the CC of the translation kernels)
+enum BatchKind : int16_t { BK_PREP = 0, BK_P2M = 1, BK_M2M = 2, BK_DOWN = 3, BK_NEAR = 4 };
+struct BatchProblem {  // one problem's device pointers and sizes (precision-specific tables)
+    int64_t N, nbox;
+    int p2, lmax;
+    int64_t lev_off[BATCH_MAX_LEVEL + 1];
+    const int32_t *perm, *dom, *nbeg, *nend, *cbeg, *cend, *parent, *ff_start, *ff_src, *nbr_start, *nbr_idx;
+    const int16_t *ff_off;
+    const uint64_t *key;
+    const double *nrm64, *w;
+    const void *pos_hi, *pos_lo, *nrm;  // the near field's positions and normals in the precision
+    const void *dc;                     // DomainConsts [J+1]
+    const void *Bp2m, *Bl2p, *Tmm, *Tm2l, *Tll;
+    void *dens, *C, *D;
+    const c64 *Mself;
+    const c64 *x;
+    c64 *y;
+};
+struct BatchItem {
+    int32_t prob;
+    int16_t kind, level;  // BatchKind; the level of M2M (child level) and DOWN items
+    int32_t a;            // node block, leaf, parent or box index within its level
+    int16_t b, c;         // domain; right-hand side or column chunk
+};
+// counter indices of a problem: completion of every stage, and the stage an item waits for
+__host__ __device__ inline int batch_done_counter(int kind, int level, int lmax) {
+    return kind == BK_PREP ? 0 : kind == BK_P2M ? 1 + lmax : kind == BK_M2M ? 1 + level - 1 : kind == BK_DOWN ? 12 + level : 23;
+}
+void run_batch_kernel(int precision, const BatchProblem *probs, const BatchItem *items, int64_t n_items,
+                      unsigned long long *next, unsigned *cnt, const unsigned *tgt, int *err, uint64_t wait_ns,
+                      int stall_problem, int p2max, int64_t nr, cudaStream_t s);
+void batch_ensure_scratch(fmbem *h, int64_t nr, int precision);
 void build_near_singular(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s);
 void apply_near_singular(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, bool transpose);
 void run_precond(fmbem *h, const c64 *v, c64 *z, int64_t n_rhs, cudaStream_t s);

@@ -29,11 +29,15 @@ struct DomainConsts {  // per domain, device array
 // ---------------------------------------------------------------- source densities (a2)
 // dens[side][r][i][6] = (w v, w q) for side 0 (background: v = Phi, q = -Psi) and side 1 (own
 // scatterer j: v = T_j Phi, q = gamma_j Psi), nodes in sorted order.
+// The bodies of k_prep, k_p2m, k_m2m, k_down and k_near take their block coordinates as
+// arguments (bx, by, bz), so that the persistent kernel over many problems (k_batch) runs the same
+// code on work items; the __global__ wrappers pass blockIdx.
 template <typename R>
-__global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm, const double *w,
-                       const int32_t *dom, const DomainConsts *dc, cx<R> *dens) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t r = blockIdx.y;
+__device__ __forceinline__ void prep_body(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm,
+                                          const double *w, const int32_t *dom, const DomainConsts *dc, cx<R> *dens,
+                                          int64_t bx, int64_t by) {
+    int64_t i = bx * (int64_t)blockDim.x + threadIdx.x;
+    int64_t r = by;
     if (i >= N) return;
     const c64 *xi = x + (r * N + perm[i]) * 6;
     double n[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
@@ -51,6 +55,11 @@ __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm,
         d1[q] = to<R>(wi * (Phi[q] + n[q] * tn));
         d1[3 + q] = to<R>(gw * Psi[q]);
     }
+}
+template <typename R>
+__global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm, const double *w,
+                       const int32_t *dom, const DomainConsts *dc, cx<R> *dens) {
+    prep_body<R>(N, nr, x, perm, nrm, w, dom, dc, dens, blockIdx.x, blockIdx.y);
 }
 
 // The single-precision densities node-major within blocks of 32 right-hand sides,
@@ -79,13 +88,14 @@ __global__ void __launch_bounds__(256) k_dens_node_major(int64_t N, int64_t nr, 
 // once per node in shared memory, P2M_WN nodes at a time.
 constexpr int P2M_WN = 64;
 template <typename R>
-__global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
-                      const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens, const cx<R> *Bp2m,
-                      cx<R> *C) {
+__device__ __forceinline__ void p2m_body(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                         const int32_t *nbeg, const int32_t *nend, const int32_t *dom,
+                                         const double *nrm, const cx<R> *dens, const cx<R> *Bp2m, cx<R> *C, int64_t bx,
+                                         int by, int64_t bz) {
     __shared__ cx<R> W[P2M_WN][4][3];
-    const int64_t g = leaf_off + blockIdx.x;
-    const int d = blockIdx.y;
-    const int64_t r = blockIdx.z;
+    const int64_t g = leaf_off + bx;
+    const int d = by;
+    const int64_t r = bz;
     const int side = d == 0 ? 0 : 1;
     const R sg = d == 0 ? (R)-1 : (R)1;
     const int i0 = nbeg[g], i1 = nend[g];
@@ -127,6 +137,12 @@ __global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t n
     }
     if (q < p2)
         for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
+}
+template <typename R>
+__global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+                      const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens, const cx<R> *Bp2m,
+                      cx<R> *C) {
+    p2m_body<R>(leaf_off, N, nr, p2, nbox, nbeg, nend, dom, nrm, dens, Bp2m, C, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // P2M for blocks of RB right-hand sides: the basis values of a (node, coefficient) are read once
@@ -289,18 +305,20 @@ __device__ __forceinline__ void apply_T(const cx<R> *__restrict__ T, const cx<R>
 }
 
 constexpr int CC = 6;  // columns per CTA in the translation kernels
+static_assert(CC == BATCH_CHUNK_COLS, "the batch's column chunks are the translation kernels'");
 
 // M2M (Eq. 2.20): parent multipole = sum over children S|S(child octant) child multipole
 // grid (parent box at level l-1, domain, chunk of NC columns); NC = 3 for one right-hand side,
 // so that no multiply-add of the unrolled column loop is issued for an absent column
 template <typename R, int NC>
-__global__ void k_m2m(int64_t par_off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *cbeg,
-                      const int32_t *cend, const uint64_t *key, const cx<R> *Tmm, cx<R> *C) {
+__device__ __forceinline__ void m2m_body(int64_t par_off, int l, int lmax, int64_t nr, int p2, int64_t nbox,
+                                         const int32_t *cbeg, const int32_t *cend, const uint64_t *key, const cx<R> *Tmm,
+                                         cx<R> *C, int64_t bx, int by, int bz) {
     extern __shared__ unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
-    int64_t g = par_off + blockIdx.x;
-    int d = blockIdx.y;
-    int col0 = blockIdx.z * NC;
+    int64_t g = par_off + bx;
+    int d = by;
+    int col0 = bz * NC;
     int ncol = min(NC, (int)(3 * nr) - col0);
     int r = threadIdx.x;
     cx<R> acc[NC];
@@ -316,17 +334,23 @@ __global__ void k_m2m(int64_t par_off, int l, int lmax, int64_t nr, int p2, int6
     if (r < p2)
         for (int cc = 0; cc < ncol; ++cc) C[(((int64_t)d * nbox + g) * 3 * nr + col0 + cc) * p2 + r] = acc[cc];
 }
+template <typename R, int NC>
+__global__ void k_m2m(int64_t par_off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *cbeg,
+                      const int32_t *cend, const uint64_t *key, const cx<R> *Tmm, cx<R> *C) {
+    m2m_body<R, NC>(par_off, l, lmax, nr, p2, nbox, cbeg, cend, key, Tmm, C, blockIdx.x, blockIdx.y, blockIdx.z);
+}
 
 // M2L + L2L (Eq. 2.21): D(l,q) = R|R D(parent) + sum_{FF(l,q)} S|R C(source)
 template <typename R>
-__global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *parent,
-                       const uint64_t *key, const int32_t *ff_start, const int32_t *ff_src, const int16_t *ff_off,
-                       const cx<R> *Tm2l, const cx<R> *Tll, const cx<R> *C, cx<R> *D) {
+__device__ __forceinline__ void down_body(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t nbox,
+                                          const int32_t *parent, const uint64_t *key, const int32_t *ff_start,
+                                          const int32_t *ff_src, const int16_t *ff_off, const cx<R> *Tm2l,
+                                          const cx<R> *Tll, const cx<R> *C, cx<R> *D, int64_t bx, int by, int bz) {
     extern __shared__ unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
-    int64_t g = off + blockIdx.x;
-    int d = blockIdx.y;
-    int col0 = blockIdx.z * CC;
+    int64_t g = off + bx;
+    int d = by;
+    int col0 = bz * CC;
     int ncol = min(CC, (int)(3 * nr) - col0);
     int r = threadIdx.x;
     cx<R> acc[CC];
@@ -349,6 +373,13 @@ __global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t
     }
     if (r < p2)
         for (int cc = 0; cc < ncol; ++cc) D[(((int64_t)d * nbox + g) * 3 * nr + col0 + cc) * p2 + r] = acc[cc];
+}
+template <typename R>
+__global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t nbox, const int32_t *parent,
+                       const uint64_t *key, const int32_t *ff_start, const int32_t *ff_src, const int16_t *ff_off,
+                       const cx<R> *Tm2l, const cx<R> *Tll, const cx<R> *C, cx<R> *D) {
+    down_body<R>(off, l, lmax, nr, p2, nbox, parent, key, ff_start, ff_src, ff_off, Tm2l, Tll, C, D, blockIdx.x,
+                 blockIdx.y, blockIdx.z);
 }
 
 // M2L on a chunk of FF pairs that share one offset o (S|R part of Eq. 2.21): the chunk's
@@ -1030,18 +1061,18 @@ __device__ __forceinline__ int source_range(const int *cum, int nnb, int e) {
 // store of the 6 result rows in user order.  Up to 128 targets per pass; the 128 threads split as
 // (target, source slice) with 128 / n_targets slices, reduced in a fixed order.
 template <typename R, bool DOUBLE_FLOAT>
-__global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
-                                              const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
-                                              const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
-                                              const int32_t *dom, const int32_t *perm, const cx<R> *dens,
-                                              const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
-                                              const c64 *x, c64 *y, const int64_t *cache_base,
-                                              const V4<R> *cache, bool side1) {
+__device__ __forceinline__ void near_body(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                          const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                          const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
+                                          const int32_t *dom, const int32_t *perm, const cx<R> *dens,
+                                          const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
+                                          const c64 *x, c64 *y, const int64_t *cache_base, const V4<R> *cache,
+                                          bool side1, int64_t bx) {
     __shared__ NearSmem<R> S;
     __shared__ int rng_beg[32], rng_cum[33];
     SrcTile<R> &T = S.tile;
-    const int64_t g = leaf_off + blockIdx.x;
-    const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
+    const int64_t g = leaf_off + bx;
+    const int nb0 = nbr_start[bx], nnb = nbr_start[bx + 1] - nb0;
     if (threadIdx.x == 0) {
         int cum = 0;
         for (int q = 0; q < nnb; ++q) {
@@ -1099,7 +1130,7 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
                 const R adom_r = side1 ? (R)adom : (R)-1;  // -1: no scatterer-side pairs (impedance boundary)
                 // cached pair scalars of this target: [side][source][target] within the leaf's block
                 const int NT = t1 - t0;
-                const V4<R> *cs0 = cache ? cache + 2 * cache_base[blockIdx.x] + (tb - t0 + tg) : nullptr;
+                const V4<R> *cs0 = cache ? cache + 2 * cache_base[bx] + (tb - t0 + tg) : nullptr;
                 if (active)
                     for (int u = slice; u < ns; u += nsl) {
                         const V4<R> pa = T.pa[u], pb = T.pb[u];
@@ -1170,6 +1201,17 @@ __global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64
             }
         }
     }
+}
+template <typename R, bool DOUBLE_FLOAT>
+__global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+                                              const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+                                              const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
+                                              const int32_t *dom, const int32_t *perm, const cx<R> *dens,
+                                              const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
+                                              const c64 *x, c64 *y, const int64_t *cache_base,
+                                              const V4<R> *cache, bool side1) {
+    near_body<R, DOUBLE_FLOAT>(leaf_off, N, nr, p2, nbox, nbeg, nend, nbr_start, nbr_idx, pos_hi, pos_lo, nrm, dom,
+                               perm, dens, dc, Bl2p, D, Mself, x, y, cache_base, cache, side1, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- near field for blocks of RHS
@@ -2176,6 +2218,111 @@ __global__ void __launch_bounds__(128) k_near_adj(int64_t leaf_off, int64_t N, i
     }
 }
 
+// ---------------------------------------------------------------- one launch over many problems
+// A persistent kernel over the work items of many independent problems (one product y_i = A_i x_i
+// each): densities, P2M per (leaf, domain, right-hand side), M2M per (parent, domain, column chunk)
+// level by level, M2L + L2L per (box, domain, column chunk) level by level, near field + L2P + self
+// per leaf.  Blocks take items in queue order from one counter; the items are sorted by stage
+// rank, and an item only waits for stages of its own problem that rank lower, so with every block
+// resident (the grid is sized by the occupancy) the lowest unfinished item can always proceed.
+// Each block waits for its item's inputs on per-problem completion counters with a bounded spin
+// (%globaltimer); when a wait runs out it raises the error flag and every block leaves at its next
+// item.  stall_problem >= 0 (fault injection for tests) withholds the completion of that problem's
+// P2M items, so that its later items wait until the limit.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t batch_clock() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ bool batch_wait(const unsigned *c, unsigned target, uint64_t wait_ns, const int *err) {
+    if (ld_acquire_u32(c) >= target) return true;
+    const uint64_t t0 = batch_clock();
+    for (;;) {
+        for (int i = 0; i < 32; ++i) {
+            if (ld_acquire_u32(c) >= target) return true;
+            __nanosleep(64);
+        }
+        if (*(const volatile int *)err) return false;  // another block gave up already
+        if (batch_clock() - t0 > wait_ns) return false;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_batch(const BatchProblem *probs, const BatchItem *items, int64_t n_items,
+                                               int64_t nr, unsigned long long *next, unsigned *cnt,
+                                               const unsigned *tgt, int *err, uint64_t wait_ns, int stall_problem) {
+    __shared__ int64_t s_it;
+    __shared__ int s_go;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t it = (int64_t)atomicAdd(next, 1ull);
+            int go = it < n_items && !*(volatile int *)err;
+            if (go) {
+                const BatchItem w = items[it];
+                const int lmax = probs[w.prob].lmax;
+                const unsigned *c = cnt + (int64_t)w.prob * BATCH_COUNTERS;
+                const unsigned *t = tgt + (int64_t)w.prob * BATCH_COUNTERS;
+                int k1 = -1, k2 = -1;
+                if (w.kind == BK_P2M) k1 = 0;
+                else if (w.kind == BK_M2M) k1 = 1 + w.level;
+                else if (w.kind == BK_DOWN) { k1 = 1 + w.level; if (w.level >= 3) k2 = 12 + w.level - 1; }
+                else if (w.kind == BK_NEAR) k1 = 12 + lmax;
+                bool ok = (k1 < 0 || batch_wait(c + k1, t[k1], wait_ns, err)) &&
+                          (k2 < 0 || batch_wait(c + k2, t[k2], wait_ns, err));
+                if (!ok) {
+                    atomicExch(err, 1);
+                    go = 0;
+                }
+                __threadfence();
+            }
+            s_it = it;
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const BatchItem w = items[s_it];
+        const BatchProblem &P = probs[w.prob];
+        const int lmax = P.lmax;
+        switch (w.kind) {
+            case BK_PREP:
+                prep_body<R>(P.N, nr, P.x, P.perm, P.nrm64, P.w, P.dom, (const DomainConsts *)P.dc, (cx<R> *)P.dens,
+                             w.a, w.c);
+                break;
+            case BK_P2M:
+                p2m_body<R>(P.lev_off[lmax], P.N, nr, P.p2, P.nbox, P.nbeg, P.nend, P.dom, P.nrm64,
+                            (const cx<R> *)P.dens, (const cx<R> *)P.Bp2m, (cx<R> *)P.C, w.a, w.b, w.c);
+                break;
+            case BK_M2M:
+                m2m_body<R, CC>(P.lev_off[w.level - 1], w.level, lmax, nr, P.p2, P.nbox, P.cbeg, P.cend, P.key,
+                                (const cx<R> *)P.Tmm, (cx<R> *)P.C, w.a, w.b, w.c);
+                break;
+            case BK_DOWN:
+                down_body<R>(P.lev_off[w.level], w.level, lmax, nr, P.p2, P.nbox, P.parent, P.key, P.ff_start,
+                             P.ff_src, P.ff_off, (const cx<R> *)P.Tm2l, (const cx<R> *)P.Tll, (const cx<R> *)P.C,
+                             (cx<R> *)P.D, w.a, w.b, w.c);
+                break;
+            default:
+                near_body<R, sizeof(R) == 4>(P.lev_off[lmax], P.N, nr, P.p2, P.nbox, P.nbeg, P.nend, P.nbr_start,
+                                             P.nbr_idx, (const R *)P.pos_hi, (const R *)P.pos_lo, (const R *)P.nrm,
+                                             P.dom, P.perm, (const cx<R> *)P.dens, (const DomainConsts *)P.dc,
+                                             (const cx<R> *)P.Bl2p, (const cx<R> *)P.D, P.Mself, P.x, P.y, nullptr,
+                                             nullptr, true, w.a);
+                break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (!(w.prob == stall_problem && w.kind == BK_P2M))
+                atomicAdd(cnt + (int64_t)w.prob * BATCH_COUNTERS + batch_done_counter(w.kind, w.level, lmax), 1u);
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -2919,7 +3066,15 @@ static void check_tc_err(fmbem *h, cudaStream_t s) {
     }
 }
 
+// a handle that keeps only single-precision tables runs FP32 passes only
+static void check_fp32_only(const fmbem *h, int precision) {
+    if (h->opt.fp32_only && precision != FMBEM_FP32)
+        throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT,
+                          "this handle keeps single-precision tables only (fp32_only): FP32 passes only"};
+}
+
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
+    check_fp32_only(h, precision);
     ensure_scratch(h, nr, precision);
     const DomainConsts *dc = (const DomainConsts *)h->dcons;
     if (precision == FMBEM_TF32 || precision == FMBEM_BF16X3) {
@@ -2933,6 +3088,7 @@ void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precisio
 }
 
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
+    check_fp32_only(h, precision);
     ensure_scratch(h, nr, precision);
     static_assert(sizeof(DomainConsts) == 3 * sizeof(c64), "layout");
     DomainConsts *dc = (DomainConsts *)h->dcons;
@@ -3022,7 +3178,32 @@ static void matvec_static_scratch(fmbem *h, const c64 *x, c64 *y, int64_t nr, cu
 }
 
 void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t nr, int precision, cudaStream_t s) {
+    check_fp32_only(h, precision);
     if (precision == FMBEM_FP32) matvec_static_scratch<float>(h, x, y, nr, s);
     else matvec_static_scratch<double>(h, x, y, nr, s);
     h->have_times = h->profile && h->ev[0] != nullptr;
 }
+
+// one launch of the persistent many-problem kernel (see k_batch); the grid is the number of
+// blocks that can be resident at once, so that no item waits for an item that is not running
+void run_batch_kernel(int precision, const BatchProblem *probs, const BatchItem *items, int64_t n_items,
+                      unsigned long long *next, unsigned *cnt, const unsigned *tgt, int *err, uint64_t wait_ns,
+                      int stall_problem, int p2max, int64_t nr, cudaStream_t s) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // single precision only: the double-precision bodies together need more than 48 KiB of static
+    // shared memory
+    if (precision != FMBEM_FP32) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "the batch runs in FP32"};
+    const size_t smem = sizeof(c32) * CC * p2max;
+    CK(cudaFuncSetAttribute(k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<float>, 128, smem));
+    if (per_sm < 1) throw fmbem_error{FMBEM_ERR_CUDA, "the batch kernel cannot be resident"};
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)per_sm * nsm));
+    k_batch<float><<<(unsigned)grid, 128, smem, s>>>(probs, items, n_items, nr, next, cnt, tgt, err, wait_ns,
+                                                     stall_problem);
+    CKL("k_batch");
+}
+
+// scratch of a handle for an n_rhs product in the given precision (batch.cu)
+void batch_ensure_scratch(fmbem *h, int64_t nr, int precision) { ensure_scratch(h, nr, precision); }
