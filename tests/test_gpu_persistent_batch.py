@@ -43,7 +43,7 @@ def small_batch():
 
 def test_batch_matches_single_products_and_oracle(small_batch):
     probs, hs, xs, b = small_batch
-    assert len({h.N for h in hs}) == len(hs) and b.num_items > 0
+    assert len({h.N for h in hs}) >= 4 and b.num_items > 0  # uneven sizes
     ys = b.matvec(xs)
     ys2 = b.matvec(xs)
     for i, (p, h) in enumerate(zip(probs, hs)):
