@@ -169,6 +169,7 @@ struct fmbem {
     // tensor-core (tcgen05, TF32) M2L tables: real-form 128-byte-swizzled images, see m2l_tc.cu
     float *Atc = nullptr, *Lltc = nullptr;
     float *Abf = nullptr, *Llbf = nullptr;  // the same matrices as bf16 hi/lo images (BF16x3)
+    void *Aofs = nullptr;  // S|R bf16 hi/lo images for the offset-stationary few-column M2L (BF16x3)
     int *tc_err = nullptr;
     bool m2l_rotation = false;
     int n_tlen = 0;
@@ -304,6 +305,11 @@ void run_absorption(fmbem *h, const c64 *x, int64_t n_rhs, double *out_host, cud
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3);
+bool m2l_ofs_supported(const fmbem *h);
+void build_ofs_tables(fmbem *h, cudaStream_t s);
+void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s);
+void run_m2l_ofs(fmbem *h, const float *C, float *Y, int l, int d, int64_t nr, int64_t c0, int64_t nch,
+                 int64_t e_first, cudaStream_t s);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
 void pack_rot_tables_mm(fmbem *h, cudaStream_t s);
 void build_rot_mm_lists(fmbem *h, cudaStream_t s);

@@ -2615,7 +2615,7 @@ static size_t ybuf_need(const fmbem *h, int64_t ncol, size_t elem) {
     return elem * (size_t)mp * (size_t)ncol * h->p2;
 }
 
-static void ensure_scratch(fmbem *h, int64_t nr, int precision) {
+static void ensure_scratch(fmbem *h, int64_t nr, int precision, bool pair_results = true) {
     const size_t cb = sizeof(c64);
     if (h->scratch_rhs < nr) {
         if (h->dens) { dev_free(h, h->dens); dev_free(h, h->Cexp); dev_free(h, h->Dexp); }
@@ -2628,7 +2628,7 @@ static void ensure_scratch(fmbem *h, int64_t nr, int precision) {
     // one column window of the FP64 rotation form for more columns); sized by the columns of
     // this call, so that a few-column call after a many-column one still takes the chunked path
     const bool many = rot_many_path(h, nr, precision == FMBEM_FP64);
-    if (3 * nr <= 24 || many) {
+    if (pair_results && (3 * nr <= 24 || many)) {
         const size_t need = ybuf_need(h, many ? rot_many_cols(h) : 3 * nr, cb);
         if (h->ybuf == nullptr || h->ybuf_bytes < need) {
             if (h->ybuf) dev_free(h, h->ybuf);
@@ -2801,6 +2801,9 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
         const cx<R> *RZll = f32 ? (const cx<R> *)h->R_Zll32 : (const cx<R> *)h->R_Zll64;
         const bool use_rot_mm = use_rot && h->rmm_chunk_beg != nullptr;
         cx<R> *Y = (cx<R> *)h->ybuf;
+        // BF16x3 with few columns: the S|R products of each offset chunk on the tensor cores
+        const bool ofs = tensor_mode == 2 && f32 && h->Aofs != nullptr && 3 * nr <= MAXC;
+        if (ofs) split_expansions_bf16(h, (float *)C, nr, s);
         for (int l = 2; l <= lmax; ++l) {
             const LevelInfo &Lv = h->lev[l];
             const int64_t c0 = h->h_chunk_first[l], nch = h->h_chunk_first[l + 1] - c0;
@@ -2809,7 +2812,9 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
                 for (int col0 = 0; col0 < 3 * nr; col0 += ncol) {
                     const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
                     if (nch > 0) {
-                        if (use_rot)
+                        if (ofs)
+                            run_m2l_ofs(h, (const float *)C, (float *)Y, l, d, nr, c0, nch, e_first, s);
+                        else if (use_rot)
                             launch_rot<R>(rl, nch, s, c0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->chunk_beg,
                                           h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD,
                                           RP, RZ, C, Y, e_first);
@@ -3205,5 +3210,6 @@ void run_batch_kernel(int precision, const BatchProblem *probs, const BatchItem 
     CKL("k_batch");
 }
 
-// scratch of a handle for an n_rhs product in the given precision (batch.cu)
-void batch_ensure_scratch(fmbem *h, int64_t nr, int precision) { ensure_scratch(h, nr, precision); }
+// scratch of a handle for an n_rhs product in the given precision (batch.cu): densities and
+// expansions only, the batch's dense translation items keep no per-pair results
+void batch_ensure_scratch(fmbem *h, int64_t nr, int precision) { ensure_scratch(h, nr, precision, false); }

@@ -474,6 +474,200 @@ CUtensorMap make_column_map_bf16(const __nv_bfloat16 *base, int64_t rows, int p2
 
 int tc_kblocks(int p2) { return (2 * p2 + KBLK - 1) / KBLK; }
 
+// ------------------------------------------------------------------------------------------
+// Offset-stationary M2L for few columns (BF16x3 precision, up to 8 right-hand sides): the FF pairs
+// of one level and domain, sorted by translation offset and cut into chunks of up to 32 pairs that
+// share one S|R matrix, are a GEMM per chunk:
+//   Y[pair column m][real-form row n] = sum_k C[source column m][k] S|R[n][k],
+// with M = the chunk's pair columns (3 n_rhs per pair, up to 128 per pass), N = 2 p^2 rounded up
+// to 16 (the S|R image rows), K = 2 p^2 (32-element blocks).  Both operands are split into bf16 hi
+// and lo parts and each K step accumulates M_hi S_hi + M_hi S_lo + M_lo S_hi (tcgen05.mma kind::f16,
+// FP32 in tensor memory).  The S|R image arrives by bulk copy; the source columns are gathered by
+// the four producer warps (16-byte loads into the 64-byte-swizzled layout, then a proxy fence), warp
+// w filling ring slot w; warp 4's first lane issues the MMAs; the producer warps then drain tensor
+// memory and store each pair column's 2 p^2 results at the pair's CSR position, the layout
+// k_l2l_reduce sums per target.  Every wait is bounded as in k_m2l_tc.
+constexpr int OFS_STAGES = 4;
+constexpr int OFS_M = 128;
+
+struct OfsLevel {
+    int64_t nbox;
+    int ncols;      // columns per pair (3 n_rhs) = rows of C per box
+    int p2, kblocks, np;
+    int d;
+    int64_t e_first;
+    int ppp;        // pairs per pass: floor(128 / ncols)
+    int64_t amat0;  // first S|R image of this (domain, level)
+    uint32_t tmem_cols;
+};
+
+__global__ void __launch_bounds__(160, 1)
+    k_m2l_ofs(const OfsLevel P, int64_t chunk0, const int32_t *__restrict__ chunk_beg,
+              const int32_t *__restrict__ chunk_cnt, const int16_t *__restrict__ chunk_off,
+              const int32_t *__restrict__ pair_e, const int32_t *__restrict__ ff_src, const __nv_bfloat16 *Chi,
+              const __nv_bfloat16 *Clo, const __nv_bfloat16 *__restrict__ Aofs, float *Y, int *err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full[OFS_STAGES], empty[OFS_STAGES], done, tfree, fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ck = chunk0 + blockIdx.x;
+    const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+    const int16_t off = chunk_off[ck];
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t b_half = (uint32_t)P.np * 64u;             // one bf16 part of an S|R K block
+    const uint32_t stage_bytes = 2u * OFS_M * 64u + 2u * b_half;
+    const int passes = (cnt + P.ppp - 1) / P.ppp;
+    const int units = passes * P.kblocks;
+    const int twop2 = 2 * P.p2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OFS_STAGES; ++s) {
+            mbar_init(&full[s], 33);  // the filling warp's 32 lanes + the bulk copy's expect_tx
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        mbar_init(&tfree, 128);
+        mbar_init(&fin, 1);
+        s_abort = *(volatile int *)err;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(P.tmem_cols)
+                     : "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const __nv_bfloat16 *Amat = Aofs + (P.amat0 + off) * (int64_t)P.kblocks * P.np * 64;
+
+    if (warp < 4) {
+        int last_issued = -1;  // this warp's last unit whose bulk copy was issued
+        for (int pass = 0; pass < passes && !s_abort; ++pass) {
+            // ---- fill this warp's slots of the pass
+            for (int kb = 0; kb < P.kblocks; ++kb) {
+                const int u = pass * P.kblocks + kb;
+                if ((u & 3) != warp) continue;
+                const int q = u >> 2;
+                bool ok = q == 0 || mbar_wait(&empty[warp], (uint32_t)(q - 1) & 1u);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok || s_abort) { if (lane == 0) { atomicExch(err, 1); s_abort = 1; } break; }
+                const uint32_t sM = sbase + (uint32_t)warp * stage_bytes, sB = sM + 2u * OFS_M * 64u;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[warp], 2u * b_half);
+                    bulk_load(sB, Amat + (int64_t)kb * P.np * 64, 2u * b_half, &full[warp]);
+                    last_issued = u;
+                }
+                // gather 128 rows x (4 hi + 4 lo) 16-byte chunks of source coefficients
+                for (int i = lane; i < OFS_M * 8; i += 32) {
+                    const int m = i >> 3, part = i & 7, lohalf = part >> 2, qc = part & 3;
+                    const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
+                    const int k0 = kb * KBLK + 8 * qc;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (m < P.ppp * P.ncols && jj < cnt && k0 < twop2) {
+                        const int64_t row = ((int64_t)P.d * P.nbox + ff_src[pair_e[beg + jj]]) * P.ncols + c;
+                        const __nv_bfloat16 *src = (lohalf ? Clo : Chi) + row * twop2 + k0;
+                        v = *reinterpret_cast<const uint4 *>(src);
+                    }
+                    const uint32_t dst = sM + (uint32_t)lohalf * (OFS_M * 64u) + (uint32_t)m * 64u +
+                                         (uint32_t)((qc ^ ((m >> 1) & 3)) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y), "r"(v.z),
+                                 "r"(v.w)
+                                 : "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[warp])) : "memory");
+            }
+            if (s_abort) break;
+            // ---- drain this pass's accumulators: lane = pair column 32 warp + lane
+            bool ok = mbar_wait(&done, (uint32_t)pass & 1u);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) { if (lane == 0) { atomicExch(err, 1); s_abort = 1; } break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m = warp * 32 + lane;
+            const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
+            const bool valid = m < P.ppp * P.ncols && jj < cnt;
+            float *out = valid ? Y + (((int64_t)pair_e[beg + jj] - P.e_first) * P.ncols + c) * twop2 : nullptr;
+            for (int c0 = 0; c0 < P.np; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (valid)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < twop2) out[c0 + j] = __uint_as_float(v[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
+        }
+        // copies still in flight after an abort: wait (bounded) for this warp's last bulk copy
+        if (lane == 0 && last_issued >= 0 && s_abort)
+            if (!mbar_wait(&full[warp], (uint32_t)(last_issued >> 2) & 1u)) atomicExch(err, 1);
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16(P.np);
+        bool ok = true;
+        for (int u = 0; u < units && !s_abort; ++u) {
+            const int s = u & 3, q = u >> 2, pass = u / P.kblocks, kb = u - pass * P.kblocks;
+            if (kb == 0 && pass > 0 && !mbar_wait(&tfree, (uint32_t)(pass - 1) & 1u)) { ok = false; break; }
+            if (!mbar_wait(&full[s], (uint32_t)q & 1u)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sM = sbase + (uint32_t)s * stage_bytes, sB = sM + 2u * OFS_M * 64u;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {  // K = 16 bf16 per MMA, 32 bytes along the 64-byte rows
+                const uint64_t mh = smem_desc_sw64(sM + 32u * j), ml = smem_desc_sw64(sM + OFS_M * 64u + 32u * j);
+                const uint64_t bh = smem_desc_sw64(sB + 32u * j), bl = smem_desc_sw64(sB + b_half + 32u * j);
+                mma_bf16(tmem, mh, bh, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+                mma_bf16(tmem, mh, bl, idesc, 1u);
+                mma_bf16(tmem, ml, bh, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+            if (kb == P.kblocks - 1) mma_commit(&done);
+        }
+        mma_commit(&fin);  // arrives once every MMA issued above has completed
+        if (!ok) { atomicExch(err, 1); s_abort = 1; }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x == 0 && units > 0 && !mbar_wait(&fin, 0)) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+}
+
+// bf16 hi/lo images of the S|R matrices for k_m2l_ofs: per matrix and K block, np rows (the
+// real-form output rows 2r + a, zero past 2 p^2) x 32 K elements of hi, then of lo, in the
+// 64-byte-swizzled K-major layout
+__global__ void k_build_ofs_tables(const c64 *T, int64_t nmat, int p2, int np, int kblocks, __nv_bfloat16 *out) {
+    const int64_t per = (int64_t)kblocks * np * KBLK;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nmat * per) return;
+    const int64_t m = idx / per;
+    const int rem = (int)(idx % per);
+    const int kb = rem / (np * KBLK), R = (rem % (np * KBLK)) / KBLK, kk = rem % KBLK;
+    const int K = kb * KBLK + kk;
+    const int r = R >> 1, a = R & 1, k = K >> 1, b = K & 1;
+    double x = 0.0;
+    if (r < p2 && k < p2) {
+        const c64 t = T[(m * p2 + k) * p2 + r];
+        x = (a == 0) ? (b == 0 ? t.re : -t.im) : (b == 0 ? t.im : t.re);  // [[Re, -Im], [Im, Re]]
+    }
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+    __nv_bfloat16 *blk = out + m * 2 * per + (int64_t)kb * 2 * np * KBLK;
+    blk[sw64_index(R, kk)] = hi;
+    blk[(int64_t)np * KBLK + sw64_index(R, kk)] = lo;
+}
+
 }  // namespace
 
 // 2 p^2 <= 128 fills the 128-row real form; p >= 4 makes a column's 2 p^2 floats at least one
@@ -565,4 +759,52 @@ void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool b
                                                     h->tc_err);
         CKL("k_m2l_tc");
     }
+}
+
+// the offset-stationary few-column M2L runs for even p up to 10 (2 p^2 <= 200 rows of 16-byte
+// aligned bf16 coefficient rows, N = 2 p^2 rounded up to 16 <= 256)
+bool m2l_ofs_supported(const fmbem *h) { return h->p >= 4 && h->p <= 10 && h->p % 2 == 0; }
+
+static int ofs_np(int p2) { return ((2 * p2 + 15) / 16) * 16; }
+
+void build_ofs_tables(fmbem *h, cudaStream_t s) {
+    const int p2 = h->p2, kb = tc_kblocks(p2), np = ofs_np(p2);
+    const int64_t nmat = (int64_t)(h->J + 1) * (h->lmax + 1) * 316;
+    const int64_t per = (int64_t)kb * np * KBLK;
+    h->Aofs = dev_alloc(h, sizeof(__nv_bfloat16) * 2 * per * nmat);
+    const int tb = 256;
+    k_build_ofs_tables<<<(unsigned)((nmat * per + tb - 1) / tb), tb, 0, s>>>(h->T_m2l64, nmat, p2, np, kb,
+                                                                            (__nv_bfloat16 *)h->Aofs);
+    CKL("k_build_ofs_tables");
+    if (!h->tc_err) {
+        h->tc_err = (int *)dev_alloc(h, sizeof(int));
+        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+    }
+}
+
+// bf16 hi/lo split of the multipole expansions into the second half of their buffer (see
+// run_m2l_tc) before the offset-stationary M2L reads them
+void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s) {
+    const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * 3 * nr * 2 * h->p2;
+    __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
+    k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
+    CKL("k_split_bf16");
+}
+
+// one launch of k_m2l_ofs over the nch chunks from c0 of level l, domain d; Y as k_l2l_reduce reads it
+void run_m2l_ofs(fmbem *h, const float *C, float *Y, int l, int d, int64_t nr, int64_t c0, int64_t nch,
+                 int64_t e_first, cudaStream_t s) {
+    if (nch <= 0) return;
+    const int p2 = h->p2, kb = tc_kblocks(p2), np = ofs_np(p2);
+    const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * 3 * nr * 2 * p2;
+    const __nv_bfloat16 *Chi = (const __nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
+    uint32_t tcols = 32;
+    while ((int)tcols < np) tcols <<= 1;
+    const OfsLevel P{h->nbox, (int)(3 * nr), p2, kb, np, d, e_first, (int)(OFS_M / (3 * nr)),
+                     ((int64_t)d * (h->lmax + 1) + l) * 316, tcols};
+    const size_t smem = (size_t)OFS_STAGES * (2 * OFS_M * 64 + 2 * (size_t)np * 64) + 1024;
+    CK(cudaFuncSetAttribute(k_m2l_ofs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_m2l_ofs<<<(unsigned)nch, 160, smem, s>>>(P, c0, h->chunk_beg, h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src,
+                                                Chi, Clo, (const __nv_bfloat16 *)h->Aofs, Y, h->tc_err);
+    CKL("k_m2l_ofs");
 }

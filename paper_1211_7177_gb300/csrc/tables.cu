@@ -476,6 +476,8 @@ void build_tables(fmbem *h, cudaStream_t s) {
     dev_free(h, dl);
     // tensor-core images of the S|R and R|R matrices for the batched TF32 path
     if (m2l_tc_supported(h) && !h->opt.fp32_only) build_tc_tables(h, s);
+    // bf16 S|R images for the offset-stationary few-column tensor-core M2L (BF16x3)
+    if (m2l_ofs_supported(h) && !h->opt.fp32_only) build_ofs_tables(h, s);
     if (h->opt.fp32_only) {  // single-precision tables only: the FP64 bases and matrices go
         CK(cudaStreamSynchronize(s));
         for (c64 **q : {&h->T_m2l64, &h->T_mm64, &h->T_ll64, &h->B_p2m64, &h->B_l2p64, &h->B_l2pg64}) {

@@ -161,3 +161,51 @@ def test_fp64_rotation_form_in_column_windows():
     assert rel(Y, o.matvec(x)) < MATVEC_TOL
     assert rel(YT, o.matvec_transpose(x)) < MATVEC_TOL
     g.close()
+
+
+@pytest.mark.parametrize("p,n_rhs", [(10, 1), (8, 3), (6, 2), (4, 1)])
+def test_bf16x3_offset_stationary_m2l_few_columns(p, n_rhs):
+    """With at most 8 right-hand sides the BF16x3 precision runs the S|R products of every offset
+    chunk as one tensor-core GEMM (k_m2l_ofs: the chunk's pair columns x the offset's S|R image,
+    bf16 hi/lo operands, three products per K step); L2L, P2M, M2M and the near field stay in FP32.
+    The product must agree with the FP32 one to ~1e-5, the transposed product likewise, and both
+    must meet the oracle bar on sampled rows (p = 10 and 8; looser for the truncation of p = 6, 4)."""
+    V, F, D = fi.icosphere(5)  # 10242 nodes
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=p)
+    x = fi.random_complex((n_rhs, o.N, 6), seed=61)
+    xd = to_dev(x)
+    y32 = g.matvec(xd, precision=fm.FP32).cpu().numpy()
+    yb = g.matvec(xd, precision=fm.BF16X3).cpu().numpy()
+    assert np.array_equal(yb, g.matvec(xd, precision=fm.BF16X3).cpu().numpy())
+    rows = fi.sample_rows(o.N, 256, seed=62)
+    yo = o.matvec_rows(x, rows)
+    print(f"p {p} n_rhs {n_rhs}: BF16x3 vs FP32 {rel(yb, y32):.3e}; vs oracle rows {rel(yb[:, rows], yo):.3e}; "
+          f"FP32 vs oracle rows {rel(y32[:, rows], yo):.3e}")
+    assert rel(yb, y32) < 2e-5
+    tol = {4: 1e-2, 6: 1e-3}.get(p, MATVEC_TOL)
+    assert rel(yb[:, rows], yo) < tol
+    t32 = g.adjoint_matvec(xd, precision=fm.FP32).cpu().numpy()
+    tb = g.adjoint_matvec(xd, precision=fm.BF16X3).cpu().numpy()
+    assert rel(tb, t32) < 2e-5
+    g.close()
+
+
+def test_bf16x3_single_rhs_at_scale_and_refined_solve():
+    """Silver-like sphere, icosphere subdivision 7 (163842 nodes), p = 10, one right-hand side:
+    the BF16x3 product on 2048 seeded rows of the dense operator (1e-4), and the refined solve with
+    BF16x3 inner iterations and FP64 true residuals to 1e-6."""
+    V, F, D = fi.icosphere(7)
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=10, solve_precision=fm.BF16X3, inner_tol=5e-5, outer_precision=fm.FP64)
+    x = fi.random_complex((1, o.N, 6), seed=1)
+    rows = fi.sample_rows(o.N, 2048, seed=2)
+    err = rel(g.matvec(to_dev(x), precision=fm.BF16X3).cpu().numpy()[:, rows], o.matvec_rows(x, rows))
+    print(f"s7 BF16x3 rel L2 on 2048 rows = {err:.3e}")
+    assert err < MATVEC_TOL
+    b = g.plane_wave_rhs([[0, 0, 1.0]], [[1.0, 0, 0]])
+    xs, its, res, st = g.solve(b, tol=1e-6)
+    assert st == 0 and res[0] <= 1e-6, (st, res)
+    g.close()
