@@ -76,6 +76,21 @@ PEAK_TFLOPS = {"fp64": 1.2, "fp32": 74.6}  # measured FMA throughput on GB300 (s
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor-core rate
 
 
+class nvtx_range:
+    """An NVTX range around a timed region (named for profiler filters: ncu --nvtx-include name/)."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        torch.cuda.nvtx.range_push(self.name)
+
+    def __exit__(self, *a):
+        import torch
+        torch.cuda.nvtx.range_pop()
+
+
 def tensor_peak_tf32():
     """Dense TF32 tensor-core peak: the measured cuBLAS BF16 burst rate times the nominal ratio."""
     try:
@@ -93,7 +108,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="silver_sphere_s7", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"])
     ap.add_argument("--p", type=int, default=0, help="truncation number (0 = the workload's)")
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--no-solve", action="store_true")
@@ -240,7 +255,10 @@ def roofline(info, p, nr, n_dom, phases, precision):
     avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
     dom = max(keys, key=lambda k: avg[k])
     if dom == "m2l_l2l":
-        per_col, form = m2l_flops_per_column(p, nr)
+        if precision == "bf16x3" and (3 * nr <= 24 or tensor_path(nr)):
+            per_col, form = 8.0 * p ** 4, "dense S|R on tcgen05, BF16x3 (bf16 hi/lo operands, three products)"
+        else:
+            per_col, form = m2l_flops_per_column(p, nr)
         flops = per_col * 3 * nr * info["ff_pairs"] * n_dom
         name = f"M2L + L2L, {form}"
     elif dom == "near_l2p_self":
@@ -254,8 +272,11 @@ def roofline(info, p, nr, n_dom, phases, precision):
     if precision == "tf32" and dom == "m2l_l2l" and tensor_path(nr):
         peak, src = tensor_peak_tf32()
         bound, name = "tensor", name.replace("M2L + L2L", "M2L + L2L on tcgen05 TF32")
+    elif precision == "bf16x3" and dom == "m2l_l2l" and (3 * nr <= 24 or tensor_path(nr)):
+        peak, src = tensor_peak_bf16x3()
+        bound = "tensor"
     else:
-        arith = "fp32" if precision == "tf32" else precision
+        arith = "fp32" if precision in ("tf32", "bf16x3") else precision
         peak, bound = PEAK_TFLOPS[arith], "alu"
         src = f"measured {arith.upper()} FMA throughput of GB300 (self-written probe)"
     return dict(kernel=name, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
@@ -427,14 +448,15 @@ def run_batched(args, world, flush):
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         ph = []
-        for k in range(steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            g.matvec(xx, yy, precision=prec)
-            ev[k][1].record(stream)
-            if with_phases:
-                ph.append(g.last_matvec_times())
-        torch.cuda.synchronize()
+        with nvtx_range(f"{name}_{ {fm.FP64: 'fp64', fm.FP32: 'fp32', fm.TF32: 'tf32'}.get(prec, 'bf16x3')}_{xx.shape[0]}"):
+            for k in range(steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                g.matvec(xx, yy, precision=prec)
+                ev[k][1].record(stream)
+                if with_phases:
+                    ph.append(g.last_matvec_times())
+            torch.cuda.synchronize()
         return max_over_ranks(statistics.mean(a.elapsed_time(bb) for a, bb in ev), "cuda"), ph
 
     ms, phases = time_matvec(x, y, fm.BF16X3, args.steps, args.warmup)
@@ -568,27 +590,28 @@ def run_uneven_batch(args, world, flush):
     stream = torch.cuda.current_stream()
     nodes = sum(h.N for h in hs)
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, name):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for k in range(steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            fn()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        with nvtx_range(name):
+            for k in range(steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
         return max_over_ranks(statistics.mean(a.elapsed_time(bb) for a, bb in ev), "cuda")
 
-    ms = timed(lambda: b.matvec(xs, ys), args.steps, args.warmup)
+    ms = timed(lambda: b.matvec(xs, ys), args.steps, args.warmup, "particle_batch")
     y_batch = [y.clone() for y in ys]
 
     def one_by_one():
         for h, x, y in zip(hs, xs, ys):
             h.matvec(x, y, precision=fm.FP32)
 
-    ms_seq = timed(one_by_one, max(2, args.steps // 4), 2)
+    ms_seq = timed(one_by_one, max(2, args.steps // 4), 2, "particle_one_by_one")
     dev = max(float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c)) for a, c in zip(y_batch, ys))
     out = dict(workload="particle_batch_256", n_problems=len(hs), nodes_total=nodes, n_rhs=nr,
                triangles=[int(min(len(p["F"]) for p in probs)), int(max(len(p["F"]) for p in probs))],
@@ -634,7 +657,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     p = args.p or wl["p"]
-    prec = {"fp64": fm.FP64, "fp32": fm.FP32, "tf32": fm.TF32}[args.precision]
+    prec = {"fp64": fm.FP64, "fp32": fm.FP32, "tf32": fm.TF32, "bf16x3": fm.BF16X3}[args.precision]
     V, F, D = wl["mesh"]()
     t0 = time.perf_counter()
     g = fm.FMBEM(V, F, D, wl["eps"], wl["mu"], wl["k0"], p=p, leaf_size=args.leaf, profile_phases=1)
@@ -661,13 +684,14 @@ def run_ours(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         phases = []
         wall0 = time.perf_counter()
-        for k in range(steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            g.matvec(x, y, precision=precision)
-            ev[k][1].record(stream)
-            phases.append(g.last_matvec_times())
-        torch.cuda.synchronize()
+        with nvtx_range(f"{args.workload}_{ {fm.FP64: 'fp64', fm.FP32: 'fp32', fm.TF32: 'tf32'}.get(precision, 'bf16x3')}"):
+            for k in range(steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                g.matvec(x, y, precision=precision)
+                ev[k][1].record(stream)
+                phases.append(g.last_matvec_times())
+            torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         if world > 1:
             dist.barrier()
@@ -703,9 +727,10 @@ def run_ours(args):
 
     other = None
     if not args.no_fp32:
-        others = [o for o in ("fp32", "tf32") if o != args.precision and (o == "fp32" or tensor_path(nr))]
+        others = [o for o in ("fp32", "tf32", "bf16x3") if o != args.precision and
+                  (o == "fp32" or tensor_path(nr) or (o == "bf16x3" and 3 * nr <= 24))]
         for o in others:
-            mso, pho, _, _ = timed({"fp32": fm.FP32, "tf32": fm.TF32}[o], args.steps, args.warmup)
+            mso, pho, _, _ = timed({"fp32": fm.FP32, "tf32": fm.TF32, "bf16x3": fm.BF16X3}[o], args.steps, args.warmup)
             other = dict(other or {}, **{o: dict(value=world * N * nr / (mso * 1e-3), ms_per_step=mso,
                                                  roofline=roofline(info, p, nr, n_dom, pho, o))})
     if nr > 1:
@@ -724,7 +749,7 @@ def run_ours(args):
         other = dict(other or {}, fp64_single_rhs=dict(value=world * N / (ms1 * 1e-3), ms_per_step=ms1))
 
     # the adjoint (transposed) product through the same tree and translations, in the bench's precision
-    aprec = {"fp64": fm.FP64, "fp32": fm.FP32, "tf32": fm.TF32}[args.precision]
+    aprec = {"fp64": fm.FP64, "fp32": fm.FP32, "tf32": fm.TF32, "bf16x3": fm.BF16X3}[args.precision]
     for _ in range(2):
         g.adjoint_matvec(x, y, precision=aprec)
     torch.cuda.synchronize()
@@ -764,7 +789,8 @@ def run_ours(args):
     if not args.no_solve:
         solve = {}
         if nr == 1:
-            kinds = (("plain_fp64", fm.FP64, 0.5e-4), ("fp32_inner_fp64_refined", fm.FP32, 0.5e-4))
+            kinds = (("plain_fp64", fm.FP64, 0.5e-4), ("fp32_inner_fp64_refined", fm.FP32, 0.5e-4),
+                     ("bf16x3_inner_fp64_refined", fm.BF16X3, 0.5e-4))
         else:
             kinds = (("fp32_inner_fp64_refined", fm.FP32, 0.5e-4),) + \
                 ((("tf32_inner_fp64_refined", fm.TF32, 1e-2),) if tensor_path(nr) else ())
@@ -805,7 +831,8 @@ def run_ours(args):
     launches_per_step = launches_per_matvec(info["l_max"], nr, n_dom, args.precision)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype={"fp64": "f64", "fp32": "f32", "tf32": "f32 (M2L on TF32 tensor cores)"}[args.precision],
+                dtype={"fp64": "f64", "fp32": "f32", "tf32": "f32 (M2L on TF32 tensor cores)",
+                       "bf16x3": "f32 (M2L on tensor cores, bf16 hi/lo split operands)"}[args.precision],
                 data="synthetic",
                 config=dict(workload=args.workload, desc=wl["desc"], nodes=N, n_rhs=nr, p=p, leaf_size=args.leaf,
                             tree=info, parallelism=f"replicas x{world}",

@@ -510,6 +510,8 @@ __global__ void __launch_bounds__(160, 1)
     __shared__ uint64_t full[OFS_STAGES], empty[OFS_STAGES], done, tfree, fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
+    __shared__ int64_t rowoff[4][OFS_M];  // per producer warp: element offset of each pair column's
+                                          // coefficients in this pass, -1 past the pass's pairs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ck = chunk0 + blockIdx.x;
     const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
@@ -545,6 +547,14 @@ __global__ void __launch_bounds__(160, 1)
     if (warp < 4) {
         int last_issued = -1;  // this warp's last unit whose bulk copy was issued
         for (int pass = 0; pass < passes && !s_abort; ++pass) {
+            // ---- the pass's source rows, in this warp's own table (no other warp waits for it)
+            for (int m = lane; m < OFS_M; m += 32) {
+                const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
+                rowoff[warp][m] = (m < P.ppp * P.ncols && jj < cnt)
+                                      ? (((int64_t)P.d * P.nbox + ff_src[pair_e[beg + jj]]) * P.ncols + c) * twop2
+                                      : (int64_t)-1;
+            }
+            __syncwarp();
             // ---- fill this warp's slots of the pass
             for (int kb = 0; kb < P.kblocks; ++kb) {
                 const int u = pass * P.kblocks + kb;
@@ -559,23 +569,22 @@ __global__ void __launch_bounds__(160, 1)
                     bulk_load(sB, Amat + (int64_t)kb * P.np * 64, 2u * b_half, &full[warp]);
                     last_issued = u;
                 }
-                // gather 128 rows x (4 hi + 4 lo) 16-byte chunks of source coefficients
+                // gather 128 rows x (4 hi + 4 lo) 16-byte chunks of source coefficients with
+                // asynchronous copies (zero-filled past the pass's pairs and past 2 p^2), all in
+                // flight together, then wait for them and make them visible to the tensor cores
                 for (int i = lane; i < OFS_M * 8; i += 32) {
                     const int m = i >> 3, part = i & 7, lohalf = part >> 2, qc = part & 3;
-                    const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
                     const int k0 = kb * KBLK + 8 * qc;
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (m < P.ppp * P.ncols && jj < cnt && k0 < twop2) {
-                        const int64_t row = ((int64_t)P.d * P.nbox + ff_src[pair_e[beg + jj]]) * P.ncols + c;
-                        const __nv_bfloat16 *src = (lohalf ? Clo : Chi) + row * twop2 + k0;
-                        v = *reinterpret_cast<const uint4 *>(src);
-                    }
+                    const int64_t ro = rowoff[warp][m];
+                    const bool valid = ro >= 0 && k0 < twop2;
+                    const __nv_bfloat16 *src = valid ? (lohalf ? Clo : Chi) + ro + k0 : Chi;
                     const uint32_t dst = sM + (uint32_t)lohalf * (OFS_M * 64u) + (uint32_t)m * 64u +
                                          (uint32_t)((qc ^ ((m >> 1) & 3)) << 4);
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y), "r"(v.z),
-                                 "r"(v.w)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                                 "r"(valid ? 16 : 0)
                                  : "memory");
                 }
+                asm volatile("cp.async.wait_all;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[warp])) : "memory");
             }
