@@ -501,154 +501,204 @@ struct OfsLevel {
     uint32_t tmem_cols;
 };
 
-__global__ void __launch_bounds__(160, 1)
-    k_m2l_ofs(const OfsLevel P, int64_t chunk0, const int32_t *__restrict__ chunk_beg,
+// Persistent form: each CTA walks the chunks blockIdx.x, blockIdx.x + gridDim.x, ... as a sequence
+// of (chunk, pass) tiles; warps 0-3 gather (warp w fills ring slot w of every fourth K block of the
+// sequence), warp 4 issues the MMAs into one of two tensor-memory accumulators (tile t uses buffer
+// t mod 2), and warps 5-8 drain the other accumulator meanwhile (warp 5 + i reads lanes 32 ((i + 1)
+// mod 4) ...), so that gathering, MMAs and stores of consecutive tiles overlap.
+constexpr int OFS_THREADS = 288;
+
+__global__ void __launch_bounds__(OFS_THREADS, 1)
+    k_m2l_ofs(const OfsLevel P, int64_t chunk0, int64_t nch, const int32_t *__restrict__ chunk_beg,
               const int32_t *__restrict__ chunk_cnt, const int16_t *__restrict__ chunk_off,
               const int32_t *__restrict__ pair_e, const int32_t *__restrict__ ff_src, const __nv_bfloat16 *Chi,
               const __nv_bfloat16 *Clo, const __nv_bfloat16 *__restrict__ Aofs, float *Y, int *err) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t full[OFS_STAGES], empty[OFS_STAGES], done, tfree, fin;
+    __shared__ uint64_t full[OFS_STAGES], empty[OFS_STAGES], done[2], tfree[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ int64_t rowoff[4][OFS_M];  // per producer warp: element offset of each pair column's
-                                          // coefficients in this pass, -1 past the pass's pairs
+                                          // coefficients in its current tile, -1 past the tile's pairs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ck = chunk0 + blockIdx.x;
-    const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
-    const int16_t off = chunk_off[ck];
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
-    const uint32_t b_half = (uint32_t)P.np * 64u;             // one bf16 part of an S|R K block
+    const uint32_t b_half = (uint32_t)P.np * 64u;  // one bf16 part of an S|R K block
     const uint32_t stage_bytes = 2u * OFS_M * 64u + 2u * b_half;
-    const int passes = (cnt + P.ppp - 1) / P.ppp;
-    const int units = passes * P.kblocks;
     const int twop2 = 2 * P.p2;
+    const bool any = (int64_t)blockIdx.x < nch;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OFS_STAGES; ++s) {
             mbar_init(&full[s], 33);  // the filling warp's 32 lanes + the bulk copy's expect_tx
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
-        mbar_init(&tfree, 128);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&done[b], 1);
+            mbar_init(&tfree[b], 128);
+        }
         mbar_init(&fin, 1);
         s_abort = *(volatile int *)err;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(P.tmem_cols)
+                     "r"(2 * P.tmem_cols)
                      : "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const __nv_bfloat16 *Amat = Aofs + (P.amat0 + off) * (int64_t)P.kblocks * P.np * 64;
 
     if (warp < 4) {
-        int last_issued = -1;  // this warp's last unit whose bulk copy was issued
-        for (int pass = 0; pass < passes && !s_abort; ++pass) {
-            // ---- the pass's source rows, in this warp's own table (no other warp waits for it)
-            for (int m = lane; m < OFS_M; m += 32) {
-                const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
-                rowoff[warp][m] = (m < P.ppp * P.ncols && jj < cnt)
-                                      ? (((int64_t)P.d * P.nbox + ff_src[pair_e[beg + jj]]) * P.ncols + c) * twop2
-                                      : (int64_t)-1;
-            }
-            __syncwarp();
-            // ---- fill this warp's slots of the pass
-            for (int kb = 0; kb < P.kblocks; ++kb) {
-                const int u = pass * P.kblocks + kb;
-                if ((u & 3) != warp) continue;
-                const int q = u >> 2;
-                bool ok = q == 0 || mbar_wait(&empty[warp], (uint32_t)(q - 1) & 1u);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok || s_abort) { if (lane == 0) { atomicExch(err, 1); s_abort = 1; } break; }
-                const uint32_t sM = sbase + (uint32_t)warp * stage_bytes, sB = sM + 2u * OFS_M * 64u;
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[warp], 2u * b_half);
-                    bulk_load(sB, Amat + (int64_t)kb * P.np * 64, 2u * b_half, &full[warp]);
-                    last_issued = u;
+        // ------------------------------------------------------------------ producers
+        int64_t last_issued = -1;  // this warp's last unit whose bulk copy was issued
+        int64_t u = 0;             // unit (K block of a tile) counter of the CTA's sequence
+        bool stop = false;
+        for (int64_t ckl = blockIdx.x; ckl < nch && !stop; ckl += gridDim.x) {
+            const int64_t ck = chunk0 + ckl;
+            const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+            const int passes = (cnt + P.ppp - 1) / P.ppp;
+            for (int pass = 0; pass < passes && !stop; ++pass) {
+                bool table = false;  // this tile's source rows are in this warp's table
+                for (int kb = 0; kb < P.kblocks; ++kb, ++u) {
+                    if ((u & 3) != warp) continue;
+                    if (!table) {
+                        __syncwarp();
+                        for (int m = lane; m < OFS_M; m += 32) {
+                            const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
+                            rowoff[warp][m] = (m < P.ppp * P.ncols && jj < cnt)
+                                                  ? (((int64_t)P.d * P.nbox + ff_src[pair_e[beg + jj]]) * P.ncols + c) *
+                                                        twop2
+                                                  : (int64_t)-1;
+                        }
+                        __syncwarp();
+                        table = true;
+                    }
+                    const int64_t q = u >> 2;
+                    bool ok = q == 0 || mbar_wait(&empty[warp], (uint32_t)(q - 1) & 1u);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok || s_abort) {
+                        if (lane == 0) { atomicExch(err, 1); s_abort = 1; }
+                        stop = true;
+                        break;
+                    }
+                    const uint32_t sM = sbase + (uint32_t)warp * stage_bytes, sB = sM + 2u * OFS_M * 64u;
+                    if (lane == 0) {
+                        const __nv_bfloat16 *Amat =
+                            Aofs + ((P.amat0 + chunk_off[ck]) * (int64_t)P.kblocks + kb) * (int64_t)P.np * 64;
+                        mbar_arrive_expect_tx(&full[warp], 2u * b_half);
+                        bulk_load(sB, Amat, 2u * b_half, &full[warp]);
+                        last_issued = u;
+                    }
+                    // 128 rows x (4 hi + 4 lo) 16-byte chunks of source coefficients by asynchronous
+                    // copies (zero-filled past the tile's pairs and past 2 p^2), all in flight together
+                    for (int i = lane; i < OFS_M * 8; i += 32) {
+                        const int m = i >> 3, part = i & 7, lohalf = part >> 2, qc = part & 3;
+                        const int k0 = kb * KBLK + 8 * qc;
+                        const int64_t ro = rowoff[warp][m];
+                        const bool valid = ro >= 0 && k0 < twop2;
+                        const __nv_bfloat16 *src = valid ? (lohalf ? Clo : Chi) + ro + k0 : Chi;
+                        const uint32_t dst = sM + (uint32_t)lohalf * (OFS_M * 64u) + (uint32_t)m * 64u +
+                                             (uint32_t)((qc ^ ((m >> 1) & 3)) << 4);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                                     "r"(valid ? 16 : 0)
+                                     : "memory");
+                    }
+                    asm volatile("cp.async.wait_all;" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[warp])) : "memory");
                 }
-                // gather 128 rows x (4 hi + 4 lo) 16-byte chunks of source coefficients with
-                // asynchronous copies (zero-filled past the pass's pairs and past 2 p^2), all in
-                // flight together, then wait for them and make them visible to the tensor cores
-                for (int i = lane; i < OFS_M * 8; i += 32) {
-                    const int m = i >> 3, part = i & 7, lohalf = part >> 2, qc = part & 3;
-                    const int k0 = kb * KBLK + 8 * qc;
-                    const int64_t ro = rowoff[warp][m];
-                    const bool valid = ro >= 0 && k0 < twop2;
-                    const __nv_bfloat16 *src = valid ? (lohalf ? Clo : Chi) + ro + k0 : Chi;
-                    const uint32_t dst = sM + (uint32_t)lohalf * (OFS_M * 64u) + (uint32_t)m * 64u +
-                                         (uint32_t)((qc ^ ((m >> 1) & 3)) << 4);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                                 "r"(valid ? 16 : 0)
-                                 : "memory");
-                }
-                asm volatile("cp.async.wait_all;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[warp])) : "memory");
             }
-            if (s_abort) break;
-            // ---- drain this pass's accumulators: lane = pair column 32 warp + lane
-            bool ok = mbar_wait(&done, (uint32_t)pass & 1u);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) { if (lane == 0) { atomicExch(err, 1); s_abort = 1; } break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int m = warp * 32 + lane;
-            const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
-            const bool valid = m < P.ppp * P.ncols && jj < cnt;
-            float *out = valid ? Y + (((int64_t)pair_e[beg + jj] - P.e_first) * P.ncols + c) * twop2 : nullptr;
-            for (int c0 = 0; c0 < P.np; c0 += 16) {
-                uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (valid)
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < twop2) out[c0 + j] = __uint_as_float(v[j]);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
         }
-        // copies still in flight after an abort: wait (bounded) for this warp's last bulk copy
+        // a copy still in flight after an abort: wait (bounded) for this warp's last bulk copy
         if (lane == 0 && last_issued >= 0 && s_abort)
             if (!mbar_wait(&full[warp], (uint32_t)(last_issued >> 2) & 1u)) atomicExch(err, 1);
-    } else if (lane == 0) {
-        // ------------------------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_bf16(P.np);
-        bool ok = true;
-        for (int u = 0; u < units && !s_abort; ++u) {
-            const int s = u & 3, q = u >> 2, pass = u / P.kblocks, kb = u - pass * P.kblocks;
-            if (kb == 0 && pass > 0 && !mbar_wait(&tfree, (uint32_t)(pass - 1) & 1u)) { ok = false; break; }
-            if (!mbar_wait(&full[s], (uint32_t)q & 1u)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sM = sbase + (uint32_t)s * stage_bytes, sB = sM + 2u * OFS_M * 64u;
+    } else if (warp == 4) {
+        if (lane == 0) {
+            // -------------------------------------------------------------- MMA issuer
+            const uint32_t idesc = idesc_bf16(P.np);
+            bool ok = true;
+            int64_t u = 0, t = 0;
+            for (int64_t ckl = blockIdx.x; ckl < nch && ok && !s_abort; ckl += gridDim.x) {
+                const int passes = (chunk_cnt[chunk0 + ckl] + P.ppp - 1) / P.ppp;
+                for (int pass = 0; pass < passes && ok && !s_abort; ++pass, ++t) {
+                    const int buf = (int)(t & 1);
+                    const uint32_t acc = tmem + (uint32_t)buf * P.tmem_cols;
+                    if (t >= 2 && !mbar_wait(&tfree[buf], (uint32_t)((t >> 1) - 1) & 1u)) { ok = false; break; }
+                    for (int kb = 0; kb < P.kblocks; ++kb, ++u) {
+                        const int s = (int)(u & 3);
+                        if (!mbar_wait(&full[s], (uint32_t)(u >> 2) & 1u)) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sM = sbase + (uint32_t)s * stage_bytes, sB = sM + 2u * OFS_M * 64u;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {  // K = 16 bf16 per MMA, 32 bytes along the 64-byte rows
-                const uint64_t mh = smem_desc_sw64(sM + 32u * j), ml = smem_desc_sw64(sM + OFS_M * 64u + 32u * j);
-                const uint64_t bh = smem_desc_sw64(sB + 32u * j), bl = smem_desc_sw64(sB + b_half + 32u * j);
-                mma_bf16(tmem, mh, bh, idesc, (kb > 0 || j > 0) ? 1u : 0u);
-                mma_bf16(tmem, mh, bl, idesc, 1u);
-                mma_bf16(tmem, ml, bh, idesc, 1u);
+                        for (int j = 0; j < 2; ++j) {  // K = 16 bf16 per MMA, 32 bytes along the 64-byte rows
+                            const uint64_t mh = smem_desc_sw64(sM + 32u * j);
+                            const uint64_t ml = smem_desc_sw64(sM + OFS_M * 64u + 32u * j);
+                            const uint64_t bh = smem_desc_sw64(sB + 32u * j), bl = smem_desc_sw64(sB + b_half + 32u * j);
+                            mma_bf16(acc, mh, bh, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+                            mma_bf16(acc, mh, bl, idesc, 1u);
+                            mma_bf16(acc, ml, bh, idesc, 1u);
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                    if (ok) mma_commit(&done[buf]);
+                }
             }
-            mma_commit(&empty[s]);
-            if (kb == P.kblocks - 1) mma_commit(&done);
+            mma_commit(&fin);  // arrives once every MMA issued above has completed
+            if (!ok) { atomicExch(err, 1); s_abort = 1; }
         }
-        mma_commit(&fin);  // arrives once every MMA issued above has completed
-        if (!ok) { atomicExch(err, 1); s_abort = 1; }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ epilogue warps 5..8
+        const int ew = (warp - 5 + 1) & 3;  // the tensor-memory lane quarter this warp may read
+        int64_t t = 0;
+        bool stop = false;
+        for (int64_t ckl = blockIdx.x; ckl < nch && !stop; ckl += gridDim.x) {
+            const int64_t ck = chunk0 + ckl;
+            const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+            const int passes = (cnt + P.ppp - 1) / P.ppp;
+            for (int pass = 0; pass < passes; ++pass, ++t) {
+                const int buf = (int)(t & 1);
+                bool ok = !s_abort && mbar_wait(&done[buf], (uint32_t)(t >> 1) & 1u);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0) { atomicExch(err, 1); s_abort = 1; }
+                    stop = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int m = ew * 32 + lane;
+                const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
+                const bool valid = m < P.ppp * P.ncols && jj < cnt;
+                float *out = valid ? Y + (((int64_t)pair_e[beg + jj] - P.e_first) * P.ncols + c) * twop2 : nullptr;
+                for (int c0 = 0; c0 < P.np; c0 += 16) {
+                    uint32_t v[16];
+                    const uint32_t taddr = tmem + (uint32_t)buf * P.tmem_cols + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0;
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                          "=r"(v[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (valid)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < twop2) out[c0 + j] = __uint_as_float(v[j]);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[buf])) : "memory");
+            }
+        }
     }
     __syncwarp();
     __syncthreads();
-    if (threadIdx.x == 0 && units > 0 && !mbar_wait(&fin, 0)) atomicExch(err, 1);
+    if (threadIdx.x == 0 && any && !mbar_wait(&fin, 0)) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * P.tmem_cols)
+                     : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 }
@@ -807,13 +857,18 @@ void run_m2l_ofs(fmbem *h, const float *C, float *Y, int l, int d, int64_t nr, i
     const int p2 = h->p2, kb = tc_kblocks(p2), np = ofs_np(p2);
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * 3 * nr * 2 * p2;
     const __nv_bfloat16 *Chi = (const __nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
-    uint32_t tcols = 32;
+    uint32_t tcols = 32;  // one accumulator; two are allocated (2 x 256 columns at most)
     while ((int)tcols < np) tcols <<= 1;
     const OfsLevel P{h->nbox, (int)(3 * nr), p2, kb, np, d, e_first, (int)(OFS_M / (3 * nr)),
                      ((int64_t)d * (h->lmax + 1) + l) * 316, tcols};
     const size_t smem = (size_t)OFS_STAGES * (2 * OFS_M * 64 + 2 * (size_t)np * 64) + 1024;
     CK(cudaFuncSetAttribute(k_m2l_ofs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_m2l_ofs<<<(unsigned)nch, 160, smem, s>>>(P, c0, h->chunk_beg, h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src,
-                                                Chi, Clo, (const __nv_bfloat16 *)h->Aofs, Y, h->tc_err);
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = std::min<int64_t>(nch, nsm);  // one persistent CTA per SM
+    k_m2l_ofs<<<(unsigned)grid, OFS_THREADS, smem, s>>>(P, c0, nch, h->chunk_beg, h->chunk_cnt, h->chunk_off,
+                                                         h->pair_e, h->ff_src, Chi, Clo,
+                                                         (const __nv_bfloat16 *)h->Aofs, Y, h->tc_err);
     CKL("k_m2l_ofs");
 }
