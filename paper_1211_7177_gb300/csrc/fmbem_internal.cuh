@@ -170,6 +170,7 @@ struct fmbem {
     float *Atc = nullptr, *Lltc = nullptr;
     float *Abf = nullptr, *Llbf = nullptr;  // the same matrices as bf16 hi/lo images (BF16x3)
     void *Aofs = nullptr;  // S|R bf16 hi/lo images for the offset-stationary few-column M2L (BF16x3)
+    void *chunk_pairs = nullptr;  // int2 [chunks][32]: (source box, CSR position) of each chunk's pairs
     int *tc_err = nullptr;
     bool m2l_rotation = false;
     int n_tlen = 0;

@@ -2802,7 +2802,7 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
         const bool use_rot_mm = use_rot && h->rmm_chunk_beg != nullptr;
         cx<R> *Y = (cx<R> *)h->ybuf;
         // BF16x3 with few columns: the S|R products of each offset chunk on the tensor cores
-        const bool ofs = tensor_mode == 2 && f32 && h->Aofs != nullptr && 3 * nr <= MAXC;
+        const bool ofs = tensor_mode == 2 && f32 && h->Aofs != nullptr && h->chunk_pairs != nullptr && 3 * nr <= MAXC;
         if (ofs) split_expansions_bf16(h, (float *)C, nr, s);
         for (int l = 2; l <= lmax; ++l) {
             const LevelInfo &Lv = h->lev[l];

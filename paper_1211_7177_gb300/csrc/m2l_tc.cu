@@ -509,9 +509,8 @@ struct OfsLevel {
 constexpr int OFS_THREADS = 288;
 
 __global__ void __launch_bounds__(OFS_THREADS, 1)
-    k_m2l_ofs(const OfsLevel P, int64_t chunk0, int64_t nch, const int32_t *__restrict__ chunk_beg,
-              const int32_t *__restrict__ chunk_cnt, const int16_t *__restrict__ chunk_off,
-              const int32_t *__restrict__ pair_e, const int32_t *__restrict__ ff_src, const __nv_bfloat16 *Chi,
+    k_m2l_ofs(const OfsLevel P, int64_t chunk0, int64_t nch, const int32_t *__restrict__ chunk_cnt,
+              const int16_t *__restrict__ chunk_off, const int2 *__restrict__ chunk_pairs, const __nv_bfloat16 *Chi,
               const __nv_bfloat16 *Clo, const __nv_bfloat16 *__restrict__ Aofs, float *Y, int *err) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[OFS_STAGES], empty[OFS_STAGES], done[2], tfree[2], fin;
@@ -555,7 +554,9 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
         bool stop = false;
         for (int64_t ckl = blockIdx.x; ckl < nch && !stop; ckl += gridDim.x) {
             const int64_t ck = chunk0 + ckl;
-            const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
+            // the chunk's (source box, CSR position) pairs, one per lane, and its size
+            const int2 pr = chunk_pairs[ck * 32 + lane];
+            const int cnt = P.ppp >= 32 ? 32 : chunk_cnt[ck];  // one pass holds every chunk when ppp >= 32
             const int passes = (cnt + P.ppp - 1) / P.ppp;
             for (int pass = 0; pass < passes && !stop; ++pass) {
                 bool table = false;  // this tile's source rows are in this warp's table
@@ -565,9 +566,9 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
                         __syncwarp();
                         for (int m = lane; m < OFS_M; m += 32) {
                             const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
-                            rowoff[warp][m] = (m < P.ppp * P.ncols && jj < cnt)
-                                                  ? (((int64_t)P.d * P.nbox + ff_src[pair_e[beg + jj]]) * P.ncols + c) *
-                                                        twop2
+                            const int src = __shfl_sync(0xffffffffu, pr.x, jj & 31);
+                            rowoff[warp][m] = (m < P.ppp * P.ncols && jj < 32 && src >= 0)
+                                                  ? (((int64_t)P.d * P.nbox + src) * P.ncols + c) * twop2
                                                   : (int64_t)-1;
                         }
                         __syncwarp();
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
             bool ok = true;
             int64_t u = 0, t = 0;
             for (int64_t ckl = blockIdx.x; ckl < nch && ok && !s_abort; ckl += gridDim.x) {
-                const int passes = (chunk_cnt[chunk0 + ckl] + P.ppp - 1) / P.ppp;
+                const int passes = P.ppp >= 32 ? 1 : (chunk_cnt[chunk0 + ckl] + P.ppp - 1) / P.ppp;
                 for (int pass = 0; pass < passes && ok && !s_abort; ++pass, ++t) {
                     const int buf = (int)(t & 1);
                     const uint32_t acc = tmem + (uint32_t)buf * P.tmem_cols;
@@ -654,8 +655,8 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
         bool stop = false;
         for (int64_t ckl = blockIdx.x; ckl < nch && !stop; ckl += gridDim.x) {
             const int64_t ck = chunk0 + ckl;
-            const int beg = chunk_beg[ck], cnt = chunk_cnt[ck];
-            const int passes = (cnt + P.ppp - 1) / P.ppp;
+            const int2 pr = chunk_pairs[ck * 32 + lane];
+            const int passes = P.ppp >= 32 ? 1 : (chunk_cnt[ck] + P.ppp - 1) / P.ppp;
             for (int pass = 0; pass < passes; ++pass, ++t) {
                 const int buf = (int)(t & 1);
                 bool ok = !s_abort && mbar_wait(&done[buf], (uint32_t)(t >> 1) & 1u);
@@ -668,8 +669,9 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int m = ew * 32 + lane;
                 const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
-                const bool valid = m < P.ppp * P.ncols && jj < cnt;
-                float *out = valid ? Y + (((int64_t)pair_e[beg + jj] - P.e_first) * P.ncols + c) * twop2 : nullptr;
+                const int e = __shfl_sync(0xffffffffu, pr.y, jj & 31);
+                const bool valid = m < P.ppp * P.ncols && jj < 32 && e >= 0;
+                float *out = valid ? Y + (((int64_t)e - P.e_first) * P.ncols + c) * twop2 : nullptr;
                 for (int c0 = 0; c0 < P.np; c0 += 16) {
                     uint32_t v[16];
                     const uint32_t taddr = tmem + (uint32_t)buf * P.tmem_cols + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0;
@@ -681,10 +683,13 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
                           "=r"(v[15])
                         : "r"(taddr));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (valid)
+                    if (valid)  // 16-byte stores (rows of 2 p^2 floats, p even: 16-byte aligned)
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < twop2) out[c0 + j] = __uint_as_float(v[j]);
+                        for (int j = 0; j < 16; j += 4)
+                            if (c0 + j < twop2)
+                                *reinterpret_cast<float4 *>(out + c0 + j) =
+                                    make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[buf])) : "memory");
@@ -700,6 +705,21 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * P.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+}
+
+// per chunk of FF pairs, 32 entries (source box, CSR position of the pair); (-1, -1) past the chunk
+__global__ void k_chunk_pairs(int64_t nch, const int32_t *chunk_beg, const int32_t *chunk_cnt, const int32_t *pair_e,
+                              const int32_t *ff_src, int2 *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nch * 32) return;
+    const int64_t ck = i >> 5;
+    const int j = (int)(i & 31);
+    if (j < chunk_cnt[ck]) {
+        const int e = pair_e[chunk_beg[ck] + j];
+        out[i] = make_int2(ff_src[e], e);
+    } else {
+        out[i] = make_int2(-1, -1);
     }
 }
 
@@ -835,6 +855,13 @@ void build_ofs_tables(fmbem *h, cudaStream_t s) {
     k_build_ofs_tables<<<(unsigned)((nmat * per + tb - 1) / tb), tb, 0, s>>>(h->T_m2l64, nmat, p2, np, kb,
                                                                             (__nv_bfloat16 *)h->Aofs);
     CKL("k_build_ofs_tables");
+    const int64_t nch = h->h_chunk_first.empty() ? 0 : h->h_chunk_first.back();
+    if (nch > 0) {
+        h->chunk_pairs = dev_alloc(h, sizeof(int2) * 32 * nch);
+        k_chunk_pairs<<<(unsigned)((nch * 32 + tb - 1) / tb), tb, 0, s>>>(nch, h->chunk_beg, h->chunk_cnt, h->pair_e,
+                                                                         h->ff_src, (int2 *)h->chunk_pairs);
+        CKL("k_chunk_pairs");
+    }
     if (!h->tc_err) {
         h->tc_err = (int *)dev_alloc(h, sizeof(int));
         CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
@@ -867,8 +894,8 @@ void run_m2l_ofs(fmbem *h, const float *C, float *Y, int l, int d, int64_t nr, i
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int64_t grid = std::min<int64_t>(nch, nsm);  // one persistent CTA per SM
-    k_m2l_ofs<<<(unsigned)grid, OFS_THREADS, smem, s>>>(P, c0, nch, h->chunk_beg, h->chunk_cnt, h->chunk_off,
-                                                         h->pair_e, h->ff_src, Chi, Clo,
+    k_m2l_ofs<<<(unsigned)grid, OFS_THREADS, smem, s>>>(P, c0, nch, h->chunk_cnt, h->chunk_off,
+                                                         (const int2 *)h->chunk_pairs, Chi, Clo,
                                                          (const __nv_bfloat16 *)h->Aofs, Y, h->tc_err);
     CKL("k_m2l_ofs");
 }
