@@ -153,6 +153,16 @@ typedef struct {
                                 small problems on one GPU, e.g. fmbem_batch_*); products, solves and
                                 observables that need FP64, TF32 or BF16X3 passes are then refused
                                 with FMBEM_ERR_INVALID_ARGUMENT, and the near-field cache is off [0] */
+    double fmm_tol;          /* > 0: choose the truncation number from this tolerance instead of p
+                                (Eq. 2.17 truncated after degree p - 1): for every level and domain
+                                the relative RMS error of the truncated addition theorem (the
+                                multipole expansion about the source box centre plus the local
+                                expansion about the target box centre, Eq. 2.14) is sampled over
+                                points of a box and its far-field neighbours at offsets (2,0,0) ...
+                                (3,2,1) box widths; each level takes the smallest p in 2..20 that
+                                meets the tolerance, and the handle uses the largest of them (the
+                                expansions of all levels have one length); fmbem_truncation
+                                reports both.  0: use p [0]                                     */
 } fmbem_options;
 
 void fmbem_default_options(fmbem_options *opt);
@@ -203,6 +213,11 @@ fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, do
 /* Number of (target, source) node pairs that take the near-singular correction (0 when
  * near_singular_radius is 0). */
 int64_t fmbem_num_near_singular_pairs(const fmbem *h);
+
+/* The truncation number p the handle uses, and (arrays of l_max + 1 entries, levels 0 and 1
+ * unused) the truncation each level needs for fmm_tol and the sampled relative error estimate at p
+ * (-1 without fmm_tol, when p is the option's).  Any pointer may be NULL. */
+fmbem_status fmbem_truncation(const fmbem *h, int32_t *p, int32_t *p_level, double *err_level);
 
 /* Octree summary: l_max, number of leaves, total number of boxes on levels 2..l_max, and the
  * number of near-field (source, target) node pairs and of far-field box pairs (S|R

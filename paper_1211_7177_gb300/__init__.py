@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("outer_precision", ctypes.c_int), ("m2l_rotation", ctypes.c_int),
                 ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("near_singular_radius", ctypes.c_double), ("near_singular_levels", ctypes.c_int),
-                ("fp32_only", ctypes.c_int)]
+                ("fp32_only", ctypes.c_int), ("fmm_tol", ctypes.c_double)]
 
 
 class Mesh(ctypes.Structure):
@@ -76,6 +76,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_last_error": (ctypes.c_char_p, [P]),
         "fmbem_num_nodes": (i64, [P]),
         "fmbem_num_near_singular_pairs": (i64, [P]),
+        "fmbem_truncation": (i32, [P, P, P, P]),
         "fmbem_node_geometry": (i32, [P, P, P, P]),
         "fmbem_tree_info": (i32, [P, P, P, P, P, P]),
         "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
@@ -182,6 +183,16 @@ def fmbem_num_nodes(h):
 
 def fmbem_num_near_singular_pairs(h):
     return int(load_library().fmbem_num_near_singular_pairs(h))
+
+
+def fmbem_truncation(h):
+    """(p, {level: p_l}, {level: estimated error at p}) of a handle (see include/fmbem.h)."""
+    lm = fmbem_tree_info(h)["l_max"]
+    p = ctypes.c_int32()
+    pl = np.zeros(lm + 1, dtype=np.int32)
+    el = np.zeros(lm + 1)
+    _check(h, load_library().fmbem_truncation(h, ctypes.byref(p), _ptr(pl), _ptr(el)))
+    return p.value, {l: int(pl[l]) for l in range(2, lm + 1)}, {l: float(el[l]) for l in range(2, lm + 1)}
 
 
 def fmbem_node_geometry(h):
@@ -462,6 +473,9 @@ class FMBEM:
 
     def num_near_singular_pairs(self):
         return fmbem_num_near_singular_pairs(self.h)
+
+    def truncation(self):
+        return fmbem_truncation(self.h)
 
     def plane_wave_rhs(self, dirs, pols, out=None, stream=None):
         return fmbem_plane_wave_rhs(self.h, dirs, pols, out, stream)

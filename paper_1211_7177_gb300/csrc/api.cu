@@ -113,6 +113,7 @@ void fmbem_default_options(fmbem_options *o) {
     o->near_singular_radius = 0.0;
     o->near_singular_levels = 3;
     o->fp32_only = 0;
+    o->fmm_tol = 0.0;
 }
 
 fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
@@ -140,7 +141,8 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         o.m2l_rotation > 1 || o.near_cache < -1 || o.near_cache > 1 ||
         (o.boundary != FMBEM_BOUNDARY_PENETRABLE && o.boundary != FMBEM_BOUNDARY_IMPEDANCE) ||
         !(o.near_singular_radius >= 0 && std::isfinite(o.near_singular_radius)) || o.near_singular_levels < 0 ||
-        o.near_singular_levels > 6 || o.fp32_only < 0 || o.fp32_only > 1) {
+        o.near_singular_levels > 6 || o.fp32_only < 0 || o.fp32_only > 1 ||
+        !(o.fmm_tol >= 0 && o.fmm_tol < 1)) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
@@ -186,6 +188,10 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         }
         build_geometry(h, mesh, s);
         build_tree(h, s);
+        if (h->opt.fmm_tol > 0) {  // the truncation number from the tolerance, per level
+            choose_truncation(h, s);
+            h->m2l_rotation = o.m2l_rotation == 1 || (o.m2l_rotation == -1 && h->p >= 9);
+        }
         build_tables(h, s);
         near_work_items(h, s);
         std::vector<c64> dc(3 * (h->J + 1));
@@ -224,6 +230,16 @@ const char *fmbem_last_error(const fmbem *h) { return h ? h->err.c_str() : g_cre
 int64_t fmbem_num_nodes(const fmbem *h) { return h ? h->N : 0; }
 
 int64_t fmbem_num_near_singular_pairs(const fmbem *h) { return h ? h->ns_pairs : 0; }
+
+fmbem_status fmbem_truncation(const fmbem *h, int32_t *p, int32_t *p_level, double *err_level) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (p) *p = h->p;
+    for (int l = 0; l <= h->lmax; ++l) {
+        if (p_level) p_level[l] = l < (int)h->p_level.size() ? h->p_level[l] : (l >= 2 ? h->p : 0);
+        if (err_level) err_level[l] = l < (int)h->trunc_err.size() ? h->trunc_err[l] : -1.0;
+    }
+    return FMBEM_OK;
+}
 
 fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, double *weight) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;

@@ -92,6 +92,8 @@ struct fmbem {
     std::vector<c64> zeta;  // [J+1], entry 0 unused
     c64 *d_zeta = nullptr;  // device copy
     int p = 0, p2 = 0;                 // truncation number and p^2 coefficients
+    std::vector<int> p_level;          // option fmm_tol: the truncation each level needs [lmax+1]
+    std::vector<double> trunc_err;     // and the sampled error estimate at the p used
 
     // host copies of geometry (user order)
     std::vector<double> h_pos, h_nrm, h_w;
@@ -317,6 +319,7 @@ void build_rot_mm_lists(fmbem *h, cudaStream_t s);
 void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, const c64 *Tzb, cudaStream_t s);
 void near_work_items(fmbem *h, cudaStream_t s);
 void build_near_cache(fmbem *h, cudaStream_t s);
+void choose_truncation(fmbem *h, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // one persistent launch over many problems (batch.cu, kernel in fmm.cu)

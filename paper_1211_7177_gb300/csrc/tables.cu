@@ -196,6 +196,135 @@ __global__ void k_project(int nmat, int Q, int p2, const c64 *Yc, const c64 *F, 
 
 }  // namespace
 
+// ---- truncation number from a tolerance (option fmm_tol; reading of Eq. 2.17 and "FMM tolerance")
+// For every level l and domain d, the relative RMS error of the truncated addition theorem
+// (Eq. 2.14 summed over m: g = (i k / 4 pi) sum_n (2n + 1) j_n(k rho) h_n(k r) P_n(cos gamma)) is
+// sampled over source points s in a box of width w_l centred at the origin and target points t in
+// boxes of the far-field offsets (2,0,0), (2,1,0), (2,1,1), (2,2,1), (3,0,0), (3,2,1) w_l: the
+// multipole expansion about the source centre (rho = s, r = t) and the local expansion about the
+// target centre (rho = t - c_t, r = s - c_t) each truncated after degree p - 1, their errors added
+// per sample; err[(l * (J+1) + d) * (TRUNC_PMAX + 1) + p] = sqrt(sum err^2 / sum |g|^2).
+constexpr int TRUNC_PMAX = 20;
+__device__ inline uint64_t trunc_hash(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+__device__ inline double trunc_u01(uint64_t a, uint64_t b) { return (trunc_hash(a * 1000003ull + b) >> 11) * 0x1.0p-53; }
+
+__device__ inline void gegenbauer_partials(c64 k, double rho, double r, double cg, c64 *part) {
+    c64 jn[TRUNC_PMAX + 1], hn[TRUNC_PMAX + 1];
+    sph_j(TRUNC_PMAX, k * rho, jn);
+    sph_h1(TRUNC_PMAX, k * r, hn);
+    double P0 = 1.0, P1 = cg;  // Legendre P_n(cos gamma) by the three-term recurrence
+    c64 acc = {0, 0};
+    const c64 pre = (1.0 / (4.0 * FMBEM_PI)) * (c64{0.0, 1.0} * k);
+    part[0] = acc;
+    for (int n = 0; n < TRUNC_PMAX; ++n) {
+        const double Pn = n == 0 ? P0 : (n == 1 ? P1 : 0.0);
+        double Pcur = Pn;
+        if (n >= 2) {
+            Pcur = ((2.0 * n - 1.0) * cg * P1 - (n - 1.0) * P0) / n;
+            P0 = P1;
+            P1 = Pcur;
+        }
+        acc += (2.0 * n + 1.0) * Pcur * (jn[n] * hn[n]);
+        part[n + 1] = pre * acc;  // sum over degrees 0..n: truncation number n + 1
+    }
+}
+
+__global__ void k_trunc_error(int nlev, int lev0, const double *wl, int nd, const c64 *kd, int nsamp, double *err) {
+    const int li = blockIdx.x, d = blockIdx.y;
+    const double w = wl[li];
+    const c64 k = kd[d];
+    __shared__ double se[TRUNC_PMAX + 1], sg;
+    for (int q = threadIdx.x; q <= TRUNC_PMAX; q += blockDim.x) se[q] = 0.0;
+    if (threadIdx.x == 0) sg = 0.0;
+    __syncthreads();
+    const int offs[6][3] = {{2, 0, 0}, {2, 1, 0}, {2, 1, 1}, {2, 2, 1}, {3, 0, 0}, {3, 2, 1}};
+    double le[TRUNC_PMAX + 1];
+    for (int q = 0; q <= TRUNC_PMAX; ++q) le[q] = 0.0;
+    double lg = 0.0;
+    for (int i = threadIdx.x; i < nsamp; i += blockDim.x) {
+        const uint64_t key = ((uint64_t)(lev0 + li) * 64 + d) * 1000000ull + i;
+        const int o = i % 6;
+        double sp[3], tp[3], ct[3];
+        for (int c = 0; c < 3; ++c) {
+            sp[c] = (trunc_u01(key, c) - 0.5) * w;
+            ct[c] = offs[o][c] * w;
+            tp[c] = ct[c] + (trunc_u01(key, 3 + c) - 0.5) * w;
+        }
+        const double R = sqrt((tp[0] - sp[0]) * (tp[0] - sp[0]) + (tp[1] - sp[1]) * (tp[1] - sp[1]) +
+                              (tp[2] - sp[2]) * (tp[2] - sp[2]));
+        const c64 g = (1.0 / (4.0 * FMBEM_PI * R)) * cexpd(c64{-k.im * R, k.re * R});
+        // multipole about the source centre (the origin)
+        const double rs = sqrt(sp[0] * sp[0] + sp[1] * sp[1] + sp[2] * sp[2]);
+        const double rt = sqrt(tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2]);
+        const double cm = (sp[0] * tp[0] + sp[1] * tp[1] + sp[2] * tp[2]) / fmax(rs * rt, 1e-300);
+        // local about the target centre
+        double a[3], b[3];
+        for (int c = 0; c < 3; ++c) { a[c] = tp[c] - ct[c]; b[c] = sp[c] - ct[c]; }
+        const double ra = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        const double rb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        const double cl = (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / fmax(ra * rb, 1e-300);
+        c64 pm[TRUNC_PMAX + 1], pl[TRUNC_PMAX + 1];
+        gegenbauer_partials(k, rs, rt, cm, pm);
+        gegenbauer_partials(k, ra, rb, cl, pl);
+        for (int q = 0; q <= TRUNC_PMAX; ++q) {
+            const double e = sqrt(abs2(g - pm[q])) + sqrt(abs2(g - pl[q]));
+            le[q] += e * e;
+        }
+        lg += abs2(g);
+    }
+    for (int q = 0; q <= TRUNC_PMAX; ++q) atomicAdd(&se[q], le[q]);
+    atomicAdd(&sg, lg);
+    __syncthreads();
+    for (int q = threadIdx.x; q <= TRUNC_PMAX; q += blockDim.x)
+        err[((int64_t)li * nd + d) * (TRUNC_PMAX + 1) + q] = sqrt(se[q] / fmax(sg, 1e-300));
+}
+
+void choose_truncation(fmbem *h, cudaStream_t s) {
+    const double tol = h->opt.fmm_tol;
+    const int lmax = h->lmax, nlev = lmax - 1, nd = h->Jf + 1;  // levels 2..lmax
+    std::vector<double> wl(nlev);
+    for (int l = 2; l <= lmax; ++l) wl[l - 2] = h->lev[l].w;
+    double *dw = (double *)dev_alloc(h, sizeof(double) * nlev);
+    c64 *dk = (c64 *)dev_alloc(h, sizeof(c64) * nd);
+    double *de = (double *)dev_alloc(h, sizeof(double) * nlev * nd * (TRUNC_PMAX + 1));
+    CK(cudaMemcpyAsync(dw, wl.data(), sizeof(double) * nlev, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dk, h->k.data(), sizeof(c64) * nd, cudaMemcpyHostToDevice, s));
+    k_trunc_error<<<dim3((unsigned)nlev, (unsigned)nd), 128, 0, s>>>(nlev, 2, dw, nd, dk, 6 * 512, de);
+    CKL("k_trunc_error");
+    std::vector<double> e((size_t)nlev * nd * (TRUNC_PMAX + 1));
+    CK(cudaMemcpyAsync(e.data(), de, sizeof(double) * e.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dev_free(h, dw);
+    dev_free(h, dk);
+    dev_free(h, de);
+    h->p_level.assign(lmax + 1, 0);
+    h->trunc_err.assign(lmax + 1, 0.0);
+    int p = 2;
+    for (int l = 2; l <= lmax; ++l) {
+        int pl = 2;
+        for (int d = 0; d < nd; ++d) {
+            const double *el = &e[((size_t)(l - 2) * nd + d) * (TRUNC_PMAX + 1)];
+            int q = 2;
+            while (q < TRUNC_PMAX && !(el[q] <= tol)) ++q;
+            pl = std::max(pl, q);
+        }
+        h->p_level[l] = pl;
+        p = std::max(p, pl);
+    }
+    for (int l = 2; l <= lmax; ++l) {
+        double worst = 0.0;
+        for (int d = 0; d < nd; ++d) worst = std::max(worst, e[((size_t)(l - 2) * nd + d) * (TRUNC_PMAX + 1) + p]);
+        h->trunc_err[l] = worst;
+    }
+    h->p = p;
+    h->p2 = p * p;
+}
+
 void build_tables(fmbem *h, cudaStream_t s) {
     const int p = h->p, p2 = p * p, J = h->J, lmax = h->lmax;
     const int64_t N = h->N;

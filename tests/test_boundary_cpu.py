@@ -172,3 +172,13 @@ def test_near_singular_options_validated_before_device_work():
             _create(V, F, D, **kw)
         assert e.value.status == 1, kw
     assert fm.load_library().fmbem_num_near_singular_pairs(None) == 0
+
+
+def test_fmm_tol_validated_before_device_work():
+    o = fm.fmbem_default_options()
+    assert o.fmm_tol == 0.0
+    V, F, D = fi.icosphere(1)
+    for bad in (-1e-5, 1.0, float("nan")):
+        with pytest.raises(fm.FMBEMError) as e:
+            _create(V, F, D, fmm_tol=bad)
+        assert e.value.status == 1, bad
