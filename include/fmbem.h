@@ -416,6 +416,67 @@ fmbem_status fmbem_near_field_fmm(fmbem *h, const void *x_dev, int64_t n_rhs, in
 fmbem_status fmbem_near_field_functional(fmbem *h, int64_t n_fun, int64_t n_pts, const double *pts,
                                          const fmbem_c64 *cE, const fmbem_c64 *cH, void *out_dev, void *stream);
 
+/* Cross sections and the far-zone optical force of solutions x of the plane waves (dir[r],
+ * pol[r]) (Section 4), all on the device: the far-field amplitude F of fmbem_far_field in the
+ * forward directions and on a Gauss-Legendre (cos theta, n_theta nodes) x trapezoid (phi, n_phi
+ * nodes) rule on the unit sphere, then per right-hand side
+ *   C_ext = (4 pi / k) Im[conj(e) . F(d)]   (optical theorem),
+ *   C_sca = sum_q w_q |F(u_q)|^2,
+ *   C_abs = -(1/k) sum_b w_b Im(Phi_b . conj(Psi_b))   (Eq. 4.2),
+ *   F_far = (C_ext d - sum_q w_q |F(u_q)|^2 u_q) / 2   (momentum balance in the far zone; the
+ *           time-averaged force on all scatterers together in units with eps_0 = mu_0 = c = 1 and
+ *           a unit-amplitude wave), k the background wavenumber.
+ *   x_dev     device [n_rhs][N][6] complex128 (user order), read.
+ *   dir, pol  host [n_rhs][3] each (pol complex128).
+ *   out_host  host [n_rhs][6] = (C_ext, C_sca, C_abs, F_far x, y, z), written.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (counts, NULL pointers, n_theta or n_phi < 2, a lossy
+ * background), FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
+fmbem_status fmbem_cross_sections(fmbem *h, const void *x_dev, int64_t n_rhs, const double *dir, const fmbem_c64 *pol,
+                                  int32_t n_theta, int32_t n_phi, double *out_host, void *stream);
+
+/* Time-averaged optical force on the scatterers inside the sphere (center, radius) in the plane
+ * waves (dir[r], pol[r]) (Appendix D): the total E and H of fmbem_near_field on the points
+ * center + radius u_q of the sphere rule of fmbem_cross_sections, and
+ *   F = sum_q w_q radius^2 T n_q,  T n = Re[E (E*.n) + H (H*.n) - (|E|^2 + |H|^2) n / 2] / 2
+ * (Maxwell stress tensor, units with eps_0 = mu_0 = c = 1), reduced on the device.  The sphere
+ * must lie in the background, enclosing the scatterers whose force is wanted and no others.
+ *   out_host host [n_rhs][3], written.
+ * Errors as fmbem_cross_sections (radius > 0). */
+fmbem_status fmbem_force_stress(fmbem *h, const void *x_dev, int64_t n_rhs, const double *dir, const fmbem_c64 *pol,
+                                const double *center, double radius, int32_t n_theta, int32_t n_phi, double *out_host,
+                                void *stream);
+
+/* The stress force of fmbem_force_stress for one plane wave (dir, pol) [n_rhs = 1], and, for its
+ * adjoint gradient, the Wirtinger coefficients of its three components with respect to the
+ * fields at the sphere points,
+ *   cE[i][q][j] = w_q / 4 [delta_ij (conj(E_q) . n_q) + conj(E_q,i) n_q,j - n_q,i conj(E_q,j)]
+ *   (cH likewise with H), so that dF_i = 2 Re sum_q (cE[i][q] . dE_q + cH[i][q] . dH_q),
+ * mapped to the unknowns as in fmbem_near_field_functional: L[i] with F_i's first-order change
+ * 2 Re(L[i]^T dx).  All on the device.
+ *   force_host  host [3], written; pts_host host [P][3] (P = n_theta n_phi), written when not NULL;
+ *   cE_host, cH_host host [3][P][3] complex128, written when not NULL (for fmbem_shape_gradient_near);
+ *   L_dev       device [3][N][6] complex128 (user order), written.
+ * Errors as fmbem_force_stress. */
+fmbem_status fmbem_force_stress_functional(fmbem *h, const void *x_dev, const double *dir, const fmbem_c64 *pol,
+                                           const double *center, double radius, int32_t n_theta, int32_t n_phi,
+                                           double *force_host, double *pts_host, fmbem_c64 *cE_host,
+                                           fmbem_c64 *cH_host, void *L_dev, void *stream);
+
+/* s[r] = lambda_r^T (dA/deps_j) x_r (complex bilinear) for the operator of Eq. (2.9), which
+ * depends holomorphically on eps_j (through k_j = k0 sqrt(eps_j mu_j), T_j of Eq. 2.13 and the self
+ * blocks of Appendix B): the central difference (A(eps_j + step) - A(eps_j - step)) x / (2 step) of
+ * two FP64 products on handles the library builds from the same mesh, media and options (kept for
+ * the next call with the same j and step), then the bilinear reduction, on the device.  For an
+ * objective f = L^T x with A x = b (b independent of eps_j) and A^T lambda = L:
+ * df/deps_j = -s.  The paper has no adjoint; the adjoint gradients need it.
+ *   j        scatterer 1..J; step > 0 (e.g. 1e-5 max(1, |eps_j|)).
+ *   x_dev, lam_dev  device [n_rhs][N][6] complex128 (user order).
+ *   out_host host [n_rhs] complex128, written.
+ * Errors: FMBEM_ERR_INVALID_ARGUMENT (j, counts, NULL pointers, the impedance boundary or an
+ * fp32_only handle), FMBEM_ERR_CUDA, FMBEM_ERR_OOM. */
+fmbem_status fmbem_eps_sensitivity(fmbem *h, int32_t j, const void *x_dev, const void *lam_dev, int64_t n_rhs,
+                                   double step, fmbem_c64 *out_host, void *stream);
+
 /* sum_b w_b Im(Phi_b . conj(Psi_b)) per right-hand side (host [n_rhs], written): with
  * n x curl E = Psi the inward flux of the time-averaged Poynting vector, Eq. (4.2), gives the
  * absorption cross section C_abs = -(1/k0) times this sum. */

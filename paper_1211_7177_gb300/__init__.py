@@ -77,6 +77,10 @@ def load_library(build_if_missing: bool = True):
         "fmbem_num_nodes": (i64, [P]),
         "fmbem_num_near_singular_pairs": (i64, [P]),
         "fmbem_truncation": (i32, [P, P, P, P]),
+        "fmbem_cross_sections": (i32, [P, P, i64, P, P, i32, i32, P, P]),
+        "fmbem_force_stress": (i32, [P, P, i64, P, P, P, dbl, i32, i32, P, P]),
+        "fmbem_force_stress_functional": (i32, [P, P, P, P, P, dbl, i32, i32, P, P, P, P, P, P]),
+        "fmbem_eps_sensitivity": (i32, [P, i32, P, P, i64, dbl, P, P]),
         "fmbem_node_geometry": (i32, [P, P, P, P]),
         "fmbem_tree_info": (i32, [P, P, P, P, P, P]),
         "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
@@ -453,6 +457,7 @@ class FMBEM:
         # background wavenumber k0 sqrt(eps_0 mu_0) (real for the cross sections)
         self.kb = complex(k0 * np.sqrt(complex(eps[0]) * complex(mu[0])))
         self.eps0, self.mu0 = complex(eps[0]), complex(mu[0])
+        self._eps = [complex(v) for v in eps]
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -505,52 +510,78 @@ class FMBEM:
         if self.eps0 != 1 or self.mu0 != 1:
             raise ValueError("the optical force here assumes a vacuum background (eps_0 = mu_0 = 1)")
 
+    def _cross(self, x, dirs, pols, n_theta, n_phi, stream):
+        x = _dev(x, self.N, "x")
+        n = x.shape[0]
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dirs, dtype=np.float64), (n, 3)))
+        p = np.ascontiguousarray(np.broadcast_to(np.asarray(pols, dtype=np.complex128), (n, 3)))
+        out = np.empty((n, 6))
+        _check(self.h, load_library().fmbem_cross_sections(self.h, ctypes.c_void_p(x.data_ptr()), n, _ptr(d), _ptr(p),
+                                                           int(n_theta), int(n_phi), _ptr(out), _stream(stream)))
+        return out
+
     def force_farfield(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
         """Time-averaged force [n_rhs, 3] on all scatterers together in the unit plane waves
         (dirs[r], pols[r]) (vacuum background, eps_0 = mu_0 = c = 1): momentum balance in the far
-        zone, F = (C_ext d - int |F(u)|^2 u dOmega) / 2, with the far fields on the device."""
+        zone, F = (C_ext d - int |F(u)|^2 u dOmega) / 2 (fmbem_cross_sections, on the device)."""
         self._vacuum_background()
-        k0 = self.kb.real
-        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
-        pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
-        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
-        ph = 2 * np.pi * np.arange(n_phi) / n_phi
-        MU, PH = np.meshgrid(mu, ph, indexing="ij")
-        ST = np.sqrt(1 - MU ** 2)
-        rq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
-        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel()
-        F = fmbem_far_field(self.h, x, np.concatenate([dirs, rq]), stream)
-        nr = F.shape[0]
-        out = np.zeros((nr, 3))
-        for r in range(nr):
-            cext = 4 * np.pi / k0 * np.imag(np.vdot(pols[r], F[r, r]))
-            f2 = np.sum(np.abs(F[r, len(dirs):]) ** 2, axis=1)
-            out[r] = 0.5 * (cext * dirs[r] - np.sum((wq * f2)[:, None] * rq, axis=0))
-        return out
+        return self._cross(x, dirs, pols, n_theta, n_phi, stream)[:, 3:6].copy()
 
     def force_stress(self, x, dirs, pols, center, radius, n_theta=32, n_phi=64, stream=None):
         """Time-averaged force [n_rhs, 3] on the scatterers inside the sphere (center, radius) in
         the unit plane waves (dirs[r], pols[r]) (vacuum background): the Maxwell stress tensor
-        T = Re[E E* + H H* - (|E|^2 + |H|^2) I / 2] / 2 integrated over the sphere (Gauss-Legendre
-        in cos theta x trapezoid in phi), E and H evaluated on the device."""
+        integrated over the sphere (fmbem_force_stress: fields and reduction on the device)."""
         self._vacuum_background()
-        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
-        ph = 2 * np.pi * np.arange(n_phi) / n_phi
-        MU, PH = np.meshgrid(mu, ph, indexing="ij")
-        ST = np.sqrt(1 - MU ** 2)
-        nq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
-        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel() * radius ** 2
-        pts = np.asarray(center, dtype=np.float64)[None, :] + radius * nq
-        E, H = fmbem_near_field(self.h, x, pts, dirs, pols, stream, magnetic=True)
-        out = np.zeros((E.shape[0], 3))
-        for r in range(E.shape[0]):
-            e, hm = E[r], H[r]
-            en = np.sum(np.conj(e) * nq, axis=1)
-            hn = np.sum(np.conj(hm) * nq, axis=1)
-            u = np.sum(np.abs(e) ** 2 + np.abs(hm) ** 2, axis=1)
-            tn = 0.5 * np.real(e * en[:, None] + hm * hn[:, None] - 0.5 * u[:, None] * nq)
-            out[r] = np.sum(wq[:, None] * tn, axis=0)
+        x = _dev(x, self.N, "x")
+        n = x.shape[0]
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dirs, dtype=np.float64), (n, 3)))
+        p = np.ascontiguousarray(np.broadcast_to(np.asarray(pols, dtype=np.complex128), (n, 3)))
+        c = np.ascontiguousarray(center, dtype=np.float64)
+        out = np.empty((n, 3))
+        _check(self.h, load_library().fmbem_force_stress(self.h, ctypes.c_void_p(x.data_ptr()), n, _ptr(d), _ptr(p),
+                                                         _ptr(c), float(radius), int(n_theta), int(n_phi), _ptr(out),
+                                                         _stream(stream)))
         return out
+
+    def force_stress_functional(self, x, d, e, center, radius, n_theta=24, n_phi=48, stream=None):
+        """(force [3], pts [P, 3], cE [3, P, 3], cH [3, P, 3], L [3, N, 6] CUDA) of one plane wave
+        (fmbem_force_stress_functional): the stress force and the near-field functionals of its
+        components' Wirtinger coefficients, computed on the device."""
+        import torch
+        self._vacuum_background()
+        x = _dev(x, self.N, "x")
+        if x.shape[0] != 1:
+            raise ValueError("one right-hand side")
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.float64).reshape(3))
+        e = np.ascontiguousarray(np.asarray(e, dtype=np.complex128).reshape(3))
+        c = np.ascontiguousarray(center, dtype=np.float64)
+        P = int(n_theta) * int(n_phi)
+        force = np.empty(3)
+        pts = np.empty((P, 3))
+        cE = np.empty((3, P, 3), dtype=np.complex128)
+        cH = np.empty((3, P, 3), dtype=np.complex128)
+        L = torch.empty((3, self.N, 6), dtype=torch.complex128, device="cuda")
+        _check(self.h, load_library().fmbem_force_stress_functional(
+            self.h, ctypes.c_void_p(x.data_ptr()), _ptr(d), _ptr(e), _ptr(c), float(radius), int(n_theta), int(n_phi),
+            _ptr(force), _ptr(pts), _ptr(cE), _ptr(cH), ctypes.c_void_p(L.data_ptr()), _stream(stream)))
+        return force, pts, cE, cH, L
+
+    def eps_sensitivity(self, j, x, lam, step=None, stream=None):
+        """s [n_rhs] complex: lambda_r^T (dA/deps_j) x_r (fmbem_eps_sensitivity, on the device)."""
+        x = _dev(x, self.N, "x")
+        lam = _dev(lam, self.N, "lam")
+        if lam.shape[0] != x.shape[0]:
+            raise ValueError("x and lam need the same number of right-hand sides")
+        if step is None:
+            step = 1e-5 * max(1.0, abs(complex(self.eps_j(j))))
+        out = np.empty(x.shape[0], dtype=np.complex128)
+        _check(self.h, load_library().fmbem_eps_sensitivity(self.h, int(j), ctypes.c_void_p(x.data_ptr()),
+                                                            ctypes.c_void_p(lam.data_ptr()), x.shape[0], float(step),
+                                                            _ptr(out), _stream(stream)))
+        return out
+
+    def eps_j(self, j):
+        return self._eps[j]
 
     def dscs(self, x, rhat, pols=None, stream=None):
         """Differential scattering cross section dC_sca/dOmega = |F(rhat)|^2 / |e|^2 [n_rhs, n_dir]
@@ -587,26 +618,10 @@ class FMBEM:
 
     def cross_sections(self, x, dirs, pols, n_theta=48, n_phi=96, stream=None):
         """(C_ext, C_sca, C_abs) per right-hand side for the plane waves (dirs[r], pols[r]) that
-        produced the solutions x[r]: extinction by the optical theorem, scattering as the
-        Gauss-Legendre (cos theta) x trapezoid (phi) integral of |F|^2, absorption by Eq. (4.2);
-        the far fields and the absorption sums are evaluated on the device."""
-        if self.kb.imag != 0:
-            raise ValueError("cross sections need a lossless background")
-        k0 = self.kb.real
-        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
-        pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
-        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
-        ph = 2 * np.pi * np.arange(n_phi) / n_phi
-        MU, PH = np.meshgrid(mu, ph, indexing="ij")
-        ST = np.sqrt(1 - MU ** 2)
-        rq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
-        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel()
-        F = fmbem_far_field(self.h, x, np.concatenate([dirs, rq]), stream)
-        nr = F.shape[0]
-        cext = np.array([4 * np.pi / k0 * np.imag(np.vdot(pols[r], F[r, r])) for r in range(nr)])
-        csca = np.sum(wq[None, :] * np.sum(np.abs(F[:, len(dirs):]) ** 2, axis=2), axis=1)
-        cabs = -fmbem_absorption(self.h, x, stream) / k0
-        return cext, csca, cabs
+        produced the solutions x[r] (fmbem_cross_sections: far fields, quadrature and absorption
+        on the device)."""
+        out = self._cross(x, dirs, pols, n_theta, n_phi, stream)
+        return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy()
 
     def precond_apply(self, v, z=None, stream=None):
         return fmbem_precond_apply(self.h, v, z, stream)

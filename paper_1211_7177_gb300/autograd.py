@@ -74,10 +74,10 @@ class _Extinction(torch.autograd.Function):
             raise FMBEMError(st, "forward solve did not converge")
         coef = 4 * np.pi / g.kb.real * np.conj(pols)
         L = g.far_field_functional(dirs, coef)
-        cext = torch.sum(L * x, dim=(1, 2)).imag
+        cext = g.cross_sections(x, dirs, pols, n_theta=2, n_phi=2)[0]
         ctx.state = (g, x, L, coef, Vn, en, F, D, mu, k0, dirs, pols, options)
         ctx.devices = (V.device, eps.device)
-        return cext.to(device=V.device, dtype=torch.float64)
+        return torch.as_tensor(np.asarray(cext, dtype=np.float64), device=V.device)
 
     @staticmethod
     def backward(ctx, go):
@@ -100,13 +100,7 @@ class _Extinction(torch.autograd.Function):
             ge = np.zeros(len(en), dtype=np.complex128)
             ge[0] = complex(np.nan, np.nan)
             for j in range(1, len(en)):
-                h = 1e-5 * max(1.0, abs(en[j]))
-                ep, em = list(en), list(en)
-                ep[j] += h
-                em[j] -= h
-                dAx = (FMBEM(Vn, F, D, ep, mu, k0, **options).matvec(x) -
-                       FMBEM(Vn, F, D, em, mu, k0, **options).matvec(x)) / (2 * h)
-                df = -torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()  # d f / d eps_j (holomorphic)
+                df = -g.eps_sensitivity(j, x, lam)  # d f / d eps_j (holomorphic), fmbem_eps_sensitivity
                 # C = Im f: dC/dRe = Im df, dC/dIm = Re df; the complex gradient is dRe + i dIm
                 ge[j] = np.sum(w * (df.imag + 1j * df.real))
             geps = torch.from_numpy(ge).to(ctx.devices[1])
@@ -161,14 +155,9 @@ class _Force(torch.autograd.Function):
         if ctx.needs_input_grad[1]:
             ge = np.zeros(len(en), dtype=np.complex128)
             ge[0] = complex(np.nan, np.nan)  # eps_0 held fixed (see _Extinction.backward)
+            x3 = x.expand(3, -1, -1).contiguous()
             for j in range(1, len(en)):
-                h = 1e-5 * max(1.0, abs(en[j]))
-                ep, em = list(en), list(en)
-                ep[j] += h
-                em[j] -= h
-                dAx = (FMBEM(Vn, F, D, ep, mu, k0, **options).matvec(x) -
-                       FMBEM(Vn, F, D, em, mu, k0, **options).matvec(x)) / (2 * h)
-                sv = torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()  # s_i = lambda_i^T (dA/deps_j) x
+                sv = g.eps_sensitivity(j, x3, lam)  # s_i = lambda_i^T (dA/deps_j) x, fmbem_eps_sensitivity
                 ge[j] = np.sum(w * (-2 * sv.real + 1j * 2 * sv.imag))  # dF_i/dRe + i dF_i/dIm
             geps = torch.from_numpy(ge).to(ctx.devices[1])
         return gV, geps, None, None, None, None, None, None, None, None, None, None, None

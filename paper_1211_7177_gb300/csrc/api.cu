@@ -169,6 +169,11 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
             h->k[d] = k0 * root_with_nonneg_imag(h->eps[d] * h->mu[d]);
             h->gam[d] = d == 0 ? c64{1.0, 0.0} : cdiv(h->mu[d], h->mu[0]);
         }
+        h->mesh_V.assign(mesh->vertices, mesh->vertices + 3 * mesh->n_vertices);
+        h->mesh_F.assign(mesh->triangles, mesh->triangles + 3 * mesh->n_triangles);
+        h->mesh_D.assign(mesh->tri_domain, mesh->tri_domain + mesh->n_triangles);
+        h->eps_user = h->eps;
+        h->mu_user = h->mu;
         h->ibc = o.boundary == FMBEM_BOUNDARY_IMPEDANCE;
         h->Jf = h->ibc ? 0 : h->J;
         if (h->ibc) {
@@ -221,6 +226,8 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
 void fmbem_destroy(fmbem *h) {
     if (!h) return;
     cudaDeviceSynchronize();
+    if (h->eps_plus) fmbem_destroy(h->eps_plus);
+    if (h->eps_minus) fmbem_destroy(h->eps_minus);
     free_all(h);
     delete h;
 }
@@ -365,6 +372,67 @@ fmbem_status fmbem_near_field(fmbem *h, const void *x_dev, int64_t n_rhs, int64_
     return guarded(h, [&] {
         run_near_field(h, (const c64 *)x_dev, n_rhs, n_pts, pts, dir, (const c64 *)pol, (c64 *)E_host, (c64 *)H_host,
                        (cudaStream_t)stream);
+    });
+}
+
+fmbem_status fmbem_cross_sections(fmbem *h, const void *x_dev, int64_t n_rhs, const double *dir, const fmbem_c64 *pol,
+                                  int32_t n_theta, int32_t n_phi, double *out_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_rhs > 65535 || !x_dev || !dir || !pol || !out_host || n_theta < 2 || n_phi < 2 ||
+        (int64_t)n_theta * n_phi > (1 << 22)) {
+        h->err = "invalid argument (n_rhs in 1..65535, non-NULL x, dir, pol, out; n_theta, n_phi >= 2)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_cross_sections(h, (const c64 *)x_dev, n_rhs, dir, (const c64 *)pol, n_theta, n_phi, out_host,
+                           (cudaStream_t)stream);
+    });
+}
+
+fmbem_status fmbem_force_stress(fmbem *h, const void *x_dev, int64_t n_rhs, const double *dir, const fmbem_c64 *pol,
+                                const double *center, double radius, int32_t n_theta, int32_t n_phi, double *out_host,
+                                void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || n_rhs > 65535 || !x_dev || !dir || !pol || !center || !out_host || !(radius > 0) ||
+        n_theta < 2 || n_phi < 2 || (int64_t)n_theta * n_phi > (1 << 22)) {
+        h->err = "invalid argument (n_rhs in 1..65535, non-NULL x, dir, pol, center, out; radius > 0; n_theta, n_phi >= 2)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_force_stress(h, (const c64 *)x_dev, n_rhs, dir, (const c64 *)pol, center, radius, n_theta, n_phi,
+                         out_host, (cudaStream_t)stream);
+    });
+}
+
+fmbem_status fmbem_force_stress_functional(fmbem *h, const void *x_dev, const double *dir, const fmbem_c64 *pol,
+                                           const double *center, double radius, int32_t n_theta, int32_t n_phi,
+                                           double *force_host, double *pts_host, fmbem_c64 *cE_host,
+                                           fmbem_c64 *cH_host, void *L_dev, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (!x_dev || !dir || !pol || !center || !force_host || !L_dev || !(radius > 0) || n_theta < 2 || n_phi < 2 ||
+        (int64_t)n_theta * n_phi > (1 << 22)) {
+        h->err = "invalid argument (non-NULL x, dir, pol, center, force, L; radius > 0; n_theta, n_phi >= 2)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_force_stress_functional(h, (const c64 *)x_dev, dir, (const c64 *)pol, center, radius, n_theta, n_phi,
+                                    force_host, pts_host, (c64 *)cE_host, (c64 *)cH_host, (c64 *)L_dev,
+                                    (cudaStream_t)stream);
+    });
+}
+
+fmbem_status fmbem_eps_sensitivity(fmbem *h, int32_t j, const void *x_dev, const void *lam_dev, int64_t n_rhs,
+                                   double step, fmbem_c64 *out_host, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (j < 1 || j > h->J || !x_dev || !lam_dev || !out_host || n_rhs < 1 || n_rhs > 65535 || !(step > 0) || h->ibc ||
+        h->opt.fp32_only) {
+        h->err = "invalid argument (j in 1..J, non-NULL x, lambda, out; n_rhs in 1..65535; step > 0; penetrable "
+                 "boundary; FP64 tables)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_eps_sensitivity(h, j, (const c64 *)x_dev, (const c64 *)lam_dev, n_rhs, step, (c64 *)out_host,
+                            (cudaStream_t)stream);
     });
 }
 

@@ -92,6 +92,14 @@ struct fmbem {
     std::vector<c64> zeta;  // [J+1], entry 0 unused
     c64 *d_zeta = nullptr;  // device copy
     int p = 0, p2 = 0;                 // truncation number and p^2 coefficients
+    // a copy of the mesh and media as given, for the operators with a perturbed permittivity
+    // (fmbem_eps_sensitivity), and those operators once built
+    std::vector<double> mesh_V;
+    std::vector<int32_t> mesh_F, mesh_D;
+    std::vector<c64> eps_user, mu_user;
+    fmbem *eps_plus = nullptr, *eps_minus = nullptr;
+    int eps_j = -1;
+    double eps_step = 0;
     std::vector<int> p_level;          // option fmm_tol: the truncation each level needs [lmax+1]
     std::vector<double> trunc_err;     // and the sampled error estimate at the p used
 
@@ -320,6 +328,16 @@ void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, 
 void near_work_items(fmbem *h, cudaStream_t s);
 void build_near_cache(fmbem *h, cudaStream_t s);
 void choose_truncation(fmbem *h, cudaStream_t s);
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
+void run_cross_sections(fmbem *h, const c64 *x, int64_t nr, const double *dir_host, const c64 *pol_host, int nt, int np,
+                        double *out_host, cudaStream_t s);
+void run_force_stress_functional(fmbem *h, const c64 *x, const double *dir_host, const c64 *pol_host,
+                                 const double *center, double radius, int nt, int np, double *force_host,
+                                 double *pts_host, c64 *cE_host, c64 *cH_host, c64 *L, cudaStream_t s);
+void run_eps_sensitivity(fmbem *h, int j, const c64 *x, const c64 *lam, int64_t nr, double step, c64 *out_host,
+                         cudaStream_t s);
+void run_force_stress(fmbem *h, const c64 *x, int64_t nr, const double *dir_host, const c64 *pol_host,
+                      const double *center, double radius, int nt, int np, double *out_host, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // one persistent launch over many problems (batch.cu, kernel in fmm.cu)

@@ -452,6 +452,119 @@ __global__ void __launch_bounds__(OB_NT) k_near_field_functional(int64_t N, cons
     }
 }
 
+// Cross sections and the far-zone force of every right-hand side from its far field F[r][dir][3]
+// on directions (d_0 .. d_{nr-1}, q_0 .. q_{nq-1}): the forward direction d_r of its own plane wave
+// and the quadrature directions q with weights wq (Gauss-Legendre in cos theta x trapezoid in
+// phi).  out[r] = (C_ext, C_sca, Fx, Fy, Fz):
+//   C_ext = (4 pi / k0) Im[conj(e_r) . F_r(d_r)] (optical theorem), C_sca = sum_q wq |F_r(q)|^2,
+//   F = (C_ext d_r - sum_q wq |F_r(q)|^2 q) / 2 (momentum balance in the far zone, vacuum units).
+__global__ void __launch_bounds__(OB_TB) k_far_reduce(int64_t nr, int64_t nq, const c64 *F, const double *dirs,
+                                                    const c64 *pol, const double *wq, double k0, double *out) {
+    __shared__ double red[4][OB_TB];
+    const int64_t r = blockIdx.x, ndir = nr + nq;
+    double a[4] = {0, 0, 0, 0};
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        const c64 *f = F + ((r * ndir) + nr + q) * 3;
+        const double f2 = abs2(f[0]) + abs2(f[1]) + abs2(f[2]);
+        const double *u = dirs + 3 * (nr + q);
+        a[0] += wq[q] * f2;
+        for (int c = 0; c < 3; ++c) a[1 + c] += wq[q] * f2 * u[c];
+    }
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int off = OB_TB / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const c64 *fd = F + (r * ndir + r) * 3;
+        double im = 0;
+        for (int c = 0; c < 3; ++c) im += (conjg(pol[3 * r + c]) * fd[c]).im;
+        const double cext = 4 * FMBEM_PI / k0 * im;
+        double *o = out + 5 * r;
+        o[0] = cext;
+        o[1] = red[0][0];
+        for (int c = 0; c < 3; ++c) o[2 + c] = 0.5 * (cext * dirs[3 * r + c] - red[1 + c][0]);
+    }
+}
+
+// Time-averaged Maxwell-stress force on the surface points p_q = c + R n_q with weights wq
+// (R^2 included): F = sum_q wq T n_q, T n = Re[E (E*.n) + H (H*.n) - (|E|^2 + |H|^2) n / 2] / 2
+// (vacuum units), E and H the total fields E[r][q][3], H[r][q][3].  out[r][3].
+__global__ void __launch_bounds__(OB_TB) k_stress_reduce(int64_t nq, const c64 *E, const c64 *H, const double *nq_dir,
+                                                       const double *wq, double *out) {
+    __shared__ double red[3][OB_TB];
+    const int64_t r = blockIdx.x;
+    double a[3] = {0, 0, 0};
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        const c64 *e = E + (r * nq + q) * 3, *hh = H + (r * nq + q) * 3;
+        const double *n = nq_dir + 3 * q;
+        c64 en = {0, 0}, hn = {0, 0};
+        for (int c = 0; c < 3; ++c) {
+            en += n[c] * conjg(e[c]);
+            hn += n[c] * conjg(hh[c]);
+        }
+        const double u = abs2(e[0]) + abs2(e[1]) + abs2(e[2]) + abs2(hh[0]) + abs2(hh[1]) + abs2(hh[2]);
+        for (int c = 0; c < 3; ++c) a[c] += wq[q] * 0.5 * ((e[c] * en).re + (hh[c] * hn).re - 0.5 * u * n[c]);
+    }
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int off = OB_TB / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) out[3 * r + c] = red[c][0];
+}
+
+// Wirtinger coefficients of the stress force's components with respect to the fields at the
+// sphere points (see fmbem_force_stress_functional): for component i, point q and field index j,
+//   c[i][q][j] = w_q / 4 [delta_ij (conj(F_q) . n_q) + conj(F_q,i) n_q,j - n_q,i conj(F_q,j)],
+// F = E (cE) or H (cH); one thread per (i, q, j).
+__global__ void k_stress_wirtinger(int64_t nq, const c64 *E, const c64 *H, const double *nq_dir, const double *wq,
+                                   c64 *cE, c64 *cH) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= 9 * nq) return;
+    const int i = (int)(idx / (3 * nq)), j = (int)(idx % 3);
+    const int64_t q = (idx / 3) % nq;
+    const double *n = nq_dir + 3 * q;
+    for (int f = 0; f < 2; ++f) {
+        const c64 *F = (f == 0 ? E : H) + 3 * q;
+        c64 fn = {0, 0};
+        for (int c = 0; c < 3; ++c) fn += n[c] * conjg(F[c]);
+        c64 v = n[j] * conjg(F[i]) - n[i] * conjg(F[j]);
+        if (i == j) v += fn;
+        (f == 0 ? cE : cH)[idx] = (0.25 * wq[q]) * v;
+    }
+}
+
+// y = (a - b) * s elementwise over n complex values (central difference of two products)
+__global__ void k_cdiff(int64_t n, const c64 *a, const c64 *b, double s, c64 *y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = s * (a[i] - b[i]);
+}
+
+// out[r] = sum_k lam[r][k] y[r][k] (bilinear), one block per right-hand side
+__global__ void __launch_bounds__(OB_TB) k_bilinear(int64_t n, const c64 *lam, const c64 *y, c64 *out) {
+    __shared__ double red[2][OB_TB];
+    const int64_t r = blockIdx.x;
+    c64 acc = {0, 0};
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) cfma(acc, lam[r * n + k], y[r * n + k]);
+    red[0][threadIdx.x] = acc.re;
+    red[1][threadIdx.x] = acc.im;
+    __syncthreads();
+    for (int off = OB_TB / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + off];
+            red[1][threadIdx.x] += red[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = c64{red[0][0], red[1][0]};
+}
+
 }  // namespace
 
 void run_near_field_functional(fmbem *h, int64_t nf, int64_t n_pts, const double *pts_host, const c64 *cE_host,
@@ -675,4 +788,230 @@ void run_absorption(fmbem *h, const c64 *x, int64_t nr, double *out_host, cudaSt
         throw;
     }
     dev_free(h, d);
+}
+
+// unit directions and weights of the Gauss-Legendre (cos theta) x trapezoid (phi) rule on the sphere
+static void sphere_rule(int nt, int np, std::vector<double> &dirs, std::vector<double> &w) {
+    std::vector<double> x, gw;
+    gauss_legendre(nt, x, gw);
+    dirs.resize(3 * (size_t)nt * np);
+    w.resize((size_t)nt * np);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < np; ++j) {
+            const double ct = x[i], st = std::sqrt(std::max(0.0, 1 - ct * ct)), ph = 2 * FMBEM_PI * j / np;
+            const size_t q = (size_t)i * np + j;
+            dirs[3 * q] = st * std::cos(ph);
+            dirs[3 * q + 1] = st * std::sin(ph);
+            dirs[3 * q + 2] = ct;
+            w[q] = gw[i] * 2 * FMBEM_PI / np;
+        }
+}
+
+// C_ext, C_sca, C_abs and the far-zone force of the plane waves (dir, pol) that produced x
+// (see fmbem_cross_sections); out_host [nr][6] = (C_ext, C_sca, C_abs, Fx, Fy, Fz)
+void run_cross_sections(fmbem *h, const c64 *x, int64_t nr, const double *dir_host, const c64 *pol_host, int nt, int np,
+                        double *out_host, cudaStream_t s) {
+    if (h->k[0].im != 0.0 || !(h->k[0].re > 0))
+        throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "cross sections need a lossless background"};
+    std::vector<double> q, wq;
+    sphere_rule(nt, np, q, wq);
+    const int64_t nq = (int64_t)wq.size(), ndir = nr + nq;
+    std::vector<double> dirs(3 * ndir);
+    std::copy(dir_host, dir_host + 3 * nr, dirs.begin());
+    std::copy(q.begin(), q.end(), dirs.begin() + 3 * nr);
+    double *dd = (double *)dev_alloc(h, sizeof(double) * 3 * ndir);
+    double *dw = (double *)dev_alloc(h, sizeof(double) * nq);
+    c64 *dp = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
+    c64 *dF = (c64 *)dev_alloc(h, sizeof(c64) * 3 * ndir * nr);
+    double *dout = (double *)dev_alloc(h, sizeof(double) * 5 * nr);
+    double *dabs = (double *)dev_alloc(h, sizeof(double) * nr);
+    auto cleanup = [&] {
+        for (void *p : {(void *)dd, (void *)dw, (void *)dp, (void *)dF, (void *)dout, (void *)dabs}) dev_free(h, p);
+    };
+    try {
+        CK(cudaMemcpyAsync(dd, dirs.data(), sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dw, wq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dp, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        k_far_field<<<dim3((unsigned)ndir, (unsigned)nr), OB_TB, 0, s>>>(h->N, h->upos, h->unrm, h->uw, x, dd, h->k[0],
+                                                                        ndir, dF);
+        CKL("k_far_field");
+        k_far_reduce<<<(unsigned)nr, OB_TB, 0, s>>>(nr, nq, dF, dd, dp, dw, h->k[0].re, dout);
+        CKL("k_far_reduce");
+        k_absorption<<<(unsigned)nr, OB_TB, 0, s>>>(h->N, h->uw, x, dabs);
+        CKL("k_absorption");
+        std::vector<double> o(5 * nr), a(nr);
+        CK(cudaMemcpyAsync(o.data(), dout, sizeof(double) * 5 * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(a.data(), dabs, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int64_t r = 0; r < nr; ++r) {
+            double *row = out_host + 6 * r;
+            row[0] = o[5 * r];
+            row[1] = o[5 * r + 1];
+            row[2] = -a[r] / h->k[0].re;  // Eq. (4.2): C_abs = -(1/k0) sum w Im(Phi . conj(Psi))
+            for (int c = 0; c < 3; ++c) row[3 + c] = o[5 * r + 2 + c];
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+// Maxwell-stress force on the scatterers inside the sphere (center, radius) in the plane waves
+// (dir, pol): total E and H on the sphere's quadrature points by direct summation, then the
+// stress-tensor reduction (see fmbem_force_stress); out_host [nr][3]
+void run_force_stress(fmbem *h, const c64 *x, int64_t nr, const double *dir_host, const c64 *pol_host,
+                      const double *center, double radius, int nt, int np, double *out_host, cudaStream_t s) {
+    std::vector<double> q, wq;
+    sphere_rule(nt, np, q, wq);
+    const int64_t nq = (int64_t)wq.size();
+    std::vector<double> pts(3 * nq);
+    for (int64_t i = 0; i < nq; ++i) {
+        for (int c = 0; c < 3; ++c) pts[3 * i + c] = center[c] + radius * q[3 * i + c];
+        wq[i] *= radius * radius;
+    }
+    double *dpts = (double *)dev_alloc(h, sizeof(double) * 3 * nq);
+    double *dq = (double *)dev_alloc(h, sizeof(double) * 3 * nq);
+    double *dw = (double *)dev_alloc(h, sizeof(double) * nq);
+    double *ddir = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
+    c64 *dpol = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nr);
+    c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nq * nr);
+    c64 *dH = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nq * nr);
+    double *dout = (double *)dev_alloc(h, sizeof(double) * 3 * nr);
+    auto cleanup = [&] {
+        for (void *p : {(void *)dpts, (void *)dq, (void *)dw, (void *)ddir, (void *)dpol, (void *)dE, (void *)dH,
+                        (void *)dout})
+            dev_free(h, p);
+    };
+    try {
+        CK(cudaMemcpyAsync(dpts, pts.data(), sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dq, q.data(), sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dw, wq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ddir, dir_host, sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dpol, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
+        const dim3 grid((unsigned)((nq + OB_NT - 1) / OB_NT), (unsigned)nr);
+        const c64 iwmu = c64{0, h->k0} * h->mu[0];
+        k_near_field<true><<<grid, OB_NT, 0, s>>>(h->N, h->upos, h->unrm, h->uw, x, nq, dpts, h->k[0], iwmu, ddir, dpol,
+                                                  dE, dH);
+        CKL("k_near_field");
+        k_stress_reduce<<<(unsigned)nr, OB_TB, 0, s>>>(nq, dE, dH, dq, dw, dout);
+        CKL("k_stress_reduce");
+        CK(cudaMemcpyAsync(out_host, dout, sizeof(double) * 3 * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+// the stress force of one plane wave and, on the device, the near-field functionals of its three
+// components' Wirtinger coefficients (see fmbem_force_stress_functional)
+void run_force_stress_functional(fmbem *h, const c64 *x, const double *dir_host, const c64 *pol_host,
+                                 const double *center, double radius, int nt, int np, double *force_host,
+                                 double *pts_host, c64 *cE_host, c64 *cH_host, c64 *L, cudaStream_t s) {
+    std::vector<double> q, wq;
+    sphere_rule(nt, np, q, wq);
+    const int64_t nq = (int64_t)wq.size();
+    std::vector<double> pts(3 * nq);
+    for (int64_t i = 0; i < nq; ++i) {
+        for (int c = 0; c < 3; ++c) pts[3 * i + c] = center[c] + radius * q[3 * i + c];
+        wq[i] *= radius * radius;
+    }
+    double *dpts = (double *)dev_alloc(h, sizeof(double) * 3 * nq);
+    double *dq = (double *)dev_alloc(h, sizeof(double) * 3 * nq);
+    double *dw = (double *)dev_alloc(h, sizeof(double) * nq);
+    double *ddir = (double *)dev_alloc(h, sizeof(double) * 3);
+    c64 *dpol = (c64 *)dev_alloc(h, sizeof(c64) * 3);
+    c64 *dE = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nq);
+    c64 *dH = (c64 *)dev_alloc(h, sizeof(c64) * 3 * nq);
+    c64 *dcE = (c64 *)dev_alloc(h, sizeof(c64) * 9 * nq);
+    c64 *dcH = (c64 *)dev_alloc(h, sizeof(c64) * 9 * nq);
+    double *dout = (double *)dev_alloc(h, sizeof(double) * 3);
+    auto cleanup = [&] {
+        for (void *p : {(void *)dpts, (void *)dq, (void *)dw, (void *)ddir, (void *)dpol, (void *)dE, (void *)dH,
+                        (void *)dcE, (void *)dcH, (void *)dout})
+            dev_free(h, p);
+    };
+    try {
+        CK(cudaMemcpyAsync(dpts, pts.data(), sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dq, q.data(), sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dw, wq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ddir, dir_host, sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dpol, pol_host, sizeof(c64) * 3, cudaMemcpyHostToDevice, s));
+        const c64 iwmu = c64{0, h->k0} * h->mu[0];
+        k_near_field<true><<<dim3((unsigned)((nq + OB_NT - 1) / OB_NT), 1), OB_NT, 0, s>>>(
+            h->N, h->upos, h->unrm, h->uw, x, nq, dpts, h->k[0], iwmu, ddir, dpol, dE, dH);
+        CKL("k_near_field");
+        k_stress_reduce<<<1, OB_TB, 0, s>>>(nq, dE, dH, dq, dw, dout);
+        CKL("k_stress_reduce");
+        k_stress_wirtinger<<<(unsigned)((9 * nq + 255) / 256), 256, 0, s>>>(nq, dE, dH, dq, dw, dcE, dcH);
+        CKL("k_stress_wirtinger");
+        // the scattered-field functional of the three components (the incident wave does not
+        // depend on the solution)
+        k_near_field_functional<true><<<dim3((unsigned)((h->N + OB_NT - 1) / OB_NT), 3), OB_NT, 0, s>>>(
+            h->N, h->upos, h->unrm, h->uw, nq, dpts, dcE, dcH, h->k[0], iwmu, L);
+        CKL("k_near_field_functional");
+        CK(cudaMemcpyAsync(force_host, dout, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+        if (cE_host) CK(cudaMemcpyAsync(cE_host, dcE, sizeof(c64) * 9 * nq, cudaMemcpyDeviceToHost, s));
+        if (cH_host) CK(cudaMemcpyAsync(cH_host, dcH, sizeof(c64) * 9 * nq, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (pts_host) std::copy(pts.begin(), pts.end(), pts_host);
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+// s[r] = lam_r^T (dA/deps_j) x_r with dA/deps_j the central difference of the operators with
+// eps_j +- step (handles built once per (j, step) and kept, same mesh and options)
+void run_eps_sensitivity(fmbem *h, int j, const c64 *x, const c64 *lam, int64_t nr, double step, c64 *out_host,
+                         cudaStream_t s) {
+    if (h->mesh_V.empty()) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "the handle keeps no mesh copy"};
+    if (h->eps_j != j || h->eps_step != step || !h->eps_plus || !h->eps_minus) {
+        if (h->eps_plus) fmbem_destroy(h->eps_plus);
+        if (h->eps_minus) fmbem_destroy(h->eps_minus);
+        h->eps_plus = h->eps_minus = nullptr;
+        const fmbem_mesh m{(int64_t)h->mesh_V.size() / 3, h->mesh_V.data(), (int64_t)h->mesh_F.size() / 3,
+                           h->mesh_F.data(), h->mesh_D.data(), (int32_t)h->J};
+        std::vector<fmbem_c64> ep(h->J + 1), em(h->J + 1), mu(h->J + 1);
+        for (int d = 0; d <= h->J; ++d) {
+            ep[d] = em[d] = fmbem_c64{h->eps_user[d].re, h->eps_user[d].im};
+            mu[d] = fmbem_c64{h->mu_user[d].re, h->mu_user[d].im};
+        }
+        ep[j].re += step;
+        em[j].re -= step;
+        fmbem_options o = h->opt;
+        o.near_cache = 0;
+        o.profile_phases = 0;
+        fmbem_status st = fmbem_create(&m, ep.data(), mu.data(), h->k0, &o, s, &h->eps_plus);
+        if (st == FMBEM_OK) st = fmbem_create(&m, em.data(), mu.data(), h->k0, &o, s, &h->eps_minus);
+        if (st != FMBEM_OK) throw fmbem_error{st, std::string("perturbed operator: ") + fmbem_last_error(nullptr)};
+        h->eps_j = j;
+        h->eps_step = step;
+    }
+    const int64_t n = 6 * h->N;
+    c64 *yp = (c64 *)dev_alloc(h, sizeof(c64) * n * nr);
+    c64 *ym = (c64 *)dev_alloc(h, sizeof(c64) * n * nr);
+    c64 *dout = (c64 *)dev_alloc(h, sizeof(c64) * nr);
+    auto cleanup = [&] {
+        dev_free(h, yp);
+        dev_free(h, ym);
+        dev_free(h, dout);
+    };
+    try {
+        run_matvec(h->eps_plus, x, yp, nr, FMBEM_FP64, s);
+        run_matvec(h->eps_minus, x, ym, nr, FMBEM_FP64, s);
+        k_cdiff<<<(unsigned)((n * nr + 255) / 256), 256, 0, s>>>(n * nr, yp, ym, 0.5 / step, yp);
+        CKL("k_cdiff");
+        k_bilinear<<<(unsigned)nr, OB_TB, 0, s>>>(n, lam, yp, dout);
+        CKL("k_bilinear");
+        CK(cudaMemcpyAsync(out_host, dout, sizeof(c64) * nr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
 }

@@ -29,6 +29,8 @@ constexpr int PMAX = 20;  // largest supported truncation number
 
 inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
+}  // namespace
+
 // Gauss-Legendre nodes and weights on [-1,1] (Newton iteration on P_n)
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
     x.resize(n);
@@ -51,6 +53,8 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
         w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
 }
+
+namespace {
 
 __global__ void k_to32(const c64 *a, c32 *b, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

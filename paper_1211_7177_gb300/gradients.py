@@ -10,12 +10,13 @@ method gives for any parameter p of A
 
 so one forward solve and one adjoint solve serve every parameter.  A depends holomorphically on
 eps_j (through k_j = k0 sqrt(eps_j mu_j), the jump T_j and the self blocks of Appendix B), so
-(dA/deps_j) x is the complex derivative, taken here as the central difference of two FMM products
-on handles with eps_j +- h (same mesh and tree); then
+(dA/deps_j) x is the complex derivative, taken by the library as the central difference of two FMM
+products on operators with eps_j +- h (same mesh and tree, fmbem_eps_sensitivity); then
 
     dC/dRe(eps_j) = Im(df/deps_j),   dC/dIm(eps_j) = Re(df/deps_j).
 
-Every solve, product and far-field evaluation runs in the library's CUDA kernels.
+Every solve, product, functional, reduction and far-field evaluation runs in the library's CUDA
+kernels; this module only sequences the calls.
 """
 from __future__ import annotations
 
@@ -25,23 +26,17 @@ from . import FMBEM, FMBEMError
 
 
 def extinction(handle, x, dirs, pols):
-    """C_ext [n_rhs] of the solutions x [n_rhs, N, 6] (CUDA) of the plane waves (dirs, pols)."""
-    import torch
-    k0 = handle.kb
-    if k0.imag != 0:
-        raise ValueError("the extinction cross section needs a lossless background")
-    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
-    pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
-    L = handle.far_field_functional(dirs, 4 * np.pi / k0.real * np.conj(pols))
-    return torch.sum(L * x, dim=(1, 2)).imag.cpu().numpy()
+    """C_ext [n_rhs] of the solutions x [n_rhs, N, 6] (CUDA) of the plane waves (dirs, pols), by
+    the optical theorem on the device (fmbem_cross_sections)."""
+    return handle.cross_sections(x, dirs, pols, n_theta=2, n_phi=2)[0]
 
 
 def extinction_eps_gradient(V, F, D, eps, mu, k0, dirs, pols, j, tol=1e-10, h=None, **options):
     """(C_ext, dC_ext/dRe(eps_j), dC_ext/dIm(eps_j)), each [n_rhs], for the plane waves
     (dirs[r], pols[r]) on the mesh (V, F, D) with permittivities eps and permeabilities mu
-    (index 0 the background), by one forward and one adjoint GMRES solve to tol.  h is the
-    step of the operator's central difference in eps_j (default 1e-5 max(1, |eps_j|))."""
-    import torch
+    (index 0 the background), by one forward and one adjoint GMRES solve to tol and the library's
+    sensitivity lambda^T (dA/deps_j) x (fmbem_eps_sensitivity; h is its central-difference step,
+    default 1e-5 max(1, |eps_j|))."""
     eps = [complex(e) for e in eps]
     if not 1 <= j < len(eps):
         raise ValueError("j must index a scatterer (1..J)")
@@ -52,18 +47,11 @@ def extinction_eps_gradient(V, F, D, eps, mu, k0, dirs, pols, j, tol=1e-10, h=No
     if st != 0:
         raise FMBEMError(st, "forward solve did not converge")
     L = g.far_field_functional(dirs, 4 * np.pi / g.kb.real * np.conj(pols))
-    cext = torch.sum(L * x, dim=(1, 2)).imag.cpu().numpy()
+    cext = extinction(g, x, dirs, pols)
     lam, _, _, st = g.adjoint_solve(L, tol=tol)
     if st != 0:
         raise FMBEMError(st, "adjoint solve did not converge")
-    step = h if h is not None else 1e-5 * max(1.0, abs(eps[j]))
-    ep, em = list(eps), list(eps)
-    ep[j] += step
-    em[j] -= step
-    gp = FMBEM(V, F, D, ep, mu, k0, **options)
-    gm = FMBEM(V, F, D, em, mu, k0, **options)
-    dAx = (gp.matvec(x) - gm.matvec(x)) / (2 * step)
-    df = -torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()
+    df = -g.eps_sensitivity(j, x, lam, step=h)  # d f / d eps_j (holomorphic)
     return cext, df.imag, df.real
 
 
@@ -72,7 +60,6 @@ def extinction_vertex_gradient(V, F, D, eps, mu, k0, dirs, pols, tol=1e-10, **op
     (V, F, D) (vertex nodes): one forward and one adjoint GMRES solve through the FMM, then the
     vertex derivative of L^T x + lambda^T b - lambda^T A x at fixed x and lambda
     (fmbem_shape_gradient), whose imaginary part is the extinction's."""
-    import torch
     g = FMBEM(V, F, D, eps, mu, k0, **options)
     dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
     pols = np.atleast_2d(np.asarray(pols, dtype=np.complex128))
@@ -81,7 +68,7 @@ def extinction_vertex_gradient(V, F, D, eps, mu, k0, dirs, pols, tol=1e-10, **op
         raise FMBEMError(st, "forward solve did not converge")
     coef = 4 * np.pi / g.kb.real * np.conj(pols)
     L = g.far_field_functional(dirs, coef)
-    cext = torch.sum(L * x, dim=(1, 2)).imag.cpu().numpy()
+    cext = extinction(g, x, dirs, pols)
     lam, _, _, st = g.adjoint_solve(L, tol=tol)
     if st != 0:
         raise FMBEMError(st, "adjoint solve did not converge")
@@ -89,38 +76,15 @@ def extinction_vertex_gradient(V, F, D, eps, mu, k0, dirs, pols, tol=1e-10, **op
     return cext, grad.imag
 
 
-def _sphere_points(center, radius, n_theta, n_phi):
-    mu, wmu = np.polynomial.legendre.leggauss(n_theta)
-    ph = 2 * np.pi * np.arange(n_phi) / n_phi
-    MU, PH = np.meshgrid(mu, ph, indexing="ij")
-    ST = np.sqrt(1 - MU ** 2)
-    nq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
-    wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel() * radius ** 2
-    return np.asarray(center, dtype=np.float64)[None, :] + radius * nq, nq, wq
-
-
 def _force_adjoint(g, d, e, center, radius, n_theta, n_phi, tol):
     """Forward solve, the Maxwell-stress force on the sphere (center, radius), the Wirtinger
-    coefficients cE, cH [3, P, 3] of its components and their adjoints lambda [3, N, 6]."""
+    coefficients cE, cH [3, P, 3] of its components at the sphere points pts, their near-field
+    functionals L [3, N, 6] (all from fmbem_force_stress_functional) and the adjoints lambda."""
     g._vacuum_background()
     x, _, _, st = g.solve(g.plane_wave_rhs(d, e), tol=tol)
     if st != 0:
         raise FMBEMError(st, "forward solve did not converge")
-    pts, nq, wq = _sphere_points(center, radius, n_theta, n_phi)
-    E, H = g.near_field(x, pts, d, e, magnetic=True)
-    E, H = E[0], H[0]
-    en, hn = np.sum(np.conj(E) * nq, 1), np.sum(np.conj(H) * nq, 1)
-    u = np.sum(np.abs(E) ** 2 + np.abs(H) ** 2, 1)
-    force = np.sum(wq[:, None] * 0.5 * np.real(E * en[:, None] + H * hn[:, None] - 0.5 * u[:, None] * nq), 0)
-    eye = np.eye(3)
-
-    def wirtinger(Fv, fn):  # [3 (component i), P, 3 (field index j)]
-        c = (eye[:, None, :] * fn[None, :, None] + np.conj(Fv).T[:, :, None] * nq[None, :, :]
-             - nq.T[:, :, None] * np.conj(Fv)[None, :, :])
-        return 0.25 * wq[None, :, None] * c
-
-    cE, cH = wirtinger(E, en), wirtinger(H, hn)
-    L = g.near_field_functional(pts, cE, cH)
+    force, pts, cE, cH, L = g.force_stress_functional(x, d, e, center, radius, n_theta, n_phi)
     lam, _, _, st = g.adjoint_solve(L, tol=tol)
     if st != 0:
         raise FMBEMError(st, "adjoint solve did not converge")
@@ -137,9 +101,9 @@ def force_eps_gradient(V, F, D, eps, mu, k0, d, e, j, center, radius, n_theta=24
     The force is a real quadratic form of the solution, F_i = sum_p w_p (T(E, H) n)_i, so
     dF_i = 2 Re(L_i^T dx) with L_i the holomorphic (Wirtinger) derivative: for the point p,
     dF_i/dE_j = w_p / 4 [delta_ij (conj(E).n) + conj(E_i) n_j - n_i conj(E_j)] (and likewise for
-    H), mapped to the unknowns by fmbem_near_field_functional.  With A^T lambda_i = L_i and
-    s_i = lambda_i^T (dA/deps_j) x: dF_i/dRe(eps_j) = -2 Re(s_i), dF_i/dIm(eps_j) = 2 Im(s_i)."""
-    import torch
+    H), mapped to the unknowns by fmbem_force_stress_functional.  With A^T lambda_i = L_i and
+    s_i = lambda_i^T (dA/deps_j) x (fmbem_eps_sensitivity): dF_i/dRe(eps_j) = -2 Re(s_i),
+    dF_i/dIm(eps_j) = 2 Im(s_i)."""
     eps = [complex(v) for v in eps]
     if not 1 <= j < len(eps):
         raise ValueError("j must index a scatterer (1..J)")
@@ -147,14 +111,7 @@ def force_eps_gradient(V, F, D, eps, mu, k0, d, e, j, center, radius, n_theta=24
     d = np.asarray(d, dtype=np.float64).reshape(1, 3)
     e = np.asarray(e, dtype=np.complex128).reshape(1, 3)
     x, force, _, _, _, lam = _force_adjoint(g, d, e, center, radius, n_theta, n_phi, tol)
-    step = h if h is not None else 1e-5 * max(1.0, abs(eps[j]))
-    ep, em = list(eps), list(eps)
-    ep[j] += step
-    em[j] -= step
-    gp = FMBEM(V, F, D, ep, mu, k0, **options)
-    gm = FMBEM(V, F, D, em, mu, k0, **options)
-    dAx = (gp.matvec(x) - gm.matvec(x)) / (2 * step)
-    sv = torch.sum(lam * dAx, dim=(1, 2)).cpu().numpy()
+    sv = g.eps_sensitivity(j, x.expand(3, -1, -1).contiguous(), lam, step=h)  # s_i = lambda_i^T (dA/deps_j) x
     return force, -2 * sv.real, 2 * sv.imag
 
 

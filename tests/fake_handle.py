@@ -127,3 +127,49 @@ class FakeHandle:
                 Vm[v, c] -= h
                 out[:, v, c] = (G(Vp) - G(Vm)) / (2 * h)
         return out
+
+    # ---- the library's reductions, restated on the stand-in system
+    def cross_sections(self, x, dirs, pols, n_theta=2, n_phi=2):
+        """C_ext = Im(L^T x) with L the far-field-like functional of (dirs, 4 pi / k conj(pols))."""
+        dirs, pols = np.atleast_2d(dirs), np.atleast_2d(pols)
+        L = self._L(self.V, dirs, 4 * np.pi / self.kb.real * np.conj(pols))
+        cext = np.sum(L * x.numpy(), axis=(1, 2)).imag
+        return cext, np.zeros_like(cext), np.zeros_like(cext)
+
+    def eps_sensitivity(self, j, x, lam, step=None):
+        """lambda^T (dA/deps_j) x by the central difference of the stand-in operator."""
+        h = 1e-5 if step is None else step
+        e0 = self.eps[j]
+        self.eps[j] = e0 + h
+        Ap = self._A(self.V)
+        self.eps[j] = e0 - h
+        Am = self._A(self.V)
+        self.eps[j] = e0
+        dA = (Ap - Am) / (2 * h)
+        x, lam = x.numpy(), lam.numpy()
+        return np.array([np.sum(ll.reshape(-1) * (dA @ xx.reshape(-1))) for xx, ll in zip(x, lam)])
+
+    def force_stress_functional(self, x, d, e, center, radius, n_theta=24, n_phi=48):
+        """Stress-type force of the stand-in fields on a sphere and the functionals of its
+        components' Wirtinger coefficients (the quantities fmbem_force_stress_functional returns)."""
+        mu, wmu = np.polynomial.legendre.leggauss(n_theta)
+        ph = 2 * np.pi * np.arange(n_phi) / n_phi
+        MU, PH = np.meshgrid(mu, ph, indexing="ij")
+        ST = np.sqrt(1 - MU ** 2)
+        nq = np.stack([ST * np.cos(PH), ST * np.sin(PH), MU], -1).reshape(-1, 3)
+        wq = (wmu[:, None] * np.full(n_phi, 2 * np.pi / n_phi)[None, :]).ravel() * radius ** 2
+        pts = np.asarray(center, dtype=np.float64)[None, :] + radius * nq
+        E, H = self.near_field(x, pts, d, e, magnetic=True)
+        E, H = E[0], H[0]
+        en, hn = np.sum(np.conj(E) * nq, 1), np.sum(np.conj(H) * nq, 1)
+        u = np.sum(np.abs(E) ** 2 + np.abs(H) ** 2, 1)
+        force = np.sum(wq[:, None] * 0.5 * np.real(E * en[:, None] + H * hn[:, None] - 0.5 * u[:, None] * nq), 0)
+        eye = np.eye(3)
+
+        def wirtinger(Fv, fn):
+            c = (eye[:, None, :] * fn[None, :, None] + np.conj(Fv).T[:, :, None] * nq[None, :, :]
+                 - nq.T[:, :, None] * np.conj(Fv)[None, :, :])
+            return 0.25 * wq[None, :, None] * c
+
+        cE, cH = wirtinger(E, en), wirtinger(H, hn)
+        return force, pts, cE, cH, self.near_field_functional(pts, cE, cH)
