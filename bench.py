@@ -250,38 +250,50 @@ def m2l_flops_per_column(p, nr):
     return 8.0 * p ** 4, "dense S|R matrices"
 
 
-def roofline(info, p, nr, n_dom, phases, precision):
+def roofline(info, p, nr, n_dom, phases, precision, workload=None):
+    """Roofline of the dominant phase of the matvec, and in `phases` the same figures for the near
+    field (+ L2P + self) and for M2L + L2L, each against the peak of the arithmetic it runs in."""
     keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
     avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
-    dom = max(keys, key=lambda k: avg[k])
-    if dom == "m2l_l2l":
-        if precision == "bf16x3" and (3 * nr <= 24 or tensor_path(nr)):
-            per_col, form = 8.0 * p ** 4, "dense S|R on tcgen05, BF16x3 (bf16 hi/lo operands, three products)"
+    arith = "fp32" if precision in ("tf32", "bf16x3") else precision
+    alu_peak, alu_src = PEAK_TFLOPS[arith], f"measured {arith.upper()} FMA throughput of GB300 (self-written probe)"
+    out = {}
+    # M2L + L2L
+    tensor = (precision == "bf16x3" and (3 * nr <= 24 or tensor_path(nr))) or (precision == "tf32" and tensor_path(nr))
+    if tensor:
+        per_col = 8.0 * p ** 4
+        if precision == "bf16x3":
+            form = "dense S|R on tcgen05, BF16x3 (bf16 hi/lo operands, three products)"
+            peak, src = tensor_peak_bf16x3()
         else:
-            per_col, form = m2l_flops_per_column(p, nr)
-        flops = per_col * 3 * nr * info["ff_pairs"] * n_dom
-        name = f"M2L + L2L, {form}"
-    elif dom == "near_l2p_self":
-        cached = precision == "fp64" and nr < 4
-        per_pair, per_rhs = (NEAR_PAIR_CACHED, NEAR_RHS_CACHED) if cached else (NEAR_PAIR, NEAR_RHS)
-        flops = info["near_pairs"] * n_dom * (per_pair + per_rhs * nr)
-        name = "near field + L2P + self (k_near, k_near_w, k_near_r)"
-    else:
-        flops, name = None, dom
-    achieved = flops / (avg[dom] * 1e-3) / 1e12 if flops else None
-    if precision == "tf32" and dom == "m2l_l2l" and tensor_path(nr):
-        peak, src = tensor_peak_tf32()
-        bound, name = "tensor", name.replace("M2L + L2L", "M2L + L2L on tcgen05 TF32")
-    elif precision == "bf16x3" and dom == "m2l_l2l" and (3 * nr <= 24 or tensor_path(nr)):
-        peak, src = tensor_peak_bf16x3()
+            form = "dense S|R on tcgen05 TF32"
+            peak, src = tensor_peak_tf32()
         bound = "tensor"
     else:
-        arith = "fp32" if precision in ("tf32", "bf16x3") else precision
-        peak, bound = PEAK_TFLOPS[arith], "alu"
-        src = f"measured {arith.upper()} FMA throughput of GB300 (self-written probe)"
-    return dict(kernel=name, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
-                frac=achieved / peak if achieved else None, traffic=None, peak_source=src,
-                algorithmic_flops_per_launch=flops, phase_ms=avg)
+        per_col, form = m2l_flops_per_column(p, nr)
+        peak, src, bound = alu_peak, alu_src, "alu"
+    flops = per_col * 3 * nr * info["ff_pairs"] * n_dom
+    ach = flops / (avg["m2l_l2l"] * 1e-3) / 1e12
+    out["m2l_l2l"] = dict(kernel=f"M2L + L2L, {form}", bound=bound, achieved=ach, peak=peak, unit="TFLOP/s",
+                          frac=ach / peak, ms=avg["m2l_l2l"], algorithmic_flops_per_launch=flops, peak_source=src,
+                          traffic=phase_traffic(workload, precision, nr, "m2l_l2l"))
+    # near field + L2P + self
+    cached = precision == "fp64" and nr < 4
+    per_pair, per_rhs = (NEAR_PAIR_CACHED, NEAR_RHS_CACHED) if cached else (NEAR_PAIR, NEAR_RHS)
+    flops = info["near_pairs"] * n_dom * (per_pair + per_rhs * nr)
+    ach = flops / (avg["near_l2p_self"] * 1e-3) / 1e12
+    kern = ("k_near (pair-scalar cache)" if cached else "k_near_rb") if arith == "fp64" else \
+        ("k_near_ws" if nr < 4 else "k_near_r + k_near_w" if nr >= 32 else "k_near_w")
+    out["near_l2p_self"] = dict(kernel=f"near field + L2P + self ({kern})", bound="alu", achieved=ach, peak=alu_peak,
+                                unit="TFLOP/s", frac=ach / alu_peak, ms=avg["near_l2p_self"],
+                                algorithmic_flops_per_launch=flops, peak_source=alu_src,
+                                traffic=phase_traffic(workload, precision, nr, "near_l2p_self"))
+    dom = max(out, key=lambda k: avg[k])
+    r = dict(out[dom])
+    r.pop("ms")
+    r["phase_ms"] = avg
+    r["phases"] = out
+    return r
 
 
 def tensor_path(nr):
@@ -701,7 +713,7 @@ def run_ours(args):
 
     ms_step, phases, wall, clk = timed(prec, args.steps, args.warmup, clocks=True)
     value = job_throughput(N * nr, world, ms_step)
-    roof = roofline(info, p, nr, n_dom, phases, args.precision)
+    roof = roofline(info, p, nr, n_dom, phases, args.precision, args.workload)
 
     # e2e through the C ABI: pinned host x -> device, matvec, device -> pinned host y
     xh = x.cpu().pin_memory()
@@ -732,7 +744,7 @@ def run_ours(args):
         for o in others:
             mso, pho, _, _ = timed({"fp32": fm.FP32, "tf32": fm.TF32, "bf16x3": fm.BF16X3}[o], args.steps, args.warmup)
             other = dict(other or {}, **{o: dict(value=world * N * nr / (mso * 1e-3), ms_per_step=mso,
-                                                 roofline=roofline(info, p, nr, n_dom, pho, o))})
+                                                 roofline=roofline(info, p, nr, n_dom, pho, o, args.workload))})
     if nr > 1:
         # the plain method's form for comparison: FP64 arithmetic, one right-hand side per matvec
         x1, y1 = x[:1].contiguous(), y[:1].contiguous()

@@ -35,7 +35,7 @@ struct DomainConsts {  // per domain, device array
 template <typename R>
 __device__ __forceinline__ void prep_body(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm,
                                           const double *w, const int32_t *dom, const DomainConsts *dc, cx<R> *dens,
-                                          int64_t bx, int64_t by) {
+                                          int64_t bx, int64_t by, cx<R> *sj = nullptr) {
     int64_t i = bx * (int64_t)blockDim.x + threadIdx.x;
     int64_t r = by;
     if (i >= N) return;
@@ -55,11 +55,12 @@ __device__ __forceinline__ void prep_body(int64_t N, int64_t nr, const c64 *x, c
         d1[q] = to<R>(wi * (Phi[q] + n[q] * tn));
         d1[3 + q] = to<R>(gw * Psi[q]);
     }
+    if (sj) sj[r * N + i] = to<R>(wi * tn);  // v_1 - v_0 = s n (see k_near_ws)
 }
 template <typename R>
 __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm, const double *w,
-                       const int32_t *dom, const DomainConsts *dc, cx<R> *dens) {
-    prep_body<R>(N, nr, x, perm, nrm, w, dom, dc, dens, blockIdx.x, blockIdx.y);
+                       const int32_t *dom, const DomainConsts *dc, cx<R> *dens, cx<R> *sj) {
+    prep_body<R>(N, nr, x, perm, nrm, w, dom, dc, dens, blockIdx.x, blockIdx.y, sj);
 }
 
 // The single-precision densities node-major within blocks of 32 right-hand sides,
@@ -981,12 +982,27 @@ union NearSmem {
     cx<R> red[6][128];             // partial sums of the source slices
 };
 
-// fast single-precision transcendentals, precise double-precision ones
-__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// fast single-precision transcendentals, precise double-precision ones.  In single precision the
+// PTX approximations of the special-function unit with subnormals flushed (the arguments of the
+// near field are distances, R k and -Im k R: never subnormal where the result matters):
+// rsqrt.approx (relative error about 2^-23), ex2.approx of x log2(e), sin/cos.approx (absolute
+// error about 2^-21 for |x| <= pi; near-field pairs have |k| R well inside that range)
+__device__ __forceinline__ float rsqrt_(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
-__device__ __forceinline__ float exp_(float x) { return __expf(x); }
+__device__ __forceinline__ float exp_(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 1.44269504088896340736f));
+    return y;
+}
 __device__ __forceinline__ double exp_(double x) { return exp(x); }
-__device__ __forceinline__ void sincos_(float x, float *s, float *c) { __sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(float x, float *s, float *c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+}
 __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
 
 // One (source, target) pair of one domain: acc_i += -(K v)_i + g q_i (Eq. 2.12 for beta != alpha),
@@ -1643,6 +1659,219 @@ __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
             cfma(v, M[2], xa[2]);
             cfma(v, M[3 + c], xa[3 + c]);
             y[((rb0 + rr) * N + u) * 6 + 3 * side + c] = v;
+        }
+    }
+}
+
+// Steps 4-5 for one to three right-hand sides in single precision, both sides of every pair in
+// one pass.  One warp owns one unit: an item of near_work_items (tg targets of one leaf over nsl
+// source slices) and one right-hand side.  The densities of k_prep tie the two sides together:
+// v_1 = v_0 + s n with s = w t_j (n . Phi) (k_prep writes s beside the densities), and
+// q_1 = -gamma_j q_0; on the scatterer side only sources in the target's own scatterer j count,
+// so gamma_j is the target's and that side's q-part is -gamma_j times the sum of g_1 q_0.
+// With w = n x r and U = w x v_0 + (n . r) v_0 (the bracket of Eq. 2.12 for the source normal n),
+// the background's bracket is -U (it sees the normal -n) and the scatterer side's is U + s r,
+// since (n x r) x n + (n . r) n = r for a unit n.  So the geometry and U are evaluated once per
+// pair, and only the scalars g, c of grad'g = c r once per wavenumber.
+// The sources go through two warp-private tiles of NS_TS (one per lane, cp.async) as in
+// k_near_w; then the far field (L2P, Eq. 2.23 first term) and the rows of the analytic self block
+// (App. B) of both sides, as in k_near_w's epilogue.
+constexpr int NS_TS = 32;    // sources per tile, one staged by each lane
+constexpr int NS_WARPS = 4;  // warps per block; each fetches its own units
+struct SideTile {
+    float4 geo[3][NS_TS];  // source record: position hi + scatterer id bits, position lo + n_x, n_y n_z
+    float4 dv[3][NS_TS];   // background densities (v0, v1), (v2, q0), (q1, q2)
+    float2 sj[NS_TS];      // s of the source
+};
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__global__ void __launch_bounds__(32 * NS_WARPS, 6) k_near_ws(
+    int64_t leaf_off, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N,
+    int64_t nr, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
+    const float4 *__restrict__ rec, const cx<float> *dens, const cx<float> *sjump, const DomainConsts *dc,
+    const int32_t *perm, int p2, int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
+    const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y, bool side1) {
+    __shared__ SideTile tiles[NS_WARPS][2];
+    __shared__ int rng_beg[NS_WARPS][32], rng_cum[NS_WARPS][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    SideTile *T = tiles[warp];
+    int *rb_ = rng_beg[warp], *rc_ = rng_cum[warp];
+    for (;;) {
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(next_unit, 1);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= n_units) break;
+        const int64_t r = unit / n_items;
+        const int item_id = unit - (int)r * n_items;
+        __syncwarp();  // the previous unit's shared-memory reads are done
+        const int4 it = items[item_id];
+        const int leaf = it.x, tg = it.z, nsl = it.w;
+        const int64_t g = leaf_off + leaf;
+        // the Neighbor leaves' node ranges and their running sum (at most 27 entries)
+        const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
+        {
+            int beg = 0, cnt = 0;
+            if (lane < nnb) {
+                const int b = nbr_idx[nb0 + lane];
+                beg = nbeg[b];
+                cnt = nend[b] - beg;
+            }
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane < nnb) { rb_[lane] = beg; rc_[lane] = incl - cnt; }
+            if (lane == nnb - 1) rc_[nnb] = incl;
+        }
+        __syncwarp();
+        const int nsrc = rc_[nnb];
+        const int ti = lane % tg, sl = lane / tg;
+        const bool busy = sl < nsl;
+        const int a = nbeg[g] + it.y + ti;  // lanes past tg * nsl shadow a valid target and never store
+        const float4 ra = rec[3 * a], rla = rec[3 * a + 1];
+        const int adom = __float_as_int(ra.w);
+        const cx<float> k0 = to<float>(dc[0].k), kj = to<float>(dc[adom].k);
+        const cx<float> *d0 = dens + r * N * 6;
+        const cx<float> *sr = sjump + r * N;
+        int qcur = 0;
+        auto stage = [&](SideTile &B, int s0) {
+            const int e = s0 + lane;
+            if (e < nsrc) {
+                while (rc_[qcur + 1] <= e) ++qcur;
+                const int64_t i = rb_[qcur] + (e - rc_[qcur]);
+#pragma unroll
+                for (int part = 0; part < 3; ++part) cp_async16(&B.geo[part][lane], rec + 3 * i + part);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cp_async16(&B.dv[c][lane], d0 + 6 * i + 2 * c);
+                if (side1) cp_async8(&B.sj[lane], sr + i);
+            }
+            cp_async_commit();
+        };
+        cx<float> acc0[3], acc1[3], bq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc0[c] = acc1[c] = bq[c] = {0, 0};
+        const int ntile = (nsrc + NS_TS - 1) / NS_TS;
+        stage(T[0], 0);
+        for (int t = 0; t < ntile; ++t) {
+            if (t + 1 < ntile) stage(T[(t + 1) & 1], (t + 1) * NS_TS);
+            else cp_async_commit();  // an empty group keeps "all but the newest group done" meaning tile t
+            cp_async_wait1();
+            __syncwarp();
+            const SideTile &B = T[t & 1];
+            const int ns = busy ? min(NS_TS, nsrc - t * NS_TS) : 0;
+            for (int u = sl; u < ns; u += nsl) {
+                const float4 pa = B.geo[0][u], pb = B.geo[1][u], pc = B.geo[2][u];
+                const float rv[3] = {(pa.x - ra.x) + (pb.x - rla.x), (pa.y - ra.y) + (pb.y - rla.y),
+                                     (pa.z - ra.z) + (pb.z - rla.z)};
+                const float R2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+                const float inv = R2 > 0.f ? rsqrt_(R2) : 0.f;  // the node itself drops out
+                const float Rr = R2 * inv;
+                const float nrv = pb.w * rv[0] + pc.x * rv[1] + pc.y * rv[2];
+                const float w[3] = {pc.x * rv[2] - pc.y * rv[1], pc.y * rv[0] - pb.w * rv[2], pb.w * rv[1] - pc.x * rv[0]};
+                const float4 a0 = B.dv[0][u], a1 = B.dv[1][u], a2 = B.dv[2][u];
+                const cx<float> v[3] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}};
+                const cx<float> q[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+                const cx<float> U[3] = {w[1] * v[2] - w[2] * v[1] + nrv * v[0], w[2] * v[0] - w[0] * v[2] + nrv * v[1],
+                                        w[0] * v[1] - w[1] * v[0] + nrv * v[2]};
+                cx<float> gs, cs;
+                pair_scalars<float>(inv, Rr, k0, gs, cs);
+                const cx<float> mc = {-cs.re, -cs.im};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    cfma(acc0[c], mc, U[c]);
+                    cfma(acc0[c], gs, q[c]);
+                }
+                if (side1 && __float_as_int(pa.w) == adom) {
+                    const float2 s2 = B.sj[u];
+                    const cx<float> sc = {s2.x, s2.y};
+                    pair_scalars<float>(inv, Rr, kj, gs, cs);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        cfma(acc1[c], cs, U[c] + rv[c] * sc);
+                        cfma(bq[c], gs, q[c]);
+                    }
+                }
+            }
+            __syncwarp();  // the next stage overwrites this buffer
+        }
+        if (side1) {
+            const cx<float> mg = to<float>(dc[adom].gamma);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cfma(acc1[c], cx<float>{-mg.re, -mg.im}, bq[c]);
+        }
+        // far field of each side: the local expansion of the side's domain at the leaf, three
+        // columns, staged through the tiles' shared memory in chunks of qc coefficients; on the
+        // scatterer side the warp's targets may lie in several scatterers, taken in turn
+        cx<float> *Ds = reinterpret_cast<cx<float> *>(T);
+        const int qc = min(p2, (int)(2 * sizeof(SideTile) / sizeof(cx<float>)) / 3);
+        auto l2p = [&](int side, cx<float>(&acc)[3]) {
+            const int mydom = side == 0 ? 0 : adom;
+            const cx<float> *Ba = Bl2p + ((int64_t)side * N + a) * p2;
+            unsigned pending = 0xffffffffu;
+            while (pending) {
+                const int d = __shfl_sync(0xffffffffu, mydom, __ffs(pending) - 1);
+                const bool mine = mydom == d;
+                pending &= ~__ballot_sync(0xffffffffu, mine);
+                const cx<float> *Dg = D + (((int64_t)d * nbox + g) * 3 * nr + 3 * r) * p2;
+                for (int q0 = 0; q0 < p2; q0 += qc) {
+                    const int qn = min(qc, p2 - q0);
+                    __syncwarp();
+                    for (int e = lane; e < 3 * qn; e += 32) {
+                        const int col = e / qn, qq = e - col * qn;
+                        Ds[col * qc + qq] = Dg[(int64_t)col * p2 + q0 + qq];
+                    }
+                    __syncwarp();
+                    if (busy && mine) {
+                        for (int qq = sl; qq < qn; qq += nsl) {
+                            const cx<float> b = Ba[q0 + qq];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) cfma(acc[c], b, Ds[c * qc + qq]);
+                        }
+                    }
+                }
+            }
+        };
+        l2p(0, acc0);
+        if (side1) l2p(1, acc1);
+        // sum the slices of each target: lane ti + tg * sl, fixed tree over sl
+        for (int off = nsl >> 1; off >= 1; off >>= 1) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float re = __shfl_down_sync(0xffffffffu, acc0[c].re, off * tg);
+                float im = __shfl_down_sync(0xffffffffu, acc0[c].im, off * tg);
+                if (sl < off) { acc0[c].re += re; acc0[c].im += im; }
+                re = __shfl_down_sync(0xffffffffu, acc1[c].re, off * tg);
+                im = __shfl_down_sync(0xffffffffu, acc1[c].im, off * tg);
+                if (sl < off) { acc1[c].re += re; acc1[c].im += im; }
+            }
+        }
+        // the slice-0 sums to shared memory (the tiles are free), then the whole warp adds the
+        // rows of the self block in double precision and stores, one (target, row) per lane and pass
+        cx<float> *Ys = reinterpret_cast<cx<float> *>(T);  // [target][6]
+        __syncwarp();
+        if (sl == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { Ys[ti * 6 + c] = acc0[c]; Ys[ti * 6 + 3 + c] = acc1[c]; }
+        }
+        __syncwarp();
+        const int nrow = side1 ? 6 : 3;
+        for (int o = lane; o < tg * nrow; o += 32) {
+            const int t = o / nrow, row = o - t * nrow, side = row / 3, c = row - 3 * side;
+            const int64_t u = perm[nbeg[g] + it.y + t];
+            const c64 *M = Mself + 36 * u + 18 * side + 6 * c;
+            const c64 *xa = x + (r * N + u) * 6;
+            const cx<float> f = Ys[t * 6 + row];
+            c64 v = {(double)f.re, (double)f.im};
+            cfma(v, M[0], xa[0]);
+            cfma(v, M[1], xa[1]);
+            cfma(v, M[2], xa[2]);
+            cfma(v, M[3 + c], xa[3 + c]);
+            y[(r * N + u) * 6 + row] = v;
         }
     }
 }
@@ -2916,8 +3145,10 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // k_near_r in the half of the density buffer that double precision would use
     const int64_t nrT = f32 ? (nr / 32) * 32 : 0;
     cx<R> *densT = nrT > 0 ? dens + 2 * nr * N * 6 : nullptr;
+    // and with fewer than 4, the normal jump s of the densities (k_near_ws) in the same place
+    cx<R> *sj = f32 && nr < 4 ? dens + 2 * nr * N * 6 : nullptr;
     if (h->ibc) clear_unused_domains(h, nr, sizeof(R), s);
-    k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens);
+    k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens, sj);
     CKL("k_prep");
     if (densT != nullptr) {
         k_dens_node_major<<<dim3((unsigned)((N + 15) / 16), (unsigned)(nrT / 32), 2), 256, 0, s>>>(
@@ -2993,10 +3224,20 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             if (nblk > 0) launch_r(nblk);
             if (rest >= 8) launch_w(k_near_w<8>, 8, sizeof(WarpTile<8>), 32 * nblk);
             else if (rest > 0) launch_w(k_near_w<4>, 4, sizeof(WarpTile<4>), 32 * nblk);
-        } else  // few right-hand sides: the block-cooperative kernel spreads a leaf's pairs over more threads
-            k_near<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
-                                                          h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens,
-                                                          dc, Bl2p, D, h->Mself, x, y, nullptr, nullptr, !h->ibc);
+        } else {  // few right-hand sides: both sides of a pair in one pass, one unit per item and RHS
+            if (h->near_items == nullptr) throw fmbem_error{FMBEM_ERR_CUDA, "near-field work items were not built"};
+            const int64_t units = (int64_t)h->n_near_items * nr;
+            int per_sm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_ws, 32 * NS_WARPS, 0));
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((units + NS_WARPS - 1) / NS_WARPS,
+                                                                        (int64_t)std::max(per_sm, 1) * nsm));
+            CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
+            k_near_ws<<<(unsigned)grid, 32 * NS_WARPS, 0, s>>>(
+                L.off, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
+                h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, (const cx<float> *)sj, dc, h->perm, p2,
+                h->nbox, (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y, !h->ibc);
+            CKL("k_near_ws");
+        }
     } else if (nr >= 4) {
         constexpr int RBLK = 2;
         const size_t smn = sizeof(NearSmemRB<R, RBLK>);
@@ -3149,8 +3390,10 @@ template <typename R>
 static void matvec_static_scratch(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s) {
     const size_t S = sizeof(cx<R>);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    // single precision with 32 or more right-hand sides also keeps the node-major density copy
-    const size_t b_dens = up(S * 2 * nr * h->N * 6 * (sizeof(R) == 4 && nr >= 32 ? 2 : 1));
+    // single precision with 32 or more right-hand sides also keeps the node-major density copy,
+    // with fewer than 4 the densities' normal jump, both after the densities
+    const size_t extra = sizeof(R) == 4 ? (nr >= 32 ? 2 * nr * h->N * 6 : nr < 4 ? nr * h->N : 0) : 0;
+    const size_t b_dens = up(S * (2 * nr * h->N * 6 + extra));
     const size_t b_exp = up(S * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
     size_t b_y = 0;
     if (3 * nr <= 24) {
