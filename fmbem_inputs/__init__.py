@@ -107,12 +107,17 @@ def spheroid(a: float, c: float, subdiv: int, center=(0.0, 0.0, 0.0), domain: in
 
 
 def split_ring(R: float, side: float, gap_deg: float, nu: int, nv_side: int,
-               center=(0.0, 0.0, 0.0), domain: int = 1):
+               center=(0.0, 0.0, 0.0), domain: int = 1, grading: float = 1.0):
     """Split ring: a square cross-section (``side`` x ``side``) swept along a circle of radius R
     in the xy-plane over the angle range [gap/2, 2 pi - gap/2], closed by two flat end caps.
-    ``nu`` segments along the ring, ``nv_side`` segments per side of the square."""
+    ``nu`` segments along the ring, ``nv_side`` segments per side of the square.  ``grading`` q > 1
+    crowds the cross-sections towards the gap: the angle runs over t^q / (t^q + (1 - t)^q) of the
+    range for uniform t in [0, 1] (q = 1: uniform), so segments next to the gap are about
+    (1/nu)^(q-1) times shorter than at the far side."""
     g = math.radians(gap_deg)
-    u = np.linspace(g / 2, 2 * np.pi - g / 2, nu + 1)
+    t = np.linspace(0.0, 1.0, nu + 1)
+    f = t ** grading / (t ** grading + (1.0 - t) ** grading)
+    u = g / 2 + (2 * np.pi - g) * f
     h = side / 2
     # square cross-section perimeter, counter-clockwise in the (radial, z) plane
     s = np.linspace(0, 1, nv_side, endpoint=False)

@@ -163,6 +163,18 @@ typedef struct {
                                 meets the tolerance, and the handle uses the largest of them (the
                                 expansions of all levels have one length); fmbem_truncation
                                 reports both.  0: use p [0]                                     */
+    int adaptive;            /* octree: 0 the paper's uniform tree (all leaves on l_max, chosen by the
+                                mean occupancy as above); 1 per-branch adaptive: a box is split
+                                while it holds more than leaf_size nodes, down to max_level, so that
+                                leaves lie on several levels (strongly non-uniform meshes, e.g.
+                                narrow gaps).  M2L still runs between well-separated boxes of one
+                                level whose parents are adjacent (the FF lists of Appendix C); the
+                                sources a leaf gets neither through its own nor an ancestor's FF
+                                list are summed directly: the boxes of its level adjacent to it
+                                (all nodes below them) and, for every ancestor, the leaves of the
+                                ancestor's level adjacent to that ancestor.  FMBEM_ERR_INVALID_ARGUMENT
+                                when a leaf's direct sources need more than 32 node ranges;
+                                fmbem_batch_create refuses adaptive handles [0]                  */
 } fmbem_options;
 
 void fmbem_default_options(fmbem_options *opt);
@@ -218,6 +230,11 @@ int64_t fmbem_num_near_singular_pairs(const fmbem *h);
  * unused) the truncation each level needs for fmm_tol and the sampled relative error estimate at p
  * (-1 without fmm_tol, when p is the option's).  Any pointer may be NULL. */
 fmbem_status fmbem_truncation(const fmbem *h, int32_t *p, int32_t *p_level, double *err_level);
+
+/* Boxes and leaves per level (Appendix C; with option adaptive the leaves lie on several levels):
+ * boxes[l] = non-empty boxes of level l, leaves[l] = those that are leaves, for l = 0 .. n - 1
+ * (0 past l_max).  Either pointer may be NULL; host arrays of n entries. */
+fmbem_status fmbem_tree_levels(const fmbem *h, int32_t n, int64_t *boxes, int64_t *leaves);
 
 /* Octree summary: l_max, number of leaves, total number of boxes on levels 2..l_max, and the
  * number of near-field (source, target) node pairs and of far-field box pairs (S|R

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("outer_precision", ctypes.c_int), ("m2l_rotation", ctypes.c_int),
                 ("profile_phases", ctypes.c_int), ("near_cache", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("near_singular_radius", ctypes.c_double), ("near_singular_levels", ctypes.c_int),
-                ("fp32_only", ctypes.c_int), ("fmm_tol", ctypes.c_double)]
+                ("fp32_only", ctypes.c_int), ("fmm_tol", ctypes.c_double), ("adaptive", ctypes.c_int)]
 
 
 class Mesh(ctypes.Structure):
@@ -83,6 +83,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_eps_sensitivity": (i32, [P, i32, P, P, i64, dbl, P, P]),
         "fmbem_node_geometry": (i32, [P, P, P, P]),
         "fmbem_tree_info": (i32, [P, P, P, P, P, P]),
+        "fmbem_tree_levels": (i32, [P, i32, P, P]),
         "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
         "fmbem_matvec": (i32, [P, P, P, i64, i32, P]),
         "fmbem_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
@@ -212,6 +213,14 @@ def fmbem_tree_info(h):
     _check(h, load_library().fmbem_tree_info(h, ctypes.byref(lm), ctypes.byref(nl), ctypes.byref(nb),
                                              ctypes.byref(npairs), ctypes.byref(nff)))
     return dict(l_max=lm.value, n_leaves=nl.value, n_boxes=nb.value, near_pairs=npairs.value, ff_pairs=nff.value)
+
+
+def fmbem_tree_levels(h):
+    """Boxes and leaves per level 0..l_max (two int64 arrays)."""
+    n = fmbem_tree_info(h)["l_max"] + 1
+    boxes, leaves = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    _check(h, load_library().fmbem_tree_levels(h, n, _ptr(boxes), _ptr(leaves)))
+    return boxes, leaves
 
 
 def _dev(t, N, name, out=False):
@@ -475,6 +484,10 @@ class FMBEM:
 
     def tree_info(self):
         return fmbem_tree_info(self.h)
+
+    def tree_levels(self):
+        """(boxes, leaves) per level 0..l_max."""
+        return fmbem_tree_levels(self.h)
 
     def num_near_singular_pairs(self):
         return fmbem_num_near_singular_pairs(self.h)

@@ -114,6 +114,7 @@ void fmbem_default_options(fmbem_options *o) {
     o->near_singular_levels = 3;
     o->fp32_only = 0;
     o->fmm_tol = 0.0;
+    o->adaptive = 0;
 }
 
 fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fmbem_c64 *mu, double k0,
@@ -142,7 +143,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         (o.boundary != FMBEM_BOUNDARY_PENETRABLE && o.boundary != FMBEM_BOUNDARY_IMPEDANCE) ||
         !(o.near_singular_radius >= 0 && std::isfinite(o.near_singular_radius)) || o.near_singular_levels < 0 ||
         o.near_singular_levels > 6 || o.fp32_only < 0 || o.fp32_only > 1 ||
-        !(o.fmm_tol >= 0 && o.fmm_tol < 1)) {
+        !(o.fmm_tol >= 0 && o.fmm_tol < 1) || o.adaptive < 0 || o.adaptive > 1) {
         g_create_error = "invalid option value";
         delete h;
         return FMBEM_ERR_INVALID_ARGUMENT;
@@ -152,6 +153,7 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
     fmbem_status st = guarded(h, [&] {
         h->J = mesh->n_scatterers;
         h->k0 = k0;
+        h->adaptive = o.adaptive == 1;
         h->p = o.p;
         h->p2 = o.p * o.p;
         h->profile = o.profile_phases != 0;
@@ -256,11 +258,23 @@ fmbem_status fmbem_node_geometry(const fmbem *h, double *pos, double *normal, do
     return FMBEM_OK;
 }
 
+fmbem_status fmbem_tree_levels(const fmbem *h, int32_t n, int64_t *boxes, int64_t *leaves) {
+    if (!h || n < 0) return FMBEM_ERR_INVALID_ARGUMENT;
+    for (int32_t l = 0; l < n; ++l) {
+        if (boxes) boxes[l] = l <= h->lmax ? h->lev[l].n : 0;
+        if (leaves) leaves[l] = 0;
+    }
+    if (leaves)
+        for (int32_t lv : h->h_leaf_level)
+            if (lv < n) ++leaves[lv];
+    return FMBEM_OK;
+}
+
 fmbem_status fmbem_tree_info(const fmbem *h, int32_t *l_max, int64_t *n_leaves, int64_t *n_boxes, int64_t *near_pairs,
                              int64_t *ff_pairs) {
     if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
     if (l_max) *l_max = h->lmax;
-    if (n_leaves) *n_leaves = h->lev[h->lmax].n;
+    if (n_leaves) *n_leaves = h->n_leaves;
     if (n_boxes) {
         int64_t t = 0;
         for (int l = 2; l <= h->lmax; ++l) t += h->lev[l].n;

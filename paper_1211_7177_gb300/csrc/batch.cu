@@ -102,9 +102,10 @@ fmbem_status fmbem_batch_create(fmbem *const *handles, int32_t n_problems, int64
             g_batch_create_error = "handle " + std::to_string(i) + " is NULL";
             return FMBEM_ERR_INVALID_ARGUMENT;
         }
-        if (h->ibc || h->ns_pairs > 0 || h->p2 > 128 || h->lmax > BATCH_MAX_LEVEL) {
+        if (h->ibc || h->ns_pairs > 0 || h->p2 > 128 || h->lmax > BATCH_MAX_LEVEL || h->adaptive) {
             g_batch_create_error = "handle " + std::to_string(i) +
-                                   ": the batch needs the penetrable boundary, no near-singular correction, p <= 11";
+                                   ": the batch needs the penetrable boundary, the uniform octree, no near-singular "
+                                   "correction, p <= 11";
             return FMBEM_ERR_INVALID_ARGUMENT;
         }
     }

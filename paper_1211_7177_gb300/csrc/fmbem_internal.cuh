@@ -132,9 +132,20 @@ struct fmbem {
     double *box_ctr = nullptr;   // [nbox][3]
     int32_t *box_parent = nullptr;                        // [nbox] global index (-1 at level 0)
     int32_t *box_cbeg = nullptr, *box_cend = nullptr;     // [nbox] children range (global)
-    int32_t *box_nbeg = nullptr, *box_nend = nullptr;     // [nbox] sorted-node range
+    // [nbox + n_range_boxes] sorted-node range of every box, then of the merged node ranges that
+    // the near lists of an adaptive tree refer to
+    int32_t *box_nbeg = nullptr, *box_nend = nullptr;
+    int64_t n_range_boxes = 0;
+    // leaves (all at l_max in the paper's uniform tree; at any level in the adaptive tree), in
+    // node order: global box of each leaf, and the leaf position of every box (-1: not a leaf)
+    bool adaptive = false;
+    int64_t n_leaves = 0;
+    int32_t *leaf_box = nullptr, *box_leafpos = nullptr, *leaf_level = nullptr;
+    std::vector<int32_t> h_leaf_box, h_leaf_level;
     int32_t *node_leaf = nullptr;                         // [N] global leaf box of each sorted node
-    int32_t *nbr_start = nullptr, *nbr_idx = nullptr;     // leaf-level CSR of Neighbor+self (global ids)
+    // per leaf (leaf position order), CSR of the boxes whose nodes are its direct sources
+    // (uniform tree: Neighbor + self at l_max; adaptive tree: merged node ranges, see tree.cu)
+    int32_t *nbr_start = nullptr, *nbr_idx = nullptr;
     int32_t *ff_start = nullptr, *ff_src = nullptr;       // CSR of FF lists over global boxes
     int16_t *ff_off = nullptr;                            // offset code 0..315 per FF entry
     int64_t n_ff = 0, n_nbr = 0, near_pairs = 0;

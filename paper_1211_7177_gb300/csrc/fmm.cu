@@ -89,12 +89,11 @@ __global__ void __launch_bounds__(256) k_dens_node_major(int64_t N, int64_t nr, 
 // once per node in shared memory, P2M_WN nodes at a time.
 constexpr int P2M_WN = 64;
 template <typename R>
-__device__ __forceinline__ void p2m_body(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+__device__ __forceinline__ void p2m_body(int64_t g, int64_t N, int64_t nr, int p2, int64_t nbox,
                                          const int32_t *nbeg, const int32_t *nend, const int32_t *dom,
                                          const double *nrm, const cx<R> *dens, const cx<R> *Bp2m, cx<R> *C, int64_t bx,
                                          int by, int64_t bz) {
     __shared__ cx<R> W[P2M_WN][4][3];
-    const int64_t g = leaf_off + bx;
     const int d = by;
     const int64_t r = bz;
     const int side = d == 0 ? 0 : 1;
@@ -140,20 +139,21 @@ __device__ __forceinline__ void p2m_body(int64_t leaf_off, int64_t N, int64_t nr
         for (int c = 0; c < 3; ++c) C[(((int64_t)d * nbox + g) * 3 * nr + 3 * r + c) * p2 + q] = acc[c];
 }
 template <typename R>
-__global__ void k_p2m(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+__global__ void k_p2m(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
                       const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens, const cx<R> *Bp2m,
                       cx<R> *C) {
-    p2m_body<R>(leaf_off, N, nr, p2, nbox, nbeg, nend, dom, nrm, dens, Bp2m, C, blockIdx.x, blockIdx.y, blockIdx.z);
+    p2m_body<R>(leaf_box[blockIdx.x], N, nr, p2, nbox, nbeg, nend, dom, nrm, dens, Bp2m, C, blockIdx.x, blockIdx.y,
+                blockIdx.z);
 }
 
 // P2M for blocks of RB right-hand sides: the basis values of a (node, coefficient) are read once
 // and applied to every right-hand side of the block; grid (leaf, domain, rhs block), thread per
 // coefficient; same arithmetic, order and layout as k_p2m
 template <typename R, int RB>
-__global__ void k_p2m_rb(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+__global__ void k_p2m_rb(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
                          const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens,
                          const cx<R> *Bp2m, cx<R> *C) {
-    const int64_t g = leaf_off + blockIdx.x;
+    const int64_t g = leaf_box[blockIdx.x];
     const int d = blockIdx.y;
     const int64_t rb0 = (int64_t)blockIdx.z * RB;
     const int nrb = (int)min((int64_t)RB, nr - rb0);
@@ -206,13 +206,13 @@ __global__ void k_p2m_rb(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_
 constexpr int P2M_KC = 8;   // nodes per shared-memory chunk
 constexpr int P2M_MT = 48;  // columns per block (16 right-hand sides)
 template <typename R>
-__global__ void k_p2m_gemm(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+__global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
                            const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens,
                            const cx<R> *Bp2m, cx<R> *C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *Bs = reinterpret_cast<cx<R> *>(smem_raw);  // [4 P2M_KC][p2]
     cx<R> *Ws = Bs + 4 * P2M_KC * p2;                   // [4 P2M_KC][P2M_MT]
-    const int64_t g = leaf_off + blockIdx.x;
+    const int64_t g = leaf_box[blockIdx.x];
     const int d = blockIdx.y;
     const int ncols = (int)(3 * nr), col0 = blockIdx.z * P2M_MT;
     const int nh = min(P2M_MT, ncols - col0);
@@ -318,6 +318,7 @@ __device__ __forceinline__ void m2m_body(int64_t par_off, int l, int lmax, int64
     extern __shared__ unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
     int64_t g = par_off + bx;
+    if (cbeg[g] == cend[g]) return;  // a leaf of an adaptive tree: its multipole expansion is P2M's
     int d = by;
     int col0 = bz * NC;
     int ncol = min(NC, (int)(3 * nr) - col0);
@@ -877,6 +878,7 @@ __global__ void k_mm_reduce(int64_t par_off, int d, int64_t nr, int p2, int64_t 
                             const int32_t *cbeg, const int32_t *cend, const int32_t *entry, int64_t e_first,
                             const cx<R> *Y, cx<R> *C) {
     const int64_t g = par_off + blockIdx.x;
+    if (cbeg[g] == cend[g]) return;  // a leaf of an adaptive tree: its multipole expansion is P2M's
     const int64_t nel = (int64_t)ncol * p2;
     for (int64_t e = threadIdx.x; e < nel; e += blockDim.x) {
         cx<R> a = {0, 0};
@@ -1077,7 +1079,7 @@ __device__ __forceinline__ int source_range(const int *cum, int nnb, int e) {
 // store of the 6 result rows in user order.  Up to 128 targets per pass; the 128 threads split as
 // (target, source slice) with 128 / n_targets slices, reduced in a fixed order.
 template <typename R, bool DOUBLE_FLOAT>
-__device__ __forceinline__ void near_body(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+__device__ __forceinline__ void near_body(int64_t g, int64_t N, int64_t nr, int p2, int64_t nbox,
                                           const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
                                           const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
                                           const int32_t *dom, const int32_t *perm, const cx<R> *dens,
@@ -1087,7 +1089,6 @@ __device__ __forceinline__ void near_body(int64_t leaf_off, int64_t N, int64_t n
     __shared__ NearSmem<R> S;
     __shared__ int rng_beg[32], rng_cum[33];
     SrcTile<R> &T = S.tile;
-    const int64_t g = leaf_off + bx;
     const int nb0 = nbr_start[bx], nnb = nbr_start[bx + 1] - nb0;
     if (threadIdx.x == 0) {
         int cum = 0;
@@ -1219,14 +1220,14 @@ __device__ __forceinline__ void near_body(int64_t leaf_off, int64_t N, int64_t n
     }
 }
 template <typename R, bool DOUBLE_FLOAT>
-__global__ void __launch_bounds__(128) k_near(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+__global__ void __launch_bounds__(128) k_near(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox,
                                               const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
                                               const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo, const R *nrm,
                                               const int32_t *dom, const int32_t *perm, const cx<R> *dens,
                                               const DomainConsts *dc, const cx<R> *Bl2p, const cx<R> *D, const c64 *Mself,
                                               const c64 *x, c64 *y, const int64_t *cache_base,
                                               const V4<R> *cache, bool side1) {
-    near_body<R, DOUBLE_FLOAT>(leaf_off, N, nr, p2, nbox, nbeg, nend, nbr_start, nbr_idx, pos_hi, pos_lo, nrm, dom,
+    near_body<R, DOUBLE_FLOAT>(leaf_box[blockIdx.x], N, nr, p2, nbox, nbeg, nend, nbr_start, nbr_idx, pos_hi, pos_lo, nrm, dom,
                                perm, dens, dc, Bl2p, D, Mself, x, y, cache_base, cache, side1, blockIdx.x);
 }
 
@@ -1247,11 +1248,11 @@ __device__ __forceinline__ void pair_scalars(R inv, R Rr, cx<R> k, cx<R> &g, cx<
 // leaf's Neighbor list (in k_near's order) and every target t of the leaf, g and c of
 // grad'g = c r (Eq. 2.12) at entry (side, e, t) of the leaf's block, in double precision.
 template <typename R>
-__global__ void k_near_cache(int64_t leaf_off, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+__global__ void k_near_cache(const int32_t *leaf_box, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
                              const int32_t *nbr_idx, const double *pos, const int32_t *dom, const DomainConsts *dc,
                              const int64_t *base, V4<R> *cache) {
     __shared__ int rng_beg[32], rng_cum[33];
-    const int64_t g = leaf_off + blockIdx.x;
+    const int64_t g = leaf_box[blockIdx.x];
     const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
     if (threadIdx.x == 0) {
         int cum = 0;
@@ -1297,7 +1298,7 @@ union NearSmemRB {
 };
 
 template <typename R, bool DOUBLE_FLOAT, int RB>
-__global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+__global__ void __launch_bounds__(128) k_near_rb(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox,
                                                  const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
                                                  const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
                                                  const R *nrm, const int32_t *dom, const int32_t *perm,
@@ -1308,7 +1309,7 @@ __global__ void __launch_bounds__(128) k_near_rb(int64_t leaf_off, int64_t N, in
     NearSmemRB<R, RB> &S = *reinterpret_cast<NearSmemRB<R, RB> *>(smem_raw);
     SrcTileRB<R, RB> &T = S.tile;
     __shared__ int rng_beg[32], rng_cum[33];
-    const int64_t g = leaf_off + blockIdx.x;
+    const int64_t g = leaf_box[blockIdx.x];
     const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
     if (threadIdx.x == 0) {
         int cum = 0;
@@ -1459,7 +1460,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 
 template <int RB>
 __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
-    int64_t leaf_off, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N, int64_t nr,
+    const int32_t *leaf_box, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N, int64_t nr,
     int64_t rhs_base,
     const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
     const float4 *__restrict__ rec, const cx<float> *dens, const DomainConsts *dc, const int32_t *perm, int p2,
@@ -1482,7 +1483,7 @@ __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
         __syncwarp();  // the previous unit's shared-memory reads are done
         const int4 it = items[item_id];
         const int leaf = it.x, tg = it.z, nsl = it.w;
-        const int64_t g = leaf_off + leaf;
+        const int64_t g = leaf_box[leaf];
         // the Neighbor leaves' node ranges and their running sum (a Neighbor list has at most 27 entries)
         const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
         {
@@ -1690,7 +1691,7 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 }
 
 __global__ void __launch_bounds__(32 * NS_WARPS, 6) k_near_ws(
-    int64_t leaf_off, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N,
+    const int32_t *leaf_box, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N,
     int64_t nr, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
     const float4 *__restrict__ rec, const cx<float> *dens, const cx<float> *sjump, const DomainConsts *dc,
     const int32_t *perm, int p2, int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
@@ -1710,7 +1711,7 @@ __global__ void __launch_bounds__(32 * NS_WARPS, 6) k_near_ws(
         __syncwarp();  // the previous unit's shared-memory reads are done
         const int4 it = items[item_id];
         const int leaf = it.x, tg = it.z, nsl = it.w;
-        const int64_t g = leaf_off + leaf;
+        const int64_t g = leaf_box[leaf];
         // the Neighbor leaves' node ranges and their running sum (at most 27 entries)
         const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
         {
@@ -1897,7 +1898,7 @@ struct RhsTile {
 };
 
 __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
-    int64_t leaf_off, const int4 *__restrict__ groups, int n_groups, int n_units, int *next_unit, int64_t N,
+    const int32_t *leaf_box, const int4 *__restrict__ groups, int n_groups, int n_units, int *next_unit, int64_t N,
     int64_t nr, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
     const float4 *__restrict__ rec, const cx<float> *densT, const DomainConsts *dc, const int32_t *perm, int p2,
     int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
@@ -1918,7 +1919,7 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
         __syncwarp();  // the previous unit's shared-memory reads are done
         const int4 gi = groups[slab == 2 * (nr / 32) - 1 ? n_groups + grp : grp];  // last slab: longest first
         const int leaf = gi.x, ntg = gi.z;
-        const int64_t g = leaf_off + leaf;
+        const int64_t g = leaf_box[leaf];
         const int tbase = nbeg[g] + gi.y;
         const int nb0 = nbr_start[leaf], nnb = nbr_start[leaf + 1] - nb0;
         {
@@ -2222,9 +2223,9 @@ __global__ void k_prep_adj(int64_t N, int64_t nr, const c64 *x, const int32_t *p
 // monopole P2M: C[d][leaf][3 r + c][q] = sum over the leaf's nodes of domain d of b0(i, q) x_{i,c},
 // with b0 the monopole row of the P2M basis (Eqs. 2.18-2.19)
 template <typename R>
-__global__ void k_p2m_adj(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
+__global__ void k_p2m_adj(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
                           const int32_t *nend, const int32_t *dom, const cx<R> *dens, const cx<R> *Bp2m, cx<R> *C) {
-    const int64_t g = leaf_off + blockIdx.x;
+    const int64_t g = leaf_box[blockIdx.x];
     const int d = blockIdx.y;
     const int64_t r = blockIdx.z;
     const int side = d == 0 ? 0 : 1;
@@ -2257,7 +2258,7 @@ union AdjSmem {
 // near field, L2P (value and gradient), assembly and the transposed self block for one leaf;
 // threads split as (target, source slice) like k_near, both domains one after the other
 template <typename R, bool DOUBLE_FLOAT>
-__global__ void __launch_bounds__(128) k_near_adj(int64_t leaf_off, int64_t N, int64_t nr, int p2, int64_t nbox,
+__global__ void __launch_bounds__(128) k_near_adj(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox,
                                                   const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
                                                   const int32_t *nbr_idx, const R *pos_hi, const R *pos_lo,
                                                   const double *nrm, const double *w, const int32_t *dom,
@@ -2268,7 +2269,7 @@ __global__ void __launch_bounds__(128) k_near_adj(int64_t leaf_off, int64_t N, i
     __shared__ AdjSmem<R> S;
     __shared__ int rng_beg[32], rng_cum[33];
     AdjTile<R> &T = S.tile;
-    const int64_t g = leaf_off + blockIdx.x;
+    const int64_t g = leaf_box[blockIdx.x];
     const int nb0 = nbr_start[blockIdx.x], nnb = nbr_start[blockIdx.x + 1] - nb0;
     if (threadIdx.x == 0) {
         int cum = 0;
@@ -2523,7 +2524,7 @@ __global__ void __launch_bounds__(128) k_batch(const BatchProblem *probs, const 
                              w.a, w.c);
                 break;
             case BK_P2M:
-                p2m_body<R>(P.lev_off[lmax], P.N, nr, P.p2, P.nbox, P.nbeg, P.nend, P.dom, P.nrm64,
+                p2m_body<R>(P.lev_off[lmax] + w.a, P.N, nr, P.p2, P.nbox, P.nbeg, P.nend, P.dom, P.nrm64,
                             (const cx<R> *)P.dens, (const cx<R> *)P.Bp2m, (cx<R> *)P.C, w.a, w.b, w.c);
                 break;
             case BK_M2M:
@@ -2536,7 +2537,7 @@ __global__ void __launch_bounds__(128) k_batch(const BatchProblem *probs, const 
                              (cx<R> *)P.D, w.a, w.b, w.c);
                 break;
             default:
-                near_body<R, sizeof(R) == 4>(P.lev_off[lmax], P.N, nr, P.p2, P.nbox, P.nbeg, P.nend, P.nbr_start,
+                near_body<R, sizeof(R) == 4>(P.lev_off[lmax] + w.a, P.N, nr, P.p2, P.nbox, P.nbeg, P.nend, P.nbr_start,
                                              P.nbr_idx, (const R *)P.pos_hi, (const R *)P.pos_lo, (const R *)P.nrm,
                                              P.dom, P.perm, (const cx<R> *)P.dens, (const DomainConsts *)P.dc,
                                              (const cx<R> *)P.Bl2p, (const cx<R> *)P.D, P.Mself, P.x, P.y, nullptr,
@@ -2647,33 +2648,35 @@ void pack_rot_factors(fmbem *h, const c64 *Tzf, const c64 *Tyf, const c64 *Tyb, 
 // device memory)
 void build_near_cache(fmbem *h, cudaStream_t s) {
     if (h->opt.near_cache == 0) return;
-    const LevelInfo &L = h->lev[h->lmax];
-    std::vector<int32_t> nb(h->nbox), ne(h->nbox), ns(L.n + 1);
-    CK(cudaMemcpyAsync(nb.data(), h->box_nbeg, sizeof(int32_t) * h->nbox, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ne.data(), h->box_nend, sizeof(int32_t) * h->nbox, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ns.data(), h->nbr_start, sizeof(int32_t) * (L.n + 1), cudaMemcpyDeviceToHost, s));
-    std::vector<int32_t> idx(ns[L.n]);
-    CK(cudaMemcpyAsync(idx.data(), h->nbr_idx, sizeof(int32_t) * idx.size(), cudaMemcpyDeviceToHost, s));
+    const int64_t nl = h->n_leaves, nrng = h->nbox + h->n_range_boxes;
+    std::vector<int32_t> nb(nrng), ne(nrng), ns(nl + 1);
+    CK(cudaMemcpyAsync(nb.data(), h->box_nbeg, sizeof(int32_t) * nrng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ne.data(), h->box_nend, sizeof(int32_t) * nrng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ns.data(), h->nbr_start, sizeof(int32_t) * (nl + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    std::vector<int64_t> base(L.n + 1, 0);
-    for (int64_t lf = 0; lf < L.n; ++lf) {
+    std::vector<int32_t> idx(std::max(ns[nl], 1));
+    CK(cudaMemcpyAsync(idx.data(), h->nbr_idx, sizeof(int32_t) * ns[nl], cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int64_t> base(nl + 1, 0);
+    for (int64_t lf = 0; lf < nl; ++lf) {
         int64_t nsrc = 0;
         for (int q = ns[lf]; q < ns[lf + 1]; ++q) nsrc += ne[idx[q]] - nb[idx[q]];
-        base[lf + 1] = base[lf] + nsrc * (ne[L.off + lf] - nb[L.off + lf]);
+        const int32_t g = h->h_leaf_box[lf];
+        base[lf + 1] = base[lf] + nsrc * (ne[g] - nb[g]);
     }
-    const size_t pairs = (size_t)base[L.n];
+    const size_t pairs = (size_t)base[nl];
     const size_t bytes = 2 * pairs * sizeof(V4<double>);
     if (h->opt.near_cache == -1) {
         size_t freeb = 0, totb = 0;
         CK(cudaMemGetInfo(&freeb, &totb));
         if (bytes > freeb / 4) return;
     }
-    h->near_base = (int64_t *)dev_alloc(h, sizeof(int64_t) * (L.n + 1));
-    CK(cudaMemcpyAsync(h->near_base, base.data(), sizeof(int64_t) * (L.n + 1), cudaMemcpyHostToDevice, s));
+    h->near_base = (int64_t *)dev_alloc(h, sizeof(int64_t) * (nl + 1));
+    CK(cudaMemcpyAsync(h->near_base, base.data(), sizeof(int64_t) * (nl + 1), cudaMemcpyHostToDevice, s));
     h->near_cache64 = dev_alloc(h, 2 * pairs * sizeof(V4<double>));
     const DomainConsts *dc = (const DomainConsts *)h->dcons;
-    k_near_cache<double><<<(unsigned)L.n, 256, 0, s>>>(L.off, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, h->pos,
-                                                        h->dom, dc, h->near_base, (V4<double> *)h->near_cache64);
+    k_near_cache<double><<<(unsigned)nl, 256, 0, s>>>(h->leaf_box, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx,
+                                                       h->pos, h->dom, dc, h->near_base, (V4<double> *)h->near_cache64);
     CKL("k_near_cache");
     CK(cudaStreamSynchronize(s));
 }
@@ -2683,20 +2686,21 @@ void build_near_cache(fmbem *h, cudaStream_t s) {
 // nsl the largest power of two with tg * nsl <= 32, up to 8 warps per leaf
 void near_work_items(fmbem *h, cudaStream_t s) {
     if (h->near_items) return;
-    const LevelInfo &L = h->lev[h->lmax];
-    std::vector<int32_t> nb(L.n), ne(L.n);
-    CK(cudaMemcpyAsync(nb.data(), h->box_nbeg + L.off, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ne.data(), h->box_nend + L.off, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, s));
+    const int64_t nl = h->n_leaves, nrng = h->nbox + h->n_range_boxes;
+    std::vector<int32_t> nbA(nrng), neA(nrng), ns(nl + 1), ni;
+    CK(cudaMemcpyAsync(nbA.data(), h->box_nbeg, sizeof(int32_t) * nrng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(neA.data(), h->box_nend, sizeof(int32_t) * nrng, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ns.data(), h->nbr_start, sizeof(int32_t) * (nl + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    std::vector<int32_t> ns(L.n + 1), ni;
-    CK(cudaMemcpyAsync(ns.data(), h->nbr_start, sizeof(int32_t) * (L.n + 1), cudaMemcpyDeviceToHost, s));
+    ni.resize(std::max(ns[nl], 1));
+    CK(cudaMemcpyAsync(ni.data(), h->nbr_idx, sizeof(int32_t) * ns[nl], cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    ni.resize(std::max(ns[L.n], 1));
-    CK(cudaMemcpyAsync(ni.data(), h->nbr_idx, sizeof(int32_t) * ns[L.n], cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    // the leaves' own node ranges, in leaf order
+    std::vector<int32_t> nb(nl), ne(nl);
+    for (int64_t lf = 0; lf < nl; ++lf) { nb[lf] = nbA[h->h_leaf_box[lf]]; ne[lf] = neA[h->h_leaf_box[lf]]; }
     std::vector<int4> items;
     std::vector<int64_t> cost;  // a lane's pair count: the leaf's Neighbor sources over the slices
-    for (int64_t leaf = 0; leaf < L.n; ++leaf) {
+    for (int64_t leaf = 0; leaf < nl; ++leaf) {
         const int nt = ne[leaf] - nb[leaf];
         if (nt <= 0) continue;
         int bestW = (nt + 31) / 32, bestP = 1;
@@ -2710,7 +2714,7 @@ void near_work_items(fmbem *h, cudaStream_t s) {
         }
         const int tg = (nt + bestW - 1) / bestW;
         int64_t nsrc = 0;
-        for (int q = ns[leaf]; q < ns[leaf + 1]; ++q) nsrc += ne[ni[q] - L.off] - nb[ni[q] - L.off];
+        for (int q = ns[leaf]; q < ns[leaf + 1]; ++q) nsrc += neA[ni[q]] - nbA[ni[q]];
         for (int t = 0; t < nt; t += tg) {
             items.push_back(int4{(int)leaf, t, std::min(tg, nt - t), bestP});
             cost.push_back((nsrc + bestP - 1) / bestP);
@@ -2732,11 +2736,11 @@ void near_work_items(fmbem *h, cudaStream_t s) {
     // work first, for the last slab
     std::vector<int4> groups;
     std::vector<int64_t> gcost;
-    for (int64_t leaf = 0; leaf < L.n; ++leaf) {
+    for (int64_t leaf = 0; leaf < nl; ++leaf) {
         const int nt = ne[leaf] - nb[leaf];
         if (nt <= 0) continue;
         int64_t nsrc = 0;
-        for (int q = ns[leaf]; q < ns[leaf + 1]; ++q) nsrc += ne[ni[q] - L.off] - nb[ni[q] - L.off];
+        for (int q = ns[leaf]; q < ns[leaf + 1]; ++q) nsrc += neA[ni[q]] - nbA[ni[q]];
         const int ng = (nt + NR_TT - 1) / NR_TT;
         for (int k = 0, t0 = 0; k < ng; ++k) {
             const int cnt = nt / ng + (k < nt % ng ? 1 : 0);
@@ -3155,21 +3159,20 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             N, nr, (const float4 *)dens, (float4 *)densT);
         CKL("k_dens_node_major");
     }
-    const LevelInfo &L = h->lev[lmax];
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
     constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
     if (nr >= 16) {
         const int nthr = ((p2 + 3) / 4) * (P2M_MT / 4);
         const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + P2M_MT);
         CK(cudaFuncSetAttribute(k_p2m_gemm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
-        k_p2m_gemm<R><<<dim3((unsigned)L.n, J + 1, (unsigned)((3 * nr + P2M_MT - 1) / P2M_MT)), nthr, smp, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+        k_p2m_gemm<R><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)((3 * nr + P2M_MT - 1) / P2M_MT)), nthr, smp, s>>>(
+            h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     } else if (nr >= 4)
-        k_p2m_rb<R, P2M_RB><<<dim3((unsigned)L.n, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+        k_p2m_rb<R, P2M_RB><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
+            h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     else  // one thread per coefficient
-        k_p2m<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), ((p2 + 31) / 32) * 32, 0, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
+        k_p2m<R><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)nr), ((p2 + 31) / 32) * 32, 0, s>>>(
+            h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     CKL("k_p2m");
     if (timing) CK(cudaEventRecord(h->ev[1], s));
     upward_m2m<R>(h, nr, s);
@@ -3198,7 +3201,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                                     (int64_t)std::max(per_sm, 1) * nsm));
         CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
         kern<<<(unsigned)grid, 32 * NW_WARPS, smw, s>>>(
-            L.off, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, rhs_base, h->box_nbeg,
+            h->leaf_box, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, rhs_base, h->box_nbeg,
             h->box_nend, h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, dc, h->perm, p2, h->nbox,
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_w");
@@ -3213,7 +3216,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                                     (int64_t)std::max(per_sm, 1) * nsm));
         CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
         k_near_r<<<(unsigned)grid, 32 * NR_WARPS, 0, s>>>(
-            L.off, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
+            h->leaf_box, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
             h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)densT, dc, h->perm, p2, h->nbox,
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_r");
@@ -3233,7 +3236,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                                         (int64_t)std::max(per_sm, 1) * nsm));
             CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
             k_near_ws<<<(unsigned)grid, 32 * NS_WARPS, 0, s>>>(
-                L.off, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
+                h->leaf_box, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
                 h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, (const cx<float> *)sj, dc, h->perm, p2,
                 h->nbox, (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y, !h->ibc);
             CKL("k_near_ws");
@@ -3242,11 +3245,11 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
         constexpr int RBLK = 2;
         const size_t smn = sizeof(NearSmemRB<R, RBLK>);
         CK(cudaFuncSetAttribute(k_near_rb<R, false, RBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn));
-        k_near_rb<R, false, RBLK><<<dim3((unsigned)L.n, (unsigned)((nr + RBLK - 1) / RBLK)), 128, smn, s>>>(
-            L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm,
+        k_near_rb<R, false, RBLK><<<dim3((unsigned)h->n_leaves, (unsigned)((nr + RBLK - 1) / RBLK)), 128, smn, s>>>(
+            h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start, h->nbr_idx, ph, pl, nn, h->dom, h->perm,
             dens, dc, Bl2p, D, h->Mself, x, y, !h->ibc);
     } else {
-        k_near<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
+        k_near<R, false><<<(unsigned)h->n_leaves, 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->nbr_start,
                                                        h->nbr_idx, ph, pl, nn, h->dom, h->perm, dens, dc, Bl2p, D,
                                                        h->Mself, x, y, h->near_base, (const V4<R> *)h->near_cache64,
                                                        !h->ibc);
@@ -3277,9 +3280,8 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
     if (h->ibc) clear_unused_domains(h, nr, sizeof(R), s);
     k_prep_adj<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->ibc ? 1 : 2, dens);
     CKL("k_prep_adj");
-    const LevelInfo &L = h->lev[lmax];
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
-    k_p2m_adj<R><<<dim3((unsigned)L.n, J + 1, (unsigned)nr), tbc, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg,
+    k_p2m_adj<R><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)nr), tbc, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg,
                                                                            h->box_nend, h->dom, dens, Bp2m, C);
     CKL("k_p2m_adj");
     upward_m2m<R>(h, nr, s);
@@ -3288,12 +3290,12 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
     const V4<R> *cache = f32 ? nullptr : (const V4<R> *)h->near_cache64;
     if constexpr (sizeof(R) == 4)
-        k_near_adj<R, true><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+        k_near_adj<R, true><<<(unsigned)h->n_leaves, 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                           h->nbr_start, h->nbr_idx, ph, pl, h->nrm, h->w, h->dom,
                                                           h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
                                                           h->near_base, cache);
     else
-        k_near_adj<R, false><<<(unsigned)L.n, 128, 0, s>>>(L.off, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+        k_near_adj<R, false><<<(unsigned)h->n_leaves, 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                            h->nbr_start, h->nbr_idx, ph, pl, h->nrm, h->w, h->dom,
                                                            h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
                                                            h->near_base, cache);

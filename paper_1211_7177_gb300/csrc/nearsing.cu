@@ -71,14 +71,14 @@ __device__ __forceinline__ bool ns_pair(const double *pos, const double *w, int6
 
 // pass 1 (start == NULL): count the qualifying sources of every target; pass 2: write them at
 // start[target] (user indices of target and source), in the order of the Neighbor list.
-// node_leaf holds global box ids; nbr_start is indexed by the leaf's position in the leaf level
-__global__ void k_ns_pairs(int64_t N, double rho, int64_t leaf_off, const int32_t *node_leaf, const int32_t *nbr_start,
+// node_leaf holds global box ids; nbr_start is indexed by the leaf's position (box_leafpos)
+__global__ void k_ns_pairs(int64_t N, double rho, const int32_t *box_leafpos, const int32_t *node_leaf, const int32_t *nbr_start,
                            const int32_t *nbr_idx, const int32_t *box_nbeg, const int32_t *box_nend, const double *pos,
                            const double *w, const int32_t *perm, int32_t *cnt, const int64_t *start, int32_t *tgt,
                            int32_t *src) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int64_t leaf = node_leaf[i] - leaf_off;  // the Neighbor CSR is indexed by leaf within the leaf level
+    const int64_t leaf = box_leafpos[node_leaf[i]];
     const int32_t ui = perm[i];
     int64_t k = start ? start[ui] : 0;
     int32_t c = 0;
@@ -325,7 +325,7 @@ void build_near_singular(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s) {
     }
     // pairs: count, prefix sum, fill
     int32_t *dcnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
-    k_ns_pairs<<<(unsigned)((N + TB - 1) / TB), TB, 0, s>>>(N, rho, h->lev[h->lmax].off, h->node_leaf, h->nbr_start, h->nbr_idx, h->box_nbeg,
+    k_ns_pairs<<<(unsigned)((N + TB - 1) / TB), TB, 0, s>>>(N, rho, h->box_leafpos, h->node_leaf, h->nbr_start, h->nbr_idx, h->box_nbeg,
                                                           h->box_nend, h->pos, h->w, h->perm, dcnt, nullptr, nullptr,
                                                           nullptr);
     CKL("k_ns_pairs");
@@ -342,7 +342,7 @@ void build_near_singular(fmbem *h, const fmbem_mesh *mesh, cudaStream_t s) {
         h->ns_tgt = (int32_t *)dev_alloc(h, sizeof(int32_t) * np);
         h->ns_src = (int32_t *)dev_alloc(h, sizeof(int32_t) * np);
         h->ns_coef = (c64 *)dev_alloc(h, sizeof(c64) * 8 * np);
-        k_ns_pairs<<<(unsigned)((N + TB - 1) / TB), TB, 0, s>>>(N, rho, h->lev[h->lmax].off, h->node_leaf, h->nbr_start, h->nbr_idx,
+        k_ns_pairs<<<(unsigned)((N + TB - 1) / TB), TB, 0, s>>>(N, rho, h->box_leafpos, h->node_leaf, h->nbr_start, h->nbr_idx,
                                                               h->box_nbeg, h->box_nend, h->pos, h->w, h->perm, dcnt,
                                                               h->ns_start, h->ns_tgt, h->ns_src);
         CKL("k_ns_pairs");

@@ -303,13 +303,14 @@ __device__ void exterior_term(const double *t, const double *s, const double *n,
 // every leaf sums all nodes directly.  Thread per (point, rhs).
 constexpr int FF_PMAX = 20;
 template <bool WITH_H>
-__global__ void __launch_bounds__(128) k_field_fmm(int64_t N, int64_t nr, int p, int64_t nbox, int64_t leaf_off,
+__global__ void __launch_bounds__(128) k_field_fmm(int64_t N, int64_t nr, int p, int64_t nbox,
+                                                 const int32_t *leaf_box, const int32_t *leaf_level,
                                                  const int32_t *leaf_of, const double *box_ctr,
                                                  const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
                                                  const int32_t *nbr_idx, const double *spos, const double *snrm,
                                                  const double *sw, const int32_t *perm, const double *upos,
                                                  const double *unrm, const double *uw, const c64 *x, const c64 *D,
-                                                 double lam, int64_t n_pts, const double *pts, c64 k0, c64 iwmu,
+                                                 double kw0, int64_t n_pts, const double *pts, c64 k0, c64 iwmu,
                                                  const double *dir, const c64 *pol, c64 *E, c64 *H) {
     const int64_t pt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, r = blockIdx.y;
     if (pt >= n_pts) return;
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(128) k_field_fmm(int64_t N, int64_t nr, int p,
             exterior_term<WITH_H>(t, upos + 3 * b, unrm + 3 * b, uw[b], x + (r * N + b) * 6, x + (r * N + b) * 6 + 3, ik,
                                   acc, cur);
     } else {
-        const int64_t g = leaf_off + lf;
+        const int64_t g = leaf_box[lf];
+        const double lam = ldexp(kw0, -leaf_level[lf]);  // |k_0| w of the leaf's level
         for (int q = nbr_start[lf]; q < nbr_start[lf + 1]; ++q) {
             const int32_t bx = nbr_idx[q];
             for (int i = nbeg[bx]; i < nend[bx]; ++i) {
@@ -711,19 +713,18 @@ void run_near_field_fmm(fmbem *h, const c64 *x, int64_t nr, int64_t n_pts, const
             CK(cudaMemcpyAsync(dpol, pol_host, sizeof(c64) * 3 * nr, cudaMemcpyHostToDevice, s));
         }
         run_locate_leaves(h, dp, n_pts, dl, s);
-        const LevelInfo &L = h->lev[h->lmax];
-        const double lam = h->lam[h->lmax];  // domain 0, leaf level
+        const double kw0 = cabsd(h->k[0]) * h->lev[0].w;  // the scale of level l is kw0 / 2^l
         const c64 iwmu = c64{0, h->k0} * h->mu[0];
         const dim3 grid((unsigned)((n_pts + 127) / 128), (unsigned)nr);
         if (dH)
-            k_field_fmm<true><<<grid, 128, 0, s>>>(h->N, nr, h->p, h->nbox, L.off, dl, h->box_ctr, h->box_nbeg,
+            k_field_fmm<true><<<grid, 128, 0, s>>>(h->N, nr, h->p, h->nbox, h->leaf_box, h->leaf_level, dl, h->box_ctr, h->box_nbeg,
                                                    h->box_nend, h->nbr_start, h->nbr_idx, h->pos, h->nrm, h->w,
-                                                   h->perm, h->upos, h->unrm, h->uw, x, (const c64 *)h->Dexp, lam,
+                                                   h->perm, h->upos, h->unrm, h->uw, x, (const c64 *)h->Dexp, kw0,
                                                    n_pts, dp, h->k[0], iwmu, dd, dpol, dE, dH);
         else
-            k_field_fmm<false><<<grid, 128, 0, s>>>(h->N, nr, h->p, h->nbox, L.off, dl, h->box_ctr, h->box_nbeg,
+            k_field_fmm<false><<<grid, 128, 0, s>>>(h->N, nr, h->p, h->nbox, h->leaf_box, h->leaf_level, dl, h->box_ctr, h->box_nbeg,
                                                     h->box_nend, h->nbr_start, h->nbr_idx, h->pos, h->nrm, h->w,
-                                                    h->perm, h->upos, h->unrm, h->uw, x, (const c64 *)h->Dexp, lam,
+                                                    h->perm, h->upos, h->unrm, h->uw, x, (const c64 *)h->Dexp, kw0,
                                                     n_pts, dp, h->k[0], iwmu, dd, dpol, dE, nullptr);
         CKL("k_field_fmm");
         CK(cudaMemcpyAsync(E_host, dE, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyDeviceToHost, s));

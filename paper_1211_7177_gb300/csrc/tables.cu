@@ -62,15 +62,17 @@ __global__ void k_to32(const c64 *a, c32 *b, int64_t n) {
 }
 
 // per node and side: P2M basis (scaled, with the i k prefactor) and L2P basis
+// (the scale lambda = |k_d| w_l of the node's leaf level: |k_d| w_0 / 2^l, as the level tables')
 __global__ void k_node_bases(int64_t N, int p, const double *pos, const int32_t *dom, const int32_t *node_leaf,
-                             const double *box_ctr, const c64 *kd, const double *lam /* [J+1] at the leaf level */,
-                             c64 *Bp2m, c64 *Bl2p, c64 *Bl2pg) {
+                             const int32_t *box_leafpos, const int32_t *leaf_level, const double *box_ctr,
+                             const c64 *kd, const double *kw0 /* [J+1] |k_d| w_0 */, c64 *Bp2m, c64 *Bl2p,
+                             c64 *Bl2pg) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int side = blockIdx.y;
     if (i >= N) return;
     int d = side == 0 ? 0 : dom[i];
     c64 k = kd[d];
-    double la = lam[d];
+    double la = ldexp(kw0[d], -leaf_level[box_leafpos[node_leaf[i]]]);
     const double *c = box_ctr + 3 * node_leaf[i];
     double r[3] = {pos[3 * i] - c[0], pos[3 * i + 1] - c[1], pos[3 * i + 2] - c[2]};
     c64 R[(PMAX + 1) * (PMAX + 1)], rad[PMAX + 2];
@@ -342,7 +344,7 @@ void build_tables(fmbem *h, cudaStream_t s) {
     c64 *dk = (c64 *)dev_alloc(h, sizeof(c64) * (J + 1));
     double *dl = (double *)dev_alloc(h, sizeof(double) * (J + 1));
     std::vector<double> lleaf(J + 1);
-    for (int d = 0; d <= J; ++d) lleaf[d] = h->lam[d * (lmax + 1) + lmax];
+    for (int d = 0; d <= J; ++d) lleaf[d] = cabsd(h->k[d]) * h->lev[0].w;
     CK(cudaMemcpyAsync(dk, h->k.data(), sizeof(c64) * (J + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dl, lleaf.data(), sizeof(double) * (J + 1), cudaMemcpyHostToDevice, s));
     h->B_p2m64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * 4 * p2);
@@ -350,7 +352,8 @@ void build_tables(fmbem *h, cudaStream_t s) {
     h->B_l2pg64 = (c64 *)dev_alloc(h, sizeof(c64) * 2 * N * 3 * p2);
     {
         dim3 grid(nblk(N, 64), 2);
-        k_node_bases<<<grid, 64, 0, s>>>(N, p, h->pos, h->dom, h->node_leaf, h->box_ctr, dk, dl, h->B_p2m64, h->B_l2p64,
+        k_node_bases<<<grid, 64, 0, s>>>(N, p, h->pos, h->dom, h->node_leaf, h->box_leafpos, h->leaf_level, h->box_ctr,
+                                          dk, dl, h->B_p2m64, h->B_l2p64,
                                           h->B_l2pg64);
         CKL("k_node_bases");
     }

@@ -312,11 +312,14 @@ __global__ void k_add_offset(int32_t *a, int64_t n, int32_t off) {
 
 inline unsigned nblk(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
-// the leaf (index within level lmax) containing each point, or -1 when the point lies outside
-// the root cube or in an empty box: the key of the point's box at level lmax (as k_keys, without
-// clamping) looked up by bisection among the sorted leaf keys
-__global__ void k_locate_leaf(int64_t n, const double *pts, double x0, double y0, double z0, double inv_w,
-                              int shift, const uint64_t *leaf_key, int64_t nleaf, int32_t *leaf) {
+// the leaf (position in the leaf order) containing each point, or -1 when the point lies outside
+// the root cube or in an empty box: the key of the point's box at each level (as k_keys, without
+// clamping), looked up by bisection among that level's sorted keys from the deepest level up; the
+// first box found is the deepest one that contains the point, and the answer is its leaf position
+// (-1 when it is not a leaf: the point lies in an empty part of a subdivided box)
+__global__ void k_locate_leaf(int64_t n, const double *pts, double x0, double y0, double z0, double inv_w, int lmax,
+                              const int64_t *lev_off, const uint64_t *box_key, const int32_t *box_leafpos,
+                              int32_t *leaf) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int M = 1 << KEY_LEVELS;
@@ -330,14 +333,21 @@ __global__ void k_locate_leaf(int64_t n, const double *pts, double x0, double y0
     }
     int32_t found = -1;
     if (inside) {
-        const uint64_t key = morton(c[0], c[1], c[2]) >> shift;
-        int64_t lo = 0, hi = nleaf;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) / 2;
-            if (leaf_key[mid] < key) lo = mid + 1;
-            else hi = mid;
+        const uint64_t full = morton(c[0], c[1], c[2]);
+        for (int l = lmax; l >= 0; --l) {
+            const uint64_t key = full >> (3 * (KEY_LEVELS - l));
+            const int64_t off = lev_off[l], nb = lev_off[l + 1] - off;
+            int64_t lo = 0, hi = nb;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) / 2;
+                if (box_key[off + mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < nb && box_key[off + lo] == key) {
+                found = box_leafpos[off + lo];
+                break;
+            }
         }
-        if (lo < nleaf && leaf_key[lo] == key) found = (int32_t)lo;
     }
     leaf[i] = found;
 }
@@ -345,52 +355,244 @@ __global__ void k_locate_leaf(int64_t n, const double *pts, double x0, double y0
 }  // namespace
 
 void run_locate_leaves(fmbem *h, const double *pts_dev, int64_t n, int32_t *leaf_dev, cudaStream_t s) {
-    const LevelInfo &L = h->lev[h->lmax];
+    std::vector<int64_t> off(h->lmax + 2);
+    for (int l = 0; l <= h->lmax; ++l) off[l] = h->lev[l].off;
+    off[h->lmax + 1] = h->nbox;
+    int64_t *doff = (int64_t *)dev_alloc(h, sizeof(int64_t) * off.size());
+    CK(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
     k_locate_leaf<<<nblk(n, 128), 128, 0, s>>>(n, pts_dev, h->root_min[0], h->root_min[1], h->root_min[2],
-                                               (double)(1 << KEY_LEVELS) / h->root_w, 3 * (KEY_LEVELS - h->lmax),
-                                               h->box_key + L.off, L.n, leaf_dev);
+                                               (double)(1 << KEY_LEVELS) / h->root_w, h->lmax, doff, h->box_key,
+                                               h->box_leafpos, leaf_dev);
     CKL("k_locate_leaf");
+    CK(cudaStreamSynchronize(s));
+    dev_free(h, doff);
 }
 
-void build_tree(fmbem *h, cudaStream_t s) {
+namespace {
+
+// leaf arrays from h_leaf_box (global boxes of the leaves, node order): device copy, the leaf
+// position of every box (-1 for the others) and the level of every leaf
+void finish_leaves(fmbem *h, cudaStream_t s) {
+    const int64_t nl = (int64_t)h->h_leaf_box.size();
+    h->n_leaves = nl;
+    h->h_leaf_level.resize(nl);
+    std::vector<int32_t> pos(h->nbox, -1);
+    for (int64_t i = 0; i < nl; ++i) {
+        const int32_t g = h->h_leaf_box[i];
+        pos[g] = (int32_t)i;
+        int l = h->lmax;
+        while (l > 0 && h->lev[l].off > g) --l;
+        h->h_leaf_level[i] = l;
+    }
+    h->leaf_box = (int32_t *)dev_alloc(h, sizeof(int32_t) * std::max<int64_t>(nl, 1));
+    h->leaf_level = (int32_t *)dev_alloc(h, sizeof(int32_t) * std::max<int64_t>(nl, 1));
+    h->box_leafpos = (int32_t *)dev_alloc(h, sizeof(int32_t) * h->nbox);
+    CK(cudaMemcpyAsync(h->leaf_box, h->h_leaf_box.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->leaf_level, h->h_leaf_level.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_leafpos, pos.data(), sizeof(int32_t) * h->nbox, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+namespace {
+
+// Per-branch adaptive octree: a box is split into its non-empty octants while it holds more than
+// leaf_size nodes (levels 0 and 1 always; no box below max_level), so leaves lie on several
+// levels.  The passes then count every (target, source) pair once: by M2L between well-separated
+// boxes of one level whose parents are adjacent (the paper's FF lists, built as for the uniform
+// tree: a parent's colleague that is a leaf has no children), or directly.  The direct sources of
+// a leaf T on level l are
+//   (a) the boxes of level l adjacent to T, and T itself, leaves or not (all nodes below them),
+//   (b) for every ancestor A of T, the leaves on A's level adjacent to A
+// (the per-target form of the U, W and X lists of adaptive FMMs with the W and X interactions
+// summed directly).  The nodes below a box are contiguous in Morton order, so each entry is a node
+// range; a leaf's ranges are sorted and merged, and a merged range that is not one box's becomes
+// a range entry after the boxes in box_nbeg / box_nend.
+constexpr int NEAR_RANGES_MAX = 32;  // the near-field kernels stage at most 32 ranges per leaf
+
+void adaptive_boxes(fmbem *h, const uint64_t *key_dev, double side, cudaStream_t s) {
+    const int64_t N = h->N;
+    std::vector<uint64_t> hk(N);
+    CK(cudaMemcpyAsync(hk.data(), key_dev, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int cap = std::max(2, std::min(h->opt.max_level, KEY_LEVELS));
+    const int64_t leaf_size = h->opt.leaf_size;
+    struct Box {
+        uint64_t key;
+        int32_t nb, ne, parent, cb, ce;
+        bool leaf;
+    };
+    std::vector<std::vector<Box>> L(1);
+    L[0].push_back(Box{0, 0, (int32_t)N, -1, 0, 0, false});
+    for (int l = 0;; ++l) {
+        std::vector<Box> next;
+        const int shift = 3 * (KEY_LEVELS - (l + 1));
+        for (size_t b = 0; b < L[l].size(); ++b) {
+            Box &B = L[l][b];
+            B.leaf = l >= 2 && (B.ne - B.nb <= leaf_size || l == cap);
+            if (B.leaf) continue;
+            B.cb = (int32_t)next.size();
+            for (int32_t i = B.nb; i < B.ne;) {
+                const uint64_t ck = hk[i] >> shift;
+                int32_t j = i + 1;
+                while (j < B.ne && (hk[j] >> shift) == ck) ++j;
+                next.push_back(Box{ck, i, j, (int32_t)b, 0, 0, false});
+                i = j;
+            }
+            B.ce = (int32_t)next.size();
+        }
+        if (next.empty()) break;
+        L.push_back(std::move(next));
+    }
+    const int lmax = (int)L.size() - 1;
+    h->lmax = lmax;
+    h->lev.assign(lmax + 1, LevelInfo{});
+    int64_t tot = 0;
+    for (int l = 0; l <= lmax; ++l) {
+        h->lev[l].off = tot;
+        h->lev[l].n = (int64_t)L[l].size();
+        h->lev[l].w = side / (double)(1 << l);
+        tot += h->lev[l].n;
+    }
+    h->nbox = tot;
+    // global box arrays, and per level the sorted keys for lookups
+    std::vector<uint64_t> gkey(tot);
+    std::vector<double> gctr(3 * tot);
+    std::vector<int32_t> gpar(tot), gcb(tot, 0), gce(tot, 0), gnb(tot), gne(tot);
+    std::vector<char> is_leaf(tot, 0);
+    std::vector<std::pair<int32_t, int32_t>> leaves;  // (first node, global box)
+    for (int l = 0; l <= lmax; ++l)
+        for (size_t b = 0; b < L[l].size(); ++b) {
+            const Box &B = L[l][b];
+            const int64_t g = h->lev[l].off + (int64_t)b;
+            gkey[g] = B.key;
+            int ix, iy, iz;
+            demorton(B.key, ix, iy, iz);
+            gctr[3 * g] = h->root_min[0] + (ix + 0.5) * h->lev[l].w;
+            gctr[3 * g + 1] = h->root_min[1] + (iy + 0.5) * h->lev[l].w;
+            gctr[3 * g + 2] = h->root_min[2] + (iz + 0.5) * h->lev[l].w;
+            gpar[g] = l > 0 ? (int32_t)(h->lev[l - 1].off + B.parent) : -1;
+            if (!B.leaf && l < lmax) {
+                gcb[g] = (int32_t)(h->lev[l + 1].off + B.cb);
+                gce[g] = (int32_t)(h->lev[l + 1].off + B.ce);
+            }
+            gnb[g] = B.nb;
+            gne[g] = B.ne;
+            if (B.leaf) {
+                is_leaf[g] = 1;
+                leaves.emplace_back(B.nb, (int32_t)g);
+            }
+        }
+    std::sort(leaves.begin(), leaves.end());
+    const int64_t nl = (int64_t)leaves.size();
+    h->h_leaf_box.resize(nl);
+    std::vector<int32_t> node_leaf(N);
+    int32_t max_leaf = 0;
+    for (int64_t i = 0; i < nl; ++i) {
+        const int32_t g = leaves[i].second;
+        h->h_leaf_box[i] = g;
+        for (int32_t j = gnb[g]; j < gne[g]; ++j) node_leaf[j] = g;
+        max_leaf = std::max(max_leaf, gne[g] - gnb[g]);
+    }
+    h->max_leaf = max_leaf;
+    // box of level l at integer coordinates (ix, iy, iz), or -1
+    auto find = [&](int l, int ix, int iy, int iz) -> int64_t {
+        const int M = 1 << l;
+        if (ix < 0 || iy < 0 || iz < 0 || ix >= M || iy >= M || iz >= M) return -1;
+        const uint64_t kk = morton((uint32_t)ix, (uint32_t)iy, (uint32_t)iz);
+        const uint64_t *k0 = gkey.data() + h->lev[l].off, *k1 = k0 + h->lev[l].n;
+        const uint64_t *it = std::lower_bound(k0, k1, kk);
+        return (it != k1 && *it == kk) ? h->lev[l].off + (it - k0) : -1;
+    };
+    std::vector<int32_t> nstart(nl + 1, 0), nidx, rnb, rne;
+    int64_t pairs = 0;
+    for (int64_t i = 0; i < nl; ++i) {
+        const int32_t g = h->h_leaf_box[i];
+        int l = lmax;
+        while (h->lev[l].off > g) --l;
+        int ix, iy, iz;
+        demorton(gkey[g], ix, iy, iz);
+        std::vector<int64_t> src;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const int64_t q = find(l, ix + dx, iy + dy, iz + dz);
+                    if (q >= 0) src.push_back(q);
+                }
+        for (int la = l - 1; la >= 0; --la) {
+            const int sh = l - la, ax = ix >> sh, ay = iy >> sh, az = iz >> sh;
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        if (dx == 0 && dy == 0 && dz == 0) continue;
+                        const int64_t q = find(la, ax + dx, ay + dy, az + dz);
+                        if (q >= 0 && is_leaf[q]) src.push_back(q);
+                    }
+        }
+        // node ranges in node order, merged where they touch
+        std::sort(src.begin(), src.end(), [&](int64_t u, int64_t v) { return gnb[u] < gnb[v]; });
+        int64_t nsrc = 0;
+        for (size_t a = 0; a < src.size();) {
+            size_t b = a + 1;
+            while (b < src.size() && gnb[src[b]] == gne[src[b - 1]]) ++b;
+            const int32_t beg = gnb[src[a]], end = gne[src[b - 1]];
+            if (b == a + 1) {
+                nidx.push_back((int32_t)src[a]);
+            } else {
+                nidx.push_back((int32_t)(tot + (int64_t)rnb.size()));
+                rnb.push_back(beg);
+                rne.push_back(end);
+            }
+            nsrc += end - beg;
+            a = b;
+        }
+        nstart[i + 1] = (int32_t)nidx.size();
+        if (nstart[i + 1] - nstart[i] > NEAR_RANGES_MAX)
+            throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT,
+                              "adaptive octree: a leaf has " + std::to_string(nstart[i + 1] - nstart[i]) +
+                                  " direct-source node ranges (at most " + std::to_string(NEAR_RANGES_MAX) +
+                                  "); use a larger leaf_size or a smaller max_level"};
+        pairs += nsrc * (gne[g] - gnb[g]);
+    }
+    h->near_pairs = pairs - N;  // minus the self pairs
+    h->n_nbr = (int64_t)nidx.size();
+    h->n_range_boxes = (int64_t)rnb.size();
+    // device copies
+    const int64_t nr_all = tot + h->n_range_boxes;
+    h->box_key = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * tot);
+    h->box_ctr = (double *)dev_alloc(h, sizeof(double) * 3 * tot);
+    h->box_parent = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_cbeg = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_cend = (int32_t *)dev_alloc(h, sizeof(int32_t) * tot);
+    h->box_nbeg = (int32_t *)dev_alloc(h, sizeof(int32_t) * nr_all);
+    h->box_nend = (int32_t *)dev_alloc(h, sizeof(int32_t) * nr_all);
+    h->nbr_start = (int32_t *)dev_alloc(h, sizeof(int32_t) * (nl + 1));
+    h->nbr_idx = (int32_t *)dev_alloc(h, sizeof(int32_t) * std::max<size_t>(nidx.size(), 1));
+    h->node_leaf = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    gnb.insert(gnb.end(), rnb.begin(), rnb.end());
+    gne.insert(gne.end(), rne.begin(), rne.end());
+    CK(cudaMemcpyAsync(h->box_key, gkey.data(), sizeof(uint64_t) * tot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_ctr, gctr.data(), sizeof(double) * 3 * tot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_parent, gpar.data(), sizeof(int32_t) * tot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_cbeg, gcb.data(), sizeof(int32_t) * tot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_cend, gce.data(), sizeof(int32_t) * tot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_nbeg, gnb.data(), sizeof(int32_t) * nr_all, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->box_nend, gne.data(), sizeof(int32_t) * nr_all, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->nbr_start, nstart.data(), sizeof(int32_t) * (nl + 1), cudaMemcpyHostToDevice, s));
+    if (!nidx.empty())
+        CK(cudaMemcpyAsync(h->nbr_idx, nidx.data(), sizeof(int32_t) * nidx.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->node_leaf, node_leaf.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    finish_leaves(h, s);
+}
+
+// The paper's octree (App. C): uniform depth l_max, the smallest level >= 2 at which the mean
+// occupancy of the non-empty boxes is at most leaf_size; empty boxes dropped; all leaves at l_max;
+// Neighbor lists of the leaves (with the leaf itself).  key: the sorted Morton keys.
+void uniform_boxes(fmbem *h, const uint64_t *key, double side, int32_t *f, int32_t *fs, cudaStream_t s) {
     const int64_t N = h->N;
     const int TB = 256;
-    // root cube: centre of the bounding box, side 1.000001 x the largest extent
-    int nbb = (int)std::min<int64_t>(nblk(N, TB), 1024);
-    double *bb = (double *)dev_alloc(h, sizeof(double) * 6 * nbb);
-    k_bbox<<<nbb, TB, 0, s>>>(h->upos, N, bb);
-    CKL("k_bbox");
-    std::vector<double> hb(6 * nbb);
-    CK(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * 6 * nbb, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    dev_free(h, bb);
-    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-    for (int b = 0; b < nbb; ++b)
-        for (int q = 0; q < 3; ++q) { mn[q] = std::min(mn[q], hb[6 * b + q]); mx[q] = std::max(mx[q], hb[6 * b + 3 + q]); }
-    double ext = std::max(mx[0] - mn[0], std::max(mx[1] - mn[1], mx[2] - mn[2]));
-    if (!(ext > 0)) throw fmbem_error{FMBEM_ERR_INVALID_MESH, "all nodes coincide"};
-    double side = 1.000001 * ext;
-    for (int q = 0; q < 3; ++q) h->root_min[q] = 0.5 * (mn[q] + mx[q]) - 0.5 * side;
-    h->root_w = side;
-
-    // keys and stable sort
-    uint64_t *key = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * N), *key2 = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * N);
-    int32_t *idx = (int32_t *)dev_alloc(h, sizeof(int32_t) * N), *idx2 = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
-    int32_t *f = (int32_t *)dev_alloc(h, sizeof(int32_t) * N), *fs = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
-    k_keys<<<nblk(N, TB), TB, 0, s>>>(h->upos, N, h->root_min[0], h->root_min[1], h->root_min[2],
-                                      (double)(1 << KEY_LEVELS) / side, key, idx);
-    CKL("k_keys");
-    for (int bit = 0; bit < 3 * KEY_LEVELS; ++bit) {
-        k_bitflag<<<nblk(N, TB), TB, 0, s>>>(key, N, bit, f);
-        int64_t nzero = scan_exclusive(h, f, fs, N, s);
-        k_bitscatter<<<nblk(N, TB), TB, 0, s>>>(key, idx, fs, N, nzero, bit, key2, idx2);
-        CKL("k_bitscatter");
-        std::swap(key, key2);
-        std::swap(idx, idx2);
-    }
-    h->perm = idx;
-    dev_free(h, idx2);
-
     // node -> box maps of every level up to KEY_LEVELS, and max occupancy per level
     std::vector<int32_t *> node_box(KEY_LEVELS + 1, nullptr), box_start(KEY_LEVELS + 1, nullptr);
     std::vector<uint64_t *> lkey(KEY_LEVELS + 1, nullptr);
@@ -474,12 +676,75 @@ void build_tree(fmbem *h, cudaStream_t s) {
         dev_free(h, cnt);
         dev_free(h, pc);
     }
+    // leaf of every sorted node
+    h->node_leaf = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    CK(cudaMemcpyAsync(h->node_leaf, node_box[lmax], sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    k_add_offset<<<nblk(N, TB), TB, 0, s>>>(h->node_leaf, N, (int32_t)h->lev[lmax].off);
+    CKL("k_add_offset");
+
+    // the leaves: the boxes of level l_max, in node order
+    h->h_leaf_box.resize(h->lev[h->lmax].n);
+    for (int64_t i = 0; i < h->lev[h->lmax].n; ++i) h->h_leaf_box[i] = (int32_t)(h->lev[h->lmax].off + i);
+    finish_leaves(h, s);
+    for (int l = 0; l <= KEY_LEVELS; ++l) {
+        if (node_box[l]) dev_free(h, node_box[l]);
+        if (box_start[l]) dev_free(h, box_start[l]);
+        if (lkey[l]) dev_free(h, lkey[l]);
+    }
+}
+
+}  // namespace
+
+void build_tree(fmbem *h, cudaStream_t s) {
+    const int64_t N = h->N;
+    const int TB = 256;
+    // root cube: centre of the bounding box, side 1.000001 x the largest extent
+    int nbb = (int)std::min<int64_t>(nblk(N, TB), 1024);
+    double *bb = (double *)dev_alloc(h, sizeof(double) * 6 * nbb);
+    k_bbox<<<nbb, TB, 0, s>>>(h->upos, N, bb);
+    CKL("k_bbox");
+    std::vector<double> hb(6 * nbb);
+    CK(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * 6 * nbb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dev_free(h, bb);
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int b = 0; b < nbb; ++b)
+        for (int q = 0; q < 3; ++q) { mn[q] = std::min(mn[q], hb[6 * b + q]); mx[q] = std::max(mx[q], hb[6 * b + 3 + q]); }
+    double ext = std::max(mx[0] - mn[0], std::max(mx[1] - mn[1], mx[2] - mn[2]));
+    if (!(ext > 0)) throw fmbem_error{FMBEM_ERR_INVALID_MESH, "all nodes coincide"};
+    double side = 1.000001 * ext;
+    for (int q = 0; q < 3; ++q) h->root_min[q] = 0.5 * (mn[q] + mx[q]) - 0.5 * side;
+    h->root_w = side;
+
+    // keys and stable sort
+    uint64_t *key = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * N), *key2 = (uint64_t *)dev_alloc(h, sizeof(uint64_t) * N);
+    int32_t *idx = (int32_t *)dev_alloc(h, sizeof(int32_t) * N), *idx2 = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    int32_t *f = (int32_t *)dev_alloc(h, sizeof(int32_t) * N), *fs = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
+    k_keys<<<nblk(N, TB), TB, 0, s>>>(h->upos, N, h->root_min[0], h->root_min[1], h->root_min[2],
+                                      (double)(1 << KEY_LEVELS) / side, key, idx);
+    CKL("k_keys");
+    for (int bit = 0; bit < 3 * KEY_LEVELS; ++bit) {
+        k_bitflag<<<nblk(N, TB), TB, 0, s>>>(key, N, bit, f);
+        int64_t nzero = scan_exclusive(h, f, fs, N, s);
+        k_bitscatter<<<nblk(N, TB), TB, 0, s>>>(key, idx, fs, N, nzero, bit, key2, idx2);
+        CKL("k_bitscatter");
+        std::swap(key, key2);
+        std::swap(idx, idx2);
+    }
+    h->perm = idx;
+    dev_free(h, idx2);
+
+    if (h->adaptive) adaptive_boxes(h, key, side, s);
+    else uniform_boxes(h, key, side, f, fs, s);
+    const int lmax = h->lmax;
+    const int64_t tot = h->nbox;
+
     // FF lists on levels 2..lmax (global CSR over all boxes; empty for levels 0..1)
     {
         int32_t *cnt = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tot + 1));
         CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (tot + 1), s));
         for (int l = 2; l <= lmax; ++l)
-            k_farfield<<<nblk(nbl[l], TB), TB, 0, s>>>(nbl[l], h->lev[l].off, l, h->box_key, h->lev[l - 1].off, nbl[l - 1],
+            k_farfield<<<nblk(h->lev[l].n, TB), TB, 0, s>>>(h->lev[l].n, h->lev[l].off, l, h->box_key, h->lev[l - 1].off, h->lev[l - 1].n,
                                                        h->box_cbeg, h->box_cend, nullptr, cnt + h->lev[l].off, nullptr,
                                                        nullptr);
         CKL("k_farfield count");
@@ -489,7 +754,7 @@ void build_tree(fmbem *h, cudaStream_t s) {
         h->ff_src = (int32_t *)dev_alloc(h, sizeof(int32_t) * std::max<int64_t>(total, 1));
         h->ff_off = (int16_t *)dev_alloc(h, sizeof(int16_t) * std::max<int64_t>(total, 1));
         for (int l = 2; l <= lmax; ++l)
-            k_farfield<<<nblk(nbl[l], TB), TB, 0, s>>>(nbl[l], h->lev[l].off, l, h->box_key, h->lev[l - 1].off, nbl[l - 1],
+            k_farfield<<<nblk(h->lev[l].n, TB), TB, 0, s>>>(h->lev[l].n, h->lev[l].off, l, h->box_key, h->lev[l - 1].off, h->lev[l - 1].n,
                                                        h->box_cbeg, h->box_cend, h->ff_start + h->lev[l].off, nullptr,
                                                        h->ff_src, h->ff_off);
         CKL("k_farfield fill");
@@ -552,12 +817,6 @@ void build_tree(fmbem *h, cudaStream_t s) {
         dev_free(h, ocnt);
     }
 
-    // leaf of every sorted node
-    h->node_leaf = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
-    CK(cudaMemcpyAsync(h->node_leaf, node_box[lmax], sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
-    k_add_offset<<<nblk(N, TB), TB, 0, s>>>(h->node_leaf, N, (int32_t)h->lev[lmax].off);
-    CKL("k_add_offset");
-
     // sorted geometry
     h->iperm = (int32_t *)dev_alloc(h, sizeof(int32_t) * N);
     h->pos = (double *)dev_alloc(h, sizeof(double) * 3 * N);
@@ -572,11 +831,6 @@ void build_tree(fmbem *h, cudaStream_t s) {
                                                  h->iperm, h->pos_hi, h->pos_lo, h->nrm_f, h->src_rec);
     CKL("k_sorted_geometry");
     CK(cudaStreamSynchronize(s));
-    for (int l = 0; l <= KEY_LEVELS; ++l) {
-        if (node_box[l]) dev_free(h, node_box[l]);
-        if (box_start[l]) dev_free(h, box_start[l]);
-        if (lkey[l]) dev_free(h, lkey[l]);
-    }
     dev_free(h, key);
     dev_free(h, key2);
     dev_free(h, f);

@@ -182,3 +182,41 @@ def test_fmm_tol_validated_before_device_work():
         with pytest.raises(fm.FMBEMError) as e:
             _create(V, F, D, fmm_tol=bad)
         assert e.value.status == 1, bad
+
+
+def test_adaptive_option_validated_before_device_work():
+    """The octree is the paper's uniform tree by default; values other than 0 and 1 are refused
+    before any device work."""
+    o = fm.fmbem_default_options()
+    assert o.adaptive == 0
+    V, F, D = fi.icosphere(1)
+    for bad in (-1, 2):
+        with pytest.raises(fm.FMBEMError) as e:
+            _create(V, F, D, adaptive=bad)
+        assert e.value.status == 1, bad
+
+
+def test_options_struct_layout_matches_the_header(tmp_path):
+    """The binding's Options structure has the size and field offsets of the C fmbem_options
+    (a C program prints them), so every option reaches the library as set."""
+    import os
+    import shutil
+    import subprocess
+    import ctypes
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = [n for n, _ in fm.Options._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"fmbem.h\"\nint main(void) {\n"
+                   "    printf(\"%zu\\n\", sizeof(fmbem_options));\n" +
+                   "".join(f"    printf(\"%zu\\n\", offsetof(fmbem_options, {n}));\n" for n in names) +
+                   "    return 0;\n}\n")
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", include, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout.split()]
+    assert out[0] == ctypes.sizeof(fm.Options)
+    assert out[1:] == [getattr(fm.Options, n).offset for n in names]
