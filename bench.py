@@ -381,6 +381,41 @@ def phase_traffic(workload, precision, nr, phase):
     return t["bytes"]
 
 
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def gmres_roofline(N, iters, restart, ms_total, matvec_ms):
+    """Roofline of the plain FP64 GMRES(m) work outside the products, per Arnoldi step: the
+    solve's time less its products (iters Arnoldi products + one true residual per cycle + the
+    final one), over the algorithmic bytes and FP64 flops of the steps it ran.  Step j (j + 1
+    basis vectors, b = 96 bytes per node per vector): preconditioner (V_j, the 6 x 6 LU factors,
+    z: 2b + 582), classical Gram-Schmidt twice (dots: (j + 2) b, subtract: (j + 3) b, each pass),
+    norm (b) and scale (2b); FP64 flops 2 passes x 2 x (j + 1) x 6 complex MACs (8 flops) per
+    node plus the LU solve (288)."""
+    b = 96.0
+    js = [k % restart for k in range(iters)]
+    cycles = (iters + restart - 1) // restart
+    step_bytes = sum(582.0 + b * (4 * j + 15) for j in js) * N / max(iters, 1)
+    step_flops = sum(192.0 * (j + 1) + 288.0 for j in js) * N / max(iters, 1)
+    products = iters + cycles + 1
+    over_ms = (ms_total - products * matvec_ms) / max(iters, 1)
+    hbm, hsrc = hbm_peak()
+    ach_gbs = step_bytes / (over_ms * 1e-3) / 1e9 if over_ms > 0 else None
+    ach_tf = step_flops / (over_ms * 1e-3) / 1e12 if over_ms > 0 else None
+    t_hbm, t_fp64 = step_bytes / (hbm * 1e9), step_flops / (PEAK_TFLOPS["fp64"] * 1e12)
+    return dict(bound="fp64" if t_fp64 > t_hbm else "hbm", ms_per_step=over_ms, products=products,
+                bytes_per_step=step_bytes, flops_per_step=step_flops,
+                achieved_gbs=ach_gbs, hbm_peak_gbs=hbm, hbm_frac=ach_gbs / hbm if ach_gbs else None,
+                achieved_fp64_tflops=ach_tf, fp64_frac=ach_tf / PEAK_TFLOPS["fp64"] if ach_tf else None,
+                bound_ms_per_step=1e3 * max(t_hbm, t_fp64),
+                peak_source=f"HBM {hsrc} copy bandwidth; FP64 measured FMA throughput (self-written probe)")
+
+
 def tensor_peak_bf16x3():
     """Effective tensor peak of the BF16x3 form: the measured cuBLAS BF16 burst rate over the three
     bf16 products that carry one algorithmic product."""
@@ -526,7 +561,8 @@ def run_batched(args, world, flush):
         torch.cuda.synchronize()
         t_plain = time.perf_counter() - s0
         solve["plain_fp64_single_rhs"] = dict(tol=1e-4, ms=1e3 * t_plain, iters=int(its.max()), relres=float(rr.max()),
-                                              status=int(st), restart=restart)
+                                              status=int(st), restart=restart,
+                                              gmres=gmres_roofline(N, int(its.max()), restart, 1e3 * t_plain, ms1))
         gp.close()
         del gp
         # batched: inner GMRES(100) with the BF16x3 tensor-core operator to 1e-2 and a
@@ -821,6 +857,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             solve[label] = dict(tol=1e-4, ms=1e3 * (time.perf_counter() - s0), iters=int(its.max()),
                                 relres=float(rr.max()), status=int(st), restart=args.restart, inner_tol=itol)
+            if sp == fm.FP64 and nr == 1:
+                solve[label]["gmres"] = gmres_roofline(N, int(its.max()), args.restart, solve[label]["ms"], ms_step)
             h2.close()
 
     gradients = run_gradients() if args.gradients and rank == 0 else None
