@@ -330,8 +330,8 @@ void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool b
 bool m2l_ofs_supported(const fmbem *h);
 void build_ofs_tables(fmbem *h, cudaStream_t s);
 void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s);
-void run_m2l_ofs(fmbem *h, const float *C, float *Y, int l, int d, int64_t nr, int64_t c0, int64_t nch,
-                 int64_t e_first, cudaStream_t s);
+int64_t ofs_y_dom(const fmbem *h, int64_t nr);
+void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
 void pack_rot_tables_mm(fmbem *h, cudaStream_t s);
 void build_rot_mm_lists(fmbem *h, cudaStream_t s);

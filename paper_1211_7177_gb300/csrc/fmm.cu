@@ -2849,6 +2849,15 @@ static size_t ybuf_need(const fmbem *h, int64_t ncol, size_t elem) {
     return elem * (size_t)mp * (size_t)ncol * h->p2;
 }
 
+// per-pair results of the one-launch offset-stationary M2L (BF16x3, few columns): every level's
+// pairs for every multipole domain, then one level's rotation-form L2L entries
+static size_t ofs_ybuf_need(const fmbem *h, int64_t nr) {
+    int64_t ne = 1;
+    for (int l = 2; l <= h->lmax; ++l)
+        if (!h->h_rmm_first.empty()) ne = std::max(ne, h->h_rmm_first[l + 1] - h->h_rmm_first[l]);
+    return sizeof(float) * ((size_t)(h->Jf + 1) * ofs_y_dom(h, nr) + (size_t)ne * 3 * nr * 2 * h->p2);
+}
+
 static void ensure_scratch(fmbem *h, int64_t nr, int precision, bool pair_results = true) {
     const size_t cb = sizeof(c64);
     if (h->scratch_rhs < nr) {
@@ -2863,7 +2872,8 @@ static void ensure_scratch(fmbem *h, int64_t nr, int precision, bool pair_result
     // this call, so that a few-column call after a many-column one still takes the chunked path
     const bool many = rot_many_path(h, nr, precision == FMBEM_FP64);
     if (pair_results && (3 * nr <= 24 || many)) {
-        const size_t need = ybuf_need(h, many ? rot_many_cols(h) : 3 * nr, cb);
+        size_t need = ybuf_need(h, many ? rot_many_cols(h) : 3 * nr, cb);
+        if (precision == FMBEM_BF16X3 && h->Aofs != nullptr && 3 * nr <= 24) need = std::max(need, ofs_ybuf_need(h, nr));
         if (h->ybuf == nullptr || h->ybuf_bytes < need) {
             if (h->ybuf) dev_free(h, h->ybuf);
             h->ybuf = nullptr;
@@ -3036,18 +3046,27 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
         const bool use_rot_mm = use_rot && h->rmm_chunk_beg != nullptr;
         cx<R> *Y = (cx<R> *)h->ybuf;
         // BF16x3 with few columns: the S|R products of each offset chunk on the tensor cores
-        const bool ofs = tensor_mode == 2 && f32 && h->Aofs != nullptr && h->chunk_pairs != nullptr && 3 * nr <= MAXC;
-        if (ofs) split_expansions_bf16(h, (float *)C, nr, s);
+        // (all levels and domains in one launch first: the S|R products read only C; the pair
+        // results of every level then wait in Y[d][CSR position], and the rotation form's L2L
+        // results go after them)
+        const bool ofs = tensor_mode == 2 && f32 && h->Aofs != nullptr && h->chunk_pairs != nullptr && 3 * nr <= MAXC &&
+                         h->ybuf_bytes >= ofs_ybuf_need(h, nr);
+        if (ofs) {
+            split_expansions_bf16(h, (float *)C, nr, s);
+            run_m2l_ofs(h, (const float *)C, (float *)Y, nr, s);
+        }
+        const int64_t y_dom = ofs ? ofs_y_dom(h, nr) / 2 : 0;  // in complex values
         for (int l = 2; l <= lmax; ++l) {
             const LevelInfo &Lv = h->lev[l];
             const int64_t c0 = h->h_chunk_first[l], nch = h->h_chunk_first[l + 1] - c0;
-            const int64_t e_first = h->h_pair_first[l];
             for (int d = 0; d <= J; ++d)
                 for (int col0 = 0; col0 < 3 * nr; col0 += ncol) {
                     const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
+                    const int64_t e_first = ofs ? 0 : h->h_pair_first[l];
+                    cx<R> *Yd = ofs ? Y + d * y_dom : Y;
                     if (nch > 0) {
                         if (ofs)
-                            run_m2l_ofs(h, (const float *)C, (float *)Y, l, d, nr, c0, nch, e_first, s);
+                            ;  // done above
                         else if (use_rot)
                             launch_rot<R>(rl, nch, s, c0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->chunk_beg,
                                           h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD,
@@ -3069,7 +3088,7 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
                     if (use_rot_mm && l >= 3) {
                         const int64_t lc0 = h->h_rmm_chunk_first[l], lnch = h->h_rmm_chunk_first[l + 1] - lc0;
                         ll_first = h->h_rmm_first[l];
-                        Yll = Y + (h->h_pair_first[l + 1] - e_first) * nc * p2;
+                        Yll = ofs ? Y + (J + 1) * y_dom : Y + (h->h_pair_first[l + 1] - e_first) * nc * p2;
                         launch_rot<R>(rl, lnch, s, lc0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->rmm_chunk_beg,
                                       h->rmm_chunk_cnt, h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP,
                                       RZll, D, Yll, ll_first);
@@ -3078,7 +3097,7 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
                     const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
                     k_l2l_reduce<R><<<(unsigned)Lv.n, rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
                         Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll,
-                        Y, e_first, D, Yll, h->rmm_entry, ll_first);
+                        Yd, e_first, D, Yll, h->rmm_entry, ll_first);
                     CKL("k_l2l_reduce");
                 }
         }
@@ -3137,7 +3156,7 @@ template <typename R>
 static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
                         int tensor_mode = 0) {
     const int64_t N = h->N;
-    const int p2 = h->p2, lmax = h->lmax, J = h->Jf;  // multipole passes over domains 0..Jf
+    const int p2 = h->p2, J = h->Jf;  // multipole passes over domains 0..Jf
     const bool f32 = sizeof(R) == 4;
     cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
     const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;
@@ -3268,7 +3287,7 @@ template <typename R>
 static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t s, const DomainConsts *dc,
                          int tensor_mode = 0) {
     const int64_t N = h->N;
-    const int p2 = h->p2, lmax = h->lmax, J = h->Jf;  // multipole passes over domains 0..Jf
+    const int p2 = h->p2, J = h->Jf;  // multipole passes over domains 0..Jf
     const bool f32 = sizeof(R) == 4;
     cx<R> *dens = (cx<R> *)h->dens, *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
     const cx<R> *Bp2m = f32 ? (const cx<R> *)h->B_p2m32 : (const cx<R> *)h->B_p2m64;

@@ -490,16 +490,26 @@ int tc_kblocks(int p2) { return (2 * p2 + KBLK - 1) / KBLK; }
 constexpr int OFS_STAGES = 4;
 constexpr int OFS_M = 128;
 
+// the work of one launch: every chunk of levels 2..l_max (chunk indices chunk0 + [0, nch)) for
+// every domain 0..ndom-1, unit v = d * nch + chunk; Y[d][CSR position][column][2 p^2] floats
+constexpr int OFS_MAX_LEVELS = 12;
 struct OfsLevel {
     int64_t nbox;
     int ncols;      // columns per pair (3 n_rhs) = rows of C per box
     int p2, kblocks, np;
-    int d;
-    int64_t e_first;
+    int lmax, ndom;
     int ppp;        // pairs per pass: floor(128 / ncols)
-    int64_t amat0;  // first S|R image of this (domain, level)
     uint32_t tmem_cols;
+    int64_t y_dom;  // floats of Y per domain
+    int64_t level_first[OFS_MAX_LEVELS + 1];  // first chunk (relative to chunk0) of each level
 };
+
+// level of relative chunk index ckl (the levels' chunk ranges are contiguous and ascending)
+__device__ __forceinline__ int ofs_level(const OfsLevel &P, int64_t ckl) {
+    int l = 2;
+    while (l < P.lmax && P.level_first[l + 1] <= ckl) ++l;
+    return l;
+}
 
 // Persistent form: each CTA walks the chunks blockIdx.x, blockIdx.x + gridDim.x, ... as a sequence
 // of (chunk, pass) tiles; warps 0-3 gather (warp w fills ring slot w of every fourth K block of the
@@ -523,7 +533,8 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
     const uint32_t b_half = (uint32_t)P.np * 64u;  // one bf16 part of an S|R K block
     const uint32_t stage_bytes = 2u * OFS_M * 64u + 2u * b_half;
     const int twop2 = 2 * P.p2;
-    const bool any = (int64_t)blockIdx.x < nch;
+    const int64_t nunit = nch * P.ndom;
+    const bool any = (int64_t)blockIdx.x < nunit;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OFS_STAGES; ++s) {
@@ -552,8 +563,10 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
         int64_t last_issued = -1;  // this warp's last unit whose bulk copy was issued
         int64_t u = 0;             // unit (K block of a tile) counter of the CTA's sequence
         bool stop = false;
-        for (int64_t ckl = blockIdx.x; ckl < nch && !stop; ckl += gridDim.x) {
-            const int64_t ck = chunk0 + ckl;
+        for (int64_t v = blockIdx.x; v < nunit && !stop; v += gridDim.x) {
+            const int d = (int)(v / nch);
+            const int64_t ckl = v - (int64_t)d * nch, ck = chunk0 + ckl;
+            const int64_t amat = ((int64_t)d * (P.lmax + 1) + ofs_level(P, ckl)) * 316 + chunk_off[ck];
             // the chunk's (source box, CSR position) pairs, one per lane, and its size
             const int2 pr = chunk_pairs[ck * 32 + lane];
             const int cnt = P.ppp >= 32 ? 32 : chunk_cnt[ck];  // one pass holds every chunk when ppp >= 32
@@ -568,7 +581,7 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
                             const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
                             const int src = __shfl_sync(0xffffffffu, pr.x, jj & 31);
                             rowoff[warp][m] = (m < P.ppp * P.ncols && jj < 32 && src >= 0)
-                                                  ? (((int64_t)P.d * P.nbox + src) * P.ncols + c) * twop2
+                                                  ? (((int64_t)d * P.nbox + src) * P.ncols + c) * twop2
                                                   : (int64_t)-1;
                         }
                         __syncwarp();
@@ -585,7 +598,7 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
                     const uint32_t sM = sbase + (uint32_t)warp * stage_bytes, sB = sM + 2u * OFS_M * 64u;
                     if (lane == 0) {
                         const __nv_bfloat16 *Amat =
-                            Aofs + ((P.amat0 + chunk_off[ck]) * (int64_t)P.kblocks + kb) * (int64_t)P.np * 64;
+                            Aofs + (amat * (int64_t)P.kblocks + kb) * (int64_t)P.np * 64;
                         mbar_arrive_expect_tx(&full[warp], 2u * b_half);
                         bulk_load(sB, Amat, 2u * b_half, &full[warp]);
                         last_issued = u;
@@ -619,7 +632,8 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
             const uint32_t idesc = idesc_bf16(P.np);
             bool ok = true;
             int64_t u = 0, t = 0;
-            for (int64_t ckl = blockIdx.x; ckl < nch && ok && !s_abort; ckl += gridDim.x) {
+            for (int64_t v = blockIdx.x; v < nunit && ok && !s_abort; v += gridDim.x) {
+                const int64_t ckl = v % nch;
                 const int passes = P.ppp >= 32 ? 1 : (chunk_cnt[chunk0 + ckl] + P.ppp - 1) / P.ppp;
                 for (int pass = 0; pass < passes && ok && !s_abort; ++pass, ++t) {
                     const int buf = (int)(t & 1);
@@ -653,8 +667,10 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
         const int ew = (warp - 5 + 1) & 3;  // the tensor-memory lane quarter this warp may read
         int64_t t = 0;
         bool stop = false;
-        for (int64_t ckl = blockIdx.x; ckl < nch && !stop; ckl += gridDim.x) {
-            const int64_t ck = chunk0 + ckl;
+        for (int64_t v = blockIdx.x; v < nunit && !stop; v += gridDim.x) {
+            const int d = (int)(v / nch);
+            const int64_t ck = chunk0 + (v - (int64_t)d * nch);
+            float *Yd = Y + (int64_t)d * P.y_dom;
             const int2 pr = chunk_pairs[ck * 32 + lane];
             const int passes = P.ppp >= 32 ? 1 : (chunk_cnt[ck] + P.ppp - 1) / P.ppp;
             for (int pass = 0; pass < passes; ++pass, ++t) {
@@ -671,7 +687,7 @@ __global__ void __launch_bounds__(OFS_THREADS, 1)
                 const int jj = pass * P.ppp + m / P.ncols, c = m % P.ncols;
                 const int e = __shfl_sync(0xffffffffu, pr.y, jj & 31);
                 const bool valid = m < P.ppp * P.ncols && jj < 32 && e >= 0;
-                float *out = valid ? Y + (((int64_t)e - P.e_first) * P.ncols + c) * twop2 : nullptr;
+                float *out = valid ? Yd + ((int64_t)e * P.ncols + c) * twop2 : nullptr;
                 for (int c0 = 0; c0 < P.np; c0 += 16) {
                     uint32_t v[16];
                     const uint32_t taddr = tmem + (uint32_t)buf * P.tmem_cols + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0;
@@ -877,23 +893,39 @@ void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s) {
     CKL("k_split_bf16");
 }
 
-// one launch of k_m2l_ofs over the nch chunks from c0 of level l, domain d; Y as k_l2l_reduce reads it
-void run_m2l_ofs(fmbem *h, const float *C, float *Y, int l, int d, int64_t nr, int64_t c0, int64_t nch,
-                 int64_t e_first, cudaStream_t s) {
+// one launch of k_m2l_ofs over every chunk of levels 2..l_max and every domain 0..Jf: the M2L
+// of all levels at once (they read only the multipole expansions), into Y[d][CSR position]
+// (Y + d * ofs_y_dom(h, nr) floats, the layout k_l2l_reduce reads with e_first = 0)
+int64_t ofs_y_dom(const fmbem *h, int64_t nr) { return std::max<int64_t>(h->n_ff, 1) * 3 * nr * 2 * h->p2; }
+
+void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s) {
+    if (h->lmax + 1 > OFS_MAX_LEVELS) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many octree levels"};
+    const int64_t c0 = h->h_chunk_first[2], nch = h->h_chunk_first[h->lmax + 1] - c0;
     if (nch <= 0) return;
     const int p2 = h->p2, kb = tc_kblocks(p2), np = ofs_np(p2);
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * 3 * nr * 2 * p2;
     const __nv_bfloat16 *Chi = (const __nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
     uint32_t tcols = 32;  // one accumulator; two are allocated (2 x 256 columns at most)
     while ((int)tcols < np) tcols <<= 1;
-    const OfsLevel P{h->nbox, (int)(3 * nr), p2, kb, np, d, e_first, (int)(OFS_M / (3 * nr)),
-                     ((int64_t)d * (h->lmax + 1) + l) * 316, tcols};
+    OfsLevel P{};
+    P.nbox = h->nbox;
+    P.ncols = (int)(3 * nr);
+    P.p2 = p2;
+    P.kblocks = kb;
+    P.np = np;
+    P.lmax = h->lmax;
+    P.ndom = h->Jf + 1;
+    P.ppp = (int)(OFS_M / (3 * nr));
+    P.tmem_cols = tcols;
+    P.y_dom = ofs_y_dom(h, nr);
+    for (int l = 0; l <= OFS_MAX_LEVELS; ++l)
+        P.level_first[l] = l <= h->lmax + 1 ? std::max<int64_t>(h->h_chunk_first[std::max(l, 2)] - c0, 0) : nch;
     const size_t smem = (size_t)OFS_STAGES * (2 * OFS_M * 64 + 2 * (size_t)np * 64) + 1024;
     CK(cudaFuncSetAttribute(k_m2l_ofs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t grid = std::min<int64_t>(nch, nsm);  // one persistent CTA per SM
+    const int64_t grid = std::min<int64_t>(nch * P.ndom, nsm);  // one persistent CTA per SM
     k_m2l_ofs<<<(unsigned)grid, OFS_THREADS, smem, s>>>(P, c0, nch, h->chunk_cnt, h->chunk_off,
                                                          (const int2 *)h->chunk_pairs, Chi, Clo,
                                                          (const __nv_bfloat16 *)h->Aofs, Y, h->tc_err);
