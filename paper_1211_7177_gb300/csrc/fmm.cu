@@ -393,10 +393,12 @@ __global__ void k_down(int64_t off, int l, int lmax, int64_t nr, int p2, int64_t
 // TSM: the translation matrix is staged in shared memory; otherwise (large p in double
 // precision) it is read from L2, coalesced across the rows, and shared memory holds the columns.
 template <typename R, int MAXC, bool TSM>
-__global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0,
+__global__ void k_m2l_chunks(int64_t chunk0, int l, int lmax, int d0, int64_t nr, int p2, int64_t nbox, int col0,
                              int ncol, int pc, int cg, const int32_t *chunk_beg, const int32_t *chunk_cnt,
                              const int16_t *chunk_off, const int32_t *pair_e, const int32_t *ff_src,
-                             const cx<R> *Tm2l, const cx<R> *C, cx<R> *Y, int64_t e_first) {
+                             const cx<R> *Tm2l, const cx<R> *C, cx<R> *Y, int64_t e_first, int64_t y_dstride) {
+    const int d = d0 + (int)blockIdx.y;  // domain: one grid row per domain, each with its own Y block
+    Y += (int64_t)blockIdx.y * y_dstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *Tsh = reinterpret_cast<cx<R> *>(smem_raw);  // [k][r]
     cx<R> *Xs = Tsh + (TSM ? p2 * p2 : 0);              // [pair * ncol + col][k]
@@ -492,12 +494,14 @@ __device__ __forceinline__ int slot_by_order(int p, int k) {
     return 0;
 }
 template <typename R, int MAXC>
-__global__ void __launch_bounds__(512) k_m2l_rot(int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox,
+__global__ void __launch_bounds__(512) k_m2l_rot(int64_t chunk0, int l, int lmax, int d0, int64_t nr, int p, int64_t nbox,
                                                  int col0, int ncol, int pc, int cg, const int32_t *chunk_beg,
                                                  const int32_t *chunk_cnt, const int16_t *chunk_off, const int32_t *pair_e,
                                                  const int32_t *ff_src, const int8_t *tidx, int n_tlen, const R *RD,
                                                  const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y,
-                                                 int64_t e_first) {
+                                                 int64_t e_first, int64_t y_dstride) {
+    const int d = d0 + (int)blockIdx.y;  // domain: one grid row per domain, each with its own Y block
+    Y += (int64_t)blockIdx.y * y_dstride;
     const int p2 = p * p;
     const int nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -666,10 +670,12 @@ constexpr int ROTC_S = ROTC_N + 1;  // row stride of the staged coefficients (co
 constexpr int ROTC_WARPS = 16;
 template <typename R>
 __global__ void __launch_bounds__(32 * ROTC_WARPS) k_m2l_rot_cols(
-    int64_t chunk0, int l, int lmax, int d, int64_t nr, int p, int64_t nbox, int col0, int ncol, int pc, int cg,
+    int64_t chunk0, int l, int lmax, int d0, int64_t nr, int p, int64_t nbox, int col0, int ncol, int pc, int cg,
     const int32_t *chunk_beg, const int32_t *chunk_cnt, const int16_t *chunk_off, const int32_t *pair_e,
     const int32_t *ff_src, const int8_t *tidx, int n_tlen, const R *RD, const cx<R> *RP, const cx<R> *RZ,
-    const cx<R> *C, cx<R> *Y, int64_t e_first) {
+    const cx<R> *C, cx<R> *Y, int64_t e_first, int64_t y_dstride) {
+    const int d = d0 + (int)blockIdx.y;  // domain: one grid row per domain, each with its own Y block
+    Y += (int64_t)blockIdx.y * y_dstride;
     const int p2 = p * p;
     const int nrot = rot_off(p), ncoax = p * (2 * p * p + 1) / 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -815,10 +821,13 @@ __global__ void __launch_bounds__(32 * ROTC_WARPS) k_m2l_rot_cols(
 // Threads: rows_pad x ct column groups; a thread owns columns cid * L2L_CPT .. + L2L_CPT - 1.
 constexpr int L2L_CPT = 3;
 template <typename R>
-__global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
+__global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d0, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
                              int ct, const int32_t *parent, const uint64_t *key, const int32_t *ff_start,
                              const cx<R> *Tll, const cx<R> *Y, int64_t e_first, cx<R> *D, const cx<R> *Yll,
-                             const int32_t *ll_entry, int64_t ll_first) {
+                             const int32_t *ll_entry, int64_t ll_first, int64_t y_dstride, int64_t yll_dstride) {
+    const int d = d0 + (int)blockIdx.y;  // domain: one grid row per domain, each with its own Y blocks
+    Y += (int64_t)blockIdx.y * y_dstride;
+    if (Yll) Yll += (int64_t)blockIdx.y * yll_dstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *X = reinterpret_cast<cx<R> *>(smem_raw);
     const int64_t g = off + blockIdx.x;
@@ -874,9 +883,11 @@ __global__ void k_l2l_reduce(int64_t off, int l, int lmax, int d, int64_t nr, in
 // Rotation-form M2M: the parent's multipole is the sum of its children's translated expansions,
 // C(g) = sum_{children ch} Y[entry(ch)], columns col0 .. col0 + ncol - 1 (Eq. 2.20).
 template <typename R>
-__global__ void k_mm_reduce(int64_t par_off, int d, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
+__global__ void k_mm_reduce(int64_t par_off, int d0, int64_t nr, int p2, int64_t nbox, int col0, int ncol,
                             const int32_t *cbeg, const int32_t *cend, const int32_t *entry, int64_t e_first,
-                            const cx<R> *Y, cx<R> *C) {
+                            const cx<R> *Y, cx<R> *C, int64_t y_dstride) {
+    const int d = d0 + (int)blockIdx.y;  // domain: one grid row per domain, each with its own Y block
+    Y += (int64_t)blockIdx.y * y_dstride;
     const int64_t g = par_off + blockIdx.x;
     if (cbeg[g] == cend[g]) return;  // a leaf of an adaptive tree: its multipole expansion is P2M's
     const int64_t nel = (int64_t)ncol * p2;
@@ -2840,13 +2851,15 @@ static bool rot_many_path(const fmbem *h, int64_t nr, bool fp64) {
 }
 // bytes of the per-pair M2L result buffer for ncol columns: the largest level's pair results,
 // then (rotation form) its child entries
+// per level, every multipole domain's pair results and rotation-form child entries (the passes
+// run the domains of a level in one launch each)
 static size_t ybuf_need(const fmbem *h, int64_t ncol, size_t elem) {
     int64_t mp = 1;
     for (int l = 2; l <= h->lmax; ++l) {
         const int64_t ne = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
         mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l] + ne);
     }
-    return elem * (size_t)mp * (size_t)ncol * h->p2;
+    return elem * (size_t)(h->Jf + 1) * (size_t)mp * (size_t)ncol * h->p2;
 }
 
 // per-pair results of the one-launch offset-stationary M2L (BF16x3, few columns): every level's
@@ -2855,7 +2868,7 @@ static size_t ofs_ybuf_need(const fmbem *h, int64_t nr) {
     int64_t ne = 1;
     for (int l = 2; l <= h->lmax; ++l)
         if (!h->h_rmm_first.empty()) ne = std::max(ne, h->h_rmm_first[l + 1] - h->h_rmm_first[l]);
-    return sizeof(float) * ((size_t)(h->Jf + 1) * ofs_y_dom(h, nr) + (size_t)ne * 3 * nr * 2 * h->p2);
+    return sizeof(float) * (size_t)(h->Jf + 1) * (ofs_y_dom(h, nr) + (size_t)ne * 3 * nr * 2 * h->p2);
 }
 
 static void ensure_scratch(fmbem *h, int64_t nr, int precision, bool pair_results = true) {
@@ -2928,21 +2941,24 @@ static RotLaunch rot_launch(fmbem *h, int ncol, size_t budget) {
     if (rl.ok) CK(cudaFuncSetAttribute(k_m2l_rot<R, ROT_MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rl.bytes));
     return rl;
 }
-// one launch of the rotation-form kernel chosen by rot_launch over nch chunks
+// one launch of the rotation-form kernel chosen by rot_launch over nch chunks, for domains
+// 0 .. ndom - 1 (grid rows), domain d's results at Y + d * y_dstride
 template <typename R>
-static void launch_rot(const RotLaunch &rl, int64_t nch, cudaStream_t s, int64_t c0, int l, int lmax, int d, int64_t nr,
-                       int p, int64_t nbox, int col0, int nc, const int32_t *cbeg, const int32_t *ccnt,
+static void launch_rot(const RotLaunch &rl, int64_t nch, cudaStream_t s, int64_t c0, int l, int lmax, int ndom,
+                       int64_t nr, int p, int64_t nbox, int col0, int nc, const int32_t *cbeg, const int32_t *ccnt,
                        const int16_t *coff, const int32_t *pair_e, const int32_t *src, const int8_t *tidx, int n_tlen,
-                       const R *RD, const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y, int64_t e_first) {
+                       const R *RD, const cx<R> *RP, const cx<R> *RZ, const cx<R> *C, cx<R> *Y, int64_t e_first,
+                       int64_t y_dstride) {
     if (nch <= 0) return;
+    const dim3 grid((unsigned)nch, (unsigned)ndom);
     if (rl.cols)
-        k_m2l_rot_cols<R><<<(unsigned)nch, 32 * ROTC_WARPS, rl.bytes, s>>>(c0, l, lmax, d, nr, p, nbox, col0, nc, rl.pc,
-                                                                          1, cbeg, ccnt, coff, pair_e, src, tidx, n_tlen,
-                                                                          RD, RP, RZ, C, Y, e_first);
+        k_m2l_rot_cols<R><<<grid, 32 * ROTC_WARPS, rl.bytes, s>>>(c0, l, lmax, 0, nr, p, nbox, col0, nc, rl.pc, 1, cbeg,
+                                                                  ccnt, coff, pair_e, src, tidx, n_tlen, RD, RP, RZ, C,
+                                                                  Y, e_first, y_dstride);
     else
-        k_m2l_rot<R, ROT_MAXC><<<(unsigned)nch, rl.rows * rl.cg, rl.bytes, s>>>(c0, l, lmax, d, nr, p, nbox, col0, nc,
-                                                                               rl.pc, rl.cg, cbeg, ccnt, coff, pair_e,
-                                                                               src, tidx, n_tlen, RD, RP, RZ, C, Y, e_first);
+        k_m2l_rot<R, ROT_MAXC><<<grid, rl.rows * rl.cg, rl.bytes, s>>>(c0, l, lmax, 0, nr, p, nbox, col0, nc, rl.pc,
+                                                                       rl.cg, cbeg, ccnt, coff, pair_e, src, tidx,
+                                                                       n_tlen, RD, RP, RZ, C, Y, e_first, y_dstride);
 }
 
 // M2M (Eq. 2.20) from level l_max up to level 2, on the multipole expansions in h->Cexp
@@ -2967,15 +2983,15 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
                 const LevelInfo &P = h->lev[l - 1];
                 const int64_t c0 = h->h_rmm_chunk_first[l], nch = h->h_rmm_chunk_first[l + 1] - c0;
                 const int64_t e_first = h->h_rmm_first[l];
-                for (int d = 0; d <= J; ++d) {
-                    launch_rot<R>(rl, nch, s, c0, l, lmax, d, nr, h->p, h->nbox, 0, ncol, h->rmm_chunk_beg,
-                                  h->rmm_chunk_cnt, h->rmm_chunk_mm, h->rmm_iota, h->rmm_child, h->rot_zero, 1, RD, RP,
-                                  RZmm, C, Y, e_first);
-                    CKL("k_m2l_rot (M2M)");
-                    k_mm_reduce<R><<<(unsigned)P.n, 128, 0, s>>>(P.off, d, nr, p2, h->nbox, 0, ncol, h->box_cbeg,
-                                                                h->box_cend, h->rmm_entry, e_first, Y, C);
-                    CKL("k_mm_reduce");
-                }
+                // all domains in one launch each: domain d's child entries at Y + d * ystr
+                const int64_t ystr = (h->h_rmm_first[l + 1] - e_first) * ncol * p2;
+                launch_rot<R>(rl, nch, s, c0, l, lmax, J + 1, nr, h->p, h->nbox, 0, ncol, h->rmm_chunk_beg,
+                              h->rmm_chunk_cnt, h->rmm_chunk_mm, h->rmm_iota, h->rmm_child, h->rot_zero, 1, RD, RP,
+                              RZmm, C, Y, e_first, ystr);
+                CKL("k_m2l_rot (M2M)");
+                k_mm_reduce<R><<<dim3((unsigned)P.n, (unsigned)(J + 1)), 128, 0, s>>>(
+                    P.off, 0, nr, p2, h->nbox, 0, ncol, h->box_cbeg, h->box_cend, h->rmm_entry, e_first, Y, C, ystr);
+                CKL("k_mm_reduce");
             }
             return;
         }
@@ -3056,50 +3072,52 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
             run_m2l_ofs(h, (const float *)C, (float *)Y, nr, s);
         }
         const int64_t y_dom = ofs ? ofs_y_dom(h, nr) / 2 : 0;  // in complex values
+        // per level and column window, all domains in one launch each (grid rows): domain d's pair
+        // results at Y + d * ystr, its rotation-form L2L entries after every domain's pair results
         for (int l = 2; l <= lmax; ++l) {
             const LevelInfo &Lv = h->lev[l];
             const int64_t c0 = h->h_chunk_first[l], nch = h->h_chunk_first[l + 1] - c0;
-            for (int d = 0; d <= J; ++d)
-                for (int col0 = 0; col0 < 3 * nr; col0 += ncol) {
-                    const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
-                    const int64_t e_first = ofs ? 0 : h->h_pair_first[l];
-                    cx<R> *Yd = ofs ? Y + d * y_dom : Y;
-                    if (nch > 0) {
-                        if (ofs)
-                            ;  // done above
-                        else if (use_rot)
-                            launch_rot<R>(rl, nch, s, c0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->chunk_beg,
-                                          h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD,
-                                          RP, RZ, C, Y, e_first);
-                        else if (tsm)
-                            k_m2l_chunks<R, MAXC, true><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
-                                c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt,
-                                h->chunk_off, h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
-                        else
-                            k_m2l_chunks<R, MAXC, false><<<(unsigned)nch, rows_pad * cg, smc, s>>>(
-                                c0, l, lmax, d, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt,
-                                h->chunk_off, h->pair_e, h->ff_src, Tm2l, C, Y, e_first);
-                    }
+            const int64_t nchild = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
+            for (int col0 = 0; col0 < 3 * nr; col0 += ncol) {
+                const int nc = (int)std::min<int64_t>(ncol, 3 * nr - col0);
+                const int64_t e_first = ofs ? 0 : h->h_pair_first[l];
+                const int64_t ystr = ofs ? y_dom : (h->h_pair_first[l + 1] - e_first) * nc * p2;
+                const dim3 grid((unsigned)nch, (unsigned)(J + 1));
+                if (nch > 0 && !ofs) {  // (the offset-stationary products ran above)
+                    if (use_rot)
+                        launch_rot<R>(rl, nch, s, c0, l, lmax, J + 1, nr, pp, h->nbox, col0, nc, h->chunk_beg,
+                                      h->chunk_cnt, h->chunk_off, h->pair_e, h->ff_src, h->rot_tidx, h->n_tlen, RD, RP,
+                                      RZ, C, Y, e_first, ystr);
+                    else if (tsm)
+                        k_m2l_chunks<R, MAXC, true><<<grid, rows_pad * cg, smc, s>>>(
+                            c0, l, lmax, 0, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt, h->chunk_off,
+                            h->pair_e, h->ff_src, Tm2l, C, Y, e_first, ystr);
+                    else
+                        k_m2l_chunks<R, MAXC, false><<<grid, rows_pad * cg, smc, s>>>(
+                            c0, l, lmax, 0, nr, p2, h->nbox, col0, nc, pc, cg, h->chunk_beg, h->chunk_cnt, h->chunk_off,
+                            h->pair_e, h->ff_src, Tm2l, C, Y, e_first, ystr);
                     CKL("k_m2l_chunks");
-                    // L2L in rotation form: the children of level l, by octant, from their parents'
-                    // local expansions, into the buffer after this level's pair results
-                    cx<R> *Yll = nullptr;
-                    int64_t ll_first = 0;
-                    if (use_rot_mm && l >= 3) {
-                        const int64_t lc0 = h->h_rmm_chunk_first[l], lnch = h->h_rmm_chunk_first[l + 1] - lc0;
-                        ll_first = h->h_rmm_first[l];
-                        Yll = ofs ? Y + (J + 1) * y_dom : Y + (h->h_pair_first[l + 1] - e_first) * nc * p2;
-                        launch_rot<R>(rl, lnch, s, lc0, l, lmax, d, nr, pp, h->nbox, col0, nc, h->rmm_chunk_beg,
-                                      h->rmm_chunk_cnt, h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP,
-                                      RZll, D, Yll, ll_first);
-                        CKL("k_m2l_rot (L2L)");
-                    }
-                    const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
-                    k_l2l_reduce<R><<<(unsigned)Lv.n, rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
-                        Lv.off, l, lmax, d, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll,
-                        Yd, e_first, D, Yll, h->rmm_entry, ll_first);
-                    CKL("k_l2l_reduce");
                 }
+                // L2L in rotation form: the children of level l, by octant, from their parents'
+                // local expansions
+                cx<R> *Yll = nullptr;
+                int64_t ll_first = 0;
+                const int64_t yll_str = nchild * nc * p2;
+                if (use_rot_mm && l >= 3) {
+                    const int64_t lc0 = h->h_rmm_chunk_first[l], lnch = h->h_rmm_chunk_first[l + 1] - lc0;
+                    ll_first = h->h_rmm_first[l];
+                    Yll = Y + (J + 1) * ystr;
+                    launch_rot<R>(rl, lnch, s, lc0, l, lmax, J + 1, nr, pp, h->nbox, col0, nc, h->rmm_chunk_beg,
+                                  h->rmm_chunk_cnt, h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP,
+                                  RZll, D, Yll, ll_first, yll_str);
+                    CKL("k_m2l_rot (L2L)");
+                }
+                const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
+                k_l2l_reduce<R><<<dim3((unsigned)Lv.n, (unsigned)(J + 1)), rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
+                    Lv.off, l, lmax, 0, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll, Y,
+                    e_first, D, Yll, h->rmm_entry, ll_first, ystr, yll_str);
+                CKL("k_l2l_reduce");
+            }
         }
     } else if (sizeof(cx<R>) * (size_t)(p2 * p2 + p2 * MT_COLS) <= budget &&
                ((p2 + 3) / 4) * (MT_COLS / 4) <= [] {
@@ -3418,12 +3436,7 @@ static void matvec_static_scratch(fmbem *h, const c64 *x, c64 *y, int64_t nr, cu
     const size_t b_exp = up(S * (size_t)(h->J + 1) * h->nbox * 3 * nr * h->p2);
     size_t b_y = 0;
     if (3 * nr <= 24) {
-        int64_t mp = 1;  // as in ensure_scratch: pair results, then the rotation form's child entries
-        for (int l = 2; l <= h->lmax; ++l) {
-            const int64_t ne = h->h_rmm_first.empty() ? 0 : h->h_rmm_first[l + 1] - h->h_rmm_first[l];
-            mp = std::max(mp, h->h_pair_first[l + 1] - h->h_pair_first[l] + ne);
-        }
-        b_y = up(S * (size_t)mp * 3 * nr * h->p2);
+        b_y = up(ybuf_need(h, 3 * nr, S));  // as ensure_scratch: every domain's pair results and child entries
     }
     const size_t need = b_dens + 2 * b_exp + b_y;
     if (need > STATIC_SCRATCH_BYTES)
