@@ -190,6 +190,7 @@ struct fmbem {
     // tensor-core (tcgen05, TF32) M2L tables: real-form 128-byte-swizzled images, see m2l_tc.cu
     float *Atc = nullptr, *Lltc = nullptr;
     float *Abf = nullptr, *Llbf = nullptr;  // the same matrices as bf16 hi/lo images (BF16x3)
+    float *Mmbf = nullptr;                  // and the S|S matrices of M2M (BF16x3)
     void *Aofs = nullptr;  // S|R bf16 hi/lo images for the offset-stationary few-column M2L (BF16x3)
     void *chunk_pairs = nullptr;  // int2 [chunks][32]: (source box, CSR position) of each chunk's pairs
     int *tc_err = nullptr;
@@ -326,7 +327,8 @@ void run_far_field(fmbem *h, const c64 *x, int64_t n_rhs, int64_t n_dir, const d
 void run_absorption(fmbem *h, const c64 *x, int64_t n_rhs, double *out_host, cudaStream_t s);
 bool m2l_tc_supported(const fmbem *h);
 void build_tc_tables(fmbem *h, cudaStream_t s);
-void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3);
+void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3, bool c_split = false);
+void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s);
 bool m2l_ofs_supported(const fmbem *h);
 void build_ofs_tables(fmbem *h, cudaStream_t s);
 void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s);

@@ -3012,7 +3012,8 @@ static void upward_m2m(fmbem *h, int64_t nr, cudaStream_t s) {
 // downward pass (Eq. 2.21): M2L over the FF lists and L2L, h->Cexp -> h->Dexp, all levels
 template <typename R>
 // tensor_mode: 0 CUDA cores, 1 TF32 tensor cores, 2 BF16x3 tensor cores (many columns)
-static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode) {
+// c_split: the BF16x3 tensor-core path finds C already split into bf16 hi/lo parts (run_m2m_tc)
+static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode, bool c_split = false) {
     const int p2 = h->p2, lmax = h->lmax, J = h->Jf;
     const bool f32 = sizeof(R) == 4;
     cx<R> *C = (cx<R> *)h->Cexp, *D = (cx<R> *)h->Dexp;
@@ -3051,7 +3052,7 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode)
         h->ybuf != nullptr && rows_pad <= max_thr;
     const bool use_rot = chunked && rl.ok;
     if (tensor_mode && f32 && h->Atc != nullptr && 3 * nr >= 48) {
-        run_m2l_tc(h, (float *)C, (float *)D, nr, s, tensor_mode == 2);
+        run_m2l_tc(h, (float *)C, (float *)D, nr, s, tensor_mode == 2, c_split);
     } else if (chunked) {
         if (tsm) CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
         else CK(cudaFuncSetAttribute(k_m2l_chunks<R, MAXC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
@@ -3212,9 +3213,13 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     CKL("k_p2m");
     if (timing) CK(cudaEventRecord(h->ev[1], s));
-    upward_m2m<R>(h, nr, s);
+    // BF16x3 with many columns: M2M on the tensor cores as well (its products then leave C split
+    // for M2L); otherwise on the CUDA cores
+    const bool tc_up = f32 && tensor_mode == 2 && h->Mmbf != nullptr && 3 * nr >= 48;
+    if (tc_up) run_m2m_tc(h, (float *)C, nr, s);
+    else upward_m2m<R>(h, nr, s);
     if (timing) CK(cudaEventRecord(h->ev[2], s));
-    downward_pass<R>(h, nr, s, tensor_mode);
+    downward_pass<R>(h, nr, s, tensor_mode, tc_up);
     if (timing) CK(cudaEventRecord(h->ev[3], s));
     const R *ph = f32 ? (const R *)h->pos_hi : (const R *)h->pos;
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;

@@ -170,6 +170,7 @@ struct TcLevel {
     int n, nsub, stages;  // columns per sub-tile (multiple of 16, <= 256), sub-tiles per CTA, depth
     uint32_t tmem_cols;   // power of two >= nsub * n
     int round_out;        // round D to TF32 (it feeds the next level's L2L product)
+    int m2m;              // 1: M2M (Eq. 2.20): box g of level l - 1 sums S|S C(child) over its children
 };
 
 // BF3 = false: TF32 operands (tmC, tmD over the TF32-rounded FP32 expansions, A images of TF32
@@ -182,7 +183,10 @@ __global__ void __launch_bounds__(128, 1)
              const __grid_constant__ CUtensorMap tmC2, const __grid_constant__ CUtensorMap tmD2, const TcLevel P,
              const int32_t *__restrict__ parent, const uint64_t *__restrict__ key, const int32_t *__restrict__ ff_start,
              const int32_t *__restrict__ ff_src, const int16_t *__restrict__ ff_off, const float *__restrict__ Atc,
-             const float *__restrict__ Lltc, float *D, __nv_bfloat16 *Dh, __nv_bfloat16 *Dl, int *err) {
+             const float *__restrict__ Lltc, float *D, __nv_bfloat16 *Dh, __nv_bfloat16 *Dl, int *err,
+             const int32_t *__restrict__ cbeg, const int32_t *__restrict__ cend) {
+    // M2M: a box without children (a leaf of an adaptive tree) keeps its P2M expansion
+    if (P.m2m && cbeg[P.off + blockIdx.x] == cend[P.off + blockIdx.x]) return;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[MAX_STAGES], empty[MAX_STAGES], done;
     __shared__ uint32_t tmem_slot;
@@ -220,8 +224,10 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    const int e0 = ff_start[g], e1 = ff_start[g + 1];
-    const int has_l2l = P.l >= 3 ? 1 : 0;
+    // products: M2L + L2L (the parent's R|R, then the FF list), or M2M (the children's S|S; Atc
+    // then holds the S|S images, Lltc is unused)
+    const int e0 = P.m2m ? cbeg[g] : ff_start[g], e1 = P.m2m ? cend[g] : ff_start[g + 1];
+    const int has_l2l = P.l >= 3 && !P.m2m ? 1 : 0;
     const int nprod = has_l2l + (e1 - e0);
     const int nunits = nprod * P.kblocks;
     const int64_t tbl = (int64_t)d * (P.lmax + 1) + P.l;
@@ -244,6 +250,12 @@ __global__ void __launch_bounds__(128, 1)
                 tm = &tmD;
                 tm2 = &tmD2;
                 y = (int)(((int64_t)d * P.nbox + parent[g]) * P.ncols + col0);
+            } else if (P.m2m) {
+                const int ch = e0 + i;
+                Asrc = Atc + (tbl * 8 + (int)(key[ch] & 7)) * a_mat;
+                tm = &tmC;
+                tm2 = &tmC2;
+                y = (int)(((int64_t)d * P.nbox + ch) * P.ncols + col0);
             } else {
                 const int e = e0 + i - has_l2l;
                 Asrc = Atc + (tbl * 316 + ff_off[e]) * a_mat;
@@ -789,6 +801,10 @@ void build_tc_tables(fmbem *h, cudaStream_t s) {
     k_build_bf3_tables<<<(unsigned)((n_oct * per + tb - 1) / tb), tb, 0, s>>>(h->T_ll64, n_oct, p2, kb,
                                                                             (__nv_bfloat16 *)h->Llbf);
     CKL("k_build_bf3_tables");
+    h->Mmbf = (float *)dev_alloc(h, sizeof(float) * per * n_oct);  // S|S images for M2M (BF16x3)
+    k_build_bf3_tables<<<(unsigned)((n_oct * per + tb - 1) / tb), tb, 0, s>>>(h->T_mm64, n_oct, p2, kb,
+                                                                            (__nv_bfloat16 *)h->Mmbf);
+    CKL("k_build_bf3_tables");
     h->tc_err = (int *)dev_alloc(h, sizeof(int));
     CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
 }
@@ -808,50 +824,92 @@ void tc_tile_shape(int64_t ncols, int *n, int *nsub, int *ntile) {
 // (TF32), or split into bf16 hi/lo parts in the second half of their buffer (BF16x3; the handle's
 // expansion buffers hold double-precision complex values, so single precision leaves that half
 // free); from here on only these products read them.  Then one launch per level.
-void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3) {
+// launch shape and tensor maps of the tile kernel for nr right-hand sides
+struct TcSetup {
+    int n, nsub, ntile, stages;
+    size_t smem;
+    uint32_t tcols;
+    CUtensorMap tmC, tmD, tmC2, tmD2;
+};
+static TcSetup tc_setup(fmbem *h, float *C, float *D, int64_t nr, bool bf3) {
+    TcSetup t{};
+    const int64_t ncols = 3 * nr;
+    const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
+    tc_tile_shape(ncols, &t.n, &t.nsub, &t.ntile);
+    const int stage = A_KB_BYTES + t.nsub * t.n * 128;
+    t.stages = std::min(MAX_STAGES, SMEM_BUDGET / stage);
+    t.smem = (size_t)t.stages * stage + 1024;  // + slack to align the stages to 1024 bytes
+    t.tcols = 32;
+    while ((int)t.tcols < t.nsub * t.n) t.tcols <<= 1;
+    const int64_t rows = (int64_t)(h->J + 1) * h->nbox * ncols;
+    if (bf3) {
+        CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem));
+        __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
+        __nv_bfloat16 *Dhi = (__nv_bfloat16 *)(D + nfloat), *Dlo = Dhi + nfloat;
+        t.tmC = make_column_map_bf16(Chi, rows, h->p2, t.n);
+        t.tmC2 = make_column_map_bf16(Clo, rows, h->p2, t.n);
+        t.tmD = make_column_map_bf16(Dhi, rows, h->p2, t.n);
+        t.tmD2 = make_column_map_bf16(Dlo, rows, h->p2, t.n);
+    } else {
+        CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem));
+        t.tmC = t.tmC2 = make_column_map(C, rows, h->p2, t.n);
+        t.tmD = t.tmD2 = make_column_map(D, rows, h->p2, t.n);
+    }
+    return t;
+}
+
+// M2M (Eq. 2.20) on the tensor cores in the BF16x3 form, for the passes that then run M2L + L2L
+// there too: the leaves' multipole expansions are split into bf16 hi/lo parts (the whole buffer:
+// the other boxes' parts are written below), then one launch per level, l_max - 1 down to 2, in
+// which every box sums the S|S products of its children and writes its expansion in FP32 and
+// split; the M2L + L2L pass then finds C split (run_m2l_tc with c_split)
+void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s) {
+    const int64_t ncols = 3 * nr;
+    const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
+    __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
+    k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
+    CKL("k_split_bf16");
+    const TcSetup t = tc_setup(h, C, C, nr, true);
+    for (int l = h->lmax; l >= 3; --l) {
+        const LevelInfo &Lv = h->lev[l - 1];  // the parents
+        const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), t.n, t.nsub, t.stages,
+                        t.tcols, 1, 1};
+        const dim3 grid((unsigned)Lv.n, h->Jf + 1, (unsigned)t.ntile);
+        k_m2l_tc<true><<<grid, 128, t.smem, s>>>(t.tmC, t.tmC, t.tmC2, t.tmC2, P, h->box_parent, h->box_key,
+                                                 h->ff_start, h->ff_src, h->ff_off, h->Mmbf, nullptr, C, Chi, Clo,
+                                                 h->tc_err, h->box_cbeg, h->box_cend);
+        CKL("k_m2l_tc (M2M)");
+    }
+}
+
+void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3, bool c_split) {
     const int64_t ncols = 3 * nr;
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
     __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
     __nv_bfloat16 *Dhi = (__nv_bfloat16 *)(D + nfloat), *Dlo = Dhi + nfloat;
     if (bf3) {
-        k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
-        CKL("k_split_bf16");
+        if (!c_split) {
+            k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
+            CKL("k_split_bf16");
+        }
     } else {
         k_round_tf32<<<152 * 8, 256, 0, s>>>(C, nfloat);
         CKL("k_round_tf32");
     }
-    int n, nsub, ntile;
-    tc_tile_shape(ncols, &n, &nsub, &ntile);
-    const int stage = A_KB_BYTES + nsub * n * 128;
-    const int stages = std::min(MAX_STAGES, SMEM_BUDGET / stage);
-    const size_t smem = (size_t)stages * stage + 1024;  // + slack to align the stages to 1024 bytes
-    uint32_t tcols = 32;
-    while ((int)tcols < nsub * n) tcols <<= 1;
-    const int64_t rows = (int64_t)(h->J + 1) * h->nbox * ncols;
-    CUtensorMap tmC, tmD, tmC2, tmD2;
-    if (bf3) {
-        CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tmC = make_column_map_bf16(Chi, rows, h->p2, n);
-        tmC2 = make_column_map_bf16(Clo, rows, h->p2, n);
-        tmD = make_column_map_bf16(Dhi, rows, h->p2, n);
-        tmD2 = make_column_map_bf16(Dlo, rows, h->p2, n);
-    } else {
-        CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tmC = tmC2 = make_column_map(C, rows, h->p2, n);
-        tmD = tmD2 = make_column_map(D, rows, h->p2, n);
-    }
+    const TcSetup t = tc_setup(h, C, D, nr, bf3);
     for (int l = 2; l <= h->lmax; ++l) {
         const LevelInfo &Lv = h->lev[l];
-        const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), n, nsub, stages, tcols,
-                        l < h->lmax ? 1 : 0};
-        const dim3 grid((unsigned)Lv.n, h->Jf + 1, (unsigned)ntile);
+        const TcLevel P{Lv.off, l, h->lmax, h->nbox, (int)ncols, h->p2, tc_kblocks(h->p2), t.n, t.nsub, t.stages,
+                        t.tcols, l < h->lmax ? 1 : 0, 0};
+        const dim3 grid((unsigned)Lv.n, h->Jf + 1, (unsigned)t.ntile);
         if (bf3)
-            k_m2l_tc<true><<<grid, 128, smem, s>>>(tmC, tmD, tmC2, tmD2, P, h->box_parent, h->box_key, h->ff_start,
-                                                   h->ff_src, h->ff_off, h->Abf, h->Llbf, D, Dhi, Dlo, h->tc_err);
+            k_m2l_tc<true><<<grid, 128, t.smem, s>>>(t.tmC, t.tmD, t.tmC2, t.tmD2, P, h->box_parent, h->box_key,
+                                                     h->ff_start, h->ff_src, h->ff_off, h->Abf, h->Llbf, D, Dhi, Dlo,
+                                                     h->tc_err, h->box_cbeg, h->box_cend);
         else
-            k_m2l_tc<false><<<grid, 128, smem, s>>>(tmC, tmD, tmC2, tmD2, P, h->box_parent, h->box_key, h->ff_start,
-                                                    h->ff_src, h->ff_off, h->Atc, h->Lltc, D, nullptr, nullptr,
-                                                    h->tc_err);
+            k_m2l_tc<false><<<grid, 128, t.smem, s>>>(t.tmC, t.tmD, t.tmC2, t.tmD2, P, h->box_parent, h->box_key,
+                                                      h->ff_start, h->ff_src, h->ff_off, h->Atc, h->Lltc, D, nullptr,
+                                                      nullptr, h->tc_err, h->box_cbeg, h->box_cend);
         CKL("k_m2l_tc");
     }
 }
