@@ -116,7 +116,9 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-impedance", action="store_true", help="skip the impedance-boundary product")
     ap.add_argument("--gradients", action="store_true",
-                    help="also time the adjoint gradients on the torus + sphere differentiation case")
+                    help="with the adjoint gradients, also check one vertex against central differences")
+    ap.add_argument("--no-gradients", action="store_true",
+                    help="skip the adjoint gradients on the torus + sphere differentiation case")
     ap.add_argument("--restart", type=int, default=50, help="GMRES restart length of the timed solves")
     ap.add_argument("--n-rhs", type=int, default=0, help="right-hand sides (0 = the workload's)")
     ap.add_argument("--no-batched", action="store_true",
@@ -315,45 +317,51 @@ def launches_per_matvec(lmax, nr, n_dom, precision):
     return 2 + (lmax - 2) + down + 1
 
 
-def run_gradients():
+def run_gradients(fd_check=False):
     """Differentiation case: a silver-like torus (R = 1, r = 0.25, 256 x 64 grid, 32768 triangles,
     eps = -10 + 0.4i) and a dielectric sphere (a = 0.1, eps = 2.5, 1280 triangles) a seeded gap
     above the tube, k0 R = 1.5, one plane wave along -z.  Times the extinction's gradient with
     respect to eps and to every vertex, and the Maxwell-stress force on the sphere with its vertex
-    gradient (forward and adjoint FMM solves included), and checks one sphere vertex of the force
-    gradient against central differences of full GPU solves."""
+    gradient (forward and adjoint FMM solves included: refined, BF16x3-operator inner GMRES and
+    FP64-operator true residuals), and with fd_check compares one sphere vertex of the force
+    gradient with central differences of full GPU solves."""
     import torch
 
+    import paper_1211_7177_gb300 as fm
     from paper_1211_7177_gb300 import gradients as gr
+    opts = dict(solve_precision=fm.BF16X3, inner_tol=1e-3)
     a = 0.1
     (V, F, D), gap, ctr = fi.torus_and_sphere(seed=4, a=a)
     eps, mu, k0 = [1.0, -10 + 0.4j, 2.5], [1.0, 1.0, 1.0], 1.5
     d = np.array([0.0, 0.0, -1.0])
     e = np.array([1.0, 0.0, 0.0], dtype=np.complex128)
     rad = a + 0.5 * gap
-    out = dict(nodes=len(V), gap=gap, stress_sphere_radius=rad)
+    out = dict(nodes=len(V), gap=gap, stress_sphere_radius=rad, solves="refined: BF16x3 inner, FP64 outer, tol 1e-8")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    c, de_re, de_im = gr.extinction_eps_gradient(V, F, D, eps, mu, k0, d[None], e[None], j=2, tol=1e-8)
+    c, de_re, de_im = gr.extinction_eps_gradient(V, F, D, eps, mu, k0, d[None], e[None], j=2, tol=1e-8, **opts)
     torch.cuda.synchronize()
     out["extinction_eps_gradient_s"] = time.perf_counter() - t0
+    out["dcext_deps2"] = [float(de_re[0]), float(de_im[0])]
     t0 = time.perf_counter()
-    c, gV = gr.extinction_vertex_gradient(V, F, D, eps, mu, k0, d[None], e[None], tol=1e-8)
+    c, gV = gr.extinction_vertex_gradient(V, F, D, eps, mu, k0, d[None], e[None], tol=1e-8, **opts)
     torch.cuda.synchronize()
     out["extinction_vertex_gradient_s"] = time.perf_counter() - t0
     out["cext"] = float(c[0])
     t0 = time.perf_counter()
-    Fo, gF = gr.force_vertex_gradient(V, F, D, eps, mu, k0, d, e, ctr, rad, tol=1e-10)
+    Fo, gF = gr.force_vertex_gradient(V, F, D, eps, mu, k0, d, e, ctr, rad, tol=1e-8, **opts)
     torch.cuda.synchronize()
     out["force_vertex_gradient_s"] = time.perf_counter() - t0
     out["force"] = [float(v) for v in Fo]
+    if not fd_check:
+        return out
     # central difference of the force for one vertex of the sphere (its vertices follow the torus')
     v, h = len(V) - 5, 1e-6
     fd = []
     for sgn in (1, -1):
         Vx = V.copy()
         Vx[v, 2] += sgn * h
-        fd.append(gr.force_vertex_gradient(Vx, F, D, eps, mu, k0, d, e, ctr, rad, tol=1e-12)[0])
+        fd.append(gr.force_vertex_gradient(Vx, F, D, eps, mu, k0, d, e, ctr, rad, tol=1e-12, **opts)[0])
     out["force_fd_check"] = dict(vertex=int(v), coordinate="z", adjoint=[float(q) for q in gF[:, v, 2]],
                                  central_difference=[float(q) for q in (fd[0] - fd[1]) / (2 * h)])
     return out
@@ -861,7 +869,9 @@ def run_ours(args):
                 solve[label]["gmres"] = gmres_roofline(N, int(its.max()), args.restart, solve[label]["ms"], ms_step)
             h2.close()
 
-    gradients = run_gradients() if args.gradients and rank == 0 else None
+    gradients = None
+    if rank == 0 and args.workload == "silver_sphere_s7" and not args.no_gradients:
+        gradients = run_gradients(fd_check=args.gradients)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

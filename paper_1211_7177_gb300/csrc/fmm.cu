@@ -202,30 +202,39 @@ __global__ void k_p2m_rb(const int32_t *leaf_box, int64_t N, int64_t nr, int p2,
 // 3 r + c (right-hand side r, component c), W_0 = q_c and W_k = v_c n_k + (n.v) delta_ck - n_c v_k
 // (so that sum_k W_k B_k = m_c . grad R + q_c R, Eqs. 2.18-2.19).  Nodes are taken P2M_KC at a time:
 // the block stages their basis rows and weights in shared memory, and each thread accumulates a
-// 4 x 4 tile of (coefficient, column) outputs.  Grid (leaf, domain, tile of P2M_MT columns).
+// tile of (coefficient, column) outputs: PT pairs of coefficients 2 (rg + nrg a) + {0, 1}
+// (a = 0..PT-1; the lanes of a warp read consecutive pairs, free of bank conflicts) and columns
+// 4 cgp .. 4 cgp + 3: a 4 x 4 tile (8 x 4 measured slower: fewer resident warps to hide the
+// staging's global loads).  Grid (leaf, domain, tile of MT columns); MT = 96 (32 right-hand
+// sides) in single precision, 48 in double (register budget).
 constexpr int P2M_KC = 8;   // nodes per shared-memory chunk
-constexpr int P2M_MT = 48;  // columns per block (16 right-hand sides)
+template <typename R>
+__host__ __device__ constexpr int p2m_mt() { return sizeof(R) == 4 ? 96 : 48; }
+template <typename R>
+__host__ __device__ constexpr int p2m_pt() { return 2; }
 template <typename R>
 __global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox, const int32_t *nbeg,
                            const int32_t *nend, const int32_t *dom, const double *nrm, const cx<R> *dens,
                            const cx<R> *Bp2m, cx<R> *C) {
+    constexpr int MT = p2m_mt<R>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R> *Bs = reinterpret_cast<cx<R> *>(smem_raw);  // [4 P2M_KC][p2]
-    cx<R> *Ws = Bs + 4 * P2M_KC * p2;                   // [4 P2M_KC][P2M_MT]
+    cx<R> *Ws = Bs + 4 * P2M_KC * p2;                   // [4 P2M_KC][MT]
     const int64_t g = leaf_box[blockIdx.x];
     const int d = blockIdx.y;
-    const int ncols = (int)(3 * nr), col0 = blockIdx.z * P2M_MT;
-    const int nh = min(P2M_MT, ncols - col0);
+    const int ncols = (int)(3 * nr), col0 = blockIdx.z * MT;
+    const int nh = min(MT, ncols - col0);
     const int side = d == 0 ? 0 : 1;
     const R sg = d == 0 ? (R)-1 : (R)1;
     const int i0 = nbeg[g], i1 = nend[g];
-    const int nrg = (p2 + 3) / 4;
-    const int rg = threadIdx.x % nrg, cgp = threadIdx.x / nrg;  // 4 coefficients x 4 columns
-    const int r0 = 4 * rg, c0 = 4 * cgp;
-    const bool owner = cgp < P2M_MT / 4;
-    cx<R> acc[4][4];
+    constexpr int PT = p2m_pt<R>();  // coefficient pairs per thread
+    const int nrg = (p2 + 2 * PT - 1) / (2 * PT);
+    const int rg = threadIdx.x % nrg, cgp = threadIdx.x / nrg;
+    const int c0 = 4 * cgp;
+    const bool owner = cgp < MT / 4;
+    cx<R> acc[2 * PT][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2 * PT; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = {0, 0};
     for (int ib = i0; ib < i1; ib += P2M_KC) {
@@ -238,8 +247,8 @@ __global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p
             if (il < nk && (d == 0 || dom[i] == d)) v = Bp2m[((int64_t)side * N + i) * 4 * p2 + (int64_t)(kk & 3) * p2 + q];
             Bs[e] = v;
         }
-        for (int e = threadIdx.x; e < P2M_KC * (P2M_MT / 3); e += blockDim.x) {
-            const int il = e / (P2M_MT / 3), rl = e - il * (P2M_MT / 3);
+        for (int e = threadIdx.x; e < P2M_KC * (MT / 3); e += blockDim.x) {
+            const int il = e / (MT / 3), rl = e - il * (MT / 3);
             const int i = ib + il, col = 3 * rl;
             cx<R> w[4][3];
 #pragma unroll
@@ -266,18 +275,22 @@ __global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) Ws[(4 * il + k) * P2M_MT + col + c] = w[k][c];
+                for (int c = 0; c < 3; ++c) Ws[(4 * il + k) * MT + col + c] = w[k][c];
         }
         __syncthreads();
         if (owner) {
             for (int kk = 0; kk < 4 * nk; ++kk) {
-                cx<R> bq[4], wc[4];
+                cx<R> bq[2 * PT], wc[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) bq[a] = (r0 + a < p2) ? Bs[kk * p2 + r0 + a] : cx<R>{0, 0};
+                for (int a = 0; a < PT; ++a) {
+                    const int q = 2 * (rg + nrg * a);  // p2 is even when p is, and Bs rows start 16-byte aligned
+                    bq[2 * a] = q < p2 ? Bs[kk * p2 + q] : cx<R>{0, 0};
+                    bq[2 * a + 1] = q + 1 < p2 ? Bs[kk * p2 + q + 1] : cx<R>{0, 0};
+                }
 #pragma unroll
-                for (int b = 0; b < 4; ++b) wc[b] = Ws[kk * P2M_MT + c0 + b];
+                for (int b = 0; b < 4; ++b) wc[b] = Ws[kk * MT + c0 + b];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 2 * PT; ++a)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) cfma(acc[a][b], bq[a], wc[b]);
             }
@@ -288,8 +301,10 @@ __global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p
         for (int b = 0; b < 4; ++b)
             if (c0 + b < nh)
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    if (r0 + a < p2) C[(((int64_t)d * nbox + g) * ncols + col0 + c0 + b) * p2 + r0 + a] = acc[a][b];
+                for (int a = 0; a < 2 * PT; ++a) {
+                    const int q = 2 * (rg + nrg * (a >> 1)) + (a & 1);
+                    if (q < p2) C[(((int64_t)d * nbox + g) * ncols + col0 + c0 + b) * p2 + q] = acc[a][b];
+                }
 }
 
 // ---------------------------------------------------------------- translation apply helper
@@ -1472,7 +1487,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 template <int RB>
 __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
     const int32_t *leaf_box, const int4 *__restrict__ items, int n_items, int n_units, int *next_unit, int64_t N, int64_t nr,
-    int64_t rhs_base,
+    int64_t rhs_base, int nsides,
     const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
     const float4 *__restrict__ rec, const cx<float> *dens, const DomainConsts *dc, const int32_t *perm, int p2,
     int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
@@ -1512,8 +1527,10 @@ __global__ void __launch_bounds__(32 * NW_WARPS, 4) k_near_w(
             if (lane < nnb) { rb_[lane] = beg; rc_[lane] = incl - cnt; }
             if (lane == nnb - 1) rc_[nnb] = incl;
         }
-        const int side = yslab & 1;
-        const int64_t rb0 = rhs_base + (int64_t)(yslab >> 1) * RB;
+        // slabs (RHS block, side); with the impedance boundary only the background side (k_local_rows
+        // writes the scatterer rows)
+        const int side = yslab % nsides;
+        const int64_t rb0 = rhs_base + (int64_t)(yslab / nsides) * RB;
         const int nrb = (int)min((int64_t)RB, nr - rb0);
         // densities of the RHS past the block's end stay zero in both tiles
         for (int e = nrb * 3 * NW_TS + lane; e < RB * 3 * NW_TS; e += 32) {
@@ -1910,7 +1927,7 @@ struct RhsTile {
 
 __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
     const int32_t *leaf_box, const int4 *__restrict__ groups, int n_groups, int n_units, int *next_unit, int64_t N,
-    int64_t nr, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
+    int64_t nr, int nsides, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
     const float4 *__restrict__ rec, const cx<float> *densT, const DomainConsts *dc, const int32_t *perm, int p2,
     int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
     const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y) {
@@ -1924,11 +1941,12 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
         if (lane == 0) unit = atomicAdd(next_unit, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= n_units) break;
+        // slabs (32-RHS block, side); with the impedance boundary only the background side
         const int slab = unit / n_groups, grp = unit - slab * n_groups;
-        const int side = slab & 1;
-        const int64_t r = (int64_t)(slab >> 1) * 32 + lane;  // this lane's right-hand side
+        const int side = slab % nsides;
+        const int64_t r = (int64_t)(slab / nsides) * 32 + lane;  // this lane's right-hand side
         __syncwarp();  // the previous unit's shared-memory reads are done
-        const int4 gi = groups[slab == 2 * (nr / 32) - 1 ? n_groups + grp : grp];  // last slab: longest first
+        const int4 gi = groups[slab == nsides * (nr / 32) - 1 ? n_groups + grp : grp];  // last slab: longest first
         const int leaf = gi.x, ntg = gi.z;
         const int64_t g = leaf_box[leaf];
         const int tbase = nbeg[g] + gi.y;
@@ -1961,7 +1979,7 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
         const float sgn = side == 0 ? -1.f : 1.f;  // domain 0 sees the scatterer normal reversed
         const int64_t nblk = nr / 32;  // node-major densities: this lane's of source i at dl + 96 i
         const float4 *dl =
-            reinterpret_cast<const float4 *>(densT + (((side * nblk + (slab >> 1)) * N) * 32 + lane) * 6);
+            reinterpret_cast<const float4 *>(densT + (((side * nblk + slab / nsides) * N) * 32 + lane) * 6);
         cx<float> acc[NR_TT][3];
 #pragma unroll
         for (int t = 0; t < NR_TT; ++t)
@@ -3200,10 +3218,11 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
     constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
     if (nr >= 16) {
-        const int nthr = ((p2 + 3) / 4) * (P2M_MT / 4);
-        const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + P2M_MT);
+        constexpr int MT = p2m_mt<R>(), PT = p2m_pt<R>();
+        const int nthr = ((p2 + 2 * PT - 1) / (2 * PT)) * (MT / 4);
+        const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + MT);
         CK(cudaFuncSetAttribute(k_p2m_gemm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
-        k_p2m_gemm<R><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)((3 * nr + P2M_MT - 1) / P2M_MT)), nthr, smp, s>>>(
+        k_p2m_gemm<R><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)((3 * nr + MT - 1) / MT)), nthr, smp, s>>>(
             h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     } else if (nr >= 4)
         k_p2m_rb<R, P2M_RB><<<dim3((unsigned)h->n_leaves, J + 1, (unsigned)((nr + P2M_RB - 1) / P2M_RB)), tbc, 0, s>>>(
@@ -3230,11 +3249,13 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // the scatterer side's near field is not needed with the impedance boundary (k_local_rows)
+    const int nsides = h->ibc ? 1 : 2;
     // k_near_w over the right-hand sides rhs_base .. nr - 1 in blocks of rb
     auto launch_w = [&](auto kern, int rb, size_t tile_bytes, int64_t rhs_base) {
         if (h->near_items == nullptr) throw fmbem_error{FMBEM_ERR_CUDA, "near-field work items were not built"};
         const size_t smw = 2 * tile_bytes * NW_WARPS;  // two tiles per warp
-        const int64_t units = (int64_t)h->n_near_items * 2 * ((nr - rhs_base + rb - 1) / rb);
+        const int64_t units = (int64_t)h->n_near_items * nsides * ((nr - rhs_base + rb - 1) / rb);
         if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
         int per_sm = 0;
@@ -3243,14 +3264,14 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                                     (int64_t)std::max(per_sm, 1) * nsm));
         CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
         kern<<<(unsigned)grid, 32 * NW_WARPS, smw, s>>>(
-            h->leaf_box, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, rhs_base, h->box_nbeg,
+            h->leaf_box, h->near_items, h->n_near_items, (int)units, h->near_next, N, nr, rhs_base, nsides, h->box_nbeg,
             h->box_nend, h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)dens, dc, h->perm, p2, h->nbox,
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_w");
     };
     // k_near_r over the right-hand sides 0 .. 32 nblk - 1
     auto launch_r = [&](int64_t nblk) {
-        const int64_t units = (int64_t)h->n_near_groups * 2 * nblk;
+        const int64_t units = (int64_t)h->n_near_groups * nsides * nblk;
         if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_r, 32 * NR_WARPS, 0));
@@ -3258,7 +3279,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
                                                                     (int64_t)std::max(per_sm, 1) * nsm));
         CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
         k_near_r<<<(unsigned)grid, 32 * NR_WARPS, 0, s>>>(
-            h->leaf_box, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, h->box_nbeg, h->box_nend,
+            h->leaf_box, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, nsides, h->box_nbeg, h->box_nend,
             h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)densT, dc, h->perm, p2, h->nbox,
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_r");
