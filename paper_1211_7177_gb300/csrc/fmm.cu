@@ -63,22 +63,37 @@ __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm,
     prep_body<R>(N, nr, x, perm, nrm, w, dom, dc, dens, blockIdx.x, blockIdx.y, sj);
 }
 
-// The single-precision densities node-major within blocks of 32 right-hand sides,
-// densT[side][block][node][32][6], for the lane-per-RHS near field (a source's 32 right-hand sides
-// are contiguous): grid (node tiles of 16, block, side), 32 x 16 entries of 48 bytes per block
-// through shared memory, read and written in whole rows.
-__global__ void __launch_bounds__(256) k_dens_node_major(int64_t N, int64_t nr, const float4 *dens, float4 *densT) {
-    __shared__ float4 t[32][16 * 3 + 1];
-    const int64_t i0 = (int64_t)blockIdx.x * 16, rb = blockIdx.y, side = blockIdx.z, nb = gridDim.y;
+// The single-precision densities node-major within blocks of 32 right-hand sides, for the
+// lane-per-RHS near field (a source's 32 right-hand sides are contiguous):
+// densS[block][node][32][4 float4] = (v0x, v0y), (v0z, q0x), (q0y, q0z), (s, 0) of the background
+// side, with s = n . (v_1 - v_0) the scatterer side's jump along the normal (v_1 = v_0 + s n, see
+// k_near_ws); grid (node tiles of 16, block), 32 x 16 entries through shared memory, written in
+// whole rows.
+__global__ void __launch_bounds__(256) k_dens_node_major(int64_t N, int64_t nr, const float4 *dens, const float4 *rec,
+                                                         float4 *densS) {
+    __shared__ float4 t[32][16 * 4 + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * 16, rb = blockIdx.y;
     const int ni = (int)min((int64_t)16, N - i0);
-    for (int e = threadIdx.x; e < 32 * 48; e += blockDim.x) {  // row r: 16 nodes x 3 float4
-        const int rl = e / 48, k = e - rl * 48;
-        if (k < 3 * ni) t[rl][k] = dens[((side * nr + rb * 32 + rl) * N + i0) * 3 + k];
+    for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {  // (right-hand side rl, node il)
+        const int rl = e / 16, il = e - rl * 16;
+        if (il < ni) {
+            const int64_t i = i0 + il;
+            const float4 *a = dens + ((rb * 32 + rl) * N + i) * 3;         // background side
+            const float4 *b = dens + ((nr + rb * 32 + rl) * N + i) * 3;    // scatterer side
+            const float4 a0 = a[0], a1 = a[1], b0 = b[0], b1 = b[1];
+            const float4 n1 = rec[3 * i + 1], n2 = rec[3 * i + 2];        // n = (n1.w, n2.x, n2.y)
+            const float sre = n1.w * (b0.x - a0.x) + n2.x * (b0.z - a0.z) + n2.y * (b1.x - a1.x);
+            const float sim = n1.w * (b0.y - a0.y) + n2.x * (b0.w - a0.w) + n2.y * (b1.y - a1.y);
+            t[rl][il * 4] = a0;
+            t[rl][il * 4 + 1] = a1;
+            t[rl][il * 4 + 2] = a[2];
+            t[rl][il * 4 + 3] = make_float4(sre, sim, 0.f, 0.f);
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 16 * 96; e += blockDim.x) {  // node i: 32 right-hand sides x 3 float4
-        const int il = e / 96, k = e - il * 96, rl = k / 3, c = k - rl * 3;
-        if (il < ni) densT[((side * nb + rb) * N + i0 + il) * 96 + k] = t[rl][il * 3 + c];
+    for (int e = threadIdx.x; e < 16 * 128; e += blockDim.x) {  // node il: 32 right-hand sides x 4 float4
+        const int il = e / 128, k = e - il * 128, rl = k / 4, c = k - rl * 4;
+        if (il < ni) densS[(rb * N + i0 + il) * 128 + k] = t[rl][il * 4 + c];
     }
 }
 
@@ -1905,48 +1920,52 @@ __global__ void __launch_bounds__(32 * NS_WARPS, 6) k_near_ws(
     }
 }
 
-// Steps 4-5 for 32 or more right-hand sides in single precision, one lane per right-hand side.
-// A warp owns one unit: a group of at most NR_TT targets of one leaf, one side and a block of 32
-// right-hand sides.  The sources of the leaf's Neighbor list go by in tiles of 32:
-// - pair phase: lane l takes source l of the tile and evaluates the kernel scalars (w = n x r,
-//   n.r, g, c) against every target of the group into shared memory (zero where the source lies in
-//   another scatterer on the scatterer side, or past the list's end);
-// - right-hand-side phase: every lane reads its own densities of each source (the next source's
-//   loads are in flight while the current one is applied) and applies the broadcast scalars of all
-//   targets, so a pair's scalars serve 32 right-hand sides and no lane idles.
-// Then L2P (Eq. 2.23 first term) from the lane's three columns of the leaf's local expansion, and
-// the side's rows of the analytic self block (App. B) in double precision; each lane stores its
-// right-hand side's rows.
+// Steps 4-5 for 32 or more right-hand sides in single precision, one lane per right-hand side,
+// both sides of every pair in one pass (the relations of k_near_ws: v_1 = v_0 + s n,
+// q_1 = -gamma_j q_0).  A warp owns one unit: a group of at most NR_TT targets of one leaf and a
+// block of 32 right-hand sides.  The sources of the leaf's Neighbor list go by in tiles of 32:
+// - pair phase: lane l takes source l of the tile and evaluates, against every target of the
+//   group, w = n x r, n.r and r, the background's scalars (-c_0, g_0) and the scatterer side's
+//   (c_1, -gamma_j g_1; zero where the source lies in another scatterer or past the list's end)
+//   into shared memory;
+// - right-hand-side phase: every lane reads its own (v_0, q_0, s) of each source (node-major copy
+//   k_dens_node_major; the next source's loads in flight while the current one is applied) and, per
+//   target, U = w x v_0 + (n.r) v_0 once, then acc_0 += -c_0 U + g_0 q_0 and
+//   acc_1 += c_1 (U + s r) - gamma_j g_1 q_0; a pair's scalars serve 32 right-hand sides.
+// Then L2P (Eq. 2.23 first term) of both sides from the lane's three columns of the leaf's local
+// expansions, and the rows of the analytic self block (App. B) in double precision; each lane
+// stores its right-hand side's rows.  With the impedance boundary (side1 false) the background
+// side only (k_local_rows writes the scatterer rows).
 constexpr int NR_TT = 8;   // targets per unit
 constexpr int NR_WARPS = 4;
 struct RhsTile {
-    float4 ps[NR_TT][32][2];  // (w, n.r), (g, c) per target and source of the tile
+    float4 ps[NR_TT][32][4];  // (w, n.r), (-c_0, g_0), (c_1, -gamma g_1), (r, 0) per target and source
     float4 tp[NR_TT][2];      // target position hi + scatterer id bits, position lo
-    float2 tk[NR_TT];         // the wavenumber each target sees on this side
+    float4 tk[NR_TT];         // the target's scatterer wavenumber k_j and -gamma_j
 };
 
-__global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
+__global__ void __launch_bounds__(32 * NR_WARPS, 3) k_near_r(
     const int32_t *leaf_box, const int4 *__restrict__ groups, int n_groups, int n_units, int *next_unit, int64_t N,
-    int64_t nr, int nsides, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start, const int32_t *nbr_idx,
-    const float4 *__restrict__ rec, const cx<float> *densT, const DomainConsts *dc, const int32_t *perm, int p2,
-    int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
+    int64_t nr, bool side1, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
+    const int32_t *nbr_idx, const float4 *__restrict__ rec, const float4 *densS, const DomainConsts *dc,
+    const int32_t *perm, int p2, int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
     const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y) {
-    __shared__ RhsTile tiles[NR_WARPS];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int rng_beg[NR_WARPS][32], rng_cum[NR_WARPS][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    RhsTile &S = tiles[warp];
+    RhsTile &S = reinterpret_cast<RhsTile *>(smem_raw)[warp];
     int *rb_ = rng_beg[warp], *rc_ = rng_cum[warp];
+    const cx<float> k0 = to<float>(dc[0].k);
     for (;;) {
         int unit = 0;
         if (lane == 0) unit = atomicAdd(next_unit, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= n_units) break;
-        // slabs (32-RHS block, side); with the impedance boundary only the background side
+        // slabs of 32 right-hand sides; the last one takes its groups longest first
         const int slab = unit / n_groups, grp = unit - slab * n_groups;
-        const int side = slab % nsides;
-        const int64_t r = (int64_t)(slab / nsides) * 32 + lane;  // this lane's right-hand side
+        const int64_t r = (int64_t)slab * 32 + lane;  // this lane's right-hand side
         __syncwarp();  // the previous unit's shared-memory reads are done
-        const int4 gi = groups[slab == nsides * (nr / 32) - 1 ? n_groups + grp : grp];  // last slab: longest first
+        const int4 gi = groups[slab == (int)(nr / 32) - 1 ? n_groups + grp : grp];
         const int leaf = gi.x, ntg = gi.z;
         const int64_t g = leaf_box[leaf];
         const int tbase = nbeg[g] + gi.y;
@@ -1971,20 +1990,19 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
             const float4 ta = rec[3 * a];
             S.tp[lane][0] = ta;
             S.tp[lane][1] = rec[3 * a + 1];
-            const cx<float> kt = to<float>(dc[side == 0 ? 0 : __float_as_int(ta.w)].k);
-            S.tk[lane] = make_float2(kt.re, kt.im);
+            const int td = __float_as_int(ta.w);
+            const cx<float> kt = to<float>(dc[td].k), gm = to<float>(dc[td].gamma);
+            S.tk[lane] = make_float4(kt.re, kt.im, -gm.re, -gm.im);
         }
         __syncwarp();
         const int nsrc = rc_[nnb];
-        const float sgn = side == 0 ? -1.f : 1.f;  // domain 0 sees the scatterer normal reversed
-        const int64_t nblk = nr / 32;  // node-major densities: this lane's of source i at dl + 96 i
-        const float4 *dl =
-            reinterpret_cast<const float4 *>(densT + (((side * nblk + slab / nsides) * N) * 32 + lane) * 6);
-        cx<float> acc[NR_TT][3];
+        // node-major (v_0, q_0, s) of this lane's right-hand side: source i at dl + 128 i
+        const float4 *dl = densS + ((int64_t)slab * N * 32 + lane) * 4;
+        cx<float> acc0[NR_TT][3], acc1[NR_TT][3];
 #pragma unroll
         for (int t = 0; t < NR_TT; ++t)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[t][c] = {0, 0};
+            for (int c = 0; c < 3; ++c) acc0[t][c] = acc1[t][c] = {0, 0};
         int qcur = 0;
         for (int s0 = 0; s0 < nsrc; s0 += 32) {
             // pair phase: source s0 + lane against the group's targets
@@ -1997,54 +2015,85 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
             }
             const float4 pa = rec[3 * i], pb = rec[3 * i + 1], pc = rec[3 * i + 2];
             const int sdom = __float_as_int(pa.w);
-            const float nn[3] = {sgn * pb.w, sgn * pc.x, sgn * pc.y};
+            const float nn[3] = {pb.w, pc.x, pc.y};
 #pragma unroll
             for (int t = 0; t < NR_TT; ++t) {
                 if (t < ntg) {
                     const float4 ta = S.tp[t][0], tl = S.tp[t][1];
-                    const float rv3[3] = {(pa.x - ta.x) + (pb.x - tl.x), (pa.y - ta.y) + (pb.y - tl.y),
-                                          (pa.z - ta.z) + (pb.z - tl.z)};
-                    const float R2 = rv3[0] * rv3[0] + rv3[1] * rv3[1] + rv3[2] * rv3[2];
+                    const float rv[3] = {(pa.x - ta.x) + (pb.x - tl.x), (pa.y - ta.y) + (pb.y - tl.y),
+                                         (pa.z - ta.z) + (pb.z - tl.z)};
+                    const float R2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
                     const float inv = R2 > 0.f ? rsqrt_(R2) : 0.f;  // the node itself drops out
                     const float Rr = R2 * inv;
-                    const float nrv = nn[0] * rv3[0] + nn[1] * rv3[1] + nn[2] * rv3[2];
-                    const float2 kt = S.tk[t];
-                    cx<float> gs, cs;
-                    pair_scalars<float>(inv, Rr, cx<float>{kt.x, kt.y}, gs, cs);
-                    if (!valid || (side == 1 && sdom != __float_as_int(ta.w))) gs = cs = cx<float>{0.f, 0.f};
-                    S.ps[t][lane][0] = make_float4(nn[1] * rv3[2] - nn[2] * rv3[1], nn[2] * rv3[0] - nn[0] * rv3[2],
-                                                   nn[0] * rv3[1] - nn[1] * rv3[0], nrv);
-                    S.ps[t][lane][1] = make_float4(gs.re, gs.im, cs.re, cs.im);
+                    const float nrv = nn[0] * rv[0] + nn[1] * rv[1] + nn[2] * rv[2];
+                    cx<float> g0, c0, g1 = {0, 0}, c1 = {0, 0};
+                    pair_scalars<float>(inv, Rr, k0, g0, c0);
+                    if (!valid) g0 = c0 = cx<float>{0.f, 0.f};
+                    if (side1 && valid && sdom == __float_as_int(ta.w)) {
+                        const float4 tk = S.tk[t];
+                        pair_scalars<float>(inv, Rr, cx<float>{tk.x, tk.y}, g1, c1);
+                        g1 = cx<float>{tk.z, tk.w} * g1;  // -gamma_j g_1: q_1 = -gamma_j q_0
+                    }
+                    S.ps[t][lane][0] = make_float4(nn[1] * rv[2] - nn[2] * rv[1], nn[2] * rv[0] - nn[0] * rv[2],
+                                                   nn[0] * rv[1] - nn[1] * rv[0], nrv);
+                    S.ps[t][lane][1] = make_float4(-c0.re, -c0.im, g0.re, g0.im);
+                    S.ps[t][lane][2] = make_float4(c1.re, c1.im, g1.re, g1.im);
+                    S.ps[t][lane][3] = make_float4(rv[0], rv[1], rv[2], 0.f);
                 }
             }
             __syncwarp();
             // right-hand-side phase
             const int nsv = min(32, nsrc - s0);
             int ic = __shfl_sync(0xffffffffu, i, 0);
-            float4 c0 = dl[96 * ic], c1 = dl[96 * ic + 1], c2 = dl[96 * ic + 2];
+            float4 d0 = dl[128 * (int64_t)ic], d1 = dl[128 * (int64_t)ic + 1], d2 = dl[128 * (int64_t)ic + 2],
+                   d3 = dl[128 * (int64_t)ic + 3];
             for (int sv = 0; sv < nsv; ++sv) {
-                float4 n0 = c0, n1 = c1, n2 = c2;
+                float4 n0 = d0, n1 = d1, n2 = d2, n3 = d3;
                 const int in = __shfl_sync(0xffffffffu, i, (sv + 1) & 31);
-                if (sv + 1 < nsv) { n0 = dl[96 * in]; n1 = dl[96 * in + 1]; n2 = dl[96 * in + 2]; }
-                const cx<float> v[3] = {{c0.x, c0.y}, {c0.z, c0.w}, {c1.x, c1.y}};
-                const cx<float> qv[3] = {{c1.z, c1.w}, {c2.x, c2.y}, {c2.z, c2.w}};
+                if (sv + 1 < nsv) {
+                    n0 = dl[128 * (int64_t)in];
+                    n1 = dl[128 * (int64_t)in + 1];
+                    n2 = dl[128 * (int64_t)in + 2];
+                    n3 = dl[128 * (int64_t)in + 3];
+                }
+                const cx<float> v[3] = {{d0.x, d0.y}, {d0.z, d0.w}, {d1.x, d1.y}};
+                const cx<float> q[3] = {{d1.z, d1.w}, {d2.x, d2.y}, {d2.z, d2.w}};
+                const cx<float> sj = {d3.x, d3.y};
 #pragma unroll
                 for (int t = 0; t < NR_TT; ++t) {
                     if (t < ntg) {
                         const float4 p0 = S.ps[t][sv][0], p1 = S.ps[t][sv][1];
                         const float w[3] = {p0.x, p0.y, p0.z};
-                        cross_apply<float>(w, p0.w, cx<float>{p1.x, p1.y}, cx<float>{p1.z, p1.w}, v, qv, acc[t]);
+                        const cx<float> U[3] = {w[1] * v[2] - w[2] * v[1] + p0.w * v[0],
+                                                w[2] * v[0] - w[0] * v[2] + p0.w * v[1],
+                                                w[0] * v[1] - w[1] * v[0] + p0.w * v[2]};
+                        const cx<float> mc0 = {p1.x, p1.y}, g0 = {p1.z, p1.w};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            cfma(acc0[t][c], mc0, U[c]);
+                            cfma(acc0[t][c], g0, q[c]);
+                        }
+                        if (side1) {
+                            const float4 p2v = S.ps[t][sv][2], p3 = S.ps[t][sv][3];
+                            const cx<float> c1 = {p2v.x, p2v.y}, g1 = {p2v.z, p2v.w};
+                            const float rr[3] = {p3.x, p3.y, p3.z};
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                cfma(acc1[t][c], c1, U[c] + rr[c] * sj);
+                                cfma(acc1[t][c], g1, q[c]);
+                            }
+                        }
                     }
                 }
-                c0 = n0; c1 = n1; c2 = n2;
+                d0 = n0; d1 = n1; d2 = n2; d3 = n3;
             }
             __syncwarp();  // the next tile's pair phase overwrites the scalars
         }
-        // far field: this lane's three columns of the leaf's local expansion of the side's domain
-        // (on the scatterer side each target's own scatterer: the group's scatterers in turn); the
-        // targets' L2P rows are staged in the scalars' shared memory, chunks of qc coefficients, and
-        // the lane's expansion coefficients are loaded two coefficients ahead
-        {
+        // far field of each side: this lane's three columns of the leaf's local expansion of the
+        // side's domain (on the scatterer side each target's own scatterer: the group's scatterers
+        // in turn); the targets' L2P rows are staged in the scalars' shared memory, chunks of qc
+        // coefficients, and the lane's expansion coefficients are loaded two coefficients ahead
+        auto l2p = [&](int side, cx<float>(&acc)[NR_TT][3]) {
             cx<float> *Bs = reinterpret_cast<cx<float> *>(&S.ps[0][0][0]);
             constexpr int BS_CAP = (int)(sizeof(S.ps) / sizeof(cx<float>));
             const int qc = min(p2, BS_CAP / NR_TT);
@@ -2065,18 +2114,18 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
                         Bs[t * qc + qq] = Bl2p[((int64_t)side * N + tbase + t) * p2 + q0 + qq];
                     }
                     __syncwarp();
-                    cx<float> d1[3], d2[3];
+                    cx<float> e1[3], e2[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        d1[c] = Dr[c * p2 + q0];
-                        d2[c] = Dr[c * p2 + q0 + min(1, qn - 1)];
+                        e1[c] = Dr[c * p2 + q0];
+                        e2[c] = Dr[c * p2 + q0 + min(1, qn - 1)];
                     }
                     for (int qq = 0; qq < qn; ++qq) {
-                        const cx<float> dq[3] = {d1[0], d1[1], d1[2]};
+                        const cx<float> dq[3] = {e1[0], e1[1], e1[2]};
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            d1[c] = d2[c];
-                            if (qq + 2 < qn) d2[c] = Dr[c * p2 + q0 + qq + 2];
+                            e1[c] = e2[c];
+                            if (qq + 2 < qn) e2[c] = Dr[c * p2 + q0 + qq + 2];
                         }
 #pragma unroll
                         for (int t = 0; t < NR_TT; ++t) {
@@ -2089,24 +2138,31 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 4) k_near_r(
                     }
                 }
             }
-        }
-        // the side's rows of the self block (Psi columns diagonal) in double precision, stored
+        };
+        l2p(0, acc0);
+        if (side1) l2p(1, acc1);
+        // the rows of the self block (Psi columns diagonal) in double precision, stored
 #pragma unroll
         for (int t = 0; t < NR_TT; ++t) {
             if (t < ntg) {
                 const int64_t u = perm[tbase + t];
-                const c64 *M = Mself + 36 * u + 18 * side;
                 const c64 *xa = x + (r * N + u) * 6;
-                c64 *ya = y + (r * N + u) * 6 + 3 * side;
+                c64 *ya = y + (r * N + u) * 6;
                 const c64 x0 = xa[0], x1 = xa[1], x2 = xa[2];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    c64 v = {(double)acc[t][c].re, (double)acc[t][c].im};
-                    cfma(v, M[6 * c], x0);
-                    cfma(v, M[6 * c + 1], x1);
-                    cfma(v, M[6 * c + 2], x2);
-                    cfma(v, M[6 * c + 3 + c], xa[3 + c]);
-                    ya[c] = v;
+                for (int side = 0; side < 2; ++side) {
+                    if (side == 1 && !side1) break;
+                    const c64 *M = Mself + 36 * u + 18 * side;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const cx<float> a = side == 0 ? acc0[t][c] : acc1[t][c];
+                        c64 v = {(double)a.re, (double)a.im};
+                        cfma(v, M[6 * c], x0);
+                        cfma(v, M[6 * c + 1], x1);
+                        cfma(v, M[6 * c + 2], x2);
+                        cfma(v, M[6 * c + 3 + c], xa[3 + c]);
+                        ya[3 * side + c] = v;
+                    }
                 }
             }
         }
@@ -3201,8 +3257,9 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     const bool timing = h->profile && h->ev[0] != nullptr;
     if (timing) CK(cudaEventRecord(h->ev[0], s));
 
-    // single precision with 32 or more right-hand sides: a node-major copy of the densities for
-    // k_near_r in the half of the density buffer that double precision would use
+    // single precision with 32 or more right-hand sides: a node-major copy of the background
+    // densities and the normal jumps for k_near_r in the half of the density buffer that double
+    // precision would use (64 bytes per node and RHS, within its 96)
     const int64_t nrT = f32 ? (nr / 32) * 32 : 0;
     cx<R> *densT = nrT > 0 ? dens + 2 * nr * N * 6 : nullptr;
     // and with fewer than 4, the normal jump s of the densities (k_near_ws) in the same place
@@ -3211,8 +3268,8 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens, sj);
     CKL("k_prep");
     if (densT != nullptr) {
-        k_dens_node_major<<<dim3((unsigned)((N + 15) / 16), (unsigned)(nrT / 32), 2), 256, 0, s>>>(
-            N, nr, (const float4 *)dens, (float4 *)densT);
+        k_dens_node_major<<<dim3((unsigned)((N + 15) / 16), (unsigned)(nrT / 32)), 256, 0, s>>>(
+            N, nr, (const float4 *)dens, h->src_rec, (float4 *)densT);
         CKL("k_dens_node_major");
     }
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
@@ -3271,16 +3328,18 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     };
     // k_near_r over the right-hand sides 0 .. 32 nblk - 1
     auto launch_r = [&](int64_t nblk) {
-        const int64_t units = (int64_t)h->n_near_groups * nsides * nblk;
+        const int64_t units = (int64_t)h->n_near_groups * nblk;
         if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
+        const size_t smr = sizeof(RhsTile) * NR_WARPS;
+        CK(cudaFuncSetAttribute(k_near_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
         int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_r, 32 * NR_WARPS, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_r, 32 * NR_WARPS, smr));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((units + NR_WARPS - 1) / NR_WARPS,
                                                                     (int64_t)std::max(per_sm, 1) * nsm));
         CK(cudaMemsetAsync(h->near_next, 0, sizeof(int), s));
-        k_near_r<<<(unsigned)grid, 32 * NR_WARPS, 0, s>>>(
-            h->leaf_box, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, nsides, h->box_nbeg, h->box_nend,
-            h->nbr_start, h->nbr_idx, h->src_rec, (const cx<float> *)densT, dc, h->perm, p2, h->nbox,
+        k_near_r<<<(unsigned)grid, 32 * NR_WARPS, smr, s>>>(
+            h->leaf_box, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, nsides == 2, h->box_nbeg,
+            h->box_nend, h->nbr_start, h->nbr_idx, h->src_rec, (const float4 *)densT, dc, h->perm, p2, h->nbox,
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_r");
     };
