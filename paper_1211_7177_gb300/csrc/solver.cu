@@ -231,8 +231,10 @@ struct ArithOf<c32> {
 // relative to ||rhs||.  V holds (m + 2) vectors of nr * n elements of TV (the last one is scratch
 // for the final combination); z and w are nr * n double vectors.
 template <typename TV>
+// x_zero: x is zero on entry, so the first residual is the right-hand side (no product)
 void gmres(fmbem *h, Work &W, int precision, bool tr, const c64 *rhs, c64 *x, double tol, int max_iter, TV *V, c64 *z,
-           c64 *w, std::vector<int> &its, std::vector<double> &relres, std::vector<char> &conv, bool &breakdown) {
+           c64 *w, std::vector<int> &its, std::vector<double> &relres, std::vector<char> &conv, bool &breakdown,
+           bool x_zero) {
     using R = typename ArithOf<TV>::R;
     const int64_t n = W.n, nr = W.nr;
     const int m = std::max(1, h->opt.gmres_restart);
@@ -246,9 +248,12 @@ void gmres(fmbem *h, Work &W, int precision, bool tr, const c64 *rhs, c64 *x, do
     conv.assign(nr, 0);
     std::vector<double> rn;
     int total = 0;
+    bool first = true;
     for (;;) {
         // true residual r = rhs - A x
-        apply_op(h, x, w, nr, precision, s, tr);
+        if (first && x_zero) CK(cudaMemsetAsync(w, 0, sizeof(c64) * (size_t)nr * n, s));
+        else apply_op(h, x, w, nr, precision, s, tr);
+        first = false;
         k_axpy<<<grid, 256, 0, s>>>(1, rhs, w, n, nr);
         CKL("k_axpy");
         W.norms<double>(w, rn);
@@ -378,8 +383,13 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
     fmbem_status st = FMBEM_OK;
     const dim3 grid(nblk(n, 256), (unsigned)nr);
     try {
+        // a zero initial guess (the usual one) makes the first residual b itself
+        std::vector<double> xn;
+        W.norms<double>(x, xn);
+        const bool x_zero = std::all_of(xn.begin(), xn.end(), [](double v) { return v == 0.0; });
         if (!refine) {
-            gmres<c64>(h, W, FMBEM_FP64, transpose, b, x, tol, max_iter, (c64 *)base, z, w, its, rr, conv, breakdown);
+            gmres<c64>(h, W, FMBEM_FP64, transpose, b, x, tol, max_iter, (c64 *)base, z, w, its, rr, conv, breakdown,
+                       x_zero);
         } else {
             // iterative refinement: r = b - A x (outer_precision passes, double vectors); solve
             // A' d = r to inner_tol with the FP32 or TF32 operator and a single-precision basis;
@@ -389,7 +399,8 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
             std::vector<double> bn;
             W.norms<double>(b, bn);
             for (int outer = 0;; ++outer) {
-                apply_op(h, x, r, nr, h->opt.outer_precision, s, transpose);
+                if (outer == 0 && x_zero) CK(cudaMemsetAsync(r, 0, vec, s));
+                else apply_op(h, x, r, nr, h->opt.outer_precision, s, transpose);
                 k_axpy<<<grid, 256, 0, s>>>(1, b, r, n, nr);
                 CKL("k_axpy");
                 std::vector<double> rn;
@@ -411,7 +422,7 @@ fmbem_status run_solve(fmbem *h, const c64 *b, c64 *x, int64_t nr, double tol, i
                 std::vector<char> ic;
                 const double itol = std::max(h->opt.inner_tol, 0.5 * tol);
                 gmres<c32>(h, W, h->opt.solve_precision, transpose, r, d, itol, max_iter - used, (c32 *)base, z, w, ii,
-                           ir, ic, breakdown);
+                           ir, ic, breakdown, true);  // d = 0
                 for (int64_t q = 0; q < nr; ++q) itot[q] += ii[q];
                 k_axpy<<<grid, 256, 0, s>>>(2, d, x, n, nr);
                 CKL("k_axpy");
