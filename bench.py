@@ -368,10 +368,28 @@ def run_gradients(fd_check=False):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one matvec phase, from ncu
-# captures summarised under profiles/, keyed by (workload, precision, n_rhs, phase); each entry
-# records the SHA-256 prefix of the kernel source it was taken with, and the bench reports null
-# once that source has changed.
-TRAFFIC = {}
+# captures summarised under profiles/ (launches_*.md: the timed steps' launches, one metric pass,
+# caches flushed between kernels), keyed by (workload, precision, n_rhs, phase); each entry
+# records the SHA-256 prefixes of the kernel sources it was taken with, and the bench reports null
+# once a source has changed.
+TRAFFIC = {
+    ('silver_sphere_s7', 'fp64', 1, 'p2m'): dict(bytes=2213297920, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp64', 1, 'm2m'): dict(bytes=117221888, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp64', 1, 'm2l_l2l'): dict(bytes=5563443968, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp64', 1, 'near_l2p_self'): dict(bytes=6585120256, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp32', 1, 'p2m'): dict(bytes=1114339328, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp32', 1, 'm2m'): dict(bytes=58548736, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp32', 1, 'm2l_l2l'): dict(bytes=2676558848, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp32', 1, 'near_l2p_self'): dict(bytes=465758976, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'p2m'): dict(bytes=1114337792, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'm2m'): dict(bytes=58540800, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'm2l_l2l'): dict(bytes=3281379328, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'near_l2p_self'): dict(bytes=465598720, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('torus_512x128', 'bf16x3', 128, 'p2m'): dict(bytes=5644286208, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('torus_512x128', 'bf16x3', 128, 'm2m'): dict(bytes=3871661568, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('torus_512x128', 'bf16x3', 128, 'm2l_l2l'): dict(bytes=4913641984, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('torus_512x128', 'bf16x3', 128, 'near_l2p_self'): dict(bytes=4970880768, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+}
 
 
 def _src_sha(name):
