@@ -454,9 +454,10 @@ def tensor_peak_bf16x3():
 
 
 def phase_rooflines(info, p, nr, n_dom, N, phases, workload, form="bf16x3"):
-    """Per-phase roofline of the batched matvec: near field against the FP32 ALU peak, M2L + L2L
-    (algorithmic flops of the dense complex contraction) against the tensor peak of the form
-    (BF16x3: the BF16 rate over three; TF32), P2M and M2M against the FP32 ALU peak."""
+    """Per-phase roofline of the batched matvec: near field and P2M against the FP32 ALU peak, M2L +
+    L2L (algorithmic flops of the dense complex contraction) against the tensor peak of the form
+    (BF16x3: the BF16 rate over three; TF32), M2M against the BF16x3 tensor peak in that form (it
+    runs on the tensor cores there) and against the FP32 ALU peak in the TF32 form."""
     keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
     avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
     tpk, tsrc = tensor_peak_bf16x3() if form == "bf16x3" else tensor_peak_tf32()
@@ -473,7 +474,7 @@ def phase_rooflines(info, p, nr, n_dom, N, phases, workload, form="bf16x3"):
     }
     out = {}
     for k in keys:
-        tensor = k == "m2l_l2l"
+        tensor = k == "m2l_l2l" or (k == "m2m" and form == "bf16x3")
         peak = tpk if tensor else PEAK_TFLOPS["fp32"]
         ach = flops[k] / (avg[k] * 1e-3) / 1e12
         out[k] = dict(bound="tensor" if tensor else "alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
