@@ -407,6 +407,26 @@ def test_autotune_picks_a_config_that_meets_the_target():
     assert err <= 1e-4, err
 
 
+def test_autotune_over_translation_form_octree_and_precision():
+    """The autotuner's wider grid (translation form, octree, product precision): every candidate
+    is timed and checked, and the chosen configuration meets the target against the dense
+    operator in its own precision."""
+    from paper_1211_7177_gb300.autotune import autotune
+    V, F, D = fi.icosphere(4)
+    eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
+    res = autotune(V, F, D, eps, mu, k0, tol=1e-4, p_candidates=(8, 10), leaf_candidates=(64,),
+                   rotation_candidates=(0, 1), adaptive_candidates=(0, 1),
+                   precision_candidates=(fm.FP32, fm.BF16X3), reps=2)
+    print({k: v for k, v in res.items() if k != "table"})
+    assert len(res["table"]) == 2 * 2 * 2 * 2 and res["err"] <= 0.5e-4
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=res["p"], leaf_size=res["leaf_size"], m2l_rotation=res["m2l_rotation"],
+                 adaptive=res["adaptive"])
+    x = fi.random_complex((1, o.N, 6), seed=72)
+    err = rel(g.matvec(to_dev(x), precision=res["precision"]).cpu().numpy(), o.matvec(x))
+    assert err <= 1e-4, err
+
+
 def test_uneven_batch_of_independent_problems():
     """Five independent problems of uneven sizes and shapes (spheroids of aspect 2 and 4, tori of
     R/r 4 and 2, a split ring) with the permittivities of the uneven-batch workload, 4 plane
