@@ -255,12 +255,24 @@ __global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p
     for (int ib = i0; ib < i1; ib += P2M_KC) {
         const int nk = min(P2M_KC, i1 - ib);
         __syncthreads();
-        for (int e = threadIdx.x; e < 4 * P2M_KC * p2; e += blockDim.x) {
-            const int kk = e / p2, q = e - kk * p2, il = kk >> 2;
-            const int i = ib + il;
-            cx<R> v = {0, 0};
-            if (il < nk && (d == 0 || dom[i] == d)) v = Bp2m[((int64_t)side * N + i) * 4 * p2 + (int64_t)(kk & 3) * p2 + q];
-            Bs[e] = v;
+        if (sizeof(R) == 4 && (p2 & 1) == 0) {  // pairs of coefficients as 16-byte words
+            const int hp = p2 >> 1;
+            for (int e = threadIdx.x; e < 4 * P2M_KC * hp; e += blockDim.x) {
+                const int kk = e / hp, q2 = e - kk * hp, il = kk >> 2;
+                const int i = ib + il;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (il < nk && (d == 0 || dom[i] == d))
+                    v = reinterpret_cast<const float4 *>(Bp2m + ((int64_t)side * N + i) * 4 * p2 + (int64_t)(kk & 3) * p2)[q2];
+                reinterpret_cast<float4 *>(Bs + kk * p2)[q2] = v;
+            }
+        } else {
+            for (int e = threadIdx.x; e < 4 * P2M_KC * p2; e += blockDim.x) {
+                const int kk = e / p2, q = e - kk * p2, il = kk >> 2;
+                const int i = ib + il;
+                cx<R> v = {0, 0};
+                if (il < nk && (d == 0 || dom[i] == d)) v = Bp2m[((int64_t)side * N + i) * 4 * p2 + (int64_t)(kk & 3) * p2 + q];
+                Bs[e] = v;
+            }
         }
         for (int e = threadIdx.x; e < P2M_KC * (MT / 3); e += blockDim.x) {
             const int il = e / (MT / 3), rl = e - il * (MT / 3);
@@ -293,17 +305,37 @@ __global__ void k_p2m_gemm(const int32_t *leaf_box, int64_t N, int64_t nr, int p
                 for (int c = 0; c < 3; ++c) Ws[(4 * il + k) * MT + col + c] = w[k][c];
         }
         __syncthreads();
+        // single precision with p2 even: the coefficient pairs and the four columns as 16-byte words
+        // (Bs rows and Ws column groups then start 16-byte aligned)
+        const bool vec = sizeof(R) == 4 && (p2 & 1) == 0;
         if (owner) {
             for (int kk = 0; kk < 4 * nk; ++kk) {
                 cx<R> bq[2 * PT], wc[4];
+                if (vec) {
 #pragma unroll
-                for (int a = 0; a < PT; ++a) {
-                    const int q = 2 * (rg + nrg * a);  // p2 is even when p is, and Bs rows start 16-byte aligned
-                    bq[2 * a] = q < p2 ? Bs[kk * p2 + q] : cx<R>{0, 0};
-                    bq[2 * a + 1] = q + 1 < p2 ? Bs[kk * p2 + q + 1] : cx<R>{0, 0};
+                    for (int a = 0; a < PT; ++a) {
+                        const int q = 2 * (rg + nrg * a);
+                        const float4 v = q < p2 ? reinterpret_cast<const float4 *>(Bs + kk * p2)[q >> 1]
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                        bq[2 * a] = cx<R>{(R)v.x, (R)v.y};
+                        bq[2 * a + 1] = cx<R>{(R)v.z, (R)v.w};
+                    }
+                    const float4 w0 = reinterpret_cast<const float4 *>(Ws + kk * MT + c0)[0];
+                    const float4 w1 = reinterpret_cast<const float4 *>(Ws + kk * MT + c0)[1];
+                    wc[0] = cx<R>{(R)w0.x, (R)w0.y};
+                    wc[1] = cx<R>{(R)w0.z, (R)w0.w};
+                    wc[2] = cx<R>{(R)w1.x, (R)w1.y};
+                    wc[3] = cx<R>{(R)w1.z, (R)w1.w};
+                } else {
+#pragma unroll
+                    for (int a = 0; a < PT; ++a) {
+                        const int q = 2 * (rg + nrg * a);
+                        bq[2 * a] = q < p2 ? Bs[kk * p2 + q] : cx<R>{0, 0};
+                        bq[2 * a + 1] = q + 1 < p2 ? Bs[kk * p2 + q + 1] : cx<R>{0, 0};
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) wc[b] = Ws[kk * MT + c0 + b];
                 }
-#pragma unroll
-                for (int b = 0; b < 4; ++b) wc[b] = Ws[kk * MT + c0 + b];
 #pragma unroll
                 for (int a = 0; a < 2 * PT; ++a)
 #pragma unroll
