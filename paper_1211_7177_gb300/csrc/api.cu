@@ -51,6 +51,9 @@ static void free_all(fmbem *h) {
     h->allocations.clear();
     for (auto &e : h->ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (cudaEvent_t *e : {&h->ev_fork, &h->ev_join})
+        if (*e) { cudaEventDestroy(*e); *e = nullptr; }
+    if (h->aux_stream) { cudaStreamDestroy(h->aux_stream); h->aux_stream = nullptr; }
 }
 
 // wraps a call: converts exceptions into a status and the handle's message
@@ -213,6 +216,11 @@ fmbem_status fmbem_create(const fmbem_mesh *mesh, const fmbem_c64 *eps, const fm
         build_near_singular(h, mesh, s);
         if (h->profile)
             for (auto &e : h->ev) CK(cudaEventCreate(&e));
+        if (h->Aofs) {  // the few-column BF16x3 downward pass forks onto a second stream
+            CK(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        }
         CK(cudaStreamSynchronize(s));
     });
     if (st != FMBEM_OK) {

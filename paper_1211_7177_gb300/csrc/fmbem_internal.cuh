@@ -239,6 +239,10 @@ struct fmbem {
     // timing
     bool profile = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // a second stream for the few-column BF16x3 downward pass: the coarse levels' L2L + reduction
+    // chain runs there beside the leaf level's tensor-core M2L (fork and join events)
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool have_times = false;
 
     std::vector<void *> allocations;
@@ -333,7 +337,7 @@ bool m2l_ofs_supported(const fmbem *h);
 void build_ofs_tables(fmbem *h, cudaStream_t s);
 void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s);
 int64_t ofs_y_dom(const fmbem *h, int64_t nr);
-void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s);
+void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s, int l0, int l1, int reserve_sms);
 void pack_rot_tables(fmbem *h, cudaStream_t s);
 void pack_rot_tables_mm(fmbem *h, cudaStream_t s);
 void build_rot_mm_lists(fmbem *h, cudaStream_t s);

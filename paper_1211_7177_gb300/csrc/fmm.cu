@@ -3174,9 +3174,22 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode,
         // results go after them)
         const bool ofs = tensor_mode == 2 && f32 && h->Aofs != nullptr && h->chunk_pairs != nullptr && 3 * nr <= MAXC &&
                          h->ybuf_bytes >= ofs_ybuf_need(h, nr);
+        // With a second stream the coarse levels' M2L (levels 2..l_max-1) runs first; then, while
+        // the leaf level's M2L occupies all but OFS_AUX_SMS SMs, the second stream runs those
+        // levels' L2L + reductions and the leaf level's L2L, which are latency-bound chains of
+        // small launches; the leaf level's reduction joins both.
+        constexpr int OFS_AUX_SMS = 8;
+        const bool overlap = ofs && h->aux_stream != nullptr && lmax >= 3;
         if (ofs) {
             split_expansions_bf16(h, (float *)C, nr, s);
-            run_m2l_ofs(h, (const float *)C, (float *)Y, nr, s);
+            if (overlap) {
+                run_m2l_ofs(h, (const float *)C, (float *)Y, nr, s, 2, lmax - 1, 0);
+                CK(cudaEventRecord(h->ev_fork, s));
+                CK(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+                run_m2l_ofs(h, (const float *)C, (float *)Y, nr, s, lmax, lmax, OFS_AUX_SMS);
+            } else {
+                run_m2l_ofs(h, (const float *)C, (float *)Y, nr, s, 2, lmax, 0);
+            }
         }
         const int64_t y_dom = ofs ? ofs_y_dom(h, nr) / 2 : 0;  // in complex values
         // per level and column window, all domains in one launch each (grid rows): domain d's pair
@@ -3210,17 +3223,23 @@ static void downward_pass(fmbem *h, int64_t nr, cudaStream_t s, int tensor_mode,
                 cx<R> *Yll = nullptr;
                 int64_t ll_first = 0;
                 const int64_t yll_str = nchild * nc * p2;
+                cudaStream_t sl = overlap ? h->aux_stream : s;  // this level's L2L
                 if (use_rot_mm && l >= 3) {
                     const int64_t lc0 = h->h_rmm_chunk_first[l], lnch = h->h_rmm_chunk_first[l + 1] - lc0;
                     ll_first = h->h_rmm_first[l];
                     Yll = Y + (J + 1) * ystr;
-                    launch_rot<R>(rl, lnch, s, lc0, l, lmax, J + 1, nr, pp, h->nbox, col0, nc, h->rmm_chunk_beg,
+                    launch_rot<R>(rl, lnch, sl, lc0, l, lmax, J + 1, nr, pp, h->nbox, col0, nc, h->rmm_chunk_beg,
                                   h->rmm_chunk_cnt, h->rmm_chunk_ll, h->rmm_iota, h->rmm_par, h->rot_zero, 1, RD, RP,
                                   RZll, D, Yll, ll_first, yll_str);
                     CKL("k_m2l_rot (L2L)");
                 }
+                if (overlap && l == lmax) {  // join: the leaf level's reduction on the caller's stream
+                    CK(cudaEventRecord(h->ev_join, h->aux_stream));
+                    CK(cudaStreamWaitEvent(s, h->ev_join, 0));
+                }
+                cudaStream_t sr = overlap && l < lmax ? h->aux_stream : s;  // this level's reduction
                 const int ct = (nc + L2L_CPT - 1) / L2L_CPT;
-                k_l2l_reduce<R><<<dim3((unsigned)Lv.n, (unsigned)(J + 1)), rows_pad * ct, sizeof(cx<R>) * nc * p2, s>>>(
+                k_l2l_reduce<R><<<dim3((unsigned)Lv.n, (unsigned)(J + 1)), rows_pad * ct, sizeof(cx<R>) * nc * p2, sr>>>(
                     Lv.off, l, lmax, 0, nr, p2, h->nbox, col0, nc, ct, h->box_parent, h->box_key, h->ff_start, Tll, Y,
                     e_first, D, Yll, h->rmm_entry, ll_first, ystr, yll_str);
                 CKL("k_l2l_reduce");

@@ -956,9 +956,13 @@ void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s) {
 // (Y + d * ofs_y_dom(h, nr) floats, the layout k_l2l_reduce reads with e_first = 0)
 int64_t ofs_y_dom(const fmbem *h, int64_t nr) { return std::max<int64_t>(h->n_ff, 1) * 3 * nr * 2 * h->p2; }
 
-void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s) {
+// (levels l0..l1; reserve_sms SMs left free for work on other streams)
+void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s, int l0, int l1, int reserve_sms) {
     if (h->lmax + 1 > OFS_MAX_LEVELS) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many octree levels"};
-    const int64_t c0 = h->h_chunk_first[2], nch = h->h_chunk_first[h->lmax + 1] - c0;
+    l0 = std::max(l0, 2);
+    l1 = std::min(l1, h->lmax);
+    if (l1 < l0) return;
+    const int64_t c0 = h->h_chunk_first[l0], nch = h->h_chunk_first[l1 + 1] - c0;
     if (nch <= 0) return;
     const int p2 = h->p2, kb = tc_kblocks(p2), np = ofs_np(p2);
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * 3 * nr * 2 * p2;
@@ -983,7 +987,7 @@ void run_m2l_ofs(fmbem *h, const float *C, float *Y, int64_t nr, cudaStream_t s)
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t grid = std::min<int64_t>(nch * P.ndom, nsm);  // one persistent CTA per SM
+    const int64_t grid = std::min<int64_t>(nch * P.ndom, std::max(1, nsm - reserve_sms));  // one persistent CTA per SM
     k_m2l_ofs<<<(unsigned)grid, OFS_THREADS, smem, s>>>(P, c0, nch, h->chunk_cnt, h->chunk_off,
                                                          (const int2 *)h->chunk_pairs, Chi, Clo,
                                                          (const __nv_bfloat16 *)h->Aofs, Y, h->tc_err);
