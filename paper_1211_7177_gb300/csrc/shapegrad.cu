@@ -7,7 +7,7 @@
 // s_u, weight w_u, normal n_u) of the nodes of the vertex's 1-ring and through their self blocks
 // (Appendix B).  Here the sensitivities of G = L^T x + lambda^T b - lambda^T A x to the node data
 // of every node are summed over all partners (the pair blocks of Eq. 2.12 depend on s_a, s_b,
-// w_b and n_b), by central differences in FP64, O(N^2) pair evaluations in all;
+// w_b and n_b), by closed-form pair derivatives in FP64, O(N^2) pair evaluations in all;
 // k_vertex_shape_grad (geometry.cu) then chains them with the node data of each vertex's 1-ring
 // and adds the self blocks' change.
 #include <algorithm>
@@ -22,51 +22,82 @@ struct DomainC {  // per domain, as in the matvec: k, t = (eps_0 - eps_d)/eps_d,
 
 __device__ __forceinline__ double dot3d(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
-// lambda_a . (pair block of Eq. 2.12 for target a, source b) x_b with r = s_b - s_a: the background
-// side always (normal -n_b, Psi^(0) = -Psi), the scatterer side when a and b share scatterer j
-__device__ c64 pair_val(const double *r, double wb, const double *nb, bool same, c64 k0, c64 kj, c64 tj, c64 gj,
-                        const c64 *la, const c64 *xb) {
-    const double R = sqrt(dot3d(r, r));
+// lambda_a . (pair block of Eq. 2.12 for target a, source b) x_b with r = s_b - s_a (val): the
+// background side always (normal -n_b, Psi^(0) = -Psi), the scatterer side when a and b share
+// scatterer j; and its derivatives with respect to r (gr) and, if gn != nullptr, to the source
+// normal n_b (as a free vector, unnormalised), in closed form: with
+// g = e^{ikR}/(4 pi R) and c = g (ik - 1/R)/R, grad_r g = c r and grad_r c = c2 r with
+// c2 = g (-k^2/R^2 - 3ik/R^3 + 3/R^4); the brackets are linear in r and n (the scatterer side's
+// density v = Phi + t n (n.Phi) depends on n too).  One exponential per domain instead of the
+// central differences' 2 per derivative.
+__device__ void pair_grad(const double *r, double wb, const double *nb, bool same, c64 k0, c64 kj, c64 tj, c64 gj,
+                          const c64 *la, const c64 *xb, c64 *val, c64 *gr, c64 *gn) {
+    const double R2 = dot3d(r, r), R = sqrt(R2);
     const double iR = 1.0 / R;
     const c64 *Phi = xb, *Psi = xb + 3;
     const double nr = dot3d(nb, r);
-    c64 val = {0, 0};
+    c64 v0 = {0, 0}, g3[3] = {{0, 0}, {0, 0}, {0, 0}}, n3[3] = {{0, 0}, {0, 0}, {0, 0}};
     {
         const c64 ik = {-k0.im, k0.re};
         const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
         const c64 c = g * (ik - c64{iR, 0}) * iR;
+        const c64 c2 = g * ((ik * ik) * (iR * iR) - ik * (3.0 * iR * iR * iR) + c64{3.0 * iR * iR * iR * iR, 0});
         const c64 rP = r[0] * Phi[0] + r[1] * Phi[1] + r[2] * Phi[2];
         const c64 nP = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
-        for (int q = 0; q < 3; ++q) {
-            // bracket with the background normal -n_b: -n (a.Phi) + (n.a) Phi + a (n.Phi), a = c r
-            const c64 B = c * (-nb[q] * rP + nr * Phi[q] + r[q] * nP);
-            val += la[q] * (-wb * (B + g * Psi[q]));
+        const c64 lP = la[0] * Phi[0] + la[1] * Phi[1] + la[2] * Phi[2];
+        const c64 lPs = la[0] * Psi[0] + la[1] * Psi[1] + la[2] * Psi[2];
+        const c64 ln = la[0] * nb[0] + la[1] * nb[1] + la[2] * nb[2];
+        const c64 lr = la[0] * r[0] + la[1] * r[1] + la[2] * r[2];
+        // lambda . beta with beta_q = -n_q (r.Phi) + (n.r) Phi_q + r_q (n.Phi)
+        const c64 lb = -(ln * rP) + nr * lP + lr * nP;
+        v0 = -wb * (c * lb + g * lPs);
+        for (int j = 0; j < 3; ++j) {
+            g3[j] = -wb * (c2 * lb * r[j] + c * (-(ln * Phi[j]) + nb[j] * lP + la[j] * nP) + c * lPs * r[j]);
+            n3[j] = -wb * (c * (-(la[j] * rP) + r[j] * lP + lr * Phi[j]));
         }
     }
     if (same) {
         const c64 ik = {-kj.im, kj.re};
         const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
         const c64 c = g * (ik - c64{iR, 0}) * iR;
+        const c64 c2 = g * ((ik * ik) * (iR * iR) - ik * (3.0 * iR * iR * iR) + c64{3.0 * iR * iR * iR * iR, 0});
+        const c64 *l = la + 3;
         const c64 nP0 = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
+        const c64 tn = tj * nP0;
         c64 v[3];
-        for (int q = 0; q < 3; ++q) v[q] = Phi[q] + nb[q] * (tj * nP0);  // T_j Phi (Eq. 2.13)
+        for (int q = 0; q < 3; ++q) v[q] = Phi[q] + nb[q] * tn;  // T_j Phi (Eq. 2.13)
         const c64 rv = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
         const c64 nv = nb[0] * v[0] + nb[1] * v[1] + nb[2] * v[2];
-        for (int q = 0; q < 3; ++q) {
-            const c64 B = c * (nb[q] * rv - nr * v[q] - r[q] * nv);
-            val += la[3 + q] * (-wb * B + (gj * g) * (wb * 1.0) * Psi[q]);
+        const c64 lv = l[0] * v[0] + l[1] * v[1] + l[2] * v[2];
+        const c64 ln = l[0] * nb[0] + l[1] * nb[1] + l[2] * nb[2];
+        const c64 lr = l[0] * r[0] + l[1] * r[1] + l[2] * r[2];
+        const c64 lPs = l[0] * Psi[0] + l[1] * Psi[1] + l[2] * Psi[2];
+        const double nn = dot3d(nb, nb);
+        // lambda' . beta' with beta'_q = n_q (r.v) - (n.r) v_q - r_q (n.v)
+        const c64 lb = ln * rv - nr * lv - lr * nv;
+        v0 += -wb * (c * lb) + (gj * g) * wb * lPs;
+        for (int j = 0; j < 3; ++j) {
+            g3[j] += -wb * (c2 * lb * r[j] + c * (ln * v[j] - nb[j] * lv - l[j] * nv)) + (gj * c) * wb * lPs * r[j];
+            const c64 drv = tj * (r[j] * nP0 + nr * Phi[j]);                // d(r.v)/dn_j
+            const c64 dnv = v[j] + tj * (nb[j] * nP0 + nn * Phi[j]);         // d(n.v)/dn_j
+            const c64 dlv = tj * (l[j] * nP0 + ln * Phi[j]);                 // d(lambda'.v)/dn_j
+            const c64 dlb = l[j] * rv + ln * drv - r[j] * lv - nr * dlv - lr * dnv;
+            n3[j] += -wb * (c * dlb);
         }
     }
-    return val;
+    *val = v0;
+    for (int j = 0; j < 3; ++j) {
+        gr[j] = g3[j];
+        if (gn) gn[j] = n3[j];
+    }
 }
 
-// partial sensitivities of G's pair part over one slice of partners:
-// part[slice][r][u][7] = dG/d(s_u (3), w_u, n_u (3)); grid (node tiles, slices, rhs)
+// partial sensitivities of G's pair part over one slice of partners (closed-form pair derivatives,
+// pair_grad): part[slice][r][u][7] = dG/d(s_u (3), w_u, n_u (3)); grid (node tiles, slices, rhs)
 constexpr int SG_NT = 128, SG_NS = 32;
 __global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, const double *pos, const double *nrm,
                                                    const double *w, const int32_t *dom, const DomainC *dc,
-                                                   const c64 *x, const c64 *lam, double hs, double hn,
-                                                   int64_t slice_len, c64 *part) {
+                                                   const c64 *x, const c64 *lam, int64_t slice_len, c64 *part) {
     __shared__ double sp[SG_NS][3], sn[SG_NS][3], sw[SG_NS];
     __shared__ int sd[SG_NS];
     __shared__ c64 sx[SG_NS][6], sl[SG_NS][6];
@@ -86,7 +117,6 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, cons
     const int64_t b0s = slice * slice_len, b1s = min(N, b0s + slice_len);
     c64 acc[7];
     for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
-    const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
     for (int64_t b0 = b0s; b0 < b1s; b0 += SG_NS) {
         const int nb = (int)min((int64_t)SG_NS, b1s - b0);
         __syncthreads();
@@ -103,29 +133,18 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, cons
             if (b0 + e == u) continue;
             const bool same = sd[e] == du;
             const double rt[3] = {sp[e][0] - su[0], sp[e][1] - su[1], sp[e][2] - su[2]};
+            c64 val, gr[3], gn[3];
             // u as the target: r = s_m - s_u, dG/ds_u = +dt/dr (G holds -t)
-            for (int c = 0; c < 3; ++c) {
-                double rp[3] = {rt[0], rt[1], rt[2]}, rm[3] = {rt[0], rt[1], rt[2]};
-                rp[c] += hs;
-                rm[c] -= hs;
-                acc[c] += (pair_val(rp, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e]) -
-                           pair_val(rm, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e])) * i2s;
-            }
+            pair_grad(rt, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e], &val, gr, nullptr);
+            for (int c = 0; c < 3; ++c) acc[c] += gr[c];
             // u as the source: r = s_u - s_m, dG/ds_u = -dsigma/dr, dG/dn_u, dG/dw_u = -sigma / w_u
             const double rs[3] = {-rt[0], -rt[1], -rt[2]};
+            pair_grad(rs, wu, nu, same, k0, kj, tj, gj, sl[e], xu, &val, gr, gn);
             for (int c = 0; c < 3; ++c) {
-                double rp[3] = {rs[0], rs[1], rs[2]}, rm[3] = {rs[0], rs[1], rs[2]};
-                rp[c] += hs;
-                rm[c] -= hs;
-                acc[c] -= (pair_val(rp, wu, nu, same, k0, kj, tj, gj, sl[e], xu) -
-                           pair_val(rm, wu, nu, same, k0, kj, tj, gj, sl[e], xu)) * i2s;
-                double np_[3] = {nu[0], nu[1], nu[2]}, nm[3] = {nu[0], nu[1], nu[2]};
-                np_[c] += hn;
-                nm[c] -= hn;
-                acc[4 + c] -= (pair_val(rs, wu, np_, same, k0, kj, tj, gj, sl[e], xu) -
-                               pair_val(rs, wu, nm, same, k0, kj, tj, gj, sl[e], xu)) * i2n;
+                acc[c] -= gr[c];
+                acc[4 + c] -= gn[c];
             }
-            acc[3] -= pair_val(rs, wu, nu, same, k0, kj, tj, gj, sl[e], xu) * (1.0 / wu);
+            acc[3] -= val * (1.0 / wu);
         }
     }
     if (valid)
@@ -338,7 +357,7 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
             if (dcH) CK(cudaMemcpyAsync(dcH, cH_host, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyHostToDevice, s));
         }
         k_node_sens<<<dim3((unsigned)ntile, (unsigned)n_slices, (unsigned)nr), SG_NT, 0, s>>>(
-            N, nr, h->upos, h->unrm, h->uw, h->udom, ddc, x, lam, hs, hn, slice_len, part);
+            N, nr, h->upos, h->unrm, h->uw, h->udom, ddc, x, lam, slice_len, part);
         CKL("k_node_sens");
         k_node_sens_reduce<<<dim3((unsigned)((N + 127) / 128), (unsigned)nr), 128, 0, s>>>(
             N, nr, n_slices, part, h->upos, h->unrm, h->uw, h->k[0], dd, dp, rhat_host ? dr : nullptr, dcf, x, lam, hs,
