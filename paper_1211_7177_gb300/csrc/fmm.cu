@@ -39,23 +39,26 @@ __device__ __forceinline__ void prep_body(int64_t N, int64_t nr, const c64 *x, c
     int64_t i = bx * (int64_t)blockDim.x + threadIdx.x;
     int64_t r = by;
     if (i >= N) return;
+    // in the working precision R: single precision rounds x, n, w and the constants first (the
+    // densities are rounded to it in any case; the FP64 pipe would bound this kernel otherwise)
     const c64 *xi = x + (r * N + perm[i]) * 6;
-    double n[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
-    double wi = w[i];
-    int j = dom[i];
-    c64 Phi[3] = {xi[0], xi[1], xi[2]}, Psi[3] = {xi[3], xi[4], xi[5]};
+    const R n[3] = {(R)nrm[3 * i], (R)nrm[3 * i + 1], (R)nrm[3 * i + 2]};
+    const R wi = (R)w[i];
+    const int j = dom[i];
+    const cx<R> Phi[3] = {to<R>(xi[0]), to<R>(xi[1]), to<R>(xi[2])};
+    const cx<R> Psi[3] = {to<R>(xi[3]), to<R>(xi[4]), to<R>(xi[5])};
     cx<R> *d0 = dens + ((0 * nr + r) * N + i) * 6;
     cx<R> *d1 = dens + ((1 * nr + r) * N + i) * 6;
-    c64 nP = n[0] * Phi[0] + n[1] * Phi[1] + n[2] * Phi[2];
-    c64 tn = dc[j].t * nP;
-    c64 gw = dc[j].gamma * wi;
+    const cx<R> nP = n[0] * Phi[0] + n[1] * Phi[1] + n[2] * Phi[2];
+    const cx<R> tn = to<R>(dc[j].t) * nP;
+    const cx<R> gw = to<R>(dc[j].gamma) * wi;
     for (int q = 0; q < 3; ++q) {
-        d0[q] = to<R>(wi * Phi[q]);
-        d0[3 + q] = to<R>(-wi * Psi[q]);
-        d1[q] = to<R>(wi * (Phi[q] + n[q] * tn));
-        d1[3 + q] = to<R>(gw * Psi[q]);
+        d0[q] = wi * Phi[q];
+        d0[3 + q] = (-wi) * Psi[q];
+        d1[q] = wi * (Phi[q] + n[q] * tn);
+        d1[3 + q] = gw * Psi[q];
     }
-    if (sj) sj[r * N + i] = to<R>(wi * tn);  // v_1 - v_0 = s n (see k_near_ws)
+    if (sj) sj[r * N + i] = wi * tn;  // v_1 - v_0 = s n (see k_near_ws)
 }
 template <typename R>
 __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm, const double *nrm, const double *w,
@@ -3325,7 +3328,13 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     }
     const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
     constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
-    if (nr >= 16) {
+    // BF16x3 with many columns: P2M and M2M on the tensor cores as well (their products then leave
+    // C split for M2L); otherwise on the CUDA cores
+    const bool tc_up = f32 && tensor_mode == 2 && h->Mmbf != nullptr && 3 * nr >= 48;
+    const bool tc_p2m = tc_up && p2m_tc_supported(h, nr);
+    if (tc_p2m) {
+        run_p2m_tc(h, (const float *)dens, (const float *)Bp2m, (float *)C, nr, s);
+    } else if (nr >= 16) {
         constexpr int MT = p2m_mt<R>(), PT = p2m_pt<R>();
         const int nthr = ((p2 + 2 * PT - 1) / (2 * PT)) * (MT / 4);
         const size_t smp = sizeof(cx<R>) * 4 * P2M_KC * (p2 + MT);
@@ -3340,10 +3349,7 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend, h->dom, h->nrm, dens, Bp2m, C);
     CKL("k_p2m");
     if (timing) CK(cudaEventRecord(h->ev[1], s));
-    // BF16x3 with many columns: M2M on the tensor cores as well (its products then leave C split
-    // for M2L); otherwise on the CUDA cores
-    const bool tc_up = f32 && tensor_mode == 2 && h->Mmbf != nullptr && 3 * nr >= 48;
-    if (tc_up) run_m2m_tc(h, (float *)C, nr, s);
+    if (tc_up) run_m2m_tc(h, (float *)C, nr, s, tc_p2m);
     else upward_m2m<R>(h, nr, s);
     if (timing) CK(cudaEventRecord(h->ev[2], s));
     downward_pass<R>(h, nr, s, tensor_mode, tc_up);

@@ -436,6 +436,277 @@ __global__ void k_round_tf32(float *x, int64_t n) {
         x[i] = to_tf32(x[i]);
 }
 
+// ------------------------------------------------------------------------------------------
+// P2M (Eqs. 2.18-2.19) for many right-hand sides on the tensor cores, BF16x3.  For one leaf and
+// domain, C[col][q] = sum over (node i, k = 0..3) of B_k(i, q) W_k(i, col): the P2M basis rows
+// (B_0 = R_n^{-m}, B_{1..3} = grad R) times the density weights (W_0 = q_c and
+// W_k = v_c n_k + (n.v) delta_ck - n_c v_k for column col = 3 r + c, so that sum_k W_k B_k =
+// m_c . grad R + q_c R).  In real form -- row 2q + a the real (a = 0) or imaginary (a = 1) part of
+// coefficient q; K index 8 il + 2 k + b for node il of a group of four, b selecting Re / Im W --
+//   A[2q][.] = (Re B_k, -Im B_k),  A[2q+1][.] = (Im B_k, Re B_k),  B[col][.] = (Re W_k, Im W_k),
+// a 128 x NT x (8 per node) product per (leaf, domain, column tile).  Both operands are formed in
+// registers from the basis table and the densities, split into bf16 hi / lo parts and stored into
+// shared memory in the 64-byte-swizzled K-major layout (one K block of 32 = four nodes per stage,
+// two stages), then thread 0 issues A_hi B_hi + A_hi B_lo + A_lo B_hi (tcgen05.mma kind::f16, FP32
+// in tensor memory) after a proxy fence and a block barrier; the stage is rebuilt once the MMAs'
+// commit has arrived on its mbarrier (a bounded wait).  The epilogue writes the bf16 hi / lo split
+// of C (the operands of the tensor-core M2M and M2L, the only readers of the leaves' expansions on
+// this path), and the FP32 values too when C is given.
+constexpr int P2M_TC_THREADS = 256, P2M_TC_STAGES = 2;
+constexpr uint32_t P2M_TC_A_BYTES = TC_M * KBLK * 2 * 2;  // hi + lo, 16 KiB
+
+struct P2mTc {
+    int64_t N, nr, nbox;
+    int p2, ncols, nt, ntile;  // columns per tile: a multiple of 48 (whole right-hand sides, N % 16 == 0)
+    uint32_t tmem_cols;
+};
+
+// eight floats -> eight bf16 hi parts and eight bf16 lo parts (x - hi), as 16-byte words
+__device__ __forceinline__ void split8_bf16(const float *v, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+        h[j] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[j] = *reinterpret_cast<const uint32_t *>(&ll);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__global__ void __launch_bounds__(P2M_TC_THREADS, 2)
+    k_p2m_tc(const P2mTc P, const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ nbeg,
+             const int32_t *__restrict__ nend, const int32_t *__restrict__ dom, const float *__restrict__ nrm,
+             const float2 *__restrict__ dens, const float2 *__restrict__ Bp2m, float *C, __nv_bfloat16 *Ch,
+             __nv_bfloat16 *Cl, int *err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t empty[P2M_TC_STAGES], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    __shared__ int s_fin;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t lf = blockIdx.x / P.ntile;
+    const int tile = (int)(blockIdx.x - lf * P.ntile), d = blockIdx.y;
+    const int64_t g = leaf_box[lf];
+    const int col0 = tile * P.nt;
+    const int nh = min(P.nt, P.ncols - col0);  // valid columns of the tile
+    const int side = d == 0 ? 0 : 1;
+    const float sg = d == 0 ? -1.f : 1.f;
+    const int i0 = nbeg[g], i1 = nend[g];
+    const int nkb = (i1 - i0 + 3) / 4;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;  // swizzle atoms: 512-byte alignment
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    const uint32_t b_half = (uint32_t)P.nt * 64u;  // one K block of B, hi or lo
+    const uint32_t stage_bytes = P2M_TC_A_BYTES + 2u * b_half;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P2M_TC_STAGES; ++s) mbar_init(&empty[s], 1);
+        mbar_init(&done, 1);
+        s_abort = *(volatile int *)err;  // an earlier CTA timed out: issue nothing
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(P.tmem_cols)
+                     : "memory");
+        // give up the allocation permit at once: the next CTA on this SM may allocate (and be
+        // resident) while this one runs
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_bf16(P.nt);
+    int issued = 0;  // K blocks whose MMAs thread 0 issued
+
+    // Each thread stages the same two A items (q0 = tid / 8 and q0 + 32, node il_a, part a) and at
+    // most one B item (node il_b, right-hand side rl) of every K block.  Their global inputs are
+    // loaded one K block ahead into registers (nxt) while the current block (cur) is converted
+    // and stored, so the loads overlap the stores, the barriers and the MMAs.
+    const int a_part = threadIdx.x & 1, il_a = (threadIdx.x >> 1) & 3, q0 = threadIdx.x >> 3;
+    const int il_b = threadIdx.x & 3, rl = threadIdx.x >> 2;
+    const bool b_item = rl < P.nt / 3 && 3 * rl < nh;
+    const int64_t r_b = col0 / 3 + rl;
+    struct In {
+        float2 a[2][4];  // B_k(i, q0), B_k(i, q0 + 32)
+        int dom_a, dom_b;
+        float2 b[6];     // the densities (v, q) of node il_b, right-hand side r_b
+        float n[3];
+    };
+    auto load = [&](In &x, int kb) {
+        const int ia = i0 + 4 * kb + il_a, ibn = i0 + 4 * kb + il_b;
+        x.dom_a = -1;
+        x.dom_b = -1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x.a[h][k] = make_float2(0.f, 0.f);
+        if (ia < i1) {
+            x.dom_a = dom[ia];
+            const float2 *Bq = Bp2m + ((int64_t)side * P.N + ia) * 4 * P.p2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (q0 + 32 * h < P.p2)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x.a[h][k] = Bq[(int64_t)k * P.p2 + q0 + 32 * h];
+        }
+        if (b_item && ibn < i1) {
+            x.dom_b = dom[ibn];
+            const float2 *dn = dens + (((int64_t)side * P.nr + r_b) * P.N + ibn) * 6;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) x.b[c] = dn[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x.n[c] = nrm[3 * ibn + c];
+        }
+    };
+    In cur, nxt;
+    if (nkb > 0) load(cur, 0);
+
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % P2M_TC_STAGES;
+        if (threadIdx.x == 0 && kb >= P2M_TC_STAGES && !s_abort &&
+            !mbar_wait(&empty[s], (uint32_t)(kb / P2M_TC_STAGES - 1) & 1u)) {
+            atomicExch(err, 1);
+            s_abort = 1;
+        }
+        __syncthreads();  // stage s is free again (or the CTA gives up)
+        if (s_abort) break;
+        if (kb + 1 < nkb) load(nxt, kb + 1);
+        __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(gbase + (size_t)s * stage_bytes);
+        __nv_bfloat16 *sB = sA + P2M_TC_A_BYTES / 2;
+        // A: item (q, node il, part a) -> the 16-byte chunk il of row 2q + a (hi and lo); the
+        // eight threads of a shared-memory phase fill two whole rows
+        {
+            const bool ok = cur.dom_a >= 0 && (d == 0 || cur.dom_a == d);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 b = ok ? cur.a[h][k] : make_float2(0.f, 0.f);
+                    v[2 * k] = a_part == 0 ? b.x : b.y;
+                    v[2 * k + 1] = a_part == 0 ? -b.y : b.x;
+                }
+                uint4 hi, lo;
+                split8_bf16(v, hi, lo);
+                const int o = sw64_index(2 * (q0 + 32 * h) + a_part, 8 * il_a);
+                *reinterpret_cast<uint4 *>(sA + o) = hi;
+                *reinterpret_cast<uint4 *>(sA + TC_M * KBLK + o) = lo;
+            }
+        }
+        // B: item (right-hand side rl of the tile, node il) -> chunk il of rows 3 rl + c
+        if (rl < P.nt / 3) {
+            float w[3][8];
+            if (cur.dom_b >= 0 && (d == 0 || cur.dom_b == d)) {
+                const float2 *v = cur.b;
+                const float n[3] = {sg * cur.n[0], sg * cur.n[1], sg * cur.n[2]};
+                const float nvr = n[0] * v[0].x + n[1] * v[1].x + n[2] * v[2].x;
+                const float nvi = n[0] * v[0].y + n[1] * v[1].y + n[2] * v[2].y;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    w[c][0] = v[3 + c].x;
+                    w[c][1] = v[3 + c].y;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        float tr = n[k] * v[c].x - n[c] * v[k].x, ti = n[k] * v[c].y - n[c] * v[k].y;
+                        if (k == c) {
+                            tr += nvr;
+                            ti += nvi;
+                        }
+                        w[c][2 + 2 * k] = tr;
+                        w[c][3 + 2 * k] = ti;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) w[c][k] = 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint4 hi, lo;
+                split8_bf16(w[c], hi, lo);
+                const int o = sw64_index(3 * rl + c, 8 * il_b);
+                *reinterpret_cast<uint4 *>(sB + o) = hi;
+                *reinterpret_cast<uint4 *>(sB + P.nt * KBLK + o) = lo;
+            }
+        }
+        if (kb + 1 < nkb) cur = nxt;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the MMAs read what was stored
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t aA = sbase + (uint32_t)s * stage_bytes, aB = aA + P2M_TC_A_BYTES;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {  // K = 16 bf16 per MMA = 32 bytes along the 64-byte row
+                const uint64_t ah = smem_desc_sw64(aA + 32u * j), al = smem_desc_sw64(aA + 8192u + 32u * j);
+                const uint64_t bh = smem_desc_sw64(aB + 32u * j), bl = smem_desc_sw64(aB + b_half + 32u * j);
+                mma_bf16(tmem, ah, bh, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+                mma_bf16(tmem, ah, bl, idesc, 1u);
+                mma_bf16(tmem, al, bh, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+            ++issued;
+        }
+    }
+    if (threadIdx.x == 0) {
+        bool fin = !s_abort && issued == nkb;
+        if (issued > 0) {
+            mma_commit(&done);  // arrives once every MMA issued above has completed
+            if (!mbar_wait(&done, 0)) {
+                fin = false;
+                atomicExch(err, 1);
+            }
+        }
+        s_fin = fin ? 1 : 0;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    const int64_t ob = (((int64_t)d * P.nbox + g) * P.ncols + col0) * 2 * P.p2;
+    if (nkb == 0) {  // no sources: a zero expansion
+        for (int i = threadIdx.x; i < nh * 2 * P.p2; i += blockDim.x) {
+            if (C) C[ob + i] = 0.f;
+            Ch[ob + i] = __float2bfloat16_rn(0.f);
+            Cl[ob + i] = __float2bfloat16_rn(0.f);
+        }
+    } else if (s_fin) {
+        // warp w reads accumulator lanes 32 (w mod 4) .. + 31 (real-form rows R); warps 0-3 take the
+        // even 16-column groups, warps 4-7 the odd ones
+        const int R = (warp & 3) * 32 + lane;
+        const bool row_ok = R < 2 * P.p2;
+        for (int c0 = 16 * (warp >> 2); c0 < P.nt; c0 += 32) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row_ok)
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < nh) {
+                        const float x = __uint_as_float(v[j]);
+                        const int64_t o = ob + (int64_t)(c0 + j) * 2 * P.p2 + R;
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                        if (C) C[o] = x;
+                        Ch[o] = hi;
+                        Cl[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                    }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -863,12 +1134,16 @@ static TcSetup tc_setup(fmbem *h, float *C, float *D, int64_t nr, bool bf3) {
 // the other boxes' parts are written below), then one launch per level, l_max - 1 down to 2, in
 // which every box sums the S|S products of its children and writes its expansion in FP32 and
 // split; the M2L + L2L pass then finds C split (run_m2l_tc with c_split)
-void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s) {
+// (leaves_split: run_p2m_tc wrote the leaves' expansions split already, and the M2M launches write
+// every other box of levels 2 .. l_max - 1, so the split pass is skipped)
+void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s, bool leaves_split) {
     const int64_t ncols = 3 * nr;
     const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
     __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
-    k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
-    CKL("k_split_bf16");
+    if (!leaves_split) {
+        k_split_bf16<<<152 * 8, 256, 0, s>>>(C, Chi, Clo, nfloat);
+        CKL("k_split_bf16");
+    }
     const TcSetup t = tc_setup(h, C, C, nr, true);
     for (int l = h->lmax; l >= 3; --l) {
         const LevelInfo &Lv = h->lev[l - 1];  // the parents
@@ -880,6 +1155,36 @@ void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s) {
                                                  h->tc_err, h->box_cbeg, h->box_cend);
         CKL("k_m2l_tc (M2M)");
     }
+}
+
+// P2M of the leaves on the tensor cores (k_p2m_tc): BF16x3, 2 p^2 <= 128, 16 or more right-hand
+// sides; the second half of C receives the bf16 hi / lo split of the leaves' expansions (run_m2m_tc
+// with leaves_split)
+bool p2m_tc_supported(const fmbem *h, int64_t nr) { return 2 * h->p2 <= TC_M && nr >= 16; }
+
+void run_p2m_tc(fmbem *h, const float *dens, const float *Bp2m, float *C, int64_t nr, cudaStream_t s) {
+    if (!p2m_tc_supported(h, nr)) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "tensor-core P2M: unsupported shape"};
+    if (!h->tc_err) throw fmbem_error{FMBEM_ERR_CUDA, "tensor-core P2M: the error flag was not allocated"};
+    const int64_t ncols = 3 * nr;
+    const int64_t nfloat = (int64_t)(h->J + 1) * h->nbox * ncols * 2 * h->p2;
+    __nv_bfloat16 *Chi = (__nv_bfloat16 *)(C + nfloat), *Clo = Chi + nfloat;
+    // tiles of whole right-hand sides: 48-column units, up to four (192 columns) per tile
+    const int units = (int)((ncols + 47) / 48), ntile = (units + 3) / 4;
+    const int nt = 48 * ((units + ntile - 1) / ntile);
+    const uint32_t tcols = nt <= 64 ? 64u : nt <= 128 ? 128u : 256u;
+    // shared memory: two stages; at least enough that no more CTAs share an SM than its 512 TMEM
+    // columns hold (an allocation would otherwise wait for another CTA to free its columns)
+    const int per_sm = 512 / (int)tcols;
+    const size_t need = 1024 + P2M_TC_STAGES * (P2M_TC_A_BYTES + (size_t)nt * 128);
+    const size_t smem = std::max(need, (size_t)(228 * 1024) / (per_sm + 1) + 1024);
+    CK(cudaFuncSetAttribute(k_p2m_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const P2mTc P{h->N, nr, h->nbox, h->p2, (int)ncols, nt, ntile, tcols};
+    const dim3 grid((unsigned)(h->n_leaves * ntile), (unsigned)(h->Jf + 1));
+    // the FP32 copy of the leaves' expansions is not written: M2M and M2L read the split
+    k_p2m_tc<<<grid, P2M_TC_THREADS, smem, s>>>(P, h->leaf_box, h->box_nbeg, h->box_nend, h->dom, h->nrm_f,
+                                                (const float2 *)dens, (const float2 *)Bp2m, nullptr, Chi, Clo,
+                                                h->tc_err);
+    CKL("k_p2m_tc");
 }
 
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3, bool c_split) {

@@ -35,10 +35,12 @@ def to_dev(x):
 
 @pytest.mark.parametrize("n_rhs,p", [(16, 8), (100, 8), (40, 6), (24, 4)])
 def test_bf16x3_tensor_core_m2l_matches_fp32(n_rhs, p):
-    """The BF16x3 tensor-core M2L + L2L (hi/lo bf16 operands, three products per step) on the
-    cases of the TF32 test (one 48-column tile, two ragged 160-column tiles, p = 6 with a partial
-    last K block, p = 4): it must agree with the FP32 CUDA-core product to ~1e-5 (the split leaves
-    ~2^-16 per product where TF32 leaves ~2^-11), be deterministic, and match the oracle rows."""
+    """The BF16x3 tensor-core passes (hi/lo bf16 operands, three products per step: P2M of the
+    leaves with 48-, 96-, 144- and 192-column tiles, the last one ragged at 100 RHS; M2M; M2L +
+    L2L) on the cases of the TF32 test (one 48-column tile, two ragged 160-column tiles, p = 6 with
+    a partial last K block, p = 4): it must agree with the FP32 CUDA-core product to ~1e-5 (the
+    split leaves ~2^-16 per product where TF32 leaves ~2^-11), be deterministic, and match the
+    oracle rows."""
     V, F, D = fi.icosphere(5)  # 10242 nodes, l_max 3: both S|R and R|R products
     eps, mu, k0 = [1.0, -8.5 + 0.3j], [1.0, 1.0], 0.5
     o = oracle.Oracle(V, F, D, eps, mu, k0)
