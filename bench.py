@@ -418,16 +418,17 @@ def hbm_peak():
 def gmres_roofline(N, iters, restart, ms_total, matvec_ms):
     """Roofline of the plain FP64 GMRES(m) work outside the products, per Arnoldi step: the
     solve's time less its products (iters Arnoldi products + one true residual per cycle + the
-    final one), over the algorithmic bytes and FP64 flops of the steps it ran.  Step j (j + 1
-    basis vectors, b = 96 bytes per node per vector): preconditioner (V_j, the 6 x 6 LU factors,
-    z: 2b + 582), classical Gram-Schmidt twice (dots: (j + 2) b, subtract: (j + 3) b, each pass),
-    norm (b) and scale (2b); FP64 flops 2 passes x 2 x (j + 1) x 6 complex MACs (8 flops) per
-    node plus the LU solve (288)."""
+    final one), over the algorithmic bytes and FP64 flops of the steps it ran.  Step j (slots
+    0..j of the basis, b = 96 bytes per node per vector): preconditioner (u_j, the 6 x 6 LU
+    factors, z: 2b + 582); classical Gram-Schmidt twice with the second pass delayed: one
+    reduction of slots 0..j against u_j and w ((j + 2) b), the norm of w (b), one update pass
+    (slots 0..j and w read, v_j and u_{j+1} written: (j + 4) b); FP64 flops (2 (j + 1) + 2 j + 2)
+    x 6 complex MACs (8 flops) per node plus the LU solve (288)."""
     b = 96.0
     js = [k % restart for k in range(iters)]
     cycles = (iters + restart - 1) // restart
-    step_bytes = sum(582.0 + b * (4 * j + 15) for j in js) * N / max(iters, 1)
-    step_flops = sum(192.0 * (j + 1) + 288.0 for j in js) * N / max(iters, 1)
+    step_bytes = sum(582.0 + b * (2 * j + 9) for j in js) * N / max(iters, 1)
+    step_flops = sum(48.0 * (4 * j + 4) + 288.0 for j in js) * N / max(iters, 1)
     products = iters + cycles + 1
     over_ms = (ms_total - products * matvec_ms) / max(iters, 1)
     hbm, hsrc = hbm_peak()
@@ -543,7 +544,8 @@ def run_batched(args, world, flush):
                value=job_throughput(N * nr, world, ms), unit=UNIT, ms_per_step=ms, steps=args.steps,
                roofline=dict(roof[dom], kernel=dom), phase_roofline=roof)
 
-    # e2e through the C ABI: pinned host x -> device, matvec, device -> pinned host y
+    # e2e through the C ABI with host buffers (fmbem_matvec_host): pinned host x -> device,
+    # matvec, device -> pinned host y (one chunk of 128 right-hand sides)
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -551,9 +553,7 @@ def run_batched(args, world, flush):
     for k in range(args.warmup + args.steps):
         flush.fill_(float(k))
         e0.record(stream)
-        x.copy_(xh, non_blocking=True)
-        g.matvec(x, y, precision=fm.BF16X3)
-        yh.copy_(y, non_blocking=True)
+        g.matvec_host(xh, yh, precision=fm.BF16X3, stream=stream, sync=False)
         e1.record(stream)
         e1.synchronize()
         if k >= args.warmup:
@@ -782,22 +782,19 @@ def run_ours(args):
     value = job_throughput(N * nr, world, ms_step)
     roof = roofline(info, p, nr, n_dom, phases, args.precision, args.workload)
 
-    # e2e through the C ABI: pinned host x -> device, matvec, device -> pinned host y
+    # e2e through the C ABI with host buffers (fmbem_matvec_host): pinned host x -> device,
+    # matvec, device -> pinned host y, the copies inside the timed region
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     for _ in range(2):
-        x.copy_(xh, non_blocking=True)
-        g.matvec(x, y, precision=prec)
-        yh.copy_(y, non_blocking=True)
+        g.matvec_host(xh, yh, precision=prec)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = []
     for k in range(args.steps):
         flush.fill_(float(k))
         e0.record(stream)
-        x.copy_(xh, non_blocking=True)
-        g.matvec(x, y, precision=prec)
-        yh.copy_(y, non_blocking=True)
+        g.matvec_host(xh, yh, precision=prec, stream=stream, sync=False)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))

@@ -260,6 +260,25 @@ fmbem_status fmbem_plane_wave_rhs(fmbem *h, int64_t n_rhs, const double *dir, co
  * demand, so the first call with a larger n_rhs allocates. */
 fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision, void *stream);
 
+/* The same product with x and y in HOST memory, the copies included: the right-hand sides are
+ * taken in chunks of chunk_rhs; chunk k is copied to the device, multiplied (exactly the kernels
+ * of fmbem_matvec with n_rhs = the chunk's size) and copied back, with the copy of chunk k + 1 to
+ * the device and of chunk k - 1 back on two internal copy streams, running beside the product
+ * of chunk k.  The paper has no counterpart (its data never leave one machine's memory); this is
+ * a library-level variant for callers whose right-hand sides arrive in and leave through host
+ * memory.
+ *   x_host, y_host  host [n_rhs][N][6] complex128 (user order), read / written; page-locked
+ *                   (cudaHostAlloc, torch pin_memory) for the copies to overlap the kernels.
+ *   chunk_rhs       right-hand sides per chunk (>= 0); 0 = the library's choice: chunks of
+ *                   up to 128 right-hand sides (one chunk for a batch of 128 or fewer).
+ *   stream          the products run on it, and it waits for the last copy back: y_host is
+ *                   complete once the work queued on the stream so far has completed (the call
+ *                   itself may return earlier).  x_host must stay unchanged until then.
+ * Device memory: four chunk-sized buffers (two for x, two for y), owned by the handle and grown
+ * on demand, plus the product's own scratch. */
+fmbem_status fmbem_matvec_host(fmbem *h, const void *x_host, void *y_host, int64_t n_rhs, int precision,
+                               int64_t chunk_rhs, void *stream);
+
 /* y = A^T x, the transpose (complex bilinear, no conjugation) of the operator of Eq. (2.9) as
  * fmbem_matvec evaluates it; A^H x is conj(A^T conj(x)).  The paper has no adjoint; it is the
  * product an adjoint (gradient) solve needs.  Gathering the transposed blocks of Eq. (2.12) at a

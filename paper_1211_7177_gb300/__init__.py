@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True):
         "fmbem_tree_levels": (i32, [P, i32, P, P]),
         "fmbem_plane_wave_rhs": (i32, [P, i64, P, P, P, P]),
         "fmbem_matvec": (i32, [P, P, P, i64, i32, P]),
+        "fmbem_matvec_host": (i32, [P, P, P, i64, i32, i64, P]),
         "fmbem_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
         "fmbem_adjoint_matvec": (i32, [P, P, P, i64, i32, P]),
         "fmbem_adjoint_solve": (i32, [P, P, P, i64, dbl, i32, P, P, P]),
@@ -260,6 +261,40 @@ def fmbem_matvec(h, x, y=None, precision=FP64, stream=None):
     y = torch.empty_like(x) if y is None else _dev(y, N, "y", out=True)
     _check(h, load_library().fmbem_matvec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                           x.shape[0], int(precision), _stream(stream)))
+    return y
+
+
+def _host(t, N, name, out=False):
+    """Checks a host vector [n_rhs, N, 6] complex128 (a CPU tensor, pinned for overlapped copies)."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous complex128 CPU tensor")
+    if t.is_conj() or t.is_neg():
+        if out:
+            raise TypeError(f"{name} must not be a conjugate or negative view (it is written in place)")
+        t = t.resolve_conj().resolve_neg()
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if t.dim() != 3 or t.shape[1] != N or t.shape[2] != 6:
+        raise ValueError(f"{name} must have shape [n_rhs, {N}, 6]")
+    return t
+
+
+def fmbem_matvec_host(h, x, y=None, precision=FP64, chunk_rhs=0, stream=None, sync=True):
+    """y = A x with x and y in host memory (CPU tensors; pinned for the copies to overlap the
+    kernels), the copies included (see include/fmbem.h).  sync=False returns once the work is
+    queued: y is complete when the stream has completed it."""
+    import torch
+    N = fmbem_num_nodes(h)
+    x = _host(x, N, "x")
+    y = torch.empty(x.shape, dtype=x.dtype, pin_memory=x.is_pinned()) if y is None else _host(y, N, "y", out=True)
+    _check(h, load_library().fmbem_matvec_host(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                               x.shape[0], int(precision), int(chunk_rhs), _stream(stream)))
+    if sync:
+        if isinstance(stream, int):
+            torch.cuda.synchronize()
+        else:
+            (stream if stream is not None else torch.cuda.current_stream()).synchronize()
     return y
 
 
@@ -500,6 +535,9 @@ class FMBEM:
 
     def matvec(self, x, y=None, precision=FP64, stream=None):
         return fmbem_matvec(self.h, x, y, precision, stream)
+
+    def matvec_host(self, x, y=None, precision=FP64, chunk_rhs=0, stream=None, sync=True):
+        return fmbem_matvec_host(self.h, x, y, precision, chunk_rhs, stream, sync)
 
     def adjoint_matvec(self, x, y=None, precision=FP64, stream=None):
         return fmbem_adjoint_matvec(self.h, x, y, precision, stream)

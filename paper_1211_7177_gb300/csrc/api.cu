@@ -54,6 +54,12 @@ static void free_all(fmbem *h) {
     for (cudaEvent_t *e : {&h->ev_fork, &h->ev_join})
         if (*e) { cudaEventDestroy(*e); *e = nullptr; }
     if (h->aux_stream) { cudaStreamDestroy(h->aux_stream); h->aux_stream = nullptr; }
+    for (auto &e : h->io_ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (auto &st : h->io_stream)
+        if (st) { cudaStreamDestroy(st); st = nullptr; }
+    h->io_buf = nullptr;  // freed with the allocations above
+    h->io_bytes = 0;
 }
 
 // wraps a call: converts exceptions into a status and the handle's message
@@ -308,6 +314,20 @@ fmbem_status fmbem_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rh
         return FMBEM_ERR_INVALID_ARGUMENT;
     }
     return guarded(h, [&] { run_matvec(h, (const c64 *)x_dev, (c64 *)y_dev, n_rhs, precision, (cudaStream_t)stream); });
+}
+
+fmbem_status fmbem_matvec_host(fmbem *h, const void *x_host, void *y_host, int64_t n_rhs, int precision,
+                               int64_t chunk_rhs, void *stream) {
+    if (!h) return FMBEM_ERR_INVALID_ARGUMENT;
+    if (n_rhs < 1 || chunk_rhs < 0 || !x_host || !y_host || x_host == y_host ||
+        (precision != FMBEM_FP64 && precision != FMBEM_FP32 && precision != FMBEM_TF32 && precision != FMBEM_BF16X3)) {
+        h->err = "invalid argument (n_rhs >= 1, chunk_rhs >= 0, distinct non-NULL x and y, precision FP64, FP32, "
+                 "TF32 or BF16X3)";
+        return FMBEM_ERR_INVALID_ARGUMENT;
+    }
+    return guarded(h, [&] {
+        run_matvec_host(h, (const c64 *)x_host, (c64 *)y_host, n_rhs, precision, chunk_rhs, (cudaStream_t)stream);
+    });
 }
 
 fmbem_status fmbem_adjoint_matvec(fmbem *h, const void *x_dev, void *y_dev, int64_t n_rhs, int precision,

@@ -244,6 +244,12 @@ struct fmbem {
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool have_times = false;
+    // host-buffer products (fmbem_matvec_host): copy streams (to and from the device), their
+    // events, and the chunk buffers (two x slots, two y slots)
+    cudaStream_t io_stream[2] = {nullptr, nullptr};
+    cudaEvent_t io_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *io_buf = nullptr;
+    size_t io_bytes = 0;
 
     std::vector<void *> allocations;
 };
@@ -308,6 +314,8 @@ void build_tables(fmbem *h, cudaStream_t s);
 // per-call operations
 void run_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_matvec_noalloc(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
+void run_matvec_host(fmbem *h, const c64 *x_host, c64 *y_host, int64_t n_rhs, int precision, int64_t chunk_rhs,
+                     cudaStream_t s);
 void run_adjoint_matvec(fmbem *h, const c64 *x, c64 *y, int64_t n_rhs, int precision, cudaStream_t s);
 void run_near_field_functional(fmbem *h, int64_t nf, int64_t n_pts, const double *pts_host, const c64 *cE_host,
                                const c64 *cH_host, c64 *out, cudaStream_t s);

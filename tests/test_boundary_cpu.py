@@ -92,6 +92,7 @@ def test_boundary_option_and_null_handles_rejected():
     assert lib.fmbem_interior_field(N, 1, 1, 1, p3, p3, pc, None, None) == 1
     assert lib.fmbem_near_field_fmm(N, 1, 1, 1, p3, None, None, pc, None, None) == 1
     assert lib.fmbem_near_field(N, 1, 1, 1, p3, None, None, pc, None, None) == 1
+    assert lib.fmbem_matvec_host(N, pc, pc, 1, 0, 0, None) == 1
 
 
 def test_injected_device_budget_fails_create_with_oom():
