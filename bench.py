@@ -373,22 +373,22 @@ def run_gradients(fd_check=False):
 # records the SHA-256 prefixes of the kernel sources it was taken with, and the bench reports null
 # once a source has changed.
 TRAFFIC = {
-    ('silver_sphere_s7', 'fp64', 1, 'p2m'): dict(bytes=2213297920, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp64', 1, 'm2m'): dict(bytes=117221888, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp64', 1, 'm2l_l2l'): dict(bytes=5563443968, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp64', 1, 'near_l2p_self'): dict(bytes=6585120256, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp32', 1, 'p2m'): dict(bytes=1114339328, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp32', 1, 'm2m'): dict(bytes=58548736, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp32', 1, 'm2l_l2l'): dict(bytes=2676558848, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'fp32', 1, 'near_l2p_self'): dict(bytes=465758976, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'bf16x3', 1, 'p2m'): dict(bytes=1114337792, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'bf16x3', 1, 'm2m'): dict(bytes=58540800, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'bf16x3', 1, 'm2l_l2l'): dict(bytes=3281379328, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('silver_sphere_s7', 'bf16x3', 1, 'near_l2p_self'): dict(bytes=465598720, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('torus_512x128', 'bf16x3', 128, 'p2m'): dict(bytes=5644286208, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('torus_512x128', 'bf16x3', 128, 'm2m'): dict(bytes=3871661568, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('torus_512x128', 'bf16x3', 128, 'm2l_l2l'): dict(bytes=4913641984, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
-    ('torus_512x128', 'bf16x3', 128, 'near_l2p_self'): dict(bytes=4970880768, src={'fmm.cu': '0939e62589e2a5e5', 'm2l_tc.cu': '2f4bc0eca4871fbe'}),
+    ('silver_sphere_s7', 'fp64', 1, 'p2m'): dict(bytes=2213201920, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp64', 1, 'm2m'): dict(bytes=117108224, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp64', 1, 'm2l_l2l'): dict(bytes=5562462208, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp64', 1, 'near_l2p_self'): dict(bytes=6584094976, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp32', 1, 'p2m'): dict(bytes=1114464768, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp32', 1, 'm2m'): dict(bytes=58543872, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp32', 1, 'm2l_l2l'): dict(bytes=2676097536, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'fp32', 1, 'near_l2p_self'): dict(bytes=466597632, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'p2m'): dict(bytes=1114493696, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'm2m'): dict(bytes=58550272, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'm2l_l2l'): dict(bytes=3222970368, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('silver_sphere_s7', 'bf16x3', 1, 'near_l2p_self'): dict(bytes=465327104, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('torus_512x128', 'bf16x3', 128, 'p2m'): dict(bytes=4813660416, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('torus_512x128', 'bf16x3', 128, 'm2m'): dict(bytes=1576931584, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('torus_512x128', 'bf16x3', 128, 'm2l_l2l'): dict(bytes=4895353600, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
+    ('torus_512x128', 'bf16x3', 128, 'near_l2p_self'): dict(bytes=4966780416, src={'fmm.cu': '2883887ae990ff96', 'm2l_tc.cu': '0f9157a819001c6f'}),
 }
 
 
@@ -417,8 +417,9 @@ def hbm_peak():
 
 def gmres_roofline(N, iters, restart, ms_total, matvec_ms):
     """Roofline of the plain FP64 GMRES(m) work outside the products, per Arnoldi step: the
-    solve's time less its products (iters Arnoldi products + one true residual per cycle + the
-    final one), over the algorithmic bytes and FP64 flops of the steps it ran.  Step j (slots
+    solve's time less its products (iters Arnoldi products + one true residual per cycle after the
+    first -- x0 = 0 makes the first residual b itself -- + the final one), over the algorithmic
+    bytes and FP64 flops of the steps it ran.  Step j (slots
     0..j of the basis, b = 96 bytes per node per vector): preconditioner (u_j, the 6 x 6 LU
     factors, z: 2b + 582); classical Gram-Schmidt twice with the second pass delayed: one
     reduction of slots 0..j against u_j and w ((j + 2) b), the norm of w (b), one update pass
@@ -429,7 +430,7 @@ def gmres_roofline(N, iters, restart, ms_total, matvec_ms):
     cycles = (iters + restart - 1) // restart
     step_bytes = sum(582.0 + b * (2 * j + 9) for j in js) * N / max(iters, 1)
     step_flops = sum(48.0 * (4 * j + 4) + 288.0 for j in js) * N / max(iters, 1)
-    products = iters + cycles + 1
+    products = iters + cycles
     over_ms = (ms_total - products * matvec_ms) / max(iters, 1)
     hbm, hsrc = hbm_peak()
     ach_gbs = step_bytes / (over_ms * 1e-3) / 1e9 if over_ms > 0 else None
@@ -455,10 +456,11 @@ def tensor_peak_bf16x3():
 
 
 def phase_rooflines(info, p, nr, n_dom, N, phases, workload, form="bf16x3"):
-    """Per-phase roofline of the batched matvec: near field and P2M against the FP32 ALU peak, M2L +
-    L2L (algorithmic flops of the dense complex contraction) against the tensor peak of the form
-    (BF16x3: the BF16 rate over three; TF32), M2M against the BF16x3 tensor peak in that form (it
-    runs on the tensor cores there) and against the FP32 ALU peak in the TF32 form."""
+    """Per-phase roofline of the batched matvec: near field against the FP32 ALU peak, M2L + L2L
+    (algorithmic flops of the dense complex contraction) against the tensor peak of the form
+    (BF16x3: the BF16 rate over three; TF32), M2M and P2M against the BF16x3 tensor peak in that
+    form (they run on the tensor cores there; the P2M phase also forms the densities, k_prep) and
+    against the FP32 ALU peak in the TF32 form."""
     keys = ["p2m", "m2m", "m2l_l2l", "near_l2p_self"]
     avg = {k: statistics.mean(ph[k] for ph in phases) for k in keys}
     tpk, tsrc = tensor_peak_bf16x3() if form == "bf16x3" else tensor_peak_tf32()
@@ -475,7 +477,7 @@ def phase_rooflines(info, p, nr, n_dom, N, phases, workload, form="bf16x3"):
     }
     out = {}
     for k in keys:
-        tensor = k == "m2l_l2l" or (k == "m2m" and form == "bf16x3")
+        tensor = k == "m2l_l2l" or (k in ("m2m", "p2m") and form == "bf16x3" and nr >= 16 and 2 * p * p <= 128)
         peak = tpk if tensor else PEAK_TFLOPS["fp32"]
         ach = flops[k] / (avg[k] * 1e-3) / 1e12
         out[k] = dict(bound="tensor" if tensor else "alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
@@ -563,7 +565,7 @@ def run_batched(args, world, flush):
                       h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes)
     y_bf3 = yh.numpy().copy()
     # the TF32 operand form of the same product, for comparison (faster rounding, less accurate)
-    ms_tf, _ = time_matvec(x, y, fm.TF32, args.steps, 2, with_phases=False)
+    ms_tf, _ = time_matvec(x, y, fm.TF32, args.steps, args.warmup, with_phases=False)
     y_tf32 = y.cpu().numpy()
     out["tf32_form"] = dict(value=job_throughput(N * nr, world, ms_tf), unit=UNIT, ms_per_step=ms_tf)
 
