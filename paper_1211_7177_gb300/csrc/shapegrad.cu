@@ -7,7 +7,8 @@
 // s_u, weight w_u, normal n_u) of the nodes of the vertex's 1-ring and through their self blocks
 // (Appendix B).  Here the sensitivities of G = L^T x + lambda^T b - lambda^T A x to the node data
 // of every node are summed over all partners (the pair blocks of Eq. 2.12 depend on s_a, s_b,
-// w_b and n_b), by closed-form pair derivatives in FP64, O(N^2) pair evaluations in all;
+// w_b and n_b), by closed-form pair derivatives (FP64 for pairs closer than 8 mean edge lengths,
+// FP32 beyond), O(N^2) pair evaluations in all;
 // k_vertex_shape_grad (geometry.cu) then chains them with the node data of each vertex's 1-ring
 // and adds the self blocks' change.
 #include <algorithm>
@@ -21,6 +22,19 @@ struct DomainC {  // per domain, as in the matvec: k, t = (eps_0 - eps_d)/eps_d,
 };
 
 __device__ __forceinline__ double dot3d(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <typename T>
+__device__ __forceinline__ T dot3(const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <typename T>
+__device__ __forceinline__ cx<T> cexp_t(cx<T> z);
+template <>
+__device__ __forceinline__ c64 cexp_t<double>(c64 z) { return cexpd(z); }
+template <>
+__device__ __forceinline__ c32 cexp_t<float>(c32 z) {
+    float sn, cs;
+    sincosf(z.im, &sn, &cs);
+    const float e = expf(z.re);
+    return c32{e * cs, e * sn};
+}
 
 // lambda_a . (pair block of Eq. 2.12 for target a, source b) x_b with r = s_b - s_a (val): the
 // background side always (normal -n_b, Psi^(0) = -Psi), the scatterer side when a and b share
@@ -30,26 +44,28 @@ __device__ __forceinline__ double dot3d(const double *a, const double *b) { retu
 // c2 = g (-k^2/R^2 - 3ik/R^3 + 3/R^4); the brackets are linear in r and n (the scatterer side's
 // density v = Phi + t n (n.Phi) depends on n too).  One exponential per domain instead of the
 // central differences' 2 per derivative.
-__device__ void pair_grad(const double *r, double wb, const double *nb, bool same, c64 k0, c64 kj, c64 tj, c64 gj,
-                          const c64 *la, const c64 *xb, c64 *val, c64 *gr, c64 *gn) {
-    const double R2 = dot3d(r, r), R = sqrt(R2);
-    const double iR = 1.0 / R;
-    const c64 *Phi = xb, *Psi = xb + 3;
-    const double nr = dot3d(nb, r);
-    c64 v0 = {0, 0}, g3[3] = {{0, 0}, {0, 0}, {0, 0}}, n3[3] = {{0, 0}, {0, 0}, {0, 0}};
+template <typename T>
+__device__ void pair_grad(const T *r, T wb, const T *nb, bool same, cx<T> k0, cx<T> kj, cx<T> tj, cx<T> gj,
+                          const cx<T> *la, const cx<T> *xb, cx<T> *val, cx<T> *gr, cx<T> *gn) {
+    using C = cx<T>;
+    const T R2 = dot3<T>(r, r), R = sqrt(R2);
+    const T iR = (T)1 / R;
+    const C *Phi = xb, *Psi = xb + 3;
+    const T nr = dot3<T>(nb, r);
+    C v0 = {0, 0}, g3[3] = {{0, 0}, {0, 0}, {0, 0}}, n3[3] = {{0, 0}, {0, 0}, {0, 0}};
     {
-        const c64 ik = {-k0.im, k0.re};
-        const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
-        const c64 c = g * (ik - c64{iR, 0}) * iR;
-        const c64 c2 = g * ((ik * ik) * (iR * iR) - ik * (3.0 * iR * iR * iR) + c64{3.0 * iR * iR * iR * iR, 0});
-        const c64 rP = r[0] * Phi[0] + r[1] * Phi[1] + r[2] * Phi[2];
-        const c64 nP = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
-        const c64 lP = la[0] * Phi[0] + la[1] * Phi[1] + la[2] * Phi[2];
-        const c64 lPs = la[0] * Psi[0] + la[1] * Psi[1] + la[2] * Psi[2];
-        const c64 ln = la[0] * nb[0] + la[1] * nb[1] + la[2] * nb[2];
-        const c64 lr = la[0] * r[0] + la[1] * r[1] + la[2] * r[2];
+        const C ik = {-k0.im, k0.re};
+        const C g = cexp_t<T>(ik * R) * (iR / (T)(4.0 * FMBEM_PI));
+        const C c = g * (ik - C{iR, 0}) * iR;
+        const C c2 = g * ((ik * ik) * (iR * iR) - ik * ((T)3 * iR * iR * iR) + C{(T)3 * iR * iR * iR * iR, 0});
+        const C rP = r[0] * Phi[0] + r[1] * Phi[1] + r[2] * Phi[2];
+        const C nP = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
+        const C lP = la[0] * Phi[0] + la[1] * Phi[1] + la[2] * Phi[2];
+        const C lPs = la[0] * Psi[0] + la[1] * Psi[1] + la[2] * Psi[2];
+        const C ln = la[0] * nb[0] + la[1] * nb[1] + la[2] * nb[2];
+        const C lr = la[0] * r[0] + la[1] * r[1] + la[2] * r[2];
         // lambda . beta with beta_q = -n_q (r.Phi) + (n.r) Phi_q + r_q (n.Phi)
-        const c64 lb = -(ln * rP) + nr * lP + lr * nP;
+        const C lb = -(ln * rP) + nr * lP + lr * nP;
         v0 = -wb * (c * lb + g * lPs);
         for (int j = 0; j < 3; ++j) {
             g3[j] = -wb * (c2 * lb * r[j] + c * (-(ln * Phi[j]) + nb[j] * lP + la[j] * nP) + c * lPs * r[j]);
@@ -57,31 +73,31 @@ __device__ void pair_grad(const double *r, double wb, const double *nb, bool sam
         }
     }
     if (same) {
-        const c64 ik = {-kj.im, kj.re};
-        const c64 g = cexpd(ik * R) * (iR / (4.0 * FMBEM_PI));
-        const c64 c = g * (ik - c64{iR, 0}) * iR;
-        const c64 c2 = g * ((ik * ik) * (iR * iR) - ik * (3.0 * iR * iR * iR) + c64{3.0 * iR * iR * iR * iR, 0});
-        const c64 *l = la + 3;
-        const c64 nP0 = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
-        const c64 tn = tj * nP0;
-        c64 v[3];
+        const C ik = {-kj.im, kj.re};
+        const C g = cexp_t<T>(ik * R) * (iR / (T)(4.0 * FMBEM_PI));
+        const C c = g * (ik - C{iR, 0}) * iR;
+        const C c2 = g * ((ik * ik) * (iR * iR) - ik * ((T)3 * iR * iR * iR) + C{(T)3 * iR * iR * iR * iR, 0});
+        const C *l = la + 3;
+        const C nP0 = nb[0] * Phi[0] + nb[1] * Phi[1] + nb[2] * Phi[2];
+        const C tn = tj * nP0;
+        C v[3];
         for (int q = 0; q < 3; ++q) v[q] = Phi[q] + nb[q] * tn;  // T_j Phi (Eq. 2.13)
-        const c64 rv = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
-        const c64 nv = nb[0] * v[0] + nb[1] * v[1] + nb[2] * v[2];
-        const c64 lv = l[0] * v[0] + l[1] * v[1] + l[2] * v[2];
-        const c64 ln = l[0] * nb[0] + l[1] * nb[1] + l[2] * nb[2];
-        const c64 lr = l[0] * r[0] + l[1] * r[1] + l[2] * r[2];
-        const c64 lPs = l[0] * Psi[0] + l[1] * Psi[1] + l[2] * Psi[2];
-        const double nn = dot3d(nb, nb);
+        const C rv = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+        const C nv = nb[0] * v[0] + nb[1] * v[1] + nb[2] * v[2];
+        const C lv = l[0] * v[0] + l[1] * v[1] + l[2] * v[2];
+        const C ln = l[0] * nb[0] + l[1] * nb[1] + l[2] * nb[2];
+        const C lr = l[0] * r[0] + l[1] * r[1] + l[2] * r[2];
+        const C lPs = l[0] * Psi[0] + l[1] * Psi[1] + l[2] * Psi[2];
+        const T nn = dot3<T>(nb, nb);
         // lambda' . beta' with beta'_q = n_q (r.v) - (n.r) v_q - r_q (n.v)
-        const c64 lb = ln * rv - nr * lv - lr * nv;
+        const C lb = ln * rv - nr * lv - lr * nv;
         v0 += -wb * (c * lb) + (gj * g) * wb * lPs;
         for (int j = 0; j < 3; ++j) {
             g3[j] += -wb * (c2 * lb * r[j] + c * (ln * v[j] - nb[j] * lv - l[j] * nv)) + (gj * c) * wb * lPs * r[j];
-            const c64 drv = tj * (r[j] * nP0 + nr * Phi[j]);                // d(r.v)/dn_j
-            const c64 dnv = v[j] + tj * (nb[j] * nP0 + nn * Phi[j]);         // d(n.v)/dn_j
-            const c64 dlv = tj * (l[j] * nP0 + ln * Phi[j]);                 // d(lambda'.v)/dn_j
-            const c64 dlb = l[j] * rv + ln * drv - r[j] * lv - nr * dlv - lr * dnv;
+            const C drv = tj * (r[j] * nP0 + nr * Phi[j]);                // d(r.v)/dn_j
+            const C dnv = v[j] + tj * (nb[j] * nP0 + nn * Phi[j]);         // d(n.v)/dn_j
+            const C dlv = tj * (l[j] * nP0 + ln * Phi[j]);                 // d(lambda'.v)/dn_j
+            const C dlb = l[j] * rv + ln * drv - r[j] * lv - nr * dlv - lr * dnv;
             n3[j] += -wb * (c * dlb);
         }
     }
@@ -93,19 +109,25 @@ __device__ void pair_grad(const double *r, double wb, const double *nb, bool sam
 }
 
 // partial sensitivities of G's pair part over one slice of partners (closed-form pair derivatives,
-// pair_grad): part[slice][r][u][7] = dG/d(s_u (3), w_u, n_u (3)); grid (node tiles, slices, rhs)
+// pair_grad): part[slice][r][u][7] = dG/d(s_u (3), w_u, n_u (3)); grid (node tiles, slices, rhs).
+// Pairs farther apart than far_r take the derivatives in single precision (their terms are smooth
+// and small against the near pairs', where the kernel's 1/R^3 growth makes double precision
+// count); each tile's single-precision sums are added to the double accumulators.
 constexpr int SG_NT = 128, SG_NS = 32;
 __global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, const double *pos, const double *nrm,
                                                    const double *w, const int32_t *dom, const DomainC *dc,
-                                                   const c64 *x, const c64 *lam, int64_t slice_len, c64 *part) {
+                                                   const c64 *x, const c64 *lam, int64_t slice_len, double far_r,
+                                                   c64 *part) {
     __shared__ double sp[SG_NS][3], sn[SG_NS][3], sw[SG_NS];
     __shared__ int sd[SG_NS];
     __shared__ c64 sx[SG_NS][6], sl[SG_NS][6];
+    __shared__ c32 sx32[SG_NS][6], sl32[SG_NS][6];
     const int64_t u = blockIdx.x * (int64_t)SG_NT + threadIdx.x, slice = blockIdx.y, r = blockIdx.z;
     const bool valid = u < N;
     double su[3] = {0, 0, 0}, nu[3] = {0, 0, 1}, wu = 1;
     int du = 0;
     c64 xu[6], lu[6];
+    c32 xu32[6], lu32[6];
     for (int q = 0; q < 6; ++q) { xu[q] = {0, 0}; lu[q] = {0, 0}; }
     if (valid) {
         for (int q = 0; q < 3; ++q) { su[q] = pos[3 * u + q]; nu[q] = nrm[3 * u + q]; }
@@ -113,7 +135,11 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, cons
         du = dom[u];
         for (int q = 0; q < 6; ++q) { xu[q] = x[(r * N + u) * 6 + q]; lu[q] = lam[(r * N + u) * 6 + q]; }
     }
+    for (int q = 0; q < 6; ++q) { xu32[q] = to<float>(xu[q]); lu32[q] = to<float>(lu[q]); }
     const c64 k0 = dc[0].k, kj = dc[du].k, tj = dc[du].t, gj = dc[du].gamma;
+    const c32 k0f = to<float>(k0), kjf = to<float>(kj), tjf = to<float>(tj), gjf = to<float>(gj);
+    const float nuf[3] = {(float)nu[0], (float)nu[1], (float)nu[2]}, wuf = (float)wu;
+    const double far2 = far_r * far_r;
     const int64_t b0s = slice * slice_len, b1s = min(N, b0s + slice_len);
     c64 acc[7];
     for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
@@ -125,27 +151,50 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens(int64_t N, int64_t nr, cons
             for (int q = 0; q < 3; ++q) { sp[e][q] = pos[3 * m + q]; sn[e][q] = nrm[3 * m + q]; }
             sw[e] = w[m];
             sd[e] = dom[m];
-            for (int q = 0; q < 6; ++q) { sx[e][q] = x[(r * N + m) * 6 + q]; sl[e][q] = lam[(r * N + m) * 6 + q]; }
+            for (int q = 0; q < 6; ++q) {
+                sx[e][q] = x[(r * N + m) * 6 + q];
+                sl[e][q] = lam[(r * N + m) * 6 + q];
+                sx32[e][q] = to<float>(sx[e][q]);
+                sl32[e][q] = to<float>(sl[e][q]);
+            }
         }
         __syncthreads();
         if (!valid) continue;
+        c32 accf[7];
+        for (int q = 0; q < 7; ++q) accf[q] = {0, 0};
         for (int e = 0; e < nb; ++e) {
             if (b0 + e == u) continue;
             const bool same = sd[e] == du;
             const double rt[3] = {sp[e][0] - su[0], sp[e][1] - su[1], sp[e][2] - su[2]};
+            if (dot3d(rt, rt) > far2) {
+                const float rf[3] = {(float)rt[0], (float)rt[1], (float)rt[2]};
+                const float rs[3] = {-rf[0], -rf[1], -rf[2]};
+                const float snf[3] = {(float)sn[e][0], (float)sn[e][1], (float)sn[e][2]};
+                c32 val, gr[3], gn[3];
+                pair_grad<float>(rf, (float)sw[e], snf, same, k0f, kjf, tjf, gjf, lu32, sx32[e], &val, gr, nullptr);
+                for (int c = 0; c < 3; ++c) accf[c] += gr[c];
+                pair_grad<float>(rs, wuf, nuf, same, k0f, kjf, tjf, gjf, sl32[e], xu32, &val, gr, gn);
+                for (int c = 0; c < 3; ++c) {
+                    accf[c] -= gr[c];
+                    accf[4 + c] -= gn[c];
+                }
+                accf[3] -= val * (1.0f / wuf);
+                continue;
+            }
             c64 val, gr[3], gn[3];
             // u as the target: r = s_m - s_u, dG/ds_u = +dt/dr (G holds -t)
-            pair_grad(rt, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e], &val, gr, nullptr);
+            pair_grad<double>(rt, sw[e], sn[e], same, k0, kj, tj, gj, lu, sx[e], &val, gr, nullptr);
             for (int c = 0; c < 3; ++c) acc[c] += gr[c];
             // u as the source: r = s_u - s_m, dG/ds_u = -dsigma/dr, dG/dn_u, dG/dw_u = -sigma / w_u
             const double rs[3] = {-rt[0], -rt[1], -rt[2]};
-            pair_grad(rs, wu, nu, same, k0, kj, tj, gj, sl[e], xu, &val, gr, gn);
+            pair_grad<double>(rs, wu, nu, same, k0, kj, tj, gj, sl[e], xu, &val, gr, gn);
             for (int c = 0; c < 3; ++c) {
                 acc[c] -= gr[c];
                 acc[4 + c] -= gn[c];
             }
             acc[3] -= val * (1.0 / wu);
         }
+        for (int q = 0; q < 7; ++q) acc[q] += c64{(double)accf[q].re, (double)accf[q].im};
     }
     if (valid)
         for (int q = 0; q < 7; ++q) part[((slice * nr + r) * N + u) * 7 + q] = acc[q];
@@ -250,10 +299,11 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr,
                                                         const double *nrm, const double *w, const c64 *x,
                                                         int64_t n_pts, const double *pts, const c64 *cE,
                                                         const c64 *cH, c64 k0, c64 iwmu, double hs, double hn,
-                                                        c64 *sens) {
+                                                        int64_t pslice_len, c64 *part) {
     __shared__ double spt[SG_NS][3];
     __shared__ c64 sce[SG_NS][3], sch[SG_NS][3];
-    const int64_t u = blockIdx.x * (int64_t)SG_NT + threadIdx.x, r = blockIdx.y;
+    const int64_t u = blockIdx.x * (int64_t)SG_NT + threadIdx.x, r = blockIdx.y, slice = blockIdx.z;
+    const int64_t pb = slice * pslice_len, pe = min(n_pts, pb + pslice_len);
     const bool valid = u < N;
     double s[3] = {0, 0, 0}, n[3] = {0, 0, 1}, wu = 1;
     c64 xu[6];
@@ -266,8 +316,8 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr,
     c64 acc[7];
     for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
     const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
-    for (int64_t p0 = 0; p0 < n_pts; p0 += SG_NS) {
-        const int np = (int)min((int64_t)SG_NS, n_pts - p0);
+    for (int64_t p0 = pb; p0 < pe; p0 += SG_NS) {
+        const int np = (int)min((int64_t)SG_NS, pe - p0);
         __syncthreads();
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             for (int q = 0; q < 3; ++q) {
@@ -296,7 +346,16 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr,
         }
     }
     if (valid)
-        for (int q = 0; q < 7; ++q) sens[(r * N + u) * 7 + q] += acc[q];
+        for (int q = 0; q < 7; ++q) part[((slice * nr + r) * N + u) * 7 + q] = acc[q];
+}
+
+// sens[r][u] += sum over the point slices of k_node_sens_near's partial sums, fixed order
+__global__ void k_node_sens_near_reduce(int64_t N, int64_t nr, int n_slices, const c64 *part, c64 *sens) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (r, u, q)
+    if (e >= nr * N * 7) return;
+    c64 a = sens[e];
+    for (int sl = 0; sl < n_slices; ++sl) a += part[sl * nr * N * 7 + e];
+    sens[e] = a;
 }
 
 }  // namespace
@@ -320,7 +379,9 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
     ledge /= (double)(3 * nt);
     const double hs = 1e-6 * ledge, hn = 1e-6;
     const int64_t ntile = (N + SG_NT - 1) / SG_NT;
-    const int n_slices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (4 * 152 + ntile * nr - 1) / (ntile * nr)));
+    // partner slices (and point slices of the force's near-field functional): enough blocks for
+    // about 16 per SM, so that the last wave is a small part of the launch
+    const int n_slices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (16 * 152 + ntile * nr - 1) / (ntile * nr)));
     const int64_t slice_len = (N + n_slices - 1) / n_slices;
     std::vector<c64> dch(3 * (h->J + 1));
     for (int d = 0; d <= h->J; ++d) {
@@ -357,7 +418,7 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
             if (dcH) CK(cudaMemcpyAsync(dcH, cH_host, sizeof(c64) * 3 * n_pts * nr, cudaMemcpyHostToDevice, s));
         }
         k_node_sens<<<dim3((unsigned)ntile, (unsigned)n_slices, (unsigned)nr), SG_NT, 0, s>>>(
-            N, nr, h->upos, h->unrm, h->uw, h->udom, ddc, x, lam, slice_len, part);
+            N, nr, h->upos, h->unrm, h->uw, h->udom, ddc, x, lam, slice_len, 8.0 * ledge, part);
         CKL("k_node_sens");
         k_node_sens_reduce<<<dim3((unsigned)((N + 127) / 128), (unsigned)nr), 128, 0, s>>>(
             N, nr, n_slices, part, h->upos, h->unrm, h->uw, h->k[0], dd, dp, rhat_host ? dr : nullptr, dcf, x, lam, hs,
@@ -365,9 +426,13 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
         CKL("k_node_sens_reduce");
         if (nearf) {
             const c64 iwmu = c64{0, h->k0} * h->mu[0];  // i omega mu_0 with omega = k0 (c = 1)
-            k_node_sens_near<<<dim3((unsigned)ntile, (unsigned)nr), SG_NT, 0, s>>>(
-                N, nr, h->upos, h->unrm, h->uw, x, n_pts, dpt, dcE, dcH, h->k[0], iwmu, hs, hn, sens);
+            // point slices into the partner-slice buffer (free again after k_node_sens_reduce)
+            const int64_t pslice_len = (n_pts + n_slices - 1) / n_slices;
+            k_node_sens_near<<<dim3((unsigned)ntile, (unsigned)nr, (unsigned)n_slices), SG_NT, 0, s>>>(
+                N, nr, h->upos, h->unrm, h->uw, x, n_pts, dpt, dcE, dcH, h->k[0], iwmu, hs, hn, pslice_len, part);
             CKL("k_node_sens_near");
+            k_node_sens_near_reduce<<<(unsigned)((nr * N * 7 + 255) / 256), 256, 0, s>>>(N, nr, n_slices, part, sens);
+            CKL("k_node_sens_near_reduce");
         }
         run_vertex_shape_grad(h, nr, x, lam, sens, hs, dout, s);
         CK(cudaMemcpyAsync(out_host, dout, sizeof(c64) * 3 * N * nr, cudaMemcpyDeviceToHost, s));

@@ -114,6 +114,24 @@ def test_solve_mixed_precision_refinement():
     assert rel(x.cpu().numpy(), xo) < SOLVE_TOL
 
 
+@pytest.mark.parametrize("sp", [fm.FP64, fm.FP32])
+def test_solve_batch_with_zero_and_repeated_right_hand_sides(sp):
+    """A batch holding a plane wave, a zero right-hand side and the same plane wave again: the zero
+    one is solved by x = 0 at once (its Krylov space is empty: the Arnoldi step freezes it), the two
+    equal ones take the same iterates (independent Krylov spaces), and all agree with the
+    single-RHS solve; plain FP64 and FP32-inner refined solves."""
+    o, g = case(fi.icosphere(4), [1.0, 2.25], [1.0, 1.0], 1.0, solve_precision=sp)
+    b1 = o.plane_wave_rhs([0, 0, 1.0], [1.0, 0, 0])
+    b = np.concatenate([b1, np.zeros_like(b1), b1])
+    x, its, res, st = g.solve(to_dev(b), tol=1e-6)
+    x = x.cpu().numpy()
+    assert st == 0 and np.all(res <= 1e-6), (st, res)
+    assert res[1] == 0 and not np.any(x[1])
+    assert rel(x[2], x[0]) < 1e-12
+    x1, _, _, _ = g.solve(to_dev(b1), tol=1e-6)
+    assert rel(x[0], x1.cpu().numpy()[0]) < 1e-5
+
+
 # small leaves put more of the operator into the expansions, so they need a larger p for 1e-4
 @pytest.mark.parametrize("opt", [dict(node_mode=1), dict(p=4), dict(p=12), dict(leaf_size=8, p=10),
                                  dict(leaf_size=400)])
