@@ -2376,7 +2376,8 @@ union AdjSmem {
 };
 
 // near field, L2P (value and gradient), assembly and the transposed self block for one leaf;
-// threads split as (target, source slice) like k_near, both domains one after the other
+// threads split as (target, source slice) like k_near, both domains one after the other; grid
+// (leaf, right-hand side)
 template <typename R, bool DOUBLE_FLOAT>
 __global__ void __launch_bounds__(128) k_near_adj(const int32_t *leaf_box, int64_t N, int64_t nr, int p2, int64_t nbox,
                                                   const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
@@ -2404,7 +2405,7 @@ __global__ void __launch_bounds__(128) k_near_adj(const int32_t *leaf_box, int64
     __syncthreads();
     const int nsrc = rng_cum[nnb];
     const int t0 = nbeg[g], t1 = nend[g], NT = t1 - t0;
-    for (int64_t r = 0; r < nr; ++r) {
+    for (int64_t r = blockIdx.y; r < nr; r += gridDim.y) {  // right-hand sides across the grid
         for (int tb = t0; tb < t1; tb += 128) {
             const int nt = min(128, t1 - tb);
             const int nsl = 128 / nt;
@@ -3469,12 +3470,12 @@ static void adjoint_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_
     const R *pl = f32 ? (const R *)h->pos_lo : nullptr;
     const V4<R> *cache = f32 ? nullptr : (const V4<R> *)h->near_cache64;
     if constexpr (sizeof(R) == 4)
-        k_near_adj<R, true><<<(unsigned)h->n_leaves, 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+        k_near_adj<R, true><<<dim3((unsigned)h->n_leaves, (unsigned)std::min<int64_t>(nr, 65535)), 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                           h->nbr_start, h->nbr_idx, ph, pl, h->nrm, h->w, h->dom,
                                                           h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
                                                           h->near_base, cache);
     else
-        k_near_adj<R, false><<<(unsigned)h->n_leaves, 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
+        k_near_adj<R, false><<<dim3((unsigned)h->n_leaves, (unsigned)std::min<int64_t>(nr, 65535)), 128, 0, s>>>(h->leaf_box, N, nr, p2, h->nbox, h->box_nbeg, h->box_nend,
                                                            h->nbr_start, h->nbr_idx, ph, pl, h->nrm, h->w, h->dom,
                                                            h->perm, dens, dc, Bl2p, Bl2pg, D, h->Mself, x, y,
                                                            h->near_base, cache);
