@@ -342,7 +342,8 @@ void build_tc_tables(fmbem *h, cudaStream_t s);
 void run_m2l_tc(fmbem *h, float *C, float *D, int64_t nr, cudaStream_t s, bool bf3, bool c_split = false);
 void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s, bool leaves_split = false);
 bool p2m_tc_supported(const fmbem *h, int64_t nr);
-void run_p2m_tc(fmbem *h, const float *dens, const float *Bp2m, float *C, int64_t nr, cudaStream_t s);
+void run_p2m_tc(fmbem *h, const float *dens, const float4 *densS, const float *Bp2m, float *C, int64_t nr,
+                cudaStream_t s);
 bool m2l_ofs_supported(const fmbem *h);
 void build_ofs_tables(fmbem *h, cudaStream_t s);
 void split_expansions_bf16(fmbem *h, float *C, int64_t nr, cudaStream_t s);

@@ -66,6 +66,38 @@ __global__ void k_prep(int64_t N, int64_t nr, const c64 *x, const int32_t *perm,
     prep_body<R>(N, nr, x, perm, nrm, w, dom, dc, dens, blockIdx.x, blockIdx.y, sj);
 }
 
+// The single-precision densities straight into the node-major layout below (k_dens_node_major's
+// densS), for 32 k right-hand sides whose every consumer reads that layout (k_near_r, and P2M on
+// the tensor cores, which forms the scatterer side from v_1 = v_0 + s n, q_1 = -gamma_j q_0):
+// block = 8 nodes x 32 right-hand sides, lane = right-hand side, so that each warp stores one
+// node's 2 KB row whole; arithmetic as in prep_body<float>
+__global__ void __launch_bounds__(256) k_prep_node_major(int64_t N, int64_t nr, const c64 *x, const int32_t *perm,
+                                                         const double *nrm, const double *w, const int32_t *dom,
+                                                         const DomainConsts *dc, float4 *densS) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), rb = blockIdx.y;
+    if (i >= N) return;
+    const int64_t r = rb * 32 + lane;
+    const c64 *xi = x + (r * N + perm[i]) * 6;
+    const float n[3] = {(float)nrm[3 * i], (float)nrm[3 * i + 1], (float)nrm[3 * i + 2]};
+    const float wi = (float)w[i];
+    const cx<float> Phi[3] = {to<float>(xi[0]), to<float>(xi[1]), to<float>(xi[2])};
+    const cx<float> Psi[3] = {to<float>(xi[3]), to<float>(xi[4]), to<float>(xi[5])};
+    const cx<float> nP = n[0] * Phi[0] + n[1] * Phi[1] + n[2] * Phi[2];
+    const cx<float> tn = to<float>(dc[dom[i]].t) * nP;
+    cx<float> v[3], q[3];
+    for (int c = 0; c < 3; ++c) {
+        v[c] = wi * Phi[c];
+        q[c] = (-wi) * Psi[c];
+    }
+    const cx<float> sj = wi * tn;  // n . (v_1 - v_0)
+    float4 *o = densS + ((rb * N + i) * 32 + lane) * 4;
+    o[0] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+    o[1] = make_float4(v[2].re, v[2].im, q[0].re, q[0].im);
+    o[2] = make_float4(q[1].re, q[1].im, q[2].re, q[2].im);
+    o[3] = make_float4(sj.re, sj.im, 0.f, 0.f);
+}
+
 // The single-precision densities node-major within blocks of 32 right-hand sides, for the
 // lane-per-RHS near field (a source's 32 right-hand sides are contiguous):
 // densS[block][node][32][4 float4] = (v0x, v0y), (v0z, q0x), (q0y, q0z), (s, 0) of the background
@@ -3320,21 +3352,32 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
     // and with fewer than 4, the normal jump s of the densities (k_near_ws) in the same place
     cx<R> *sj = f32 && nr < 4 ? dens + 2 * nr * N * 6 : nullptr;
     if (h->ibc) clear_unused_domains(h, nr, sizeof(R), s);
-    k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens, sj);
-    CKL("k_prep");
-    if (densT != nullptr) {
-        k_dens_node_major<<<dim3((unsigned)((N + 15) / 16), (unsigned)(nrT / 32)), 256, 0, s>>>(
-            N, nr, (const float4 *)dens, h->src_rec, (float4 *)densT);
-        CKL("k_dens_node_major");
-    }
-    const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
-    constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
     // BF16x3 with many columns: P2M and M2M on the tensor cores as well (their products then leave
     // C split for M2L); otherwise on the CUDA cores
     const bool tc_up = f32 && tensor_mode == 2 && h->Mmbf != nullptr && 3 * nr >= 48;
     const bool tc_p2m = tc_up && p2m_tc_supported(h, nr);
+    // whole blocks of 32 right-hand sides with P2M on the tensor cores: every consumer reads the
+    // node-major densities, which are then the only ones formed
+    const bool node_major_only = tc_p2m && nrT == nr;
+    if (node_major_only) {
+        k_prep_node_major<<<dim3((unsigned)((N + 7) / 8), (unsigned)(nr / 32)), 256, 0, s>>>(
+            N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, (float4 *)densT);
+        CKL("k_prep_node_major");
+    } else {
+        k_prep<R><<<dim3(nblk(N, 128), (unsigned)nr), 128, 0, s>>>(N, nr, x, h->perm, h->nrm, h->w, h->dom, dc, dens,
+                                                                    sj);
+        CKL("k_prep");
+        if (densT != nullptr) {
+            k_dens_node_major<<<dim3((unsigned)((N + 15) / 16), (unsigned)(nrT / 32)), 256, 0, s>>>(
+                N, nr, (const float4 *)dens, h->src_rec, (float4 *)densT);
+            CKL("k_dens_node_major");
+        }
+    }
+    const int tbc = std::min(256, ((p2 + 31) / 32) * 32);
+    constexpr int P2M_RB = sizeof(R) == 4 ? 8 : 4;
     if (tc_p2m) {
-        run_p2m_tc(h, (const float *)dens, (const float *)Bp2m, (float *)C, nr, s);
+        run_p2m_tc(h, (const float *)dens, node_major_only ? (const float4 *)densT : nullptr, (const float *)Bp2m,
+                   (float *)C, nr, s);
     } else if (nr >= 16) {
         constexpr int MT = p2m_mt<R>(), PT = p2m_pt<R>();
         const int nthr = ((p2 + 2 * PT - 1) / (2 * PT)) * (MT / 4);

@@ -479,8 +479,8 @@ __device__ __forceinline__ void split8_bf16(const float *v, uint4 &hi, uint4 &lo
 __global__ void __launch_bounds__(P2M_TC_THREADS, 2)
     k_p2m_tc(const P2mTc P, const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ nbeg,
              const int32_t *__restrict__ nend, const int32_t *__restrict__ dom, const float *__restrict__ nrm,
-             const float2 *__restrict__ dens, const float2 *__restrict__ Bp2m, float *C, __nv_bfloat16 *Ch,
-             __nv_bfloat16 *Cl, int *err) {
+             const float2 *__restrict__ dens, const float4 *__restrict__ densS, const c64 *__restrict__ dcons,
+             const float2 *__restrict__ Bp2m, float *C, __nv_bfloat16 *Ch, __nv_bfloat16 *Cl, int *err) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t empty[P2M_TC_STAGES], done;
     __shared__ uint32_t tmem_slot;
@@ -530,10 +530,15 @@ __global__ void __launch_bounds__(P2M_TC_THREADS, 2)
     const int il_b = threadIdx.x & 3, rl = threadIdx.x >> 2;
     const bool b_item = rl < P.nt / 3 && 3 * rl < nh;
     const int64_t r_b = col0 / 3 + rl;
+    // densS (node-major densities [block of 32 RHS][node][RHS][(v_0, q_0, s) as 4 float4]) when
+    // given, else dens [side][RHS][node][(v, q)]: the scatterer side from v_1 = v_0 + s n and
+    // q_1 = -gamma_d q_0
+    const cx<float> gam = d > 0 && densS ? to<float>(dcons[3 * d + 2]) : cx<float>{0.f, 0.f};
     struct In {
         float2 a[2][4];  // B_k(i, q0), B_k(i, q0 + 32)
         int dom_a, dom_b;
         float2 b[6];     // the densities (v, q) of node il_b, right-hand side r_b
+        float2 sj;       // with densS: s = n . (v_1 - v_0)
         float n[3];
     };
     auto load = [&](In &x, int kb) {
@@ -555,9 +560,21 @@ __global__ void __launch_bounds__(P2M_TC_THREADS, 2)
         }
         if (b_item && ibn < i1) {
             x.dom_b = dom[ibn];
-            const float2 *dn = dens + (((int64_t)side * P.nr + r_b) * P.N + ibn) * 6;
+            if (densS) {
+                const float4 *o = densS + (((r_b >> 5) * P.N + ibn) * 32 + (r_b & 31)) * 4;
+                const float4 o0 = o[0], o1 = o[1], o2 = o[2], o3 = o[3];
+                x.b[0] = make_float2(o0.x, o0.y);
+                x.b[1] = make_float2(o0.z, o0.w);
+                x.b[2] = make_float2(o1.x, o1.y);
+                x.b[3] = make_float2(o1.z, o1.w);
+                x.b[4] = make_float2(o2.x, o2.y);
+                x.b[5] = make_float2(o2.z, o2.w);
+                x.sj = make_float2(o3.x, o3.y);
+            } else {
+                const float2 *dn = dens + (((int64_t)side * P.nr + r_b) * P.N + ibn) * 6;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) x.b[c] = dn[c];
+                for (int c = 0; c < 6; ++c) x.b[c] = dn[c];
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) x.n[c] = nrm[3 * ibn + c];
         }
@@ -601,7 +618,18 @@ __global__ void __launch_bounds__(P2M_TC_THREADS, 2)
         if (rl < P.nt / 3) {
             float w[3][8];
             if (cur.dom_b >= 0 && (d == 0 || cur.dom_b == d)) {
-                const float2 *v = cur.b;
+                float2 v[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[c] = cur.b[c];
+                if (densS && d > 0) {  // scatterer side from the background's
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        v[c].x += cur.sj.x * cur.n[c];
+                        v[c].y += cur.sj.y * cur.n[c];
+                        const float2 q0 = cur.b[3 + c];
+                        v[3 + c] = make_float2(-(gam.re * q0.x - gam.im * q0.y), -(gam.re * q0.y + gam.im * q0.x));
+                    }
+                }
                 const float n[3] = {sg * cur.n[0], sg * cur.n[1], sg * cur.n[2]};
                 const float nvr = n[0] * v[0].x + n[1] * v[1].x + n[2] * v[2].x;
                 const float nvi = n[0] * v[0].y + n[1] * v[1].y + n[2] * v[2].y;
@@ -1159,10 +1187,12 @@ void run_m2m_tc(fmbem *h, float *C, int64_t nr, cudaStream_t s, bool leaves_spli
 
 // P2M of the leaves on the tensor cores (k_p2m_tc): BF16x3, 2 p^2 <= 128, 16 or more right-hand
 // sides; the second half of C receives the bf16 hi / lo split of the leaves' expansions (run_m2m_tc
-// with leaves_split)
+// with leaves_split).  The densities come from dens, or from the node-major densS when it is given
+// (whole blocks of 32 right-hand sides, dens then unused)
 bool p2m_tc_supported(const fmbem *h, int64_t nr) { return 2 * h->p2 <= TC_M && nr >= 16; }
 
-void run_p2m_tc(fmbem *h, const float *dens, const float *Bp2m, float *C, int64_t nr, cudaStream_t s) {
+void run_p2m_tc(fmbem *h, const float *dens, const float4 *densS, const float *Bp2m, float *C, int64_t nr,
+                cudaStream_t s) {
     if (!p2m_tc_supported(h, nr)) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "tensor-core P2M: unsupported shape"};
     if (!h->tc_err) throw fmbem_error{FMBEM_ERR_CUDA, "tensor-core P2M: the error flag was not allocated"};
     const int64_t ncols = 3 * nr;
@@ -1182,8 +1212,8 @@ void run_p2m_tc(fmbem *h, const float *dens, const float *Bp2m, float *C, int64_
     const dim3 grid((unsigned)(h->n_leaves * ntile), (unsigned)(h->Jf + 1));
     // the FP32 copy of the leaves' expansions is not written: M2M and M2L read the split
     k_p2m_tc<<<grid, P2M_TC_THREADS, smem, s>>>(P, h->leaf_box, h->box_nbeg, h->box_nend, h->dom, h->nrm_f,
-                                                (const float2 *)dens, (const float2 *)Bp2m, nullptr, Chi, Clo,
-                                                h->tc_err);
+                                                (const float2 *)dens, densS, (const c64 *)h->dcons,
+                                                (const float2 *)Bp2m, nullptr, Chi, Clo, h->tc_err);
     CKL("k_p2m_tc");
 }
 

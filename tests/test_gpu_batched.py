@@ -33,12 +33,14 @@ def to_dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
 
 
-@pytest.mark.parametrize("n_rhs,p", [(16, 8), (100, 8), (40, 6), (24, 4)])
+@pytest.mark.parametrize("n_rhs,p", [(16, 8), (100, 8), (40, 6), (24, 4), (64, 8), (32, 6)])
 def test_bf16x3_tensor_core_m2l_matches_fp32(n_rhs, p):
     """The BF16x3 tensor-core passes (hi/lo bf16 operands, three products per step: P2M of the
     leaves with 48-, 96-, 144- and 192-column tiles, the last one ragged at 100 RHS; M2M; M2L +
     L2L) on the cases of the TF32 test (one 48-column tile, two ragged 160-column tiles, p = 6 with
-    a partial last K block, p = 4): it must agree with the FP32 CUDA-core product to ~1e-5 (the
+    a partial last K block, p = 4) and on whole blocks of 32 right-hand sides (64 and 32, where the
+    densities are formed only node-major and P2M forms the scatterer side from the background's):
+    it must agree with the FP32 CUDA-core product to ~1e-5 (the
     split leaves ~2^-16 per product where TF32 leaves ~2^-11), be deterministic, and match the
     oracle rows."""
     V, F, D = fi.icosphere(5)  # 10242 nodes, l_max 3: both S|R and R|R products
