@@ -50,18 +50,25 @@ void run_matvec_host(fmbem *h, const c64 *x_host, c64 *y_host, int64_t nr, int p
                            cudaMemcpyHostToDevice, up));
         CK(cudaEventRecord(copied_in[q], up));
     };
-    copy_in(0);
-    for (int64_t k = 0; k < nchunk; ++k) {
-        const int q = (int)(k & 1);
-        if (k + 1 < nchunk) copy_in(k + 1);
-        CK(cudaStreamWaitEvent(s, copied_in[q], 0));
-        if (k >= 2) CK(cudaStreamWaitEvent(s, copied_out[q], 0));  // chunk k - 2's result is out
-        run_matvec(h, xs[q], ys[q], rhs_of(k), precision, s);
-        CK(cudaEventRecord(computed[q], s));
-        CK(cudaStreamWaitEvent(down, computed[q], 0));
-        CK(cudaMemcpyAsync(y_host + k * chunk * per_rhs, ys[q], sizeof(c64) * rhs_of(k) * per_rhs,
-                           cudaMemcpyDeviceToHost, down));
-        CK(cudaEventRecord(copied_out[q], down));
+    try {
+        copy_in(0);
+        for (int64_t k = 0; k < nchunk; ++k) {
+            const int q = (int)(k & 1);
+            if (k + 1 < nchunk) copy_in(k + 1);
+            CK(cudaStreamWaitEvent(s, copied_in[q], 0));
+            if (k >= 2) CK(cudaStreamWaitEvent(s, copied_out[q], 0));  // chunk k - 2's result is out
+            run_matvec(h, xs[q], ys[q], rhs_of(k), precision, s);
+            CK(cudaEventRecord(computed[q], s));
+            CK(cudaStreamWaitEvent(down, computed[q], 0));
+            CK(cudaMemcpyAsync(y_host + k * chunk * per_rhs, ys[q], sizeof(c64) * rhs_of(k) * per_rhs,
+                               cudaMemcpyDeviceToHost, down));
+            CK(cudaEventRecord(copied_out[q], down));
+        }
+    } catch (...) {
+        // a failed product: no copy may still touch the caller's host buffers after the return
+        cudaStreamSynchronize(up);
+        cudaStreamSynchronize(down);
+        throw;
     }
     // s waits for the last copy back (the copies back run in order on their stream)
     CK(cudaStreamWaitEvent(s, copied_out[(nchunk - 1) & 1], 0));
