@@ -56,6 +56,8 @@ static void free_all(fmbem *h) {
     if (h->aux_stream) { cudaStreamDestroy(h->aux_stream); h->aux_stream = nullptr; }
     for (auto &e : h->io_ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (auto &e : h->io_rows.ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
     for (auto &st : h->io_stream)
         if (st) { cudaStreamDestroy(st); st = nullptr; }
     h->io_buf = nullptr;  // freed with the allocations above

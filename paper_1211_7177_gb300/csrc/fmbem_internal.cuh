@@ -246,6 +246,12 @@ struct fmbem {
     bool have_times = false;
     // host-buffer products (fmbem_matvec_host): copy streams (to and from the device), their
     // events, and the chunk buffers (two x slots, two y slots)
+    struct IoRows {
+        c64 *y_host = nullptr;    // set for one product: its rows go back slab by slab
+        cudaStream_t down = nullptr;
+        cudaEvent_t ev[16] = {};  // one per slab of 32 right-hand sides
+        bool copied = false;      // the product copied its rows back itself
+    } io_rows;
     cudaStream_t io_stream[2] = {nullptr, nullptr};
     cudaEvent_t io_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void *io_buf = nullptr;

@@ -2016,7 +2016,7 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 3) k_near_r(
     int64_t nr, bool side1, const int32_t *nbeg, const int32_t *nend, const int32_t *nbr_start,
     const int32_t *nbr_idx, const float4 *__restrict__ rec, const float4 *densS, const DomainConsts *dc,
     const int32_t *perm, int p2, int64_t nbox, const cx<float> *__restrict__ Bl2p, const cx<float> *__restrict__ D,
-    const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y) {
+    const c64 *__restrict__ Mself, const c64 *__restrict__ x, c64 *y, int slab0, int slab_lf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int rng_beg[NR_WARPS][32], rng_cum[NR_WARPS][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2028,11 +2028,12 @@ __global__ void __launch_bounds__(32 * NR_WARPS, 3) k_near_r(
         if (lane == 0) unit = atomicAdd(next_unit, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= n_units) break;
-        // slabs of 32 right-hand sides; the last one takes its groups longest first
-        const int slab = unit / n_groups, grp = unit - slab * n_groups;
+        // slabs of 32 right-hand sides from slab0 on; the launch's last one (slab_lf) takes its
+        // groups longest first
+        const int slab = slab0 + unit / n_groups, grp = unit - (slab - slab0) * n_groups;
         const int64_t r = (int64_t)slab * 32 + lane;  // this lane's right-hand side
         __syncwarp();  // the previous unit's shared-memory reads are done
-        const int4 gi = groups[slab == (int)(nr / 32) - 1 ? n_groups + grp : grp];
+        const int4 gi = groups[slab == slab_lf ? n_groups + grp : grp];
         const int leaf = gi.x, ntg = gi.z;
         const int64_t g = leaf_box[leaf];
         const int tbase = nbeg[g] + gi.y;
@@ -3427,9 +3428,9 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
             (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
         CKL("k_near_w");
     };
-    // k_near_r over the right-hand sides 0 .. 32 nblk - 1
-    auto launch_r = [&](int64_t nblk) {
-        const int64_t units = (int64_t)h->n_near_groups * nblk;
+    // k_near_r over the right-hand sides 32 slab0 .. 32 (slab0 + nslab) - 1
+    auto launch_r = [&](int64_t slab0, int64_t nslab) {
+        const int64_t units = (int64_t)h->n_near_groups * nslab;
         if (units >= INT32_MAX) throw fmbem_error{FMBEM_ERR_INVALID_ARGUMENT, "too many near-field work units"};
         const size_t smr = sizeof(RhsTile) * NR_WARPS;
         CK(cudaFuncSetAttribute(k_near_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
@@ -3441,13 +3442,30 @@ static void matvec_impl(fmbem *h, const c64 *x, c64 *y, int64_t nr, cudaStream_t
         k_near_r<<<(unsigned)grid, 32 * NR_WARPS, smr, s>>>(
             h->leaf_box, h->near_groups, h->n_near_groups, (int)units, h->near_next, N, nr, nsides == 2, h->box_nbeg,
             h->box_nend, h->nbr_start, h->nbr_idx, h->src_rec, (const float4 *)densT, dc, h->perm, p2, h->nbox,
-            (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y);
+            (const cx<float> *)Bl2p, (const cx<float> *)D, h->Mself, x, y, (int)slab0, (int)(slab0 + nslab - 1));
         CKL("k_near_r");
     };
     if constexpr (sizeof(R) == 4) {
         if (nr >= 4) {  // whole blocks of 32 right-hand sides one per lane, the rest by k_near_w
             const int64_t nblk = nr / 32, rest = nr - 32 * nblk;
-            if (nblk > 0) launch_r(nblk);
+            // a host-buffer product (fmbem_matvec_host) whose rows are final after the near field:
+            // one launch per slab, each slab's rows copied back beside the next slab's launch
+            auto &io = h->io_rows;
+            const bool per_slab = io.y_host != nullptr && nblk > 1 && rest == 0 && !h->ibc && h->ns_pairs <= 0 &&
+                                  nblk <= (int64_t)(sizeof(io.ev) / sizeof(io.ev[0]));
+            if (per_slab) {
+                for (int64_t b = 0; b < nblk; ++b) {
+                    launch_r(b, 1);
+                    CK(cudaEventRecord(io.ev[b], s));
+                    CK(cudaStreamWaitEvent(io.down, io.ev[b], 0));
+                    const int64_t off = b * 32 * N * 6;
+                    CK(cudaMemcpyAsync(io.y_host + off, y + off, sizeof(c64) * 32 * N * 6, cudaMemcpyDeviceToHost,
+                                       io.down));
+                }
+                io.copied = true;
+            } else if (nblk > 0) {
+                launch_r(0, nblk);
+            }
             if (rest >= 8) launch_w(k_near_w<8>, 8, sizeof(WarpTile<8>), 32 * nblk);
             else if (rest > 0) launch_w(k_near_w<4>, 4, sizeof(WarpTile<4>), 32 * nblk);
         } else {  // few right-hand sides: both sides of a pair in one pass, one unit per item and RHS

@@ -4,7 +4,9 @@
 // multiplied on the caller's stream (run_matvec, every kernel of the device product) and copied
 // back on a second copy stream, so that the copy of chunk k + 1 to the device and of chunk k - 1
 // back run while chunk k is multiplied.  Two x slots and two y slots of chunk size alternate;
-// events order each slot's reuse after the work that still reads it.  With pinned host memory
+// events order each slot's reuse after the work that still reads it.  In single precision with
+// whole blocks of 32 right-hand sides the product itself copies its rows back per block, right
+// after the near-field launch that finishes them (h->io_rows).  With pinned host memory
 // the copies run at the link's rate beside the kernels; with pageable memory the driver stages
 // them and they do not overlap.
 #include <algorithm>
@@ -30,6 +32,8 @@ void run_matvec_host(fmbem *h, const c64 *x_host, c64 *y_host, int64_t nr, int p
     for (auto &st : h->io_stream)
         if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     for (auto &e : h->io_ev)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto &e : h->io_rows.ev)
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     cudaStream_t up = h->io_stream[0], down = h->io_stream[1];
     cudaEvent_t start = h->io_ev[0], *copied_in = h->io_ev + 1, *computed = h->io_ev + 3, *copied_out = h->io_ev + 5;
@@ -57,15 +61,25 @@ void run_matvec_host(fmbem *h, const c64 *x_host, c64 *y_host, int64_t nr, int p
             if (k + 1 < nchunk) copy_in(k + 1);
             CK(cudaStreamWaitEvent(s, copied_in[q], 0));
             if (k >= 2) CK(cudaStreamWaitEvent(s, copied_out[q], 0));  // chunk k - 2's result is out
+            // the product may copy its rows back itself, slab by slab as the near field finishes
+            // them (single precision, whole blocks of 32 right-hand sides, rows final after the
+            // near field): then the copy of the first slabs overlaps the near field of the last
+            h->io_rows.y_host = y_host + k * chunk * per_rhs;
+            h->io_rows.down = down;
+            h->io_rows.copied = false;
             run_matvec(h, xs[q], ys[q], rhs_of(k), precision, s);
+            h->io_rows.y_host = nullptr;
             CK(cudaEventRecord(computed[q], s));
-            CK(cudaStreamWaitEvent(down, computed[q], 0));
-            CK(cudaMemcpyAsync(y_host + k * chunk * per_rhs, ys[q], sizeof(c64) * rhs_of(k) * per_rhs,
-                               cudaMemcpyDeviceToHost, down));
+            if (!h->io_rows.copied) {
+                CK(cudaStreamWaitEvent(down, computed[q], 0));
+                CK(cudaMemcpyAsync(y_host + k * chunk * per_rhs, ys[q], sizeof(c64) * rhs_of(k) * per_rhs,
+                                   cudaMemcpyDeviceToHost, down));
+            }
             CK(cudaEventRecord(copied_out[q], down));
         }
     } catch (...) {
         // a failed product: no copy may still touch the caller's host buffers after the return
+        h->io_rows.y_host = nullptr;
         cudaStreamSynchronize(up);
         cudaStreamSynchronize(down);
         throw;

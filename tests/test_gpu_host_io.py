@@ -1,6 +1,7 @@
 """The host-buffer product fmbem_matvec_host: x and y in host memory, the right-hand sides in
 chunks whose copies to and from the device run on two copy streams beside the products of the
-neighbouring chunks.  Every chunk runs exactly the kernels of fmbem_matvec on that many
+neighbouring chunks (and, in single precision with two or more whole blocks of 32 right-hand
+sides per chunk, the rows of each block copied back as soon as its near-field launch ends).  Every chunk runs exactly the kernels of fmbem_matvec on that many
 right-hand sides, so each chunk of the result must equal fmbem_matvec of that chunk bit for bit
 (FP64 and BF16x3, pinned and pageable host memory, ragged last chunk, more chunks than the two
 buffer slots), and the whole product must match the oracle on sampled rows."""
@@ -30,7 +31,8 @@ def sphere():
 
 @pytest.mark.parametrize("nr,chunk,prec,pinned", [(5, 2, fm.FP64, True), (5, 2, fm.FP64, False),
                                                    (40, 16, fm.BF16X3, True), (64, 32, fm.FP32, True),
-                                                   (3, 0, fm.FP64, True)])
+                                                   (3, 0, fm.FP64, True), (64, 0, fm.FP32, True),
+                                                   (96, 0, fm.BF16X3, True), (192, 96, fm.BF16X3, False)])
 def test_host_product_equals_device_product_per_chunk(sphere, nr, chunk, prec, pinned):
     _, g = sphere
     x = torch.from_numpy(fi.random_complex((nr, g.N, 6), seed=nr))
