@@ -95,6 +95,28 @@ def test_adaptive_matvec_matches_oracle(ring):
             assert per_row.max() < 30 * TOL, (nr, prec, per_row.max())
 
 
+@pytest.mark.parametrize("nr", [32, 40])
+def test_adaptive_tensor_core_passes(nr):
+    """p = 8 on the adaptive tree with many right-hand sides: P2M of leaves on several levels and
+    M2M (a box without children keeps its P2M expansion) on the tensor cores in the BF16x3 form,
+    with the densities node-major only (32 RHS) or in both layouts (40 RHS); against the FP32
+    product and the oracle's rows."""
+    V, F, D = fi.split_ring(1.0, 0.2, 10.0, 120, 6, grading=1.5)
+    eps, mu, k0 = [1.0, 2.25], [1.0, 1.0], 1.0
+    o = oracle.Oracle(V, F, D, eps, mu, k0)
+    g = fm.FMBEM(V, F, D, eps, mu, k0, p=8, adaptive=1, leaf_size=32)
+    assert np.count_nonzero(g.tree_levels()[1]) >= 2
+    x = fi.random_complex((nr, o.N, 6), seed=nr)
+    yb = g.matvec(to_dev(x), precision=fm.BF16X3).cpu().numpy()
+    y32 = g.matvec(to_dev(x), precision=fm.FP32).cpu().numpy()
+    rows = fi.sample_rows(o.N, 96, seed=5)
+    e32, eo = rel(yb, y32), rel(yb[:, rows], o.matvec_rows(x, rows))
+    print(f"adaptive p = 8, {nr} RHS: BF16x3 vs FP32 {e32:.2e}, vs oracle rows {eo:.2e}")
+    assert e32 < 2e-5
+    assert eo < TOL
+    g.close()
+
+
 def test_adaptive_adjoint_matches_oracle_transpose(ring):
     _, o, ga, _, _ = ring
     x = fi.random_complex((2, o.N, 6), seed=7)
