@@ -303,18 +303,32 @@ def tensor_path(nr):
     return 3 * nr >= 48
 
 
-def launches_per_matvec(lmax, nr, n_dom, precision):
-    """Kernels per matvec: k_prep, P2M, k_m2m per level 3..l_max, the downward pass per level
-    2..l_max (tensor path: k_round_tf32 then one k_m2l_tc per level; chunked: k_m2l_chunks or
-    k_m2l_rot plus k_l2l_reduce per domain; many columns: k_m2l_multi), and the near field
-    (one kernel: k_near_w in single precision with at least 4 right-hand sides, else k_near*)."""
-    if precision == "tf32" and tensor_path(nr):
-        down = 1 + (lmax - 1)
-    elif 3 * nr <= 24:
-        down = (lmax - 1) * 2 * n_dom
+def launches_per_matvec(lmax, nr, n_dom, precision, p, rotation):
+    """Kernels per matvec of the main line's path, as the ncu launch lists under profiles/ show
+    them (every domain of a level in one launch):
+    - tensor-core path (BF16x3 or TF32, 16 or more RHS, p <= 8): the densities (k_prep_node_major
+      for whole blocks of 32 RHS in BF16x3, else k_prep, plus k_dens_node_major when there are
+      32 or more), P2M (k_p2m_tc in BF16x3, k_p2m_gemm in TF32), M2M per level 3..l_max
+      (k_m2l_tc in BF16x3; k_m2m on the CUDA cores in TF32), k_round_tf32 (TF32), one k_m2l_tc per
+      level 2..l_max, and the near field (k_near_r per whole block launch, k_near_w for the rest);
+    - otherwise k_prep and P2M; M2M per level 3..l_max (the rotation form: k_m2l_rot* + k_mm_reduce;
+      dense: k_m2m); the downward pass: BF16x3 with at most 8 RHS: k_split_bf16, two k_m2l_ofs
+      launches and per level a k_l2l_reduce (with a rotation-form L2L on levels 3..l_max);
+      else per level a k_l2l_reduce after the M2L (k_m2l_rot* or k_m2l_chunks), with the L2L
+      translation as its own launch on levels 3..l_max in the rotation form; one near-field
+      kernel."""
+    near = 1
+    if precision in ("bf16x3", "tf32") and tensor_path(nr) and p <= 8:
+        bf3 = precision == "bf16x3"
+        prep = 1 if (bf3 and nr % 32 == 0) else (2 if nr >= 32 else 1)
+        near = (1 if nr >= 32 else 0) + (1 if nr % 32 else 0)
+        return prep + 1 + (lmax - 2) + (0 if bf3 else 1) + (lmax - 1) + near
+    m2m = 2 * (lmax - 2) if rotation else (lmax - 2)
+    if precision == "bf16x3" and 3 * nr <= 24:
+        down = 1 + 2 + 1 + (2 if rotation else 1) * (lmax - 2)
     else:
-        down = lmax - 1
-    return 2 + (lmax - 2) + down + 1
+        down = 2 + (3 if rotation else 2) * (lmax - 2)
+    return 2 + m2m + down + near
 
 
 def run_gradients(fd_check=False):
@@ -910,7 +924,8 @@ def run_ours(args):
     if args.workload == "silver_sphere_s7" and not args.no_uneven:
         uneven = run_uneven_batch(args, world, flush)
 
-    launches_per_step = launches_per_matvec(info["l_max"], nr, n_dom, args.precision)
+    rotation = p >= 9  # the library's automatic translation form for the main line's handle
+    launches_per_step = launches_per_matvec(info["l_max"], nr, n_dom, args.precision, p, rotation)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype={"fp64": "f64", "fp32": "f32", "tf32": "f32 (M2L on TF32 tensor cores)",
