@@ -64,3 +64,17 @@ def test_host_product_arguments(sphere):
     with pytest.raises(fm.FMBEMError) as e:
         g.matvec_host(x, chunk_rhs=-1)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("opts", [dict(boundary=fm.IMPEDANCE), dict(near_singular_radius=1.0)])
+def test_host_product_with_rows_written_after_the_near_field(opts):
+    """The impedance rows (Eq. 2.24) and the near-singular corrections are written after the near
+    field, so their products copy the rows back whole: 64 RHS in single precision (two blocks of
+    32, which would otherwise go back block by block) must still equal the device product."""
+    V, F, D = fi.icosphere(3)
+    eps = [1.0, 1 + 1e4j] if opts.get("boundary") == fm.IMPEDANCE else [1.0, 2.25]
+    g = fm.FMBEM(V, F, D, eps, [1.0, 1.0], 1.0, p=8, **opts)
+    x = torch.from_numpy(fi.random_complex((64, g.N, 6), seed=5)).pin_memory()
+    y = g.matvec_host(x, precision=fm.FP32)
+    assert torch.equal(y, g.matvec(x.cuda(), precision=fm.FP32).cpu())
+    g.close()
