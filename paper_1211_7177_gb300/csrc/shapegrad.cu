@@ -298,7 +298,7 @@ __device__ c64 nf_val(const double *t, const double *s, double w, const double *
 __global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr, const double *pos,
                                                         const double *nrm, const double *w, const c64 *x,
                                                         int64_t n_pts, const double *pts, const c64 *cE,
-                                                        const c64 *cH, c64 k0, c64 iwmu, double hs, double hn,
+                                                        const c64 *cH, c64 k0, c64 iwmu, double hs,
                                                         int64_t pslice_len, c64 *part) {
     __shared__ double spt[SG_NS][3];
     __shared__ c64 sce[SG_NS][3], sch[SG_NS][3];
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr,
     }
     c64 acc[7];
     for (int q = 0; q < 7; ++q) acc[q] = {0, 0};
-    const double i2s = 1.0 / (2.0 * hs), i2n = 1.0 / (2.0 * hn);
+    const double i2s = 1.0 / (2.0 * hs);
     for (int64_t p0 = pb; p0 < pe; p0 += SG_NS) {
         const int np = (int)min((int64_t)SG_NS, pe - p0);
         __syncthreads();
@@ -330,19 +330,25 @@ __global__ void __launch_bounds__(SG_NT) k_node_sens_near(int64_t N, int64_t nr,
         if (!valid) continue;
         for (int e = 0; e < np; ++e) {
             const c64 *ch = cH ? sch[e] : nullptr;
+            // the functional is affine in the normal (the representation formula's kernel and its
+            // curl are linear in n), val(n) = val(0) + sum_c n_c dval/dn_c: the normal derivatives
+            // exactly from the unit normals, and the value from them
+            const double zero[3] = {0, 0, 0};
+            const c64 v0 = nf_val(spt[e], s, wu, zero, xu, k0, iwmu, sce[e], ch);
+            c64 val = v0;
             for (int c = 0; c < 3; ++c) {
+                double ec[3] = {0, 0, 0};
+                ec[c] = 1;
+                const c64 dn = nf_val(spt[e], s, wu, ec, xu, k0, iwmu, sce[e], ch) - v0;
+                acc[4 + c] += dn;
+                val += dn * n[c];
                 double sp_[3] = {s[0], s[1], s[2]}, sm[3] = {s[0], s[1], s[2]};
                 sp_[c] += hs;
                 sm[c] -= hs;
                 acc[c] += (nf_val(spt[e], sp_, wu, n, xu, k0, iwmu, sce[e], ch) -
                            nf_val(spt[e], sm, wu, n, xu, k0, iwmu, sce[e], ch)) * i2s;
-                double np_[3] = {n[0], n[1], n[2]}, nm[3] = {n[0], n[1], n[2]};
-                np_[c] += hn;
-                nm[c] -= hn;
-                acc[4 + c] += (nf_val(spt[e], s, wu, np_, xu, k0, iwmu, sce[e], ch) -
-                               nf_val(spt[e], s, wu, nm, xu, k0, iwmu, sce[e], ch)) * i2n;
             }
-            acc[3] += nf_val(spt[e], s, wu, n, xu, k0, iwmu, sce[e], ch) * (1.0 / wu);
+            acc[3] += val * (1.0 / wu);
         }
     }
     if (valid)
@@ -429,7 +435,7 @@ void run_shape_gradient(fmbem *h, const c64 *x, const c64 *lam, int64_t nr, cons
             // point slices into the partner-slice buffer (free again after k_node_sens_reduce)
             const int64_t pslice_len = (n_pts + n_slices - 1) / n_slices;
             k_node_sens_near<<<dim3((unsigned)ntile, (unsigned)nr, (unsigned)n_slices), SG_NT, 0, s>>>(
-                N, nr, h->upos, h->unrm, h->uw, x, n_pts, dpt, dcE, dcH, h->k[0], iwmu, hs, hn, pslice_len, part);
+                N, nr, h->upos, h->unrm, h->uw, x, n_pts, dpt, dcE, dcH, h->k[0], iwmu, hs, pslice_len, part);
             CKL("k_node_sens_near");
             k_node_sens_near_reduce<<<(unsigned)((nr * N * 7 + 255) / 256), 256, 0, s>>>(N, nr, n_slices, part, sens);
             CKL("k_node_sens_near_reduce");
